@@ -1,0 +1,159 @@
+/*
+ * tdvp.h -- C ABI of the B300 two-site TDVP engine for the open Fermi-Hubbard chain.
+ *
+ * The engine evolves a matrix product state (Eq. MPS, Sec. S2.2) of the open
+ * chain H = -J sum_{i,s} (c^dag_{i s} c_{i+1 s} + h.c.) + U sum_i n_{i up} n_{i dn}
+ * (Eq. FHM, Sec. 2) from the half-filled Neel state (Eq. neel, Sec. 2.1) with
+ * second-order two-site TDVP (Sec. S2.2), Krylov exponentials, per-sector SVD
+ * truncation on the truncated weight (Sec. S2.4), and U(1)xU(1) or U(1)xSU(2)
+ * block sparsity (Sec. S2.1, Eq. symdecomp).  All device work runs in this
+ * library's own kernels on one GPU; there is no CPU fallback.
+ *
+ * Conventions shared by every entry point
+ *   - Return value: 0 on success, a negative TDVP_E* code on failure; no C++
+ *     exception crosses this boundary.  tdvp_strerror() names a code and
+ *     tdvp_last_error() gives the message of the last failure on this thread.
+ *   - Complex numbers are interleaved FP64 pairs (re, im).
+ *   - The caller owns every array it passes in; the library owns the context
+ *     and every device buffer it allocates.  Calls on one context must be
+ *     serialised by the caller; several contexts may share a GPU.
+ *   - Sites are 0-indexed; site 0 starts with spin up (sublattice A = even).
+ *   - Internally the engine works in the particle-hole frame
+ *     c_{i dn} -> (-1)^i c^dag_{i dn}, where the charge SU(2) of Sec. S2.1 is the
+ *     ordinary spin SU(2).  Observables returned by tdvp_measure are converted
+ *     back to the frame of Eq. (FHM).  Block labels (n, t) exposed by the
+ *     block-query functions are in the engine frame: n = particle number to the
+ *     left of a bond, t = 2S (U1SU2) or 2S^z (U1U1).
+ */
+#ifndef TDVP_H_
+#define TDVP_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tdvp_ctx tdvp_ctx; /* opaque; owns all device state */
+
+enum { TDVP_SYM_U1U1 = 0, TDVP_SYM_U1SU2 = 1 };
+/* Precision of the block GEMMs.  FP64: CUDA-core FP64.  3XTF32 / BF16X3: split
+ * products on the tensor cores with FP32 accumulation (Lanczos, SVD and the
+ * recoupling coefficients stay FP64 in every mode). */
+enum { TDVP_PREC_FP64 = 0, TDVP_PREC_3XTF32 = 1, TDVP_PREC_BF16X3 = 2 };
+
+enum {
+  TDVP_OK = 0,
+  TDVP_EINVAL = -1,   /* invalid argument (L<2, chi_max<1, dt<=0, eps<0, bad sizes) */
+  TDVP_ESTATE = -2,   /* call not valid for this context */
+  TDVP_ENOMEM = -3,   /* device or host allocation failed */
+  TDVP_ENUMERIC = -4, /* an iteration did not converge or produced NaN */
+  TDVP_EINTERNAL = -5,/* inconsistent internal bookkeeping */
+  TDVP_ECUDA = -6,    /* a CUDA runtime call failed (including "no device") */
+  TDVP_ETIMEOUT = -7  /* a bounded device wait gave up */
+};
+
+typedef struct {
+  int precision;     /* TDVP_PREC_*; default FP64 */
+  int krylov_max;    /* maximal Krylov dimension, 1..32; default 20 */
+  double krylov_tol; /* stop when beta_k |[exp(-i tau T_k)]_{k,1}| < tol; default 1e-12 */
+  int timeout_ms;    /* reserved for bounded device waits; 0 = default */
+  void* cuda_stream; /* cudaStream_t to run on, or NULL for an engine-owned stream */
+  int device;        /* CUDA device ordinal, or -1 for the current device */
+} tdvp_opts;
+
+/* Fill *o with the defaults listed above. */
+void tdvp_opts_default(tdvp_opts* o);
+
+/* Create a chain of L sites (L >= 2, even for the Neel state at half filling)
+ * with hopping J and interaction U, symmetry TDVP_SYM_*, in the Neel state of
+ * Eq. (neel) (bond dimension 1).  opts may be NULL for the defaults.
+ * Errors: TDVP_EINVAL, TDVP_ENOMEM, TDVP_ECUDA. */
+int tdvp_create(int L, double J, double U, int symmetry, const tdvp_opts* opts, tdvp_ctx** out);
+
+/* One second-order two-site TDVP time step dt (Sec. S2.2): a left-to-right and a
+ * right-to-left half sweep with tau = dt/2.  After each two-site SVD the kept
+ * multiplets are the largest singular values (ties broken by sector, then
+ * index) such that the discarded weight sum s^2 stays <= eps_trunc * sum s^2
+ * and the U(1)-equivalent bond dimension sum d(2S+1) stays <= chi_max
+ * (Sec. S2.4); at least one multiplet is kept and the kept values are
+ * renormalised to unit norm.  Errors: TDVP_EINVAL (dt<=0, chi_max<1, eps<0),
+ * TDVP_ENUMERIC, TDVP_ECUDA, TDVP_ENOMEM. */
+int tdvp_step(tdvp_ctx* ctx, double dt, long long chi_max, double eps_trunc);
+
+/* Observables of the current state (Sec. 3, Figs. 1-2 use n_{i up}):
+ *   n[L]     <n_i>            sz[L]   <S^z_i> = (<n_{i up}> - <n_{i dn}>)/2
+ *   docc[L]  <n_{i up} n_{i dn}>
+ *   s_ent[L-1] von Neumann entropy (natural log) of the cut after site k
+ *   energy   <H> in the convention of Eq. (FHM)
+ * Any pointer may be NULL to skip that output (s_ent is the expensive one).
+ * n_{i up} = n_i/2 + S^z_i and n_{i dn} = n_i/2 - S^z_i.  Host pointers. */
+int tdvp_measure(tdvp_ctx* ctx, double* n, double* sz, double* docc, double* s_ent, double* energy);
+
+/* Bond dimensions of the L+1 bonds: chi[k] = sum d(2S+1) (U(1)-equivalent) and
+ * chi_red[k] = sum d (reduced); either may be NULL. */
+int tdvp_bond_dims(tdvp_ctx* ctx, long long* chi, long long* chi_red);
+
+/* Counters since creation: out[0] seconds in tdvp_step, out[1] effective
+ * Hamiltonian flops (algorithmic, 8 per complex multiply-add), out[2]
+ * environment-update flops, out[3] matvecs, out[4] largest Krylov dimension
+ * used, out[5] largest discarded weight, out[6] largest chi seen.  n = length of
+ * out (at most 7 are written). */
+int tdvp_stats(tdvp_ctx* ctx, double* out, int n);
+
+/* ---- single-bond problems (the effective-Hamiltonian benchmark) ------------
+ * tdvp_bond_create builds the two-site problem between a left bond and a right
+ * bond given as sector tables: nl (resp. nr) rows of int triples (n, t, d),
+ * n the particle number to the left of the bond, t = 2S (U1SU2) or 2S^z
+ * (U1U1), d >= 1 the degeneracy.  The two sites in between are bulk sites of
+ * Eq. (FHM) with the MPO channels
+ *   [B, c^dag(+1/2), c^dag(-1/2), c(+1/2), c(-1/2), E]
+ * (U1SU2: B (0,0), c^dag (+1, 2S=1), c (-1, 2S=1), E (0,0); U1U1: six singlets).
+ * The left environment L[a',w,a] and the right environment R[b,w,b'] start at
+ * zero; fill them with tdvp_set_tensor.  Errors: TDVP_EINVAL, TDVP_ENOMEM,
+ * TDVP_ECUDA. */
+int tdvp_bond_create(int symmetry, double J, double U, int nl, const int* left, int nr, const int* right,
+                     const tdvp_opts* opts, tdvp_ctx** out);
+
+/* which: 0 = two-site tensor theta, 1 = left environment, 2 = right environment
+ * (a bond-problem context), 3 = theta of bond (0,1) of a chain context.
+ * Number of blocks and total complex elements. */
+int tdvp_block_count(tdvp_ctx* ctx, int which, long long* nblocks, long long* nelems);
+
+/* Block list in storage order.  keys[5*i..]: theta (a, s1, t_c, s2, b) with a, b
+ * sector indices, s1, s2 site-multiplet indices and t_c the spin label of the
+ * coupled (a s1) channel; environments (a', w, a, 0, 0) / (b, w, b', 0, 0) with w
+ * a channel-multiplet index.  dims[2*i..] = (rows, cols); offsets[i] = first
+ * complex element; each block is row-major rows x cols.  Any pointer may be NULL. */
+int tdvp_block_list(tdvp_ctx* ctx, int which, int* keys, int* dims, long long* offsets);
+
+/* Copy n complex elements (interleaved FP64) into the left (which=1) or right
+ * (which=2) environment of a bond problem; on_device != 0 means data is a device
+ * pointer.  n must equal the tensor size.  Errors: TDVP_EINVAL, TDVP_ESTATE. */
+int tdvp_set_tensor(tdvp_ctx* ctx, int which, const double* data, long long n, int on_device);
+
+/* psi_out = H_eff psi_in for the two-site effective Hamiltonian of Sec. S2.3:
+ *   psi'[a',s1',s2',b'] = sum L[a',w,a] W[w,w1,s1',s1] W[w1,w2,s2',s2] R[b,w2,b'] psi[a,s1,s2,b]
+ * in the reduced block layout of which = 0 (bond problem) or 3 (chain bond
+ * (0,1), valid right after tdvp_create or tdvp_step).  bond must be 0.
+ * psi_in and psi_out hold tdvp_block_count elements; on_device != 0 means both
+ * are device pointers (no copies), otherwise host pointers (copied in and out).
+ * The call is stream-ordered on the context's stream and returns after the
+ * result is complete.  Errors: TDVP_EINVAL, TDVP_ESTATE, TDVP_ECUDA. */
+int tdvp_heff_apply(tdvp_ctx* ctx, int bond, const double* psi_in, double* psi_out, int on_device);
+
+/* Algorithmic flops of one tdvp_heff_apply (8 per complex multiply-add of the
+ * two block-GEMM stages). */
+int tdvp_heff_flops(tdvp_ctx* ctx, long long* flops);
+
+/* Destroy a context and free its device memory.  NULL is accepted. */
+int tdvp_destroy(tdvp_ctx* ctx);
+
+/* Static name of an error code. */
+const char* tdvp_strerror(int code);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* tdvp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TDVP_H_ */

@@ -1,0 +1,190 @@
+"""ctypes binding of the engine's C ABI (include/tdvp.h).
+
+Argument marshalling only: every step of the method runs inside the CUDA
+library.  Importing this module loads ``libtdvp.so`` and raises if it is
+missing; there is no Python or CPU implementation behind these calls.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtdvp.so")
+
+SYM = {"u1u1": 0, "u1su2": 1, "su2": 1}
+PREC = {"fp64": 0, "3xtf32": 1, "bf16x3": 2}
+ERRORS = {0: "ok", -1: "EINVAL", -2: "ESTATE", -3: "ENOMEM", -4: "ENUMERIC", -5: "EINTERNAL", -6: "ECUDA",
+          -7: "ETIMEOUT"}
+
+
+class TdvpError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Opts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("krylov_max", C.c_int), ("krylov_tol", C.c_double),
+                ("timeout_ms", C.c_int), ("cuda_stream", C.c_void_p), ("device", C.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is not built; run paper_2606_04771_b300/build.py")
+        L = C.CDLL(LIB_PATH)
+        P = C.POINTER
+        vp = C.c_void_p
+        sig = {
+            "tdvp_opts_default": (None, [P(Opts)]),
+            "tdvp_create": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_int, P(Opts), P(vp)]),
+            "tdvp_step": (C.c_int, [vp, C.c_double, C.c_longlong, C.c_double]),
+            "tdvp_measure": (C.c_int, [vp, vp, vp, vp, vp, vp]),
+            "tdvp_bond_dims": (C.c_int, [vp, vp, vp]),
+            "tdvp_stats": (C.c_int, [vp, vp, C.c_int]),
+            "tdvp_bond_create": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_int, vp, C.c_int, vp, P(Opts),
+                                           P(vp)]),
+            "tdvp_block_count": (C.c_int, [vp, C.c_int, P(C.c_longlong), P(C.c_longlong)]),
+            "tdvp_block_list": (C.c_int, [vp, C.c_int, vp, vp, vp]),
+            "tdvp_set_tensor": (C.c_int, [vp, C.c_int, vp, C.c_longlong, C.c_int]),
+            "tdvp_heff_apply": (C.c_int, [vp, C.c_int, vp, vp, C.c_int]),
+            "tdvp_heff_flops": (C.c_int, [vp, P(C.c_longlong)]),
+            "tdvp_destroy": (C.c_int, [vp]),
+            "tdvp_strerror": (C.c_char_p, [C.c_int]),
+            "tdvp_last_error": (C.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(rc):
+    if rc != 0:
+        raise TdvpError(rc, lib().tdvp_last_error().decode())
+
+
+def make_opts(precision="fp64", krylov_max=20, krylov_tol=1e-12, stream=None, device=-1):
+    o = Opts()
+    lib().tdvp_opts_default(C.byref(o))
+    o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
+    o.krylov_max = krylov_max
+    o.krylov_tol = krylov_tol
+    o.cuda_stream = stream
+    o.device = device
+    return o
+
+
+def _ptr(x):
+    """(pointer, on_device) for a numpy complex128 array or a torch tensor."""
+    if isinstance(x, np.ndarray):
+        assert x.dtype == np.complex128 and x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data, 0
+    # torch tensor (complex128, contiguous); device pointer when on CUDA
+    assert x.is_contiguous()
+    return x.data_ptr(), 1 if x.is_cuda else 0
+
+
+class _Ctx:
+    def __init__(self):
+        self.h = C.c_void_p()
+
+    def close(self):
+        if self.h:
+            check(lib().tdvp_destroy(self.h))
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def blocks(self, which):
+        nb, ne = C.c_longlong(), C.c_longlong()
+        check(lib().tdvp_block_count(self.h, which, C.byref(nb), C.byref(ne)))
+        keys = np.zeros((nb.value, 5), dtype=np.int32)
+        dims = np.zeros((nb.value, 2), dtype=np.int32)
+        offs = np.zeros(nb.value, dtype=np.int64)
+        check(lib().tdvp_block_list(self.h, which, keys.ctypes.data, dims.ctypes.data, offs.ctypes.data))
+        return keys, dims, offs, ne.value
+
+    def heff_apply(self, psi, out=None):
+        if out is None:
+            out = np.empty_like(psi) if isinstance(psi, np.ndarray) else psi.new_empty(psi.shape)
+        pi, di = _ptr(psi)
+        po, do = _ptr(out)
+        assert di == do
+        check(lib().tdvp_heff_apply(self.h, 0, pi, po, di))
+        return out
+
+    def heff_flops(self):
+        f = C.c_longlong()
+        check(lib().tdvp_heff_flops(self.h, C.byref(f)))
+        return f.value
+
+
+class Chain(_Ctx):
+    """An L-site chain in the Neel state, evolved with tdvp_step."""
+
+    def __init__(self, L, J=1.0, U=4.0, symmetry="su2", **opts):
+        super().__init__()
+        self.L = L
+        self.sym = symmetry
+        o = make_opts(**opts)
+        check(lib().tdvp_create(L, J, U, SYM[symmetry], C.byref(o), C.byref(self.h)))
+
+    def step(self, dt, chi_max, eps):
+        check(lib().tdvp_step(self.h, dt, int(chi_max), eps))
+
+    def measure(self, entropy=True, energy=True):
+        L = self.L
+        n, sz, docc = np.zeros(L), np.zeros(L), np.zeros(L)
+        ent = np.zeros(max(L - 1, 1))
+        e = np.zeros(1)
+        check(lib().tdvp_measure(self.h, n.ctypes.data, sz.ctypes.data, docc.ctypes.data,
+                                 ent.ctypes.data if entropy else None, e.ctypes.data if energy else None))
+        out = {"n": n, "sz": sz, "docc": docc, "n_up": 0.5 * n + sz, "n_dn": 0.5 * n - sz}
+        if entropy:
+            out["s_ent"] = ent[: L - 1]
+        if energy:
+            out["energy"] = float(e[0])
+        return out
+
+    def bond_dims(self):
+        chi = np.zeros(self.L + 1, dtype=np.int64)
+        red = np.zeros(self.L + 1, dtype=np.int64)
+        check(lib().tdvp_bond_dims(self.h, chi.ctypes.data, red.ctypes.data))
+        return chi, red
+
+    def stats(self):
+        v = np.zeros(7)
+        check(lib().tdvp_stats(self.h, v.ctypes.data, 7))
+        keys = ["seconds", "heff_flops", "env_flops", "matvecs", "max_krylov", "max_discarded", "chi_max_seen"]
+        return dict(zip(keys, v.tolist()))
+
+
+class BondProblem(_Ctx):
+    """Two-site effective-Hamiltonian problem between two given bond sector tables."""
+
+    def __init__(self, left, right, J=1.0, U=4.0, symmetry="su2", **opts):
+        super().__init__()
+        o = make_opts(**opts)
+        lt = np.ascontiguousarray(np.array(left, dtype=np.int32).reshape(-1, 3))
+        rt = np.ascontiguousarray(np.array(right, dtype=np.int32).reshape(-1, 3))
+        check(lib().tdvp_bond_create(SYM[symmetry], J, U, lt.shape[0], lt.ctypes.data, rt.shape[0],
+                                     rt.ctypes.data, C.byref(o), C.byref(self.h)))
+
+    def set_env(self, which, data):
+        p, dev = _ptr(data)
+        n = data.size if isinstance(data, np.ndarray) else data.numel()
+        check(lib().tdvp_set_tensor(self.h, which, p, n, dev))

@@ -1,0 +1,240 @@
+// extern "C" boundary of the engine (include/tdvp.h): argument checks, host/device
+// marshalling and the translation of exceptions into status codes.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/tdvp.h"
+#include "engine.hpp"
+
+struct tdvp_ctx {
+  tdvp::Engine* eng;
+};
+
+namespace {
+thread_local std::string g_last;
+
+int fail(int code, const std::string& msg) {
+  g_last = msg;
+  return code;
+}
+
+template <class F>
+int guarded(F f) {
+  try {
+    f();
+    return TDVP_OK;
+  } catch (const tdvp::Error& e) {
+    return fail(e.code, e.what());
+  } catch (const std::bad_alloc&) {
+    return fail(TDVP_ENOMEM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(TDVP_EINTERNAL, e.what());
+  }
+}
+
+tdvp::Opts to_opts(const tdvp_opts* o) {
+  tdvp::Opts r;
+  if (o) {
+    r.precision = o->precision;
+    r.krylov_max = o->krylov_max;
+    r.krylov_tol = o->krylov_tol;
+    r.timeout_ms = o->timeout_ms;
+    r.stream = reinterpret_cast<cudaStream_t>(o->cuda_stream);
+    r.device = o->device;
+  }
+  return r;
+}
+
+std::vector<tdvp::Sector> sectors(int n, const int* v) {
+  std::vector<tdvp::Sector> s;
+  for (int i = 0; i < n; ++i) s.push_back({v[3 * i], v[3 * i + 1], v[3 * i + 2]});
+  return s;
+}
+
+tdvp::BTensor* tensor_of(tdvp_ctx* ctx, int which) {
+  tdvp::Engine* e = ctx->eng;
+  if (which == 3) {
+    e->chain_heff0();
+    return &e->theta_layout();
+  }
+  if (!e->bond_only()) throw tdvp::Error(TDVP_ESTATE, "which 0-2 need a bond-problem context");
+  if (which == 0) return &e->theta_layout();
+  if (which == 1) return &e->left_env_bp();
+  if (which == 2) return &e->right_env_bp();
+  throw tdvp::Error(TDVP_EINVAL, "which must be 0..3");
+}
+}  // namespace
+
+extern "C" {
+
+void tdvp_opts_default(tdvp_opts* o) {
+  if (!o) return;
+  o->precision = TDVP_PREC_FP64;
+  o->krylov_max = 20;
+  o->krylov_tol = 1e-12;
+  o->timeout_ms = 0;
+  o->cuda_stream = nullptr;
+  o->device = -1;
+}
+
+int tdvp_create(int L, double J, double U, int symmetry, const tdvp_opts* opts, tdvp_ctx** out) {
+  if (!out) return fail(TDVP_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (symmetry != TDVP_SYM_U1U1 && symmetry != TDVP_SYM_U1SU2) return fail(TDVP_EINVAL, "unknown symmetry");
+  return guarded([&] {
+    tdvp_opts d;
+    tdvp_opts_default(&d);
+    auto* e = new tdvp::Engine(L, J, U, symmetry == TDVP_SYM_U1SU2, to_opts(opts ? opts : &d));
+    *out = new tdvp_ctx{e};
+  });
+}
+
+int tdvp_bond_create(int symmetry, double J, double U, int nl, const int* left, int nr, const int* right,
+                     const tdvp_opts* opts, tdvp_ctx** out) {
+  if (!out) return fail(TDVP_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (symmetry != TDVP_SYM_U1U1 && symmetry != TDVP_SYM_U1SU2) return fail(TDVP_EINVAL, "unknown symmetry");
+  if (nl < 1 || nr < 1 || !left || !right) return fail(TDVP_EINVAL, "empty sector table");
+  return guarded([&] {
+    tdvp_opts d;
+    tdvp_opts_default(&d);
+    auto* e = tdvp::Engine::bond_problem(symmetry == TDVP_SYM_U1SU2, J, U, sectors(nl, left), sectors(nr, right),
+                                         to_opts(opts ? opts : &d));
+    *out = new tdvp_ctx{e};
+  });
+}
+
+int tdvp_step(tdvp_ctx* ctx, double dt, long long chi_max, double eps_trunc) {
+  if (!ctx) return fail(TDVP_EINVAL, "ctx is NULL");
+  return guarded([&] { ctx->eng->step(dt, chi_max, eps_trunc); });
+}
+
+int tdvp_measure(tdvp_ctx* ctx, double* n, double* sz, double* docc, double* s_ent, double* energy) {
+  if (!ctx) return fail(TDVP_EINVAL, "ctx is NULL");
+  return guarded([&] { ctx->eng->measure(n, sz, docc, s_ent, energy); });
+}
+
+int tdvp_bond_dims(tdvp_ctx* ctx, long long* chi, long long* chi_red) {
+  if (!ctx) return fail(TDVP_EINVAL, "ctx is NULL");
+  return guarded([&] {
+    tdvp::Engine* e = ctx->eng;
+    if (e->bond_only()) throw tdvp::Error(TDVP_ESTATE, "bond problem has no chain");
+    for (int k = 0; k <= e->L(); ++k) {
+      const tdvp::BondSpace& b = e->bond(k);
+      long long c = 0, r = 0;
+      for (auto& s : b.s) {
+        c += (long long)s.d * e->model().mult_dim(s.t);
+        r += s.d;
+      }
+      if (chi) chi[k] = c;
+      if (chi_red) chi_red[k] = r;
+    }
+  });
+}
+
+int tdvp_stats(tdvp_ctx* ctx, double* out, int n) {
+  if (!ctx || !out) return fail(TDVP_EINVAL, "NULL argument");
+  return guarded([&] {
+    const tdvp::StepStats& s = ctx->eng->stats();
+    double v[7] = {s.seconds, (double)s.heff_flops, (double)s.env_flops, (double)s.matvecs, (double)s.max_krylov,
+                   s.max_discarded, (double)s.chi_max_seen};
+    for (int i = 0; i < n && i < 7; ++i) out[i] = v[i];
+  });
+}
+
+int tdvp_block_count(tdvp_ctx* ctx, int which, long long* nblocks, long long* nelems) {
+  if (!ctx) return fail(TDVP_EINVAL, "ctx is NULL");
+  return guarded([&] {
+    tdvp::BTensor* t = tensor_of(ctx, which);
+    if (nblocks) *nblocks = (long long)t->blocks.size();
+    if (nelems) *nelems = t->size;
+  });
+}
+
+int tdvp_block_list(tdvp_ctx* ctx, int which, int* keys, int* dims, long long* offsets) {
+  if (!ctx) return fail(TDVP_EINVAL, "ctx is NULL");
+  return guarded([&] {
+    tdvp::BTensor* t = tensor_of(ctx, which);
+    for (size_t i = 0; i < t->blocks.size(); ++i) {
+      const tdvp::Block& b = t->blocks[i];
+      if (keys)
+        for (int k = 0; k < 5; ++k) keys[5 * i + k] = b.key[k];
+      if (dims) {
+        dims[2 * i] = b.rows;
+        dims[2 * i + 1] = b.cols;
+      }
+      if (offsets) offsets[i] = b.off;
+    }
+  });
+}
+
+int tdvp_set_tensor(tdvp_ctx* ctx, int which, const double* data, long long n, int on_device) {
+  if (!ctx || !data) return fail(TDVP_EINVAL, "NULL argument");
+  if (which != 1 && which != 2) return fail(TDVP_EINVAL, "which must be 1 (L) or 2 (R)");
+  return guarded([&] {
+    tdvp::BTensor* t = tensor_of(ctx, which);
+    if (n != t->size) throw tdvp::Error(TDVP_EINVAL, "size mismatch");
+    cudaStream_t s = ctx->eng->stream();
+    TDVP_CUDA(cudaMemcpyAsync(t->data(), data, n * sizeof(tdvp::cplx),
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    TDVP_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+int tdvp_heff_apply(tdvp_ctx* ctx, int bond, const double* psi_in, double* psi_out, int on_device) {
+  if (!ctx || !psi_in || !psi_out) return fail(TDVP_EINVAL, "NULL argument");
+  if (bond != 0) return fail(TDVP_EINVAL, "bond must be 0");
+  return guarded([&] {
+    tdvp::Engine* e = ctx->eng;
+    tdvp::HeffPlan& H = e->bond_only() ? e->heff_plan_bond() : e->chain_heff0();
+    cudaStream_t s = e->stream();
+    const long long n = H.n;
+    if (on_device) {
+      H.apply(reinterpret_cast<const tdvp::cplx*>(psi_in), reinterpret_cast<tdvp::cplx*>(psi_out), s);
+      TDVP_CUDA(cudaStreamSynchronize(s));
+    } else {
+      tdvp::DevBuf din(std::max<long long>(n, 1) * sizeof(tdvp::cplx), s), dout(std::max<long long>(n, 1) * sizeof(tdvp::cplx), s);
+      TDVP_CUDA(cudaMemcpyAsync(din.p, psi_in, n * sizeof(tdvp::cplx), cudaMemcpyHostToDevice, s));
+      H.apply(din.as<tdvp::cplx>(), dout.as<tdvp::cplx>(), s);
+      TDVP_CUDA(cudaMemcpyAsync(psi_out, dout.p, n * sizeof(tdvp::cplx), cudaMemcpyDeviceToHost, s));
+      TDVP_CUDA(cudaStreamSynchronize(s));
+    }
+    TDVP_CUDA(cudaGetLastError());
+  });
+}
+
+int tdvp_heff_flops(tdvp_ctx* ctx, long long* flops) {
+  if (!ctx || !flops) return fail(TDVP_EINVAL, "NULL argument");
+  return guarded([&] {
+    tdvp::Engine* e = ctx->eng;
+    *flops = (e->bond_only() ? e->heff_plan_bond() : e->chain_heff0()).flops();
+  });
+}
+
+int tdvp_destroy(tdvp_ctx* ctx) {
+  if (!ctx) return TDVP_OK;
+  int rc = guarded([&] { delete ctx->eng; });
+  delete ctx;
+  return rc;
+}
+
+const char* tdvp_strerror(int code) {
+  switch (code) {
+    case TDVP_OK: return "ok";
+    case TDVP_EINVAL: return "invalid argument";
+    case TDVP_ESTATE: return "call not valid for this context";
+    case TDVP_ENOMEM: return "out of memory";
+    case TDVP_ENUMERIC: return "numerical failure";
+    case TDVP_EINTERNAL: return "internal error";
+    case TDVP_ECUDA: return "CUDA error";
+    case TDVP_ETIMEOUT: return "device wait timed out";
+    default: return "unknown error";
+  }
+}
+
+const char* tdvp_last_error(void) { return g_last.c_str(); }
+
+}  // extern "C"

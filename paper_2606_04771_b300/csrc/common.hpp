@@ -1,0 +1,110 @@
+// Task descriptors shared by the host planner and the device kernels.
+//
+// Every contraction of the method (effective Hamiltonian, environment
+// updates, two-site tensor formation, measurement) is lowered by the host into
+// flat lists of these tasks; the kernels know nothing about symmetry labels.
+#pragma once
+#include <cstdint>
+
+#ifndef __CUDACC__
+#define __host__
+#define __device__
+#endif
+
+namespace tdvp {
+
+struct cplx {
+  double x, y;
+};
+
+// One output block C (rows x cols, leading dimension ldc, row-major) computed as
+// C = sum_seg alpha_seg * op(A_seg) * op(B_seg).  A task with no segment writes zeros.
+// Pointers in GemmTask/GemmSeg are relative to one of four launch-time bases
+// (base 0 is the null address, i.e. the pointer is absolute); this lets one plan
+// serve every Krylov vector without rewriting the task list.
+struct Bases4 {
+  uintptr_t p[4];
+};
+
+struct GemmTask {
+  cplx* c;
+  int c_base;
+  int rows, cols, ldc;
+  int seg_begin, seg_count;
+  int tiles_m, tiles_n;  // filled by the planner for the tile size in use
+};
+
+// op flags
+enum : int { OP_N = 0, OP_C = 1 };  // OP_C: conjugate transpose
+
+struct GemmSeg {
+  const cplx* a;
+  const cplx* b;
+  int a_base, b_base;
+  int lda, ldb, k;
+  int op_a, op_b;
+  double alpha;
+};
+
+template <class T>
+__host__ __device__ inline T* rebase(const Bases4& B, int base, T* p) {
+  return reinterpret_cast<T*>(B.p[base] + reinterpret_cast<uintptr_t>(p));
+}
+
+// out (rows x cols, ld_out) = sum_term coef * in_term (same shape, ld_in)
+struct LincombTask {
+  cplx* out;
+  int rows, cols, ld_out;
+  int term_begin, term_count;
+};
+
+struct LincombTerm {
+  const cplx* in;
+  int ld_in;
+  double coef;
+};
+
+// Strided copy: dst[r*dst_rs + c*dst_cs] = f(src[r*src_rs + c*src_cs])
+// with f = optional conjugation and a per-column (of the destination) scale taken
+// from scale[c] (scale_mode 1: multiply, 2: divide, 0: none) and a global factor.
+struct CopyTask {
+  const cplx* src;
+  cplx* dst;
+  int rows, cols;
+  long long src_rs, src_cs, dst_rs, dst_cs;
+  const int* row_map;    // optional: source row of destination row r is row_map[r]
+  const int* col_map;    // optional: source column of destination column c is col_map[c]
+  const double* scale;   // per destination column (modes 1, 2) or row (modes 3, 4)
+  int scale_mode;        // 0 none, 1 *scale[c], 2 /scale[c], 3 *scale[r], 4 /scale[r]
+  int conj;
+  const double* gscale;  // optional device scalar applied to every element
+};
+
+// One Jacobi SVD problem: G is p x q column-major (p >= q) with leading dimension p,
+// V is q x q column-major.  On exit G holds U*S in descending order of S, V the right
+// singular vectors in the same order, sv[0..q) the singular values.
+struct SvdTask {
+  cplx* g;
+  cplx* v;
+  double* sv;   // q values, sorted descending on exit
+  int* perm;    // q entries: perm[k] = column of G/V holding the k-th largest value
+  int p, q;
+};
+
+// Truncation input: one entry per SVD problem (a bond sector)
+struct TruncSector {
+  const double* sv;  // sorted descending
+  int r;             // number of singular values
+  int mult;          // 2S+1 (SU(2)) or 1
+};
+
+// Block-weighted inner product contribution: sum_ij weight * conj(x[i,j]) * y[i,j]
+struct DotTask {
+  const cplx* x;
+  const cplx* y;
+  int rows, cols, ldx, ldy;
+  int slot;      // output slot
+  double weight;
+};
+
+}  // namespace tdvp

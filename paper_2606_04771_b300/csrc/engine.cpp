@@ -1,0 +1,1283 @@
+// Two-site TDVP engine (host orchestration of the device kernels).
+//
+// Sec. S2.2: second-order two-site TDVP.  One time step dt is a left-to-right
+// half sweep and a right-to-left half sweep with tau = dt/2: at every bond the
+// two-site tensor is evolved by exp(-i tau H_eff) (Krylov), split by a
+// per-sector SVD with truncation on the truncated weight (Sec. S2.4), the
+// environment is updated, and the new centre tensor is evolved backward by
+// exp(+i tau H_eff^(1)) except at the last bond of the half sweep.  Sec. S2.3:
+// every contraction is a list of dense block products (GEMM tasks), with the
+// MPO applied as an FP64-weighted linear combination of blocks in between.
+#include "engine.hpp"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <tuple>
+
+namespace tdvp {
+
+// ---------------------------------------------------------------------------
+// device buffers and plan uploads
+// ---------------------------------------------------------------------------
+
+DevBuf::DevBuf(size_t b, cudaStream_t st) : bytes(b), s(st) {
+  if (b) TDVP_CUDA(cudaMallocAsync(&p, b, st));
+}
+DevBuf::~DevBuf() { reset(); }
+DevBuf& DevBuf::operator=(DevBuf&& o) noexcept {
+  if (this != &o) {
+    reset();
+    p = o.p;
+    bytes = o.bytes;
+    s = o.s;
+    o.p = nullptr;
+    o.bytes = 0;
+  }
+  return *this;
+}
+void DevBuf::reset() {
+  if (p) cudaFreeAsync(p, s);
+  p = nullptr;
+  bytes = 0;
+}
+
+template <class T>
+static DevBuf upload(const std::vector<T>& v, cudaStream_t s) {
+  DevBuf b(std::max<size_t>(v.size(), 1) * sizeof(T), s);
+  if (!v.empty()) TDVP_CUDA(cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  return b;
+}
+
+void GemmPlan::finalize(cudaStream_t s) {
+  tiles.clear();
+  for (int i = 0; i < (int)tasks.size(); ++i) {
+    GemmTask& t = tasks[i];
+    t.tiles_m = (t.rows + 63) / 64;
+    t.tiles_n = (t.cols + 63) / 64;
+    for (int a = 0; a < t.tiles_m; ++a)
+      for (int b = 0; b < t.tiles_n; ++b) tiles.push_back(make_int3(i, a, b));
+  }
+  dt = upload(tasks, s);
+  ds = upload(segs, s);
+  dti = upload(tiles, s);
+}
+
+void GemmPlan::launch(cudaStream_t s, const Bases4& B) const {
+  launch_gemm_fp64(dt.as<GemmTask>(), ds.as<GemmSeg>(), dti.as<int3>(), (int)tiles.size(), B, s);
+}
+
+void LincombPlan::finalize(cudaStream_t s) {
+  chunks.clear();
+  for (int i = 0; i < (int)tasks.size(); ++i) {
+    int n = tasks[i].rows * tasks[i].cols;
+    for (int e = 0; e < n; e += LINCOMB_CHUNK) chunks.push_back(make_int2(i, e));
+  }
+  dt = upload(tasks, s);
+  dm = upload(terms, s);
+  dc = upload(chunks, s);
+}
+
+void LincombPlan::launch(cudaStream_t s) const {
+  launch_lincomb(dt.as<LincombTask>(), dm.as<LincombTerm>(), dc.as<int2>(), (int)chunks.size(), s);
+}
+
+void CopyPlan::finalize(cudaStream_t s) {
+  chunks.clear();
+  for (int i = 0; i < (int)tasks.size(); ++i) {
+    int n = tasks[i].rows * tasks[i].cols;
+    for (int e = 0; e < n; e += LINCOMB_CHUNK) chunks.push_back(make_int2(i, e));
+  }
+  dt = upload(tasks, s);
+  dc = upload(chunks, s);
+}
+
+void CopyPlan::launch(cudaStream_t s) const { launch_copy(dt.as<CopyTask>(), dc.as<int2>(), (int)chunks.size(), s); }
+
+void HeffPlan::apply(const cplx* in, cplx* out, cudaStream_t s) const {
+  Bases4 B{{0, reinterpret_cast<uintptr_t>(in), reinterpret_cast<uintptr_t>(out), 0}};
+  g1.launch(s, B);
+  lc.launch(s);
+  g3.launch(s, B);
+}
+
+static inline cplx* as_off(long long off) { return reinterpret_cast<cplx*>(static_cast<uintptr_t>(off) * sizeof(cplx)); }
+
+// ---------------------------------------------------------------------------
+// construction
+// ---------------------------------------------------------------------------
+
+void Engine::init_common(bool su2, double J, double U, const Opts& o) {
+  opt_ = o;
+  if (o.krylov_max < 1 || o.krylov_max > KRYLOV_MAX) throw Error(-1, "krylov_max must be in [1, 32]");
+  if (!(o.krylov_tol > 0)) throw Error(-1, "krylov_tol must be > 0");
+  if (o.precision < 0 || o.precision > 2) throw Error(-1, "unknown precision");
+  if (o.device >= 0) TDVP_CUDA(cudaSetDevice(o.device));
+  model_.init(su2, J, U);
+  rec_.reset(new Recoupler(&model_));
+  if (o.stream) {
+    stream_ = o.stream;
+  } else {
+    TDVP_CUDA(cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking));
+    own_stream_ = true;
+  }
+  TDVP_CUDA(cudaMallocHost(&pinned_, 4096));
+  TDVP_CUDA(cudaMalloc(&dstatus_, sizeof(int) * 4));
+  TDVP_CUDA(cudaMemsetAsync(dstatus_, 0, sizeof(int) * 4, stream_));
+}
+
+Engine::Engine(int L, double J, double U, bool su2, const Opts& o) : L_(L) {
+  if (L < 2 || (L % 2)) throw Error(-1, "L must be even and >= 2");
+  init_common(su2, J, U, o);
+  init_neel();
+}
+
+Engine* Engine::bond_problem(bool su2, double J, double U, const std::vector<Sector>& left,
+                             const std::vector<Sector>& right, const Opts& o) {
+  std::unique_ptr<Engine> e(new Engine());
+  e->L_ = 2;
+  e->bond_only_ = true;
+  e->init_common(su2, J, U, o);
+  e->bonds_.assign(3, BondSpace());
+  e->bonds_[0].s = left;
+  e->bonds_[2].s = right;
+  for (int k : {0, 2}) {
+    e->bonds_[k].build_index();
+    if (e->bonds_[k].idx.size() != e->bonds_[k].s.size()) throw Error(-1, "duplicate sector label");
+    for (auto& x : e->bonds_[k].s) {
+      if (x.d < 1) throw Error(-1, "sector degeneracy must be >= 1");
+      if (su2 && x.t < 0) throw Error(-1, "2S must be >= 0");
+    }
+  }
+  e->Lenv_.resize(3);
+  e->Renv_.resize(3);
+  e->build_lenv_layout(e->Lenv_[0], e->bonds_[0], e->bonds_[0]);
+  e->alloc(e->Lenv_[0], true);
+  e->build_renv_layout(e->Renv_[2], e->bonds_[2], e->bonds_[2]);
+  e->alloc(e->Renv_[2], true);
+  e->build_theta_layout(e->theta_, e->bonds_[0], e->bonds_[2]);
+  e->bp_heff_.reset(new HeffPlan());
+  e->plan_heff2(*e->bp_heff_, e->Lenv_[0], e->Renv_[2], e->theta_, e->bonds_[0], e->bonds_[2]);
+  TDVP_CUDA(cudaStreamSynchronize(e->stream_));
+  return e.release();
+}
+
+void Engine::heff_apply_bond(const cplx* in, cplx* out) {
+  if (!bond_only_) throw Error(-2, "not a bond problem");
+  bp_heff_->apply(in, out, stream_);
+}
+
+HeffPlan& Engine::chain_heff0() {
+  if (bond_only_) throw Error(-2, "not a chain");
+  if (!chain_heff_) {
+    build_theta_layout(theta_, bonds_[0], bonds_[2]);
+    chain_heff_.reset(new HeffPlan());
+    plan_heff2(*chain_heff_, Lenv_[0], Renv_[2], theta_, bonds_[0], bonds_[2]);
+  }
+  return *chain_heff_;
+}
+
+Engine::~Engine() {
+  if (stream_) cudaStreamSynchronize(stream_);
+  site_.clear();
+  Lenv_.clear();
+  Renv_.clear();
+  theta_.buf.reset();
+  bp_heff_.reset();
+  chain_heff_.reset();
+  kv_.reset();
+  kw_.reset();
+  kpart_.reset();
+  kh1_.reset();
+  kh2_.reset();
+  knrm_.reset();
+  kstate_.reset();
+  if (stream_) cudaStreamSynchronize(stream_);
+  if (pinned_) cudaFreeHost(pinned_);
+  if (dstatus_) cudaFree(dstatus_);
+  if (own_stream_) cudaStreamDestroy(stream_);
+}
+
+void Engine::alloc(BTensor& t, bool zero) {
+  t.buf = DevBuf(std::max<long long>(t.size, 1) * sizeof(cplx), stream_);
+  if (zero) TDVP_CUDA(cudaMemsetAsync(t.buf.p, 0, std::max<long long>(t.size, 1) * sizeof(cplx), stream_));
+}
+
+void Engine::build_site_layout(BTensor& t, const BondSpace& l, const BondSpace& r) const {
+  t = BTensor();
+  t.kind = SITE;
+  std::vector<std::pair<int, int>> f;
+  for (int a = 0; a < (int)l.s.size(); ++a)
+    for (int s = 0; s < (int)model_.site.size(); ++s) {
+      model_.fuse(l.s[a].n, l.s[a].t, model_.site[s].n, model_.site[s].t, f);
+      for (auto& q : f) {
+        int b = r.find(q.first, q.second);
+        if (b >= 0) t.add(bkey(a, s, b), a, s, b, 0, 0, l.s[a].d, r.s[b].d);
+      }
+    }
+}
+
+void Engine::build_theta_layout(BTensor& t, const BondSpace& l, const BondSpace& r) const {
+  t = BTensor();
+  t.kind = THETA;
+  std::vector<std::pair<int, int>> fc, fb;
+  for (int a = 0; a < (int)l.s.size(); ++a)
+    for (int s1 = 0; s1 < (int)model_.site.size(); ++s1) {
+      model_.fuse(l.s[a].n, l.s[a].t, model_.site[s1].n, model_.site[s1].t, fc);
+      for (auto& c : fc)
+        for (int s2 = 0; s2 < (int)model_.site.size(); ++s2) {
+          model_.fuse(c.first, c.second, model_.site[s2].n, model_.site[s2].t, fb);
+          for (auto& qb : fb) {
+            int b = r.find(qb.first, qb.second);
+            if (b >= 0) t.add(bkey(a, s1, c.second, s2, b), a, s1, c.second, s2, b, l.s[a].d, r.s[b].d);
+          }
+        }
+    }
+}
+
+void Engine::build_lenv_layout(BTensor& t, const BondSpace& bra, const BondSpace& ket) const {
+  t = BTensor();
+  t.kind = LENV;
+  std::vector<std::pair<int, int>> f;
+  for (int ap = 0; ap < (int)bra.s.size(); ++ap)
+    for (int w = 0; w < (int)model_.chan.size(); ++w)
+      for (int a = 0; a < (int)ket.s.size(); ++a) {
+        model_.fuse(ket.s[a].n, ket.s[a].t, model_.chan[w].n, model_.chan[w].t, f);
+        for (auto& q : f)
+          if (q.first == bra.s[ap].n && q.second == bra.s[ap].t)
+            t.add(bkey(ap, w, a), ap, w, a, 0, 0, bra.s[ap].d, ket.s[a].d);
+      }
+}
+
+void Engine::build_renv_layout(BTensor& t, const BondSpace& ket, const BondSpace& bra) const {
+  t = BTensor();
+  t.kind = RENV;
+  std::vector<std::pair<int, int>> f;
+  for (int b = 0; b < (int)ket.s.size(); ++b)
+    for (int w = 0; w < (int)model_.chan.size(); ++w)
+      for (int bp = 0; bp < (int)bra.s.size(); ++bp) {
+        model_.fuse(ket.s[b].n, ket.s[b].t, model_.chan[w].n, model_.chan[w].t, f);
+        for (auto& q : f)
+          if (q.first == bra.s[bp].n && q.second == bra.s[bp].t)
+            t.add(bkey(b, w, bp), b, w, bp, 0, 0, ket.s[b].d, bra.s[bp].d);
+      }
+}
+
+void Engine::init_neel() {
+  // particle-hole frame: the Neel state of Eq. (neel) becomes |2,0,2,0,...>
+  bonds_.assign(L_ + 1, BondSpace());
+  int n = 0;
+  for (int k = 0; k <= L_; ++k) {
+    bonds_[k].s = {{n, 0, 1}};
+    bonds_[k].build_index();
+    if (k < L_) n += (k % 2 == 0) ? 2 : 0;
+  }
+  site_.clear();
+  site_.resize(L_);
+  std::vector<cplx> one(1, cplx{1.0, 0.0});
+  for (int i = 0; i < L_; ++i) {
+    build_site_layout(site_[i], bonds_[i], bonds_[i + 1]);
+    if (site_[i].blocks.size() != 1) throw Error(-5, "Neel layout must have one block per site");
+    alloc(site_[i], false);
+    TDVP_CUDA(cudaMemcpyAsync(site_[i].data(), one.data(), sizeof(cplx), cudaMemcpyHostToDevice, stream_));
+  }
+  Lenv_.clear();
+  Renv_.clear();
+  Lenv_.resize(L_ + 1);
+  Renv_.resize(L_ + 1);
+  build_lenv_layout(Lenv_[0], bonds_[0], bonds_[0]);
+  alloc(Lenv_[0], true);
+  int bi = Lenv_[0].find(bkey(0, model_.chB, 0));
+  TDVP_CUDA(cudaMemcpyAsync(Lenv_[0].ptr(bi), one.data(), sizeof(cplx), cudaMemcpyHostToDevice, stream_));
+  build_renv_layout(Renv_[L_], bonds_[L_], bonds_[L_]);
+  alloc(Renv_[L_], true);
+  bi = Renv_[L_].find(bkey(0, model_.chE, 0));
+  TDVP_CUDA(cudaMemcpyAsync(Renv_[L_].ptr(bi), one.data(), sizeof(cplx), cudaMemcpyHostToDevice, stream_));
+  for (int k = L_ - 1; k >= 1; --k) update_right_env(Renv_[k + 1], site_[k], Renv_[k], bonds_[k], bonds_[k + 1]);
+  TDVP_CUDA(cudaStreamSynchronize(stream_));
+}
+
+// ---------------------------------------------------------------------------
+// planners
+// ---------------------------------------------------------------------------
+
+void Engine::plan_heff2(HeffPlan& p, const BTensor& Lenv, const BTensor& Renv, const BTensor& theta,
+                        const BondSpace& bl, const BondSpace& br) {
+  p = HeffPlan();
+  p.n = theta.size;
+  const Model& M = model_;
+  std::vector<std::vector<int>> lby(bl.s.size());
+  for (int i = 0; i < (int)Lenv.blocks.size(); ++i) lby[Lenv.blocks[i].key[2]].push_back(i);
+  // step 1 layout: T1(a',w,a,s1,c,s2,b) = L(a',w,a) theta(a,s1,c,s2,b)
+  struct T1Info {
+    int lb, tb;
+  };
+  std::vector<T1Info> t1info;
+  p.t1.kind = THETA;
+  for (int tb = 0; tb < (int)theta.blocks.size(); ++tb) {
+    const Block& th = theta.blocks[tb];
+    for (int lb : lby[th.key[0]]) {
+      const Block& lk = Lenv.blocks[lb];
+      p.t1.add((uint64_t)t1info.size(), lk.key[0], lk.key[1], tb, 0, 0, lk.rows, th.cols);
+      t1info.push_back({lb, tb});
+    }
+  }
+  alloc(p.t1, false);
+  for (int i = 0; i < (int)t1info.size(); ++i) {
+    const Block& lk = Lenv.blocks[t1info[i].lb];
+    const Block& th = theta.blocks[t1info[i].tb];
+    GemmTask t{};
+    t.c = p.t1.ptr(i);
+    t.c_base = 0;
+    t.rows = lk.rows;
+    t.cols = th.cols;
+    t.ldc = th.cols;
+    t.seg_begin = (int)p.g1.segs.size();
+    t.seg_count = 1;
+    GemmSeg sg{};
+    sg.a = Lenv.ptr(t1info[i].lb);
+    sg.a_base = 0;
+    sg.lda = lk.cols;
+    sg.b = as_off(th.off);
+    sg.b_base = 1;
+    sg.ldb = th.cols;
+    sg.k = lk.cols;
+    sg.op_a = OP_N;
+    sg.op_b = OP_N;
+    sg.alpha = 1.0;
+    p.g1.segs.push_back(sg);
+    p.g1.tasks.push_back(t);
+    p.g1.flops += 8LL * lk.rows * lk.cols * th.cols;
+  }
+  // step 2: recoupling into T2(a',s1',c',s2',b',w2,b)
+  std::map<std::tuple<int, int, int, int, int, int, int>, int> t2idx;
+  std::vector<std::vector<std::pair<int, double>>> t2terms;
+  std::vector<std::array<int, 7>> t2keys;
+  for (int i = 0; i < (int)t1info.size(); ++i) {
+    const Block& lk = Lenv.blocks[t1info[i].lb];
+    const Block& th = theta.blocks[t1info[i].tb];
+    int ap = lk.key[0], w = lk.key[1], a = th.key[0], s1 = th.key[1], tc = th.key[2], s2 = th.key[3], b = th.key[4];
+    const auto& rc = rec_->two_site(bl.s[ap].t, w, bl.s[a].t, s1, tc, s2, br.s[b].t);
+    for (const auto& e : rc) {
+      int nbp = br.s[b].n + M.chan[e.w2].n;
+      int bp = br.find(nbp, e.tbp);
+      if (bp < 0) continue;
+      if (Renv.find(bkey(b, e.w2, bp)) < 0) continue;
+      if (bl.s[ap].n + M.site[e.s1p].n + M.site[e.s2p].n != nbp) throw Error(-5, "charge mismatch in recoupling");
+      auto key = std::make_tuple(ap, e.s1p, e.tcp, e.s2p, bp, e.w2, b);
+      auto it = t2idx.find(key);
+      int id;
+      if (it == t2idx.end()) {
+        id = (int)t2keys.size();
+        t2idx[key] = id;
+        t2keys.push_back({ap, e.s1p, e.tcp, e.s2p, bp, e.w2, b});
+        t2terms.emplace_back();
+        p.t2.add((uint64_t)id, ap, e.s1p, e.tcp, e.s2p, bp, bl.s[ap].d, br.s[b].d);
+      } else {
+        id = it->second;
+      }
+      t2terms[id].push_back({i, e.f});
+    }
+  }
+  alloc(p.t2, false);
+  for (int id = 0; id < (int)t2keys.size(); ++id) {
+    const Block& bk = p.t2.blocks[id];
+    LincombTask t{};
+    t.out = p.t2.ptr(id);
+    t.rows = bk.rows;
+    t.cols = bk.cols;
+    t.ld_out = bk.cols;
+    t.term_begin = (int)p.lc.terms.size();
+    t.term_count = (int)t2terms[id].size();
+    for (auto& tm : t2terms[id]) p.lc.terms.push_back({p.t1.ptr(tm.first), p.t1.blocks[tm.first].cols, tm.second});
+    p.lc.tasks.push_back(t);
+    p.lc.bytes += (long long)sizeof(cplx) * bk.rows * bk.cols * (1 + t.term_count);
+  }
+  // step 3: theta'(a',s1',c',s2',b') = sum_{w2,b} T2 R(b,w2,b')
+  std::map<std::tuple<int, int, int, int, int>, std::vector<int>> outsegs;
+  for (int id = 0; id < (int)t2keys.size(); ++id) {
+    auto& k = t2keys[id];
+    outsegs[std::make_tuple(k[0], k[1], k[2], k[3], k[4])].push_back(id);
+  }
+  for (int ob = 0; ob < (int)theta.blocks.size(); ++ob) {
+    const Block& o = theta.blocks[ob];
+    GemmTask t{};
+    t.c = as_off(o.off);
+    t.c_base = 2;
+    t.rows = o.rows;
+    t.cols = o.cols;
+    t.ldc = o.cols;
+    t.seg_begin = (int)p.g3.segs.size();
+    auto it = outsegs.find(std::make_tuple(o.key[0], o.key[1], o.key[2], o.key[3], o.key[4]));
+    int cnt = 0;
+    if (it != outsegs.end()) {
+      for (int id : it->second) {
+        auto& k = t2keys[id];
+        int rb = Renv.find(bkey(k[6], k[5], k[4]));
+        const Block& rk = Renv.blocks[rb];
+        GemmSeg sg{};
+        sg.a = p.t2.ptr(id);
+        sg.a_base = 0;
+        sg.lda = p.t2.blocks[id].cols;
+        sg.b = Renv.ptr(rb);
+        sg.b_base = 0;
+        sg.ldb = rk.cols;
+        sg.k = rk.rows;
+        sg.op_a = OP_N;
+        sg.op_b = OP_N;
+        sg.alpha = 1.0;
+        p.g3.segs.push_back(sg);
+        p.g3.flops += 8LL * o.rows * rk.rows * rk.cols;
+        ++cnt;
+      }
+    }
+    t.seg_count = cnt;
+    p.g3.tasks.push_back(t);
+  }
+  p.g1.finalize(stream_);
+  p.lc.finalize(stream_);
+  p.g3.finalize(stream_);
+}
+
+// shared by the one-site H_eff and the left-environment update: steps 1 and 2
+// T1(a',w,a,s,b) = L(a',w,a) X(a,s,b);  T2(a',s',b'',w',b) = sum f T1
+// keep(a', s', b'', w', b) decides whether an output is needed.
+template <class Keep>
+static void plan_l_w(Engine* eng, const Model& M, Recoupler& rec, HeffPlan& p, const BTensor& Lenv, const BTensor& X,
+                     const BondSpace& bl, const BondSpace& br, Keep keep,
+                     std::vector<std::array<int, 5>>& t2keys, cudaStream_t s,
+                     void (Engine::*alloc_fn)(BTensor&, bool)) {
+  std::vector<std::vector<int>> lby(bl.s.size());
+  for (int i = 0; i < (int)Lenv.blocks.size(); ++i) lby[Lenv.blocks[i].key[2]].push_back(i);
+  std::vector<std::pair<int, int>> info;
+  for (int xb = 0; xb < (int)X.blocks.size(); ++xb) {
+    const Block& x = X.blocks[xb];
+    for (int lb : lby[x.key[0]]) {
+      const Block& lk = Lenv.blocks[lb];
+      p.t1.add((uint64_t)info.size(), lk.key[0], lk.key[1], xb, 0, 0, lk.rows, x.cols);
+      info.push_back({lb, xb});
+    }
+  }
+  (eng->*alloc_fn)(p.t1, false);
+  for (int i = 0; i < (int)info.size(); ++i) {
+    const Block& lk = Lenv.blocks[info[i].first];
+    const Block& x = X.blocks[info[i].second];
+    GemmTask t{};
+    t.c = p.t1.ptr(i);
+    t.rows = lk.rows;
+    t.cols = x.cols;
+    t.ldc = x.cols;
+    t.seg_begin = (int)p.g1.segs.size();
+    t.seg_count = 1;
+    GemmSeg sg{};
+    sg.a = Lenv.ptr(info[i].first);
+    sg.lda = lk.cols;
+    sg.b = as_off(x.off);
+    sg.b_base = 1;
+    sg.ldb = x.cols;
+    sg.k = lk.cols;
+    sg.alpha = 1.0;
+    p.g1.segs.push_back(sg);
+    p.g1.tasks.push_back(t);
+    p.g1.flops += 8LL * lk.rows * lk.cols * x.cols;
+  }
+  std::map<std::array<int, 5>, int> idx;
+  std::vector<std::vector<std::pair<int, double>>> terms;
+  for (int i = 0; i < (int)info.size(); ++i) {
+    const Block& lk = Lenv.blocks[info[i].first];
+    const Block& x = X.blocks[info[i].second];
+    int ap = lk.key[0], w = lk.key[1], a = x.key[0], sx = x.key[1], b = x.key[2];
+    const auto& rc = rec.one_site(bl.s[ap].t, w, bl.s[a].t, sx, br.s[b].t);
+    for (const auto& e : rc) {
+      int nbpp = bl.s[ap].n + M.site[e.sp].n;
+      int bpp = br.find(nbpp, e.tbpp);
+      if (bpp < 0) continue;
+      if (br.s[b].n + M.chan[e.wp].n != nbpp) throw Error(-5, "charge mismatch in one-site recoupling");
+      std::array<int, 5> key{ap, e.sp, bpp, e.wp, b};
+      if (!keep(key)) continue;
+      auto it = idx.find(key);
+      int id;
+      if (it == idx.end()) {
+        id = (int)t2keys.size();
+        idx[key] = id;
+        t2keys.push_back(key);
+        terms.emplace_back();
+        p.t2.add((uint64_t)id, ap, e.sp, bpp, e.wp, b, bl.s[ap].d, br.s[b].d);
+      } else {
+        id = it->second;
+      }
+      terms[id].push_back({i, e.f});
+    }
+  }
+  (eng->*alloc_fn)(p.t2, false);
+  for (int id = 0; id < (int)t2keys.size(); ++id) {
+    const Block& bk = p.t2.blocks[id];
+    LincombTask t{};
+    t.out = p.t2.ptr(id);
+    t.rows = bk.rows;
+    t.cols = bk.cols;
+    t.ld_out = bk.cols;
+    t.term_begin = (int)p.lc.terms.size();
+    t.term_count = (int)terms[id].size();
+    for (auto& tm : terms[id]) p.lc.terms.push_back({p.t1.ptr(tm.first), p.t1.blocks[tm.first].cols, tm.second});
+    p.lc.tasks.push_back(t);
+    p.lc.bytes += (long long)sizeof(cplx) * bk.rows * bk.cols * (1 + t.term_count);
+  }
+  (void)s;
+}
+
+void Engine::plan_heff1(HeffPlan& p, const BTensor& Lenv, const BTensor& Renv, const BTensor& Mt, const BondSpace& bl,
+                        const BondSpace& br) {
+  p = HeffPlan();
+  p.n = Mt.size;
+  std::vector<std::array<int, 5>> t2keys;
+  auto keep = [&](const std::array<int, 5>& k) {
+    return Renv.find(bkey(k[4], k[3], k[2])) >= 0 && Mt.find(bkey(k[0], k[1], k[2])) >= 0;
+  };
+  plan_l_w(this, model_, *rec_, p, Lenv, Mt, bl, br, keep, t2keys, stream_, &Engine::alloc);
+  std::map<std::array<int, 3>, std::vector<int>> outsegs;
+  for (int id = 0; id < (int)t2keys.size(); ++id) outsegs[{t2keys[id][0], t2keys[id][1], t2keys[id][2]}].push_back(id);
+  for (int ob = 0; ob < (int)Mt.blocks.size(); ++ob) {
+    const Block& o = Mt.blocks[ob];
+    GemmTask t{};
+    t.c = as_off(o.off);
+    t.c_base = 2;
+    t.rows = o.rows;
+    t.cols = o.cols;
+    t.ldc = o.cols;
+    t.seg_begin = (int)p.g3.segs.size();
+    int cnt = 0;
+    auto it = outsegs.find({o.key[0], o.key[1], o.key[2]});
+    if (it != outsegs.end())
+      for (int id : it->second) {
+        auto& k = t2keys[id];
+        int rb = Renv.find(bkey(k[4], k[3], k[2]));
+        const Block& rk = Renv.blocks[rb];
+        GemmSeg sg{};
+        sg.a = p.t2.ptr(id);
+        sg.lda = p.t2.blocks[id].cols;
+        sg.b = Renv.ptr(rb);
+        sg.ldb = rk.cols;
+        sg.k = rk.rows;
+        sg.alpha = 1.0;
+        p.g3.segs.push_back(sg);
+        p.g3.flops += 8LL * o.rows * rk.rows * rk.cols;
+        ++cnt;
+      }
+    t.seg_count = cnt;
+    p.g3.tasks.push_back(t);
+  }
+  p.g1.finalize(stream_);
+  p.lc.finalize(stream_);
+  p.g3.finalize(stream_);
+}
+
+void Engine::update_left_env(const BTensor& Lin, const BTensor& A, BTensor& Lout, const BondSpace& bl,
+                             const BondSpace& br) {
+  build_lenv_layout(Lout, br, br);
+  alloc(Lout, false);
+  HeffPlan p;
+  std::vector<std::array<int, 5>> t2keys;
+  // T2(a',s',b'',w',b) is needed when L'(b'',w',b) exists and A(a',s',b'') exists
+  auto keep = [&](const std::array<int, 5>& k) {
+    return Lout.find(bkey(k[2], k[3], k[4])) >= 0 && A.find(bkey(k[0], k[1], k[2])) >= 0;
+  };
+  plan_l_w(this, model_, *rec_, p, Lin, A, bl, br, keep, t2keys, stream_, &Engine::alloc);
+  std::map<std::array<int, 3>, std::vector<int>> outsegs;  // (b'', w', b)
+  for (int id = 0; id < (int)t2keys.size(); ++id) outsegs[{t2keys[id][2], t2keys[id][3], t2keys[id][4]}].push_back(id);
+  for (int ob = 0; ob < (int)Lout.blocks.size(); ++ob) {
+    const Block& o = Lout.blocks[ob];
+    GemmTask t{};
+    t.c = Lout.ptr(ob);
+    t.rows = o.rows;
+    t.cols = o.cols;
+    t.ldc = o.cols;
+    t.seg_begin = (int)p.g3.segs.size();
+    int cnt = 0;
+    auto it = outsegs.find({o.key[0], o.key[1], o.key[2]});
+    if (it != outsegs.end())
+      for (int id : it->second) {
+        auto& k = t2keys[id];
+        int ab = A.find(bkey(k[0], k[1], k[2]));
+        const Block& ak = A.blocks[ab];
+        GemmSeg sg{};
+        sg.a = A.ptr(ab);
+        sg.lda = ak.cols;
+        sg.op_a = OP_C;
+        sg.b = p.t2.ptr(id);
+        sg.ldb = p.t2.blocks[id].cols;
+        sg.k = ak.rows;
+        sg.alpha = 1.0;
+        p.g3.segs.push_back(sg);
+        p.g3.flops += 8LL * o.rows * ak.rows * o.cols;
+        ++cnt;
+      }
+    t.seg_count = cnt;
+    p.g3.tasks.push_back(t);
+  }
+  p.g1.finalize(stream_);
+  p.lc.finalize(stream_);
+  p.g3.finalize(stream_);
+  Bases4 B{{0, reinterpret_cast<uintptr_t>(A.data()), 0, 0}};
+  p.g1.launch(stream_, B);
+  p.lc.launch(stream_);
+  p.g3.launch(stream_, B);
+  stats_.env_flops += p.g1.flops + p.g3.flops;
+}
+
+void Engine::update_right_env(const BTensor& Rin, const BTensor& Bt, BTensor& Rout, const BondSpace& bl,
+                              const BondSpace& br) {
+  const Model& M = model_;
+  build_renv_layout(Rout, bl, bl);
+  alloc(Rout, false);
+  HeffPlan p;
+  std::vector<std::vector<int>> rby(br.s.size());
+  for (int i = 0; i < (int)Rin.blocks.size(); ++i) rby[Rin.blocks[i].key[0]].push_back(i);
+  // step 1: F1(a,s,b,w',b') = B(a,s,b) R(b,w',b')
+  std::vector<std::pair<int, int>> info;
+  for (int xb = 0; xb < (int)Bt.blocks.size(); ++xb) {
+    const Block& x = Bt.blocks[xb];
+    for (int rb : rby[x.key[2]]) {
+      const Block& rk = Rin.blocks[rb];
+      p.t1.add((uint64_t)info.size(), xb, rk.key[1], rk.key[2], 0, 0, x.rows, rk.cols);
+      info.push_back({xb, rb});
+    }
+  }
+  alloc(p.t1, false);
+  for (int i = 0; i < (int)info.size(); ++i) {
+    const Block& x = Bt.blocks[info[i].first];
+    const Block& rk = Rin.blocks[info[i].second];
+    GemmTask t{};
+    t.c = p.t1.ptr(i);
+    t.rows = x.rows;
+    t.cols = rk.cols;
+    t.ldc = rk.cols;
+    t.seg_begin = (int)p.g1.segs.size();
+    t.seg_count = 1;
+    GemmSeg sg{};
+    sg.a = Bt.ptr(info[i].first);
+    sg.lda = x.cols;
+    sg.b = Rin.ptr(info[i].second);
+    sg.ldb = rk.cols;
+    sg.k = x.cols;
+    sg.alpha = 1.0;
+    p.g1.segs.push_back(sg);
+    p.g1.tasks.push_back(t);
+    p.g1.flops += 8LL * x.rows * x.cols * rk.cols;
+  }
+  // step 2: F2(a,w,a'',s',b')
+  std::map<std::array<int, 5>, int> idx;
+  std::vector<std::array<int, 5>> keys;
+  std::vector<std::vector<std::pair<int, double>>> terms;
+  for (int i = 0; i < (int)info.size(); ++i) {
+    const Block& x = Bt.blocks[info[i].first];
+    const Block& rk = Rin.blocks[info[i].second];
+    int a = x.key[0], s = x.key[1], b = x.key[2], wp = rk.key[1], bp = rk.key[2];
+    const auto& rc = rec_->right_env(bl.s[a].t, s, br.s[b].t, wp, br.s[bp].t);
+    for (const auto& e : rc) {
+      int napp = bl.s[a].n + M.chan[e.w].n;
+      int app = bl.find(napp, e.tapp);
+      if (app < 0) continue;
+      if (Rout.find(bkey(a, e.w, app)) < 0) continue;
+      if (Bt.find(bkey(app, e.sp, bp)) < 0) continue;
+      std::array<int, 5> key{a, e.w, app, e.sp, bp};
+      auto it = idx.find(key);
+      int id;
+      if (it == idx.end()) {
+        id = (int)keys.size();
+        idx[key] = id;
+        keys.push_back(key);
+        terms.emplace_back();
+        p.t2.add((uint64_t)id, a, e.w, app, e.sp, bp, bl.s[a].d, br.s[bp].d);
+      } else {
+        id = it->second;
+      }
+      terms[id].push_back({i, e.f});
+    }
+  }
+  alloc(p.t2, false);
+  for (int id = 0; id < (int)keys.size(); ++id) {
+    const Block& bk = p.t2.blocks[id];
+    LincombTask t{};
+    t.out = p.t2.ptr(id);
+    t.rows = bk.rows;
+    t.cols = bk.cols;
+    t.ld_out = bk.cols;
+    t.term_begin = (int)p.lc.terms.size();
+    t.term_count = (int)terms[id].size();
+    for (auto& tm : terms[id]) p.lc.terms.push_back({p.t1.ptr(tm.first), p.t1.blocks[tm.first].cols, tm.second});
+    p.lc.tasks.push_back(t);
+  }
+  // step 3: R'(a,w,a'') = sum_{s',b'} F2(a,w,a'',s',b') B(a'',s',b')^H
+  std::map<std::array<int, 3>, std::vector<int>> outsegs;
+  for (int id = 0; id < (int)keys.size(); ++id) outsegs[{keys[id][0], keys[id][1], keys[id][2]}].push_back(id);
+  for (int ob = 0; ob < (int)Rout.blocks.size(); ++ob) {
+    const Block& o = Rout.blocks[ob];
+    GemmTask t{};
+    t.c = Rout.ptr(ob);
+    t.rows = o.rows;
+    t.cols = o.cols;
+    t.ldc = o.cols;
+    t.seg_begin = (int)p.g3.segs.size();
+    int cnt = 0;
+    auto it = outsegs.find({o.key[0], o.key[1], o.key[2]});
+    if (it != outsegs.end())
+      for (int id : it->second) {
+        auto& k = keys[id];
+        int bb = Bt.find(bkey(k[2], k[3], k[4]));
+        const Block& bk = Bt.blocks[bb];
+        GemmSeg sg{};
+        sg.a = p.t2.ptr(id);
+        sg.lda = p.t2.blocks[id].cols;
+        sg.b = Bt.ptr(bb);
+        sg.ldb = bk.cols;
+        sg.op_b = OP_C;
+        sg.k = bk.cols;
+        sg.alpha = 1.0;
+        p.g3.segs.push_back(sg);
+        p.g3.flops += 8LL * o.rows * bk.cols * o.cols;
+        ++cnt;
+      }
+    t.seg_count = cnt;
+    p.g3.tasks.push_back(t);
+  }
+  p.g1.finalize(stream_);
+  p.lc.finalize(stream_);
+  p.g3.finalize(stream_);
+  Bases4 B{{0, 0, 0, 0}};
+  p.g1.launch(stream_, B);
+  p.lc.launch(stream_);
+  p.g3.launch(stream_, B);
+  stats_.env_flops += p.g1.flops + p.g3.flops;
+}
+
+void Engine::form_theta(const BTensor& X, const BTensor& Y, BTensor& theta, const BondSpace& bl, const BondSpace& bm,
+                        const BondSpace& br) {
+  build_theta_layout(theta, bl, br);
+  alloc(theta, true);
+  GemmPlan g;
+  std::vector<std::vector<int>> yby(bm.s.size());
+  for (int i = 0; i < (int)Y.blocks.size(); ++i) yby[Y.blocks[i].key[0]].push_back(i);
+  for (int xi = 0; xi < (int)X.blocks.size(); ++xi) {
+    const Block& x = X.blocks[xi];
+    for (int yi : yby[x.key[2]]) {
+      const Block& y = Y.blocks[yi];
+      int tb = theta.find(bkey(x.key[0], x.key[1], bm.s[x.key[2]].t, y.key[1], y.key[2]));
+      if (tb < 0) throw Error(-5, "theta block missing");
+      GemmTask t{};
+      t.c = theta.ptr(tb);
+      t.rows = x.rows;
+      t.cols = y.cols;
+      t.ldc = y.cols;
+      t.seg_begin = (int)g.segs.size();
+      t.seg_count = 1;
+      GemmSeg sg{};
+      sg.a = X.ptr(xi);
+      sg.lda = x.cols;
+      sg.b = Y.ptr(yi);
+      sg.ldb = y.cols;
+      sg.k = x.cols;
+      sg.alpha = 1.0;
+      g.segs.push_back(sg);
+      g.tasks.push_back(t);
+    }
+  }
+  g.finalize(stream_);
+  g.launch(stream_, Bases4{{0, 0, 0, 0}});
+}
+
+// ---------------------------------------------------------------------------
+// Krylov exponential: x <- exp(-i tau H) x  (Sec. S2.2, Lanczos with full
+// re-orthogonalisation applied twice, adaptive dimension)
+// ---------------------------------------------------------------------------
+
+void Engine::expm(HeffPlan& H, cplx* x, double tau) {
+  const long long n = H.n;
+  const int kmax = opt_.krylov_max;
+  if (kcap_ < n) {
+    kv_ = DevBuf((size_t)(kmax + 1) * n * sizeof(cplx), stream_);
+    kw_ = DevBuf((size_t)n * sizeof(cplx), stream_);
+    kcap_ = n;
+  }
+  if (!kpart_.p) {
+    kpart_ = DevBuf((size_t)(KRYLOV_MAX + 1) * 296 * sizeof(cplx), stream_);
+    kh1_ = DevBuf((KRYLOV_MAX + 1) * sizeof(cplx), stream_);
+    kh2_ = DevBuf((KRYLOV_MAX + 1) * sizeof(cplx), stream_);
+    knrm_ = DevBuf(2 * sizeof(cplx), stream_);
+    kstate_ = DevBuf(sizeof(KrylovState), stream_);
+  }
+  cplx* V = kv_.as<cplx>();
+  cplx* w = kw_.as<cplx>();
+  KrylovState* st = kstate_.as<KrylovState>();
+  const int G = dots_grid(n);
+  cplx* part = kpart_.as<cplx>();
+  cplx* h1 = kh1_.as<cplx>();
+  cplx* h2 = kh2_.as<cplx>();
+  cplx* nrm = knrm_.as<cplx>();
+  const int* done = &st->done;
+  launch_dots(x, 0, 1, x, n, part, G, nrm, nullptr, stream_);
+  launch_krylov_init(st, nrm, stream_);
+  launch_scale(x, &st->beta0, V, n, done, stream_);
+  KrylovState* hst = reinterpret_cast<KrylovState*>(pinned_);
+  int* hdone = &hst->done;
+  int k = 0;
+  for (; k < kmax; ++k) {
+    cplx* vk = V + (long long)k * n;
+    H.apply(vk, w, stream_);
+    launch_dots(V, n, k + 1, w, n, part, G, h1, done, stream_);
+    launch_axpy_many(V, n, k + 1, h1, w, n, done, stream_);
+    launch_dots(V, n, k + 1, w, n, part, G, h2, done, stream_);
+    launch_axpy_many(V, n, k + 1, h2, w, n, done, stream_);
+    launch_dots(w, 0, 1, w, n, part, G, nrm, done, stream_);
+    launch_krylov_step(st, h1, nrm, tau, opt_.krylov_tol, kmax, stream_);
+    launch_scale(w, &st->beta[k], V + (long long)(k + 1) * n, n, done, stream_);
+    TDVP_CUDA(cudaMemcpyAsync(hdone, done, 2 * sizeof(int), cudaMemcpyDeviceToHost, stream_));
+    TDVP_CUDA(cudaStreamSynchronize(stream_));
+    stats_.matvecs += 1;
+    stats_.heff_flops += H.flops();
+    if (hst->bad) throw Error(-4, "non-finite value in the Krylov recurrence");
+    if (*hdone) break;
+  }
+  stats_.max_krylov = std::max(stats_.max_krylov, k + 1);
+  launch_combine(V, n, &st->nv, st->coef, &st->beta0, x, n, stream_);
+}
+
+// ---------------------------------------------------------------------------
+// SVD split with truncation (Sec. S2.4)
+// ---------------------------------------------------------------------------
+
+double Engine::split(BTensor& theta, const BondSpace& bl, const BondSpace& br, long long chi_max, double eps,
+                     bool absorb_right, BondSpace& bm, BTensor& X, BTensor& Y) {
+  const Model& M = model_;
+  // group blocks by the coupled label c = (n_a + n_s1, t_c)
+  struct Grp {
+    int n, t;
+    std::vector<std::pair<int, int>> rows;  // (a, s1)
+    std::vector<std::pair<int, int>> cols;  // (s2, b)
+    std::map<std::pair<int, int>, int> roff, coff;
+    int p = 0, q = 0;
+  };
+  std::map<std::pair<int, int>, int> gidx;
+  std::vector<Grp> groups;
+  for (const Block& b : theta.blocks) {
+    int a = b.key[0], s1 = b.key[1], tc = b.key[2], s2 = b.key[3], bb = b.key[4];
+    int nc = bl.s[a].n + M.site[s1].n;
+    auto key = std::make_pair(nc, tc);
+    auto it = gidx.find(key);
+    int g;
+    if (it == gidx.end()) {
+      g = (int)groups.size();
+      gidx[key] = g;
+      groups.push_back(Grp());
+      groups.back().n = nc;
+      groups.back().t = tc;
+    } else {
+      g = it->second;
+    }
+    Grp& G = groups[g];
+    if (!G.roff.count({a, s1})) {
+      G.roff[{a, s1}] = G.p;
+      G.rows.push_back({a, s1});
+      G.p += bl.s[a].d;
+    }
+    if (!G.coff.count({s2, bb})) {
+      G.coff[{s2, bb}] = G.q;
+      G.cols.push_back({s2, bb});
+      G.q += br.s[bb].d;
+    }
+  }
+  const int ng = (int)groups.size();
+  // workspace: per group G (max(p,q) x min(p,q)) and V (min^2), sv, perm
+  std::vector<long long> goff(ng), voff(ng);
+  std::vector<int> soff(ng);
+  long long gtot = 0, vtot = 0;
+  int stot = 0, maxq = 1;
+  for (int g = 0; g < ng; ++g) {
+    int P = std::max(groups[g].p, groups[g].q), Q = std::min(groups[g].p, groups[g].q);
+    goff[g] = gtot;
+    gtot += (long long)P * Q;
+    voff[g] = vtot;
+    vtot += (long long)Q * Q;
+    soff[g] = stot;
+    stot += Q;
+    maxq = std::max(maxq, Q);
+  }
+  DevBuf dG(std::max<long long>(gtot, 1) * sizeof(cplx), stream_);
+  DevBuf dV(std::max<long long>(vtot, 1) * sizeof(cplx), stream_);
+  DevBuf dS(std::max(stot, 1) * sizeof(double), stream_);
+  DevBuf dP(std::max(stot, 1) * sizeof(int), stream_);
+  cplx* Gp = dG.as<cplx>();
+  cplx* Vp = dV.as<cplx>();
+  double* Sp = dS.as<double>();
+  int* Pp = dP.as<int>();
+  // gather theta blocks into G (M itself if p >= q, else M^H)
+  CopyPlan gather;
+  for (const Block& b : theta.blocks) {
+    int a = b.key[0], s1 = b.key[1], s2 = b.key[3], bb = b.key[4];
+    int g = gidx[{bl.s[a].n + M.site[s1].n, b.key[2]}];
+    Grp& G = groups[g];
+    int r0 = G.roff[{a, s1}], c0 = G.coff[{s2, bb}];
+    CopyTask t{};
+    t.src = theta.data() + b.off;
+    t.rows = b.rows;
+    t.cols = b.cols;
+    t.src_rs = b.cols;
+    t.src_cs = 1;
+    if (G.p >= G.q) {  // column-major p x q
+      t.dst = Gp + goff[g] + r0 + (long long)c0 * G.p;
+      t.dst_rs = 1;
+      t.dst_cs = G.p;
+    } else {  // M^H: column-major q x p, element (col, row) = conj(M[row][col])
+      t.dst = Gp + goff[g] + c0 + (long long)r0 * G.q;
+      t.dst_rs = G.q;
+      t.dst_cs = 1;
+      t.conj = 1;
+    }
+    gather.tasks.push_back(t);
+  }
+  gather.finalize(stream_);
+  gather.launch(stream_);
+  std::vector<SvdTask> st(ng);
+  std::vector<TruncSector> ts(ng);
+  for (int g = 0; g < ng; ++g) {
+    int P = std::max(groups[g].p, groups[g].q), Q = std::min(groups[g].p, groups[g].q);
+    st[g] = {Gp + goff[g], Vp + voff[g], Sp + soff[g], Pp + soff[g], P, Q};
+    ts[g] = {Sp + soff[g], Q, M.mult_dim(groups[g].t)};
+  }
+  DevBuf dst = upload(st, stream_);
+  launch_jacobi_svd(dst.as<SvdTask>(), ng, maxq, 60, 1e-15, dstatus_, stream_);
+  // truncation
+  DevBuf dts = upload(ts, stream_);
+  DevBuf doffs = upload(soff, stream_);
+  DevBuf downer(std::max(stot, 1) * sizeof(int), stream_), dorder(std::max(stot, 1) * sizeof(int), stream_);
+  DevBuf dkept(std::max(ng, 1) * sizeof(int), stream_), dstats(8 * sizeof(double), stream_);
+  launch_truncate(dts.as<TruncSector>(), ng, doffs.as<int>(), stot, eps, chi_max, downer.as<int>(), dorder.as<int>(),
+                  dkept.as<int>(), dstats.as<double>(), stream_);
+  std::vector<int> kept(ng);
+  double hstats[8];
+  TDVP_CUDA(cudaMemcpyAsync(kept.data(), dkept.p, ng * sizeof(int), cudaMemcpyDeviceToHost, stream_));
+  TDVP_CUDA(cudaMemcpyAsync(hstats, dstats.p, 5 * sizeof(double), cudaMemcpyDeviceToHost, stream_));
+  TDVP_CUDA(cudaStreamSynchronize(stream_));
+  // new bond: kept sectors sorted by (n, t)
+  std::vector<std::pair<std::pair<int, int>, int>> ns;
+  for (int g = 0; g < ng; ++g)
+    if (kept[g] > 0) ns.push_back({{groups[g].n, groups[g].t}, g});
+  std::sort(ns.begin(), ns.end());
+  bm = BondSpace();
+  for (auto& e : ns) bm.s.push_back({e.first.first, e.first.second, kept[e.second]});
+  bm.build_index();
+  build_site_layout(X, bl, bm);
+  build_site_layout(Y, bm, br);
+  alloc(X, false);
+  alloc(Y, false);
+  double* gsc = dstats.as<double>() + 2;
+  CopyPlan scatter;
+  for (auto& e : ns) {
+    int g = e.second;
+    const Grp& G = groups[g];
+    int k = kept[g];
+    int c = bm.find(G.n, G.t);
+    const double* sv = Sp + soff[g];
+    const int* perm = Pp + soff[g];
+    cplx* Gg = Gp + goff[g];
+    cplx* Vg = Vp + voff[g];
+    bool direct = G.p >= G.q;
+    // left factor blocks (a, s1, c): rows r0.. of the left singular vectors
+    for (auto& rw : G.rows) {
+      int xb = X.find(bkey(rw.first, rw.second, c));
+      if (xb < 0) throw Error(-5, "X block missing");
+      int r0 = G.roff.at(rw);
+      CopyTask t{};
+      t.dst = X.ptr(xb);
+      t.rows = bl.s[rw.first].d;
+      t.cols = k;
+      t.dst_rs = k;
+      t.dst_cs = 1;
+      t.col_map = perm;
+      if (direct) {  // U = G / S
+        t.src = Gg + r0;
+        t.src_rs = 1;
+        t.src_cs = G.p;
+        t.scale = sv;
+        t.scale_mode = absorb_right ? 2 : 0;
+      } else {  // U = V
+        t.src = Vg + r0;
+        t.src_rs = 1;
+        t.src_cs = G.p;
+        t.scale = sv;
+        t.scale_mode = absorb_right ? 0 : 1;
+      }
+      if (!absorb_right) t.gscale = gsc;
+      scatter.tasks.push_back(t);
+    }
+    for (auto& cl : G.cols) {
+      int yb = Y.find(bkey(c, cl.first, cl.second));
+      if (yb < 0) throw Error(-5, "Y block missing");
+      int c0 = G.coff.at(cl);
+      CopyTask t{};
+      t.dst = Y.ptr(yb);
+      t.rows = k;
+      t.cols = br.s[cl.second].d;
+      t.dst_rs = t.cols;
+      t.dst_cs = 1;
+      t.row_map = perm;
+      t.conj = 1;
+      if (direct) {  // S V^H: dst[kr][col] = S conj(V[col][perm kr])
+        t.src = Vg + c0;
+        t.src_rs = G.q;
+        t.src_cs = 1;
+        t.scale = sv;
+        t.scale_mode = absorb_right ? 3 : 0;
+      } else {  // V_M = W / S: S V_M^H = conj(W)^T
+        t.src = Gg + c0;
+        t.src_rs = G.q;
+        t.src_cs = 1;
+        t.scale = sv;
+        t.scale_mode = absorb_right ? 0 : 4;
+      }
+      if (absorb_right) t.gscale = gsc;
+      scatter.tasks.push_back(t);
+    }
+  }
+  scatter.finalize(stream_);
+  scatter.launch(stream_);
+  long long chi = 0;
+  for (auto& s : bm.s) chi += (long long)s.d * M.mult_dim(s.t);
+  stats_.chi_max_seen = std::max(stats_.chi_max_seen, chi);
+  return hstats[1] / (hstats[0] > 0 ? hstats[0] : 1.0);
+}
+
+// ---------------------------------------------------------------------------
+// the time step (Sec. S2.2)
+// ---------------------------------------------------------------------------
+
+void Engine::step(double dt, long long chi_max, double eps) {
+  if (bond_only_) throw Error(-2, "a bond problem has no chain to evolve");
+  if (!(dt > 0) || chi_max < 1 || !(eps >= 0)) throw Error(-1, "invalid step arguments");
+  chain_heff_.reset();
+  auto t0 = std::chrono::steady_clock::now();
+  const double tau = dt / 2;
+  const int L = L_;
+  for (int i = 0; i + 1 < L; ++i) {
+    BTensor theta;
+    form_theta(site_[i], site_[i + 1], theta, bonds_[i], bonds_[i + 1], bonds_[i + 2]);
+    {
+      HeffPlan H;
+      plan_heff2(H, Lenv_[i], Renv_[i + 2], theta, bonds_[i], bonds_[i + 2]);
+      expm(H, theta.data(), tau);
+    }
+    BondSpace bm;
+    BTensor X, Y;
+    double disc = split(theta, bonds_[i], bonds_[i + 2], chi_max, eps, true, bm, X, Y);
+    stats_.max_discarded = std::max(stats_.max_discarded, disc);
+    bonds_[i + 1] = bm;
+    site_[i] = std::move(X);
+    site_[i + 1] = std::move(Y);
+    update_left_env(Lenv_[i], site_[i], Lenv_[i + 1], bonds_[i], bonds_[i + 1]);
+    if (i + 2 < L) {
+      HeffPlan H1;
+      plan_heff1(H1, Lenv_[i + 1], Renv_[i + 2], site_[i + 1], bonds_[i + 1], bonds_[i + 2]);
+      expm(H1, site_[i + 1].data(), -tau);
+    }
+  }
+  for (int i = L - 2; i >= 0; --i) {
+    BTensor theta;
+    form_theta(site_[i], site_[i + 1], theta, bonds_[i], bonds_[i + 1], bonds_[i + 2]);
+    {
+      HeffPlan H;
+      plan_heff2(H, Lenv_[i], Renv_[i + 2], theta, bonds_[i], bonds_[i + 2]);
+      expm(H, theta.data(), tau);
+    }
+    BondSpace bm;
+    BTensor X, Y;
+    double disc = split(theta, bonds_[i], bonds_[i + 2], chi_max, eps, false, bm, X, Y);
+    stats_.max_discarded = std::max(stats_.max_discarded, disc);
+    bonds_[i + 1] = bm;
+    site_[i] = std::move(X);
+    site_[i + 1] = std::move(Y);
+    update_right_env(Renv_[i + 2], site_[i + 1], Renv_[i + 1], bonds_[i + 1], bonds_[i + 2]);
+    if (i > 0) {
+      HeffPlan H1;
+      plan_heff1(H1, Lenv_[i], Renv_[i + 1], site_[i], bonds_[i], bonds_[i + 1]);
+      expm(H1, site_[i].data(), -tau);
+    }
+  }
+  TDVP_CUDA(cudaStreamSynchronize(stream_));
+  int hs[1];
+  TDVP_CUDA(cudaMemcpy(hs, dstatus_, sizeof(int), cudaMemcpyDeviceToHost));
+  if (hs[0] != 0) throw Error(-4, "Jacobi SVD did not converge");
+  stats_.seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// ---------------------------------------------------------------------------
+// measurement (a9): overlap environments from the centre at site 0
+// ---------------------------------------------------------------------------
+
+void Engine::measure(double* n_out, double* sz_out, double* docc_out, double* s_ent, double* energy,
+                     double* n_up_out) {
+  if (bond_only_) throw Error(-2, "a bond problem has no chain to measure");
+  const Model& M = model_;
+  const int L = L_;
+  // Omega_0 = 1 on the single sector of the left edge
+  BTensor Om;
+  Om.kind = OMEGA;
+  for (int a = 0; a < (int)bonds_[0].s.size(); ++a) Om.add(bkey(a, 0, a), a, 0, a, 0, 0, bonds_[0].s[a].d, bonds_[0].s[a].d);
+  alloc(Om, true);
+  std::vector<cplx> one(1, cplx{1.0, 0.0});
+  TDVP_CUDA(cudaMemcpyAsync(Om.data(), one.data(), sizeof(cplx), cudaMemcpyHostToDevice, stream_));
+  const int NS = 5;  // slots per site: n, n_up, n_dn, n_up n_dn, norm
+  DevBuf dres((size_t)L * NS * sizeof(double), stream_);
+  DevBuf dent((size_t)std::max(L - 1, 1) * sizeof(double), stream_);
+  for (int i = 0; i < L; ++i) {
+    const BTensor& T = site_[i];
+    // X(a,s,b) = Omega_a T(a,s,b)
+    BTensor X;
+    for (int bi = 0; bi < (int)T.blocks.size(); ++bi) {
+      const Block& b = T.blocks[bi];
+      X.add((uint64_t)bi, b.key[0], b.key[1], b.key[2], 0, 0, b.rows, b.cols);
+    }
+    alloc(X, false);
+    GemmPlan g1, g2;
+    for (int bi = 0; bi < (int)T.blocks.size(); ++bi) {
+      const Block& b = T.blocks[bi];
+      int ob = Om.find(bkey(b.key[0], 0, b.key[0]));
+      GemmTask t{};
+      t.c = X.ptr(bi);
+      t.rows = b.rows;
+      t.cols = b.cols;
+      t.ldc = b.cols;
+      t.seg_begin = (int)g1.segs.size();
+      t.seg_count = 1;
+      GemmSeg sg{};
+      sg.a = Om.ptr(ob);
+      sg.lda = b.rows;
+      sg.b = T.ptr(bi);
+      sg.ldb = b.cols;
+      sg.k = b.rows;
+      sg.alpha = 1.0;
+      g1.segs.push_back(sg);
+      g1.tasks.push_back(t);
+    }
+    g1.finalize(stream_);
+    g1.launch(stream_, Bases4{{0, 0, 0, 0}});
+    // local expectation values
+    std::vector<DotTask> dts;
+    for (int bi = 0; bi < (int)T.blocks.size(); ++bi) {
+      const Block& b = T.blocks[bi];
+      int s = b.key[1];
+      double w[NS] = {M.occ_n[s], M.occ_up[s], M.occ_dn[s], M.occ_d[s], 1.0};
+      for (int k = 0; k < NS; ++k)
+        if (w[k] != 0.0) dts.push_back({T.ptr(bi), X.ptr(bi), b.rows, b.cols, b.cols, b.cols, i * NS + k, w[k]});
+    }
+    DevBuf ddt = upload(dts, stream_);
+    DevBuf dpart(std::max<size_t>(dts.size(), 1) * sizeof(double), stream_);
+    // write into a per-site staging then copy: wdot writes all slots [0, nslots)
+    DevBuf dsite((size_t)(L * NS) * sizeof(double), stream_);
+    launch_wdot(ddt.as<DotTask>(), (int)dts.size(), dpart.as<double>(), dsite.as<double>(), L * NS, stream_);
+    TDVP_CUDA(cudaMemcpyAsync(dres.as<double>() + i * NS, dsite.as<double>() + i * NS, NS * sizeof(double),
+                              cudaMemcpyDeviceToDevice, stream_));
+    if (i == L - 1) break;
+    // Omega_{i+1}(b) = sum_{a,s} T(a,s,b)^H X(a,s,b)
+    BTensor On;
+    On.kind = OMEGA;
+    const BondSpace& br = bonds_[i + 1];
+    for (int b = 0; b < (int)br.s.size(); ++b) On.add(bkey(b, 0, b), b, 0, b, 0, 0, br.s[b].d, br.s[b].d);
+    alloc(On, true);
+    std::vector<std::vector<int>> byb(br.s.size());
+    for (int bi = 0; bi < (int)T.blocks.size(); ++bi) byb[T.blocks[bi].key[2]].push_back(bi);
+    for (int b = 0; b < (int)br.s.size(); ++b) {
+      GemmTask t{};
+      t.c = On.ptr(b);
+      t.rows = br.s[b].d;
+      t.cols = br.s[b].d;
+      t.ldc = br.s[b].d;
+      t.seg_begin = (int)g2.segs.size();
+      t.seg_count = (int)byb[b].size();
+      for (int bi : byb[b]) {
+        const Block& tb = T.blocks[bi];
+        GemmSeg sg{};
+        sg.a = T.ptr(bi);
+        sg.lda = tb.cols;
+        sg.op_a = OP_C;
+        sg.b = X.ptr(bi);
+        sg.ldb = tb.cols;
+        sg.k = tb.rows;
+        sg.alpha = 1.0;
+        g2.segs.push_back(sg);
+      }
+      g2.tasks.push_back(t);
+    }
+    g2.finalize(stream_);
+    g2.launch(stream_, Bases4{{0, 0, 0, 0}});
+    if (s_ent) {
+      // eigenvalues of each Omega block (Hermitian PSD: singular values) -> entropy
+      int ns = (int)br.s.size();
+      std::vector<long long> go(ns);
+      std::vector<int> so(ns);
+      long long gt = 0, vt = 0;
+      int stt = 0, mq = 1;
+      for (int b = 0; b < ns; ++b) {
+        go[b] = gt;
+        gt += (long long)br.s[b].d * br.s[b].d;
+        so[b] = stt;
+        stt += br.s[b].d;
+        mq = std::max(mq, br.s[b].d);
+      }
+      vt = gt;
+      DevBuf dG(gt * sizeof(cplx), stream_), dV(vt * sizeof(cplx), stream_);
+      DevBuf dS(stt * sizeof(double), stream_), dP(stt * sizeof(int), stream_);
+      TDVP_CUDA(cudaMemcpyAsync(dG.p, On.data(), gt * sizeof(cplx), cudaMemcpyDeviceToDevice, stream_));
+      std::vector<SvdTask> st(ns);
+      std::vector<TruncSector> ts(ns);
+      for (int b = 0; b < ns; ++b) {
+        st[b] = {dG.as<cplx>() + go[b], dV.as<cplx>() + go[b], dS.as<double>() + so[b], dP.as<int>() + so[b],
+                 br.s[b].d, br.s[b].d};
+        ts[b] = {dS.as<double>() + so[b], br.s[b].d, M.mult_dim(br.s[b].t)};
+      }
+      DevBuf dst = upload(st, stream_), dts2 = upload(ts, stream_);
+      launch_jacobi_svd(dst.as<SvdTask>(), ns, mq, 60, 1e-15, dstatus_, stream_);
+      launch_entropy(dts2.as<TruncSector>(), ns, dent.as<double>() + i, stream_);
+      TDVP_CUDA(cudaStreamSynchronize(stream_));
+    }
+    Om = std::move(On);
+    TDVP_CUDA(cudaStreamSynchronize(stream_));
+  }
+  std::vector<double> res((size_t)L * NS);
+  TDVP_CUDA(cudaMemcpyAsync(res.data(), dres.p, res.size() * sizeof(double), cudaMemcpyDeviceToHost, stream_));
+  std::vector<double> ent(std::max(L - 1, 1));
+  if (s_ent)
+    TDVP_CUDA(cudaMemcpyAsync(ent.data(), dent.p, (L - 1) * sizeof(double), cudaMemcpyDeviceToHost, stream_));
+  if (energy) {
+    HeffPlan H1;
+    plan_heff1(H1, Lenv_[0], Renv_[1], site_[0], bonds_[0], bonds_[1]);
+    DevBuf out(std::max<long long>(H1.n, 1) * sizeof(cplx), stream_);
+    H1.apply(site_[0].data(), out.as<cplx>(), stream_);
+    DevBuf part((size_t)296 * sizeof(cplx), stream_), e(sizeof(cplx), stream_);
+    launch_dots(site_[0].data(), 0, 1, out.as<cplx>(), H1.n, part.as<cplx>(), dots_grid(H1.n), e.as<cplx>(), nullptr,
+                stream_);
+    cplx he;
+    TDVP_CUDA(cudaMemcpyAsync(&he, e.p, sizeof(cplx), cudaMemcpyDeviceToHost, stream_));
+    TDVP_CUDA(cudaStreamSynchronize(stream_));
+    *energy = he.x;
+  }
+  TDVP_CUDA(cudaStreamSynchronize(stream_));
+  int hs = 0;
+  TDVP_CUDA(cudaMemcpy(&hs, dstatus_, sizeof(int), cudaMemcpyDeviceToHost));
+  if (hs != 0) throw Error(-4, "Jacobi eigenvalue iteration did not converge");
+  // back to the frame of Eq. (FHM): n_up = n'_up, n_dn = 1 - n'_dn
+  for (int i = 0; i < L; ++i) {
+    const double* r = &res[(size_t)i * NS];
+    double nup = r[1], ndn = r[2], dd = r[3];
+    double n_up = nup, n_dn = 1.0 - ndn;
+    if (n_out) n_out[i] = n_up + n_dn;
+    if (sz_out) sz_out[i] = 0.5 * (n_up - n_dn);
+    if (docc_out) docc_out[i] = nup - dd;
+    if (n_up_out) n_up_out[i] = n_up;
+  }
+  if (s_ent)
+    for (int k = 0; k < L - 1; ++k) s_ent[k] = ent[k];
+}
+
+}  // namespace tdvp

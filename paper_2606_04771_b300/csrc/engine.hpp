@@ -1,0 +1,209 @@
+// Two-site TDVP engine on one GPU (host orchestration).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "common.hpp"
+#include "kernels.hpp"
+#include "sym.hpp"
+
+namespace tdvp {
+
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define TDVP_CUDA(x)                                                                                 \
+  do {                                                                                               \
+    cudaError_t e_ = (x);                                                                            \
+    if (e_ != cudaSuccess)                                                                           \
+      throw ::tdvp::Error(e_ == cudaErrorMemoryAllocation ? -3 : -6,                                 \
+                          std::string(#x) + ": " + cudaGetErrorString(e_));                          \
+  } while (0)
+
+// stream-ordered device buffer
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaStream_t s = nullptr;
+  DevBuf() = default;
+  DevBuf(size_t b, cudaStream_t st);
+  ~DevBuf();
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept { *this = std::move(o); }
+  DevBuf& operator=(DevBuf&& o) noexcept;
+  void reset();
+  template <class T>
+  T* as() const {
+    return reinterpret_cast<T*>(p);
+  }
+};
+
+enum Kind { SITE = 0, THETA = 1, LENV = 2, RENV = 3, OMEGA = 4 };
+
+struct Block {
+  int key[5];
+  int rows, cols;
+  long long off;  // complex elements
+};
+
+inline uint64_t bkey(int a, int b, int c, int d = 0, int e = 0) {
+  return ((uint64_t)(a & 0xfff) << 52) | ((uint64_t)(b & 0xfff) << 40) | ((uint64_t)((c + 2048) & 0xfff) << 28) |
+         ((uint64_t)(d & 0xfff) << 16) | ((uint64_t)(e & 0xffff));
+}
+
+struct BTensor {
+  int kind = SITE;
+  std::vector<Block> blocks;
+  std::unordered_map<uint64_t, int> map;
+  long long size = 0;
+  DevBuf buf;
+  int find(uint64_t k) const {
+    auto it = map.find(k);
+    return it == map.end() ? -1 : it->second;
+  }
+  void add(uint64_t k, int k0, int k1, int k2, int k3, int k4, int r, int c) {
+    Block b{{k0, k1, k2, k3, k4}, r, c, size};
+    map[k] = (int)blocks.size();
+    blocks.push_back(b);
+    size += (long long)r * c;
+  }
+  cplx* ptr(int bi) const { return buf.as<cplx>() + blocks[bi].off; }
+  cplx* data() const { return buf.as<cplx>(); }
+};
+
+struct GemmPlan {
+  std::vector<GemmTask> tasks;
+  std::vector<GemmSeg> segs;
+  std::vector<int3> tiles;
+  DevBuf dt, ds, dti;
+  long long flops = 0;  // algorithmic real flops (8 per complex MAC)
+  void finalize(cudaStream_t s);
+  void launch(cudaStream_t s, const Bases4& B) const;
+};
+
+struct LincombPlan {
+  std::vector<LincombTask> tasks;
+  std::vector<LincombTerm> terms;
+  std::vector<int2> chunks;
+  DevBuf dt, dm, dc;
+  long long bytes = 0;  // algorithmic bytes moved
+  void finalize(cudaStream_t s);
+  void launch(cudaStream_t s) const;
+};
+
+struct CopyPlan {
+  std::vector<CopyTask> tasks;
+  std::vector<int2> chunks;
+  DevBuf dt, dc;
+  void finalize(cudaStream_t s);
+  void launch(cudaStream_t s) const;
+};
+
+// effective Hamiltonian (two-site or one-site): GEMM -> lincomb -> GEMM
+struct HeffPlan {
+  BTensor t1, t2;  // intermediates (own their buffers)
+  GemmPlan g1, g3;
+  LincombPlan lc;
+  long long n = 0;  // vector length (complex); input is base 1, output base 2
+  void apply(const cplx* in, cplx* out, cudaStream_t s) const;
+  long long flops() const { return g1.flops + g3.flops; }
+};
+
+struct Opts {
+  int precision = 0;
+  int krylov_max = 20;
+  double krylov_tol = 1e-12;
+  int timeout_ms = 0;
+  cudaStream_t stream = nullptr;
+  int device = -1;
+};
+
+struct StepStats {
+  double max_discarded = 0, seconds = 0, heff_seconds = 0;
+  long long heff_flops = 0, env_flops = 0, matvecs = 0;
+  int max_krylov = 0;
+  long long chi_max_seen = 0;
+};
+
+class Engine {
+ public:
+  Engine(int L, double J, double U, bool su2, const Opts& o);
+  ~Engine();
+
+  // chain evolution
+  void step(double dt, long long chi_max, double eps);
+  void measure(double* n, double* sz, double* docc, double* s_ent, double* energy, double* n_up = nullptr);
+  const StepStats& stats() const { return stats_; }
+  int L() const { return L_; }
+  const BondSpace& bond(int k) const { return bonds_[k]; }
+  const Model& model() const { return model_; }
+  cudaStream_t stream() const { return stream_; }
+
+  // synthetic single-bond problem (environments and theta given by the caller)
+  static Engine* bond_problem(bool su2, double J, double U, const std::vector<Sector>& left,
+                              const std::vector<Sector>& right, const Opts& o);
+  bool bond_only() const { return bond_only_; }
+  BTensor& theta_layout() { return theta_; }
+  BTensor& left_env_bp() { return Lenv_[0]; }
+  BTensor& right_env_bp() { return Renv_[2]; }
+  void heff_apply_bond(const cplx* in, cplx* out);  // device pointers, bond problem only
+  HeffPlan& heff_plan_bond() { return *bp_heff_; }
+  HeffPlan& chain_heff0();  // two-site H_eff at bond (0,1) of a chain (centre at site 0)
+
+ private:
+  Engine() = default;
+  void init_common(bool su2, double J, double U, const Opts& o);
+  void init_neel();
+  void build_site_layout(BTensor& t, const BondSpace& l, const BondSpace& r) const;
+  void build_theta_layout(BTensor& t, const BondSpace& l, const BondSpace& r) const;
+  void build_lenv_layout(BTensor& t, const BondSpace& bra, const BondSpace& ket) const;
+  void build_renv_layout(BTensor& t, const BondSpace& ket, const BondSpace& bra) const;
+  void alloc(BTensor& t, bool zero);
+
+  void plan_heff2(HeffPlan& p, const BTensor& Lenv, const BTensor& Renv, const BTensor& theta,
+                  const BondSpace& bl, const BondSpace& br);
+  void plan_heff1(HeffPlan& p, const BTensor& Lenv, const BTensor& Renv, const BTensor& M, const BondSpace& bl,
+                  const BondSpace& br);
+  void update_left_env(const BTensor& Lin, const BTensor& A, BTensor& Lout, const BondSpace& bl,
+                       const BondSpace& br);
+  void update_right_env(const BTensor& Rin, const BTensor& B, BTensor& Rout, const BondSpace& bl,
+                        const BondSpace& br);
+  void form_theta(const BTensor& X, const BTensor& Y, BTensor& theta, const BondSpace& bl, const BondSpace& bm,
+                  const BondSpace& br);
+  // split theta at bond (i,i+1); absorb_right: S goes to Y (left-to-right sweep)
+  double split(BTensor& theta, const BondSpace& bl, const BondSpace& br, long long chi_max, double eps,
+               bool absorb_right, BondSpace& bm, BTensor& X, BTensor& Y);
+  void expm(HeffPlan& H, cplx* x, double tau);
+
+  int L_ = 0;
+  Model model_;
+  Opts opt_;
+  cudaStream_t stream_ = nullptr;
+  bool own_stream_ = false;
+  std::unique_ptr<Recoupler> rec_;
+  std::vector<BondSpace> bonds_;
+  std::vector<BTensor> site_;
+  std::vector<BTensor> Lenv_, Renv_;
+  BTensor theta_;  // bond-problem theta layout
+  std::unique_ptr<HeffPlan> bp_heff_, chain_heff_;
+  bool bond_only_ = false;
+  // Krylov workspace
+  DevBuf kv_, kw_, kpart_, kh1_, kh2_, knrm_, kstate_;
+  long long kcap_ = 0;
+  void* pinned_ = nullptr;
+  StepStats stats_;
+  int* dstatus_ = nullptr;
+
+  friend struct BondAccess;
+};
+
+}  // namespace tdvp

@@ -1,0 +1,678 @@
+// FP64 device kernels of the TDVP engine (CUDA cores, sm_103a).
+//
+// These are the exact-arithmetic (FP64) building blocks: a grouped complex GEMM
+// over planner-built task lists, the MPO linear combination, strided block
+// copies, Krylov vector algebra, the small Krylov exponential, one-sided Jacobi
+// SVD, truncation selection, block-weighted dots and the entanglement entropy.
+// All kernels are symmetry-agnostic; the host planner lowers every contraction
+// to task lists (common.hpp).
+#include <cuda_runtime.h>
+
+#include <cstdio>
+
+#include "common.hpp"
+#include "kernels.hpp"
+
+namespace tdvp {
+
+__device__ __forceinline__ cplx cmul(cplx a, cplx b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+__device__ __forceinline__ cplx cconj(cplx a) { return {a.x, -a.y}; }
+__device__ __forceinline__ void cfma(cplx& acc, cplx a, cplx b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+
+// ---------------------------------------------------------------------------
+// K1 (FP64): grouped complex GEMM, 64x64 output tiles, 256 threads, 4x4 per thread
+// ---------------------------------------------------------------------------
+
+constexpr int GT = 64;   // tile edge
+constexpr int GK = 8;    // k step
+
+__global__ void __launch_bounds__(256) gemm_fp64_kernel(const GemmTask* __restrict__ tasks,
+                                                        const GemmSeg* __restrict__ segs,
+                                                        const int3* __restrict__ tiles, const Bases4 B) {
+  __shared__ cplx As[GK][GT + 1];
+  __shared__ cplx Bs[GK][GT + 1];
+  const int3 tr = tiles[blockIdx.x];
+  const GemmTask t = tasks[tr.x];
+  cplx* const cptr = rebase(B, t.c_base, t.c);
+  const int m0 = tr.y * GT, n0 = tr.z * GT;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  cplx acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = {0.0, 0.0};
+
+  for (int sgi = 0; sgi < t.seg_count; ++sgi) {
+    const GemmSeg sg = segs[t.seg_begin + sgi];
+    const cplx* const ap = rebase(B, sg.a_base, sg.a);
+    const cplx* const bp = rebase(B, sg.b_base, sg.b);
+    for (int k0 = 0; k0 < sg.k; k0 += GK) {
+      // load A tile: GT rows x GK k
+      for (int e = threadIdx.x; e < GT * GK; e += 256) {
+        int r = e / GK, kk = e % GK;
+        int gr = m0 + r, gk = k0 + kk;
+        cplx v = {0.0, 0.0};
+        if (gr < t.rows && gk < sg.k) {
+          if (sg.op_a == OP_N) v = ap[(long long)gr * sg.lda + gk];
+          else v = cconj(ap[(long long)gk * sg.lda + gr]);
+        }
+        As[kk][r] = v;
+      }
+      for (int e = threadIdx.x; e < GT * GK; e += 256) {
+        int kk = e / GT, c = e % GT;
+        int gc = n0 + c, gk = k0 + kk;
+        cplx v = {0.0, 0.0};
+        if (gc < t.cols && gk < sg.k) {
+          if (sg.op_b == OP_N) v = bp[(long long)gk * sg.ldb + gc];
+          else v = cconj(bp[(long long)gc * sg.ldb + gk]);
+        }
+        Bs[kk][c] = v;
+      }
+      __syncthreads();
+      const double al = sg.alpha;
+#pragma unroll
+      for (int kk = 0; kk < GK; ++kk) {
+        cplx a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          a[i] = As[kk][ty + 16 * i];
+          a[i].x *= al;
+          a[i].y *= al;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) cfma(acc[i][j], a[i], b[j]);
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int r = m0 + ty + 16 * i;
+    if (r >= t.rows) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int c = n0 + tx + 16 * j;
+      if (c < t.cols) cptr[(long long)r * t.ldc + c] = acc[i][j];
+    }
+  }
+}
+
+void launch_gemm_fp64(const GemmTask* tasks, const GemmSeg* segs, const int3* tiles, int ntiles, const Bases4& B,
+                      cudaStream_t s) {
+  if (ntiles <= 0) return;
+  gemm_fp64_kernel<<<ntiles, 256, 0, s>>>(tasks, segs, tiles, B);
+}
+
+// ---------------------------------------------------------------------------
+// K3: MPO linear combination  out = sum coef * in
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) lincomb_kernel(const LincombTask* __restrict__ tasks,
+                                                      const LincombTerm* __restrict__ terms,
+                                                      const int2* __restrict__ chunks) {
+  const int2 ch = chunks[blockIdx.x];
+  const LincombTask t = tasks[ch.x];
+  const int n = t.rows * t.cols;
+  for (int e = ch.y + threadIdx.x; e < min(n, ch.y + LINCOMB_CHUNK); e += 256) {
+    int r = e / t.cols, c = e - r * t.cols;
+    cplx acc = {0.0, 0.0};
+    for (int k = 0; k < t.term_count; ++k) {
+      const LincombTerm tm = terms[t.term_begin + k];
+      cplx v = tm.in[(long long)r * tm.ld_in + c];
+      acc.x = fma(tm.coef, v.x, acc.x);
+      acc.y = fma(tm.coef, v.y, acc.y);
+    }
+    t.out[(long long)r * t.ld_out + c] = acc;
+  }
+}
+
+void launch_lincomb(const LincombTask* tasks, const LincombTerm* terms, const int2* chunks, int nchunks,
+                    cudaStream_t s) {
+  if (nchunks <= 0) return;
+  lincomb_kernel<<<nchunks, 256, 0, s>>>(tasks, terms, chunks);
+}
+
+// ---------------------------------------------------------------------------
+// strided block copy with optional maps, conjugation and scaling
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) copy_kernel(const CopyTask* __restrict__ tasks, const int2* __restrict__ chunks) {
+  const int2 ch = chunks[blockIdx.x];
+  const CopyTask t = tasks[ch.x];
+  const int n = t.rows * t.cols;
+  const double g = t.gscale ? *t.gscale : 1.0;
+  for (int e = ch.y + threadIdx.x; e < min(n, ch.y + LINCOMB_CHUNK); e += 256) {
+    int r = e / t.cols, c = e - r * t.cols;
+    int sr = t.row_map ? t.row_map[r] : r;
+    int sc = t.col_map ? t.col_map[c] : c;
+    cplx v = t.src[sr * t.src_rs + sc * t.src_cs];
+    if (t.conj) v.y = -v.y;
+    double f = g;
+    switch (t.scale_mode) {
+      case 1: f *= t.scale[c]; break;
+      case 2: f = t.scale[c] != 0.0 ? f / t.scale[c] : 0.0; break;
+      case 3: f *= t.scale[r]; break;
+      case 4: f = t.scale[r] != 0.0 ? f / t.scale[r] : 0.0; break;
+      default: break;
+    }
+    v.x *= f;
+    v.y *= f;
+    t.dst[r * t.dst_rs + c * t.dst_cs] = v;
+  }
+}
+
+void launch_copy(const CopyTask* tasks, const int2* chunks, int nchunks, cudaStream_t s) {
+  if (nchunks <= 0) return;
+  copy_kernel<<<nchunks, 256, 0, s>>>(tasks, chunks);
+}
+
+// ---------------------------------------------------------------------------
+// K4: Krylov vector algebra (FP64, deterministic two-stage reductions)
+// ---------------------------------------------------------------------------
+
+// partial[j * G + g] = sum over block g's range of conj(V_j) * w, j < nv
+__global__ void __launch_bounds__(256) dots_partial_kernel(const cplx* __restrict__ V, long long pitch, int nv,
+                                                           const cplx* __restrict__ w, long long n,
+                                                           cplx* __restrict__ partial, const int* done) {
+  if (done && *done) return;
+  const int j = blockIdx.y;
+  if (j >= nv) return;
+  const cplx* v = V + pitch * j;
+  cplx acc = {0.0, 0.0};
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
+    cplx a = v[i], b = w[i];
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(-a.y, b.x, acc.y);
+  }
+  __shared__ double sx[256], sy[256];
+  sx[threadIdx.x] = acc.x;
+  sy[threadIdx.x] = acc.y;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sx[threadIdx.x] += sx[threadIdx.x + o];
+      sy[threadIdx.x] += sy[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[(long long)j * gridDim.x + blockIdx.x] = {sx[0], sy[0]};
+}
+
+// out[j] = sum_g partial[j*G+g]; one warp per j, fixed order
+__global__ void dots_final_kernel(const cplx* __restrict__ partial, int G, int nv, cplx* __restrict__ out,
+                                  const int* done) {
+  if (done && *done) return;
+  int j = blockIdx.x;
+  if (j >= nv) return;
+  double x = 0, y = 0;
+  for (int g = threadIdx.x; g < G; g += 32) {
+    x += partial[(long long)j * G + g].x;
+    y += partial[(long long)j * G + g].y;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    x += __shfl_down_sync(0xffffffffu, x, o);
+    y += __shfl_down_sync(0xffffffffu, y, o);
+  }
+  if (threadIdx.x == 0) out[j] = {x, y};
+}
+
+// w -= sum_j h[j] V_j
+__global__ void __launch_bounds__(256) axpy_many_kernel(const cplx* __restrict__ V, long long pitch, int nv,
+                                                        const cplx* __restrict__ h, cplx* __restrict__ w,
+                                                        long long n, const int* done) {
+  if (done && *done) return;
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
+    cplx acc = w[i];
+    for (int j = 0; j < nv; ++j) {
+      cplx v = V[pitch * j + i], c = h[j];
+      acc.x -= c.x * v.x - c.y * v.y;
+      acc.y -= c.x * v.y + c.y * v.x;
+    }
+    w[i] = acc;
+  }
+}
+
+// out = sum_j coef[j] * V_j * scale   (coef on device, scale = *scal)
+__global__ void __launch_bounds__(256) combine_kernel(const cplx* __restrict__ V, long long pitch, const int* nvp,
+                                                      const cplx* __restrict__ coef, const double* scal,
+                                                      cplx* __restrict__ out, long long n) {
+  const int nv = *nvp;
+  const double s = scal ? *scal : 1.0;
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
+    cplx acc = {0.0, 0.0};
+    for (int j = 0; j < nv; ++j) {
+      cplx v = V[pitch * j + i], c = coef[j];
+      acc.x += c.x * v.x - c.y * v.y;
+      acc.y += c.x * v.y + c.y * v.x;
+    }
+    out[i] = {acc.x * s, acc.y * s};
+  }
+}
+
+// y = x / (*nrm) unless done; if nrm==0 leave y = 0
+__global__ void __launch_bounds__(256) scale_kernel(const cplx* __restrict__ x, const double* nrm,
+                                                    cplx* __restrict__ y, long long n, const int* done) {
+  if (done && *done) return;
+  double b = *nrm;
+  double f = b > 0 ? 1.0 / b : 0.0;
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
+    cplx v = x[i];
+    y[i] = {v.x * f, v.y * f};
+  }
+}
+
+static int blas_grid(long long n) {
+  long long g = (n + 255) / 256;
+  if (g > 148 * 8) g = 148 * 8;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+void launch_dots(const cplx* V, long long pitch, int nv, const cplx* w, long long n, cplx* partial, int G,
+                 cplx* out, const int* done, cudaStream_t s) {
+  dim3 grid(G, nv);
+  dots_partial_kernel<<<grid, 256, 0, s>>>(V, pitch, nv, w, n, partial, done);
+  dots_final_kernel<<<nv, 32, 0, s>>>(partial, G, nv, out, done);
+}
+
+void launch_axpy_many(const cplx* V, long long pitch, int nv, const cplx* h, cplx* w, long long n, const int* done,
+                      cudaStream_t s) {
+  axpy_many_kernel<<<blas_grid(n), 256, 0, s>>>(V, pitch, nv, h, w, n, done);
+}
+
+void launch_combine(const cplx* V, long long pitch, const int* nv, const cplx* coef, const double* scal, cplx* out,
+                    long long n, cudaStream_t s) {
+  combine_kernel<<<blas_grid(n), 256, 0, s>>>(V, pitch, nv, coef, scal, out, n);
+}
+
+void launch_scale(const cplx* x, const double* nrm, cplx* y, long long n, const int* done, cudaStream_t s) {
+  scale_kernel<<<blas_grid(n), 256, 0, s>>>(x, nrm, y, n, done);
+}
+
+int dots_grid(long long n) { return blas_grid(n) > 296 ? 296 : blas_grid(n); }
+
+// ---------------------------------------------------------------------------
+// Krylov bookkeeping kernels (single thread / single warp)
+// ---------------------------------------------------------------------------
+
+// st->beta0 = sqrt(Re(nrm2)); st->k = 0; st->done = (beta0 == 0)
+__global__ void krylov_init_kernel(KrylovState* st, const cplx* nrm2) {
+  double b = sqrt(fmax(nrm2->x, 0.0));
+  st->beta0 = b;
+  st->k = 0;
+  st->done = b > 0.0 ? 0 : 1;
+  st->nv = 0;
+  st->err = 0.0;
+  st->bad = (b == b) ? 0 : 1;
+  if (st->bad) st->done = 1;
+}
+
+// After the reorthogonalised w and its squared norm: record alpha_k, beta_k, then
+// compute c = exp(-i tau T_k) e_1 by a scaled Taylor series of the vector
+// (one lane per Krylov index), estimate the error beta_k |c_k| and decide.
+__global__ void krylov_step_kernel(KrylovState* st, const cplx* h1, const cplx* nrm2, double tau, double tol,
+                                   int kmax) {
+  if (st->done) return;
+  const int lane = threadIdx.x;
+  const int k = st->k;  // index of the vector just applied (0-based)
+  if (lane == 0) {
+    st->alpha[k] = h1[k].x;
+    st->beta[k] = sqrt(fmax(nrm2->x, 0.0));
+  }
+  __syncwarp();
+  const int n = k + 1;
+  double al = lane < n ? st->alpha[lane] : 0.0;
+  double bl = lane < n - 1 ? st->beta[lane] : 0.0;          // couples lane and lane+1
+  double bm = (lane > 0 && lane < n) ? st->beta[lane - 1] : 0.0;  // couples lane-1 and lane
+  double rowsum = lane < n ? fabs(al) + bl + bm : 0.0;
+  int bad = !(rowsum < 1e12);  // NaN or absurd: stop instead of looping
+  for (int o = 16; o > 0; o >>= 1) {
+    rowsum = fmax(rowsum, __shfl_xor_sync(0xffffffffu, rowsum, o));
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if (bad) {
+    if (lane == 0) {
+      st->bad = 1;
+      st->done = 1;
+      st->nv = 0;
+    }
+    return;
+  }
+  int steps = (int)ceil(fabs(tau) * rowsum / 0.5);
+  if (steps < 1) steps = 1;
+  const double h = tau / steps;
+  double xr = lane == 0 ? 1.0 : 0.0, xi = 0.0;
+  for (int s = 0; s < steps; ++s) {
+    double tr = xr, ti = xi, sr = xr, si = xi;
+    for (int m = 1; m <= 40; ++m) {
+      // y = T t
+      double upr = __shfl_down_sync(0xffffffffu, tr, 1), upi = __shfl_down_sync(0xffffffffu, ti, 1);
+      double dnr = __shfl_up_sync(0xffffffffu, tr, 1), dni = __shfl_up_sync(0xffffffffu, ti, 1);
+      double yr = al * tr + bl * upr + bm * dnr;
+      double yi = al * ti + bl * upi + bm * dni;
+      if (lane >= n) yr = yi = 0.0;
+      // t = (-i h / m) y
+      double f = h / m;
+      tr = f * yi;
+      ti = -f * yr;
+      sr += tr;
+      si += ti;
+      double mag = fabs(tr) + fabs(ti);
+      for (int o = 16; o > 0; o >>= 1) mag = fmax(mag, __shfl_xor_sync(0xffffffffu, mag, o));
+      if (mag < 1e-22) break;
+    }
+    xr = sr;
+    xi = si;
+  }
+  if (lane < n) st->coef[lane] = {xr, xi};
+  double last_r = __shfl_sync(0xffffffffu, xr, n - 1), last_i = __shfl_sync(0xffffffffu, xi, n - 1);
+  if (lane == 0) {
+    double b = st->beta[k];
+    double err = b * sqrt(last_r * last_r + last_i * last_i);
+    st->err = err;
+    st->nv = n;
+    if (!(err == err)) {
+      st->bad = 1;
+      st->nv = 0;
+    }
+    if (err < tol || b < 1e-14 || n >= kmax) st->done = 1;
+    st->k = k + 1;
+  }
+}
+
+void launch_krylov_init(KrylovState* st, const cplx* nrm2, cudaStream_t s) { krylov_init_kernel<<<1, 1, 0, s>>>(st, nrm2); }
+
+void launch_krylov_step(KrylovState* st, const cplx* h1, const cplx* nrm2, double tau, double tol, int kmax,
+                        cudaStream_t s) {
+  krylov_step_kernel<<<1, 32, 0, s>>>(st, h1, nrm2, tau, tol, kmax);
+}
+
+// ---------------------------------------------------------------------------
+// K6: one-sided (Hestenes) Jacobi SVD, one CTA per problem
+// ---------------------------------------------------------------------------
+
+constexpr int SVD_THREADS = 256;
+
+__device__ void col_pair(cplx* __restrict__ g, int p, int i, int j, double& a, double& b, cplx& c) {
+  const int lane = threadIdx.x & 31;
+  double sa = 0, sb = 0, cx = 0, cy = 0;
+  const cplx* gi = g + (long long)i * p;
+  const cplx* gj = g + (long long)j * p;
+  for (int r = lane; r < p; r += 32) {
+    cplx x = gi[r], y = gj[r];
+    sa = fma(x.x, x.x, fma(x.y, x.y, sa));
+    sb = fma(y.x, y.x, fma(y.y, y.y, sb));
+    cx = fma(x.x, y.x, fma(x.y, y.y, cx));
+    cy = fma(x.x, y.y, fma(-x.y, y.x, cy));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sa += __shfl_xor_sync(0xffffffffu, sa, o);
+    sb += __shfl_xor_sync(0xffffffffu, sb, o);
+    cx += __shfl_xor_sync(0xffffffffu, cx, o);
+    cy += __shfl_xor_sync(0xffffffffu, cy, o);
+  }
+  a = sa;
+  b = sb;
+  c = {cx, cy};
+}
+
+__device__ void rotate_cols(cplx* __restrict__ g, int ld, int len, int i, int j, double cs, double sn, cplx e) {
+  // g_i' = cs g_i - sn conj(e) g_j ; g_j' = sn e g_i + cs g_j
+  const int lane = threadIdx.x & 31;
+  cplx* gi = g + (long long)i * ld;
+  cplx* gj = g + (long long)j * ld;
+  for (int r = lane; r < len; r += 32) {
+    cplx x = gi[r], y = gj[r];
+    cplx ey = {e.x * y.x + e.y * y.y, e.x * y.y - e.y * y.x};  // conj(e) * y
+    cplx ex = {e.x * x.x - e.y * x.y, e.x * x.y + e.y * x.x};  // e * x
+    gi[r] = {cs * x.x - sn * ey.x, cs * x.y - sn * ey.y};
+    gj[r] = {sn * ex.x + cs * y.x, sn * ex.y + cs * y.y};
+  }
+}
+
+__global__ void __launch_bounds__(SVD_THREADS) jacobi_svd_kernel(const SvdTask* __restrict__ tasks, int max_sweeps,
+                                                                 double tol, int* __restrict__ status) {
+  const SvdTask t = tasks[blockIdx.x];
+  const int p = t.p, q = t.q;
+  const int warp = threadIdx.x >> 5, nwarp = SVD_THREADS / 32;
+  for (int e = threadIdx.x; e < q * q; e += SVD_THREADS) {
+    int r = e % q, c = e / q;
+    t.v[e] = {r == c ? 1.0 : 0.0, 0.0};
+  }
+  __shared__ int rotated;
+  __syncthreads();
+  const int qq = q + (q & 1);
+  const int m = qq - 1;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    for (int r = 0; r < m; ++r) {
+      for (int k = warp; k < qq / 2; k += nwarp) {
+        int i, j;
+        if (k == 0) {
+          i = 0;
+          j = 1 + r % m;
+        } else {
+          i = 1 + (r + k) % m;
+          j = 1 + (r - k + m) % m;
+        }
+        if (i > j) {
+          int tmp = i;
+          i = j;
+          j = tmp;
+        }
+        if (j >= q) continue;
+        double a, b;
+        cplx c;
+        col_pair(t.g, p, i, j, a, b, c);
+        double ac = sqrt(c.x * c.x + c.y * c.y);
+        if (ac == 0.0 || ac <= tol * sqrt(a * b)) continue;
+        double zeta = (b - a) / (2.0 * ac);
+        double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
+        cplx e = {c.x / ac, c.y / ac};
+        rotate_cols(t.g, p, p, i, j, cs, sn, e);
+        rotate_cols(t.v, q, q, i, j, cs, sn, e);
+        if ((threadIdx.x & 31) == 0) rotated = 1;
+      }
+      __syncthreads();
+    }
+    if (!rotated) break;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && sweep >= max_sweeps) atomicAdd(status, 1);
+  // singular values = column norms, then sort descending (rank counting, ties by index)
+  for (int j = warp; j < q; j += nwarp) {
+    double a, b;
+    cplx c;
+    col_pair(t.g, p, j, j, a, b, c);
+    if ((threadIdx.x & 31) == 0) t.sv[j] = sqrt(a);  // temporarily unsorted
+  }
+  __syncthreads();
+  // rank of each value; write perm, then sorted values into shared staging via sv in place
+  extern __shared__ double sbuf[];  // q doubles; NaN ranks last so the ranks stay a permutation
+  for (int j = threadIdx.x; j < q; j += SVD_THREADS) {
+    double v = t.sv[j];
+    sbuf[j] = (v == v) ? v : -1.0;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < q; j += SVD_THREADS) {
+    double vj = sbuf[j];
+    int rank = 0;
+    for (int i = 0; i < q; ++i) {
+      double vi = sbuf[i];
+      rank += (vi > vj) || (vi == vj && i < j);
+    }
+    t.perm[rank] = j;
+    t.sv[rank] = vj < 0.0 ? 0.0 : vj;
+  }
+}
+
+void launch_jacobi_svd(const SvdTask* tasks, int ntasks, int max_q, int max_sweeps, double tol, int* status,
+                       cudaStream_t s) {
+  if (ntasks <= 0) return;
+  size_t smem = (size_t)max_q * sizeof(double);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(jacobi_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  jacobi_svd_kernel<<<ntasks, SVD_THREADS, smem, s>>>(tasks, max_sweeps, tol, status);
+}
+
+// ---------------------------------------------------------------------------
+// K7: truncation selection over all sectors of a bond (one CTA)
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(1024) truncate_kernel(const TruncSector* __restrict__ secs, int nsec,
+                                                        const int* __restrict__ offs, int n, double eps,
+                                                        long long chi_max, int* __restrict__ owner,
+                                                        int* __restrict__ order, int* __restrict__ kept,
+                                                        double* __restrict__ stats) {
+  // owner[e] = sector of flat entry e ; offs[s] = first flat index of sector s
+  for (int s = threadIdx.x; s < nsec; s += blockDim.x) {
+    for (int i = 0; i < secs[s].r; ++i) owner[offs[s] + i] = s;
+    kept[s] = 0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    int se = owner[e];
+    double ve = secs[se].sv[e - offs[se]];
+    if (!(ve == ve)) ve = -1.0;
+    int rank = 0;
+    for (int f = 0; f < n; ++f) {
+      int sf = owner[f];
+      double vf = secs[sf].sv[f - offs[sf]];
+      if (!(vf == vf)) vf = -1.0;
+      rank += (vf > ve) || (vf == ve && f < e);
+    }
+    order[rank] = e;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double total = 0.0;
+    for (int r = 0; r < n; ++r) {
+      int e = order[r], se = owner[e];
+      double v = secs[se].sv[e - offs[se]];
+      total += v * v;
+    }
+    // longest tail with weight <= eps * total
+    int keep_eps = n;
+    double tail = 0.0;
+    for (int r = n - 1; r >= 1; --r) {
+      int e = order[r], se = owner[e];
+      double v = secs[se].sv[e - offs[se]];
+      if (tail + v * v <= eps * total) {
+        tail += v * v;
+        keep_eps = r;
+      } else {
+        break;
+      }
+    }
+    // bond-dimension cap with multiplet sizes, greedy in descending order
+    long long chi = 0;
+    int keep_chi = 0;
+    for (int r = 0; r < n; ++r) {
+      int se = owner[order[r]];
+      if (r > 0 && chi + secs[se].mult > chi_max) break;
+      chi += secs[se].mult;
+      keep_chi = r + 1;
+    }
+    int K = keep_eps < keep_chi ? keep_eps : keep_chi;
+    if (K < 1) K = 1;
+    double kw = 0.0;
+    long long kchi = 0;
+    for (int r = 0; r < K; ++r) {
+      int e = order[r], se = owner[e];
+      double v = secs[se].sv[e - offs[se]];
+      kw += v * v;
+      kchi += secs[se].mult;
+      kept[se] += 1;
+    }
+    stats[0] = total;
+    stats[1] = total - kw;           // discarded weight
+    stats[2] = kw > 0 ? 1.0 / sqrt(kw) : 0.0;  // renormalisation of the kept values
+    stats[3] = (double)K;
+    stats[4] = (double)kchi;
+  }
+}
+
+void launch_truncate(const TruncSector* secs, int nsec, const int* offs, int n, double eps, long long chi_max,
+                     int* owner, int* order, int* kept, double* stats, cudaStream_t s) {
+  truncate_kernel<<<1, 1024, 0, s>>>(secs, nsec, offs, n, eps, chi_max, owner, order, kept, stats);
+}
+
+// ---------------------------------------------------------------------------
+// K9: block-weighted dots (measurement) and entanglement entropy
+// ---------------------------------------------------------------------------
+
+// one CTA per task; out[slot] accumulated with atomics in slot order is not
+// deterministic, so each task writes its own partial and a second kernel sums
+// the partials of every slot in task order.
+__global__ void __launch_bounds__(256) wdot_kernel(const DotTask* __restrict__ tasks, double* __restrict__ partial) {
+  const DotTask t = tasks[blockIdx.x];
+  double acc = 0.0;
+  const int n = t.rows * t.cols;
+  for (int e = threadIdx.x; e < n; e += 256) {
+    int r = e / t.cols, c = e - r * t.cols;
+    cplx x = t.x[(long long)r * t.ldx + c], y = t.y[(long long)r * t.ldy + c];
+    acc += x.x * y.x + x.y * y.y;  // Re(conj(x) y)
+  }
+  __shared__ double sb[256];
+  sb[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sb[threadIdx.x] += sb[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = t.weight * sb[0];
+}
+
+__global__ void wdot_final_kernel(const DotTask* __restrict__ tasks, const double* __restrict__ partial, int ntasks,
+                                  double* __restrict__ out, int nslots) {
+  for (int s = threadIdx.x; s < nslots; s += blockDim.x) {
+    double acc = 0.0;
+    for (int k = 0; k < ntasks; ++k)
+      if (tasks[k].slot == s) acc += partial[k];
+    out[s] = acc;
+  }
+}
+
+void launch_wdot(const DotTask* tasks, int ntasks, double* partial, double* out, int nslots, cudaStream_t s) {
+  if (ntasks <= 0) return;
+  wdot_kernel<<<ntasks, 256, 0, s>>>(tasks, partial);
+  wdot_final_kernel<<<1, 256, 0, s>>>(tasks, partial, ntasks, out, nslots);
+}
+
+// S = -sum_sectors sum_k lam ln(lam / mult), lam = eigenvalue (weight) of a multiplet
+__global__ void entropy_kernel(const TruncSector* __restrict__ secs, int nsec, double* __restrict__ out) {
+  double acc = 0.0;
+  for (int s = threadIdx.x; s < nsec; s += blockDim.x) {
+    for (int i = 0; i < secs[s].r; ++i) {
+      double lam = secs[s].sv[i];
+      if (lam > 1e-300) acc -= lam * log(lam / secs[s].mult);
+    }
+  }
+  __shared__ double sb[256];
+  sb[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sb[threadIdx.x] += sb[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sb[0];
+}
+
+void launch_entropy(const TruncSector* secs, int nsec, double* out, cudaStream_t s) {
+  entropy_kernel<<<1, 256, 0, s>>>(secs, nsec, out);
+}
+
+}  // namespace tdvp

@@ -1,0 +1,51 @@
+// Launch wrappers of the device kernels (kernels.cu, split.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.hpp"
+
+namespace tdvp {
+
+constexpr int LINCOMB_CHUNK = 1024;  // elements per CTA in lincomb / copy
+constexpr int KRYLOV_MAX = 32;       // one warp holds the Krylov coefficients
+
+// Device-resident Krylov state: the host launches the loop without reading it
+// until the end (kernels return immediately once done is set).
+struct KrylovState {
+  double alpha[KRYLOV_MAX];
+  double beta[KRYLOV_MAX];
+  cplx coef[KRYLOV_MAX];
+  double beta0;
+  double err;
+  int k;
+  int nv;
+  int done;
+  int bad;  // set when a non-finite value appeared
+};
+
+void launch_gemm_fp64(const GemmTask* tasks, const GemmSeg* segs, const int3* tiles, int ntiles, const Bases4& B,
+                      cudaStream_t s);
+void launch_lincomb(const LincombTask* tasks, const LincombTerm* terms, const int2* chunks, int nchunks,
+                    cudaStream_t s);
+void launch_copy(const CopyTask* tasks, const int2* chunks, int nchunks, cudaStream_t s);
+
+int dots_grid(long long n);
+void launch_dots(const cplx* V, long long pitch, int nv, const cplx* w, long long n, cplx* partial, int G, cplx* out,
+                 const int* done, cudaStream_t s);
+void launch_axpy_many(const cplx* V, long long pitch, int nv, const cplx* h, cplx* w, long long n, const int* done,
+                      cudaStream_t s);
+void launch_combine(const cplx* V, long long pitch, const int* nv, const cplx* coef, const double* scal, cplx* out,
+                    long long n, cudaStream_t s);
+void launch_scale(const cplx* x, const double* nrm, cplx* y, long long n, const int* done, cudaStream_t s);
+void launch_krylov_init(KrylovState* st, const cplx* nrm2, cudaStream_t s);
+void launch_krylov_step(KrylovState* st, const cplx* h1, const cplx* nrm2, double tau, double tol, int kmax,
+                        cudaStream_t s);
+
+void launch_jacobi_svd(const SvdTask* tasks, int ntasks, int max_q, int max_sweeps, double tol, int* status,
+                       cudaStream_t s);
+void launch_truncate(const TruncSector* secs, int nsec, const int* offs, int n, double eps, long long chi_max,
+                     int* owner, int* order, int* kept, double* stats, cudaStream_t s);
+void launch_wdot(const DotTask* tasks, int ntasks, double* partial, double* out, int nslots, cudaStream_t s);
+void launch_entropy(const TruncSector* secs, int nsec, double* out, cudaStream_t s);
+
+}  // namespace tdvp
