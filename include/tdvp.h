@@ -54,7 +54,8 @@ enum {
 typedef struct {
   int precision;     /* TDVP_PREC_*; default FP64 */
   int krylov_max;    /* maximal Krylov dimension, 1..32; default 20 */
-  double krylov_tol; /* stop when beta_k |[exp(-i tau T_k)]_{k,1}| < tol; default 1e-12 */
+  double krylov_tol; /* stop when beta_k |[exp(-i tau T_k)]_{k,1}| < tol; default 1e-12;
+                        0 = always krylov_max matvecs (fixed dimension) */
   int timeout_ms;    /* reserved for bounded device waits; 0 = default */
   void* cuda_stream; /* cudaStream_t to run on, or NULL for an engine-owned stream */
   int device;        /* CUDA device ordinal, or -1 for the current device */
@@ -140,9 +141,29 @@ int tdvp_set_tensor(tdvp_ctx* ctx, int which, const double* data, long long n, i
  * result is complete.  Errors: TDVP_EINVAL, TDVP_ESTATE, TDVP_ECUDA. */
 int tdvp_heff_apply(tdvp_ctx* ctx, int bond, const double* psi_in, double* psi_out, int on_device);
 
+/* psi_out = exp(-i tau H_eff) psi_in with the engine's Krylov exponential
+ * (Sec. S2.2): Lanczos with full re-orthogonalisation applied twice, FP64
+ * vectors, exp(-i tau T_k) e_1 from a scaled Taylor series on the GPU, stopped
+ * adaptively by the estimate beta_k |[exp(-i tau T_k)]_{k,1}| < krylov_tol or at
+ * krylov_max.  Same layout, bond and pointer rules as tdvp_heff_apply;
+ * *krylov_dim (nullable) receives the number of matvecs used and *launches
+ * (nullable) the number of kernel launches.  Errors: TDVP_EINVAL, TDVP_ESTATE,
+ * TDVP_ENUMERIC (non-finite recurrence), TDVP_ECUDA. */
+int tdvp_krylov_expm(tdvp_ctx* ctx, int bond, const double* psi_in, double* psi_out, double tau, int on_device,
+                     int* krylov_dim, int* launches);
+
 /* Algorithmic flops of one tdvp_heff_apply (8 per complex multiply-add of the
  * two block-GEMM stages). */
 int tdvp_heff_flops(tdvp_ctx* ctx, long long* flops);
+
+/* Time the three stages of tdvp_heff_apply on the context's stream with CUDA
+ * events: stage 0 = environment x theta block GEMMs, 1 = MPO linear
+ * combination, 2 = second block GEMM stage.  Runs iters applications on
+ * internal buffers; ms[s] = average milliseconds per application of stage s,
+ * flops[s] = algorithmic flops per application (8 per complex multiply-add;
+ * 0 for stage 1), bytes[s] = algorithmic bytes per application (operands read
+ * once, results written once).  Any output pointer may be NULL. */
+int tdvp_heff_profile(tdvp_ctx* ctx, int iters, double* ms, long long* flops, long long* bytes);
 
 /* Destroy a context and free its device memory.  NULL is accepted. */
 int tdvp_destroy(tdvp_ctx* ctx);

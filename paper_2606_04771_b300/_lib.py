@@ -56,6 +56,8 @@ def lib():
             "tdvp_set_tensor": (C.c_int, [vp, C.c_int, vp, C.c_longlong, C.c_int]),
             "tdvp_heff_apply": (C.c_int, [vp, C.c_int, vp, vp, C.c_int]),
             "tdvp_heff_flops": (C.c_int, [vp, P(C.c_longlong)]),
+            "tdvp_krylov_expm": (C.c_int, [vp, C.c_int, vp, vp, C.c_double, C.c_int, P(C.c_int), P(C.c_int)]),
+            "tdvp_heff_profile": (C.c_int, [vp, C.c_int, vp, vp, vp]),
             "tdvp_destroy": (C.c_int, [vp]),
             "tdvp_strerror": (C.c_char_p, [C.c_int]),
             "tdvp_last_error": (C.c_char_p, []),
@@ -126,6 +128,24 @@ class _Ctx:
         assert di == do
         check(lib().tdvp_heff_apply(self.h, 0, pi, po, di))
         return out
+
+    def krylov_expm(self, psi, out=None, tau=0.025):
+        """out = exp(-i tau H_eff) psi; returns out.  Records the Krylov dimension used."""
+        if out is None:
+            out = np.empty_like(psi) if isinstance(psi, np.ndarray) else psi.new_empty(psi.shape)
+        pi, di = _ptr(psi)
+        po, do = _ptr(out)
+        assert di == do
+        k, nl = C.c_int(), C.c_int()
+        check(lib().tdvp_krylov_expm(self.h, 0, pi, po, tau, di, C.byref(k), C.byref(nl)))
+        self._kdim, self._launches = k.value, nl.value
+        return out
+
+    def last_krylov_dim(self):
+        return self._kdim
+
+    def launches_per_step(self):
+        return self._launches
 
     def heff_flops(self):
         f = C.c_longlong()

@@ -206,11 +206,77 @@ int tdvp_heff_apply(tdvp_ctx* ctx, int bond, const double* psi_in, double* psi_o
   });
 }
 
+int tdvp_krylov_expm(tdvp_ctx* ctx, int bond, const double* psi_in, double* psi_out, double tau, int on_device,
+                     int* krylov_dim, int* launches) {
+  if (!ctx || !psi_in || !psi_out) return fail(TDVP_EINVAL, "NULL argument");
+  if (bond != 0) return fail(TDVP_EINVAL, "bond must be 0");
+  return guarded([&] {
+    tdvp::Engine* e = ctx->eng;
+    tdvp::HeffPlan& H = e->bond_only() ? e->heff_plan_bond() : e->chain_heff0();
+    cudaStream_t s = e->stream();
+    const long long n = std::max<long long>(H.n, 1);
+    tdvp::DevBuf x(n * sizeof(tdvp::cplx), s);
+    TDVP_CUDA(cudaMemcpyAsync(x.p, psi_in, H.n * sizeof(tdvp::cplx),
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    int k = 0, nl = 0;
+    e->krylov(H, x.as<tdvp::cplx>(), tau, &k, &nl);
+    TDVP_CUDA(cudaMemcpyAsync(psi_out, x.p, H.n * sizeof(tdvp::cplx),
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    TDVP_CUDA(cudaStreamSynchronize(s));
+    if (krylov_dim) *krylov_dim = k;
+    if (launches) *launches = nl;
+  });
+}
+
 int tdvp_heff_flops(tdvp_ctx* ctx, long long* flops) {
   if (!ctx || !flops) return fail(TDVP_EINVAL, "NULL argument");
   return guarded([&] {
     tdvp::Engine* e = ctx->eng;
     *flops = (e->bond_only() ? e->heff_plan_bond() : e->chain_heff0()).flops();
+  });
+}
+
+int tdvp_heff_profile(tdvp_ctx* ctx, int iters, double* ms, long long* flops, long long* bytes) {
+  if (!ctx || iters < 1) return fail(TDVP_EINVAL, "bad argument");
+  return guarded([&] {
+    tdvp::Engine* e = ctx->eng;
+    tdvp::HeffPlan& H = e->bond_only() ? e->heff_plan_bond() : e->chain_heff0();
+    cudaStream_t s = e->stream();
+    const long long n = std::max<long long>(H.n, 1);
+    tdvp::DevBuf din(n * sizeof(tdvp::cplx), s), dout(n * sizeof(tdvp::cplx), s);
+    TDVP_CUDA(cudaMemsetAsync(din.p, 0, n * sizeof(tdvp::cplx), s));
+    tdvp::Bases4 B{{0, reinterpret_cast<uintptr_t>(din.p), reinterpret_cast<uintptr_t>(dout.p), 0}};
+    cudaEvent_t ev[4];
+    for (auto& x : ev) TDVP_CUDA(cudaEventCreate(&x));
+    float acc[3] = {0, 0, 0};
+    for (int it = 0; it < iters; ++it) {
+      TDVP_CUDA(cudaEventRecord(ev[0], s));
+      H.g1.launch(s, B);
+      TDVP_CUDA(cudaEventRecord(ev[1], s));
+      H.lc.launch(s);
+      TDVP_CUDA(cudaEventRecord(ev[2], s));
+      H.g3.launch(s, B);
+      TDVP_CUDA(cudaEventRecord(ev[3], s));
+      TDVP_CUDA(cudaEventSynchronize(ev[3]));
+      for (int k = 0; k < 3; ++k) {
+        float t = 0;
+        TDVP_CUDA(cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
+        acc[k] += t;
+      }
+    }
+    for (auto& x : ev) cudaEventDestroy(x);
+    if (ms)
+      for (int k = 0; k < 3; ++k) ms[k] = acc[k] / iters;
+    if (flops) {
+      flops[0] = H.g1.flops;
+      flops[1] = 0;
+      flops[2] = H.g3.flops;
+    }
+    if (bytes) {
+      bytes[0] = H.g1.bytes;
+      bytes[1] = H.lc.bytes;
+      bytes[2] = H.g3.bytes;
+    }
   });
 }
 

@@ -52,6 +52,18 @@ static DevBuf upload(const std::vector<T>& v, cudaStream_t s) {
 }
 
 void GemmPlan::finalize(cudaStream_t s) {
+  // algorithmic bytes: each distinct operand block read once, each output written once
+  std::map<std::pair<int, uintptr_t>, long long> seen;
+  bytes = 0;
+  for (const GemmTask& t : tasks) {
+    bytes += (long long)t.rows * t.cols * (long long)sizeof(cplx);
+    for (int k = 0; k < t.seg_count; ++k) {
+      const GemmSeg& g = segs[t.seg_begin + k];
+      seen[{g.a_base, reinterpret_cast<uintptr_t>(g.a)}] = (long long)t.rows * g.k;
+      seen[{g.b_base, reinterpret_cast<uintptr_t>(g.b)}] = (long long)g.k * t.cols;
+    }
+  }
+  for (auto& e : seen) bytes += e.second * (long long)sizeof(cplx);
   tiles.clear();
   for (int i = 0; i < (int)tasks.size(); ++i) {
     GemmTask& t = tasks[i];
@@ -112,7 +124,7 @@ static inline cplx* as_off(long long off) { return reinterpret_cast<cplx*>(stati
 void Engine::init_common(bool su2, double J, double U, const Opts& o) {
   opt_ = o;
   if (o.krylov_max < 1 || o.krylov_max > KRYLOV_MAX) throw Error(-1, "krylov_max must be in [1, 32]");
-  if (!(o.krylov_tol > 0)) throw Error(-1, "krylov_tol must be > 0");
+  if (!(o.krylov_tol >= 0)) throw Error(-1, "krylov_tol must be >= 0 (0: always krylov_max matvecs)");
   if (o.precision < 0 || o.precision > 2) throw Error(-1, "unknown precision");
   if (o.device >= 0) TDVP_CUDA(cudaSetDevice(o.device));
   model_.init(su2, J, U);
@@ -793,7 +805,14 @@ void Engine::form_theta(const BTensor& X, const BTensor& Y, BTensor& theta, cons
 // re-orthogonalisation applied twice, adaptive dimension)
 // ---------------------------------------------------------------------------
 
-void Engine::expm(HeffPlan& H, cplx* x, double tau) {
+void Engine::krylov(HeffPlan& H, cplx* x, double tau, int* k, int* launches) {
+  int kd = expm(H, x, tau);
+  if (k) *k = kd;
+  // 4 set-up launches, 13 per Lanczos iteration (3 H_eff + 6 dots + 2 axpy + step + scale), 1 combine
+  if (launches) *launches = 4 + 13 * kd + 1;
+}
+
+int Engine::expm(HeffPlan& H, cplx* x, double tau) {
   const long long n = H.n;
   const int kmax = opt_.krylov_max;
   if (kcap_ < n) {
@@ -840,8 +859,10 @@ void Engine::expm(HeffPlan& H, cplx* x, double tau) {
     if (hst->bad) throw Error(-4, "non-finite value in the Krylov recurrence");
     if (*hdone) break;
   }
-  stats_.max_krylov = std::max(stats_.max_krylov, k + 1);
+  const int used = std::min(k + 1, kmax);
+  stats_.max_krylov = std::max(stats_.max_krylov, used);
   launch_combine(V, n, &st->nv, st->coef, &st->beta0, x, n, stream_);
+  return used;
 }
 
 // ---------------------------------------------------------------------------

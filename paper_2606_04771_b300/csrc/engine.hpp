@@ -86,6 +86,7 @@ struct GemmPlan {
   std::vector<int3> tiles;
   DevBuf dt, ds, dti;
   long long flops = 0;  // algorithmic real flops (8 per complex MAC)
+  long long bytes = 0;  // algorithmic bytes: every operand block read once, output written once
   void finalize(cudaStream_t s);
   void launch(cudaStream_t s, const Bases4& B) const;
 };
@@ -158,6 +159,8 @@ class Engine {
   void heff_apply_bond(const cplx* in, cplx* out);  // device pointers, bond problem only
   HeffPlan& heff_plan_bond() { return *bp_heff_; }
   HeffPlan& chain_heff0();  // two-site H_eff at bond (0,1) of a chain (centre at site 0)
+  // x <- exp(-i tau H) x; *k = matvecs used, *launches = kernel launches
+  void krylov(HeffPlan& H, cplx* x, double tau, int* k, int* launches);
 
  private:
   Engine() = default;
@@ -182,7 +185,7 @@ class Engine {
   // split theta at bond (i,i+1); absorb_right: S goes to Y (left-to-right sweep)
   double split(BTensor& theta, const BondSpace& bl, const BondSpace& br, long long chi_max, double eps,
                bool absorb_right, BondSpace& bm, BTensor& X, BTensor& Y);
-  void expm(HeffPlan& H, cplx* x, double tau);
+  int expm(HeffPlan& H, cplx* x, double tau);  // returns the Krylov dimension used
 
   int L_ = 0;
   Model model_;

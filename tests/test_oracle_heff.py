@@ -232,3 +232,25 @@ def test_table_s3_transcription():
     assert max(d) == 1735
     # parity at a bond with 30 sites to its left: n even <-> j integer
     assert all((a + t) % 2 == 0 for a, t in zip(n, tj))
+
+
+def test_blockwise_u1_matches_dense():
+    """The benchmark-scale blockwise oracle equals the dense definition on a small problem."""
+    from oracle import blockwise
+
+    left = heff.Bond([(3, 1, 2), (3, -1, 2), (4, 0, 3), (4, 2, 1), (5, 1, 2)], su2=False)
+    right = heff.Bond([(5, 1, 2), (5, -1, 1), (6, 0, 2), (6, 2, 1), (4, 0, 1)], su2=False)
+    keys = heff.theta_blocks(left, right)
+    lk, rk = heff.left_env_blocks(left, left), heff.right_env_blocks(right, right)
+    th = random_reduced(keys, [(left.sectors[k[0]][2], right.sectors[k[4]][2]) for k in keys], 3)
+    Lb = random_reduced(lk, [(left.sectors[k[0]][2], left.sectors[k[2]][2]) for k in lk], 4)
+    Rb = random_reduced(rk, [(right.sectors[k[0]][2], right.sectors[k[2]][2]) for k in rk], 5)
+    W = heff.shiba_mpo_tensor(1.0, 4.0)
+    dense = heff.heff2_dense(heff.expand_left_env(Lb, left, left), W, W, heff.expand_right_env(Rb, right, right),
+                             heff.expand_theta(th, left, None, right))
+    ref = heff.reduce_theta(dense, left, right, keys)
+    got, flops = blockwise.heff2_u1_blocks(left, right, keys, [th[k] for k in keys], lk, [Lb[k] for k in lk],
+                                           rk, [Rb[k] for k in rk], W, keys)
+    assert flops > 0
+    for k in keys:
+        assert np.abs(got[k] - ref[k]).max() < 1e-12
