@@ -165,6 +165,18 @@ int tdvp_heff_flops(tdvp_ctx* ctx, long long* flops);
  * once, results written once).  Any output pointer may be NULL. */
 int tdvp_heff_profile(tdvp_ctx* ctx, int iters, double* ms, long long* flops, long long* bytes);
 
+/* Thin SVD of one complex p x q matrix, A = U diag(s) V^H, with the engine's
+ * one-sided Jacobi kernel in FP64 (the per-sector SVD of Sec. S2.2/S2.4).
+ * a: p x q row-major; s: min(p,q) values in descending order; u: p x r
+ * row-major; vh: r x q row-major, r = min(p,q).  Columns of u (rows of vh)
+ * that belong to a zero singular value are returned as zero.  on_device != 0:
+ * all four pointers are device pointers, otherwise host pointers.  stream is a
+ * cudaStream_t or NULL (the legacy default stream); the call returns after the
+ * result is complete.  Workspace is allocated and freed on that stream.
+ * Errors: TDVP_EINVAL (p<1, q<1, NULL), TDVP_ENUMERIC (no convergence),
+ * TDVP_ENOMEM, TDVP_ECUDA. */
+int tdvp_svd(int p, int q, const double* a, double* s, double* u, double* vh, int on_device, void* stream);
+
 /* Destroy a context and free its device memory.  NULL is accepted. */
 int tdvp_destroy(tdvp_ctx* ctx);
 

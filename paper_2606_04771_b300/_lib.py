@@ -58,6 +58,7 @@ def lib():
             "tdvp_heff_flops": (C.c_int, [vp, P(C.c_longlong)]),
             "tdvp_krylov_expm": (C.c_int, [vp, C.c_int, vp, vp, C.c_double, C.c_int, P(C.c_int), P(C.c_int)]),
             "tdvp_heff_profile": (C.c_int, [vp, C.c_int, vp, vp, vp]),
+            "tdvp_svd": (C.c_int, [C.c_int, C.c_int, vp, vp, vp, vp, C.c_int, vp]),
             "tdvp_destroy": (C.c_int, [vp]),
             "tdvp_strerror": (C.c_char_p, [C.c_int]),
             "tdvp_last_error": (C.c_char_p, []),
@@ -94,6 +95,28 @@ def _ptr(x):
     # torch tensor (complex128, contiguous); device pointer when on CUDA
     assert x.is_contiguous()
     return x.data_ptr(), 1 if x.is_cuda else 0
+
+
+def svd(a, stream=None):
+    """Thin SVD of a complex128 matrix through tdvp_svd: returns (u, s, vh).
+
+    a is a numpy array (host path) or a CUDA torch tensor (device path)."""
+    p, q = a.shape
+    r = min(p, q)
+    if isinstance(a, np.ndarray):
+        a = np.ascontiguousarray(a, dtype=np.complex128)
+        u = np.empty((p, r), np.complex128)
+        vh = np.empty((r, q), np.complex128)
+        s = np.empty(r)
+        check(lib().tdvp_svd(p, q, a.ctypes.data, s.ctypes.data, u.ctypes.data, vh.ctypes.data, 0, stream))
+        return u, s, vh
+    import torch
+
+    u = torch.empty((p, r), dtype=torch.complex128, device=a.device)
+    vh = torch.empty((r, q), dtype=torch.complex128, device=a.device)
+    s = torch.empty(r, dtype=torch.float64, device=a.device)
+    check(lib().tdvp_svd(p, q, a.data_ptr(), s.data_ptr(), u.data_ptr(), vh.data_ptr(), 1, stream))
+    return u, s, vh
 
 
 class _Ctx:

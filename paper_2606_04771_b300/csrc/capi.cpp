@@ -68,6 +68,10 @@ tdvp::BTensor* tensor_of(tdvp_ctx* ctx, int which) {
 }
 }  // namespace
 
+namespace tdvp {
+void set_last_error(const char* msg) { g_last = msg; }
+}  // namespace tdvp
+
 extern "C" {
 
 void tdvp_opts_default(tdvp_opts* o) {
@@ -277,6 +281,105 @@ int tdvp_heff_profile(tdvp_ctx* ctx, int iters, double* ms, long long* flops, lo
       bytes[1] = H.lc.bytes;
       bytes[2] = H.g3.bytes;
     }
+  });
+}
+
+int tdvp_svd(int p, int q, const double* a, double* s, double* u, double* vh, int on_device, void* stream) {
+  if (p < 1 || q < 1 || !a || !s || !u || !vh) return fail(TDVP_EINVAL, "bad argument");
+  return guarded([&] {
+    using tdvp::cplx;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int r = std::min(p, q), P = std::max(p, q), Q = r;
+    const size_t na = (size_t)p * q;
+    tdvp::DevBuf dA, dU, dVh, dS;
+    const cplx* A = reinterpret_cast<const cplx*>(a);
+    cplx* Uo = reinterpret_cast<cplx*>(u);
+    cplx* Vo = reinterpret_cast<cplx*>(vh);
+    double* So = s;
+    if (!on_device) {
+      dA = tdvp::DevBuf(na * sizeof(cplx), st);
+      dU = tdvp::DevBuf((size_t)p * r * sizeof(cplx), st);
+      dVh = tdvp::DevBuf((size_t)r * q * sizeof(cplx), st);
+      dS = tdvp::DevBuf((size_t)r * sizeof(double), st);
+      TDVP_CUDA(cudaMemcpyAsync(dA.p, a, na * sizeof(cplx), cudaMemcpyHostToDevice, st));
+      A = dA.as<cplx>();
+      Uo = dU.as<cplx>();
+      Vo = dVh.as<cplx>();
+      So = dS.as<double>();
+    }
+    tdvp::DevBuf dG((size_t)P * Q * sizeof(cplx), st), dV((size_t)Q * Q * sizeof(cplx), st);
+    tdvp::DevBuf dP((size_t)Q * sizeof(int), st), dT(sizeof(tdvp::SvdTask), st), dst(sizeof(int), st);
+    TDVP_CUDA(cudaMemsetAsync(dst.p, 0, sizeof(int), st));
+    tdvp::CopyPlan gather, scatter;
+    {
+      tdvp::CopyTask t{};
+      t.src = A;
+      t.rows = p;
+      t.cols = q;
+      t.src_rs = q;
+      t.src_cs = 1;
+      t.dst = dG.as<cplx>();
+      if (p >= q) {
+        t.dst_rs = 1;
+        t.dst_cs = p;
+      } else {
+        t.dst_rs = q;
+        t.dst_cs = 1;
+        t.conj = 1;
+      }
+      gather.tasks.push_back(t);
+    }
+    gather.finalize(st);
+    gather.launch(st);
+    tdvp::SvdTask task{dG.as<cplx>(), dV.as<cplx>(), So, dP.as<int>(), P, Q};
+    TDVP_CUDA(cudaMemcpyAsync(dT.p, &task, sizeof(task), cudaMemcpyHostToDevice, st));
+    tdvp::launch_jacobi_svd(dT.as<tdvp::SvdTask>(), 1, Q, 60, 1e-15, dst.as<int>(), st);
+    tdvp::CopyTask tu{}, tv{};
+    tu.dst = Uo;
+    tu.rows = p;
+    tu.cols = r;
+    tu.dst_rs = r;
+    tu.dst_cs = 1;
+    tu.col_map = dP.as<int>();
+    tv.dst = Vo;
+    tv.rows = r;
+    tv.cols = q;
+    tv.dst_rs = q;
+    tv.dst_cs = 1;
+    tv.row_map = dP.as<int>();
+    tv.conj = 1;
+    if (p >= q) {  // U = G / s, V^H = conj(V)^T
+      tu.src = dG.as<cplx>();
+      tu.src_rs = 1;
+      tu.src_cs = p;
+      tu.scale = So;
+      tu.scale_mode = 2;
+      tv.src = dV.as<cplx>();
+      tv.src_rs = q;
+      tv.src_cs = 1;
+    } else {  // A^H = W S^-1 ... : U = V_jacobi, V^H = conj(G)^T / s
+      tu.src = dV.as<cplx>();
+      tu.src_rs = 1;
+      tu.src_cs = p;
+      tv.src = dG.as<cplx>();
+      tv.src_rs = q;
+      tv.src_cs = 1;
+      tv.scale = So;
+      tv.scale_mode = 4;
+    }
+    scatter.tasks = {tu, tv};
+    scatter.finalize(st);
+    scatter.launch(st);
+    int status = 0;
+    TDVP_CUDA(cudaMemcpyAsync(&status, dst.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (!on_device) {
+      TDVP_CUDA(cudaMemcpyAsync(u, Uo, (size_t)p * r * sizeof(cplx), cudaMemcpyDeviceToHost, st));
+      TDVP_CUDA(cudaMemcpyAsync(vh, Vo, (size_t)r * q * sizeof(cplx), cudaMemcpyDeviceToHost, st));
+      TDVP_CUDA(cudaMemcpyAsync(s, So, (size_t)r * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    TDVP_CUDA(cudaStreamSynchronize(st));
+    TDVP_CUDA(cudaGetLastError());
+    if (status) throw tdvp::Error(TDVP_ENUMERIC, "Jacobi SVD did not converge");
   });
 }
 
