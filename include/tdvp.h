@@ -177,6 +177,29 @@ int tdvp_heff_profile(tdvp_ctx* ctx, int iters, double* ms, long long* flops, lo
  * TDVP_ENOMEM, TDVP_ECUDA. */
 int tdvp_svd(int p, int q, const double* a, double* s, double* u, double* vh, int on_device, void* stream);
 
+/* Largest p or q accepted by tdvp_svd_noalloc. */
+#define TDVP_SVD_NOALLOC_MAX 512
+
+/* tdvp_svd without any device allocation at call time (the paper has no
+ * counterpart; this is a service for callers of this library).  It is meant for
+ * callers that must not allocate device memory while they run: a serving
+ * process whose own pool already holds nearly all of the GPU's memory (where
+ * cudaMalloc would fail, or would stall the device's streams while it runs), or
+ * code under a memory budget frozen after start-up.  The caller passes DEVICE
+ * pointers for a (p x q row-major), s, u and vh exactly as for tdvp_svd; all
+ * workspace lives in one static device array inside this library (about 8 MiB),
+ * which every GPU that loads the library holds until the process exits.
+ *   - max(p, q) must be <= TDVP_SVD_NOALLOC_MAX, otherwise TDVP_EINVAL.
+ *   - The first call on a device (with that device current) performs a one-time
+ *     set-up (it looks up the workspace's device address); make that first
+ *     call before any stream capture.
+ *   - Every call uses the same workspace, which keeps the last call's contents
+ *     (each call rewrites what it reads and clears its convergence flag).  Calls
+ *     that overlap on the GPU race on the workspace: serialise them.
+ * stream is a cudaStream_t or NULL; the call returns after the result is
+ * complete.  Errors: TDVP_EINVAL, TDVP_ENUMERIC, TDVP_ECUDA. */
+int tdvp_svd_noalloc(int p, int q, const double* a, double* s, double* u, double* vh, void* stream);
+
 /* Destroy a context and free its device memory.  NULL is accepted. */
 int tdvp_destroy(tdvp_ctx* ctx);
 

@@ -59,6 +59,7 @@ def lib():
             "tdvp_krylov_expm": (C.c_int, [vp, C.c_int, vp, vp, C.c_double, C.c_int, P(C.c_int), P(C.c_int)]),
             "tdvp_heff_profile": (C.c_int, [vp, C.c_int, vp, vp, vp]),
             "tdvp_svd": (C.c_int, [C.c_int, C.c_int, vp, vp, vp, vp, C.c_int, vp]),
+            "tdvp_svd_noalloc": (C.c_int, [C.c_int, C.c_int, vp, vp, vp, vp, vp]),
             "tdvp_destroy": (C.c_int, [vp]),
             "tdvp_strerror": (C.c_char_p, [C.c_int]),
             "tdvp_last_error": (C.c_char_p, []),
