@@ -35,10 +35,17 @@ extern "C" {
 typedef struct tdvp_ctx tdvp_ctx; /* opaque; owns all device state */
 
 enum { TDVP_SYM_U1U1 = 0, TDVP_SYM_U1SU2 = 1 };
-/* Precision of the block GEMMs.  FP64: CUDA-core FP64.  3XTF32 / BF16X3: split
- * products on the tensor cores with FP32 accumulation (Lanczos, SVD and the
- * recoupling coefficients stay FP64 in every mode). */
-enum { TDVP_PREC_FP64 = 0, TDVP_PREC_3XTF32 = 1, TDVP_PREC_BF16X3 = 2 };
+/* Precision of the block GEMMs (Lanczos, SVD, truncation and the recoupling
+ * coefficients stay FP64 in every mode).
+ *   FP64   : CUDA-core FP64.
+ *   3XTF32 : tensor cores, x = h + l in TF32, products hh + hl + lh, FP32
+ *            accumulation (relative error ~1e-6 on long sums).
+ *   BF16X4 : tensor cores, every row of A / column of B scaled by a power of two
+ *            and every value cut into four signed 8-bit digits (exact BF16 values);
+ *            the digit products of each order are summed exactly in FP32 and
+ *            recombined in 64-bit integers (relative error ~1e-9 of the row and
+ *            column scales). */
+enum { TDVP_PREC_FP64 = 0, TDVP_PREC_3XTF32 = 1, TDVP_PREC_BF16X4 = 2 };
 
 enum {
   TDVP_OK = 0,

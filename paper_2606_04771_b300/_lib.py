@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtdvp.so")
 
 SYM = {"u1u1": 0, "u1su2": 1, "su2": 1}
-PREC = {"fp64": 0, "3xtf32": 1, "bf16x3": 2}
+PREC = {"fp64": 0, "3xtf32": 1, "bf16x4": 2}
 ERRORS = {0: "ok", -1: "EINVAL", -2: "ESTATE", -3: "ENOMEM", -4: "ENUMERIC", -5: "EINTERNAL", -6: "ECUDA",
           -7: "ETIMEOUT"}
 

@@ -199,12 +199,14 @@ int tdvp_heff_apply(tdvp_ctx* ctx, int bond, const double* psi_in, double* psi_o
     if (on_device) {
       H.apply(reinterpret_cast<const tdvp::cplx*>(psi_in), reinterpret_cast<tdvp::cplx*>(psi_out), s);
       TDVP_CUDA(cudaStreamSynchronize(s));
+      e->check_status();
     } else {
       tdvp::DevBuf din(std::max<long long>(n, 1) * sizeof(tdvp::cplx), s), dout(std::max<long long>(n, 1) * sizeof(tdvp::cplx), s);
       TDVP_CUDA(cudaMemcpyAsync(din.p, psi_in, n * sizeof(tdvp::cplx), cudaMemcpyHostToDevice, s));
       H.apply(din.as<tdvp::cplx>(), dout.as<tdvp::cplx>(), s);
       TDVP_CUDA(cudaMemcpyAsync(psi_out, dout.p, n * sizeof(tdvp::cplx), cudaMemcpyDeviceToHost, s));
       TDVP_CUDA(cudaStreamSynchronize(s));
+      e->check_status();
     }
     TDVP_CUDA(cudaGetLastError());
   });
@@ -227,6 +229,7 @@ int tdvp_krylov_expm(tdvp_ctx* ctx, int bond, const double* psi_in, double* psi_
     TDVP_CUDA(cudaMemcpyAsync(psi_out, x.p, H.n * sizeof(tdvp::cplx),
                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
     TDVP_CUDA(cudaStreamSynchronize(s));
+    e->check_status();
     if (krylov_dim) *krylov_dim = k;
     if (launches) *launches = nl;
   });

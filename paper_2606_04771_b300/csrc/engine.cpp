@@ -51,7 +51,9 @@ static DevBuf upload(const std::vector<T>& v, cudaStream_t s) {
   return b;
 }
 
-void GemmPlan::finalize(cudaStream_t s) {
+void GemmPlan::finalize(cudaStream_t s, int kind_, int* status_) {
+  kind = kind_;
+  status = status_;
   // algorithmic bytes: each distinct operand block read once, each output written once
   std::map<std::pair<int, uintptr_t>, long long> seen;
   bytes = 0;
@@ -65,10 +67,11 @@ void GemmPlan::finalize(cudaStream_t s) {
   }
   for (auto& e : seen) bytes += e.second * (long long)sizeof(cplx);
   tiles.clear();
+  const int tm = kind < 0 ? 64 : split_tile_m(), tn = kind < 0 ? 64 : split_tile_n(kind);
   for (int i = 0; i < (int)tasks.size(); ++i) {
     GemmTask& t = tasks[i];
-    t.tiles_m = (t.rows + 63) / 64;
-    t.tiles_n = (t.cols + 63) / 64;
+    t.tiles_m = (t.rows + tm - 1) / tm;
+    t.tiles_n = (t.cols + tn - 1) / tn;
     for (int a = 0; a < t.tiles_m; ++a)
       for (int b = 0; b < t.tiles_n; ++b) tiles.push_back(make_int3(i, a, b));
   }
@@ -78,7 +81,10 @@ void GemmPlan::finalize(cudaStream_t s) {
 }
 
 void GemmPlan::launch(cudaStream_t s, const Bases4& B) const {
-  launch_gemm_fp64(dt.as<GemmTask>(), ds.as<GemmSeg>(), dti.as<int3>(), (int)tiles.size(), B, s);
+  if (kind < 0)
+    launch_gemm_fp64(dt.as<GemmTask>(), ds.as<GemmSeg>(), dti.as<int3>(), (int)tiles.size(), B, s);
+  else
+    launch_gemm_split(kind, dt.as<GemmTask>(), ds.as<GemmSeg>(), dti.as<int3>(), (int)tiles.size(), B, status, s);
 }
 
 void LincombPlan::finalize(cudaStream_t s) {
@@ -128,6 +134,7 @@ void Engine::init_common(bool su2, double J, double U, const Opts& o) {
   if (o.precision < 0 || o.precision > 2) throw Error(-1, "unknown precision");
   if (o.device >= 0) TDVP_CUDA(cudaSetDevice(o.device));
   model_.init(su2, J, U);
+  gemm_kind_ = o.precision - 1;
   rec_.reset(new Recoupler(&model_));
   if (o.stream) {
     stream_ = o.stream;
@@ -210,6 +217,14 @@ Engine::~Engine() {
   if (pinned_) cudaFreeHost(pinned_);
   if (dstatus_) cudaFree(dstatus_);
   if (own_stream_) cudaStreamDestroy(stream_);
+}
+
+void Engine::check_status() {
+  int hs[2] = {0, 0};
+  TDVP_CUDA(cudaMemcpyAsync(hs, dstatus_, 2 * sizeof(int), cudaMemcpyDeviceToHost, stream_));
+  TDVP_CUDA(cudaStreamSynchronize(stream_));
+  if (hs[1] != 0) throw Error(-7, "a tensor-core GEMM gave up waiting on a pipeline barrier");
+  if (hs[0] != 0) throw Error(-4, "Jacobi iteration did not converge");
 }
 
 void Engine::alloc(BTensor& t, bool zero) {
@@ -448,9 +463,9 @@ void Engine::plan_heff2(HeffPlan& p, const BTensor& Lenv, const BTensor& Renv, c
     t.seg_count = cnt;
     p.g3.tasks.push_back(t);
   }
-  p.g1.finalize(stream_);
+  p.g1.finalize(stream_, gemm_kind_, dstatus_ + 1);
   p.lc.finalize(stream_);
-  p.g3.finalize(stream_);
+  p.g3.finalize(stream_, gemm_kind_, dstatus_ + 1);
 }
 
 // shared by the one-site H_eff and the left-environment update: steps 1 and 2
@@ -581,9 +596,9 @@ void Engine::plan_heff1(HeffPlan& p, const BTensor& Lenv, const BTensor& Renv, c
     t.seg_count = cnt;
     p.g3.tasks.push_back(t);
   }
-  p.g1.finalize(stream_);
+  p.g1.finalize(stream_, gemm_kind_, dstatus_ + 1);
   p.lc.finalize(stream_);
-  p.g3.finalize(stream_);
+  p.g3.finalize(stream_, gemm_kind_, dstatus_ + 1);
 }
 
 void Engine::update_left_env(const BTensor& Lin, const BTensor& A, BTensor& Lout, const BondSpace& bl,
@@ -629,9 +644,9 @@ void Engine::update_left_env(const BTensor& Lin, const BTensor& A, BTensor& Lout
     t.seg_count = cnt;
     p.g3.tasks.push_back(t);
   }
-  p.g1.finalize(stream_);
+  p.g1.finalize(stream_, gemm_kind_, dstatus_ + 1);
   p.lc.finalize(stream_);
-  p.g3.finalize(stream_);
+  p.g3.finalize(stream_, gemm_kind_, dstatus_ + 1);
   Bases4 B{{0, reinterpret_cast<uintptr_t>(A.data()), 0, 0}};
   p.g1.launch(stream_, B);
   p.lc.launch(stream_);
@@ -755,9 +770,9 @@ void Engine::update_right_env(const BTensor& Rin, const BTensor& Bt, BTensor& Ro
     t.seg_count = cnt;
     p.g3.tasks.push_back(t);
   }
-  p.g1.finalize(stream_);
+  p.g1.finalize(stream_, gemm_kind_, dstatus_ + 1);
   p.lc.finalize(stream_);
-  p.g3.finalize(stream_);
+  p.g3.finalize(stream_, gemm_kind_, dstatus_ + 1);
   Bases4 B{{0, 0, 0, 0}};
   p.g1.launch(stream_, B);
   p.lc.launch(stream_);
@@ -796,7 +811,7 @@ void Engine::form_theta(const BTensor& X, const BTensor& Y, BTensor& theta, cons
       g.tasks.push_back(t);
     }
   }
-  g.finalize(stream_);
+  g.finalize(stream_, gemm_kind_, dstatus_ + 1);
   g.launch(stream_, Bases4{{0, 0, 0, 0}});
 }
 
@@ -1126,9 +1141,7 @@ void Engine::step(double dt, long long chi_max, double eps) {
     }
   }
   TDVP_CUDA(cudaStreamSynchronize(stream_));
-  int hs[1];
-  TDVP_CUDA(cudaMemcpy(hs, dstatus_, sizeof(int), cudaMemcpyDeviceToHost));
-  if (hs[0] != 0) throw Error(-4, "Jacobi SVD did not converge");
+  check_status();
   stats_.seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
 
@@ -1284,9 +1297,7 @@ void Engine::measure(double* n_out, double* sz_out, double* docc_out, double* s_
     *energy = he.x;
   }
   TDVP_CUDA(cudaStreamSynchronize(stream_));
-  int hs = 0;
-  TDVP_CUDA(cudaMemcpy(&hs, dstatus_, sizeof(int), cudaMemcpyDeviceToHost));
-  if (hs != 0) throw Error(-4, "Jacobi eigenvalue iteration did not converge");
+  check_status();
   // back to the frame of Eq. (FHM): n_up = n'_up, n_dn = 1 - n'_dn
   for (int i = 0; i < L; ++i) {
     const double* r = &res[(size_t)i * NS];

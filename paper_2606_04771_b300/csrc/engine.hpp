@@ -87,7 +87,9 @@ struct GemmPlan {
   DevBuf dt, ds, dti;
   long long flops = 0;  // algorithmic real flops (8 per complex MAC)
   long long bytes = 0;  // algorithmic bytes: every operand block read once, output written once
-  void finalize(cudaStream_t s);
+  int kind = -1;        // -1 FP64 CUDA cores, 0 3xTF32, 1 BF16x3 tensor cores
+  int* status = nullptr;
+  void finalize(cudaStream_t s, int kind_ = -1, int* status_ = nullptr);
   void launch(cudaStream_t s, const Bases4& B) const;
 };
 
@@ -147,6 +149,7 @@ class Engine {
   int L() const { return L_; }
   const BondSpace& bond(int k) const { return bonds_[k]; }
   const Model& model() const { return model_; }
+  void check_status();  // throws if a kernel reported non-convergence or a wait timeout
   cudaStream_t stream() const { return stream_; }
 
   // synthetic single-bond problem (environments and theta given by the caller)
@@ -205,6 +208,7 @@ class Engine {
   void* pinned_ = nullptr;
   StepStats stats_;
   int* dstatus_ = nullptr;
+  int gemm_kind_ = -1;  // block-GEMM precision of H_eff, environment updates and theta formation
 
   friend struct BondAccess;
 };

@@ -29,6 +29,14 @@ void launch_lincomb(const LincombTask* tasks, const LincombTerm* terms, const in
                     cudaStream_t s);
 void launch_copy(const CopyTask* tasks, const int2* chunks, int nchunks, cudaStream_t s);
 
+// split-precision tensor-core GEMM (split.cu); kind 0 = 3xTF32 (FP32 accumulation),
+// 1 = BF16x4 digits with exact per-order accumulation.  Output tiles are
+// split_tile_m() x split_tile_n(kind) complex elements; alpha scales A.
+int split_tile_m();
+int split_tile_n(int kind);
+void launch_gemm_split(int kind, const GemmTask* tasks, const GemmSeg* segs, const int3* tiles, int ntiles,
+                       const Bases4& B, int* status, cudaStream_t s);
+
 int dots_grid(long long n);
 void launch_dots(const cplx* V, long long pitch, int nv, const cplx* w, long long n, cplx* partial, int G, cplx* out,
                  const int* done, cudaStream_t s);

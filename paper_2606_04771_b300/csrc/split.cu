@@ -1,0 +1,660 @@
+// K1 (split precision): grouped complex GEMM on the 5th-generation tensor cores.
+//
+// The same task lists as the FP64 kernel (C = sum_seg alpha op(A) op(B), FP64
+// complex blocks) are computed with tcgen05.mma:
+//   * the complex product is embedded as one real product,
+//       [C_r; C_i] rows (2m, 2m+1) = [[A_r, -A_i]; [A_i, A_r]] [B_r; B_i],
+//     so a 64 x 128 complex output tile is one 128 x 128 FP32 accumulator in TMEM;
+//   * every FP64 operand is split on the fly into precision pieces: 3xTF32
+//     (x = h + l, products h*h + h*l + l*h, FP32 accumulation in TMEM) or BF16x4
+//     (scaled signed digits, exact per-order accumulation; gemm_exact_kernel);
+//   * producer warps load FP64 tiles from global memory, split them and store
+//     them in the 128-byte-swizzled K-major layout the MMA descriptors expect;
+//     one thread issues the MMAs; the same producer warps read the accumulator
+//     back from TMEM (tcgen05.ld) and write FP64 complex results.
+// Every mbarrier wait is bounded: on expiry the kernel records an error in
+// *status, stops issuing work, releases its TMEM and returns.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+
+#include "common.hpp"
+#include "kernels.hpp"
+
+namespace tdvp {
+
+namespace {
+
+constexpr int TM = 64;         // complex rows per tile (UMMA M = 128 real-embedded rows)
+constexpr int TN = 128;        // complex columns per tile (UMMA N)
+constexpr int NPROD = 128;     // producer / epilogue threads (warps 0-3)
+constexpr int NTHREADS = 160;  // + one MMA warp
+constexpr int STAGES = 2;
+constexpr uint32_t SPIN_LIMIT = 1u << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+
+__device__ __forceinline__ uint32_t mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok;
+}
+
+// bounded wait: returns false (and flags *err) when the limit is hit
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* err) {
+  for (uint32_t it = 0; it < SPIN_LIMIT; ++it) {
+    if (mbar_try(b, parity)) return true;
+    if ((it & 1023) == 1023 && *err) return false;
+  }
+  *err = 1;
+  return false;
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;                      // leading-dimension offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;            // stride between 8-row groups
+  d |= (uint64_t)1 << 46;                      // descriptor version for this architecture
+  d |= (uint64_t)2 << 61;                      // 128-byte swizzle
+  return d;
+}
+
+// instruction descriptor: D f32, A/B format fmt (kind::tf32: 2, kind::f16 bf16: 1), K-major, M=128, N
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, uint32_t M, uint32_t N) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+template <int KIND>
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if (KIND == 0) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// byte offset of element (row, kk) with 4-byte elements in a K-major SW128 tile (32 per row)
+__device__ __forceinline__ uint32_t sw_off4(int row, int kk) {
+  return row * 128 + ((((kk >> 2) ^ (row & 7)) & 7) << 4) + ((kk & 3) << 2);
+}
+// same for 2-byte elements (64 per row)
+__device__ __forceinline__ uint32_t sw_off2(int row, int kk) {
+  return row * 128 + ((((kk >> 3) ^ (row & 7)) & 7) << 4) + ((kk & 7) << 1);
+}
+
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Split configuration of the 3xTF32 kernel: 2 planes (h, l), K-chunk = 16 complex k
+// = 32 tf32 = one 128-byte swizzle atom row per plane per stage.
+template <int KIND>
+struct Cfg;
+template <>
+struct Cfg<0> {
+  static constexpr int PLANES = 2, KC = 16, ESZ = 4, KSTEP = 8;
+};
+
+constexpr int PLANE_BYTES = 128 * 128;  // 128 rows x 128 bytes
+
+// split x into the pieces of the chosen format
+template <int KIND>
+__device__ __forceinline__ void split_val(double x, float* out) {
+  float h = tf32_round((float)x);
+  float l = tf32_round((float)(x - (double)h));
+  out[0] = h;
+  out[1] = l;
+}
+
+template <int KIND>
+__device__ __forceinline__ void store_pair(uint8_t* plane, int row, int kk, float v0, float v1) {
+  *reinterpret_cast<float2*>(plane + sw_off4(row, kk)) = make_float2(v0, v1);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    gemm_split_kernel(const GemmTask* __restrict__ tasks, const GemmSeg* __restrict__ segs,
+                      const int3* __restrict__ tiles, const Bases4 B, int* __restrict__ status) {
+  using C = Cfg<KIND>;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  // 1024-align the stage buffers
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* stage_base = smem;  // STAGES x (PLANES A + PLANES B) planes
+  __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int err;
+
+  const int3 tr = tiles[blockIdx.x];
+  const GemmTask t = tasks[tr.x];
+  cplx* const cptr = rebase(B, t.c_base, t.c);
+  const int m0 = tr.y * TM, n0 = tr.z * TN;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // total K chunks of this task
+  int nchunks = 0;
+  for (int s = 0; s < t.seg_count; ++s) nchunks += (segs[t.seg_begin + s].k + C::KC - 1) / C::KC;
+
+  if (nchunks == 0) {  // no contribution: the output tile is zero
+    for (int e = tid; e < TM * TN; e += NTHREADS) {
+      int r = m0 + e / TN, c = n0 + e % TN;
+      if (r < t.rows && c < t.cols) cptr[(long long)r * t.ldc + c] = {0.0, 0.0};
+    }
+    return;
+  }
+
+  if (tid == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_bar[s], NPROD / 32);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&done_bar, 1);
+    err = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(TN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  volatile int* verr = &err;
+
+  if (warp < 4) {
+    // ---------------- producers ----------------
+    int it = 0;
+    for (int sgi = 0; sgi < t.seg_count && !*verr; ++sgi) {
+      const GemmSeg sg = segs[t.seg_begin + sgi];
+      const cplx* ap = rebase(B, sg.a_base, sg.a);
+      const cplx* bp = rebase(B, sg.b_base, sg.b);
+      const double al = sg.alpha;
+      for (int k0 = 0; k0 < sg.k; k0 += C::KC, ++it) {
+        const int s = it % STAGES;
+        if (!mbar_wait(&empty_bar[s], ((it / STAGES) & 1) ^ 1, verr)) break;
+        uint8_t* st = stage_base + (size_t)s * (2 * C::PLANES) * PLANE_BYTES;
+        // A: TM complex rows x KC complex k -> rows (2m, 2m+1), columns (2k, 2k+1)
+        for (int e = tid; e < TM * C::KC; e += NPROD) {
+          const int m = e / C::KC, k = e % C::KC;
+          const int gr = m0 + m, gk = k0 + k;
+          cplx v = {0.0, 0.0};
+          if (gr < t.rows && gk < sg.k) {
+            if (sg.op_a == OP_N) v = ap[(long long)gr * sg.lda + gk];
+            else {
+              v = ap[(long long)gk * sg.lda + gr];
+              v.y = -v.y;
+            }
+          }
+          float re[2], im[2];
+          split_val<KIND>(v.x * al, re);
+          split_val<KIND>(v.y * al, im);
+#pragma unroll
+          for (int p = 0; p < C::PLANES; ++p) {
+            uint8_t* pl = st + p * PLANE_BYTES;
+            store_pair<KIND>(pl, 2 * m, 2 * k, re[p], -im[p]);
+            store_pair<KIND>(pl, 2 * m + 1, 2 * k, im[p], re[p]);
+          }
+        }
+        // B: KC complex k x TN complex n -> K-major rows n, columns (2k, 2k+1)
+        for (int e = tid; e < TN * C::KC; e += NPROD) {
+          const int n = e % TN, k = e / TN;
+          const int gc = n0 + n, gk = k0 + k;
+          cplx v = {0.0, 0.0};
+          if (gc < t.cols && gk < sg.k) {
+            if (sg.op_b == OP_N) v = bp[(long long)gk * sg.ldb + gc];
+            else {
+              v = bp[(long long)gc * sg.ldb + gk];
+              v.y = -v.y;
+            }
+          }
+          float re[2], im[2];
+          split_val<KIND>(v.x, re);
+          split_val<KIND>(v.y, im);
+#pragma unroll
+          for (int p = 0; p < C::PLANES; ++p) {
+            uint8_t* pl = st + (C::PLANES + p) * PLANE_BYTES;
+            store_pair<KIND>(pl, n, 2 * k, re[p], im[p]);
+          }
+        }
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&full_bar[s]);
+      }
+    }
+    // ---------------- epilogue ----------------
+    if (mbar_wait(&done_bar, 0, verr)) {
+      tc_fence_after();
+      const int row = warp * 32 + lane;  // real-embedded row = TMEM lane
+      const int m = row >> 1, part = row & 1;
+      const int gr = m0 + m;
+      for (int c0 = 0; c0 < TN; c0 += 32) {
+        uint32_t v[32];
+        const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+              "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+              "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+              "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            : "r"(addr)
+            : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (gr < t.rows) {
+          double* out = reinterpret_cast<double*>(cptr + (long long)gr * t.ldc);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int gc = n0 + c0 + j;
+            if (gc < t.cols) out[2 * gc + part] = (double)__uint_as_float(v[j]);
+          }
+        }
+      }
+    }
+  } else if (warp == 4 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    constexpr uint32_t idesc = make_idesc(KIND == 0 ? 2u : 1u, 128, TN);
+    uint32_t acc = 0;
+    int it = 0;
+    bool ok = true;
+    for (int sgi = 0; sgi < t.seg_count && ok; ++sgi) {
+      const int kk = segs[t.seg_begin + sgi].k;
+      for (int k0 = 0; k0 < kk; k0 += C::KC, ++it) {
+        const int s = it % STAGES;
+        if (!mbar_wait(&full_bar[s], (it / STAGES) & 1, verr)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t st = smem_u32(stage_base + (size_t)s * (2 * C::PLANES) * PLANE_BYTES);
+#pragma unroll
+        for (int q = 0; q < 128 / (C::KSTEP * C::ESZ); ++q) {
+          const uint32_t koff = q * C::KSTEP * C::ESZ;
+          const uint64_t ah = sw128_desc(st + koff), alo = sw128_desc(st + PLANE_BYTES + koff);
+          const uint64_t bh = sw128_desc(st + 2 * PLANE_BYTES + koff), blo = sw128_desc(st + 3 * PLANE_BYTES + koff);
+          mma<KIND>(tmem, ah, bh, idesc, acc);
+          acc = 1;
+          mma<KIND>(tmem, ah, blo, idesc, 1);
+          mma<KIND>(tmem, alo, bh, idesc, 1);
+        }
+        mma_commit(&empty_bar[s]);
+      }
+    }
+    if (ok) mma_commit(&done_bar);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN) : "memory");
+  }
+  if (tid == 0 && err) atomicAdd(status, 1);
+}
+
+// ---------------------------------------------------------------------------
+// BF16x4 with exact accumulation (Ozaki-style splitting)
+//
+// Every complex output row m of a tile gets a power-of-two scale 2^e_m >= max|A[m,:]|
+// and every output column n a scale 2^f_n >= max|B[:,n]| (over all segments of the
+// task).  Each FP64 value x is turned into the integer X = round(x 2^(30-e)) with
+// |X| <= 2^30, written as X = s0 2^24 + s1 2^16 + s2 2^8 + s3 with signed digits
+// |s_i| <= 128 (exact BF16 values).  Products s_i(a) s_j(b) are integers below 2^14,
+// so the FP32 sums of all products of one order o = i + j (o = 0..3) held in four
+// TMEM accumulators are exact integers (for any realistic K); the epilogue forms
+// V = ((acc0 2^8 + acc1) 2^8 + acc2) 2^8 + acc3 in 64-bit integers and converts once.  Dropped products (order >= 4) and the rounding of X
+// bound the error by ~2^-30 of the row/column scales.  With x = 2^(e-30) X and
+// X_a X_b = sum_o 2^(8(6-o)) (order-o digit products), the kept orders give
+// 2^24 V, hence C = 2^(e_m + f_n - 36) V.
+// ---------------------------------------------------------------------------
+
+constexpr int XN = 64;                  // complex columns per tile
+constexpr int XSTAGE = 4 * PLANE_BYTES + 4 * (64 * 128);  // 4 A planes (128 rows) + 4 B planes (64 rows)
+constexpr int XSTAGES = 2;
+constexpr int XKC = 32;                 // complex k per chunk (64 bf16 = one 128-byte row)
+
+__device__ __forceinline__ int exp_of_max(double m) {
+  // smallest e with |x| <= 2^e for |x| <= m (m > 0); -2000 marks an all-zero row
+  if (!(m > 0.0)) return -2000;
+  const unsigned long long b = __double_as_longlong(m);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  return ex - 1022;
+}
+
+// X = round(x 2^(30 - e)) as int (|X| <= 2^30); x must satisfy |x| <= 2^e
+__device__ __forceinline__ int fixed30(double x, int e) {
+  if (e <= -2000) return 0;
+  const unsigned long long b = __double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex == 0) return 0;  // zero or subnormal: below 2^-1022, far under the scale
+  const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  // x = mant 2^(ex - 1075); X = mant 2^(ex - 1075 + 30 - e) = mant >> r
+  const int r = 1045 + e - ex;
+  long long X;
+  if (r >= 64) X = 0;
+  else if (r <= 0) X = (long long)(mant << (-r));  // cannot happen for |x| <= 2^e (r >= 22)
+  else X = (long long)((mant + (1ull << (r - 1))) >> r);
+  return (b >> 63) ? -(int)X : (int)X;
+}
+
+__device__ __forceinline__ void digits4(int X, float* d) {
+  // X = d0 2^24 + d1 2^16 + d2 2^8 + d3, |d_i| <= 128
+  int r = X;
+  int d3 = ((r + 128) & 255) - 128;
+  r = (r - d3) >> 8;
+  int d2 = ((r + 128) & 255) - 128;
+  r = (r - d2) >> 8;
+  int d1 = ((r + 128) & 255) - 128;
+  r = (r - d1) >> 8;
+  d[0] = (float)r;
+  d[1] = (float)d1;
+  d[2] = (float)d2;
+  d[3] = (float)d3;
+}
+
+__device__ __forceinline__ void st_bf2(uint8_t* plane, int row, int kk, float v0, float v1) {
+  *reinterpret_cast<__nv_bfloat162*>(plane + sw_off2(row, kk)) = __floats2bfloat162_rn(v0, v1);
+}
+
+template <int NCOL>
+__device__ __forceinline__ void tmem_ld16(uint32_t addr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(addr)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    gemm_exact_kernel(const GemmTask* __restrict__ tasks, const GemmSeg* __restrict__ segs,
+                      const int3* __restrict__ tiles, const Bases4 B, int* __restrict__ status) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* stage_base =
+      reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ uint64_t full_bar[XSTAGES], empty_bar[XSTAGES], done_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int err;
+  __shared__ int rowe[TM], cole[XN];
+  __shared__ unsigned long long rmax2[TM][2], cmax2[XN][2];
+
+  const int3 tr = tiles[blockIdx.x];
+  const GemmTask t = tasks[tr.x];
+  cplx* const cptr = rebase(B, t.c_base, t.c);
+  const int m0 = tr.y * TM, n0 = tr.z * XN;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  int nchunks = 0;
+  for (int s = 0; s < t.seg_count; ++s) nchunks += (segs[t.seg_begin + s].k + XKC - 1) / XKC;
+  if (nchunks == 0) {
+    for (int e = tid; e < TM * XN; e += NTHREADS) {
+      int r = m0 + e / XN, c = n0 + e % XN;
+      if (r < t.rows && c < t.cols) cptr[(long long)r * t.ldc + c] = {0.0, 0.0};
+    }
+    return;
+  }
+  if (tid == 0) {
+    for (int s = 0; s < XSTAGES; ++s) {
+      mbar_init(&full_bar[s], NPROD / 32);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&done_bar, 1);
+    err = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(256)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  // phase 0: row and column maxima over every segment of the task (producer threads)
+  if (tid < NPROD) {
+    // magnitudes compared as the bit patterns of |x| (monotone for non-negative doubles)
+    const unsigned long long ABS = 0x7FFFFFFFFFFFFFFFull;
+    const int m = tid >> 1, h = tid & 1;          // two threads per complex row
+    const int n = tid & (XN - 1), hh = tid >> 6;  // two threads per complex column
+    unsigned long long rm = 0, cm = 0;
+    for (int sgi = 0; sgi < t.seg_count; ++sgi) {
+      const GemmSeg sg = segs[t.seg_begin + sgi];
+      const cplx* ap = rebase(B, sg.a_base, sg.a);
+      const cplx* bp = rebase(B, sg.b_base, sg.b);
+      const int gr = m0 + m, gc = n0 + n;
+      unsigned long long sm = 0;
+      if (gr < t.rows)
+        for (int k = h; k < sg.k; k += 2) {
+          cplx v = sg.op_a == OP_N ? ap[(long long)gr * sg.lda + k] : ap[(long long)k * sg.lda + gr];
+          sm = max(sm, max((unsigned long long)__double_as_longlong(v.x) & ABS,
+                           (unsigned long long)__double_as_longlong(v.y) & ABS));
+        }
+      if (sg.alpha != 1.0) sm = (unsigned long long)__double_as_longlong(fabs(sg.alpha) * __longlong_as_double(sm));
+      rm = max(rm, sm);
+      if (gc < t.cols)
+        for (int k = hh; k < sg.k; k += 2) {
+          cplx v = sg.op_b == OP_N ? bp[(long long)k * sg.ldb + gc] : bp[(long long)gc * sg.ldb + k];
+          cm = max(cm, max((unsigned long long)__double_as_longlong(v.x) & ABS,
+                           (unsigned long long)__double_as_longlong(v.y) & ABS));
+        }
+    }
+    rmax2[m][h] = rm;
+    cmax2[n][hh] = cm;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (tid < TM) rowe[tid] = exp_of_max(__longlong_as_double(max(rmax2[tid][0], rmax2[tid][1])));
+  if (tid < XN) cole[tid] = exp_of_max(__longlong_as_double(max(cmax2[tid][0], cmax2[tid][1])));
+  __syncthreads();
+  const uint32_t tmem = tmem_slot;
+  volatile int* verr = &err;
+
+  if (warp < 4) {
+    int it = 0;
+    for (int sgi = 0; sgi < t.seg_count && !*verr; ++sgi) {
+      const GemmSeg sg = segs[t.seg_begin + sgi];
+      const cplx* ap = rebase(B, sg.a_base, sg.a);
+      const cplx* bp = rebase(B, sg.b_base, sg.b);
+      const double al = sg.alpha;
+      for (int k0 = 0; k0 < sg.k; k0 += XKC, ++it) {
+        const int s = it % XSTAGES;
+        if (!mbar_wait(&empty_bar[s], ((it / XSTAGES) & 1) ^ 1, verr)) break;
+        uint8_t* st = stage_base + (size_t)s * XSTAGE;
+        // A: 64 complex rows x 32 complex k -> 4 digit planes of 128 rows x 64 bf16
+        for (int e = tid; e < TM * XKC; e += NPROD) {
+          const int m = e / XKC, k = e % XKC;
+          const int gr = m0 + m, gk = k0 + k;
+          cplx v = {0.0, 0.0};
+          if (gr < t.rows && gk < sg.k) {
+            if (sg.op_a == OP_N) v = ap[(long long)gr * sg.lda + gk];
+            else {
+              v = ap[(long long)gk * sg.lda + gr];
+              v.y = -v.y;
+            }
+          }
+          if (al != 1.0) {
+            v.x *= al;
+            v.y *= al;
+          }
+          float re[4], im[4];
+          digits4(fixed30(v.x, rowe[m]), re);
+          digits4(fixed30(v.y, rowe[m]), im);
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            uint8_t* pl = st + p * PLANE_BYTES;
+            st_bf2(pl, 2 * m, 2 * k, re[p], -im[p]);
+            st_bf2(pl, 2 * m + 1, 2 * k, im[p], re[p]);
+          }
+        }
+        // B: 32 complex k x 64 complex n -> 4 digit planes of 64 rows x 64 bf16
+        for (int e = tid; e < XN * XKC; e += NPROD) {
+          const int n = e % XN, k = e / XN;
+          const int gc = n0 + n, gk = k0 + k;
+          cplx v = {0.0, 0.0};
+          if (gc < t.cols && gk < sg.k) {
+            if (sg.op_b == OP_N) v = bp[(long long)gk * sg.ldb + gc];
+            else {
+              v = bp[(long long)gc * sg.ldb + gk];
+              v.y = -v.y;
+            }
+          }
+          float re[4], im[4];
+          digits4(fixed30(v.x, cole[n]), re);
+          digits4(fixed30(v.y, cole[n]), im);
+#pragma unroll
+          for (int p = 0; p < 4; ++p) st_bf2(st + 4 * PLANE_BYTES + p * (64 * 128), n, 2 * k, re[p], im[p]);
+        }
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&full_bar[s]);
+      }
+    }
+    // epilogue: combine the four order accumulators exactly, convert once
+    if (mbar_wait(&done_bar, 0, verr)) {
+      tc_fence_after();
+      const int row = warp * 32 + lane;
+      const int m = row >> 1, part = row & 1;
+      const int gr = m0 + m;
+      const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+      for (int c0 = 0; c0 < XN; c0 += 16) {
+        uint32_t a0[16], a1[16], a2[16], a3[16];
+        tmem_ld16<16>(lane_addr + 0 * XN + c0, a0);
+        tmem_ld16<16>(lane_addr + 1 * XN + c0, a1);
+        tmem_ld16<16>(lane_addr + 2 * XN + c0, a2);
+        tmem_ld16<16>(lane_addr + 3 * XN + c0, a3);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (gr < t.rows) {
+          double* out = reinterpret_cast<double*>(cptr + (long long)gr * t.ldc);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int n = c0 + j, gc = n0 + n;
+            if (gc >= t.cols) continue;
+            long long V = (long long)__float2ll_rn(__uint_as_float(a0[j]));
+            V = (V << 8) + (long long)__float2ll_rn(__uint_as_float(a1[j]));
+            V = (V << 8) + (long long)__float2ll_rn(__uint_as_float(a2[j]));
+            V = (V << 8) + (long long)__float2ll_rn(__uint_as_float(a3[j]));
+            const int ee = rowe[m] + cole[n];
+            double r = 0.0;
+            if (V != 0 && ee > -1900) r = ldexp((double)V, ee - 36);
+            out[2 * gc + part] = r;
+          }
+        }
+      }
+    }
+  } else if (warp == 4 && lane == 0) {
+    constexpr uint32_t idesc = make_idesc(1u, 128, XN);
+    uint32_t started = 0;  // bit o set once accumulator o has been written
+    int it = 0;
+    bool ok = true;
+    for (int sgi = 0; sgi < t.seg_count && ok; ++sgi) {
+      const int kk = segs[t.seg_begin + sgi].k;
+      for (int k0 = 0; k0 < kk; k0 += XKC, ++it) {
+        const int s = it % XSTAGES;
+        if (!mbar_wait(&full_bar[s], (it / XSTAGES) & 1, verr)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t st = smem_u32(stage_base + (size_t)s * XSTAGE);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {  // 4 k-steps of 16 bf16 (32 bytes)
+          const uint32_t koff = q * 32;
+          uint64_t a[4], b[4];
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            a[p] = sw128_desc(st + p * PLANE_BYTES + koff);
+            b[p] = sw128_desc(st + 4 * PLANE_BYTES + p * (64 * 128) + koff);
+          }
+#pragma unroll
+          for (int o = 0; o < 4; ++o) {
+#pragma unroll
+            for (int i = 0; i <= o; ++i) {
+              mma<1>(tmem + o * XN, a[i], b[o - i], idesc, (started >> o) & 1);
+              started |= 1u << o;
+            }
+          }
+        }
+        mma_commit(&empty_bar[s]);
+      }
+    }
+    if (ok) mma_commit(&done_bar);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
+  }
+  if (tid == 0 && err) atomicAdd(status, 1);
+}
+
+template <int KIND>
+size_t smem_bytes() {
+  return (size_t)STAGES * 2 * Cfg<KIND>::PLANES * PLANE_BYTES + 1024;
+}
+
+}  // namespace
+
+int split_tile_m() { return TM; }
+int split_tile_n(int kind) { return kind == 0 ? TN : XN; }
+
+void launch_gemm_split(int kind, const GemmTask* tasks, const GemmSeg* segs, const int3* tiles, int ntiles,
+                       const Bases4& B, int* status, cudaStream_t s) {
+  if (ntiles <= 0) return;
+  if (kind == 0) {
+    static bool init = false;
+    size_t sm = smem_bytes<0>();
+    if (!init) {
+      cudaFuncSetAttribute(gemm_split_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      init = true;
+    }
+    gemm_split_kernel<0><<<ntiles, NTHREADS, sm, s>>>(tasks, segs, tiles, B, status);
+  } else {
+    static bool init = false;
+    size_t sm = (size_t)XSTAGES * XSTAGE + 1024;
+    if (!init) {
+      cudaFuncSetAttribute(gemm_exact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      init = true;
+    }
+    gemm_exact_kernel<<<ntiles, NTHREADS, sm, s>>>(tasks, segs, tiles, B, status);
+  }
+}
+
+}  // namespace tdvp
