@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
 constexpr int XN = 64;                  // complex columns per tile
 constexpr int XSTAGE = 4 * PLANE_BYTES + 4 * (64 * 128);  // 4 A planes (128 rows) + 4 B planes (64 rows)
-constexpr int XSTAGES = 2;
+constexpr int XSTAGES = 1;  // ~100 KB of shared memory: two CTAs share an SM
 constexpr int XKC = 32;                 // complex k per chunk (64 bf16 = one 128-byte row)
 
 __device__ __forceinline__ int exp_of_max(double m) {
@@ -404,7 +404,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t addr, uint32_t* v) {
       : "memory");
 }
 
-__global__ void __launch_bounds__(NTHREADS, 1)
+__global__ void __launch_bounds__(NTHREADS, 2)
     gemm_exact_kernel(const GemmTask* __restrict__ tasks, const GemmSeg* __restrict__ segs,
                       const int3* __restrict__ tiles, const Bases4 B, int* __restrict__ status) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -459,20 +459,44 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const cplx* bp = rebase(B, sg.b_base, sg.b);
       const int gr = m0 + m, gc = n0 + n;
       unsigned long long sm = 0;
-      if (gr < t.rows)
-        for (int k = h; k < sg.k; k += 2) {
-          cplx v = sg.op_a == OP_N ? ap[(long long)gr * sg.lda + k] : ap[(long long)k * sg.lda + gr];
-          sm = max(sm, max((unsigned long long)__double_as_longlong(v.x) & ABS,
-                           (unsigned long long)__double_as_longlong(v.y) & ABS));
+      if (gr < t.rows) {
+        if (sg.op_a == OP_N) {
+          const cplx* row = ap + (long long)gr * sg.lda;
+#pragma unroll 4
+          for (int k = h; k < sg.k; k += 2) {
+            const cplx v = row[k];
+            sm = max(sm, max((unsigned long long)__double_as_longlong(v.x) & ABS,
+                             (unsigned long long)__double_as_longlong(v.y) & ABS));
+          }
+        } else {
+#pragma unroll 4
+          for (int k = h; k < sg.k; k += 2) {
+            const cplx v = ap[(long long)k * sg.lda + gr];
+            sm = max(sm, max((unsigned long long)__double_as_longlong(v.x) & ABS,
+                             (unsigned long long)__double_as_longlong(v.y) & ABS));
+          }
         }
+      }
       if (sg.alpha != 1.0) sm = (unsigned long long)__double_as_longlong(fabs(sg.alpha) * __longlong_as_double(sm));
       rm = max(rm, sm);
-      if (gc < t.cols)
-        for (int k = hh; k < sg.k; k += 2) {
-          cplx v = sg.op_b == OP_N ? bp[(long long)k * sg.ldb + gc] : bp[(long long)gc * sg.ldb + k];
-          cm = max(cm, max((unsigned long long)__double_as_longlong(v.x) & ABS,
-                           (unsigned long long)__double_as_longlong(v.y) & ABS));
+      if (gc < t.cols) {
+        if (sg.op_b == OP_N) {
+#pragma unroll 4
+          for (int k = hh; k < sg.k; k += 2) {
+            const cplx v = bp[(long long)k * sg.ldb + gc];
+            cm = max(cm, max((unsigned long long)__double_as_longlong(v.x) & ABS,
+                             (unsigned long long)__double_as_longlong(v.y) & ABS));
+          }
+        } else {
+          const cplx* col = bp + (long long)gc * sg.ldb;
+#pragma unroll 4
+          for (int k = hh; k < sg.k; k += 2) {
+            const cplx v = col[k];
+            cm = max(cm, max((unsigned long long)__double_as_longlong(v.x) & ABS,
+                             (unsigned long long)__double_as_longlong(v.y) & ABS));
+          }
         }
+      }
     }
     rmax2[m][h] = rm;
     cmax2[n][hh] = cm;
@@ -570,9 +594,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             V = (V << 8) + (long long)__float2ll_rn(__uint_as_float(a1[j]));
             V = (V << 8) + (long long)__float2ll_rn(__uint_as_float(a2[j]));
             V = (V << 8) + (long long)__float2ll_rn(__uint_as_float(a3[j]));
-            const int ee = rowe[m] + cole[n];
+            const int ee = rowe[m] + cole[n] - 36;
             double r = 0.0;
-            if (V != 0 && ee > -1900) r = ldexp((double)V, ee - 36);
+            if (V != 0 && ee > -900) {
+              // exact power-of-two scaling by adding to the exponent field of (double)V
+              r = __longlong_as_double(__double_as_longlong((double)V) + ((long long)ee << 52));
+            }
             out[2 * gc + part] = r;
           }
         }
