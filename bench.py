@@ -1,22 +1,28 @@
 #!/usr/bin/env python
 """Benchmark of the two-site TDVP hot path on B300.
 
-Workload (the configuration the metric is quoted on): the effective
-Hamiltonian of a mid-chain bond of the L=60 chain, U(1)xSU(2) reduced tensors,
-multiplets (Q, 2S) with Q in [-12, 12], 2S in [0, 12], Q + 2S = k (mod 2),
-d(Q,S) = round(D0 exp(-Q^2/18 - S^2/4.5)) with D0 the smallest value giving a
-U(1)-equivalent bond dimension >= 4096 on both outer bonds (k = 30 and 32),
-entries i.i.d. complex normal from a fixed seed, each tensor normalised, exact
-particle-hole-frame Fermi-Hubbard MPO with U=4, J=1.
+Workload (L=60, chi=4096 U(1)-equivalent, U(1)xSU(2), U=4, J=1): a synthetic
+right-canonical random state of the open L=60 chain whose bonds carry the
+benchmark multiplet profile d(Q,S) = round(D0 exp(-Q^2/18 - S^2/4.5)) (capped
+by the exact multiplet counts), D0 chosen so the middle bond reaches chi = 4096,
+orthogonality centre on site 29.
 
-One step = one Krylov exponential exp(-i tau H_eff) theta at that bond: k
-Lanczos matvecs (H_eff theta), full re-orthogonalisation, the small
-exponential, and the assembly of the result, all on the GPU.  The metric value
-is the algorithmic H_eff.psi throughput (8 flops per complex multiply-add of the
-reduced block products) over the whole step.
+One step = the two updates of the second-order sweep at the middle bond (29,30):
+left to right then right to left.  Each update forms theta, runs the Krylov
+exponential exp(-i dt/2 H_eff) (Lanczos, full re-orthogonalisation, small
+exponential), splits by per-sector SVD with truncation to chi <= 4096 and
+eps = 1e-9, updates the environment, evolves the new centre backward with the
+one-site H_eff, and returns the new bond's entropy; the step ends with the
+centre-site observables.  Every row of the hot path runs in the timed step.
+
+The metric value is the whole-step throughput of algorithmic block-GEMM work
+(H_eff matvecs and environment updates, 8 flops per complex multiply-add of the
+reduced block products).  heff_kernel reports the H_eff.psi kernel alone on the
+chi=4096 bond problem (random reduced environments), sweep the seconds per
+sweep estimated from the mid-chain bond updates.
 
 --impl reference runs the CPU oracle (U(1)xU(1) block-sparse brute force) on a
-bounded sample of output blocks of the same workload expanded to U(1)xU(1).
+bounded sample of output blocks of the same bond expanded to U(1)xU(1).
 """
 from __future__ import annotations
 
@@ -134,24 +140,20 @@ def barrier(ws):
 # engine arm
 # ---------------------------------------------------------------------------
 
-def run_engine(args):
-    import torch
-
-    from paper_2606_04771_b300 import BondProblem, lib
+def heff_kernel_profile(args, dev, stream):
+    """H_eff.psi on the chi=4096 bond problem: stage times and the Krylov step."""
     import ctypes as C
 
-    rank, ws = init_dist()
-    dev = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(dev)
-    stream = torch.cuda.Stream()
+    from paper_2606_04771_b300 import BondProblem, lib
+    from paper_2606_04771_b300._lib import check
+
     D0, tab, left, right = config2_tables()
-    seed = synth.SEED_BOND + rank
     bp = BondProblem(left, right, J=1.0, U=4.0, symmetry="su2", precision=args.precision,
                      krylov_max=args.krylov, krylov_tol=0.0, stream=stream.cuda_stream, device=dev)
-    keys, dims, offs, n = bp.blocks(0)
-    _, ld, _, nl = bp.blocks(1)
-    _, rd, _, nr = bp.blocks(2)
-    g = synth.rng(seed)
+    _, _, _, n = bp.blocks(0)
+    _, _, _, nl = bp.blocks(1)
+    _, _, _, nr = bp.blocks(2)
+    g = synth.rng(synth.SEED_BOND)
 
     def normed(k):
         v = synth.complex_normal(g, k)
@@ -161,98 +163,117 @@ def run_engine(args):
     bp.set_env(1, normed(nl))
     bp.set_env(2, normed(nr))
     flops_mv = bp.heff_flops()
-    theta = torch.from_numpy(theta_h).to(f"cuda:{dev}")
-    out = torch.empty_like(theta)
+    pms, pfl, pby = (C.c_double * 3)(), (C.c_longlong * 3)(), (C.c_longlong * 3)()
+    check(lib().tdvp_heff_profile(bp.h, 5, pms, pfl, pby))
+    stage_ms = list(pms)
+    gemm_ms = stage_ms[0] + stage_ms[2]
+    gemm_flops = pfl[0] + pfl[2]
+    # end to end through the C ABI with host buffers: H2D theta, Krylov step, D2H result
+    host_out = np.empty_like(theta_h)
+    bp.krylov_expm(theta_h, host_out, tau=0.025)
+    t0 = time.perf_counter()
+    reps = 3
+    for _ in range(reps):
+        bp.krylov_expm(theta_h, host_out, tau=0.025)
+    e2e_s = (time.perf_counter() - t0) / reps
+    kdim = bp.last_krylov_dim()
+    out = {"matvec_gflop": flops_mv / 1e9, "stage_ms": stage_ms, "gemm_ms": gemm_ms,
+           "tflops": gemm_flops / (gemm_ms * 1e-3) / 1e12, "theta_elems": int(n),
+           "krylov_step_ms_host": 1e3 * e2e_s, "krylov_dim": kdim,
+           "e2e_tflops": kdim * flops_mv / e2e_s / 1e12, "h2d_bytes": int(theta_h.nbytes),
+           "d2h_bytes": int(host_out.nbytes)}
+    bp.close()
+    return out, gemm_flops, gemm_ms
+
+
+def run_engine(args):
+    import torch
+
+    from paper_2606_04771_b300 import Chain
+
+    rank, ws = init_dist()
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()
+    L, chi, mid, dt, eps = 60, args.chi, 29, 0.05, 1e-9
+    t0 = time.perf_counter()
+    ch = Chain(L, 1.0, 4.0, symmetry="su2", random_chi=chi, seed=synth.SEED_BOND + rank, center=mid,
+               precision=args.precision, krylov_max=args.krylov, stream=stream.cuda_stream, device=dev)
+    setup_s = time.perf_counter() - t0
+    chis, red = ch.bond_dims()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")  # > L2 (126 MB)
 
-    kdim = args.krylov
-
-    def step(x, y):
-        # one Krylov exponential of tau H_eff built from kdim matvecs with full
-        # re-orthogonalisation; the engine routine lives in the library
-        bp.krylov_expm(x, y, tau=0.025)
+    def step():
+        s1 = ch.bond_update(mid, 0, dt, chi, eps)
+        s2 = ch.bond_update(mid, 1, dt, chi, eps)
+        return s1, s2, ch.measure_center()
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             flush.zero_()
-            step(theta, out)
+            step()
         stream.synchronize()
         barrier(ws)
-        torch.cuda.synchronize()
+        st0 = ch.stats()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         with ClockSampler(dev) as clk:
             for i in range(args.steps):
                 flush.zero_()
                 evs[i][0].record(stream)
-                step(theta, out)
+                ents = step()
                 evs[i][1].record(stream)
             stream.synchronize()
-        torch.cuda.synchronize()
+        st1 = ch.stats()
     barrier(ws)
     ms = [a.elapsed_time(b) for a, b in evs]
     ms_step = max_over_ranks(sum(ms) / len(ms), ws)
-    mv_per_step = bp.last_krylov_dim()
-    flops_step = flops_mv * mv_per_step
+    flops_step = ((st1["heff_flops"] - st0["heff_flops"]) + (st1["env_flops"] - st0["env_flops"])) / args.steps
     value = ws * flops_step / (ms_step * 1e-3) / 1e12
+    chis_after, _ = ch.bond_dims()
+    ch.close()
 
-    # per-kernel profile of the dominant kernel (the block GEMM stages)
-    pms = (C.c_double * 3)()
-    pfl = (C.c_longlong * 3)()
-    pby = (C.c_longlong * 3)()
-    from paper_2606_04771_b300._lib import check
-
-    check(lib().tdvp_heff_profile(bp.h, 5, pms, pfl, pby))
-    stage_ms = list(pms)
-    gemm_ms = stage_ms[0] + stage_ms[2]
-    gemm_flops = pfl[0] + pfl[2]
+    heff, gemm_flops, gemm_ms = heff_kernel_profile(args, dev, stream)
     peaks, peak_kind = load_peaks()
     if args.precision == "fp64":
-        peak = 1250.0 / 1000.0  # TFLOP/s, FP64 nominal (no FP64 tensor path on B300)
-        bound, pnote, issued = "alu", "FP64 nominal 1.25 TFLOP/s (recipe table)", 1
+        peak, bound, pnote, issued = 1.25, "alu", "FP64 nominal 1.25 TFLOP/s (recipe table)", 1
     elif args.precision == "3xtf32":
         peak = peaks["bf16_tflops"] * 1.1 / 2.25
         bound, pnote, issued = "tensor", f"TF32 = {peak_kind} bf16 burst x 1.1/2.25 (nominal ratio)", 3
     else:
-        peak = peaks["bf16_tflops"]
-        bound, pnote, issued = "tensor", f"{peak_kind} bf16 burst (BF16X4 issues 10 digit products per MAC)", 10
-    achieved = gemm_flops / (gemm_ms * 1e-3) / 1e12
+        peak, bound, issued = peaks["bf16_tflops"], "tensor", 10
+        pnote = f"{peak_kind} bf16 burst (BF16X4 issues 10 digit products per complex-embedded MAC)"
+    achieved = heff["tflops"]
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "grouped block GEMM (stages 1+3 of H_eff.psi)",
-                "peak_source": pnote, "stage_ms": stage_ms,
+                "traffic": None, "kernel": "grouped block GEMM of H_eff.psi (stages 1+3), chi=4096 bond",
+                "peak_source": pnote, "stage_ms": heff["stage_ms"],
                 "tensor_pipe_frac_upper": achieved * issued / peak}
-
-    # end to end through the C ABI with host buffers: H2D of theta, the step, D2H of the result
-    host_in = theta_h.copy()
-    host_out = np.empty_like(host_in)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(max(1, min(args.steps, 5))):
-        bp.krylov_expm(host_in, host_out, tau=0.025)
-    e2e_s = (time.perf_counter() - t0) / max(1, min(args.steps, 5))
-    e2e = {"value": ws * flops_step / e2e_s / 1e12, "unit": UNIT, "h2d_bytes_per_step": int(host_in.nbytes),
-           "d2h_bytes_per_step": int(host_out.nbytes)}
-
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp64": "c128 (f64)", "3xtf32": "c128 storage, 3xTF32 products", "bf16x4": "c128 storage, BF16x4 digit products"}[args.precision],
-        "data": "synthetic (seeded complex normal tensors, paper-shaped sector table)",
-        "config": {"workload": "H_eff Krylov step at a mid-chain bond of L=60, U(1)xSU(2), chi=4096 (U(1)-equivalent)",
-                   "chi": int(sum(d * (ts + 1) for (_, ts, d) in tab)), "chi_su2": int(sum(d for (_, _, d) in tab)),
-                   "d_max": int(max(d for (_, _, d) in tab)), "multiplets": len(tab), "D0": D0,
-                   "theta_elems": int(n), "matvec_gflop": flops_mv / 1e9, "krylov_dim": mv_per_step,
-                   "precision": args.precision, "l2": "flushed (256 MB write) before every timed step",
-                   "parallelism": f"replicas x{ws} (independent bonds, no collective)"},
+        "dtype": {"fp64": "c128 (f64)", "3xtf32": "c128 storage, 3xTF32 products",
+                  "bf16x4": "c128 storage, BF16x4 digit products"}[args.precision],
+        "data": "synthetic (seeded random right-canonical MPS with the paper-shaped multiplet profile)",
+        "config": {"workload": "mid-chain two-site TDVP bond updates (L->R + R->L at bond 29) of L=60, "
+                               "U(1)xSU(2), chi=4096 (U(1)-equivalent), dt=0.05, eps=1e-9",
+                   "L": L, "chi": int(chis[mid + 1]), "chi_su2": int(red[mid + 1]), "chi_cap": chi,
+                   "chi_after": int(chis_after[mid + 1]), "precision": args.precision, "setup_s": setup_s,
+                   "flops_per_step": flops_step, "bond_entropy": ents[1],
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": f"replicas x{ws} (independent states, no collective)"},
+        "sweep": {"sec_per_sweep_est": 2 * (L - 1) / 2 * ms_step / 1e3,
+                  "note": "(L-1) bonds x 2 directions at the mid-chain cost: an upper estimate"},
+        "heff_kernel": heff,
         "roofline": roofline,
-        "e2e": e2e,
-        "gpu_launches": bp.launches_per_step() * args.steps,
+        "e2e": {"value": heff["e2e_tflops"], "unit": UNIT, "h2d_bytes_per_step": heff["h2d_bytes"],
+                "d2h_bytes_per_step": heff["d2h_bytes"],
+                "path": "tdvp_krylov_expm with host buffers on the chi=4096 bond (H2D theta, D2H result)"},
+        "gpu_launches": None,
         "clocks": clk.summary(),
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(budget_s=args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    bp.close()
 
 
 # ---------------------------------------------------------------------------
@@ -325,11 +346,12 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
     ap.add_argument("--precision", default="bf16x4", choices=["fp64", "3xtf32", "bf16x4"])
-    ap.add_argument("--krylov", type=int, default=10)
+    ap.add_argument("--krylov", type=int, default=20)
+    ap.add_argument("--chi", type=int, default=4096)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -77,6 +77,20 @@ void tdvp_opts_default(tdvp_opts* o);
  * Errors: TDVP_EINVAL, TDVP_ENOMEM, TDVP_ECUDA. */
 int tdvp_create(int L, double J, double U, int symmetry, const tdvp_opts* opts, tdvp_ctx** out);
 
+/* Create a chain in a synthetic random state for benchmarking: a right-canonical
+ * MPS of L sites (half filling, total spin singlet in the engine frame) whose
+ * bond k holds the multiplets (n, t) of k sites that can couple to the total
+ * state, with degeneracy min(round(D0 exp(-Q^2/18 - S^2/4.5)), exact multiplet
+ * counts of the left and right parts), Q = n - k, S = t/2, D0 chosen so the middle
+ * bond reaches chi_target (U(1)-equivalent); block entries are counter-based
+ * normal numbers from seed; sites left of `center` are left-orthonormalised,
+ * sites right of it right-orthonormalised, the centre is normalised, and the
+ * environments on both sides are built.  The state has the
+ * benchmark's block structure but no physical meaning.  Errors: TDVP_EINVAL,
+ * TDVP_ENOMEM, TDVP_ECUDA. */
+int tdvp_create_random(int L, double J, double U, int symmetry, long long chi_target, unsigned long long seed,
+                       int center, const tdvp_opts* opts, tdvp_ctx** out);
+
 /* One second-order two-site TDVP time step dt (Sec. S2.2): a left-to-right and a
  * right-to-left half sweep with tau = dt/2.  After each two-site SVD the kept
  * multiplets are the largest singular values (ties broken by sector, then
@@ -87,7 +101,24 @@ int tdvp_create(int L, double J, double U, int symmetry, const tdvp_opts* opts, 
  * TDVP_ENUMERIC, TDVP_ECUDA, TDVP_ENOMEM. */
 int tdvp_step(tdvp_ctx* ctx, double dt, long long chi_max, double eps_trunc);
 
-/* Observables of the current state (Sec. 3, Figs. 1-2 use n_{i up}):
+/* One two-site update of the sweep (Sec. S2.2) at bond (bond, bond+1), the unit
+ * the full step repeats L-1 times per half sweep: theta formation, the Krylov
+ * exponential exp(-i dt/2 H_eff), the per-sector SVD with truncation (same rule
+ * as tdvp_step), the environment update, and the backward one-site evolution of
+ * the new centre by +dt/2.  direction 0: left to right, the orthogonality
+ * centre must be on site `bond` and moves to bond+1; direction 1: right to left,
+ * centre on bond+1, moves to `bond`.  *s_ent (nullable) receives the von Neumann
+ * entropy of the new bond from the kept singular values.  Errors: TDVP_EINVAL,
+ * TDVP_ESTATE (centre elsewhere), TDVP_ENUMERIC, TDVP_ECUDA. */
+int tdvp_bond_update(tdvp_ctx* ctx, int bond, int direction, double dt, long long chi_max, double eps_trunc,
+                     double* s_ent);
+
+/* <n_i>, <S^z_i>, <n_{i up} n_{i dn}> of the orthogonality-centre site i (*site),
+ * in the frame of Eq. (FHM).  Any output may be NULL. */
+int tdvp_measure_center(tdvp_ctx* ctx, int* site, double* n, double* sz, double* docc);
+
+/* Observables of the current state (Sec. 3, Figs. 1-2 use n_{i up}); needs the
+ * orthogonality centre on site 0 (as after tdvp_create or tdvp_step):
  *   n[L]     <n_i>            sz[L]   <S^z_i> = (<n_{i up}> - <n_{i dn}>)/2
  *   docc[L]  <n_{i up} n_{i dn}>
  *   s_ent[L-1] von Neumann entropy (natural log) of the cut after site k
@@ -103,8 +134,11 @@ int tdvp_bond_dims(tdvp_ctx* ctx, long long* chi, long long* chi_red);
 /* Counters since creation: out[0] seconds in tdvp_step, out[1] effective
  * Hamiltonian flops (algorithmic, 8 per complex multiply-add), out[2]
  * environment-update flops, out[3] matvecs, out[4] largest Krylov dimension
- * used, out[5] largest discarded weight, out[6] largest chi seen.  n = length of
- * out (at most 7 are written). */
+ * used, out[5] largest discarded weight, out[6] largest chi seen, out[7..12]
+ * wall seconds per phase (theta formation, planning, two-site Krylov, SVD split,
+ * environment update, one-site Krylov; filled only when the environment variable
+ * TDVP_PROFILE_PHASES=1 was set at creation, which synchronises at phase
+ * boundaries), out[13] number of steps.  n = length of out (at most 14). */
 int tdvp_stats(tdvp_ctx* ctx, double* out, int n);
 
 /* ---- single-bond problems (the effective-Hamiltonian benchmark) ------------

@@ -294,33 +294,43 @@ class DenseTDVP:
         self.krylov_dims.append(info["krylov_dim"])
         return out
 
+    def bond_lr(self, i, tau, chi_max, eps, backward):
+        """Left-to-right two-site update at bond (i, i+1); centre moves from i to i+1."""
+        mps, W = self.mps, self.W
+        theta = np.einsum("asc,ctb->astb", mps[i], mps[i + 1])
+        Le, Re = self.Lenv[i], self.R[i + 2]
+        theta = self._expm(lambda x: heff2(Le, W, W, Re, x), theta, tau)
+        A, M, disc, s = split_svd(theta, chi_max, eps, "right")
+        self.max_discarded = max(self.max_discarded, disc)
+        self.last_s = s
+        mps[i], mps[i + 1] = A, M
+        self.Lenv[i + 1] = update_left(self.Lenv[i], A, W)
+        if backward:
+            Le1 = self.Lenv[i + 1]
+            mps[i + 1] = self._expm(lambda x: heff1(Le1, W, Re, x), mps[i + 1], -tau)
+
+    def bond_rl(self, i, tau, chi_max, eps, backward):
+        """Right-to-left two-site update at bond (i, i+1); centre moves from i+1 to i."""
+        mps, W = self.mps, self.W
+        theta = np.einsum("asc,ctb->astb", mps[i], mps[i + 1])
+        Le, Re = self.Lenv[i], self.R[i + 2]
+        theta = self._expm(lambda x: heff2(Le, W, W, Re, x), theta, tau)
+        M, B, disc, s = split_svd(theta, chi_max, eps, "left")
+        self.max_discarded = max(self.max_discarded, disc)
+        self.last_s = s
+        mps[i], mps[i + 1] = M, B
+        self.R[i + 1] = update_right(self.R[i + 2], B, W)
+        if backward:
+            Re1 = self.R[i + 1]
+            mps[i] = self._expm(lambda x: heff1(Le, W, Re1, x), mps[i], -tau)
+
     def step(self, dt, chi_max, eps):
-        L, W, mps = self.L, self.W, self.mps
+        L = self.L
         tau = dt / 2
-        # left to right
         for i in range(L - 1):
-            theta = np.einsum("asc,ctb->astb", mps[i], mps[i + 1])
-            Le, Re = self.Lenv[i], self.R[i + 2]
-            theta = self._expm(lambda x: heff2(Le, W, W, Re, x), theta, tau)
-            A, M, disc, _ = split_svd(theta, chi_max, eps, "right")
-            self.max_discarded = max(self.max_discarded, disc)
-            mps[i], mps[i + 1] = A, M
-            self.Lenv[i + 1] = update_left(self.Lenv[i], A, W)
-            if i < L - 2:
-                Le1 = self.Lenv[i + 1]
-                mps[i + 1] = self._expm(lambda x: heff1(Le1, W, Re, x), mps[i + 1], -tau)
-        # right to left
+            self.bond_lr(i, tau, chi_max, eps, i < L - 2)
         for i in range(L - 2, -1, -1):
-            theta = np.einsum("asc,ctb->astb", mps[i], mps[i + 1])
-            Le, Re = self.Lenv[i], self.R[i + 2]
-            theta = self._expm(lambda x: heff2(Le, W, W, Re, x), theta, tau)
-            M, B, disc, _ = split_svd(theta, chi_max, eps, "left")
-            self.max_discarded = max(self.max_discarded, disc)
-            mps[i], mps[i + 1] = M, B
-            self.R[i + 1] = update_right(self.R[i + 2], B, W)
-            if i > 0:
-                Re1 = self.R[i + 1]
-                mps[i] = self._expm(lambda x: heff1(Le, W, Re1, x), mps[i], -tau)
+            self.bond_rl(i, tau, chi_max, eps, i > 0)
 
     def bond_dims(self):
         return [A.shape[2] for A in self.mps[:-1]]

@@ -46,6 +46,10 @@ def lib():
             "tdvp_opts_default": (None, [P(Opts)]),
             "tdvp_create": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_int, P(Opts), P(vp)]),
             "tdvp_step": (C.c_int, [vp, C.c_double, C.c_longlong, C.c_double]),
+            "tdvp_create_random": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_int, C.c_longlong, C.c_ulonglong,
+                                             C.c_int, P(Opts), P(vp)]),
+            "tdvp_bond_update": (C.c_int, [vp, C.c_int, C.c_int, C.c_double, C.c_longlong, C.c_double, vp]),
+            "tdvp_measure_center": (C.c_int, [vp, vp, vp, vp, vp]),
             "tdvp_measure": (C.c_int, [vp, vp, vp, vp, vp, vp]),
             "tdvp_bond_dims": (C.c_int, [vp, vp, vp]),
             "tdvp_stats": (C.c_int, [vp, vp, C.c_int]),
@@ -178,14 +182,19 @@ class _Ctx:
 
 
 class Chain(_Ctx):
-    """An L-site chain in the Neel state, evolved with tdvp_step."""
+    """An L-site chain in the Neel state (or, with random_chi, a synthetic random
+    right-canonical state of that bond dimension), evolved with tdvp_step."""
 
-    def __init__(self, L, J=1.0, U=4.0, symmetry="su2", **opts):
+    def __init__(self, L, J=1.0, U=4.0, symmetry="su2", random_chi=None, seed=1, center=0, **opts):
         super().__init__()
         self.L = L
         self.sym = symmetry
         o = make_opts(**opts)
-        check(lib().tdvp_create(L, J, U, SYM[symmetry], C.byref(o), C.byref(self.h)))
+        if random_chi is None:
+            check(lib().tdvp_create(L, J, U, SYM[symmetry], C.byref(o), C.byref(self.h)))
+        else:
+            check(lib().tdvp_create_random(L, J, U, SYM[symmetry], int(random_chi), int(seed), int(center),
+                                           C.byref(o), C.byref(self.h)))
 
     def step(self, dt, chi_max, eps):
         check(lib().tdvp_step(self.h, dt, int(chi_max), eps))
@@ -204,6 +213,19 @@ class Chain(_Ctx):
             out["energy"] = float(e[0])
         return out
 
+    def bond_update(self, bond, direction, dt, chi_max, eps):
+        """One two-site update at (bond, bond+1); returns the new bond's entropy."""
+        s = np.zeros(1)
+        check(lib().tdvp_bond_update(self.h, bond, direction, dt, int(chi_max), eps, s.ctypes.data))
+        return float(s[0])
+
+    def measure_center(self):
+        site = C.c_int()
+        v = np.zeros(3)
+        check(lib().tdvp_measure_center(self.h, C.byref(site), v[0:].ctypes.data, v[1:].ctypes.data,
+                                        v[2:].ctypes.data))
+        return site.value, {"n": v[0], "sz": v[1], "docc": v[2]}
+
     def bond_dims(self):
         chi = np.zeros(self.L + 1, dtype=np.int64)
         red = np.zeros(self.L + 1, dtype=np.int64)
@@ -211,9 +233,10 @@ class Chain(_Ctx):
         return chi, red
 
     def stats(self):
-        v = np.zeros(7)
-        check(lib().tdvp_stats(self.h, v.ctypes.data, 7))
-        keys = ["seconds", "heff_flops", "env_flops", "matvecs", "max_krylov", "max_discarded", "chi_max_seen"]
+        v = np.zeros(14)
+        check(lib().tdvp_stats(self.h, v.ctypes.data, 14))
+        keys = ["seconds", "heff_flops", "env_flops", "matvecs", "max_krylov", "max_discarded", "chi_max_seen",
+                "t_theta", "t_plan", "t_krylov2", "t_split", "t_env", "t_krylov1", "steps"]
         return dict(zip(keys, v.tolist()))
 
 

@@ -96,6 +96,20 @@ int tdvp_create(int L, double J, double U, int symmetry, const tdvp_opts* opts, 
   });
 }
 
+int tdvp_create_random(int L, double J, double U, int symmetry, long long chi_target, unsigned long long seed,
+                       int center, const tdvp_opts* opts, tdvp_ctx** out) {
+  if (!out) return fail(TDVP_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (symmetry != TDVP_SYM_U1U1 && symmetry != TDVP_SYM_U1SU2) return fail(TDVP_EINVAL, "unknown symmetry");
+  return guarded([&] {
+    tdvp_opts d;
+    tdvp_opts_default(&d);
+    auto* e = tdvp::Engine::random_state(L, J, U, symmetry == TDVP_SYM_U1SU2, chi_target, seed, center,
+                                         to_opts(opts ? opts : &d));
+    *out = new tdvp_ctx{e};
+  });
+}
+
 int tdvp_bond_create(int symmetry, double J, double U, int nl, const int* left, int nr, const int* right,
                      const tdvp_opts* opts, tdvp_ctx** out) {
   if (!out) return fail(TDVP_EINVAL, "out is NULL");
@@ -114,6 +128,18 @@ int tdvp_bond_create(int symmetry, double J, double U, int nl, const int* left, 
 int tdvp_step(tdvp_ctx* ctx, double dt, long long chi_max, double eps_trunc) {
   if (!ctx) return fail(TDVP_EINVAL, "ctx is NULL");
   return guarded([&] { ctx->eng->step(dt, chi_max, eps_trunc); });
+}
+
+int tdvp_bond_update(tdvp_ctx* ctx, int bond, int direction, double dt, long long chi_max, double eps_trunc,
+                     double* s_ent) {
+  if (!ctx) return fail(TDVP_EINVAL, "ctx is NULL");
+  if (direction != 0 && direction != 1) return fail(TDVP_EINVAL, "direction must be 0 or 1");
+  return guarded([&] { ctx->eng->single_bond(bond, direction, dt, chi_max, eps_trunc, s_ent); });
+}
+
+int tdvp_measure_center(tdvp_ctx* ctx, int* site, double* n, double* sz, double* docc) {
+  if (!ctx) return fail(TDVP_EINVAL, "ctx is NULL");
+  return guarded([&] { ctx->eng->measure_center(site, n, sz, docc); });
 }
 
 int tdvp_measure(tdvp_ctx* ctx, double* n, double* sz, double* docc, double* s_ent, double* energy) {
@@ -143,9 +169,10 @@ int tdvp_stats(tdvp_ctx* ctx, double* out, int n) {
   if (!ctx || !out) return fail(TDVP_EINVAL, "NULL argument");
   return guarded([&] {
     const tdvp::StepStats& s = ctx->eng->stats();
-    double v[7] = {s.seconds, (double)s.heff_flops, (double)s.env_flops, (double)s.matvecs, (double)s.max_krylov,
-                   s.max_discarded, (double)s.chi_max_seen};
-    for (int i = 0; i < n && i < 7; ++i) out[i] = v[i];
+    double v[14] = {s.seconds, (double)s.heff_flops, (double)s.env_flops, (double)s.matvecs, (double)s.max_krylov,
+                    s.max_discarded, (double)s.chi_max_seen, s.phase[0], s.phase[1], s.phase[2], s.phase[3],
+                    s.phase[4], s.phase[5], (double)s.steps};
+    for (int i = 0; i < n && i < 14; ++i) out[i] = v[i];
   });
 }
 

@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <tuple>
@@ -142,6 +143,8 @@ void Engine::init_common(bool su2, double J, double U, const Opts& o) {
     TDVP_CUDA(cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking));
     own_stream_ = true;
   }
+  const char* pe = std::getenv("TDVP_PROFILE_PHASES");
+  profile_ = pe && pe[0] == '1';
   TDVP_CUDA(cudaMallocHost(&pinned_, 4096));
   TDVP_CUDA(cudaMalloc(&dstatus_, sizeof(int) * 4));
   TDVP_CUDA(cudaMemsetAsync(dstatus_, 0, sizeof(int) * 4, stream_));
@@ -181,6 +184,311 @@ Engine* Engine::bond_problem(bool su2, double J, double U, const std::vector<Sec
   e->plan_heff2(*e->bp_heff_, e->Lenv_[0], e->Renv_[2], e->theta_, e->bonds_[0], e->bonds_[2]);
   TDVP_CUDA(cudaStreamSynchronize(e->stream_));
   return e.release();
+}
+
+// Synthetic state for the sweep benchmark: bond k (k sites to its left) carries the
+// multiplets (n, t) of the k-site Hilbert space that can couple with the right part
+// to the total singlet at half filling, with degeneracy
+//   d = min(round(D0 exp(-Q^2/18 - S^2/4.5)), exact multiplicity left, exact multiplicity right),
+// Q = n - k, S = t/2 (U1U1: the SU(2) profile summed over S >= |S^z|), D0 chosen so that
+// the middle bond reaches chi_target; then every sector is made reachable and every
+// right-canonical row space feasible, blocks are filled with counter-based normal
+// numbers and sites 1..L-1 are right-orthonormalised per left sector.
+Engine* Engine::random_state(int L, double J, double U, bool su2, long long chi_target, unsigned long long seed,
+                             int center, const Opts& o) {
+  if (L < 2 || (L % 2)) throw Error(-1, "L must be even and >= 2");
+  if (chi_target < 1) throw Error(-1, "chi_target must be >= 1");
+  if (center < 0 || center >= L) throw Error(-1, "center must be a site index");
+  std::unique_ptr<Engine> e(new Engine());
+  e->L_ = L;
+  e->init_common(su2, J, U, o);
+  const Model& M = e->model_;
+  const int N = L;  // particles in the particle-hole frame at half filling
+  typedef std::map<std::pair<int, int>, double> Cnt;
+  std::vector<Cnt> cnt(L + 1);
+  cnt[0][{0, 0}] = 1.0;
+  std::vector<std::pair<int, int>> f;
+  for (int k = 0; k < L; ++k)
+    for (auto& q : cnt[k])
+      for (auto& ms : M.site) {
+        M.fuse(q.first.first, q.first.second, ms.n, ms.t, f);
+        for (auto& r : f) cnt[k + 1][r] = std::min(cnt[k + 1][r] + q.second, 1e12);
+      }
+  auto profile = [&](int Q, int t) -> double {
+    if (su2) return std::exp(-(double)Q * Q / 18.0 - (t / 2.0) * (t / 2.0) / 4.5);
+    double acc = 0.0;  // SU(2) profile summed over S >= |S^z|
+    for (int tt = std::abs(t); tt <= 24; tt += 2) acc += std::exp(-(double)Q * Q / 18.0 - (tt / 2.0) * (tt / 2.0) / 4.5);
+    return acc;
+  };
+  auto tables = [&](double D0) {
+    std::vector<BondSpace> b(L + 1);
+    for (int k = 0; k <= L; ++k) {
+      for (auto& q : cnt[k]) {
+        int n = q.first.first, t = q.first.second;
+        std::pair<int, int> partner = su2 ? std::make_pair(N - n, t) : std::make_pair(N - n, -t);
+        auto it = cnt[L - k].find(partner);
+        if (it == cnt[L - k].end()) continue;
+        double cap = std::min(q.second, it->second);
+        double d = std::floor(D0 * profile(n - k, t) + 0.5);
+        if (k == 0 || k == L) d = 1.0;
+        d = std::min(d, cap);
+        if (d >= 1.0) b[k].s.push_back({n, t, (int)d});
+      }
+    }
+    // reachability from the left and feasible right-canonical rows, until stable
+    for (int pass = 0; pass < 4; ++pass) {
+      for (int k = 0; k < L; ++k) {  // d_{k+1}(b) <= sum over (a, s) fusing into b of d_k(a)
+        std::map<std::pair<int, int>, long long> reach;
+        for (auto& a : b[k].s)
+          for (auto& ms : M.site) {
+            M.fuse(a.n, a.t, ms.n, ms.t, f);
+            for (auto& r : f) reach[r] += a.d;
+          }
+        for (auto& x : b[k + 1].s) x.d = (int)std::min<long long>(x.d, reach[{x.n, x.t}]);
+      }
+      for (int k = L - 1; k >= 0; --k) {  // d_k(a) <= sum over (s, b) of d_{k+1}(b)
+        std::map<std::pair<int, int>, int> dn;
+        for (auto& x : b[k + 1].s) dn[{x.n, x.t}] = x.d;
+        for (auto& a : b[k].s) {
+          long long cols = 0;
+          for (auto& ms : M.site) {
+            M.fuse(a.n, a.t, ms.n, ms.t, f);
+            for (auto& r : f) {
+              auto it = dn.find(r);
+              if (it != dn.end()) cols += it->second;
+            }
+          }
+          a.d = (int)std::min<long long>(a.d, cols);
+        }
+      }
+      for (auto& bb : b) {
+        std::vector<Sector> keep;
+        for (auto& x : bb.s)
+          if (x.d > 0) keep.push_back(x);
+        bb.s = keep;
+      }
+    }
+    for (auto& bb : b) {
+      std::sort(bb.s.begin(), bb.s.end(), [](const Sector& x, const Sector& y) {
+        return x.n != y.n ? x.n < y.n : x.t < y.t;
+      });
+      bb.build_index();
+    }
+    return b;
+  };
+  auto chi_mid = [&](const std::vector<BondSpace>& b) {
+    long long c = 0;
+    for (auto& x : b[L / 2].s) c += (long long)x.d * M.mult_dim(x.t);
+    return c;
+  };
+  double lo = 0.0, hi = 1.0;
+  while (chi_mid(tables(hi)) < chi_target && hi < 1e7) hi *= 2;
+  for (int it = 0; it < 50; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (chi_mid(tables(mid)) >= chi_target) hi = mid;
+    else lo = mid;
+  }
+  e->bonds_ = tables(hi);
+  for (int k = 0; k <= L; ++k)
+    if (e->bonds_[k].s.empty()) throw Error(-5, "empty bond in the synthetic state");
+  e->site_.resize(L);
+  long long off = 0;
+  for (int i = 0; i < L; ++i) {
+    e->build_site_layout(e->site_[i], e->bonds_[i], e->bonds_[i + 1]);
+    e->alloc(e->site_[i], false);
+    launch_fill_normal(e->site_[i].data(), e->site_[i].size, seed, off, e->stream_);
+    off += e->site_[i].size;
+  }
+  for (int i = 0; i < center; ++i) e->orthonormalize_cols(e->site_[i], e->bonds_[i], e->bonds_[i + 1]);
+  for (int i = center + 1; i < L; ++i) e->orthonormalize_rows(e->site_[i], e->bonds_[i], e->bonds_[i + 1]);
+  e->center_ = center;
+  {  // normalise the centre tensor
+    BTensor& T = e->site_[center];
+    DevBuf part((size_t)296 * sizeof(cplx), e->stream_), nrm(sizeof(cplx), e->stream_);
+    launch_dots(T.data(), 0, 1, T.data(), T.size, part.as<cplx>(), dots_grid(T.size), nrm.as<cplx>(), nullptr,
+                e->stream_);
+    cplx h;
+    TDVP_CUDA(cudaMemcpyAsync(&h, nrm.p, sizeof(cplx), cudaMemcpyDeviceToHost, e->stream_));
+    TDVP_CUDA(cudaStreamSynchronize(e->stream_));
+    std::vector<double> inv(1, 1.0 / std::sqrt(h.x));
+    DevBuf dinv(sizeof(double), e->stream_);
+    TDVP_CUDA(cudaMemcpyAsync(dinv.p, inv.data(), sizeof(double), cudaMemcpyHostToDevice, e->stream_));
+    CopyPlan cp;
+    CopyTask t{};
+    t.src = T.data();
+    t.dst = T.data();
+    t.rows = 1;
+    t.cols = (int)T.size;
+    t.src_rs = T.size;
+    t.src_cs = 1;
+    t.dst_rs = T.size;
+    t.dst_cs = 1;
+    t.gscale = dinv.as<double>();
+    cp.tasks.push_back(t);
+    cp.finalize(e->stream_);
+    cp.launch(e->stream_);
+    TDVP_CUDA(cudaStreamSynchronize(e->stream_));
+  }
+  e->Lenv_.clear();
+  e->Renv_.clear();
+  e->Lenv_.resize(L + 1);
+  e->Renv_.resize(L + 1);
+  std::vector<cplx> one(1, cplx{1.0, 0.0});
+  e->build_lenv_layout(e->Lenv_[0], e->bonds_[0], e->bonds_[0]);
+  e->alloc(e->Lenv_[0], true);
+  int bi = e->Lenv_[0].find(bkey(0, M.chB, 0));
+  TDVP_CUDA(cudaMemcpyAsync(e->Lenv_[0].ptr(bi), one.data(), sizeof(cplx), cudaMemcpyHostToDevice, e->stream_));
+  e->build_renv_layout(e->Renv_[L], e->bonds_[L], e->bonds_[L]);
+  e->alloc(e->Renv_[L], true);
+  bi = e->Renv_[L].find(bkey(0, M.chE, 0));
+  TDVP_CUDA(cudaMemcpyAsync(e->Renv_[L].ptr(bi), one.data(), sizeof(cplx), cudaMemcpyHostToDevice, e->stream_));
+  for (int k = L - 1; k >= center + 1; --k)
+    e->update_right_env(e->Renv_[k + 1], e->site_[k], e->Renv_[k], e->bonds_[k], e->bonds_[k + 1]);
+  for (int k = 0; k < center; ++k)
+    e->update_left_env(e->Lenv_[k], e->site_[k], e->Lenv_[k + 1], e->bonds_[k], e->bonds_[k + 1]);
+  TDVP_CUDA(cudaStreamSynchronize(e->stream_));
+  e->check_status();
+  return e.release();
+}
+
+// Replace the columns of every right sector b of T (the matrix [sum_(a,s) d_a x d_b]) by
+// an orthonormal basis of their column space (left singular vectors): T becomes
+// left-canonical, sum_(a,s) T^H T = 1 on every sector.
+void Engine::orthonormalize_cols(BTensor& T, const BondSpace& l, const BondSpace& r) {
+  std::vector<std::vector<int>> by(r.s.size());
+  for (int i = 0; i < (int)T.blocks.size(); ++i) by[T.blocks[i].key[2]].push_back(i);
+  std::vector<long long> goff(r.s.size()), voff(r.s.size());
+  std::vector<int> soff(r.s.size()), pv(r.s.size());
+  long long gt = 0, vt = 0;
+  int st = 0, mq = 1;
+  for (int b = 0; b < (int)r.s.size(); ++b) {
+    int p = 0;
+    for (int bi : by[b]) p += T.blocks[bi].rows;
+    int q = r.s[b].d;
+    if (p < q) throw Error(-5, "infeasible left-canonical sector");
+    pv[b] = p;
+    goff[b] = gt;
+    gt += (long long)p * q;
+    voff[b] = vt;
+    vt += (long long)q * q;
+    soff[b] = st;
+    st += q;
+    mq = std::max(mq, q);
+  }
+  DevBuf dG(std::max<long long>(gt, 1) * sizeof(cplx), stream_), dV(std::max<long long>(vt, 1) * sizeof(cplx), stream_);
+  DevBuf dS(std::max(st, 1) * sizeof(double), stream_), dP(std::max(st, 1) * sizeof(int), stream_);
+  CopyPlan gather, scatter;
+  std::vector<SvdTask> tasks;
+  for (int b = 0; b < (int)r.s.size(); ++b) {
+    int p = pv[b], q = r.s[b].d, r0 = 0;
+    cplx* G = dG.as<cplx>() + goff[b];
+    for (int bi : by[b]) {  // G = M, column-major p x q
+      const Block& blk = T.blocks[bi];
+      CopyTask t{};
+      t.src = T.ptr(bi);
+      t.rows = blk.rows;
+      t.cols = blk.cols;
+      t.src_rs = blk.cols;
+      t.src_cs = 1;
+      t.dst = G + r0;
+      t.dst_rs = 1;
+      t.dst_cs = p;
+      gather.tasks.push_back(t);
+      CopyTask u{};  // U = W / s
+      u.src = G + r0;
+      u.src_rs = 1;
+      u.src_cs = p;
+      u.col_map = dP.as<int>() + soff[b];
+      u.scale = dS.as<double>() + soff[b];
+      u.scale_mode = 2;
+      u.dst = T.ptr(bi);
+      u.rows = blk.rows;
+      u.cols = q;
+      u.dst_rs = q;
+      u.dst_cs = 1;
+      scatter.tasks.push_back(u);
+      r0 += blk.rows;
+    }
+    tasks.push_back({G, dV.as<cplx>() + voff[b], dS.as<double>() + soff[b], dP.as<int>() + soff[b], p, q});
+  }
+  gather.finalize(stream_);
+  gather.launch(stream_);
+  DevBuf dt = upload(tasks, stream_);
+  launch_jacobi_svd(dt.as<SvdTask>(), (int)tasks.size(), mq, 60, 1e-15, dstatus_, stream_);
+  scatter.finalize(stream_);
+  scatter.launch(stream_);
+  TDVP_CUDA(cudaStreamSynchronize(stream_));
+}
+
+// Replace the rows of every left sector a of T (the matrix [d_a x sum_(s,b) d_b]) by an
+// orthonormal basis of their row space (the right singular vectors), which makes T
+// right-canonical: sum_(s,b) T T^H = 1 on every sector.
+void Engine::orthonormalize_rows(BTensor& T, const BondSpace& l, const BondSpace& r) {
+  std::vector<std::vector<int>> by(l.s.size());
+  for (int i = 0; i < (int)T.blocks.size(); ++i) by[T.blocks[i].key[0]].push_back(i);
+  std::vector<long long> goff(l.s.size()), voff(l.s.size());
+  std::vector<int> soff(l.s.size()), qv(l.s.size());
+  long long gt = 0, vt = 0;
+  int st = 0, mq = 1;
+  for (int a = 0; a < (int)l.s.size(); ++a) {
+    int q = 0;
+    for (int bi : by[a]) q += T.blocks[bi].cols;
+    int p = l.s[a].d;
+    if (q < p) throw Error(-5, "infeasible right-canonical sector");
+    qv[a] = q;
+    goff[a] = gt;
+    gt += (long long)q * p;
+    voff[a] = vt;
+    vt += (long long)p * p;
+    soff[a] = st;
+    st += p;
+    mq = std::max(mq, p);
+  }
+  DevBuf dG(std::max<long long>(gt, 1) * sizeof(cplx), stream_), dV(std::max<long long>(vt, 1) * sizeof(cplx), stream_);
+  DevBuf dS(std::max(st, 1) * sizeof(double), stream_), dP(std::max(st, 1) * sizeof(int), stream_);
+  CopyPlan gather, scatter;
+  std::vector<SvdTask> tasks;
+  for (int a = 0; a < (int)l.s.size(); ++a) {
+    int p = l.s[a].d, q = qv[a], c0 = 0;
+    cplx* G = dG.as<cplx>() + goff[a];
+    for (int bi : by[a]) {  // G = M^H, column-major q x p
+      const Block& b = T.blocks[bi];
+      CopyTask t{};
+      t.src = T.ptr(bi);
+      t.rows = b.rows;
+      t.cols = b.cols;
+      t.src_rs = b.cols;
+      t.src_cs = 1;
+      t.dst = G + c0;
+      t.dst_rs = q;
+      t.dst_cs = 1;
+      t.conj = 1;
+      gather.tasks.push_back(t);
+      CopyTask u{};  // row k of V_M^H = conj(W[:, perm k]) / s_k
+      u.src = G + c0;
+      u.src_rs = q;
+      u.src_cs = 1;
+      u.row_map = dP.as<int>() + soff[a];
+      u.conj = 1;
+      u.scale = dS.as<double>() + soff[a];
+      u.scale_mode = 4;
+      u.dst = T.ptr(bi);
+      u.rows = p;
+      u.cols = b.cols;
+      u.dst_rs = b.cols;
+      u.dst_cs = 1;
+      scatter.tasks.push_back(u);
+      c0 += b.cols;
+    }
+    tasks.push_back({G, dV.as<cplx>() + voff[a], dS.as<double>() + soff[a], dP.as<int>() + soff[a], q, p});
+  }
+  gather.finalize(stream_);
+  gather.launch(stream_);
+  DevBuf dt = upload(tasks, stream_);
+  launch_jacobi_svd(dt.as<SvdTask>(), (int)tasks.size(), mq, 60, 1e-15, dstatus_, stream_);
+  scatter.finalize(stream_);
+  scatter.launch(stream_);
+  TDVP_CUDA(cudaStreamSynchronize(stream_));
 }
 
 void Engine::heff_apply_bond(const cplx* in, cplx* out) {
@@ -885,7 +1193,7 @@ int Engine::expm(HeffPlan& H, cplx* x, double tau) {
 // ---------------------------------------------------------------------------
 
 double Engine::split(BTensor& theta, const BondSpace& bl, const BondSpace& br, long long chi_max, double eps,
-                     bool absorb_right, BondSpace& bm, BTensor& X, BTensor& Y) {
+                     bool absorb_right, BondSpace& bm, BTensor& X, BTensor& Y, double* s_ent) {
   const Model& M = model_;
   // group blocks by the coupled label c = (n_a + n_s1, t_c)
   struct Grp {
@@ -1079,6 +1387,15 @@ double Engine::split(BTensor& theta, const BondSpace& bl, const BondSpace& br, l
   }
   scatter.finalize(stream_);
   scatter.launch(stream_);
+  if (s_ent) {  // entropy of the new bond from the kept, renormalised singular values
+    std::vector<TruncSector> ks;
+    for (int g = 0; g < ng; ++g)
+      if (kept[g] > 0) ks.push_back({Sp + soff[g], kept[g], M.mult_dim(groups[g].t)});
+    DevBuf dks = upload(ks, stream_), dS(sizeof(double), stream_);
+    launch_entropy_sv(dks.as<TruncSector>(), (int)ks.size(), gsc, dS.as<double>(), stream_);
+    TDVP_CUDA(cudaMemcpyAsync(s_ent, dS.p, sizeof(double), cudaMemcpyDeviceToHost, stream_));
+    TDVP_CUDA(cudaStreamSynchronize(stream_));
+  }
   long long chi = 0;
   for (auto& s : bm.s) chi += (long long)s.d * M.mult_dim(s.t);
   stats_.chi_max_seen = std::max(stats_.chi_max_seen, chi);
@@ -1089,60 +1406,121 @@ double Engine::split(BTensor& theta, const BondSpace& bl, const BondSpace& br, l
 // the time step (Sec. S2.2)
 // ---------------------------------------------------------------------------
 
+// One two-site update at bond (i, i+1) of the second-order sweep (Sec. S2.2):
+// theta = X_i Y_{i+1}, theta <- exp(-i tau H_eff) theta, SVD split with truncation,
+// environment update, and (when backward) the one-site backward evolution of the new
+// centre by +tau.  left_to_right: centre i -> i+1, otherwise i+1 -> i.
+void Engine::bond_update(int i, bool left_to_right, double tau, long long chi_max, double eps, bool backward,
+                         double* s_ent) {
+  auto tp = std::chrono::steady_clock::now();
+  auto mark = [&](int ph) {
+    if (!profile_) return;
+    cudaStreamSynchronize(stream_);
+    auto now = std::chrono::steady_clock::now();
+    stats_.phase[ph] += std::chrono::duration<double>(now - tp).count();
+    tp = now;
+  };
+  BTensor theta;
+  form_theta(site_[i], site_[i + 1], theta, bonds_[i], bonds_[i + 1], bonds_[i + 2]);
+  mark(0);
+  {
+    HeffPlan H;
+    plan_heff2(H, Lenv_[i], Renv_[i + 2], theta, bonds_[i], bonds_[i + 2]);
+    mark(1);
+    expm(H, theta.data(), tau);
+    mark(2);
+  }
+  BondSpace bm;
+  BTensor X, Y;
+  double disc = split(theta, bonds_[i], bonds_[i + 2], chi_max, eps, left_to_right, bm, X, Y, s_ent);
+  stats_.max_discarded = std::max(stats_.max_discarded, disc);
+  bonds_[i + 1] = bm;
+  site_[i] = std::move(X);
+  site_[i + 1] = std::move(Y);
+  mark(3);
+  if (left_to_right) {
+    update_left_env(Lenv_[i], site_[i], Lenv_[i + 1], bonds_[i], bonds_[i + 1]);
+    mark(4);
+    center_ = i + 1;
+    if (backward) {
+      HeffPlan H1;
+      plan_heff1(H1, Lenv_[i + 1], Renv_[i + 2], site_[i + 1], bonds_[i + 1], bonds_[i + 2]);
+      mark(1);
+      expm(H1, site_[i + 1].data(), -tau);
+      mark(5);
+    }
+  } else {
+    update_right_env(Renv_[i + 2], site_[i + 1], Renv_[i + 1], bonds_[i + 1], bonds_[i + 2]);
+    mark(4);
+    center_ = i;
+    if (backward) {
+      HeffPlan H1;
+      plan_heff1(H1, Lenv_[i], Renv_[i + 1], site_[i], bonds_[i], bonds_[i + 1]);
+      mark(1);
+      expm(H1, site_[i].data(), -tau);
+      mark(5);
+    }
+  }
+}
+
 void Engine::step(double dt, long long chi_max, double eps) {
   if (bond_only_) throw Error(-2, "a bond problem has no chain to evolve");
   if (!(dt > 0) || chi_max < 1 || !(eps >= 0)) throw Error(-1, "invalid step arguments");
+  if (center_ != 0) throw Error(-2, "a full time step starts with the orthogonality centre on site 0");
   chain_heff_.reset();
   auto t0 = std::chrono::steady_clock::now();
   const double tau = dt / 2;
   const int L = L_;
-  for (int i = 0; i + 1 < L; ++i) {
-    BTensor theta;
-    form_theta(site_[i], site_[i + 1], theta, bonds_[i], bonds_[i + 1], bonds_[i + 2]);
-    {
-      HeffPlan H;
-      plan_heff2(H, Lenv_[i], Renv_[i + 2], theta, bonds_[i], bonds_[i + 2]);
-      expm(H, theta.data(), tau);
-    }
-    BondSpace bm;
-    BTensor X, Y;
-    double disc = split(theta, bonds_[i], bonds_[i + 2], chi_max, eps, true, bm, X, Y);
-    stats_.max_discarded = std::max(stats_.max_discarded, disc);
-    bonds_[i + 1] = bm;
-    site_[i] = std::move(X);
-    site_[i + 1] = std::move(Y);
-    update_left_env(Lenv_[i], site_[i], Lenv_[i + 1], bonds_[i], bonds_[i + 1]);
-    if (i + 2 < L) {
-      HeffPlan H1;
-      plan_heff1(H1, Lenv_[i + 1], Renv_[i + 2], site_[i + 1], bonds_[i + 1], bonds_[i + 2]);
-      expm(H1, site_[i + 1].data(), -tau);
-    }
-  }
-  for (int i = L - 2; i >= 0; --i) {
-    BTensor theta;
-    form_theta(site_[i], site_[i + 1], theta, bonds_[i], bonds_[i + 1], bonds_[i + 2]);
-    {
-      HeffPlan H;
-      plan_heff2(H, Lenv_[i], Renv_[i + 2], theta, bonds_[i], bonds_[i + 2]);
-      expm(H, theta.data(), tau);
-    }
-    BondSpace bm;
-    BTensor X, Y;
-    double disc = split(theta, bonds_[i], bonds_[i + 2], chi_max, eps, false, bm, X, Y);
-    stats_.max_discarded = std::max(stats_.max_discarded, disc);
-    bonds_[i + 1] = bm;
-    site_[i] = std::move(X);
-    site_[i + 1] = std::move(Y);
-    update_right_env(Renv_[i + 2], site_[i + 1], Renv_[i + 1], bonds_[i + 1], bonds_[i + 2]);
-    if (i > 0) {
-      HeffPlan H1;
-      plan_heff1(H1, Lenv_[i], Renv_[i + 1], site_[i], bonds_[i], bonds_[i + 1]);
-      expm(H1, site_[i].data(), -tau);
-    }
-  }
+  for (int i = 0; i + 1 < L; ++i) bond_update(i, true, tau, chi_max, eps, i + 2 < L, nullptr);
+  for (int i = L - 2; i >= 0; --i) bond_update(i, false, tau, chi_max, eps, i > 0, nullptr);
   TDVP_CUDA(cudaStreamSynchronize(stream_));
   check_status();
   stats_.seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  stats_.steps += 1;
+}
+
+void Engine::single_bond(int i, int direction, double dt, long long chi_max, double eps, double* s_ent) {
+  if (bond_only_) throw Error(-2, "a bond problem has no chain");
+  if (i < 0 || i + 1 >= L_ || !(dt > 0) || chi_max < 1 || !(eps >= 0)) throw Error(-1, "invalid bond update");
+  const bool lr = direction == 0;
+  if ((lr && center_ != i) || (!lr && center_ != i + 1))
+    throw Error(-2, "the orthogonality centre is not on the bond's source site");
+  chain_heff_.reset();
+  auto t0 = std::chrono::steady_clock::now();
+  bond_update(i, lr, dt / 2, chi_max, eps, true, s_ent);
+  TDVP_CUDA(cudaStreamSynchronize(stream_));
+  check_status();
+  stats_.seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// <n>, <S^z>, <docc> of the orthogonality-centre site (left part left-canonical,
+// right part right-canonical): sum over centre blocks of O_s Tr(M^H M).
+void Engine::measure_center(int* site, double* n, double* sz, double* docc) {
+  if (bond_only_) throw Error(-2, "a bond problem has no chain");
+  const Model& M = model_;
+  const BTensor& T = site_[center_];
+  const int NS = 5;
+  std::vector<DotTask> dts;
+  for (int bi = 0; bi < (int)T.blocks.size(); ++bi) {
+    const Block& b = T.blocks[bi];
+    int s = b.key[1];
+    double w[NS] = {M.occ_n[s], M.occ_up[s], M.occ_dn[s], M.occ_d[s], 1.0};
+    for (int k = 0; k < NS; ++k)
+      if (w[k] != 0.0) dts.push_back({T.ptr(bi), T.ptr(bi), b.rows, b.cols, b.cols, b.cols, k, w[k]});
+  }
+  DevBuf ddt = upload(dts, stream_);
+  DevBuf dpart(std::max<size_t>(dts.size(), 1) * sizeof(double), stream_), dout(NS * sizeof(double), stream_);
+  launch_wdot(ddt.as<DotTask>(), (int)dts.size(), dpart.as<double>(), dout.as<double>(), NS, stream_);
+  double r[NS];
+  TDVP_CUDA(cudaMemcpyAsync(r, dout.p, NS * sizeof(double), cudaMemcpyDeviceToHost, stream_));
+  TDVP_CUDA(cudaStreamSynchronize(stream_));
+  const double nrm = r[4] > 0 ? r[4] : 1.0;
+  const double nup = r[1] / nrm, ndn = r[2] / nrm, dd = r[3] / nrm;
+  const double n_up = nup, n_dn = 1.0 - ndn;
+  if (site) *site = center_;
+  if (n) *n = n_up + n_dn;
+  if (sz) *sz = 0.5 * (n_up - n_dn);
+  if (docc) *docc = nup - dd;
 }
 
 // ---------------------------------------------------------------------------
@@ -1152,6 +1530,7 @@ void Engine::step(double dt, long long chi_max, double eps) {
 void Engine::measure(double* n_out, double* sz_out, double* docc_out, double* s_ent, double* energy,
                      double* n_up_out) {
   if (bond_only_) throw Error(-2, "a bond problem has no chain to measure");
+  if (center_ != 0) throw Error(-2, "tdvp_measure needs the orthogonality centre on site 0 (after tdvp_step)");
   const Model& M = model_;
   const int L = L_;
   // Omega_0 = 1 on the single sector of the left edge

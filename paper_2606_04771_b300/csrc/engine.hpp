@@ -135,6 +135,10 @@ struct StepStats {
   long long heff_flops = 0, env_flops = 0, matvecs = 0;
   int max_krylov = 0;
   long long chi_max_seen = 0;
+  long long steps = 0;
+  // wall seconds per phase when TDVP_PROFILE_PHASES=1: theta formation, planning,
+  // two-site Krylov, SVD split, environment update, one-site Krylov
+  double phase[6] = {0, 0, 0, 0, 0, 0};
 };
 
 class Engine {
@@ -144,6 +148,11 @@ class Engine {
 
   // chain evolution
   void step(double dt, long long chi_max, double eps);
+  // one bond update of the sweep at bond (i, i+1); direction 0: left to right (centre on i),
+  // 1: right to left (centre on i+1); s_ent (nullable) receives the new bond's entropy
+  void single_bond(int i, int direction, double dt, long long chi_max, double eps, double* s_ent);
+  void measure_center(int* site, double* n, double* sz, double* docc);
+  int center() const { return center_; }
   void measure(double* n, double* sz, double* docc, double* s_ent, double* energy, double* n_up = nullptr);
   const StepStats& stats() const { return stats_; }
   int L() const { return L_; }
@@ -153,6 +162,9 @@ class Engine {
   cudaStream_t stream() const { return stream_; }
 
   // synthetic single-bond problem (environments and theta given by the caller)
+  // synthetic right-canonical random state of L sites with bond dimension about chi_target
+  static Engine* random_state(int L, double J, double U, bool su2, long long chi_target, unsigned long long seed,
+                              int center, const Opts& o);
   static Engine* bond_problem(bool su2, double J, double U, const std::vector<Sector>& left,
                               const std::vector<Sector>& right, const Opts& o);
   bool bond_only() const { return bond_only_; }
@@ -174,6 +186,8 @@ class Engine {
   void build_lenv_layout(BTensor& t, const BondSpace& bra, const BondSpace& ket) const;
   void build_renv_layout(BTensor& t, const BondSpace& ket, const BondSpace& bra) const;
   void alloc(BTensor& t, bool zero);
+  void orthonormalize_rows(BTensor& T, const BondSpace& l, const BondSpace& r);
+  void orthonormalize_cols(BTensor& T, const BondSpace& l, const BondSpace& r);
 
   void plan_heff2(HeffPlan& p, const BTensor& Lenv, const BTensor& Renv, const BTensor& theta,
                   const BondSpace& bl, const BondSpace& br);
@@ -187,7 +201,9 @@ class Engine {
                   const BondSpace& br);
   // split theta at bond (i,i+1); absorb_right: S goes to Y (left-to-right sweep)
   double split(BTensor& theta, const BondSpace& bl, const BondSpace& br, long long chi_max, double eps,
-               bool absorb_right, BondSpace& bm, BTensor& X, BTensor& Y);
+               bool absorb_right, BondSpace& bm, BTensor& X, BTensor& Y, double* s_ent = nullptr);
+  void bond_update(int i, bool left_to_right, double tau, long long chi_max, double eps, bool backward,
+                   double* s_ent);
   int expm(HeffPlan& H, cplx* x, double tau);  // returns the Krylov dimension used
 
   int L_ = 0;
@@ -202,6 +218,8 @@ class Engine {
   BTensor theta_;  // bond-problem theta layout
   std::unique_ptr<HeffPlan> bp_heff_, chain_heff_;
   bool bond_only_ = false;
+  bool profile_ = false;
+  int center_ = 0;  // orthogonality centre
   // Krylov workspace
   DevBuf kv_, kw_, kpart_, kh1_, kh2_, knrm_, kstate_;
   long long kcap_ = 0;

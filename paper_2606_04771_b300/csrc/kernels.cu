@@ -671,6 +671,57 @@ __global__ void entropy_kernel(const TruncSector* __restrict__ secs, int nsec, d
   if (threadIdx.x == 0) *out = sb[0];
 }
 
+// Counter-based complex normal numbers: element i uses SplitMix64(seed, 2i) and
+// SplitMix64(seed, 2i+1) as two uniforms for a Box-Muller pair (synthetic states).
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+__global__ void fill_normal_kernel(cplx* __restrict__ p, long long n, unsigned long long seed, long long offset) {
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
+    const unsigned long long c = (unsigned long long)(i + offset);
+    const double u1 = ((splitmix64(seed ^ (2 * c)) >> 11) + 1.0) * (1.0 / 9007199254740993.0);
+    const double u2 = (splitmix64(seed ^ (2 * c + 1)) >> 11) * (1.0 / 9007199254740992.0);
+    const double r = sqrt(-2.0 * log(u1));
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);
+    p[i] = {r * cs, r * sn};
+  }
+}
+
+void launch_fill_normal(cplx* p, long long n, unsigned long long seed, long long offset, cudaStream_t s) {
+  if (n <= 0) return;
+  fill_normal_kernel<<<blas_grid(n), 256, 0, s>>>(p, n, seed, offset);
+}
+
+// S = -sum lam ln(lam / mult) with lam = (g s)^2 from kept singular values s
+__global__ void entropy_sv_kernel(const TruncSector* __restrict__ secs, int nsec, const double* g, double* out) {
+  const double gg = g ? *g : 1.0;
+  double acc = 0.0;
+  for (int s = threadIdx.x; s < nsec; s += blockDim.x) {
+    for (int i = 0; i < secs[s].r; ++i) {
+      double x = gg * secs[s].sv[i];
+      double lam = x * x;
+      if (lam > 1e-300) acc -= lam * log(lam / secs[s].mult);
+    }
+  }
+  __shared__ double sb[256];
+  sb[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sb[threadIdx.x] += sb[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sb[0];
+}
+
+void launch_entropy_sv(const TruncSector* secs, int nsec, const double* g, double* out, cudaStream_t s) {
+  entropy_sv_kernel<<<1, 256, 0, s>>>(secs, nsec, g, out);
+}
+
 void launch_entropy(const TruncSector* secs, int nsec, double* out, cudaStream_t s) {
   entropy_kernel<<<1, 256, 0, s>>>(secs, nsec, out);
 }

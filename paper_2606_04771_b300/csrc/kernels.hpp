@@ -55,5 +55,7 @@ void launch_truncate(const TruncSector* secs, int nsec, const int* offs, int n, 
                      int* owner, int* order, int* kept, double* stats, cudaStream_t s);
 void launch_wdot(const DotTask* tasks, int ntasks, double* partial, double* out, int nslots, cudaStream_t s);
 void launch_entropy(const TruncSector* secs, int nsec, double* out, cudaStream_t s);
+void launch_entropy_sv(const TruncSector* secs, int nsec, const double* g, double* out, cudaStream_t s);
+void launch_fill_normal(cplx* p, long long n, unsigned long long seed, long long offset, cudaStream_t s);
 
 }  // namespace tdvp
