@@ -414,7 +414,8 @@ void Engine::orthonormalize_cols(BTensor& T, const BondSpace& l, const BondSpace
   gather.finalize(stream_);
   gather.launch(stream_);
   DevBuf dt = upload(tasks, stream_);
-  launch_jacobi_svd(dt.as<SvdTask>(), (int)tasks.size(), mq, 60, 1e-15, dstatus_, stream_);
+  if (run_blocked_jacobi(dt.as<SvdTask>(), tasks, 40, 1e-14, dstatus_, stream_) < 0)
+    launch_jacobi_svd(dt.as<SvdTask>(), (int)tasks.size(), mq, 60, 1e-15, dstatus_, stream_);
   scatter.finalize(stream_);
   scatter.launch(stream_);
   TDVP_CUDA(cudaStreamSynchronize(stream_));
@@ -485,7 +486,8 @@ void Engine::orthonormalize_rows(BTensor& T, const BondSpace& l, const BondSpace
   gather.finalize(stream_);
   gather.launch(stream_);
   DevBuf dt = upload(tasks, stream_);
-  launch_jacobi_svd(dt.as<SvdTask>(), (int)tasks.size(), mq, 60, 1e-15, dstatus_, stream_);
+  if (run_blocked_jacobi(dt.as<SvdTask>(), tasks, 40, 1e-14, dstatus_, stream_) < 0)
+    launch_jacobi_svd(dt.as<SvdTask>(), (int)tasks.size(), mq, 60, 1e-15, dstatus_, stream_);
   scatter.finalize(stream_);
   scatter.launch(stream_);
   TDVP_CUDA(cudaStreamSynchronize(stream_));
@@ -1291,7 +1293,8 @@ double Engine::split(BTensor& theta, const BondSpace& bl, const BondSpace& br, l
     ts[g] = {Sp + soff[g], Q, M.mult_dim(groups[g].t)};
   }
   DevBuf dst = upload(st, stream_);
-  launch_jacobi_svd(dst.as<SvdTask>(), ng, maxq, 60, 1e-15, dstatus_, stream_);
+  if (run_blocked_jacobi(dst.as<SvdTask>(), st, 40, 1e-14, dstatus_, stream_) < 0)
+    launch_jacobi_svd(dst.as<SvdTask>(), ng, maxq, 60, 1e-15, dstatus_, stream_);
   // truncation
   DevBuf dts = upload(ts, stream_);
   DevBuf doffs = upload(soff, stream_);
@@ -1650,7 +1653,8 @@ void Engine::measure(double* n_out, double* sz_out, double* docc_out, double* s_
         ts[b] = {dS.as<double>() + so[b], br.s[b].d, M.mult_dim(br.s[b].t)};
       }
       DevBuf dst = upload(st, stream_), dts2 = upload(ts, stream_);
-      launch_jacobi_svd(dst.as<SvdTask>(), ns, mq, 60, 1e-15, dstatus_, stream_);
+      if (run_blocked_jacobi(dst.as<SvdTask>(), st, 40, 1e-14, dstatus_, stream_) < 0)
+        launch_jacobi_svd(dst.as<SvdTask>(), ns, mq, 60, 1e-15, dstatus_, stream_);
       launch_entropy(dts2.as<TruncSector>(), ns, dent.as<double>() + i, stream_);
       TDVP_CUDA(cudaStreamSynchronize(stream_));
     }

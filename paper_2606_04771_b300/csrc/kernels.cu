@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <vector>
 
 #include "common.hpp"
 #include "kernels.hpp"
@@ -518,6 +519,189 @@ __global__ void __launch_bounds__(SVD_THREADS) jacobi_svd_kernel(const SvdTask* 
     t.perm[rank] = j;
     t.sv[rank] = vj < 0.0 ? 0.0 : vj;
   }
+}
+
+// ---------------------------------------------------------------------------
+// K6 (blocked): one-sided Jacobi in rounds over column blocks, many CTAs per matrix
+//
+// The Q columns of every problem are cut into blocks of bw columns (the block count
+// padded to even).  One launch performs one round of the block tournament for every
+// problem: each CTA takes one pair of blocks, copies their columns of G and V into
+// shared memory, runs one cyclic pass over all column pairs of the 2 bw columns
+// (FP64 complex Jacobi rotations, as in jacobi_svd_kernel), and writes them back.  A
+// sweep is nb - 1 rounds; a problem whose previous sweep made no rotation is skipped.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void tourney(int r, int k, int n, int& i, int& j) {
+  const int m = n - 1;
+  if (k == 0) {
+    i = 0;
+    j = 1 + r % m;
+  } else {
+    i = 1 + (r + k) % m;
+    j = 1 + (r - k + m) % m;
+  }
+  if (i > j) {
+    int t = i;
+    i = j;
+    j = t;
+  }
+}
+
+__global__ void __launch_bounds__(256) bjacobi_round_kernel(const SvdTask* __restrict__ tasks,
+                                                            const int2* __restrict__ work, int round, int bw,
+                                                            double tol, int* __restrict__ flag_now,
+                                                            const int* __restrict__ flag_prev) {
+  const int2 wk = work[blockIdx.x];
+  const SvdTask t = tasks[wk.x];
+  if (flag_prev && flag_prev[wk.x] == 0) return;  // converged in the previous sweep
+  const int nb0 = (t.q + bw - 1) / bw;
+  const int nb = nb0 + (nb0 & 1);
+  if (nb < 2 || round >= nb - 1) return;
+  int I, Jb;
+  tourney(round, wk.y, nb, I, Jb);
+  const int p = t.p, q = t.q;
+  extern __shared__ cplx sm[];
+  const int nc = 2 * bw;
+  cplx* Gs = sm;                  // nc columns x p rows
+  cplx* Vs = sm + (size_t)nc * p;  // nc columns x q rows
+  int col[64];
+  int ncol = 0;
+  for (int c = 0; c < bw; ++c)
+    if (I * bw + c < q) col[ncol++] = I * bw + c;
+  for (int c = 0; c < bw; ++c)
+    if (Jb * bw + c < q) col[ncol++] = Jb * bw + c;
+  if (ncol < 2) return;
+  for (int cc = 0; cc < ncol; ++cc) {
+    const cplx* g = t.g + (long long)col[cc] * p;
+    const cplx* v = t.v + (long long)col[cc] * q;
+    for (int r = threadIdx.x; r < p; r += blockDim.x) Gs[(size_t)cc * p + r] = g[r];
+    for (int r = threadIdx.x; r < q; r += blockDim.x) Vs[(size_t)cc * q + r] = v[r];
+  }
+  __shared__ int rotated;
+  if (threadIdx.x == 0) rotated = 0;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int nn = ncol + (ncol & 1);
+  for (int r = 0; r < nn - 1; ++r) {
+    for (int k = warp; k < nn / 2; k += nwarp) {
+      int i, j;
+      tourney(r, k, nn, i, j);
+      if (j >= ncol) continue;
+      double a, b;
+      cplx c;
+      col_pair(Gs, p, i, j, a, b, c);
+      double ac = sqrt(c.x * c.x + c.y * c.y);
+      if (ac == 0.0 || ac <= tol * sqrt(a * b)) continue;
+      double zeta = (b - a) / (2.0 * ac);
+      double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+      double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
+      cplx e = {c.x / ac, c.y / ac};
+      rotate_cols(Gs, p, p, i, j, cs, sn, e);
+      rotate_cols(Vs, q, q, i, j, cs, sn, e);
+      if ((threadIdx.x & 31) == 0) rotated = 1;
+    }
+    __syncthreads();
+  }
+  for (int cc = 0; cc < ncol; ++cc) {
+    cplx* g = t.g + (long long)col[cc] * p;
+    cplx* v = t.v + (long long)col[cc] * q;
+    for (int r = threadIdx.x; r < p; r += blockDim.x) g[r] = Gs[(size_t)cc * p + r];
+    for (int r = threadIdx.x; r < q; r += blockDim.x) v[r] = Vs[(size_t)cc * q + r];
+  }
+  if (threadIdx.x == 0 && rotated) atomicOr(&flag_now[wk.x], 1);
+}
+
+// V = identity for every problem
+__global__ void svd_init_v_kernel(const SvdTask* __restrict__ tasks) {
+  const SvdTask t = tasks[blockIdx.x];
+  for (int e = threadIdx.x; e < t.q * t.q; e += blockDim.x) t.v[e] = {(e % t.q) == (e / t.q) ? 1.0 : 0.0, 0.0};
+}
+
+// singular values = column norms, sorted descending with perm (NaN last)
+__global__ void __launch_bounds__(256) svd_finish_kernel(const SvdTask* __restrict__ tasks) {
+  const SvdTask t = tasks[blockIdx.x];
+  const int p = t.p, q = t.q;
+  const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int j = warp; j < q; j += nwarp) {
+    double a, b;
+    cplx c;
+    col_pair(t.g, p, j, j, a, b, c);
+    if ((threadIdx.x & 31) == 0) t.sv[j] = sqrt(a);
+  }
+  __syncthreads();
+  extern __shared__ double sb[];
+  for (int j = threadIdx.x; j < q; j += blockDim.x) {
+    double v = t.sv[j];
+    sb[j] = (v == v) ? v : -1.0;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < q; j += blockDim.x) {
+    double vj = sb[j];
+    int rank = 0;
+    for (int i = 0; i < q; ++i) {
+      double vi = sb[i];
+      rank += (vi > vj) || (vi == vj && i < j);
+    }
+    t.perm[rank] = j;
+    t.sv[rank] = vj < 0.0 ? 0.0 : vj;
+  }
+}
+
+// Blocked Jacobi driver: returns the number of sweeps used (host loop, one sync per sweep).
+int run_blocked_jacobi(const SvdTask* d_tasks, const std::vector<SvdTask>& h_tasks, int max_sweeps, double tol,
+                       int* status, cudaStream_t s) {
+  const int nt = (int)h_tasks.size();
+  if (nt == 0) return 0;
+  int pmax = 1, qmax = 1;
+  for (auto& t : h_tasks) {
+    pmax = max(pmax, t.p);
+    qmax = max(qmax, t.q);
+  }
+  // widest block (<= 32 columns) whose pair of column copies fits in shared memory
+  int bw = 32;
+  while (bw > 1 && (size_t)2 * bw * (pmax + qmax) * sizeof(cplx) > 200 * 1024) bw >>= 1;
+  if ((size_t)2 * bw * (pmax + qmax) * sizeof(cplx) > 200 * 1024) return -1;  // caller falls back
+  const size_t smem = (size_t)2 * bw * (pmax + qmax) * sizeof(cplx);
+  cudaFuncSetAttribute(bjacobi_round_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  std::vector<int2> work;
+  int max_rounds = 0;
+  for (int i = 0; i < nt; ++i) {
+    int nb0 = (h_tasks[i].q + bw - 1) / bw, nb = nb0 + (nb0 & 1);
+    for (int k = 0; k < nb / 2; ++k) work.push_back(make_int2(i, k));
+    max_rounds = max(max_rounds, nb - 1);
+  }
+  int2* d_work = nullptr;
+  int* flags = nullptr;
+  cudaMallocAsync(&d_work, work.size() * sizeof(int2), s);
+  cudaMallocAsync(&flags, 2 * nt * sizeof(int), s);
+  cudaMemcpyAsync(d_work, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+  svd_init_v_kernel<<<nt, 256, 0, s>>>(d_tasks);
+  std::vector<int> hf(nt);
+  int sweep = 0, *prev = nullptr, *now = flags;
+  for (; sweep < max_sweeps; ++sweep) {
+    cudaMemsetAsync(now, 0, nt * sizeof(int), s);
+    for (int r = 0; r < max_rounds; ++r)
+      bjacobi_round_kernel<<<(int)work.size(), 256, smem, s>>>(d_tasks, d_work, r, bw, tol, now, prev);
+    cudaMemcpyAsync(hf.data(), now, nt * sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    bool any = false;
+    for (int v : hf) any |= v != 0;
+    if (!any) break;
+    prev = now;
+    now = (now == flags) ? flags + nt : flags;
+  }
+  if (sweep >= max_sweeps) {
+    int one = 1;
+    cudaMemcpyAsync(status, &one, sizeof(int), cudaMemcpyHostToDevice, s);  // reported by the caller's check
+    cudaStreamSynchronize(s);
+  }
+  size_t fs = (size_t)qmax * sizeof(double);
+  if (fs > 48 * 1024) cudaFuncSetAttribute(svd_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fs);
+  svd_finish_kernel<<<nt, 256, fs, s>>>(d_tasks);
+  cudaFreeAsync(d_work, s);
+  cudaFreeAsync(flags, s);
+  return sweep;
 }
 
 void launch_jacobi_svd(const SvdTask* tasks, int ntasks, int max_q, int max_sweeps, double tol, int* status,

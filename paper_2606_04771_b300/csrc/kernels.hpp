@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "common.hpp"
 
 namespace tdvp {
@@ -51,6 +53,10 @@ void launch_krylov_step(KrylovState* st, const cplx* h1, const cplx* nrm2, doubl
 
 void launch_jacobi_svd(const SvdTask* tasks, int ntasks, int max_q, int max_sweeps, double tol, int* status,
                        cudaStream_t s);
+// blocked multi-CTA Jacobi (same result layout as launch_jacobi_svd); returns the sweeps
+// used, or -1 when the column blocks do not fit in shared memory (use launch_jacobi_svd)
+int run_blocked_jacobi(const SvdTask* d_tasks, const std::vector<SvdTask>& h_tasks, int max_sweeps, double tol,
+                       int* status, cudaStream_t s);
 void launch_truncate(const TruncSector* secs, int nsec, const int* offs, int n, double eps, long long chi_max,
                      int* owner, int* order, int* kept, double* stats, cudaStream_t s);
 void launch_wdot(const DotTask* tasks, int ntasks, double* partial, double* out, int nslots, cudaStream_t s);
