@@ -98,6 +98,28 @@ struct TruncSector {
   int mult;          // 2S+1 (SU(2)) or 1
 };
 
+// FP32 Jacobi preconditioner: g is p x q column-major complex64 (p >= q), v the
+// q x q column-major accumulated right rotations
+struct Svd32Task {
+  float2* g;
+  float2* v;
+  int p, q;
+};
+
+struct BasisTask {  // x[i][kk] = g[i, perm[kk]] / sv[kk] (or / sv[kk]^2); g column-major, rows x .
+  const cplx* g;
+  const int* perm;
+  const double* sv;
+  cplx* x;
+  int rows, k;
+  int pow2;
+};
+
+struct NsTask {  // g <- 1.5 I - 0.5 g (k x k)
+  cplx* g;
+  int k;
+};
+
 // Block-weighted inner product contribution: sum_ij weight * conj(x[i,j]) * y[i,j]
 struct DotTask {
   const cplx* x;

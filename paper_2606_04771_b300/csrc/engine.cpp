@@ -1196,6 +1196,11 @@ int Engine::expm(HeffPlan& H, cplx* x, double tau) {
 
 double Engine::split(BTensor& theta, const BondSpace& bl, const BondSpace& br, long long chi_max, double eps,
                      bool absorb_right, BondSpace& bm, BTensor& X, BTensor& Y, double* s_ent) {
+  if (gemm_kind_ >= 0) {
+    bool ok = false;
+    double r = split_mixed(theta, bl, br, chi_max, eps, absorb_right, bm, X, Y, s_ent, ok);
+    if (ok) return r;
+  }
   const Model& M = model_;
   // group blocks by the coupled label c = (n_a + n_s1, t_c)
   struct Grp {
@@ -1401,6 +1406,434 @@ double Engine::split(BTensor& theta, const BondSpace& bl, const BondSpace& br, l
   }
   long long chi = 0;
   for (auto& s : bm.s) chi += (long long)s.d * M.mult_dim(s.t);
+  stats_.chi_max_seen = std::max(stats_.chi_max_seen, chi);
+  return hstats[1] / (hstats[0] > 0 ? hstats[0] : 1.0);
+}
+
+// ---------------------------------------------------------------------------
+// Mixed-precision split (tensor-core precision modes).  The per-sector SVD of
+// Sec. S2.4 stays an FP64 SVD; FP32 only supplies a preconditioner.  For each
+// sector the working copy W (theta, or theta^H when theta is wide) is copied to
+// complex64 and an FP32 blocked Jacobi accumulates its right rotations V32; then,
+// in FP64, G = W V32 is formed and a short FP64 Jacobi (no V) makes its columns
+// orthogonal -- G = U S with S the FP64 singular values of W up to the O(1e-7)
+// departure of V32 from unitarity, far below any truncation threshold.  The FP32
+// stage leaves off-diagonals at the FP32 level, so by the quadratic convergence of
+// cyclic Jacobi the FP64 stage ends after two sweeps instead of the ~10 a cold
+// start needs.  The basis the sweep keeps (left for left to right, right for right
+// to left) is G/S when it is W's column space, otherwise W^H G / S^2
+// re-orthonormalised by two Newton-Schulz steps X <- X (3 I - X^H X) / 2 (the
+// overlaps it starts from are O(1e-7)); the other factor is the exact FP64
+// projection of theta onto that basis.  Returns false in ok when the columns do not
+// fit the blocked kernels (the caller then uses the FP64 split).
+// ---------------------------------------------------------------------------
+
+double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace& br, long long chi_max, double eps,
+                           bool absorb_right, BondSpace& bm, BTensor& X, BTensor& Y, double* s_ent, bool& ok) {
+  const Model& M = model_;
+  ok = false;
+  struct Grp {
+    int n, t;
+    std::vector<std::pair<int, int>> rows, cols;
+    std::map<std::pair<int, int>, int> roff, coff;
+    int p = 0, q = 0;
+  };
+  std::map<std::pair<int, int>, int> gidx;
+  std::vector<Grp> groups;
+  for (const Block& b : theta.blocks) {
+    int a = b.key[0], s1 = b.key[1], tc = b.key[2], s2 = b.key[3], bb = b.key[4];
+    auto key = std::make_pair(bl.s[a].n + M.site[s1].n, tc);
+    auto it = gidx.find(key);
+    int g;
+    if (it == gidx.end()) {
+      g = (int)groups.size();
+      gidx[key] = g;
+      groups.push_back(Grp());
+      groups.back().n = key.first;
+      groups.back().t = tc;
+    } else {
+      g = it->second;
+    }
+    Grp& G = groups[g];
+    if (!G.roff.count({a, s1})) {
+      G.roff[{a, s1}] = G.p;
+      G.rows.push_back({a, s1});
+      G.p += bl.s[a].d;
+    }
+    if (!G.coff.count({s2, bb})) {
+      G.coff[{s2, bb}] = G.q;
+      G.cols.push_back({s2, bb});
+      G.q += br.s[bb].d;
+    }
+  }
+  const int ng = (int)groups.size();
+  auto bigP = [](const Grp& G) { return std::max(G.p, G.q); };
+  auto smallQ = [](const Grp& G) { return std::min(G.p, G.q); };
+  // the kept basis is W's column space (U of W) when the sweep needs the side W's rows index
+  auto from_g = [&](const Grp& G) { return absorb_right == (G.p >= G.q); };
+  auto xrows = [&](const Grp& G) { return absorb_right ? G.p : G.q; };
+  std::vector<long long> toff(ng), voff(ng);
+  std::vector<int> soff(ng);
+  long long ttot = 0, vtot = 0;
+  int stot = 0, maxq = 1;
+  for (int g = 0; g < ng; ++g) {
+    toff[g] = ttot;
+    ttot += (long long)groups[g].p * groups[g].q;
+    voff[g] = vtot;
+    vtot += (long long)smallQ(groups[g]) * smallQ(groups[g]);
+    soff[g] = stot;
+    stot += smallQ(groups[g]);
+    maxq = std::max(maxq, smallQ(groups[g]));
+  }
+  const long long tt1 = std::max<long long>(ttot, 1), vt1 = std::max<long long>(vtot, 1);
+  DevBuf dT(tt1 * sizeof(cplx), stream_), dW(tt1 * sizeof(cplx), stream_), dG(tt1 * sizeof(cplx), stream_);
+  DevBuf dW32(tt1 * sizeof(float2), stream_), dV32(vt1 * sizeof(float2), stream_), dV(vt1 * sizeof(cplx), stream_);
+  DevBuf dS(std::max(stot, 1) * sizeof(double), stream_), dP(std::max(stot, 1) * sizeof(int), stream_);
+  cplx *T64 = dT.as<cplx>(), *W64 = dW.as<cplx>(), *G64 = dG.as<cplx>(), *V64 = dV.as<cplx>();
+  float2 *W32 = dW32.as<float2>(), *V32 = dV32.as<float2>();
+  double* Sp = dS.as<double>();
+  int* Pp = dP.as<int>();
+  // theta row-major p x q (for the projections) and W column-major P x Q
+  CopyPlan gather;
+  for (const Block& b : theta.blocks) {
+    int a = b.key[0], s1 = b.key[1], s2 = b.key[3], bb = b.key[4];
+    int g = gidx[{bl.s[a].n + M.site[s1].n, b.key[2]}];
+    Grp& G = groups[g];
+    const int r0 = G.roff[{a, s1}], c0 = G.coff[{s2, bb}];
+    CopyTask t{};
+    t.src = theta.data() + b.off;
+    t.rows = b.rows;
+    t.cols = b.cols;
+    t.src_rs = b.cols;
+    t.src_cs = 1;
+    t.dst = T64 + toff[g] + (long long)r0 * G.q + c0;
+    t.dst_rs = G.q;
+    t.dst_cs = 1;
+    gather.tasks.push_back(t);
+    CopyTask w = t;
+    if (G.p >= G.q) {  // W = theta, column-major p x q
+      w.dst = W64 + toff[g] + r0 + (long long)c0 * G.p;
+      w.dst_rs = 1;
+      w.dst_cs = G.p;
+    } else {  // W = theta^H, column-major q x p
+      w.dst = W64 + toff[g] + c0 + (long long)r0 * G.q;
+      w.dst_rs = G.q;
+      w.dst_cs = 1;
+      w.conj = 1;
+    }
+    gather.tasks.push_back(w);
+  }
+  gather.finalize(stream_);
+  gather.launch(stream_);
+  // FP32 preconditioner
+  launch_narrow(W64, W32, ttot, stream_);
+  std::vector<Svd32Task> st32(ng);
+  for (int g = 0; g < ng; ++g) st32[g] = {W32 + toff[g], V32 + voff[g], bigP(groups[g]), smallQ(groups[g])};
+  DevBuf dst32 = upload(st32, stream_);
+  if (run_blocked_jacobi32(dst32.as<Svd32Task>(), st32, 24, 2e-5f, stream_) < 0) return 0.0;
+  ok = true;
+  launch_widen(V32, V64, vtot, stream_);
+  // G = W V in FP64: row-major G^T (Q x P) = V^T (Q x Q) W^T (Q x P)
+  {
+    GemmPlan gp;
+    for (int g = 0; g < ng; ++g) {
+      const int P = bigP(groups[g]), Q = smallQ(groups[g]);
+      GemmTask t{};
+      GemmSeg sg{};
+      sg.alpha = 1.0;
+      t.c = G64 + toff[g];
+      t.rows = Q;
+      t.cols = P;
+      t.ldc = P;
+      sg.a = V64 + voff[g];
+      sg.lda = Q;
+      sg.b = W64 + toff[g];
+      sg.ldb = P;
+      sg.k = Q;
+      t.seg_begin = (int)gp.segs.size();
+      t.seg_count = 1;
+      gp.segs.push_back(sg);
+      gp.tasks.push_back(t);
+    }
+    gp.finalize(stream_);
+    gp.launch(stream_, Bases4{{0, 0, 0, 0}});
+  }
+  // FP64 Jacobi on G (no V): quadratic-convergence stop at sqrt(tol)
+  std::vector<SvdTask> st(ng);
+  std::vector<TruncSector> ts(ng);
+  for (int g = 0; g < ng; ++g) {
+    st[g] = {G64 + toff[g], nullptr, Sp + soff[g], Pp + soff[g], bigP(groups[g]), smallQ(groups[g])};
+    ts[g] = {Sp + soff[g], smallQ(groups[g]), M.mult_dim(groups[g].t)};
+  }
+  DevBuf dst = upload(st, stream_);
+  if (run_blocked_jacobi(dst.as<SvdTask>(), st, 30, 1e-13, dstatus_, stream_, 3e-7) < 0)
+    launch_jacobi_svd(dst.as<SvdTask>(), ng, maxq, 60, 1e-13, dstatus_, stream_);
+  DevBuf dts = upload(ts, stream_), doffs = upload(soff, stream_);
+  DevBuf downer(std::max(stot, 1) * sizeof(int), stream_), dorder(std::max(stot, 1) * sizeof(int), stream_);
+  DevBuf dkept(std::max(ng, 1) * sizeof(int), stream_), dstats(8 * sizeof(double), stream_);
+  launch_truncate(dts.as<TruncSector>(), ng, doffs.as<int>(), stot, eps, chi_max, downer.as<int>(), dorder.as<int>(),
+                  dkept.as<int>(), dstats.as<double>(), stream_);
+  std::vector<int> kept(ng);
+  double hstats[8];
+  TDVP_CUDA(cudaMemcpyAsync(kept.data(), dkept.p, ng * sizeof(int), cudaMemcpyDeviceToHost, stream_));
+  TDVP_CUDA(cudaMemcpyAsync(hstats, dstats.p, 5 * sizeof(double), cudaMemcpyDeviceToHost, stream_));
+  TDVP_CUDA(cudaStreamSynchronize(stream_));
+  std::vector<std::pair<std::pair<int, int>, int>> ns;
+  for (int g = 0; g < ng; ++g)
+    if (kept[g] > 0) ns.push_back({{groups[g].n, groups[g].t}, g});
+  std::sort(ns.begin(), ns.end());
+  bm = BondSpace();
+  for (auto& e : ns) bm.s.push_back({e.first.first, e.first.second, kept[e.second]});
+  bm.build_index();
+  // kept basis X (xrows x k, row-major) on the side the sweep needs
+  std::vector<long long> xoff(ng, 0), zoff(ng, 0), koff(ng, 0), poff(ng, 0);
+  long long xt = 0, zt = 0, kt = 0, pt = 0;
+  for (int g = 0; g < ng; ++g) {
+    const Grp& G = groups[g];
+    const int k = kept[g];
+    if (!k) continue;
+    xoff[g] = xt;
+    xt += (long long)xrows(G) * k;
+    if (!from_g(G)) {
+      zoff[g] = zt;
+      zt += (long long)bigP(G) * k;
+      koff[g] = kt;
+      kt += (long long)k * k;
+    }
+    poff[g] = pt;
+    pt += (long long)(absorb_right ? G.q : G.p) * k;
+  }
+  DevBuf dX(std::max<long long>(xt, 1) * sizeof(cplx), stream_), dZ(std::max<long long>(zt, 1) * sizeof(cplx), stream_);
+  DevBuf dK(std::max<long long>(kt, 1) * sizeof(cplx), stream_), dPr(std::max<long long>(pt, 1) * sizeof(cplx), stream_);
+  cplx *Xb = dX.as<cplx>(), *Zb = dZ.as<cplx>(), *Kb = dK.as<cplx>(), *Pr = dPr.as<cplx>();
+  std::vector<BasisTask> bt;
+  bool any_ns = false;
+  for (int g = 0; g < ng; ++g) {
+    const Grp& G = groups[g];
+    if (!kept[g]) continue;
+    if (from_g(G)) {
+      bt.push_back({G64 + toff[g], Pp + soff[g], Sp + soff[g], Xb + xoff[g], bigP(G), kept[g], 0});
+    } else {
+      bt.push_back({G64 + toff[g], Pp + soff[g], Sp + soff[g], Zb + zoff[g], bigP(G), kept[g], 1});
+      any_ns = true;
+    }
+  }
+  DevBuf dbt = upload(bt, stream_);
+  launch_basis64(dbt.as<BasisTask>(), (int)bt.size(), stream_);
+  if (any_ns) {
+    // X = W^H Z: theta Z (left to right, W = theta^H) or theta^H Z (right to left, W = theta)
+    GemmPlan xp;
+    std::vector<NsTask> nt;
+    for (int g = 0; g < ng; ++g) {
+      const Grp& G = groups[g];
+      const int k = kept[g];
+      if (!k || from_g(G)) continue;
+      GemmTask t{};
+      GemmSeg sg{};
+      sg.alpha = 1.0;
+      t.c = Xb + xoff[g];
+      t.rows = xrows(G);
+      t.cols = k;
+      t.ldc = k;
+      sg.a = T64 + toff[g];
+      sg.lda = G.q;
+      sg.b = Zb + zoff[g];
+      sg.ldb = k;
+      if (absorb_right) {
+        sg.k = G.q;
+      } else {
+        sg.op_a = OP_C;
+        sg.k = G.p;
+      }
+      t.seg_begin = (int)xp.segs.size();
+      t.seg_count = 1;
+      xp.segs.push_back(sg);
+      xp.tasks.push_back(t);
+      nt.push_back({Kb + koff[g], k});
+    }
+    xp.finalize(stream_);
+    xp.launch(stream_, Bases4{{0, 0, 0, 0}});
+    // Newton-Schulz in FP64: K = X^H X, F = 1.5 I - 0.5 K, X <- X F (Z reused as scratch)
+    DevBuf dnt = upload(nt, stream_);
+    for (int it = 0; it < 2; ++it) {
+      GemmPlan g1, g2;
+      for (int g = 0; g < ng; ++g) {
+        const Grp& G = groups[g];
+        const int k = kept[g];
+        if (!k || from_g(G)) continue;
+        const int dim = xrows(G);
+        GemmTask t{};
+        GemmSeg sg{};
+        sg.alpha = 1.0;
+        t.c = Kb + koff[g];
+        t.rows = k;
+        t.cols = k;
+        t.ldc = k;
+        sg.a = Xb + xoff[g];
+        sg.lda = k;
+        sg.op_a = OP_C;
+        sg.b = Xb + xoff[g];
+        sg.ldb = k;
+        sg.k = dim;
+        t.seg_begin = (int)g1.segs.size();
+        t.seg_count = 1;
+        g1.segs.push_back(sg);
+        g1.tasks.push_back(t);
+        GemmTask u{};
+        GemmSeg sh{};
+        sh.alpha = 1.0;
+        u.c = Zb + zoff[g];
+        u.rows = dim;
+        u.cols = k;
+        u.ldc = k;
+        sh.a = Xb + xoff[g];
+        sh.lda = k;
+        sh.b = Kb + koff[g];
+        sh.ldb = k;
+        sh.k = k;
+        u.seg_begin = (int)g2.segs.size();
+        u.seg_count = 1;
+        g2.segs.push_back(sh);
+        g2.tasks.push_back(u);
+      }
+      g1.finalize(stream_);
+      g1.launch(stream_, Bases4{{0, 0, 0, 0}});
+      launch_ns_coeff(dnt.as<NsTask>(), (int)nt.size(), stream_);
+      g2.finalize(stream_);
+      g2.launch(stream_, Bases4{{0, 0, 0, 0}});
+      CopyPlan back;  // X <- X F (Z holds X F; Z rows >= X rows, packed at the same pitch k)
+      for (int g = 0; g < ng; ++g) {
+        const Grp& G = groups[g];
+        const int k = kept[g];
+        if (!k || from_g(G)) continue;
+        CopyTask c{};
+        c.src = Zb + zoff[g];
+        c.dst = Xb + xoff[g];
+        c.rows = xrows(G);
+        c.cols = k;
+        c.src_rs = k;
+        c.src_cs = 1;
+        c.dst_rs = k;
+        c.dst_cs = 1;
+        back.tasks.push_back(c);
+      }
+      back.finalize(stream_);
+      back.launch(stream_);
+    }
+  }
+  // exact projection for the other factor: C = X^H T (left to right) or M = T X (right to left)
+  GemmPlan pg;
+  for (int g = 0; g < ng; ++g) {
+    const Grp& G = groups[g];
+    const int k = kept[g];
+    if (!k) continue;
+    GemmTask t{};
+    GemmSeg sg{};
+    sg.alpha = 1.0;
+    if (absorb_right) {
+      t.c = Pr + poff[g];
+      t.rows = k;
+      t.cols = G.q;
+      t.ldc = G.q;
+      sg.a = Xb + xoff[g];
+      sg.lda = k;
+      sg.op_a = OP_C;
+      sg.b = T64 + toff[g];
+      sg.ldb = G.q;
+      sg.k = G.p;
+    } else {
+      t.c = Pr + poff[g];
+      t.rows = G.p;
+      t.cols = k;
+      t.ldc = k;
+      sg.a = T64 + toff[g];
+      sg.lda = G.q;
+      sg.b = Xb + xoff[g];
+      sg.ldb = k;
+      sg.k = G.q;
+    }
+    t.seg_begin = (int)pg.segs.size();
+    t.seg_count = 1;
+    pg.segs.push_back(sg);
+    pg.tasks.push_back(t);
+  }
+  pg.finalize(stream_);
+  pg.launch(stream_, Bases4{{0, 0, 0, 0}});
+  // renormalise the kept state to unit norm
+  DevBuf part((size_t)296 * sizeof(cplx), stream_), nrm(sizeof(cplx), stream_), dgs(sizeof(double), stream_);
+  launch_dots(Pr, 0, 1, Pr, pt, part.as<cplx>(), dots_grid(pt), nrm.as<cplx>(), nullptr, stream_);
+  cplx hn;
+  TDVP_CUDA(cudaMemcpyAsync(&hn, nrm.p, sizeof(cplx), cudaMemcpyDeviceToHost, stream_));
+  TDVP_CUDA(cudaStreamSynchronize(stream_));
+  double gsc = hn.x > 0 ? 1.0 / std::sqrt(hn.x) : 1.0;
+  TDVP_CUDA(cudaMemcpyAsync(dgs.p, &gsc, sizeof(double), cudaMemcpyHostToDevice, stream_));
+  build_site_layout(X, bl, bm);
+  build_site_layout(Y, bm, br);
+  alloc(X, false);
+  alloc(Y, false);
+  CopyPlan scatter;
+  for (auto& e : ns) {
+    int g = e.second;
+    const Grp& G = groups[g];
+    const int k = kept[g];
+    const int c = bm.find(G.n, G.t);
+    for (auto& rw : G.rows) {
+      int xb = X.find(bkey(rw.first, rw.second, c));
+      if (xb < 0) throw Error(-5, "X block missing");
+      int r0 = G.roff.at(rw);
+      CopyTask t{};
+      t.dst = X.ptr(xb);
+      t.rows = bl.s[rw.first].d;
+      t.cols = k;
+      t.dst_rs = k;
+      t.dst_cs = 1;
+      if (absorb_right) {  // A = X rows
+        t.src = Xb + xoff[g] + (long long)r0 * k;
+      } else {  // centre M = T X rows
+        t.src = Pr + poff[g] + (long long)r0 * k;
+        t.gscale = dgs.as<double>();
+      }
+      t.src_rs = k;
+      t.src_cs = 1;
+      scatter.tasks.push_back(t);
+    }
+    for (auto& cl : G.cols) {
+      int yb = Y.find(bkey(c, cl.first, cl.second));
+      if (yb < 0) throw Error(-5, "Y block missing");
+      int c0 = G.coff.at(cl);
+      CopyTask t{};
+      t.dst = Y.ptr(yb);
+      t.rows = k;
+      t.cols = br.s[cl.second].d;
+      t.dst_rs = t.cols;
+      t.dst_cs = 1;
+      if (absorb_right) {  // centre C = X^H T columns
+        t.src = Pr + poff[g] + c0;
+        t.src_rs = G.q;
+        t.src_cs = 1;
+        t.gscale = dgs.as<double>();
+      } else {  // B = X^H: B[kk][col] = conj(X[c0 + col][kk])
+        t.src = Xb + xoff[g] + (long long)c0 * k;
+        t.src_rs = 1;
+        t.src_cs = k;
+        t.conj = 1;
+      }
+      scatter.tasks.push_back(t);
+    }
+  }
+  scatter.finalize(stream_);
+  scatter.launch(stream_);
+  if (s_ent) {
+    std::vector<TruncSector> ks;
+    for (int g = 0; g < ng; ++g)
+      if (kept[g] > 0) ks.push_back({Sp + soff[g], kept[g], M.mult_dim(groups[g].t)});
+    DevBuf dks = upload(ks, stream_), dE(sizeof(double), stream_);
+    launch_entropy_sv(dks.as<TruncSector>(), (int)ks.size(), dstats.as<double>() + 2, dE.as<double>(), stream_);
+    TDVP_CUDA(cudaMemcpyAsync(s_ent, dE.p, sizeof(double), cudaMemcpyDeviceToHost, stream_));
+  }
+  TDVP_CUDA(cudaStreamSynchronize(stream_));
+  long long chi = 0;
+  for (auto& x : bm.s) chi += (long long)x.d * M.mult_dim(x.t);
   stats_.chi_max_seen = std::max(stats_.chi_max_seen, chi);
   return hstats[1] / (hstats[0] > 0 ? hstats[0] : 1.0);
 }

@@ -202,6 +202,8 @@ class Engine {
   // split theta at bond (i,i+1); absorb_right: S goes to Y (left-to-right sweep)
   double split(BTensor& theta, const BondSpace& bl, const BondSpace& br, long long chi_max, double eps,
                bool absorb_right, BondSpace& bm, BTensor& X, BTensor& Y, double* s_ent = nullptr);
+  double split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace& br, long long chi_max, double eps,
+                     bool absorb_right, BondSpace& bm, BTensor& X, BTensor& Y, double* s_ent, bool& ok);
   void bond_update(int i, bool left_to_right, double tau, long long chi_max, double eps, bool backward,
                    double* s_ent);
   int expm(HeffPlan& H, cplx* x, double tau);  // returns the Krylov dimension used

@@ -447,7 +447,7 @@ __global__ void __launch_bounds__(SVD_THREADS) jacobi_svd_kernel(const SvdTask* 
   const SvdTask t = tasks[blockIdx.x];
   const int p = t.p, q = t.q;
   const int warp = threadIdx.x >> 5, nwarp = SVD_THREADS / 32;
-  for (int e = threadIdx.x; e < q * q; e += SVD_THREADS) {
+  for (int e = threadIdx.x; t.v && e < q * q; e += SVD_THREADS) {
     int r = e % q, c = e / q;
     t.v[e] = {r == c ? 1.0 : 0.0, 0.0};
   }
@@ -485,7 +485,7 @@ __global__ void __launch_bounds__(SVD_THREADS) jacobi_svd_kernel(const SvdTask* 
         double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
         cplx e = {c.x / ac, c.y / ac};
         rotate_cols(t.g, p, p, i, j, cs, sn, e);
-        rotate_cols(t.v, q, q, i, j, cs, sn, e);
+        if (t.v) rotate_cols(t.v, q, q, i, j, cs, sn, e);
         if ((threadIdx.x & 31) == 0) rotated = 1;
       }
       __syncthreads();
@@ -550,7 +550,7 @@ __device__ __forceinline__ void tourney(int r, int k, int n, int& i, int& j) {
 
 __global__ void __launch_bounds__(256) bjacobi_round_kernel(const SvdTask* __restrict__ tasks,
                                                             const int2* __restrict__ work, int round, int bw,
-                                                            double tol, int* __restrict__ flag_now,
+                                                            double tol, double tol_flag, int* __restrict__ flag_now,
                                                             const int* __restrict__ flag_prev) {
   const int2 wk = work[blockIdx.x];
   const SvdTask t = tasks[wk.x];
@@ -561,10 +561,11 @@ __global__ void __launch_bounds__(256) bjacobi_round_kernel(const SvdTask* __res
   int I, Jb;
   tourney(round, wk.y, nb, I, Jb);
   const int p = t.p, q = t.q;
+  const bool with_v = t.v != nullptr;
   extern __shared__ cplx sm[];
   const int nc = 2 * bw;
   cplx* Gs = sm;                  // nc columns x p rows
-  cplx* Vs = sm + (size_t)nc * p;  // nc columns x q rows
+  cplx* Vs = sm + (size_t)nc * p;  // nc columns x q rows (when V is accumulated)
   int col[64];
   int ncol = 0;
   for (int c = 0; c < bw; ++c)
@@ -574,9 +575,11 @@ __global__ void __launch_bounds__(256) bjacobi_round_kernel(const SvdTask* __res
   if (ncol < 2) return;
   for (int cc = 0; cc < ncol; ++cc) {
     const cplx* g = t.g + (long long)col[cc] * p;
-    const cplx* v = t.v + (long long)col[cc] * q;
     for (int r = threadIdx.x; r < p; r += blockDim.x) Gs[(size_t)cc * p + r] = g[r];
-    for (int r = threadIdx.x; r < q; r += blockDim.x) Vs[(size_t)cc * q + r] = v[r];
+    if (with_v) {
+      const cplx* v = t.v + (long long)col[cc] * q;
+      for (int r = threadIdx.x; r < q; r += blockDim.x) Vs[(size_t)cc * q + r] = v[r];
+    }
   }
   __shared__ int rotated;
   if (threadIdx.x == 0) rotated = 0;
@@ -598,16 +601,18 @@ __global__ void __launch_bounds__(256) bjacobi_round_kernel(const SvdTask* __res
       double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
       cplx e = {c.x / ac, c.y / ac};
       rotate_cols(Gs, p, p, i, j, cs, sn, e);
-      rotate_cols(Vs, q, q, i, j, cs, sn, e);
-      if ((threadIdx.x & 31) == 0) rotated = 1;
+      if (with_v) rotate_cols(Vs, q, q, i, j, cs, sn, e);
+      if ((threadIdx.x & 31) == 0 && ac > tol_flag * sqrt(a * b)) rotated = 1;
     }
     __syncthreads();
   }
   for (int cc = 0; cc < ncol; ++cc) {
     cplx* g = t.g + (long long)col[cc] * p;
-    cplx* v = t.v + (long long)col[cc] * q;
     for (int r = threadIdx.x; r < p; r += blockDim.x) g[r] = Gs[(size_t)cc * p + r];
-    for (int r = threadIdx.x; r < q; r += blockDim.x) v[r] = Vs[(size_t)cc * q + r];
+    if (with_v) {
+      cplx* v = t.v + (long long)col[cc] * q;
+      for (int r = threadIdx.x; r < q; r += blockDim.x) v[r] = Vs[(size_t)cc * q + r];
+    }
   }
   if (threadIdx.x == 0 && rotated) atomicOr(&flag_now[wk.x], 1);
 }
@@ -615,6 +620,7 @@ __global__ void __launch_bounds__(256) bjacobi_round_kernel(const SvdTask* __res
 // V = identity for every problem
 __global__ void svd_init_v_kernel(const SvdTask* __restrict__ tasks) {
   const SvdTask t = tasks[blockIdx.x];
+  if (!t.v) return;
   for (int e = threadIdx.x; e < t.q * t.q; e += blockDim.x) t.v[e] = {(e % t.q) == (e / t.q) ? 1.0 : 0.0, 0.0};
 }
 
@@ -649,20 +655,27 @@ __global__ void __launch_bounds__(256) svd_finish_kernel(const SvdTask* __restri
 }
 
 // Blocked Jacobi driver: returns the number of sweeps used (host loop, one sync per sweep).
+// V is accumulated (from the identity) when the tasks carry v; without v only G is
+// rotated.  A sweep in which no rotation exceeded tol_flag (relative, as tol) ends
+// the iteration: with tol_flag = tol that is the usual "no rotation at all" test,
+// with tol_flag = sqrt(tol) it relies on the quadratic convergence of cyclic Jacobi
+// (off-diagonal delta before a sweep leaves O(delta^2) after it).
 int run_blocked_jacobi(const SvdTask* d_tasks, const std::vector<SvdTask>& h_tasks, int max_sweeps, double tol,
-                       int* status, cudaStream_t s) {
+                       int* status, cudaStream_t s, double tol_flag) {
   const int nt = (int)h_tasks.size();
   if (nt == 0) return 0;
+  if (!(tol_flag >= tol)) tol_flag = tol;
   int pmax = 1, qmax = 1;
   for (auto& t : h_tasks) {
     pmax = max(pmax, t.p);
     qmax = max(qmax, t.q);
   }
+  const int vrows = h_tasks[0].v ? qmax : 0;
   // widest block (<= 32 columns) whose pair of column copies fits in shared memory
   int bw = 32;
-  while (bw > 1 && (size_t)2 * bw * (pmax + qmax) * sizeof(cplx) > 200 * 1024) bw >>= 1;
-  if ((size_t)2 * bw * (pmax + qmax) * sizeof(cplx) > 200 * 1024) return -1;  // caller falls back
-  const size_t smem = (size_t)2 * bw * (pmax + qmax) * sizeof(cplx);
+  while (bw > 1 && (size_t)2 * bw * (pmax + vrows) * sizeof(cplx) > 200 * 1024) bw >>= 1;
+  if ((size_t)2 * bw * (pmax + vrows) * sizeof(cplx) > 200 * 1024) return -1;  // caller falls back
+  const size_t smem = (size_t)2 * bw * (pmax + vrows) * sizeof(cplx);
   cudaFuncSetAttribute(bjacobi_round_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   std::vector<int2> work;
   int max_rounds = 0;
@@ -682,7 +695,7 @@ int run_blocked_jacobi(const SvdTask* d_tasks, const std::vector<SvdTask>& h_tas
   for (; sweep < max_sweeps; ++sweep) {
     cudaMemsetAsync(now, 0, nt * sizeof(int), s);
     for (int r = 0; r < max_rounds; ++r)
-      bjacobi_round_kernel<<<(int)work.size(), 256, smem, s>>>(d_tasks, d_work, r, bw, tol, now, prev);
+      bjacobi_round_kernel<<<(int)work.size(), 256, smem, s>>>(d_tasks, d_work, r, bw, tol, tol_flag, now, prev);
     cudaMemcpyAsync(hf.data(), now, nt * sizeof(int), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
     bool any = false;
@@ -702,6 +715,216 @@ int run_blocked_jacobi(const SvdTask* d_tasks, const std::vector<SvdTask>& h_tas
   cudaFreeAsync(d_work, s);
   cudaFreeAsync(flags, s);
   return sweep;
+}
+
+// ---------------------------------------------------------------------------
+// K6 (FP32 preconditioner): blocked one-sided Jacobi on a complex64 copy of G with
+// the right rotations accumulated in a complex64 V.  Used by the split-precision
+// modes: V is widened to FP64, G = A V is formed again in FP64 and a short FP64
+// Jacobi finishes the SVD, so every singular value the truncation sees is an FP64
+// one (the FP32 columns themselves are discarded).
+// ---------------------------------------------------------------------------
+
+__device__ void col_pair32(const float2* __restrict__ g, int p, int i, int j, float& a, float& b, float2& c) {
+  const int lane = threadIdx.x & 31;
+  float sa = 0, sb = 0, cx = 0, cy = 0;
+  const float2* gi = g + (long long)i * p;
+  const float2* gj = g + (long long)j * p;
+  for (int r = lane; r < p; r += 32) {
+    float2 x = gi[r], y = gj[r];
+    sa = fmaf(x.x, x.x, fmaf(x.y, x.y, sa));
+    sb = fmaf(y.x, y.x, fmaf(y.y, y.y, sb));
+    cx = fmaf(x.x, y.x, fmaf(x.y, y.y, cx));
+    cy = fmaf(x.x, y.y, fmaf(-x.y, y.x, cy));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sa += __shfl_xor_sync(0xffffffffu, sa, o);
+    sb += __shfl_xor_sync(0xffffffffu, sb, o);
+    cx += __shfl_xor_sync(0xffffffffu, cx, o);
+    cy += __shfl_xor_sync(0xffffffffu, cy, o);
+  }
+  a = sa;
+  b = sb;
+  c = make_float2(cx, cy);
+}
+
+__device__ void rotate32(float2* __restrict__ g, int ld, int len, int i, int j, float cs, float sn, float2 e) {
+  const int lane = threadIdx.x & 31;
+  float2* gi = g + (long long)i * ld;
+  float2* gj = g + (long long)j * ld;
+  for (int r = lane; r < len; r += 32) {
+    float2 x = gi[r], y = gj[r];
+    float2 ey = make_float2(e.x * y.x + e.y * y.y, e.x * y.y - e.y * y.x);
+    float2 ex = make_float2(e.x * x.x - e.y * x.y, e.x * x.y + e.y * x.x);
+    gi[r] = make_float2(cs * x.x - sn * ey.x, cs * x.y - sn * ey.y);
+    gj[r] = make_float2(sn * ex.x + cs * y.x, sn * ex.y + cs * y.y);
+  }
+}
+
+__global__ void __launch_bounds__(256) bjacobi32_round_kernel(const Svd32Task* __restrict__ tasks,
+                                                              const int2* __restrict__ work, int round, int bw,
+                                                              float tol, int* __restrict__ flag_now,
+                                                              const int* __restrict__ flag_prev) {
+  const int2 wk = work[blockIdx.x];
+  const Svd32Task t = tasks[wk.x];
+  if (flag_prev && flag_prev[wk.x] == 0) return;
+  const int nb0 = (t.q + bw - 1) / bw;
+  const int nb = nb0 + (nb0 & 1);
+  if (nb < 2 || round >= nb - 1) return;
+  int I, Jb;
+  tourney(round, wk.y, nb, I, Jb);
+  const int p = t.p, q = t.q;
+  extern __shared__ float2 sg[];
+  float2* sv = sg + (size_t)2 * bw * p;  // V columns after the G columns
+  int ncol = 0;
+  int col[64];
+  for (int c = 0; c < bw; ++c)
+    if (I * bw + c < q) col[ncol++] = I * bw + c;
+  for (int c = 0; c < bw; ++c)
+    if (Jb * bw + c < q) col[ncol++] = Jb * bw + c;
+  if (ncol < 2) return;
+  for (int cc = 0; cc < ncol; ++cc) {
+    const float2* g = t.g + (long long)col[cc] * p;
+    const float2* v = t.v + (long long)col[cc] * q;
+    for (int r = threadIdx.x; r < p; r += blockDim.x) sg[(size_t)cc * p + r] = g[r];
+    for (int r = threadIdx.x; r < q; r += blockDim.x) sv[(size_t)cc * q + r] = v[r];
+  }
+  __shared__ int rotated;
+  if (threadIdx.x == 0) rotated = 0;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int nn = ncol + (ncol & 1);
+  for (int r = 0; r < nn - 1; ++r) {
+    for (int k = warp; k < nn / 2; k += nwarp) {
+      int i, j;
+      tourney(r, k, nn, i, j);
+      if (j >= ncol) continue;
+      float a, b;
+      float2 c;
+      col_pair32(sg, p, i, j, a, b, c);
+      float ac = sqrtf(c.x * c.x + c.y * c.y);
+      if (ac == 0.0f || ac <= tol * sqrtf(a * b)) continue;
+      float zeta = (b - a) / (2.0f * ac);
+      float tt = (zeta >= 0 ? 1.0f : -1.0f) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta));
+      float cs = 1.0f / sqrtf(1.0f + tt * tt), sn = cs * tt;
+      float2 e = make_float2(c.x / ac, c.y / ac);
+      rotate32(sg, p, p, i, j, cs, sn, e);
+      rotate32(sv, q, q, i, j, cs, sn, e);
+      if ((threadIdx.x & 31) == 0) rotated = 1;
+    }
+    __syncthreads();
+  }
+  for (int cc = 0; cc < ncol; ++cc) {
+    float2* g = t.g + (long long)col[cc] * p;
+    float2* v = t.v + (long long)col[cc] * q;
+    for (int r = threadIdx.x; r < p; r += blockDim.x) g[r] = sg[(size_t)cc * p + r];
+    for (int r = threadIdx.x; r < q; r += blockDim.x) v[r] = sv[(size_t)cc * q + r];
+  }
+  if (threadIdx.x == 0 && rotated) atomicOr(&flag_now[wk.x], 1);
+}
+
+__global__ void svd32_init_v_kernel(const Svd32Task* __restrict__ tasks) {
+  const Svd32Task t = tasks[blockIdx.x];
+  for (int e = threadIdx.x; e < t.q * t.q; e += blockDim.x)
+    t.v[e] = make_float2((e % t.q) == (e / t.q) ? 1.0f : 0.0f, 0.0f);
+}
+
+int run_blocked_jacobi32(const Svd32Task* d_tasks, const std::vector<Svd32Task>& h_tasks, int max_sweeps, float tol,
+                         cudaStream_t s) {
+  const int nt = (int)h_tasks.size();
+  if (nt == 0) return 0;
+  int pmax = 1, qmax = 1;
+  for (auto& t : h_tasks) {
+    pmax = max(pmax, t.p);
+    qmax = max(qmax, t.q);
+  }
+  int bw = 32;
+  while (bw > 1 && (size_t)2 * bw * (pmax + qmax) * sizeof(float2) > 200 * 1024) bw >>= 1;
+  if ((size_t)2 * bw * (pmax + qmax) * sizeof(float2) > 200 * 1024) return -1;
+  const size_t smem = (size_t)2 * bw * (pmax + qmax) * sizeof(float2);
+  cudaFuncSetAttribute(bjacobi32_round_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  std::vector<int2> work;
+  int max_rounds = 0;
+  for (int i = 0; i < nt; ++i) {
+    int nb0 = (h_tasks[i].q + bw - 1) / bw, nb = nb0 + (nb0 & 1);
+    for (int k = 0; k < nb / 2; ++k) work.push_back(make_int2(i, k));
+    max_rounds = max(max_rounds, nb - 1);
+  }
+  int2* d_work = nullptr;
+  int* flags = nullptr;
+  cudaMallocAsync(&d_work, (work.empty() ? 1 : work.size()) * sizeof(int2), s);
+  cudaMallocAsync(&flags, 2 * nt * sizeof(int), s);
+  if (!work.empty()) cudaMemcpyAsync(d_work, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+  svd32_init_v_kernel<<<nt, 256, 0, s>>>(d_tasks);
+  std::vector<int> hf(nt);
+  int sweep = 0, *prev = nullptr, *now = flags;
+  for (; sweep < max_sweeps && !work.empty(); ++sweep) {
+    cudaMemsetAsync(now, 0, nt * sizeof(int), s);
+    for (int r = 0; r < max_rounds; ++r)
+      bjacobi32_round_kernel<<<(int)work.size(), 256, smem, s>>>(d_tasks, d_work, r, bw, tol, now, prev);
+    cudaMemcpyAsync(hf.data(), now, nt * sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    bool any = false;
+    for (int v : hf) any |= v != 0;
+    if (!any) break;
+    prev = now;
+    now = (now == flags) ? flags + nt : flags;
+  }
+  cudaFreeAsync(d_work, s);
+  cudaFreeAsync(flags, s);
+  return sweep;
+}
+
+// precision conversions of whole buffers
+__global__ void narrow_kernel(const cplx* __restrict__ src, float2* __restrict__ dst, long long n) {
+  for (long long e = blockIdx.x * 256LL + threadIdx.x; e < n; e += (long long)gridDim.x * 256)
+    dst[e] = make_float2((float)src[e].x, (float)src[e].y);
+}
+__global__ void widen_kernel(const float2* __restrict__ src, cplx* __restrict__ dst, long long n) {
+  for (long long e = blockIdx.x * 256LL + threadIdx.x; e < n; e += (long long)gridDim.x * 256)
+    dst[e] = {(double)src[e].x, (double)src[e].y};
+}
+
+// X (rows x k, row-major) column kk = column perm[kk] of G (rows x ., column-major)
+// divided by sv[kk] (pow2 = 0) or sv[kk]^2 (pow2 = 1)
+__global__ void basis64_kernel(const BasisTask* __restrict__ tasks) {
+  const BasisTask t = tasks[blockIdx.y];
+  const long long n = (long long)t.rows * t.k;
+  for (long long e = blockIdx.x * 256LL + threadIdx.x; e < n; e += (long long)gridDim.x * 256) {
+    int i = (int)(e / t.k), kk = (int)(e - (long long)i * t.k);
+    cplx g = t.g[i + (long long)t.perm[kk] * t.rows];
+    double s = t.sv[kk];
+    double f = s > 0 ? (t.pow2 ? 1.0 / (s * s) : 1.0 / s) : 0.0;
+    t.x[e] = {f * g.x, f * g.y};
+  }
+}
+
+// F = 1.5 I - 0.5 G for the Newton-Schulz step X <- X F (k x k, row-major)
+__global__ void ns_coeff_kernel(const NsTask* __restrict__ tasks) {
+  const NsTask t = tasks[blockIdx.y];
+  const int n = t.k * t.k;
+  for (int e = blockIdx.x * 256 + threadIdx.x; e < n; e += gridDim.x * 256) {
+    int i = e / t.k, j = e - i * t.k;
+    cplx g = t.g[e];
+    t.g[e] = {(i == j ? 1.5 : 0.0) - 0.5 * g.x, -0.5 * g.y};
+  }
+}
+
+static int conv_grid(long long n) {
+  long long b = (n + 255) / 256;
+  return (int)(b < 1184 ? (b < 1 ? 1 : b) : 1184);
+}
+void launch_narrow(const cplx* src, float2* dst, long long n, cudaStream_t s) {
+  if (n > 0) narrow_kernel<<<conv_grid(n), 256, 0, s>>>(src, dst, n);
+}
+void launch_widen(const float2* src, cplx* dst, long long n, cudaStream_t s) {
+  if (n > 0) widen_kernel<<<conv_grid(n), 256, 0, s>>>(src, dst, n);
+}
+void launch_basis64(const BasisTask* tasks, int n, cudaStream_t s) {
+  if (n > 0) basis64_kernel<<<dim3(32, n), 256, 0, s>>>(tasks);
+}
+void launch_ns_coeff(const NsTask* tasks, int n, cudaStream_t s) {
+  if (n > 0) ns_coeff_kernel<<<dim3(8, n), 256, 0, s>>>(tasks);
 }
 
 void launch_jacobi_svd(const SvdTask* tasks, int ntasks, int max_q, int max_sweeps, double tol, int* status,
