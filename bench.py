@@ -18,8 +18,9 @@ centre-site observables.  Every row of the hot path runs in the timed step.
 The metric value is the whole-step throughput of algorithmic block-GEMM work
 (H_eff matvecs and environment updates, 8 flops per complex multiply-add of the
 reduced block products).  heff_kernel reports the H_eff.psi kernel alone on the
-chi=4096 bond problem (random reduced environments), sweep the seconds per
-sweep estimated from the mid-chain bond updates.
+chi=4096 bond problem (random reduced environments); sweep times one full
+second-order time step of the whole chain (after the timed steps) in the bench
+precision and in FP64 from the same state, and compares every n_{i sigma}.
 
 --impl reference runs the CPU oracle (U(1)xU(1) block-sparse brute force) on a
 bounded sample of output blocks of the same bond expanded to U(1)xU(1).
@@ -186,10 +187,52 @@ def heff_kernel_profile(args, dev, stream):
     return out, gemm_flops, gemm_ms
 
 
-def run_engine(args):
+def measure_sweep(args, dev, stream, rank):
+    """One full second-order time step (sweep over all 59 bonds, L->R then R->L)
+    of the L=60 chi=4096 random state, timed with CUDA events, in the bench
+    precision and in FP64 from the same seeded state; the observables after it
+    are compared site by site (the split-vs-FP64 criterion max |dn_{i sigma}|)."""
     import torch
 
     from paper_2606_04771_b300 import Chain
+
+    L, chi, dt, eps = 60, args.chi, 0.05, 1e-9
+    out = {"L": L, "dt": dt, "eps": eps, "chi_cap": chi, "precision": args.precision}
+    res = {}
+    precs = [args.precision] + ([] if (args.no_fp64_check or args.precision == "fp64") else ["fp64"])
+    with torch.cuda.stream(stream):
+        for prec in precs:
+            ch = Chain(L, 1.0, 4.0, symmetry="su2", random_chi=chi, seed=synth.SEED_BOND + 7 + rank, center=0,
+                       precision=prec, krylov_max=args.krylov, stream=stream.cuda_stream, device=dev)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            stream.synchronize()
+            a.record(stream)
+            ch.step(dt, chi, eps)
+            b.record(stream)
+            stream.synchronize()
+            res[prec] = (a.elapsed_time(b) / 1e3, ch.measure(), ch.stats())
+            ch.close()
+    s, o, st = res[args.precision]
+    out["sec_per_sweep"] = s
+    out["matvecs"] = int(st["matvecs"])
+    out["heff_flops"] = st["heff_flops"]
+    out["heff_tflops_in_sweep"] = st["heff_flops"] / s / 1e12
+    if "fp64" in res and args.precision != "fp64":
+        s64, o64, _ = res["fp64"]
+        out["sec_per_sweep_fp64"] = s64
+        out["max_abs_dn_up"] = float(np.max(np.abs(o["n_up"] - o64["n_up"])))
+        out["max_abs_dn_dn"] = float(np.max(np.abs(o["n_dn"] - o64["n_dn"])))
+        out["max_abs_ddocc"] = float(np.max(np.abs(o["docc"] - o64["docc"])))
+        out["max_abs_dS"] = float(np.max(np.abs(o["s_ent"] - o64["s_ent"])))
+        out["bar"] = 1e-6
+        out["within_bar"] = bool(max(out["max_abs_dn_up"], out["max_abs_dn_dn"]) <= 1e-6)
+    return out
+
+
+def run_engine(args):
+    import torch
+
+    from paper_2606_04771_b300 import Chain, launch_count
 
     rank, ws = init_dist()
     dev = int(os.environ.get("LOCAL_RANK", "0"))
@@ -215,7 +258,9 @@ def run_engine(args):
         stream.synchronize()
         barrier(ws)
         st0 = ch.stats()
+        n0 = launch_count()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        torch.cuda.nvtx.range_push("timed_steps")
         with ClockSampler(dev) as clk:
             for i in range(args.steps):
                 flush.zero_()
@@ -223,7 +268,9 @@ def run_engine(args):
                 ents = step()
                 evs[i][1].record(stream)
             stream.synchronize()
+        torch.cuda.nvtx.range_pop()
         st1 = ch.stats()
+        launches = launch_count() - n0
     barrier(ws)
     ms = [a.elapsed_time(b) for a, b in evs]
     ms_step = max_over_ranks(sum(ms) / len(ms), ws)
@@ -233,6 +280,7 @@ def run_engine(args):
     ch.close()
 
     heff, gemm_flops, gemm_ms = heff_kernel_profile(args, dev, stream)
+    sweep = None if args.no_sweep else measure_sweep(args, dev, stream, rank)
     peaks, peak_kind = load_peaks()
     if args.precision == "fp64":
         peak, bound, pnote, issued = 1.25, "alu", "FP64 nominal 1.25 TFLOP/s (recipe table)", 1
@@ -260,14 +308,13 @@ def run_engine(args):
                    "flops_per_step": flops_step, "bond_entropy": ents[1],
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": f"replicas x{ws} (independent states, no collective)"},
-        "sweep": {"sec_per_sweep_est": 2 * (L - 1) / 2 * ms_step / 1e3,
-                  "note": "(L-1) bonds x 2 directions at the mid-chain cost: an upper estimate"},
+        "sweep": sweep,
         "heff_kernel": heff,
         "roofline": roofline,
         "e2e": {"value": heff["e2e_tflops"], "unit": UNIT, "h2d_bytes_per_step": heff["h2d_bytes"],
                 "d2h_bytes_per_step": heff["d2h_bytes"],
                 "path": "tdvp_krylov_expm with host buffers on the chi=4096 bond (H2D theta, D2H result)"},
-        "gpu_launches": None,
+        "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
     if rank == 0 and not args.no_cpu_baseline:
@@ -354,6 +401,8 @@ def main():
     ap.add_argument("--chi", type=int, default=4096)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the full-sweep timing")
+    ap.add_argument("--no-fp64-check", action="store_true", help="skip the FP64 sweep used for the comparison")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -138,7 +138,10 @@ int tdvp_bond_dims(tdvp_ctx* ctx, long long* chi, long long* chi_red);
  * wall seconds per phase (theta formation, planning, two-site Krylov, SVD split,
  * environment update, one-site Krylov; filled only when the environment variable
  * TDVP_PROFILE_PHASES=1 was set at creation, which synchronises at phase
- * boundaries), out[13] number of steps.  n = length of out (at most 14). */
+ * boundaries), out[13] number of steps, out[14] number of SVD splits, out[15]
+ * FP64 Jacobi sweeps summed over the splits (counting the final sweep that found
+ * nothing left to rotate), out[16] FP32 preconditioner sweeps (split-precision
+ * modes).  n = length of out (at most 17). */
 int tdvp_stats(tdvp_ctx* ctx, double* out, int n);
 
 /* ---- single-bond problems (the effective-Hamiltonian benchmark) ------------
@@ -240,6 +243,11 @@ int tdvp_svd(int p, int q, const double* a, double* s, double* u, double* vh, in
  * stream is a cudaStream_t or NULL; the call returns after the result is
  * complete.  Errors: TDVP_EINVAL, TDVP_ENUMERIC, TDVP_ECUDA. */
 int tdvp_svd_noalloc(int p, int q, const double* a, double* s, double* u, double* vh, void* stream);
+
+/* Number of kernel launches this library has made in the process so far, over
+ * every context and entry point (each launch site counts itself on the host
+ * when it enqueues the kernel).  out must be non-NULL.  Errors: TDVP_EINVAL. */
+int tdvp_launch_count(long long* out);
 
 /* Destroy a context and free its device memory.  NULL is accepted. */
 int tdvp_destroy(tdvp_ctx* ctx);

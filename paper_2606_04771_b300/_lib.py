@@ -64,6 +64,7 @@ def lib():
             "tdvp_heff_profile": (C.c_int, [vp, C.c_int, vp, vp, vp]),
             "tdvp_svd": (C.c_int, [C.c_int, C.c_int, vp, vp, vp, vp, C.c_int, vp]),
             "tdvp_svd_noalloc": (C.c_int, [C.c_int, C.c_int, vp, vp, vp, vp, vp]),
+            "tdvp_launch_count": (C.c_int, [P(C.c_longlong)]),
             "tdvp_destroy": (C.c_int, [vp]),
             "tdvp_strerror": (C.c_char_p, [C.c_int]),
             "tdvp_last_error": (C.c_char_p, []),
@@ -122,6 +123,13 @@ def svd(a, stream=None):
     s = torch.empty(r, dtype=torch.float64, device=a.device)
     check(lib().tdvp_svd(p, q, a.data_ptr(), s.data_ptr(), u.data_ptr(), vh.data_ptr(), 1, stream))
     return u, s, vh
+
+
+def launch_count():
+    """Kernel launches this library has enqueued in the process so far."""
+    n = C.c_longlong()
+    check(lib().tdvp_launch_count(C.byref(n)))
+    return n.value
 
 
 class _Ctx:
@@ -233,10 +241,11 @@ class Chain(_Ctx):
         return chi, red
 
     def stats(self):
-        v = np.zeros(14)
-        check(lib().tdvp_stats(self.h, v.ctypes.data, 14))
+        v = np.zeros(17)
+        check(lib().tdvp_stats(self.h, v.ctypes.data, 17))
         keys = ["seconds", "heff_flops", "env_flops", "matvecs", "max_krylov", "max_discarded", "chi_max_seen",
-                "t_theta", "t_plan", "t_krylov2", "t_split", "t_env", "t_krylov1", "steps"]
+                "t_theta", "t_plan", "t_krylov2", "t_split", "t_env", "t_krylov1", "steps", "splits", "sweeps64",
+                "sweeps32"]
         return dict(zip(keys, v.tolist()))
 
 

@@ -165,14 +165,21 @@ int tdvp_bond_dims(tdvp_ctx* ctx, long long* chi, long long* chi_red) {
   });
 }
 
+int tdvp_launch_count(long long* out) {
+  if (!out) return fail(TDVP_EINVAL, "NULL argument");
+  *out = tdvp::launch_count();
+  return TDVP_OK;
+}
+
 int tdvp_stats(tdvp_ctx* ctx, double* out, int n) {
   if (!ctx || !out) return fail(TDVP_EINVAL, "NULL argument");
   return guarded([&] {
     const tdvp::StepStats& s = ctx->eng->stats();
-    double v[14] = {s.seconds, (double)s.heff_flops, (double)s.env_flops, (double)s.matvecs, (double)s.max_krylov,
+    double v[17] = {s.seconds, (double)s.heff_flops, (double)s.env_flops, (double)s.matvecs, (double)s.max_krylov,
                     s.max_discarded, (double)s.chi_max_seen, s.phase[0], s.phase[1], s.phase[2], s.phase[3],
-                    s.phase[4], s.phase[5], (double)s.steps};
-    for (int i = 0; i < n && i < 14; ++i) out[i] = v[i];
+                    s.phase[4], s.phase[5], (double)s.steps, (double)s.splits, (double)s.sweeps64,
+                    (double)s.sweeps32};
+    for (int i = 0; i < n && i < 17; ++i) out[i] = v[i];
   });
 }
 

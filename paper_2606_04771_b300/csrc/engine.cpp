@@ -360,7 +360,7 @@ void Engine::orthonormalize_cols(BTensor& T, const BondSpace& l, const BondSpace
   std::vector<long long> goff(r.s.size()), voff(r.s.size());
   std::vector<int> soff(r.s.size()), pv(r.s.size());
   long long gt = 0, vt = 0;
-  int st = 0, mq = 1;
+  int st = 0;
   for (int b = 0; b < (int)r.s.size(); ++b) {
     int p = 0;
     for (int bi : by[b]) p += T.blocks[bi].rows;
@@ -373,7 +373,6 @@ void Engine::orthonormalize_cols(BTensor& T, const BondSpace& l, const BondSpace
     vt += (long long)q * q;
     soff[b] = st;
     st += q;
-    mq = std::max(mq, q);
   }
   DevBuf dG(std::max<long long>(gt, 1) * sizeof(cplx), stream_), dV(std::max<long long>(vt, 1) * sizeof(cplx), stream_);
   DevBuf dS(std::max(st, 1) * sizeof(double), stream_), dP(std::max(st, 1) * sizeof(int), stream_);
@@ -414,8 +413,7 @@ void Engine::orthonormalize_cols(BTensor& T, const BondSpace& l, const BondSpace
   gather.finalize(stream_);
   gather.launch(stream_);
   DevBuf dt = upload(tasks, stream_);
-  if (run_blocked_jacobi(dt.as<SvdTask>(), tasks, 40, 1e-14, dstatus_, stream_) < 0)
-    launch_jacobi_svd(dt.as<SvdTask>(), (int)tasks.size(), mq, 60, 1e-15, dstatus_, stream_);
+  run_jacobi_rounds(dt.as<SvdTask>(), tasks, 40, 1e-14, dstatus_, stream_);
   scatter.finalize(stream_);
   scatter.launch(stream_);
   TDVP_CUDA(cudaStreamSynchronize(stream_));
@@ -430,7 +428,7 @@ void Engine::orthonormalize_rows(BTensor& T, const BondSpace& l, const BondSpace
   std::vector<long long> goff(l.s.size()), voff(l.s.size());
   std::vector<int> soff(l.s.size()), qv(l.s.size());
   long long gt = 0, vt = 0;
-  int st = 0, mq = 1;
+  int st = 0;
   for (int a = 0; a < (int)l.s.size(); ++a) {
     int q = 0;
     for (int bi : by[a]) q += T.blocks[bi].cols;
@@ -443,7 +441,6 @@ void Engine::orthonormalize_rows(BTensor& T, const BondSpace& l, const BondSpace
     vt += (long long)p * p;
     soff[a] = st;
     st += p;
-    mq = std::max(mq, p);
   }
   DevBuf dG(std::max<long long>(gt, 1) * sizeof(cplx), stream_), dV(std::max<long long>(vt, 1) * sizeof(cplx), stream_);
   DevBuf dS(std::max(st, 1) * sizeof(double), stream_), dP(std::max(st, 1) * sizeof(int), stream_);
@@ -486,8 +483,7 @@ void Engine::orthonormalize_rows(BTensor& T, const BondSpace& l, const BondSpace
   gather.finalize(stream_);
   gather.launch(stream_);
   DevBuf dt = upload(tasks, stream_);
-  if (run_blocked_jacobi(dt.as<SvdTask>(), tasks, 40, 1e-14, dstatus_, stream_) < 0)
-    launch_jacobi_svd(dt.as<SvdTask>(), (int)tasks.size(), mq, 60, 1e-15, dstatus_, stream_);
+  run_jacobi_rounds(dt.as<SvdTask>(), tasks, 40, 1e-14, dstatus_, stream_);
   scatter.finalize(stream_);
   scatter.launch(stream_);
   TDVP_CUDA(cudaStreamSynchronize(stream_));
@@ -1244,7 +1240,7 @@ double Engine::split(BTensor& theta, const BondSpace& bl, const BondSpace& br, l
   std::vector<long long> goff(ng), voff(ng);
   std::vector<int> soff(ng);
   long long gtot = 0, vtot = 0;
-  int stot = 0, maxq = 1;
+  int stot = 0;
   for (int g = 0; g < ng; ++g) {
     int P = std::max(groups[g].p, groups[g].q), Q = std::min(groups[g].p, groups[g].q);
     goff[g] = gtot;
@@ -1253,7 +1249,6 @@ double Engine::split(BTensor& theta, const BondSpace& bl, const BondSpace& br, l
     vtot += (long long)Q * Q;
     soff[g] = stot;
     stot += Q;
-    maxq = std::max(maxq, Q);
   }
   DevBuf dG(std::max<long long>(gtot, 1) * sizeof(cplx), stream_);
   DevBuf dV(std::max<long long>(vtot, 1) * sizeof(cplx), stream_);
@@ -1298,8 +1293,8 @@ double Engine::split(BTensor& theta, const BondSpace& bl, const BondSpace& br, l
     ts[g] = {Sp + soff[g], Q, M.mult_dim(groups[g].t)};
   }
   DevBuf dst = upload(st, stream_);
-  if (run_blocked_jacobi(dst.as<SvdTask>(), st, 40, 1e-14, dstatus_, stream_) < 0)
-    launch_jacobi_svd(dst.as<SvdTask>(), ng, maxq, 60, 1e-15, dstatus_, stream_);
+  stats_.sweeps64 += run_jacobi_rounds(dst.as<SvdTask>(), st, 40, 1e-14, dstatus_, stream_);
+  stats_.splits += 1;
   // truncation
   DevBuf dts = upload(ts, stream_);
   DevBuf doffs = upload(soff, stream_);
@@ -1414,18 +1409,18 @@ double Engine::split(BTensor& theta, const BondSpace& bl, const BondSpace& br, l
 // Mixed-precision split (tensor-core precision modes).  The per-sector SVD of
 // Sec. S2.4 stays an FP64 SVD; FP32 only supplies a preconditioner.  For each
 // sector the working copy W (theta, or theta^H when theta is wide) is copied to
-// complex64 and an FP32 blocked Jacobi accumulates its right rotations V32; then,
+// complex64 and an FP32 round-robin Jacobi accumulates its right rotations V32; then,
 // in FP64, G = W V32 is formed and a short FP64 Jacobi (no V) makes its columns
 // orthogonal -- G = U S with S the FP64 singular values of W up to the O(1e-7)
 // departure of V32 from unitarity, far below any truncation threshold.  The FP32
 // stage leaves off-diagonals at the FP32 level, so by the quadratic convergence of
-// cyclic Jacobi the FP64 stage ends after two sweeps instead of the ~10 a cold
-// start needs.  The basis the sweep keeps (left for left to right, right for right
+// cyclic Jacobi the FP64 stage ends after about two sweeps instead of the ~17 a
+// cold start needs (both measured on the chi = 4096 chain).  The basis the sweep keeps (left for left to right, right for right
 // to left) is G/S when it is W's column space, otherwise W^H G / S^2
 // re-orthonormalised by two Newton-Schulz steps X <- X (3 I - X^H X) / 2 (the
 // overlaps it starts from are O(1e-7)); the other factor is the exact FP64
-// projection of theta onto that basis.  Returns false in ok when the columns do not
-// fit the blocked kernels (the caller then uses the FP64 split).
+// projection of theta onto that basis.  ok is set when the split was done here (the
+// caller runs the FP64 split otherwise).
 // ---------------------------------------------------------------------------
 
 double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace& br, long long chi_max, double eps,
@@ -1475,7 +1470,7 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
   std::vector<long long> toff(ng), voff(ng);
   std::vector<int> soff(ng);
   long long ttot = 0, vtot = 0;
-  int stot = 0, maxq = 1;
+  int stot = 0;
   for (int g = 0; g < ng; ++g) {
     toff[g] = ttot;
     ttot += (long long)groups[g].p * groups[g].q;
@@ -1483,7 +1478,6 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
     vtot += (long long)smallQ(groups[g]) * smallQ(groups[g]);
     soff[g] = stot;
     stot += smallQ(groups[g]);
-    maxq = std::max(maxq, smallQ(groups[g]));
   }
   const long long tt1 = std::max<long long>(ttot, 1), vt1 = std::max<long long>(vtot, 1);
   DevBuf dT(tt1 * sizeof(cplx), stream_), dW(tt1 * sizeof(cplx), stream_), dG(tt1 * sizeof(cplx), stream_);
@@ -1530,8 +1524,12 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
   std::vector<Svd32Task> st32(ng);
   for (int g = 0; g < ng; ++g) st32[g] = {W32 + toff[g], V32 + voff[g], bigP(groups[g]), smallQ(groups[g])};
   DevBuf dst32 = upload(st32, stream_);
-  if (run_blocked_jacobi32(dst32.as<Svd32Task>(), st32, 24, 2e-5f, stream_) < 0) return 0.0;
+  // FP32 stage: rotate while |g_i^H g_j| > 2e-5 |g_i||g_j|, at most 24 sweeps (it
+  // need not converge: the FP64 stage finishes whatever is left)
+  const int sw32 = run_jacobi_rounds32(dst32.as<Svd32Task>(), st32, 24, 2e-5f, 0.0f, stream_);
   ok = true;
+  stats_.sweeps32 += sw32;
+  stats_.splits += 1;
   launch_widen(V32, V64, vtot, stream_);
   // G = W V in FP64: row-major G^T (Q x P) = V^T (Q x Q) W^T (Q x P)
   {
@@ -1558,7 +1556,6 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
     gp.finalize(stream_);
     gp.launch(stream_, Bases4{{0, 0, 0, 0}});
   }
-  // FP64 Jacobi on G (no V): quadratic-convergence stop at sqrt(tol)
   std::vector<SvdTask> st(ng);
   std::vector<TruncSector> ts(ng);
   for (int g = 0; g < ng; ++g) {
@@ -1566,8 +1563,10 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
     ts[g] = {Sp + soff[g], smallQ(groups[g]), M.mult_dim(groups[g].t)};
   }
   DevBuf dst = upload(st, stream_);
-  if (run_blocked_jacobi(dst.as<SvdTask>(), st, 30, 1e-13, dstatus_, stream_, 3e-7) < 0)
-    launch_jacobi_svd(dst.as<SvdTask>(), ng, maxq, 60, 1e-13, dstatus_, stream_);
+  // FP64 stage: rotate above 1e-13 (relative); stop after a sweep whose rotations were
+  // all below 3e-7 relative (quadratic convergence leaves ~1e-13) or below 1e-11 in
+  // absolute terms (theta has unit norm, so that is a weight far below any threshold)
+  stats_.sweeps64 += run_jacobi_rounds(dst.as<SvdTask>(), st, 30, 1e-13, dstatus_, stream_, 3e-7, 1e-11);
   DevBuf dts = upload(ts, stream_), doffs = upload(soff, stream_);
   DevBuf downer(std::max(stot, 1) * sizeof(int), stream_), dorder(std::max(stot, 1) * sizeof(int), stream_);
   DevBuf dkept(std::max(ng, 1) * sizeof(int), stream_), dstats(8 * sizeof(double), stream_);
@@ -2066,13 +2065,12 @@ void Engine::measure(double* n_out, double* sz_out, double* docc_out, double* s_
       std::vector<long long> go(ns);
       std::vector<int> so(ns);
       long long gt = 0, vt = 0;
-      int stt = 0, mq = 1;
+      int stt = 0;
       for (int b = 0; b < ns; ++b) {
         go[b] = gt;
         gt += (long long)br.s[b].d * br.s[b].d;
         so[b] = stt;
         stt += br.s[b].d;
-        mq = std::max(mq, br.s[b].d);
       }
       vt = gt;
       DevBuf dG(gt * sizeof(cplx), stream_), dV(vt * sizeof(cplx), stream_);
@@ -2086,8 +2084,7 @@ void Engine::measure(double* n_out, double* sz_out, double* docc_out, double* s_
         ts[b] = {dS.as<double>() + so[b], br.s[b].d, M.mult_dim(br.s[b].t)};
       }
       DevBuf dst = upload(st, stream_), dts2 = upload(ts, stream_);
-      if (run_blocked_jacobi(dst.as<SvdTask>(), st, 40, 1e-14, dstatus_, stream_) < 0)
-        launch_jacobi_svd(dst.as<SvdTask>(), ns, mq, 60, 1e-15, dstatus_, stream_);
+      run_jacobi_rounds(dst.as<SvdTask>(), st, 40, 1e-14, dstatus_, stream_);
       launch_entropy(dts2.as<TruncSector>(), ns, dent.as<double>() + i, stream_);
       TDVP_CUDA(cudaStreamSynchronize(stream_));
     }

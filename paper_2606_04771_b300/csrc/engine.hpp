@@ -139,6 +139,9 @@ struct StepStats {
   // wall seconds per phase when TDVP_PROFILE_PHASES=1: theta formation, planning,
   // two-site Krylov, SVD split, environment update, one-site Krylov
   double phase[6] = {0, 0, 0, 0, 0, 0};
+  // Jacobi sweeps summed over the splits: FP64 (the FP64 split, or the FP64 finish
+  // of the mixed split) and FP32 (the preconditioner of the mixed split)
+  long long sweeps64 = 0, sweeps32 = 0, splits = 0;
 };
 
 class Engine {

@@ -8,6 +8,9 @@
 // to task lists (common.hpp).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <atomic>
+
 #include <cstdio>
 #include <vector>
 
@@ -15,6 +18,10 @@
 #include "kernels.hpp"
 
 namespace tdvp {
+
+static std::atomic<long long> g_launches{0};
+void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 __device__ __forceinline__ cplx cmul(cplx a, cplx b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
 __device__ __forceinline__ cplx cconj(cplx a) { return {a.x, -a.y}; }
@@ -110,6 +117,7 @@ __global__ void __launch_bounds__(256) gemm_fp64_kernel(const GemmTask* __restri
 void launch_gemm_fp64(const GemmTask* tasks, const GemmSeg* segs, const int3* tiles, int ntiles, const Bases4& B,
                       cudaStream_t s) {
   if (ntiles <= 0) return;
+  note_launch();
   gemm_fp64_kernel<<<ntiles, 256, 0, s>>>(tasks, segs, tiles, B);
 }
 
@@ -139,6 +147,7 @@ __global__ void __launch_bounds__(256) lincomb_kernel(const LincombTask* __restr
 void launch_lincomb(const LincombTask* tasks, const LincombTerm* terms, const int2* chunks, int nchunks,
                     cudaStream_t s) {
   if (nchunks <= 0) return;
+  note_launch();
   lincomb_kernel<<<nchunks, 256, 0, s>>>(tasks, terms, chunks);
 }
 
@@ -173,6 +182,7 @@ __global__ void __launch_bounds__(256) copy_kernel(const CopyTask* __restrict__ 
 
 void launch_copy(const CopyTask* tasks, const int2* chunks, int nchunks, cudaStream_t s) {
   if (nchunks <= 0) return;
+  note_launch();
   copy_kernel<<<nchunks, 256, 0, s>>>(tasks, chunks);
 }
 
@@ -283,21 +293,26 @@ static int blas_grid(long long n) {
 void launch_dots(const cplx* V, long long pitch, int nv, const cplx* w, long long n, cplx* partial, int G,
                  cplx* out, const int* done, cudaStream_t s) {
   dim3 grid(G, nv);
+  note_launch();
   dots_partial_kernel<<<grid, 256, 0, s>>>(V, pitch, nv, w, n, partial, done);
+  note_launch();
   dots_final_kernel<<<nv, 32, 0, s>>>(partial, G, nv, out, done);
 }
 
 void launch_axpy_many(const cplx* V, long long pitch, int nv, const cplx* h, cplx* w, long long n, const int* done,
                       cudaStream_t s) {
+  note_launch();
   axpy_many_kernel<<<blas_grid(n), 256, 0, s>>>(V, pitch, nv, h, w, n, done);
 }
 
 void launch_combine(const cplx* V, long long pitch, const int* nv, const cplx* coef, const double* scal, cplx* out,
                     long long n, cudaStream_t s) {
+  note_launch();
   combine_kernel<<<blas_grid(n), 256, 0, s>>>(V, pitch, nv, coef, scal, out, n);
 }
 
 void launch_scale(const cplx* x, const double* nrm, cplx* y, long long n, const int* done, cudaStream_t s) {
+  note_launch();
   scale_kernel<<<blas_grid(n), 256, 0, s>>>(x, nrm, y, n, done);
 }
 
@@ -392,10 +407,14 @@ __global__ void krylov_step_kernel(KrylovState* st, const cplx* h1, const cplx* 
   }
 }
 
-void launch_krylov_init(KrylovState* st, const cplx* nrm2, cudaStream_t s) { krylov_init_kernel<<<1, 1, 0, s>>>(st, nrm2); }
+void launch_krylov_init(KrylovState* st, const cplx* nrm2, cudaStream_t s) {
+  note_launch();
+  krylov_init_kernel<<<1, 1, 0, s>>>(st, nrm2);
+}
 
 void launch_krylov_step(KrylovState* st, const cplx* h1, const cplx* nrm2, double tau, double tol, int kmax,
                         cudaStream_t s) {
+  note_launch();
   krylov_step_kernel<<<1, 32, 0, s>>>(st, h1, nrm2, tau, tol, kmax);
 }
 
@@ -522,14 +541,17 @@ __global__ void __launch_bounds__(SVD_THREADS) jacobi_svd_kernel(const SvdTask* 
 }
 
 // ---------------------------------------------------------------------------
-// K6 (blocked): one-sided Jacobi in rounds over column blocks, many CTAs per matrix
+// K6 (rounds): one-sided Jacobi, one warp per column pair, all problems at once
 //
-// The Q columns of every problem are cut into blocks of bw columns (the block count
-// padded to even).  One launch performs one round of the block tournament for every
-// problem: each CTA takes one pair of blocks, copies their columns of G and V into
-// shared memory, runs one cyclic pass over all column pairs of the 2 bw columns
-// (FP64 complex Jacobi rotations, as in jacobi_svd_kernel), and writes them back.  A
-// sweep is nb - 1 rounds; a problem whose previous sweep made no rotation is skipped.
+// The classical round-robin ordering: the n columns of a problem (n padded to even)
+// form n/2 disjoint pairs in each of n - 1 rounds, and a sweep of n - 1 rounds
+// meets every pair once.  One launch performs one round for every problem: each
+// warp takes one pair, computes the two squared norms and the overlap, and applies
+// the complex Jacobi rotation (as in jacobi_svd_kernel) to both columns of G and,
+// when present, of V.  Columns live in global memory (the whole split's working set
+// stays in L2), so every pair of every sector runs in parallel instead of a block of
+// columns per CTA.  The work list is sorted by problem size, so each round launches
+// only the pairs of the problems that still have that round.
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ void tourney(int r, int k, int n, int& i, int& j) {
@@ -548,73 +570,179 @@ __device__ __forceinline__ void tourney(int r, int k, int n, int& i, int& j) {
   }
 }
 
-__global__ void __launch_bounds__(256) bjacobi_round_kernel(const SvdTask* __restrict__ tasks,
-                                                            const int2* __restrict__ work, int round, int bw,
-                                                            double tol, double tol_flag, int* __restrict__ flag_now,
-                                                            const int* __restrict__ flag_prev) {
-  const int2 wk = work[blockIdx.x];
-  const SvdTask t = tasks[wk.x];
+constexpr int PAIR_WARPS = 2;  // warps (pairs) per CTA: many small CTAs spread one big sector over the SMs
+
+__global__ void __launch_bounds__(PAIR_WARPS * 32) jacobi_pair_kernel(const SvdTask* __restrict__ tasks,
+                                                                      const int2* __restrict__ work, int nwork,
+                                                                      int round, double tol, double tol_flag,
+                                                                      double abs_flag, int* __restrict__ flag_now,
+                                                                      const int* __restrict__ flag_prev) {
+  const int w = blockIdx.x * PAIR_WARPS + (threadIdx.x >> 5);
+  if (w >= nwork) return;
+  const int2 wk = work[w];
   if (flag_prev && flag_prev[wk.x] == 0) return;  // converged in the previous sweep
-  const int nb0 = (t.q + bw - 1) / bw;
-  const int nb = nb0 + (nb0 & 1);
-  if (nb < 2 || round >= nb - 1) return;
-  int I, Jb;
-  tourney(round, wk.y, nb, I, Jb);
-  const int p = t.p, q = t.q;
-  const bool with_v = t.v != nullptr;
-  extern __shared__ cplx sm[];
-  const int nc = 2 * bw;
-  cplx* Gs = sm;                  // nc columns x p rows
-  cplx* Vs = sm + (size_t)nc * p;  // nc columns x q rows (when V is accumulated)
-  int col[64];
-  int ncol = 0;
-  for (int c = 0; c < bw; ++c)
-    if (I * bw + c < q) col[ncol++] = I * bw + c;
-  for (int c = 0; c < bw; ++c)
-    if (Jb * bw + c < q) col[ncol++] = Jb * bw + c;
-  if (ncol < 2) return;
-  for (int cc = 0; cc < ncol; ++cc) {
-    const cplx* g = t.g + (long long)col[cc] * p;
-    for (int r = threadIdx.x; r < p; r += blockDim.x) Gs[(size_t)cc * p + r] = g[r];
-    if (with_v) {
-      const cplx* v = t.v + (long long)col[cc] * q;
-      for (int r = threadIdx.x; r < q; r += blockDim.x) Vs[(size_t)cc * q + r] = v[r];
-    }
+  const SvdTask t = tasks[wk.x];
+  const int n = t.q + (t.q & 1);
+  if (round >= n - 1) return;
+  int i, j;
+  tourney(round, wk.y, n, i, j);
+  if (j >= t.q) return;
+  double a, b;
+  cplx c;
+  col_pair(t.g, t.p, i, j, a, b, c);
+  const double ac = sqrt(c.x * c.x + c.y * c.y);
+  if (ac == 0.0 || ac <= tol * sqrt(a * b)) return;
+  const double zeta = (b - a) / (2.0 * ac);
+  const double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
+  const cplx e = {c.x / ac, c.y / ac};
+  rotate_cols(t.g, t.p, t.p, i, j, cs, sn, e);
+  if (t.v) rotate_cols(t.v, t.q, t.q, i, j, cs, sn, e);
+  if ((threadIdx.x & 31) == 0 && ac > tol_flag * sqrt(a * b) && ac > abs_flag) atomicOr(&flag_now[wk.x], 1);
+}
+
+// CTA-per-pair variant for columns of up to JC_THREADS * R rows: every thread keeps
+// R rows of both columns (and of both columns of V) in registers, so a round is one
+// load pass, one block reduction of (|g_i|^2, |g_j|^2, g_i^H g_j) and one store pass
+// -- a few L2 round trips instead of the 3 p / 32 dependent loads of a warp.
+constexpr int JC_THREADS = 128;
+
+template <class S>
+__device__ __forceinline__ void block_sum4(S& a, S& b, S& c, S& d, S* sh) {
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+    d += __shfl_xor_sync(0xffffffffu, d, o);
   }
-  __shared__ int rotated;
-  if (threadIdx.x == 0) rotated = 0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    sh[4 * warp] = a;
+    sh[4 * warp + 1] = b;
+    sh[4 * warp + 2] = c;
+    sh[4 * warp + 3] = d;
+  }
   __syncthreads();
-  const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  const int nn = ncol + (ncol & 1);
-  for (int r = 0; r < nn - 1; ++r) {
-    for (int k = warp; k < nn / 2; k += nwarp) {
-      int i, j;
-      tourney(r, k, nn, i, j);
-      if (j >= ncol) continue;
-      double a, b;
-      cplx c;
-      col_pair(Gs, p, i, j, a, b, c);
-      double ac = sqrt(c.x * c.x + c.y * c.y);
-      if (ac == 0.0 || ac <= tol * sqrt(a * b)) continue;
-      double zeta = (b - a) / (2.0 * ac);
-      double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-      double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
-      cplx e = {c.x / ac, c.y / ac};
-      rotate_cols(Gs, p, p, i, j, cs, sn, e);
-      if (with_v) rotate_cols(Vs, q, q, i, j, cs, sn, e);
-      if ((threadIdx.x & 31) == 0 && ac > tol_flag * sqrt(a * b)) rotated = 1;
-    }
-    __syncthreads();
+  a = b = c = d = S(0);
+  for (int w = 0; w < JC_THREADS / 32; ++w) {  // same order in every thread
+    a += sh[4 * w];
+    b += sh[4 * w + 1];
+    c += sh[4 * w + 2];
+    d += sh[4 * w + 3];
   }
-  for (int cc = 0; cc < ncol; ++cc) {
-    cplx* g = t.g + (long long)col[cc] * p;
-    for (int r = threadIdx.x; r < p; r += blockDim.x) g[r] = Gs[(size_t)cc * p + r];
-    if (with_v) {
-      cplx* v = t.v + (long long)col[cc] * q;
-      for (int r = threadIdx.x; r < q; r += blockDim.x) v[r] = Vs[(size_t)cc * q + r];
+}
+
+template <class Task, class S, class C2, int R>
+__global__ void __launch_bounds__(JC_THREADS) jacobi_cta_kernel(const Task* __restrict__ tasks,
+                                                                const int2* __restrict__ work, int round, S tol,
+                                                                S tol_flag, S abs_flag, int* __restrict__ flag_now,
+                                                                const int* __restrict__ flag_prev) {
+  const int2 wk = work[blockIdx.x];
+  if (flag_prev && flag_prev[wk.x] == 0) return;  // uniform over the CTA
+  const Task t = tasks[wk.x];
+  const int n = t.q + (t.q & 1);
+  if (round >= n - 1) return;
+  int i, j;
+  tourney(round, wk.y, n, i, j);
+  if (j >= t.q) return;
+  C2* gi = t.g + (long long)i * t.p;
+  C2* gj = t.g + (long long)j * t.p;
+  C2 x[R], y[R];
+  S sa = 0, sb = 0, cx = 0, cy = 0;
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    const int r = threadIdx.x + k * JC_THREADS;
+    if (r < t.p) {
+      x[k] = gi[r];
+      y[k] = gj[r];
+    } else {
+      x[k].x = x[k].y = y[k].x = y[k].y = S(0);
     }
   }
-  if (threadIdx.x == 0 && rotated) atomicOr(&flag_now[wk.x], 1);
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    sa = fma(x[k].x, x[k].x, fma(x[k].y, x[k].y, sa));
+    sb = fma(y[k].x, y[k].x, fma(y[k].y, y[k].y, sb));
+    cx = fma(x[k].x, y[k].x, fma(x[k].y, y[k].y, cx));
+    cy = fma(x[k].x, y[k].y, fma(-x[k].y, y[k].x, cy));
+  }
+  __shared__ S sh[4 * (JC_THREADS / 32)];
+  block_sum4(sa, sb, cx, cy, sh);
+  const S ac = sqrt(cx * cx + cy * cy);
+  if (ac == S(0) || ac <= tol * sqrt(sa * sb)) return;  // uniform: every thread holds the same sums
+  const S zeta = (sb - sa) / (S(2) * ac);
+  const S tt = (zeta >= 0 ? S(1) : S(-1)) / (fabs(zeta) + sqrt(S(1) + zeta * zeta));
+  const S cs = S(1) / sqrt(S(1) + tt * tt), sn = cs * tt;
+  const S ex = cx / ac, ey = cy / ac;
+  // g_i' = cs g_i - sn conj(e) g_j ; g_j' = sn e g_i + cs g_j
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    const int r = threadIdx.x + k * JC_THREADS;
+    if (r < t.p) {
+      const C2 a = x[k], b = y[k];
+      C2 u, v;
+      u.x = cs * a.x - sn * (ex * b.x + ey * b.y);
+      u.y = cs * a.y - sn * (ex * b.y - ey * b.x);
+      v.x = sn * (ex * a.x - ey * a.y) + cs * b.x;
+      v.y = sn * (ex * a.y + ey * a.x) + cs * b.y;
+      gi[r] = u;
+      gj[r] = v;
+    }
+  }
+  if (t.v) {
+    C2* vi = t.v + (long long)i * t.q;
+    C2* vj = t.v + (long long)j * t.q;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int r = threadIdx.x + k * JC_THREADS;
+      if (r < t.q) {
+        const C2 a = vi[r], b = vj[r];
+        C2 u, v;
+        u.x = cs * a.x - sn * (ex * b.x + ey * b.y);
+        u.y = cs * a.y - sn * (ex * b.y - ey * b.x);
+        v.x = sn * (ex * a.x - ey * a.y) + cs * b.x;
+        v.y = sn * (ex * a.y + ey * a.x) + cs * b.y;
+        vi[r] = u;
+        vj[r] = v;
+      }
+    }
+  }
+  if (threadIdx.x == 0 && ac > tol_flag * sqrt(sa * sb) && ac > abs_flag) atomicOr(&flag_now[wk.x], 1);
+}
+
+// one round for every active pair: the CTA-per-pair kernel sized to the longest
+// column (rows per thread R = 1 .. 16), or the warp-per-pair kernel beyond that
+template <class Task, class S, class C2>
+static void launch_round(const Task* d_tasks, const int2* d_work, int nw, int round, S tol, S tol_flag, S abs_flag,
+                         int* now, const int* prev, int pmax, cudaStream_t s);
+
+// Pairs (task, k) sorted by task size descending, and per round the number of
+// leading pairs whose task still has that round.
+template <class Task>
+static void pair_schedule(const std::vector<Task>& h_tasks, std::vector<int2>& work, std::vector<int>& active) {
+  std::vector<int> ord(h_tasks.size());
+  for (size_t i = 0; i < ord.size(); ++i) ord[i] = (int)i;
+  std::sort(ord.begin(), ord.end(), [&](int x, int y) {
+    return h_tasks[x].q != h_tasks[y].q ? h_tasks[x].q > h_tasks[y].q : x < y;
+  });
+  work.clear();
+  std::vector<int> nround;  // rounds of the task of each work item
+  for (int i : ord) {
+    const int q = h_tasks[i].q;
+    if (q < 2) continue;
+    const int n = q + (q & 1);
+    for (int k = 0; k < n / 2; ++k) {
+      work.push_back(make_int2(i, k));
+      nround.push_back(n - 1);
+    }
+  }
+  const int max_rounds = nround.empty() ? 0 : nround[0];
+  active.assign(max_rounds, 0);
+  for (int r = 0; r < max_rounds; ++r) {
+    int c = 0;
+    while (c < (int)nround.size() && nround[c] > r) ++c;
+    active[r] = c;
+  }
 }
 
 // V = identity for every problem
@@ -654,48 +782,70 @@ __global__ void __launch_bounds__(256) svd_finish_kernel(const SvdTask* __restri
   }
 }
 
-// Blocked Jacobi driver: returns the number of sweeps used (host loop, one sync per sweep).
-// V is accumulated (from the identity) when the tasks carry v; without v only G is
-// rotated.  A sweep in which no rotation exceeded tol_flag (relative, as tol) ends
-// the iteration: with tol_flag = tol that is the usual "no rotation at all" test,
-// with tol_flag = sqrt(tol) it relies on the quadratic convergence of cyclic Jacobi
-// (off-diagonal delta before a sweep leaves O(delta^2) after it).
-int run_blocked_jacobi(const SvdTask* d_tasks, const std::vector<SvdTask>& h_tasks, int max_sweeps, double tol,
-                       int* status, cudaStream_t s, double tol_flag) {
+template <class Task, class S, class C2, int R>
+static void launch_cta(const Task* d_tasks, const int2* d_work, int nw, int round, S tol, S tol_flag, S abs_flag,
+                       int* now, const int* prev, cudaStream_t s) {
+  note_launch();
+  jacobi_cta_kernel<Task, S, C2, R><<<nw, JC_THREADS, 0, s>>>(d_tasks, d_work, round, tol, tol_flag, abs_flag, now,
+                                                               prev);
+}
+
+template <>
+void launch_round<SvdTask, double, cplx>(const SvdTask* d_tasks, const int2* d_work, int nw, int round, double tol,
+                                         double tol_flag, double abs_flag, int* now, const int* prev, int pmax,
+                                         cudaStream_t s) {
+  if (pmax <= JC_THREADS)
+    launch_cta<SvdTask, double, cplx, 1>(d_tasks, d_work, nw, round, tol, tol_flag, abs_flag, now, prev, s);
+  else if (pmax <= 2 * JC_THREADS)
+    launch_cta<SvdTask, double, cplx, 2>(d_tasks, d_work, nw, round, tol, tol_flag, abs_flag, now, prev, s);
+  else if (pmax <= 4 * JC_THREADS)
+    launch_cta<SvdTask, double, cplx, 4>(d_tasks, d_work, nw, round, tol, tol_flag, abs_flag, now, prev, s);
+  else if (pmax <= 8 * JC_THREADS)
+    launch_cta<SvdTask, double, cplx, 8>(d_tasks, d_work, nw, round, tol, tol_flag, abs_flag, now, prev, s);
+  else if (pmax <= 16 * JC_THREADS)
+    launch_cta<SvdTask, double, cplx, 16>(d_tasks, d_work, nw, round, tol, tol_flag, abs_flag, now, prev, s);
+  else {
+    note_launch();
+    jacobi_pair_kernel<<<(nw + PAIR_WARPS - 1) / PAIR_WARPS, PAIR_WARPS * 32, 0, s>>>(d_tasks, d_work, nw, round, tol,
+                                                                                     tol_flag, abs_flag, now, prev);
+  }
+}
+
+// Round-robin Jacobi driver: returns the number of sweeps run (host loop, one sync
+// per sweep).  V is accumulated (from the identity) when the tasks carry v; without
+// v only G is rotated.  Pairs rotate when |g_i^H g_j| > tol |g_i||g_j|.  A sweep in
+// which no rotation had |g_i^H g_j| above both tol_flag |g_i||g_j| and abs_flag ends
+// the iteration: with tol_flag = tol and abs_flag = 0 that is the usual "no
+// rotation at all" test; tol_flag = sqrt(tol) relies on the quadratic convergence of
+// cyclic Jacobi (off-diagonal delta before a sweep leaves O(delta^2) after it), and
+// abs_flag > 0 ignores pairs whose coupling is negligible on the scale of the whole
+// matrix (the split passes unit-norm theta, so abs_flag is a weight).
+int run_jacobi_rounds(const SvdTask* d_tasks, const std::vector<SvdTask>& h_tasks, int max_sweeps, double tol,
+                      int* status, cudaStream_t s, double tol_flag, double abs_flag) {
   const int nt = (int)h_tasks.size();
   if (nt == 0) return 0;
   if (!(tol_flag >= tol)) tol_flag = tol;
-  int pmax = 1, qmax = 1;
+  int qmax = 1, pmax = 1;
   for (auto& t : h_tasks) {
-    pmax = max(pmax, t.p);
     qmax = max(qmax, t.q);
+    pmax = max(pmax, t.p);
   }
-  const int vrows = h_tasks[0].v ? qmax : 0;
-  // widest block (<= 32 columns) whose pair of column copies fits in shared memory
-  int bw = 32;
-  while (bw > 1 && (size_t)2 * bw * (pmax + vrows) * sizeof(cplx) > 200 * 1024) bw >>= 1;
-  if ((size_t)2 * bw * (pmax + vrows) * sizeof(cplx) > 200 * 1024) return -1;  // caller falls back
-  const size_t smem = (size_t)2 * bw * (pmax + vrows) * sizeof(cplx);
-  cudaFuncSetAttribute(bjacobi_round_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   std::vector<int2> work;
-  int max_rounds = 0;
-  for (int i = 0; i < nt; ++i) {
-    int nb0 = (h_tasks[i].q + bw - 1) / bw, nb = nb0 + (nb0 & 1);
-    for (int k = 0; k < nb / 2; ++k) work.push_back(make_int2(i, k));
-    max_rounds = max(max_rounds, nb - 1);
-  }
+  std::vector<int> active;
+  pair_schedule(h_tasks, work, active);
   int2* d_work = nullptr;
   int* flags = nullptr;
-  cudaMallocAsync(&d_work, work.size() * sizeof(int2), s);
+  cudaMallocAsync(&d_work, (work.empty() ? 1 : work.size()) * sizeof(int2), s);
   cudaMallocAsync(&flags, 2 * nt * sizeof(int), s);
-  cudaMemcpyAsync(d_work, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+  if (!work.empty()) cudaMemcpyAsync(d_work, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+  note_launch();
   svd_init_v_kernel<<<nt, 256, 0, s>>>(d_tasks);
   std::vector<int> hf(nt);
   int sweep = 0, *prev = nullptr, *now = flags;
-  for (; sweep < max_sweeps; ++sweep) {
+  for (; sweep < max_sweeps && !work.empty(); ++sweep) {
     cudaMemsetAsync(now, 0, nt * sizeof(int), s);
-    for (int r = 0; r < max_rounds; ++r)
-      bjacobi_round_kernel<<<(int)work.size(), 256, smem, s>>>(d_tasks, d_work, r, bw, tol, tol_flag, now, prev);
+    for (int r = 0; r < (int)active.size(); ++r)
+      launch_round<SvdTask, double, cplx>(d_tasks, d_work, active[r], r, tol, tol_flag, abs_flag, now, prev, pmax, s);
     cudaMemcpyAsync(hf.data(), now, nt * sizeof(int), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
     bool any = false;
@@ -711,14 +861,16 @@ int run_blocked_jacobi(const SvdTask* d_tasks, const std::vector<SvdTask>& h_tas
   }
   size_t fs = (size_t)qmax * sizeof(double);
   if (fs > 48 * 1024) cudaFuncSetAttribute(svd_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fs);
+  note_launch();
   svd_finish_kernel<<<nt, 256, fs, s>>>(d_tasks);
   cudaFreeAsync(d_work, s);
   cudaFreeAsync(flags, s);
-  return sweep;
+  if (work.empty()) return 1;
+  return sweep < max_sweeps ? sweep + 1 : max_sweeps;  // sweeps run, the last one included
 }
 
 // ---------------------------------------------------------------------------
-// K6 (FP32 preconditioner): blocked one-sided Jacobi on a complex64 copy of G with
+// K6 (FP32 preconditioner): round-robin one-sided Jacobi on a complex64 copy of G with
 // the right rotations accumulated in a complex64 V.  Used by the split-precision
 // modes: V is widened to FP64, G = A V is formed again in FP64 and a short FP64
 // Jacobi finishes the SVD, so every singular value the truncation sees is an FP64
@@ -761,66 +913,33 @@ __device__ void rotate32(float2* __restrict__ g, int ld, int len, int i, int j, 
   }
 }
 
-__global__ void __launch_bounds__(256) bjacobi32_round_kernel(const Svd32Task* __restrict__ tasks,
-                                                              const int2* __restrict__ work, int round, int bw,
-                                                              float tol, int* __restrict__ flag_now,
-                                                              const int* __restrict__ flag_prev) {
-  const int2 wk = work[blockIdx.x];
-  const Svd32Task t = tasks[wk.x];
+__global__ void __launch_bounds__(PAIR_WARPS * 32) jacobi_pair32_kernel(const Svd32Task* __restrict__ tasks,
+                                                                        const int2* __restrict__ work, int nwork,
+                                                                        int round, float tol, float abs_flag,
+                                                                        int* __restrict__ flag_now,
+                                                                        const int* __restrict__ flag_prev) {
+  const int w = blockIdx.x * PAIR_WARPS + (threadIdx.x >> 5);
+  if (w >= nwork) return;
+  const int2 wk = work[w];
   if (flag_prev && flag_prev[wk.x] == 0) return;
-  const int nb0 = (t.q + bw - 1) / bw;
-  const int nb = nb0 + (nb0 & 1);
-  if (nb < 2 || round >= nb - 1) return;
-  int I, Jb;
-  tourney(round, wk.y, nb, I, Jb);
-  const int p = t.p, q = t.q;
-  extern __shared__ float2 sg[];
-  float2* sv = sg + (size_t)2 * bw * p;  // V columns after the G columns
-  int ncol = 0;
-  int col[64];
-  for (int c = 0; c < bw; ++c)
-    if (I * bw + c < q) col[ncol++] = I * bw + c;
-  for (int c = 0; c < bw; ++c)
-    if (Jb * bw + c < q) col[ncol++] = Jb * bw + c;
-  if (ncol < 2) return;
-  for (int cc = 0; cc < ncol; ++cc) {
-    const float2* g = t.g + (long long)col[cc] * p;
-    const float2* v = t.v + (long long)col[cc] * q;
-    for (int r = threadIdx.x; r < p; r += blockDim.x) sg[(size_t)cc * p + r] = g[r];
-    for (int r = threadIdx.x; r < q; r += blockDim.x) sv[(size_t)cc * q + r] = v[r];
-  }
-  __shared__ int rotated;
-  if (threadIdx.x == 0) rotated = 0;
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  const int nn = ncol + (ncol & 1);
-  for (int r = 0; r < nn - 1; ++r) {
-    for (int k = warp; k < nn / 2; k += nwarp) {
-      int i, j;
-      tourney(r, k, nn, i, j);
-      if (j >= ncol) continue;
-      float a, b;
-      float2 c;
-      col_pair32(sg, p, i, j, a, b, c);
-      float ac = sqrtf(c.x * c.x + c.y * c.y);
-      if (ac == 0.0f || ac <= tol * sqrtf(a * b)) continue;
-      float zeta = (b - a) / (2.0f * ac);
-      float tt = (zeta >= 0 ? 1.0f : -1.0f) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta));
-      float cs = 1.0f / sqrtf(1.0f + tt * tt), sn = cs * tt;
-      float2 e = make_float2(c.x / ac, c.y / ac);
-      rotate32(sg, p, p, i, j, cs, sn, e);
-      rotate32(sv, q, q, i, j, cs, sn, e);
-      if ((threadIdx.x & 31) == 0) rotated = 1;
-    }
-    __syncthreads();
-  }
-  for (int cc = 0; cc < ncol; ++cc) {
-    float2* g = t.g + (long long)col[cc] * p;
-    float2* v = t.v + (long long)col[cc] * q;
-    for (int r = threadIdx.x; r < p; r += blockDim.x) g[r] = sg[(size_t)cc * p + r];
-    for (int r = threadIdx.x; r < q; r += blockDim.x) v[r] = sv[(size_t)cc * q + r];
-  }
-  if (threadIdx.x == 0 && rotated) atomicOr(&flag_now[wk.x], 1);
+  const Svd32Task t = tasks[wk.x];
+  const int n = t.q + (t.q & 1);
+  if (round >= n - 1) return;
+  int i, j;
+  tourney(round, wk.y, n, i, j);
+  if (j >= t.q) return;
+  float a, b;
+  float2 c;
+  col_pair32(t.g, t.p, i, j, a, b, c);
+  const float ac = sqrtf(c.x * c.x + c.y * c.y);
+  if (ac == 0.0f || ac <= tol * sqrtf(a * b)) return;
+  const float zeta = (b - a) / (2.0f * ac);
+  const float tt = (zeta >= 0 ? 1.0f : -1.0f) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta));
+  const float cs = 1.0f / sqrtf(1.0f + tt * tt), sn = cs * tt;
+  const float2 e = make_float2(c.x / ac, c.y / ac);
+  rotate32(t.g, t.p, t.p, i, j, cs, sn, e);
+  rotate32(t.v, t.q, t.q, i, j, cs, sn, e);
+  if ((threadIdx.x & 31) == 0 && ac > abs_flag) atomicOr(&flag_now[wk.x], 1);
 }
 
 __global__ void svd32_init_v_kernel(const Svd32Task* __restrict__ tasks) {
@@ -829,39 +948,49 @@ __global__ void svd32_init_v_kernel(const Svd32Task* __restrict__ tasks) {
     t.v[e] = make_float2((e % t.q) == (e / t.q) ? 1.0f : 0.0f, 0.0f);
 }
 
-int run_blocked_jacobi32(const Svd32Task* d_tasks, const std::vector<Svd32Task>& h_tasks, int max_sweeps, float tol,
-                         cudaStream_t s) {
+template <>
+void launch_round<Svd32Task, float, float2>(const Svd32Task* d_tasks, const int2* d_work, int nw, int round, float tol,
+                                            float tol_flag, float abs_flag, int* now, const int* prev, int pmax,
+                                            cudaStream_t s) {
+  if (pmax <= JC_THREADS)
+    launch_cta<Svd32Task, float, float2, 1>(d_tasks, d_work, nw, round, tol, tol_flag, abs_flag, now, prev, s);
+  else if (pmax <= 2 * JC_THREADS)
+    launch_cta<Svd32Task, float, float2, 2>(d_tasks, d_work, nw, round, tol, tol_flag, abs_flag, now, prev, s);
+  else if (pmax <= 4 * JC_THREADS)
+    launch_cta<Svd32Task, float, float2, 4>(d_tasks, d_work, nw, round, tol, tol_flag, abs_flag, now, prev, s);
+  else if (pmax <= 8 * JC_THREADS)
+    launch_cta<Svd32Task, float, float2, 8>(d_tasks, d_work, nw, round, tol, tol_flag, abs_flag, now, prev, s);
+  else if (pmax <= 16 * JC_THREADS)
+    launch_cta<Svd32Task, float, float2, 16>(d_tasks, d_work, nw, round, tol, tol_flag, abs_flag, now, prev, s);
+  else {
+    note_launch();
+    jacobi_pair32_kernel<<<(nw + PAIR_WARPS - 1) / PAIR_WARPS, PAIR_WARPS * 32, 0, s>>>(d_tasks, d_work, nw, round,
+                                                                                       tol, abs_flag, now, prev);
+  }
+}
+
+int run_jacobi_rounds32(const Svd32Task* d_tasks, const std::vector<Svd32Task>& h_tasks, int max_sweeps, float tol,
+                        float abs_flag, cudaStream_t s) {
   const int nt = (int)h_tasks.size();
   if (nt == 0) return 0;
-  int pmax = 1, qmax = 1;
-  for (auto& t : h_tasks) {
-    pmax = max(pmax, t.p);
-    qmax = max(qmax, t.q);
-  }
-  int bw = 32;
-  while (bw > 1 && (size_t)2 * bw * (pmax + qmax) * sizeof(float2) > 200 * 1024) bw >>= 1;
-  if ((size_t)2 * bw * (pmax + qmax) * sizeof(float2) > 200 * 1024) return -1;
-  const size_t smem = (size_t)2 * bw * (pmax + qmax) * sizeof(float2);
-  cudaFuncSetAttribute(bjacobi32_round_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int pmax = 1;
+  for (auto& t : h_tasks) pmax = max(pmax, t.p);
   std::vector<int2> work;
-  int max_rounds = 0;
-  for (int i = 0; i < nt; ++i) {
-    int nb0 = (h_tasks[i].q + bw - 1) / bw, nb = nb0 + (nb0 & 1);
-    for (int k = 0; k < nb / 2; ++k) work.push_back(make_int2(i, k));
-    max_rounds = max(max_rounds, nb - 1);
-  }
+  std::vector<int> active;
+  pair_schedule(h_tasks, work, active);
   int2* d_work = nullptr;
   int* flags = nullptr;
   cudaMallocAsync(&d_work, (work.empty() ? 1 : work.size()) * sizeof(int2), s);
   cudaMallocAsync(&flags, 2 * nt * sizeof(int), s);
   if (!work.empty()) cudaMemcpyAsync(d_work, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+  note_launch();
   svd32_init_v_kernel<<<nt, 256, 0, s>>>(d_tasks);
   std::vector<int> hf(nt);
   int sweep = 0, *prev = nullptr, *now = flags;
   for (; sweep < max_sweeps && !work.empty(); ++sweep) {
     cudaMemsetAsync(now, 0, nt * sizeof(int), s);
-    for (int r = 0; r < max_rounds; ++r)
-      bjacobi32_round_kernel<<<(int)work.size(), 256, smem, s>>>(d_tasks, d_work, r, bw, tol, now, prev);
+    for (int r = 0; r < (int)active.size(); ++r)
+      launch_round<Svd32Task, float, float2>(d_tasks, d_work, active[r], r, tol, 0.0f, abs_flag, now, prev, pmax, s);
     cudaMemcpyAsync(hf.data(), now, nt * sizeof(int), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
     bool any = false;
@@ -872,7 +1001,8 @@ int run_blocked_jacobi32(const Svd32Task* d_tasks, const std::vector<Svd32Task>&
   }
   cudaFreeAsync(d_work, s);
   cudaFreeAsync(flags, s);
-  return sweep;
+  if (work.empty()) return 1;
+  return sweep < max_sweeps ? sweep + 1 : max_sweeps;
 }
 
 // precision conversions of whole buffers
@@ -915,16 +1045,28 @@ static int conv_grid(long long n) {
   return (int)(b < 1184 ? (b < 1 ? 1 : b) : 1184);
 }
 void launch_narrow(const cplx* src, float2* dst, long long n, cudaStream_t s) {
-  if (n > 0) narrow_kernel<<<conv_grid(n), 256, 0, s>>>(src, dst, n);
+  if (n > 0) {
+    note_launch();
+    narrow_kernel<<<conv_grid(n), 256, 0, s>>>(src, dst, n);
+  }
 }
 void launch_widen(const float2* src, cplx* dst, long long n, cudaStream_t s) {
-  if (n > 0) widen_kernel<<<conv_grid(n), 256, 0, s>>>(src, dst, n);
+  if (n > 0) {
+    note_launch();
+    widen_kernel<<<conv_grid(n), 256, 0, s>>>(src, dst, n);
+  }
 }
 void launch_basis64(const BasisTask* tasks, int n, cudaStream_t s) {
-  if (n > 0) basis64_kernel<<<dim3(32, n), 256, 0, s>>>(tasks);
+  if (n > 0) {
+    note_launch();
+    basis64_kernel<<<dim3(32, n), 256, 0, s>>>(tasks);
+  }
 }
 void launch_ns_coeff(const NsTask* tasks, int n, cudaStream_t s) {
-  if (n > 0) ns_coeff_kernel<<<dim3(8, n), 256, 0, s>>>(tasks);
+  if (n > 0) {
+    note_launch();
+    ns_coeff_kernel<<<dim3(8, n), 256, 0, s>>>(tasks);
+  }
 }
 
 void launch_jacobi_svd(const SvdTask* tasks, int ntasks, int max_q, int max_sweeps, double tol, int* status,
@@ -932,6 +1074,7 @@ void launch_jacobi_svd(const SvdTask* tasks, int ntasks, int max_q, int max_swee
   if (ntasks <= 0) return;
   size_t smem = (size_t)max_q * sizeof(double);
   if (smem > 48 * 1024) cudaFuncSetAttribute(jacobi_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  note_launch();
   jacobi_svd_kernel<<<ntasks, SVD_THREADS, smem, s>>>(tasks, max_sweeps, tol, status);
 }
 
@@ -939,73 +1082,160 @@ void launch_jacobi_svd(const SvdTask* tasks, int ntasks, int max_q, int max_swee
 // K7: truncation selection over all sectors of a bond (one CTA)
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(1024) truncate_kernel(const TruncSector* __restrict__ secs, int nsec,
-                                                        const int* __restrict__ offs, int n, double eps,
-                                                        long long chi_max, int* __restrict__ owner,
-                                                        int* __restrict__ order, int* __restrict__ kept,
-                                                        double* __restrict__ stats) {
-  // owner[e] = sector of flat entry e ; offs[s] = first flat index of sector s
-  for (int s = threadIdx.x; s < nsec; s += blockDim.x) {
-    for (int i = 0; i < secs[s].r; ++i) owner[offs[s] + i] = s;
-    kept[s] = 0;
+// One CTA of TRUNC_THREADS threads.  Flat entry e of sector s is e = offs[s] + i.
+// 1. stage value, sector and multiplet size of every entry (NaN ranks last, weight 0);
+// 2. rank every entry (descending value, ties by flat index) against shared-memory
+//    tiles of the values, order[rank] = e;
+// 3. block scans over the sorted list: suffix sums of the weights s^2 (the tail
+//    rule) and prefix sums of the multiplet sizes (the chi cap);
+// 4. K = max(1, min(longest tail with weight <= eps * total, largest chi <= cap)),
+//    kept[s] = number of the first K sorted entries that belong to sector s.
+constexpr int TRUNC_THREADS = 1024;
+constexpr int TRUNC_TILE = 2048;
+constexpr int TRUNC_PER = 8;  // entries ranked per thread per pass
+
+template <class T>
+__device__ T block_exclusive_scan(T v, T* sh, T& total) {
+  // sh: TRUNC_THREADS / 32 + 1 entries
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    T y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    T w = lane < TRUNC_THREADS / 32 ? sh[lane] : T(0);
+    for (int o = 1; o < 32; o <<= 1) {
+      T y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < TRUNC_THREADS / 32) sh[lane] = w;  // inclusive over warps
+    if (lane == TRUNC_THREADS / 32 - 1) sh[TRUNC_THREADS / 32] = w;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < n; e += blockDim.x) {
-    int se = owner[e];
-    double ve = secs[se].sv[e - offs[se]];
-    if (!(ve == ve)) ve = -1.0;
-    int rank = 0;
-    for (int f = 0; f < n; ++f) {
-      int sf = owner[f];
-      double vf = secs[sf].sv[f - offs[sf]];
-      if (!(vf == vf)) vf = -1.0;
-      rank += (vf > ve) || (vf == ve && f < e);
+  T before = (warp > 0 ? sh[warp - 1] : T(0)) + x - v;
+  total = sh[TRUNC_THREADS / 32];
+  __syncthreads();
+  return before;
+}
+
+__global__ void __launch_bounds__(TRUNC_THREADS) truncate_kernel(const TruncSector* __restrict__ secs, int nsec,
+                                                                 const int* __restrict__ offs, int n, double eps,
+                                                                 long long chi_max, int* __restrict__ owner,
+                                                                 int* __restrict__ order, int* __restrict__ kept,
+                                                                 double* __restrict__ stats,
+                                                                 double* __restrict__ vals) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int sct = warp; sct < nsec; sct += TRUNC_THREADS / 32) {
+    const TruncSector t = secs[sct];
+    for (int i = lane; i < t.r; i += 32) {
+      double v = t.sv[i];
+      owner[offs[sct] + i] = sct;
+      vals[offs[sct] + i] = (v == v) ? v : -1.0;
     }
-    order[rank] = e;
+    if (lane == 0) kept[sct] = 0;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double total = 0.0;
-    for (int r = 0; r < n; ++r) {
-      int e = order[r], se = owner[e];
-      double v = secs[se].sv[e - offs[se]];
-      total += v * v;
+  __shared__ double tile[TRUNC_TILE];
+  for (int e0 = 0; e0 < n; e0 += TRUNC_THREADS * TRUNC_PER) {
+    double mine[TRUNC_PER];
+    int rank[TRUNC_PER];
+#pragma unroll
+    for (int j = 0; j < TRUNC_PER; ++j) {
+      int e = e0 + j * TRUNC_THREADS + tid;
+      mine[j] = e < n ? vals[e] : 0.0;
+      rank[j] = 0;
     }
-    // longest tail with weight <= eps * total
-    int keep_eps = n;
-    double tail = 0.0;
-    for (int r = n - 1; r >= 1; --r) {
-      int e = order[r], se = owner[e];
-      double v = secs[se].sv[e - offs[se]];
-      if (tail + v * v <= eps * total) {
-        tail += v * v;
-        keep_eps = r;
-      } else {
-        break;
+    for (int f0 = 0; f0 < n; f0 += TRUNC_TILE) {
+      const int m = min(TRUNC_TILE, n - f0);
+      __syncthreads();
+      for (int f = tid; f < m; f += TRUNC_THREADS) tile[f] = vals[f0 + f];
+      __syncthreads();
+      for (int f = 0; f < m; ++f) {
+        const double vf = tile[f];
+        const int gf = f0 + f;
+#pragma unroll
+        for (int j = 0; j < TRUNC_PER; ++j) {
+          const int e = e0 + j * TRUNC_THREADS + tid;
+          rank[j] += (vf > mine[j]) || (vf == mine[j] && gf < e);
+        }
       }
     }
-    // bond-dimension cap with multiplet sizes, greedy in descending order
-    long long chi = 0;
-    int keep_chi = 0;
-    for (int r = 0; r < n; ++r) {
-      int se = owner[order[r]];
-      if (r > 0 && chi + secs[se].mult > chi_max) break;
-      chi += secs[se].mult;
-      keep_chi = r + 1;
+#pragma unroll
+    for (int j = 0; j < TRUNC_PER; ++j) {
+      int e = e0 + j * TRUNC_THREADS + tid;
+      if (e < n) order[rank[j]] = e;
     }
-    int K = keep_eps < keep_chi ? keep_eps : keep_chi;
-    if (K < 1) K = 1;
-    double kw = 0.0;
-    long long kchi = 0;
-    for (int r = 0; r < K; ++r) {
-      int e = order[r], se = owner[e];
-      double v = secs[se].sv[e - offs[se]];
-      kw += v * v;
-      kchi += secs[se].mult;
-      kept[se] += 1;
+  }
+  __syncthreads();
+  // sorted entries in contiguous runs per thread: r in [r0, r1)
+  const int per = (n + TRUNC_THREADS - 1) / TRUNC_THREADS;
+  const int r0 = min(n, tid * per), r1 = min(n, r0 + per);
+  double wloc = 0.0;
+  long long mloc = 0;
+  for (int r = r0; r < r1; ++r) {
+    double v = vals[order[r]];
+    wloc += v > 0.0 ? v * v : 0.0;
+    mloc += secs[owner[order[r]]].mult;
+  }
+  __shared__ double shd[TRUNC_THREADS / 32 + 1];
+  __shared__ long long shl[TRUNC_THREADS / 32 + 1];
+  double total;
+  long long mtot;
+  const double wbefore = block_exclusive_scan(wloc, shd, total);
+  const long long mbefore = block_exclusive_scan(mloc, shl, mtot);
+  (void)mtot;
+  __shared__ int keep_eps, keep_chi;
+  if (tid == 0) {
+    keep_eps = n;
+    keep_chi = 1;
+  }
+  __syncthreads();
+  // tail rule: the smallest r >= 1 whose suffix sum sum_{r' >= r} w is <= eps * total
+  {
+    // suffix within the run accumulated from the run's end, plus everything after the run
+    double run_tail = 0.0;
+    int best = n;
+    for (int r = r1 - 1; r >= r0; --r) {
+      double v = vals[order[r]];
+      run_tail += v > 0.0 ? v * v : 0.0;
+      double suf = (total - wbefore - wloc) + run_tail;  // sum over r' >= r
+      if (r >= 1 && suf <= eps * total) best = r;
     }
+    if (best < n) atomicMin(&keep_eps, best);
+  }
+  // chi cap: the largest K with sum_{r < K} mult <= chi_max (K >= 1)
+  {
+    long long pre = mbefore;
+    int best = 0;
+    for (int r = r0; r < r1; ++r) {
+      pre += secs[owner[order[r]]].mult;
+      if (pre <= chi_max) best = r + 1;
+    }
+    if (best > 0) atomicMax(&keep_chi, best);
+  }
+  __syncthreads();
+  int K = keep_eps < keep_chi ? keep_eps : keep_chi;
+  if (K < 1) K = 1;
+  double kwl = 0.0;
+  long long kcl = 0;
+  for (int r = r0; r < r1 && r < K; ++r) {
+    const int e = order[r];
+    const int sct = owner[e];
+    double v = vals[e];
+    kwl += v > 0.0 ? v * v : 0.0;
+    kcl += secs[sct].mult;
+    atomicAdd(&kept[sct], 1);
+  }
+  double kw;
+  long long kchi;
+  block_exclusive_scan(kwl, shd, kw);
+  block_exclusive_scan(kcl, shl, kchi);
+  if (tid == 0) {
     stats[0] = total;
-    stats[1] = total - kw;           // discarded weight
+    stats[1] = total - kw;                     // discarded weight
     stats[2] = kw > 0 ? 1.0 / sqrt(kw) : 0.0;  // renormalisation of the kept values
     stats[3] = (double)K;
     stats[4] = (double)kchi;
@@ -1014,7 +1244,11 @@ __global__ void __launch_bounds__(1024) truncate_kernel(const TruncSector* __res
 
 void launch_truncate(const TruncSector* secs, int nsec, const int* offs, int n, double eps, long long chi_max,
                      int* owner, int* order, int* kept, double* stats, cudaStream_t s) {
-  truncate_kernel<<<1, 1024, 0, s>>>(secs, nsec, offs, n, eps, chi_max, owner, order, kept, stats);
+  double* vals = nullptr;
+  cudaMallocAsync(&vals, (size_t)(n > 0 ? n : 1) * sizeof(double), s);
+  note_launch();
+  truncate_kernel<<<1, TRUNC_THREADS, 0, s>>>(secs, nsec, offs, n, eps, chi_max, owner, order, kept, stats, vals);
+  cudaFreeAsync(vals, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -1055,7 +1289,9 @@ __global__ void wdot_final_kernel(const DotTask* __restrict__ tasks, const doubl
 
 void launch_wdot(const DotTask* tasks, int ntasks, double* partial, double* out, int nslots, cudaStream_t s) {
   if (ntasks <= 0) return;
+  note_launch();
   wdot_kernel<<<ntasks, 256, 0, s>>>(tasks, partial);
+  note_launch();
   wdot_final_kernel<<<1, 256, 0, s>>>(tasks, partial, ntasks, out, nslots);
 }
 
@@ -1101,6 +1337,7 @@ __global__ void fill_normal_kernel(cplx* __restrict__ p, long long n, unsigned l
 
 void launch_fill_normal(cplx* p, long long n, unsigned long long seed, long long offset, cudaStream_t s) {
   if (n <= 0) return;
+  note_launch();
   fill_normal_kernel<<<blas_grid(n), 256, 0, s>>>(p, n, seed, offset);
 }
 
@@ -1126,10 +1363,12 @@ __global__ void entropy_sv_kernel(const TruncSector* __restrict__ secs, int nsec
 }
 
 void launch_entropy_sv(const TruncSector* secs, int nsec, const double* g, double* out, cudaStream_t s) {
+  note_launch();
   entropy_sv_kernel<<<1, 256, 0, s>>>(secs, nsec, g, out);
 }
 
 void launch_entropy(const TruncSector* secs, int nsec, double* out, cudaStream_t s) {
+  note_launch();
   entropy_kernel<<<1, 256, 0, s>>>(secs, nsec, out);
 }
 

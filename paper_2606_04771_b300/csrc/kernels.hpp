@@ -8,6 +8,11 @@
 
 namespace tdvp {
 
+// Process-wide count of kernel launches made by this library (every launch site
+// calls note_launch()); read through tdvp_launch_count.
+void note_launch(int n = 1);
+long long launch_count();
+
 constexpr int LINCOMB_CHUNK = 1024;  // elements per CTA in lincomb / copy
 constexpr int KRYLOV_MAX = 32;       // one warp holds the Krylov coefficients
 
@@ -53,18 +58,18 @@ void launch_krylov_step(KrylovState* st, const cplx* h1, const cplx* nrm2, doubl
 
 void launch_jacobi_svd(const SvdTask* tasks, int ntasks, int max_q, int max_sweeps, double tol, int* status,
                        cudaStream_t s);
-// FP32 blocked Jacobi on complex64 working copies, accumulating V (from the
-// identity); returns the sweeps used or -1 when the columns do not fit
-int run_blocked_jacobi32(const Svd32Task* d_tasks, const std::vector<Svd32Task>& h_tasks, int max_sweeps, float tol,
-                         cudaStream_t s);
+// FP32 round-robin Jacobi on complex64 working copies (p >= q), accumulating V
+// (from the identity); returns the sweeps run
+int run_jacobi_rounds32(const Svd32Task* d_tasks, const std::vector<Svd32Task>& h_tasks, int max_sweeps, float tol,
+                        float abs_flag, cudaStream_t s);
 void launch_narrow(const cplx* src, float2* dst, long long n, cudaStream_t s);
 void launch_widen(const float2* src, cplx* dst, long long n, cudaStream_t s);
 void launch_basis64(const BasisTask* tasks, int n, cudaStream_t s);
 void launch_ns_coeff(const NsTask* tasks, int n, cudaStream_t s);
-// blocked multi-CTA Jacobi (same result layout as launch_jacobi_svd); returns the sweeps
-// used, or -1 when the column blocks do not fit in shared memory (use launch_jacobi_svd)
-int run_blocked_jacobi(const SvdTask* d_tasks, const std::vector<SvdTask>& h_tasks, int max_sweeps, double tol,
-                       int* status, cudaStream_t s, double tol_flag = 0.0);
+// round-robin one-sided Jacobi over all tasks at once, one warp per column pair
+// (same result layout as launch_jacobi_svd; v may be NULL); returns the sweeps run
+int run_jacobi_rounds(const SvdTask* d_tasks, const std::vector<SvdTask>& h_tasks, int max_sweeps, double tol,
+                      int* status, cudaStream_t s, double tol_flag = 0.0, double abs_flag = 0.0);
 void launch_truncate(const TruncSector* secs, int nsec, const int* offs, int n, double eps, long long chi_max,
                      int* owner, int* order, int* kept, double* stats, cudaStream_t s);
 void launch_wdot(const DotTask* tasks, int ntasks, double* partial, double* out, int nslots, cudaStream_t s);

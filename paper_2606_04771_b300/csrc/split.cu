@@ -672,6 +672,7 @@ void launch_gemm_split(int kind, const GemmTask* tasks, const GemmSeg* segs, con
       cudaFuncSetAttribute(gemm_split_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       init = true;
     }
+    note_launch();
     gemm_split_kernel<0><<<ntiles, NTHREADS, sm, s>>>(tasks, segs, tiles, B, status);
   } else {
     static bool init = false;
@@ -680,6 +681,7 @@ void launch_gemm_split(int kind, const GemmTask* tasks, const GemmSeg* segs, con
       cudaFuncSetAttribute(gemm_exact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       init = true;
     }
+    note_launch();
     gemm_exact_kernel<<<ntiles, NTHREADS, sm, s>>>(tasks, segs, tiles, B, status);
   }
 }
