@@ -122,6 +122,15 @@ void HeffPlan::apply(const cplx* in, cplx* out, cudaStream_t s) const {
   g3.launch(s, B);
 }
 
+// a Jacobi driver's sweep count, or the CUDA error of a failed cooperative launch
+static int jacobi(int sweeps) {
+  if (sweeps < 0) {
+    cudaError_t e = cudaGetLastError();
+    throw Error(-6, std::string("cooperative Jacobi launch failed: ") + cudaGetErrorString(e));
+  }
+  return sweeps;
+}
+
 static inline cplx* as_off(long long off) { return reinterpret_cast<cplx*>(static_cast<uintptr_t>(off) * sizeof(cplx)); }
 
 // ---------------------------------------------------------------------------
@@ -413,7 +422,7 @@ void Engine::orthonormalize_cols(BTensor& T, const BondSpace& l, const BondSpace
   gather.finalize(stream_);
   gather.launch(stream_);
   DevBuf dt = upload(tasks, stream_);
-  run_jacobi_rounds(dt.as<SvdTask>(), tasks, 40, 1e-14, dstatus_, stream_);
+  jacobi(run_jacobi_rounds(dt.as<SvdTask>(), tasks, 40, 1e-14, dstatus_, stream_));
   scatter.finalize(stream_);
   scatter.launch(stream_);
   TDVP_CUDA(cudaStreamSynchronize(stream_));
@@ -483,7 +492,7 @@ void Engine::orthonormalize_rows(BTensor& T, const BondSpace& l, const BondSpace
   gather.finalize(stream_);
   gather.launch(stream_);
   DevBuf dt = upload(tasks, stream_);
-  run_jacobi_rounds(dt.as<SvdTask>(), tasks, 40, 1e-14, dstatus_, stream_);
+  jacobi(run_jacobi_rounds(dt.as<SvdTask>(), tasks, 40, 1e-14, dstatus_, stream_));
   scatter.finalize(stream_);
   scatter.launch(stream_);
   TDVP_CUDA(cudaStreamSynchronize(stream_));
@@ -1293,7 +1302,7 @@ double Engine::split(BTensor& theta, const BondSpace& bl, const BondSpace& br, l
     ts[g] = {Sp + soff[g], Q, M.mult_dim(groups[g].t)};
   }
   DevBuf dst = upload(st, stream_);
-  stats_.sweeps64 += run_jacobi_rounds(dst.as<SvdTask>(), st, 40, 1e-14, dstatus_, stream_);
+  stats_.sweeps64 += jacobi(run_jacobi_rounds(dst.as<SvdTask>(), st, 40, 1e-14, dstatus_, stream_));
   stats_.splits += 1;
   // truncation
   DevBuf dts = upload(ts, stream_);
@@ -1526,7 +1535,7 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
   DevBuf dst32 = upload(st32, stream_);
   // FP32 stage: rotate while |g_i^H g_j| > 2e-5 |g_i||g_j|, at most 24 sweeps (it
   // need not converge: the FP64 stage finishes whatever is left)
-  const int sw32 = run_jacobi_rounds32(dst32.as<Svd32Task>(), st32, 24, 2e-5f, 0.0f, stream_);
+  const int sw32 = jacobi(run_jacobi_rounds32(dst32.as<Svd32Task>(), st32, 24, 2e-5f, 0.0f, stream_));
   ok = true;
   stats_.sweeps32 += sw32;
   stats_.splits += 1;
@@ -1566,7 +1575,7 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
   // FP64 stage: rotate above 1e-13 (relative); stop after a sweep whose rotations were
   // all below 3e-7 relative (quadratic convergence leaves ~1e-13) or below 1e-11 in
   // absolute terms (theta has unit norm, so that is a weight far below any threshold)
-  stats_.sweeps64 += run_jacobi_rounds(dst.as<SvdTask>(), st, 30, 1e-13, dstatus_, stream_, 3e-7, 1e-11);
+  stats_.sweeps64 += jacobi(run_jacobi_rounds(dst.as<SvdTask>(), st, 30, 1e-13, dstatus_, stream_, 3e-7, 1e-11));
   DevBuf dts = upload(ts, stream_), doffs = upload(soff, stream_);
   DevBuf downer(std::max(stot, 1) * sizeof(int), stream_), dorder(std::max(stot, 1) * sizeof(int), stream_);
   DevBuf dkept(std::max(ng, 1) * sizeof(int), stream_), dstats(8 * sizeof(double), stream_);
@@ -2084,7 +2093,7 @@ void Engine::measure(double* n_out, double* sz_out, double* docc_out, double* s_
         ts[b] = {dS.as<double>() + so[b], br.s[b].d, M.mult_dim(br.s[b].t)};
       }
       DevBuf dst = upload(st, stream_), dts2 = upload(ts, stream_);
-      run_jacobi_rounds(dst.as<SvdTask>(), st, 40, 1e-14, dstatus_, stream_);
+      jacobi(run_jacobi_rounds(dst.as<SvdTask>(), st, 40, 1e-14, dstatus_, stream_));
       launch_entropy(dts2.as<TruncSector>(), ns, dent.as<double>() + i, stream_);
       TDVP_CUDA(cudaStreamSynchronize(stream_));
     }

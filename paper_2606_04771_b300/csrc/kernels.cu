@@ -6,6 +6,7 @@
 // SVD, truncation selection, block-weighted dots and the entanglement entropy.
 // All kernels are symmetry-agnostic; the host planner lowers every contraction
 // to task lists (common.hpp).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -16,6 +17,8 @@
 
 #include "common.hpp"
 #include "kernels.hpp"
+
+namespace cg = cooperative_groups;
 
 namespace tdvp {
 
@@ -541,17 +544,19 @@ __global__ void __launch_bounds__(SVD_THREADS) jacobi_svd_kernel(const SvdTask* 
 }
 
 // ---------------------------------------------------------------------------
-// K6 (rounds): one-sided Jacobi, one warp per column pair, all problems at once
+// K6: one-sided Jacobi SVD of many matrices at once, one cooperative launch
 //
 // The classical round-robin ordering: the n columns of a problem (n padded to even)
 // form n/2 disjoint pairs in each of n - 1 rounds, and a sweep of n - 1 rounds
-// meets every pair once.  One launch performs one round for every problem: each
-// warp takes one pair, computes the two squared norms and the overlap, and applies
-// the complex Jacobi rotation (as in jacobi_svd_kernel) to both columns of G and,
-// when present, of V.  Columns live in global memory (the whole split's working set
-// stays in L2), so every pair of every sector runs in parallel instead of a block of
-// columns per CTA.  The work list is sorted by problem size, so each round launches
-// only the pairs of the problems that still have that round.
+// meets every pair once.  A single cooperative launch runs every sweep: in each
+// round every warp of the grid takes pairs from the work list (all problems, sorted
+// by size so that the pairs still active in a round are a prefix), computes the two
+// squared norms and the overlap, and applies the complex Jacobi rotation (as in
+// jacobi_svd_kernel) to both columns of G and, when present, of V; a grid-wide
+// barrier separates rounds.  After each sweep every CTA reads the per-problem
+// rotation flags; the loop ends, uniformly over the grid, after a sweep without
+// flags.  Columns of up to 32 R rows stay in registers between the reduction and
+// the rotation.  The working copies (a bond's worth of sectors) stay in L2.
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ void tourney(int r, int k, int n, int& i, int& j) {
@@ -570,151 +575,200 @@ __device__ __forceinline__ void tourney(int r, int k, int n, int& i, int& j) {
   }
 }
 
-constexpr int PAIR_WARPS = 2;  // warps (pairs) per CTA: many small CTAs spread one big sector over the SMs
+constexpr int JT = 256;  // threads per CTA of the cooperative Jacobi
 
-__global__ void __launch_bounds__(PAIR_WARPS * 32) jacobi_pair_kernel(const SvdTask* __restrict__ tasks,
-                                                                      const int2* __restrict__ work, int nwork,
-                                                                      int round, double tol, double tol_flag,
-                                                                      double abs_flag, int* __restrict__ flag_now,
-                                                                      const int* __restrict__ flag_prev) {
-  const int w = blockIdx.x * PAIR_WARPS + (threadIdx.x >> 5);
-  if (w >= nwork) return;
-  const int2 wk = work[w];
-  if (flag_prev && flag_prev[wk.x] == 0) return;  // converged in the previous sweep
-  const SvdTask t = tasks[wk.x];
-  const int n = t.q + (t.q & 1);
-  if (round >= n - 1) return;
-  int i, j;
-  tourney(round, wk.y, n, i, j);
-  if (j >= t.q) return;
-  double a, b;
-  cplx c;
-  col_pair(t.g, t.p, i, j, a, b, c);
-  const double ac = sqrt(c.x * c.x + c.y * c.y);
-  if (ac == 0.0 || ac <= tol * sqrt(a * b)) return;
-  const double zeta = (b - a) / (2.0 * ac);
-  const double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-  const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
-  const cplx e = {c.x / ac, c.y / ac};
-  rotate_cols(t.g, t.p, t.p, i, j, cs, sn, e);
-  if (t.v) rotate_cols(t.v, t.q, t.q, i, j, cs, sn, e);
-  if ((threadIdx.x & 31) == 0 && ac > tol_flag * sqrt(a * b) && ac > abs_flag) atomicOr(&flag_now[wk.x], 1);
+// x' = cs x - sn conj(e) y ; y' = sn e x + cs y
+template <class S, class C2>
+__device__ __forceinline__ void rot2(C2& x, C2& y, S cs, S sn, S ex, S ey) {
+  const C2 a = x, b = y;
+  x.x = cs * a.x - sn * (ex * b.x + ey * b.y);
+  x.y = cs * a.y - sn * (ex * b.y - ey * b.x);
+  y.x = sn * (ex * a.x - ey * a.y) + cs * b.x;
+  y.y = sn * (ex * a.y + ey * a.x) + cs * b.y;
 }
 
-// CTA-per-pair variant for columns of up to JC_THREADS * R rows: every thread keeps
-// R rows of both columns (and of both columns of V) in registers, so a round is one
-// load pass, one block reduction of (|g_i|^2, |g_j|^2, g_i^H g_j) and one store pass
-// -- a few L2 round trips instead of the 3 p / 32 dependent loads of a warp.
-constexpr int JC_THREADS = 128;
-
-template <class S>
-__device__ __forceinline__ void block_sum4(S& a, S& b, S& c, S& d, S* sh) {
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
-    c += __shfl_xor_sync(0xffffffffu, c, o);
-    d += __shfl_xor_sync(0xffffffffu, d, o);
-  }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) {
-    sh[4 * warp] = a;
-    sh[4 * warp + 1] = b;
-    sh[4 * warp + 2] = c;
-    sh[4 * warp + 3] = d;
-  }
-  __syncthreads();
-  a = b = c = d = S(0);
-  for (int w = 0; w < JC_THREADS / 32; ++w) {  // same order in every thread
-    a += sh[4 * w];
-    b += sh[4 * w + 1];
-    c += sh[4 * w + 2];
-    d += sh[4 * w + 3];
-  }
-}
-
-template <class Task, class S, class C2, int R>
-__global__ void __launch_bounds__(JC_THREADS) jacobi_cta_kernel(const Task* __restrict__ tasks,
-                                                                const int2* __restrict__ work, int round, S tol,
-                                                                S tol_flag, S abs_flag, int* __restrict__ flag_now,
-                                                                const int* __restrict__ flag_prev) {
-  const int2 wk = work[blockIdx.x];
-  if (flag_prev && flag_prev[wk.x] == 0) return;  // uniform over the CTA
-  const Task t = tasks[wk.x];
-  const int n = t.q + (t.q & 1);
-  if (round >= n - 1) return;
-  int i, j;
-  tourney(round, wk.y, n, i, j);
-  if (j >= t.q) return;
-  C2* gi = t.g + (long long)i * t.p;
-  C2* gj = t.g + (long long)j * t.p;
-  C2 x[R], y[R];
+// one column pair (i, j) by one warp; R > 0: rows lane + 32 k (k < R) in registers
+template <class S, class C2, int R>
+__device__ __forceinline__ void warp_pair(C2* __restrict__ g, C2* __restrict__ v, int p, int q, int i, int j, S tol,
+                                          S tol_flag, S abs_flag, int* __restrict__ flag) {
+  const int lane = threadIdx.x & 31;
+  C2* gi = g + (long long)i * p;
+  C2* gj = g + (long long)j * p;
   S sa = 0, sb = 0, cx = 0, cy = 0;
+  constexpr int RR = R > 0 ? R : 1;
+  C2 x[RR], y[RR];
+  if (R > 0) {
 #pragma unroll
-  for (int k = 0; k < R; ++k) {
-    const int r = threadIdx.x + k * JC_THREADS;
-    if (r < t.p) {
-      x[k] = gi[r];
-      y[k] = gj[r];
-    } else {
-      x[k].x = x[k].y = y[k].x = y[k].y = S(0);
+    for (int k = 0; k < RR; ++k) {
+      const int r = lane + 32 * k;
+      if (r < p) {
+        x[k] = gi[r];
+        y[k] = gj[r];
+      } else {
+        x[k].x = x[k].y = y[k].x = y[k].y = S(0);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < RR; ++k) {
+      sa = fma(x[k].x, x[k].x, fma(x[k].y, x[k].y, sa));
+      sb = fma(y[k].x, y[k].x, fma(y[k].y, y[k].y, sb));
+      cx = fma(x[k].x, y[k].x, fma(x[k].y, y[k].y, cx));
+      cy = fma(x[k].x, y[k].y, fma(-x[k].y, y[k].x, cy));
+    }
+  } else {
+#pragma unroll 4
+    for (int r = lane; r < p; r += 32) {
+      const C2 a = gi[r], b = gj[r];
+      sa = fma(a.x, a.x, fma(a.y, a.y, sa));
+      sb = fma(b.x, b.x, fma(b.y, b.y, sb));
+      cx = fma(a.x, b.x, fma(a.y, b.y, cx));
+      cy = fma(a.x, b.y, fma(-a.y, b.x, cy));
     }
   }
-#pragma unroll
-  for (int k = 0; k < R; ++k) {
-    sa = fma(x[k].x, x[k].x, fma(x[k].y, x[k].y, sa));
-    sb = fma(y[k].x, y[k].x, fma(y[k].y, y[k].y, sb));
-    cx = fma(x[k].x, y[k].x, fma(x[k].y, y[k].y, cx));
-    cy = fma(x[k].x, y[k].y, fma(-x[k].y, y[k].x, cy));
+  for (int o = 16; o > 0; o >>= 1) {
+    sa += __shfl_xor_sync(0xffffffffu, sa, o);
+    sb += __shfl_xor_sync(0xffffffffu, sb, o);
+    cx += __shfl_xor_sync(0xffffffffu, cx, o);
+    cy += __shfl_xor_sync(0xffffffffu, cy, o);
   }
-  __shared__ S sh[4 * (JC_THREADS / 32)];
-  block_sum4(sa, sb, cx, cy, sh);
   const S ac = sqrt(cx * cx + cy * cy);
-  if (ac == S(0) || ac <= tol * sqrt(sa * sb)) return;  // uniform: every thread holds the same sums
+  if (ac == S(0) || ac <= tol * sqrt(sa * sb)) return;  // warp-uniform
   const S zeta = (sb - sa) / (S(2) * ac);
   const S tt = (zeta >= 0 ? S(1) : S(-1)) / (fabs(zeta) + sqrt(S(1) + zeta * zeta));
   const S cs = S(1) / sqrt(S(1) + tt * tt), sn = cs * tt;
   const S ex = cx / ac, ey = cy / ac;
-  // g_i' = cs g_i - sn conj(e) g_j ; g_j' = sn e g_i + cs g_j
+  if (R > 0) {
 #pragma unroll
-  for (int k = 0; k < R; ++k) {
-    const int r = threadIdx.x + k * JC_THREADS;
-    if (r < t.p) {
-      const C2 a = x[k], b = y[k];
-      C2 u, v;
-      u.x = cs * a.x - sn * (ex * b.x + ey * b.y);
-      u.y = cs * a.y - sn * (ex * b.y - ey * b.x);
-      v.x = sn * (ex * a.x - ey * a.y) + cs * b.x;
-      v.y = sn * (ex * a.y + ey * a.x) + cs * b.y;
-      gi[r] = u;
-      gj[r] = v;
-    }
-  }
-  if (t.v) {
-    C2* vi = t.v + (long long)i * t.q;
-    C2* vj = t.v + (long long)j * t.q;
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
-      const int r = threadIdx.x + k * JC_THREADS;
-      if (r < t.q) {
-        const C2 a = vi[r], b = vj[r];
-        C2 u, v;
-        u.x = cs * a.x - sn * (ex * b.x + ey * b.y);
-        u.y = cs * a.y - sn * (ex * b.y - ey * b.x);
-        v.x = sn * (ex * a.x - ey * a.y) + cs * b.x;
-        v.y = sn * (ex * a.y + ey * a.x) + cs * b.y;
-        vi[r] = u;
-        vj[r] = v;
+    for (int k = 0; k < RR; ++k) {
+      const int r = lane + 32 * k;
+      if (r < p) {
+        rot2(x[k], y[k], cs, sn, ex, ey);
+        gi[r] = x[k];
+        gj[r] = y[k];
       }
     }
+  } else {
+#pragma unroll 4
+    for (int r = lane; r < p; r += 32) {
+      C2 a = gi[r], b = gj[r];
+      rot2(a, b, cs, sn, ex, ey);
+      gi[r] = a;
+      gj[r] = b;
+    }
   }
-  if (threadIdx.x == 0 && ac > tol_flag * sqrt(sa * sb) && ac > abs_flag) atomicOr(&flag_now[wk.x], 1);
+  if (v) {
+    C2* vi = v + (long long)i * q;
+    C2* vj = v + (long long)j * q;
+#pragma unroll 4
+    for (int r = lane; r < q; r += 32) {
+      C2 a = vi[r], b = vj[r];
+      rot2(a, b, cs, sn, ex, ey);
+      vi[r] = a;
+      vj[r] = b;
+    }
+  }
+  if (lane == 0 && ac > tol_flag * sqrt(sa * sb) && ac > abs_flag) atomicOr(flag, 1);
 }
 
-// one round for every active pair: the CTA-per-pair kernel sized to the longest
-// column (rows per thread R = 1 .. 16), or the warp-per-pair kernel beyond that
-template <class Task, class S, class C2>
-static void launch_round(const Task* d_tasks, const int2* d_work, int nw, int round, S tol, S tol_flag, S abs_flag,
-                         int* now, const int* prev, int pmax, cudaStream_t s);
+template <class Task, class S, class C2, int R>
+__global__ void __launch_bounds__(JT) jacobi_coop_kernel(const Task* __restrict__ tasks, int nt,
+                                                         const int2* __restrict__ work, const int* __restrict__ active,
+                                                         int nrounds, int max_sweeps, S tol, S tol_flag, S abs_flag,
+                                                         int* __restrict__ flags, int* __restrict__ out) {
+  cg::grid_group grid = cg::this_grid();
+  // pair w goes to CTA w mod G (warp w div G there): consecutive pairs -- the pairs of
+  // one large sector -- land on different SMs instead of sharing one SM's pipes
+  const int nwarps = (gridDim.x * JT) >> 5;
+  const int gw = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+  __shared__ int any_s;
+  int* now = flags;
+  const int* prev = nullptr;
+  int sweep = 0;
+  bool conv = false;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (blockIdx.x == 0)
+      for (int e = threadIdx.x; e < nt; e += JT) now[e] = 0;
+    grid.sync();
+    for (int r = 0; r < nrounds; ++r) {
+      const int na = active[r];
+      for (int w = gw; w < na; w += nwarps) {
+        const int2 wk = work[w];
+        if (prev && prev[wk.x] == 0) continue;  // converged in the previous sweep
+        const Task t = tasks[wk.x];
+        const int n = t.q + (t.q & 1);
+        if (r >= n - 1) continue;
+        int i, j;
+        tourney(r, wk.y, n, i, j);
+        if (j >= t.q) continue;
+        warp_pair<S, C2, R>(t.g, t.v, t.p, t.q, i, j, tol, tol_flag, abs_flag, now + wk.x);
+      }
+      grid.sync();
+    }
+    if (threadIdx.x == 0) {
+      int any = 0;
+      for (int e = 0; e < nt; ++e) any |= reinterpret_cast<volatile int*>(now)[e];
+      any_s = any;
+    }
+    __syncthreads();
+    const int any = any_s;
+    __syncthreads();
+    if (!any) {
+      conv = true;
+      ++sweep;
+      break;
+    }
+    prev = now;
+    now = (now == flags) ? flags + nt : flags;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    out[0] = sweep;
+    out[1] = conv ? 0 : 1;
+  }
+}
+
+// V = identity for every problem
+__global__ void svd_init_v_kernel(const SvdTask* __restrict__ tasks) {
+  const SvdTask t = tasks[blockIdx.x];
+  if (!t.v) return;
+  for (int e = threadIdx.x; e < t.q * t.q; e += blockDim.x) t.v[e] = {(e % t.q) == (e / t.q) ? 1.0 : 0.0, 0.0};
+}
+
+// singular values = column norms, sorted descending with perm (NaN last)
+__global__ void __launch_bounds__(256) svd_finish_kernel(const SvdTask* __restrict__ tasks) {
+  const SvdTask t = tasks[blockIdx.x];
+  const int p = t.p, q = t.q;
+  const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int j = warp; j < q; j += nwarp) {
+    double a, b;
+    cplx c;
+    col_pair(t.g, p, j, j, a, b, c);
+    if ((threadIdx.x & 31) == 0) t.sv[j] = sqrt(a);
+  }
+  __syncthreads();
+  // rank on integer keys (bit patterns of the non-negative values; NaN last)
+  extern __shared__ unsigned long long sb[];
+  for (int j = threadIdx.x; j < q; j += blockDim.x) {
+    double v = t.sv[j];
+    sb[j] = (v == v && v >= 0.0) ? (unsigned long long)__double_as_longlong(v) + 1ull : 0ull;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < q; j += blockDim.x) {
+    const unsigned long long kj = sb[j];
+    int rank = 0;
+    for (int i = 0; i < q; ++i) {
+      const unsigned long long ki = sb[i];
+      rank += (ki > kj) || (ki == kj && i < j);
+    }
+    t.perm[rank] = j;
+    t.sv[rank] = kj ? __longlong_as_double((long long)(kj - 1ull)) : 0.0;
+  }
+}
+
+__global__ void svd32_init_v_kernel(const Svd32Task* __restrict__ tasks) {
+  const Svd32Task t = tasks[blockIdx.x];
+  for (int e = threadIdx.x; e < t.q * t.q; e += blockDim.x)
+    t.v[e] = make_float2((e % t.q) == (e / t.q) ? 1.0f : 0.0f, 0.0f);
+}
 
 // Pairs (task, k) sorted by task size descending, and per round the number of
 // leading pairs whose task still has that round.
@@ -745,116 +799,92 @@ static void pair_schedule(const std::vector<Task>& h_tasks, std::vector<int2>& w
   }
 }
 
-// V = identity for every problem
-__global__ void svd_init_v_kernel(const SvdTask* __restrict__ tasks) {
-  const SvdTask t = tasks[blockIdx.x];
-  if (!t.v) return;
-  for (int e = threadIdx.x; e < t.q * t.q; e += blockDim.x) t.v[e] = {(e % t.q) == (e / t.q) ? 1.0 : 0.0, 0.0};
-}
-
-// singular values = column norms, sorted descending with perm (NaN last)
-__global__ void __launch_bounds__(256) svd_finish_kernel(const SvdTask* __restrict__ tasks) {
-  const SvdTask t = tasks[blockIdx.x];
-  const int p = t.p, q = t.q;
-  const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  for (int j = warp; j < q; j += nwarp) {
-    double a, b;
-    cplx c;
-    col_pair(t.g, p, j, j, a, b, c);
-    if ((threadIdx.x & 31) == 0) t.sv[j] = sqrt(a);
-  }
-  __syncthreads();
-  extern __shared__ double sb[];
-  for (int j = threadIdx.x; j < q; j += blockDim.x) {
-    double v = t.sv[j];
-    sb[j] = (v == v) ? v : -1.0;
-  }
-  __syncthreads();
-  for (int j = threadIdx.x; j < q; j += blockDim.x) {
-    double vj = sb[j];
-    int rank = 0;
-    for (int i = 0; i < q; ++i) {
-      double vi = sb[i];
-      rank += (vi > vj) || (vi == vj && i < j);
-    }
-    t.perm[rank] = j;
-    t.sv[rank] = vj < 0.0 ? 0.0 : vj;
-  }
+// registers per lane for the longest column: 32 R >= pmax (R = 0: streamed from memory)
+static int rows_per_lane(int pmax) {
+  for (int R = 1; R <= 16; R *= 2)
+    if (32 * R >= pmax) return R;
+  return 0;
 }
 
 template <class Task, class S, class C2, int R>
-static void launch_cta(const Task* d_tasks, const int2* d_work, int nw, int round, S tol, S tol_flag, S abs_flag,
-                       int* now, const int* prev, cudaStream_t s) {
+static int coop_launch(const Task* d_tasks, int nt, const int2* d_work, const int* d_active, int nrounds,
+                       int max_sweeps, S tol, S tol_flag, S abs_flag, int* flags, int* out, cudaStream_t s) {
+  auto kern = jacobi_coop_kernel<Task, S, C2, R>;
+  int dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, JT, 0);
+  if (per < 1 || nsm < 1) return -1;
+  const int grid = nsm * (per < 4 ? per : 4);
+  void* args[] = {(void*)&d_tasks, (void*)&nt,  (void*)&d_work,   (void*)&d_active, (void*)&nrounds, (void*)&max_sweeps,
+                  (void*)&tol,     (void*)&tol_flag, (void*)&abs_flag, (void*)&flags,    (void*)&out};
   note_launch();
-  jacobi_cta_kernel<Task, S, C2, R><<<nw, JC_THREADS, 0, s>>>(d_tasks, d_work, round, tol, tol_flag, abs_flag, now,
-                                                               prev);
+  return cudaLaunchCooperativeKernel((void*)kern, dim3(grid), dim3(JT), args, 0, s) == cudaSuccess ? 0 : -1;
 }
 
-template <>
-void launch_round<SvdTask, double, cplx>(const SvdTask* d_tasks, const int2* d_work, int nw, int round, double tol,
-                                         double tol_flag, double abs_flag, int* now, const int* prev, int pmax,
-                                         cudaStream_t s) {
-  if (pmax <= JC_THREADS)
-    launch_cta<SvdTask, double, cplx, 1>(d_tasks, d_work, nw, round, tol, tol_flag, abs_flag, now, prev, s);
-  else if (pmax <= 2 * JC_THREADS)
-    launch_cta<SvdTask, double, cplx, 2>(d_tasks, d_work, nw, round, tol, tol_flag, abs_flag, now, prev, s);
-  else if (pmax <= 4 * JC_THREADS)
-    launch_cta<SvdTask, double, cplx, 4>(d_tasks, d_work, nw, round, tol, tol_flag, abs_flag, now, prev, s);
-  else if (pmax <= 8 * JC_THREADS)
-    launch_cta<SvdTask, double, cplx, 8>(d_tasks, d_work, nw, round, tol, tol_flag, abs_flag, now, prev, s);
-  else if (pmax <= 16 * JC_THREADS)
-    launch_cta<SvdTask, double, cplx, 16>(d_tasks, d_work, nw, round, tol, tol_flag, abs_flag, now, prev, s);
-  else {
-    note_launch();
-    jacobi_pair_kernel<<<(nw + PAIR_WARPS - 1) / PAIR_WARPS, PAIR_WARPS * 32, 0, s>>>(d_tasks, d_work, nw, round, tol,
-                                                                                     tol_flag, abs_flag, now, prev);
+template <class Task, class S, class C2>
+static int coop_run(const Task* d_tasks, const std::vector<Task>& h_tasks, int max_sweeps, S tol, S tol_flag,
+                    S abs_flag, int* nonconv, cudaStream_t s) {
+  const int nt = (int)h_tasks.size();
+  int pmax = 1;
+  for (auto& t : h_tasks) pmax = max(pmax, t.p);
+  std::vector<int2> work;
+  std::vector<int> active;
+  pair_schedule(h_tasks, work, active);
+  if (work.empty()) return 1;
+  int2* d_work = nullptr;
+  int *d_active = nullptr, *flags = nullptr, *out = nullptr;
+  cudaMallocAsync(&d_work, work.size() * sizeof(int2), s);
+  cudaMallocAsync(&d_active, active.size() * sizeof(int), s);
+  cudaMallocAsync(&flags, (2 * nt + 2) * sizeof(int), s);
+  out = flags + 2 * nt;
+  cudaMemcpyAsync(d_work, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(d_active, active.data(), active.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+  const int nr = (int)active.size();
+  int rc;
+  switch (rows_per_lane(pmax)) {
+    case 1: rc = coop_launch<Task, S, C2, 1>(d_tasks, nt, d_work, d_active, nr, max_sweeps, tol, tol_flag, abs_flag, flags, out, s); break;
+    case 2: rc = coop_launch<Task, S, C2, 2>(d_tasks, nt, d_work, d_active, nr, max_sweeps, tol, tol_flag, abs_flag, flags, out, s); break;
+    case 4: rc = coop_launch<Task, S, C2, 4>(d_tasks, nt, d_work, d_active, nr, max_sweeps, tol, tol_flag, abs_flag, flags, out, s); break;
+    case 8: rc = coop_launch<Task, S, C2, 8>(d_tasks, nt, d_work, d_active, nr, max_sweeps, tol, tol_flag, abs_flag, flags, out, s); break;
+    case 16: rc = coop_launch<Task, S, C2, 16>(d_tasks, nt, d_work, d_active, nr, max_sweeps, tol, tol_flag, abs_flag, flags, out, s); break;
+    default: rc = coop_launch<Task, S, C2, 0>(d_tasks, nt, d_work, d_active, nr, max_sweeps, tol, tol_flag, abs_flag, flags, out, s); break;
   }
+  int h[2] = {max_sweeps, 1};
+  if (rc == 0) {
+    cudaMemcpyAsync(h, out, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+  }
+  cudaFreeAsync(d_work, s);
+  cudaFreeAsync(d_active, s);
+  cudaFreeAsync(flags, s);
+  if (nonconv) *nonconv = h[1];
+  return rc == 0 ? h[0] : -1;
 }
 
-// Round-robin Jacobi driver: returns the number of sweeps run (host loop, one sync
-// per sweep).  V is accumulated (from the identity) when the tasks carry v; without
-// v only G is rotated.  Pairs rotate when |g_i^H g_j| > tol |g_i||g_j|.  A sweep in
-// which no rotation had |g_i^H g_j| above both tol_flag |g_i||g_j| and abs_flag ends
-// the iteration: with tol_flag = tol and abs_flag = 0 that is the usual "no
-// rotation at all" test; tol_flag = sqrt(tol) relies on the quadratic convergence of
-// cyclic Jacobi (off-diagonal delta before a sweep leaves O(delta^2) after it), and
-// abs_flag > 0 ignores pairs whose coupling is negligible on the scale of the whole
-// matrix (the split passes unit-norm theta, so abs_flag is a weight).
+// Jacobi driver: returns the number of sweeps run, or -1 when the cooperative launch
+// failed (the CUDA error is left for the caller's check).  V is accumulated (from
+// the identity) when the tasks carry v; without v only G is rotated.  Pairs rotate
+// when |g_i^H g_j| > tol |g_i||g_j|.  A sweep in which no rotation had |g_i^H g_j|
+// above both tol_flag |g_i||g_j| and abs_flag ends the iteration: with tol_flag =
+// tol and abs_flag = 0 that is the usual "no rotation at all" test; tol_flag =
+// sqrt(tol) relies on the quadratic convergence of cyclic Jacobi (off-diagonal
+// delta before a sweep leaves O(delta^2) after it), and abs_flag > 0 ignores pairs
+// whose coupling is negligible on the scale of the whole matrix (the split passes
+// unit-norm theta, so abs_flag is a weight).  Non-convergence within max_sweeps
+// sets *status to 1.
 int run_jacobi_rounds(const SvdTask* d_tasks, const std::vector<SvdTask>& h_tasks, int max_sweeps, double tol,
                       int* status, cudaStream_t s, double tol_flag, double abs_flag) {
   const int nt = (int)h_tasks.size();
   if (nt == 0) return 0;
   if (!(tol_flag >= tol)) tol_flag = tol;
-  int qmax = 1, pmax = 1;
-  for (auto& t : h_tasks) {
-    qmax = max(qmax, t.q);
-    pmax = max(pmax, t.p);
-  }
-  std::vector<int2> work;
-  std::vector<int> active;
-  pair_schedule(h_tasks, work, active);
-  int2* d_work = nullptr;
-  int* flags = nullptr;
-  cudaMallocAsync(&d_work, (work.empty() ? 1 : work.size()) * sizeof(int2), s);
-  cudaMallocAsync(&flags, 2 * nt * sizeof(int), s);
-  if (!work.empty()) cudaMemcpyAsync(d_work, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+  int qmax = 1;
+  for (auto& t : h_tasks) qmax = max(qmax, t.q);
   note_launch();
   svd_init_v_kernel<<<nt, 256, 0, s>>>(d_tasks);
-  std::vector<int> hf(nt);
-  int sweep = 0, *prev = nullptr, *now = flags;
-  for (; sweep < max_sweeps && !work.empty(); ++sweep) {
-    cudaMemsetAsync(now, 0, nt * sizeof(int), s);
-    for (int r = 0; r < (int)active.size(); ++r)
-      launch_round<SvdTask, double, cplx>(d_tasks, d_work, active[r], r, tol, tol_flag, abs_flag, now, prev, pmax, s);
-    cudaMemcpyAsync(hf.data(), now, nt * sizeof(int), cudaMemcpyDeviceToHost, s);
-    cudaStreamSynchronize(s);
-    bool any = false;
-    for (int v : hf) any |= v != 0;
-    if (!any) break;
-    prev = now;
-    now = (now == flags) ? flags + nt : flags;
-  }
-  if (sweep >= max_sweeps) {
+  int nonconv = 0;
+  const int sweeps = coop_run<SvdTask, double, cplx>(d_tasks, h_tasks, max_sweeps, tol, tol_flag, abs_flag, &nonconv, s);
+  if (sweeps > 0 && nonconv) {
     int one = 1;
     cudaMemcpyAsync(status, &one, sizeof(int), cudaMemcpyHostToDevice, s);  // reported by the caller's check
     cudaStreamSynchronize(s);
@@ -863,147 +893,27 @@ int run_jacobi_rounds(const SvdTask* d_tasks, const std::vector<SvdTask>& h_task
   if (fs > 48 * 1024) cudaFuncSetAttribute(svd_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fs);
   note_launch();
   svd_finish_kernel<<<nt, 256, fs, s>>>(d_tasks);
-  cudaFreeAsync(d_work, s);
-  cudaFreeAsync(flags, s);
-  if (work.empty()) return 1;
-  return sweep < max_sweeps ? sweep + 1 : max_sweeps;  // sweeps run, the last one included
+  return sweeps;
 }
 
 // ---------------------------------------------------------------------------
-// K6 (FP32 preconditioner): round-robin one-sided Jacobi on a complex64 copy of G with
-// the right rotations accumulated in a complex64 V.  Used by the split-precision
-// modes: V is widened to FP64, G = A V is formed again in FP64 and a short FP64
-// Jacobi finishes the SVD, so every singular value the truncation sees is an FP64
-// one (the FP32 columns themselves are discarded).
+// K6 (FP32 preconditioner): the same Jacobi on complex64 copies of G with the right
+// rotations accumulated in a complex64 V.  Used by the split-precision modes: V is
+// widened to FP64, G = A V is formed again in FP64 and a short FP64 Jacobi finishes
+// the SVD, so every singular value the truncation sees is an FP64 one (the FP32
+// columns themselves are discarded).  It need not converge: it stops after
+// max_sweeps without an error.
 // ---------------------------------------------------------------------------
-
-__device__ void col_pair32(const float2* __restrict__ g, int p, int i, int j, float& a, float& b, float2& c) {
-  const int lane = threadIdx.x & 31;
-  float sa = 0, sb = 0, cx = 0, cy = 0;
-  const float2* gi = g + (long long)i * p;
-  const float2* gj = g + (long long)j * p;
-  for (int r = lane; r < p; r += 32) {
-    float2 x = gi[r], y = gj[r];
-    sa = fmaf(x.x, x.x, fmaf(x.y, x.y, sa));
-    sb = fmaf(y.x, y.x, fmaf(y.y, y.y, sb));
-    cx = fmaf(x.x, y.x, fmaf(x.y, y.y, cx));
-    cy = fmaf(x.x, y.y, fmaf(-x.y, y.x, cy));
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    sa += __shfl_xor_sync(0xffffffffu, sa, o);
-    sb += __shfl_xor_sync(0xffffffffu, sb, o);
-    cx += __shfl_xor_sync(0xffffffffu, cx, o);
-    cy += __shfl_xor_sync(0xffffffffu, cy, o);
-  }
-  a = sa;
-  b = sb;
-  c = make_float2(cx, cy);
-}
-
-__device__ void rotate32(float2* __restrict__ g, int ld, int len, int i, int j, float cs, float sn, float2 e) {
-  const int lane = threadIdx.x & 31;
-  float2* gi = g + (long long)i * ld;
-  float2* gj = g + (long long)j * ld;
-  for (int r = lane; r < len; r += 32) {
-    float2 x = gi[r], y = gj[r];
-    float2 ey = make_float2(e.x * y.x + e.y * y.y, e.x * y.y - e.y * y.x);
-    float2 ex = make_float2(e.x * x.x - e.y * x.y, e.x * x.y + e.y * x.x);
-    gi[r] = make_float2(cs * x.x - sn * ey.x, cs * x.y - sn * ey.y);
-    gj[r] = make_float2(sn * ex.x + cs * y.x, sn * ex.y + cs * y.y);
-  }
-}
-
-__global__ void __launch_bounds__(PAIR_WARPS * 32) jacobi_pair32_kernel(const Svd32Task* __restrict__ tasks,
-                                                                        const int2* __restrict__ work, int nwork,
-                                                                        int round, float tol, float abs_flag,
-                                                                        int* __restrict__ flag_now,
-                                                                        const int* __restrict__ flag_prev) {
-  const int w = blockIdx.x * PAIR_WARPS + (threadIdx.x >> 5);
-  if (w >= nwork) return;
-  const int2 wk = work[w];
-  if (flag_prev && flag_prev[wk.x] == 0) return;
-  const Svd32Task t = tasks[wk.x];
-  const int n = t.q + (t.q & 1);
-  if (round >= n - 1) return;
-  int i, j;
-  tourney(round, wk.y, n, i, j);
-  if (j >= t.q) return;
-  float a, b;
-  float2 c;
-  col_pair32(t.g, t.p, i, j, a, b, c);
-  const float ac = sqrtf(c.x * c.x + c.y * c.y);
-  if (ac == 0.0f || ac <= tol * sqrtf(a * b)) return;
-  const float zeta = (b - a) / (2.0f * ac);
-  const float tt = (zeta >= 0 ? 1.0f : -1.0f) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta));
-  const float cs = 1.0f / sqrtf(1.0f + tt * tt), sn = cs * tt;
-  const float2 e = make_float2(c.x / ac, c.y / ac);
-  rotate32(t.g, t.p, t.p, i, j, cs, sn, e);
-  rotate32(t.v, t.q, t.q, i, j, cs, sn, e);
-  if ((threadIdx.x & 31) == 0 && ac > abs_flag) atomicOr(&flag_now[wk.x], 1);
-}
-
-__global__ void svd32_init_v_kernel(const Svd32Task* __restrict__ tasks) {
-  const Svd32Task t = tasks[blockIdx.x];
-  for (int e = threadIdx.x; e < t.q * t.q; e += blockDim.x)
-    t.v[e] = make_float2((e % t.q) == (e / t.q) ? 1.0f : 0.0f, 0.0f);
-}
-
-template <>
-void launch_round<Svd32Task, float, float2>(const Svd32Task* d_tasks, const int2* d_work, int nw, int round, float tol,
-                                            float tol_flag, float abs_flag, int* now, const int* prev, int pmax,
-                                            cudaStream_t s) {
-  if (pmax <= JC_THREADS)
-    launch_cta<Svd32Task, float, float2, 1>(d_tasks, d_work, nw, round, tol, tol_flag, abs_flag, now, prev, s);
-  else if (pmax <= 2 * JC_THREADS)
-    launch_cta<Svd32Task, float, float2, 2>(d_tasks, d_work, nw, round, tol, tol_flag, abs_flag, now, prev, s);
-  else if (pmax <= 4 * JC_THREADS)
-    launch_cta<Svd32Task, float, float2, 4>(d_tasks, d_work, nw, round, tol, tol_flag, abs_flag, now, prev, s);
-  else if (pmax <= 8 * JC_THREADS)
-    launch_cta<Svd32Task, float, float2, 8>(d_tasks, d_work, nw, round, tol, tol_flag, abs_flag, now, prev, s);
-  else if (pmax <= 16 * JC_THREADS)
-    launch_cta<Svd32Task, float, float2, 16>(d_tasks, d_work, nw, round, tol, tol_flag, abs_flag, now, prev, s);
-  else {
-    note_launch();
-    jacobi_pair32_kernel<<<(nw + PAIR_WARPS - 1) / PAIR_WARPS, PAIR_WARPS * 32, 0, s>>>(d_tasks, d_work, nw, round,
-                                                                                       tol, abs_flag, now, prev);
-  }
-}
 
 int run_jacobi_rounds32(const Svd32Task* d_tasks, const std::vector<Svd32Task>& h_tasks, int max_sweeps, float tol,
                         float abs_flag, cudaStream_t s) {
   const int nt = (int)h_tasks.size();
   if (nt == 0) return 0;
-  int pmax = 1;
-  for (auto& t : h_tasks) pmax = max(pmax, t.p);
-  std::vector<int2> work;
-  std::vector<int> active;
-  pair_schedule(h_tasks, work, active);
-  int2* d_work = nullptr;
-  int* flags = nullptr;
-  cudaMallocAsync(&d_work, (work.empty() ? 1 : work.size()) * sizeof(int2), s);
-  cudaMallocAsync(&flags, 2 * nt * sizeof(int), s);
-  if (!work.empty()) cudaMemcpyAsync(d_work, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
   note_launch();
   svd32_init_v_kernel<<<nt, 256, 0, s>>>(d_tasks);
-  std::vector<int> hf(nt);
-  int sweep = 0, *prev = nullptr, *now = flags;
-  for (; sweep < max_sweeps && !work.empty(); ++sweep) {
-    cudaMemsetAsync(now, 0, nt * sizeof(int), s);
-    for (int r = 0; r < (int)active.size(); ++r)
-      launch_round<Svd32Task, float, float2>(d_tasks, d_work, active[r], r, tol, 0.0f, abs_flag, now, prev, pmax, s);
-    cudaMemcpyAsync(hf.data(), now, nt * sizeof(int), cudaMemcpyDeviceToHost, s);
-    cudaStreamSynchronize(s);
-    bool any = false;
-    for (int v : hf) any |= v != 0;
-    if (!any) break;
-    prev = now;
-    now = (now == flags) ? flags + nt : flags;
-  }
-  cudaFreeAsync(d_work, s);
-  cudaFreeAsync(flags, s);
-  if (work.empty()) return 1;
-  return sweep < max_sweeps ? sweep + 1 : max_sweeps;
+  return coop_run<Svd32Task, float, float2>(d_tasks, h_tasks, max_sweeps, tol, 0.0f, abs_flag, nullptr, s);
 }
+
 
 // precision conversions of whole buffers
 __global__ void narrow_kernel(const cplx* __restrict__ src, float2* __restrict__ dst, long long n) {
@@ -1133,28 +1043,34 @@ __global__ void __launch_bounds__(TRUNC_THREADS) truncate_kernel(const TruncSect
     for (int i = lane; i < t.r; i += 32) {
       double v = t.sv[i];
       owner[offs[sct] + i] = sct;
-      vals[offs[sct] + i] = (v == v) ? v : -1.0;
+      vals[offs[sct] + i] = (v == v && v >= 0.0) ? v : -1.0;
     }
     if (lane == 0) kept[sct] = 0;
   }
   __syncthreads();
-  __shared__ double tile[TRUNC_TILE];
+  // ranking on integer keys: for non-negative doubles the IEEE bit pattern is
+  // monotone, the NaN sentinel -1 maps to 0 (the FP64 unit is far too slow on this
+  // part for n^2 floating-point compares)
+  auto key = [](double v) -> unsigned long long {
+    return v >= 0.0 ? (unsigned long long)__double_as_longlong(v) + 1ull : 0ull;
+  };
+  __shared__ unsigned long long tile[TRUNC_TILE];
   for (int e0 = 0; e0 < n; e0 += TRUNC_THREADS * TRUNC_PER) {
-    double mine[TRUNC_PER];
+    unsigned long long mine[TRUNC_PER];
     int rank[TRUNC_PER];
 #pragma unroll
     for (int j = 0; j < TRUNC_PER; ++j) {
       int e = e0 + j * TRUNC_THREADS + tid;
-      mine[j] = e < n ? vals[e] : 0.0;
+      mine[j] = e < n ? key(vals[e]) : 0ull;
       rank[j] = 0;
     }
     for (int f0 = 0; f0 < n; f0 += TRUNC_TILE) {
       const int m = min(TRUNC_TILE, n - f0);
       __syncthreads();
-      for (int f = tid; f < m; f += TRUNC_THREADS) tile[f] = vals[f0 + f];
+      for (int f = tid; f < m; f += TRUNC_THREADS) tile[f] = key(vals[f0 + f]);
       __syncthreads();
       for (int f = 0; f < m; ++f) {
-        const double vf = tile[f];
+        const unsigned long long vf = tile[f];
         const int gf = f0 + f;
 #pragma unroll
         for (int j = 0; j < TRUNC_PER; ++j) {
