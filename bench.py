@@ -179,6 +179,7 @@ def heff_kernel_profile(args, dev, stream):
     e2e_s = (time.perf_counter() - t0) / reps
     kdim = bp.last_krylov_dim()
     out = {"matvec_gflop": flops_mv / 1e9, "stage_ms": stage_ms, "gemm_ms": gemm_ms,
+           "stage_alg_bytes": list(pby), "stage_alg_flops": list(pfl),
            "tflops": gemm_flops / (gemm_ms * 1e-3) / 1e12, "theta_elems": int(n),
            "krylov_step_ms_host": 1e3 * e2e_s, "krylov_dim": kdim,
            "e2e_tflops": kdim * flops_mv / e2e_s / 1e12, "h2d_bytes": int(theta_h.nbytes),
