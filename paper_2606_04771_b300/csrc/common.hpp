@@ -32,6 +32,7 @@ struct GemmTask {
   int rows, cols, ldc;
   int seg_begin, seg_count;
   int tiles_m, tiles_n;  // filled by the planner for the tile size in use
+  int roff, coff;        // BF16x4: scale-group offsets of this task's rows and columns
 };
 
 // op flags
@@ -44,6 +45,24 @@ struct GemmSeg {
   int lda, ldb, k;
   int op_a, op_b;
   double alpha;
+  // BF16x4: digit records of the operands in logical orientation (A: rows x k,
+  // B: k x cols, row-major, 8 bytes per complex element), filled per launch
+  const unsigned long long* a_dig;
+  const unsigned long long* b_dig;
+};
+
+// BF16x4: one distinct operand block split into digit records.  A operands get a
+// power-of-two scale per row, B operands per column; operands that meet in one task
+// share their group's scales (grp: offset of the group's first row/column).
+struct DigitOp {
+  const cplx* src;
+  int base;
+  int rows, cols;  // logical (after op): A: M x K, B: K x N
+  int ld, op;
+  double alpha;    // A only
+  int side;        // 0: A (row scales), 1: B (column scales)
+  int grp;
+  unsigned long long* dig;
 };
 
 template <class T>

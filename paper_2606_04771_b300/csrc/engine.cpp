@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <tuple>
 
@@ -73,19 +74,124 @@ void GemmPlan::finalize(cudaStream_t s, int kind_, int* status_) {
     GemmTask& t = tasks[i];
     t.tiles_m = (t.rows + tm - 1) / tm;
     t.tiles_n = (t.cols + tn - 1) / tn;
+    t.roff = t.coff = 0;
     for (int a = 0; a < t.tiles_m; ++a)
       for (int b = 0; b < t.tiles_n; ++b) tiles.push_back(make_int3(i, a, b));
   }
+  if (kind == 1) plan_digits(s);
   dt = upload(tasks, s);
   ds = upload(segs, s);
   dti = upload(tiles, s);
 }
 
+// BF16x4: every distinct operand block (same storage, shape, op and alpha) is split
+// once per launch into digit records.  Exactness of a task's accumulation needs one
+// scale per output row across all of its A operands and one per output column
+// across its B operands, so operands that meet in a task are merged (union-find)
+// into scale groups; a group's scales are the maxima over all of its operands.
+void GemmPlan::plan_digits(cudaStream_t s) {
+  typedef std::tuple<int, int, uintptr_t, int, int, int, int, double> Key;  // side, base, ptr, rows, cols, ld, op, alpha
+  std::map<Key, int> idx;
+  std::vector<Key> keys;
+  std::vector<int> parent;
+  auto get = [&](const Key& k) {
+    auto it = idx.find(k);
+    if (it != idx.end()) return it->second;
+    const int i = (int)keys.size();
+    idx[k] = i;
+    keys.push_back(k);
+    parent.push_back(i);
+    return i;
+  };
+  std::function<int(int)> find = [&](int x) {
+    while (parent[x] != x) x = parent[x] = parent[parent[x]];
+    return x;
+  };
+  std::vector<int> first_a(tasks.size(), -1), first_b(tasks.size(), -1);
+  std::vector<std::pair<int, int>> segop(segs.size(), {-1, -1});
+  for (int i = 0; i < (int)tasks.size(); ++i) {
+    const GemmTask& t = tasks[i];
+    for (int k = 0; k < t.seg_count; ++k) {
+      const int si = t.seg_begin + k;
+      const GemmSeg& g = segs[si];
+      if (g.k <= 0) continue;
+      const int ia = get(Key(0, g.a_base, reinterpret_cast<uintptr_t>(g.a), t.rows, g.k, g.lda, g.op_a, g.alpha));
+      const int ib = get(Key(1, g.b_base, reinterpret_cast<uintptr_t>(g.b), g.k, t.cols, g.ldb, g.op_b, 1.0));
+      segop[si] = {ia, ib};
+      if (first_a[i] < 0) first_a[i] = ia;
+      else parent[find(ia)] = find(first_a[i]);
+      if (first_b[i] < 0) first_b[i] = ib;
+      else parent[find(ib)] = find(first_b[i]);
+    }
+  }
+  // group offsets: A groups take rows entries, B groups cols entries
+  std::map<int, int> goff;
+  long long ng = 0;
+  for (int i = 0; i < (int)keys.size(); ++i) {
+    const int r = find(i);
+    if (goff.count(r)) continue;
+    goff[r] = (int)ng;
+    ng += std::get<0>(keys[r]) == 0 ? std::get<3>(keys[r]) : std::get<4>(keys[r]);
+  }
+  if (ng > INT32_MAX) throw Error(-5, "GEMM plan too large for 32-bit scale offsets");
+  ngrp = (int)ng;
+  long long nrec = 0;
+  std::vector<long long> roff(keys.size());
+  for (int i = 0; i < (int)keys.size(); ++i) {
+    roff[i] = nrec;
+    nrec += (long long)std::get<3>(keys[i]) * std::get<4>(keys[i]);
+  }
+  ddig = DevBuf(std::max<long long>(nrec, 1) * sizeof(unsigned long long), s);
+  dmax = DevBuf(std::max(ngrp, 1) * sizeof(unsigned long long), s);
+  dexp = DevBuf(std::max(ngrp, 1) * sizeof(int), s);
+  unsigned long long* dig = ddig.as<unsigned long long>();
+  dops.assign(keys.size(), DigitOp{});
+  djobs.clear();
+  const int job = digit_job_size();
+  for (int i = 0; i < (int)keys.size(); ++i) {
+    const Key& k = keys[i];
+    DigitOp& o = dops[i];
+    o.side = std::get<0>(k);
+    o.base = std::get<1>(k);
+    o.src = reinterpret_cast<const cplx*>(std::get<2>(k));
+    o.rows = std::get<3>(k);
+    o.cols = std::get<4>(k);
+    o.ld = std::get<5>(k);
+    o.op = std::get<6>(k);
+    o.alpha = std::get<7>(k);
+    o.grp = goff[find(i)];
+    o.dig = dig + roff[i];
+    const long long n = (long long)o.rows * o.cols;
+    for (long long e = 0; e < n; e += job) djobs.push_back(make_int2(i, (int)e));
+  }
+  for (int i = 0; i < (int)tasks.size(); ++i) {
+    if (first_a[i] >= 0) tasks[i].roff = goff[find(first_a[i])];
+    if (first_b[i] >= 0) tasks[i].coff = goff[find(first_b[i])];
+  }
+  for (int si = 0; si < (int)segs.size(); ++si) {
+    segs[si].a_dig = segop[si].first >= 0 ? dops[segop[si].first].dig : nullptr;
+    segs[si].b_dig = segop[si].second >= 0 ? dops[segop[si].second].dig : nullptr;
+  }
+  ddops = upload(dops, s);
+  djb = upload(djobs, s);
+  // the persistent kernel walks the tiles with a stride of the grid: the most
+  // expensive (most K chunks) first balances the SMs
+  std::vector<int> cost(tasks.size(), 0);
+  for (int i = 0; i < (int)tasks.size(); ++i)
+    for (int k = 0; k < tasks[i].seg_count; ++k) cost[i] += (segs[tasks[i].seg_begin + k].k + 31) / 32;
+  std::stable_sort(tiles.begin(), tiles.end(), [&](const int3& x, const int3& y) { return cost[x.x] > cost[y.x]; });
+}
+
 void GemmPlan::launch(cudaStream_t s, const Bases4& B) const {
   if (kind < 0)
     launch_gemm_fp64(dt.as<GemmTask>(), ds.as<GemmSeg>(), dti.as<int3>(), (int)tiles.size(), B, s);
-  else
-    launch_gemm_split(kind, dt.as<GemmTask>(), ds.as<GemmSeg>(), dti.as<int3>(), (int)tiles.size(), B, status, s);
+  else {
+    if (kind == 1)
+      launch_digits(ddops.as<DigitOp>(), (int)dops.size(), djb.as<int2>(), (int)djobs.size(),
+                    dmax.as<unsigned long long>(), dexp.as<int>(), ngrp, B, s);
+    launch_gemm_split(kind, dt.as<GemmTask>(), ds.as<GemmSeg>(), dti.as<int3>(), (int)tiles.size(), dexp.as<int>(),
+                      B, status, s);
+  }
 }
 
 void LincombPlan::finalize(cudaStream_t s) {

@@ -85,11 +85,17 @@ struct GemmPlan {
   std::vector<GemmSeg> segs;
   std::vector<int3> tiles;
   DevBuf dt, ds, dti;
+  // BF16x4: distinct operands, their split jobs, digit records, group maxima and exponents
+  std::vector<DigitOp> dops;
+  std::vector<int2> djobs;
+  DevBuf ddops, djb, ddig, dmax, dexp;
+  int ngrp = 0;
   long long flops = 0;  // algorithmic real flops (8 per complex MAC)
   long long bytes = 0;  // algorithmic bytes: every operand block read once, output written once
   int kind = -1;        // -1 FP64 CUDA cores, 0 3xTF32, 1 BF16x3 tensor cores
   int* status = nullptr;
   void finalize(cudaStream_t s, int kind_ = -1, int* status_ = nullptr);
+  void plan_digits(cudaStream_t s);
   void launch(cudaStream_t s, const Bases4& B) const;
 };
 

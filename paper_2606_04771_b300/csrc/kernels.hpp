@@ -42,7 +42,12 @@ void launch_copy(const CopyTask* tasks, const int2* chunks, int nchunks, cudaStr
 int split_tile_m();
 int split_tile_n(int kind);
 void launch_gemm_split(int kind, const GemmTask* tasks, const GemmSeg* segs, const int3* tiles, int ntiles,
-                       const Bases4& B, int* status, cudaStream_t s);
+                       const int* exps, const Bases4& B, int* status, cudaStream_t s);
+// BF16x4 operand splitting (once per launch): group maxima, exponents, digit records.
+// jobs = (operand, first element) in steps of digit_job_size() elements.
+int digit_job_size();
+void launch_digits(const DigitOp* ops, int nops, const int2* jobs, int njobs, unsigned long long* maxv, int* exps,
+                   int ngrp, const Bases4& B, cudaStream_t s);
 
 int dots_grid(long long n);
 void launch_dots(const cplx* V, long long pitch, int nv, const cplx* w, long long n, cplx* partial, int G, cplx* out,

@@ -10,8 +10,9 @@
 //     (scaled signed digits, exact per-order accumulation; gemm_exact_kernel);
 //   * producer warps load FP64 tiles from global memory, split them and store
 //     them in the 128-byte-swizzled K-major layout the MMA descriptors expect;
-//     one thread issues the MMAs; the same producer warps read the accumulator
-//     back from TMEM (tcgen05.ld) and write FP64 complex results.
+//     one thread issues the MMAs; the accumulator is read back from TMEM
+//     (tcgen05.ld) and written as FP64 complex results (the BF16x4 kernel is
+//     persistent with separate epilogue warps and two accumulator sets).
 // Every mbarrier wait is bounded: on expiry the kernel records an error in
 // *status, stops issuing work, releases its TMEM and returns.
 #include <cuda_runtime.h>
@@ -348,8 +349,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
 constexpr int XN = 64;                  // complex columns per tile
 constexpr int XSTAGE = 4 * PLANE_BYTES + 4 * (64 * 128);  // 4 A planes (128 rows) + 4 B planes (64 rows)
-constexpr int XSTAGES = 1;  // ~100 KB of shared memory: two CTAs share an SM
+constexpr int XSTAGES = 2;              // 192 KB of stages: one persistent CTA per SM
 constexpr int XKC = 32;                 // complex k per chunk (64 bf16 = one 128-byte row)
+constexpr int XPROD = 256;              // producer threads (warps 0-7)
+constexpr int XMMA_WARP = 8;            // MMA issuer warp
+constexpr int XTHREADS = XPROD + 32 + 128;  // + MMA warp + four epilogue warps (9-12)
+constexpr int XACC = 4 * XN;            // TMEM columns of one accumulator set (four orders)
 
 __device__ __forceinline__ int exp_of_max(double m) {
   // smallest e with |x| <= 2^e for |x| <= m (m > 0); -2000 marks an all-zero row
@@ -404,179 +409,262 @@ __device__ __forceinline__ void tmem_ld16(uint32_t addr, uint32_t* v) {
       : "memory");
 }
 
-__global__ void __launch_bounds__(NTHREADS, 2)
+// ---- operand splitting, once per launch --------------------------------------
+// pass 1: per-row (A) / per-column (B) maxima of |Re|, |Im| into the operand's
+// scale group (bit patterns of non-negative doubles order like the values)
+__global__ void __launch_bounds__(256) digit_max_kernel(const DigitOp* __restrict__ ops, const Bases4 B,
+                                                        unsigned long long* __restrict__ maxv) {
+  const DigitOp o = ops[blockIdx.x];
+  const cplx* src = rebase(B, o.base, o.src);
+  const unsigned long long ABS = 0x7FFFFFFFFFFFFFFFull;
+  auto at = [&](int r, int c) -> cplx {  // logical element (r, c)
+    return o.op == OP_N ? src[(long long)r * o.ld + c] : src[(long long)c * o.ld + r];
+  };
+  if (o.side == 0) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int r = warp; r < o.rows; r += 8) {
+      unsigned long long m = 0;
+      for (int c = lane; c < o.cols; c += 32) {
+        const cplx v = at(r, c);
+        m = max(m, max((unsigned long long)__double_as_longlong(v.x) & ABS,
+                       (unsigned long long)__double_as_longlong(v.y) & ABS));
+      }
+      for (int d = 16; d > 0; d >>= 1) m = max(m, (unsigned long long)__shfl_xor_sync(0xffffffffu, m, d));
+      if (m && o.alpha != 1.0) m = (unsigned long long)__double_as_longlong(fabs(o.alpha) * __longlong_as_double(m));
+      if (lane == 0 && m) atomicMax(&maxv[o.grp + r], m);
+    }
+  } else {
+    for (int c = threadIdx.x; c < o.cols; c += 256) {
+      unsigned long long m = 0;
+      for (int r = 0; r < o.rows; ++r) {
+        const cplx v = at(r, c);
+        m = max(m, max((unsigned long long)__double_as_longlong(v.x) & ABS,
+                       (unsigned long long)__double_as_longlong(v.y) & ABS));
+      }
+      if (m) atomicMax(&maxv[o.grp + c], m);
+    }
+  }
+}
+
+// pass 2: the exponent of every group row/column
+__global__ void digit_exp_kernel(const unsigned long long* __restrict__ maxv, int* __restrict__ exps, int n) {
+  for (int i = blockIdx.x * 256 + threadIdx.x; i < n; i += gridDim.x * 256) exps[i] = exp_of_max(__longlong_as_double(maxv[i]));
+}
+
+__device__ __forceinline__ unsigned long long pack_digits(double re, double im, int e) {
+  float d[4], f[4];
+  digits4(fixed30(re, e), d);
+  digits4(fixed30(im, e), f);
+  unsigned long long w = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    w |= (unsigned long long)((unsigned)((int)d[i]) & 0xFFu) << (8 * i);
+    w |= (unsigned long long)((unsigned)((int)f[i]) & 0xFFu) << (8 * (4 + i));
+  }
+  return w;
+}
+
+// pass 3: every element of every operand as one 8-byte record (Re digits 0-3, Im
+// digits 0-3, signed bytes), logical row-major; jobs = (operand, first element)
+constexpr int DIGIT_JOB = 4096;
+__global__ void __launch_bounds__(256) digit_convert_kernel(const DigitOp* __restrict__ ops,
+                                                            const int2* __restrict__ jobs, const Bases4 B,
+                                                            const int* __restrict__ exps) {
+  const int2 jb = jobs[blockIdx.x];
+  const DigitOp o = ops[jb.x];
+  const cplx* src = rebase(B, o.base, o.src);
+  const long long n = (long long)o.rows * o.cols;
+  const long long e1 = min(n, (long long)jb.y + DIGIT_JOB);
+  for (long long e = jb.y + threadIdx.x; e < e1; e += 256) {
+    const int r = (int)(e / o.cols), c = (int)(e - (long long)r * o.cols);
+    cplx v = o.op == OP_N ? src[(long long)r * o.ld + c] : src[(long long)c * o.ld + r];
+    if (o.op != OP_N) v.y = -v.y;
+    if (o.alpha != 1.0) {
+      v.x *= o.alpha;
+      v.y *= o.alpha;
+    }
+    o.dig[e] = pack_digits(v.x, v.y, exps[o.grp + (o.side == 0 ? r : c)]);
+  }
+}
+
+__device__ __forceinline__ float sbyte(unsigned long long w, int i) { return (float)(int)(signed char)(w >> (8 * i)); }
+
+__device__ __forceinline__ int task_chunks(const GemmTask& t, const GemmSeg* __restrict__ segs) {
+  int n = 0;
+  for (int s = 0; s < t.seg_count; ++s) n += (segs[t.seg_begin + s].k + XKC - 1) / XKC;
+  return n;
+}
+
+// Persistent, warp-specialised BF16x4 kernel: one CTA per SM walks the tile list
+// (sorted by cost) with stride gridDim.x.  Warps 0-7 split FP64 operand chunks into
+// digit planes in a two-stage ring, warp 8 issues the MMAs into one of two TMEM
+// accumulator sets, warps 9-12 drain the other set (exact combination, scaling,
+// FP64 stores) while the next tile accumulates.
+__global__ void __launch_bounds__(XTHREADS, 1)
     gemm_exact_kernel(const GemmTask* __restrict__ tasks, const GemmSeg* __restrict__ segs,
-                      const int3* __restrict__ tiles, const Bases4 B, int* __restrict__ status) {
+                      const int3* __restrict__ tiles, int ntiles, const Bases4 B, const int* __restrict__ exps,
+                      int* __restrict__ status) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* stage_base =
       reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  __shared__ uint64_t full_bar[XSTAGES], empty_bar[XSTAGES], done_bar;
+  __shared__ uint64_t full_bar[XSTAGES], empty_bar[XSTAGES], tfull[2], tempty[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int err;
-  __shared__ int rowe[TM], cole[XN];
-  __shared__ unsigned long long rmax2[TM][2], cmax2[XN][2];
-
-  const int3 tr = tiles[blockIdx.x];
-  const GemmTask t = tasks[tr.x];
-  cplx* const cptr = rebase(B, t.c_base, t.c);
-  const int m0 = tr.y * TM, n0 = tr.z * XN;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-
-  int nchunks = 0;
-  for (int s = 0; s < t.seg_count; ++s) nchunks += (segs[t.seg_begin + s].k + XKC - 1) / XKC;
-  if (nchunks == 0) {
-    for (int e = tid; e < TM * XN; e += NTHREADS) {
-      int r = m0 + e / XN, c = n0 + e % XN;
-      if (r < t.rows && c < t.cols) cptr[(long long)r * t.ldc + c] = {0.0, 0.0};
-    }
-    return;
-  }
   if (tid == 0) {
     for (int s = 0; s < XSTAGES; ++s) {
-      mbar_init(&full_bar[s], NPROD / 32);
+      mbar_init(&full_bar[s], XPROD / 32);
       mbar_init(&empty_bar[s], 1);
     }
-    mbar_init(&done_bar, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);
+    }
     err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                 "r"(256)
+                 "r"(2 * XACC)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  // phase 0: row and column maxima over every segment of the task (producer threads)
-  if (tid < NPROD) {
-    // magnitudes compared as the bit patterns of |x| (monotone for non-negative doubles)
-    const unsigned long long ABS = 0x7FFFFFFFFFFFFFFFull;
-    const int m = tid >> 1, h = tid & 1;          // two threads per complex row
-    const int n = tid & (XN - 1), hh = tid >> 6;  // two threads per complex column
-    unsigned long long rm = 0, cm = 0;
-    for (int sgi = 0; sgi < t.seg_count; ++sgi) {
-      const GemmSeg sg = segs[t.seg_begin + sgi];
-      const cplx* ap = rebase(B, sg.a_base, sg.a);
-      const cplx* bp = rebase(B, sg.b_base, sg.b);
-      const int gr = m0 + m, gc = n0 + n;
-      unsigned long long sm = 0;
-      if (gr < t.rows) {
-        if (sg.op_a == OP_N) {
-          const cplx* row = ap + (long long)gr * sg.lda;
-#pragma unroll 4
-          for (int k = h; k < sg.k; k += 2) {
-            const cplx v = row[k];
-            sm = max(sm, max((unsigned long long)__double_as_longlong(v.x) & ABS,
-                             (unsigned long long)__double_as_longlong(v.y) & ABS));
-          }
-        } else {
-#pragma unroll 4
-          for (int k = h; k < sg.k; k += 2) {
-            const cplx v = ap[(long long)k * sg.lda + gr];
-            sm = max(sm, max((unsigned long long)__double_as_longlong(v.x) & ABS,
-                             (unsigned long long)__double_as_longlong(v.y) & ABS));
-          }
-        }
-      }
-      if (sg.alpha != 1.0) sm = (unsigned long long)__double_as_longlong(fabs(sg.alpha) * __longlong_as_double(sm));
-      rm = max(rm, sm);
-      if (gc < t.cols) {
-        if (sg.op_b == OP_N) {
-#pragma unroll 4
-          for (int k = hh; k < sg.k; k += 2) {
-            const cplx v = bp[(long long)k * sg.ldb + gc];
-            cm = max(cm, max((unsigned long long)__double_as_longlong(v.x) & ABS,
-                             (unsigned long long)__double_as_longlong(v.y) & ABS));
-          }
-        } else {
-          const cplx* col = bp + (long long)gc * sg.ldb;
-#pragma unroll 4
-          for (int k = hh; k < sg.k; k += 2) {
-            const cplx v = col[k];
-            cm = max(cm, max((unsigned long long)__double_as_longlong(v.x) & ABS,
-                             (unsigned long long)__double_as_longlong(v.y) & ABS));
-          }
-        }
-      }
-    }
-    rmax2[m][h] = rm;
-    cmax2[n][hh] = cm;
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (tid < TM) rowe[tid] = exp_of_max(__longlong_as_double(max(rmax2[tid][0], rmax2[tid][1])));
-  if (tid < XN) cole[tid] = exp_of_max(__longlong_as_double(max(cmax2[tid][0], cmax2[tid][1])));
-  __syncthreads();
   const uint32_t tmem = tmem_slot;
   volatile int* verr = &err;
 
-  if (warp < 4) {
+  if (warp < XPROD / 32) {
+    // ---------------- producers ----------------
     int it = 0;
-    for (int sgi = 0; sgi < t.seg_count && !*verr; ++sgi) {
-      const GemmSeg sg = segs[t.seg_begin + sgi];
-      const cplx* ap = rebase(B, sg.a_base, sg.a);
-      const cplx* bp = rebase(B, sg.b_base, sg.b);
-      const double al = sg.alpha;
-      for (int k0 = 0; k0 < sg.k; k0 += XKC, ++it) {
-        const int s = it % XSTAGES;
-        if (!mbar_wait(&empty_bar[s], ((it / XSTAGES) & 1) ^ 1, verr)) break;
-        uint8_t* st = stage_base + (size_t)s * XSTAGE;
-        // A: 64 complex rows x 32 complex k -> 4 digit planes of 128 rows x 64 bf16
-        for (int e = tid; e < TM * XKC; e += NPROD) {
-          const int m = e / XKC, k = e % XKC;
-          const int gr = m0 + m, gk = k0 + k;
-          cplx v = {0.0, 0.0};
-          if (gr < t.rows && gk < sg.k) {
-            if (sg.op_a == OP_N) v = ap[(long long)gr * sg.lda + gk];
-            else {
-              v = ap[(long long)gk * sg.lda + gr];
-              v.y = -v.y;
+    for (int ti = blockIdx.x; ti < ntiles && !*verr; ti += gridDim.x) {
+      const int3 tr = tiles[ti];
+      const GemmTask t = tasks[tr.x];
+      const int m0 = tr.y * TM, n0 = tr.z * XN;
+      for (int sgi = 0; sgi < t.seg_count && !*verr; ++sgi) {
+        const GemmSeg sg = segs[t.seg_begin + sgi];
+        const unsigned long long* ad = sg.a_dig;
+        const unsigned long long* bd = sg.b_dig;
+        for (int k0 = 0; k0 < sg.k; k0 += XKC, ++it) {
+          const int s = it % XSTAGES;
+          if (!mbar_wait(&empty_bar[s], ((it / XSTAGES) & 1) ^ 1, verr)) break;
+          uint8_t* st = stage_base + (size_t)s * XSTAGE;
+          // all 16 records of this thread first (loads in flight together), then
+          // A: 64 complex rows x 32 complex k -> 4 digit planes of 128 rows x 64 bf16,
+          // B: 32 complex k x 64 complex n -> 4 digit planes of 64 rows x 64 bf16
+          constexpr int NA = TM * XKC / XPROD, NB = XN * XKC / XPROD;
+          unsigned long long wa[NA], wb[NB];
+#pragma unroll
+          for (int j = 0; j < NA; ++j) {
+            const int e = tid + j * XPROD, m = e / XKC, k = e % XKC;
+            const int gr = m0 + m, gk = k0 + k;
+            wa[j] = (gr < t.rows && gk < sg.k) ? __ldg(ad + (long long)gr * sg.k + gk) : 0ull;
+          }
+#pragma unroll
+          for (int j = 0; j < NB; ++j) {
+            const int e = tid + j * XPROD, n = e % XN, k = e / XN;
+            const int gc = n0 + n, gk = k0 + k;
+            wb[j] = (gc < t.cols && gk < sg.k) ? __ldg(bd + (long long)gk * t.cols + gc) : 0ull;
+          }
+#pragma unroll
+          for (int j = 0; j < NA; ++j) {
+            const int e = tid + j * XPROD, m = e / XKC, k = e % XKC;
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+              const float re = sbyte(wa[j], p), im = sbyte(wa[j], 4 + p);
+              uint8_t* pl = st + p * PLANE_BYTES;
+              st_bf2(pl, 2 * m, 2 * k, re, -im);
+              st_bf2(pl, 2 * m + 1, 2 * k, im, re);
             }
           }
-          if (al != 1.0) {
-            v.x *= al;
-            v.y *= al;
-          }
-          float re[4], im[4];
-          digits4(fixed30(v.x, rowe[m]), re);
-          digits4(fixed30(v.y, rowe[m]), im);
 #pragma unroll
-          for (int p = 0; p < 4; ++p) {
-            uint8_t* pl = st + p * PLANE_BYTES;
-            st_bf2(pl, 2 * m, 2 * k, re[p], -im[p]);
-            st_bf2(pl, 2 * m + 1, 2 * k, im[p], re[p]);
-          }
-        }
-        // B: 32 complex k x 64 complex n -> 4 digit planes of 64 rows x 64 bf16
-        for (int e = tid; e < XN * XKC; e += NPROD) {
-          const int n = e % XN, k = e / XN;
-          const int gc = n0 + n, gk = k0 + k;
-          cplx v = {0.0, 0.0};
-          if (gc < t.cols && gk < sg.k) {
-            if (sg.op_b == OP_N) v = bp[(long long)gk * sg.ldb + gc];
-            else {
-              v = bp[(long long)gc * sg.ldb + gk];
-              v.y = -v.y;
-            }
-          }
-          float re[4], im[4];
-          digits4(fixed30(v.x, cole[n]), re);
-          digits4(fixed30(v.y, cole[n]), im);
+          for (int j = 0; j < NB; ++j) {
+            const int e = tid + j * XPROD, n = e % XN, k = e / XN;
 #pragma unroll
-          for (int p = 0; p < 4; ++p) st_bf2(st + 4 * PLANE_BYTES + p * (64 * 128), n, 2 * k, re[p], im[p]);
+            for (int p = 0; p < 4; ++p)
+              st_bf2(st + 4 * PLANE_BYTES + p * (64 * 128), n, 2 * k, sbyte(wb[j], p), sbyte(wb[j], 4 + p));
+          }
+          fence_proxy_async();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&full_bar[s]);
         }
-        fence_proxy_async();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&full_bar[s]);
       }
     }
-    // epilogue: combine the four order accumulators exactly, convert once
-    if (mbar_wait(&done_bar, 0, verr)) {
+  } else if (warp == XMMA_WARP) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      constexpr uint32_t idesc = make_idesc(1u, 128, XN);
+      int it = 0, j = 0;
+      bool ok = true;
+      for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
+        const GemmTask t = tasks[tiles[ti].x];
+        if (task_chunks(t, segs) == 0) continue;
+        const int buf = j & 1;
+        if (!mbar_wait(&tempty[buf], ((j >> 1) & 1) ^ 1, verr)) break;
+        tc_fence_after();
+        const uint32_t acc = tmem + buf * XACC;
+        uint32_t started = 0;  // bit o set once accumulator o has been written
+        for (int sgi = 0; sgi < t.seg_count && ok; ++sgi) {
+          const int kk = segs[t.seg_begin + sgi].k;
+          for (int k0 = 0; k0 < kk; k0 += XKC, ++it) {
+            const int s = it % XSTAGES;
+            if (!mbar_wait(&full_bar[s], (it / XSTAGES) & 1, verr)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t st = smem_u32(stage_base + (size_t)s * XSTAGE);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {  // 4 k-steps of 16 bf16 (32 bytes)
+              const uint32_t koff = q * 32;
+              uint64_t a[4], b[4];
+#pragma unroll
+              for (int p = 0; p < 4; ++p) {
+                a[p] = sw128_desc(st + p * PLANE_BYTES + koff);
+                b[p] = sw128_desc(st + 4 * PLANE_BYTES + p * (64 * 128) + koff);
+              }
+#pragma unroll
+              for (int o = 0; o < 4; ++o) {
+#pragma unroll
+                for (int i = 0; i <= o; ++i) {
+                  mma<1>(acc + o * XN, a[i], b[o - i], idesc, (started >> o) & 1);
+                  started |= 1u << o;
+                }
+              }
+            }
+            mma_commit(&empty_bar[s]);
+          }
+        }
+        if (ok) mma_commit(&tfull[buf]);
+        ++j;
+      }
+    }
+  } else {
+    // ---------------- epilogue (warps 9-12: TMEM lane quarters 1, 2, 3, 0) ----------------
+    const int quarter = warp & 3;
+    const int etid = tid - (XPROD + 32);  // 0..127
+    int j = 0;
+    for (int ti = blockIdx.x; ti < ntiles && !*verr; ti += gridDim.x) {
+      const int3 tr = tiles[ti];
+      const GemmTask t = tasks[tr.x];
+      cplx* const cptr = rebase(B, t.c_base, t.c);
+      const int m0 = tr.y * TM, n0 = tr.z * XN;
+      if (task_chunks(t, segs) == 0) {  // no contribution: the output tile is zero
+        for (int e = etid; e < TM * XN; e += 128) {
+          const int r = m0 + e / XN, c = n0 + e % XN;
+          if (r < t.rows && c < t.cols) cptr[(long long)r * t.ldc + c] = {0.0, 0.0};
+        }
+        continue;
+      }
+      const int buf = j & 1;
+      if (!mbar_wait(&tfull[buf], (j >> 1) & 1, verr)) break;
       tc_fence_after();
-      const int row = warp * 32 + lane;
+      const int row = quarter * 32 + lane;
       const int m = row >> 1, part = row & 1;
       const int gr = m0 + m;
-      const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+      const int re_m = gr < t.rows ? exps[t.roff + gr] : 0;
+      const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) + buf * XACC;
       for (int c0 = 0; c0 < XN; c0 += 16) {
         uint32_t a0[16], a1[16], a2[16], a3[16];
         tmem_ld16<16>(lane_addr + 0 * XN + c0, a0);
@@ -587,14 +675,14 @@ __global__ void __launch_bounds__(NTHREADS, 2)
         if (gr < t.rows) {
           double* out = reinterpret_cast<double*>(cptr + (long long)gr * t.ldc);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int n = c0 + j, gc = n0 + n;
+          for (int jj = 0; jj < 16; ++jj) {
+            const int gc = n0 + c0 + jj;
             if (gc >= t.cols) continue;
-            long long V = (long long)__float2ll_rn(__uint_as_float(a0[j]));
-            V = (V << 8) + (long long)__float2ll_rn(__uint_as_float(a1[j]));
-            V = (V << 8) + (long long)__float2ll_rn(__uint_as_float(a2[j]));
-            V = (V << 8) + (long long)__float2ll_rn(__uint_as_float(a3[j]));
-            const int ee = rowe[m] + cole[n] - 36;
+            long long V = (long long)__float2ll_rn(__uint_as_float(a0[jj]));
+            V = (V << 8) + (long long)__float2ll_rn(__uint_as_float(a1[jj]));
+            V = (V << 8) + (long long)__float2ll_rn(__uint_as_float(a2[jj]));
+            V = (V << 8) + (long long)__float2ll_rn(__uint_as_float(a3[jj]));
+            const int ee = re_m + exps[t.coff + gc] - 36;
             double r = 0.0;
             if (V != 0 && ee > -900) {
               // exact power-of-two scaling by adding to the exponent field of (double)V
@@ -604,50 +692,17 @@ __global__ void __launch_bounds__(NTHREADS, 2)
           }
         }
       }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[buf]);
+      ++j;
     }
-  } else if (warp == 4 && lane == 0) {
-    constexpr uint32_t idesc = make_idesc(1u, 128, XN);
-    uint32_t started = 0;  // bit o set once accumulator o has been written
-    int it = 0;
-    bool ok = true;
-    for (int sgi = 0; sgi < t.seg_count && ok; ++sgi) {
-      const int kk = segs[t.seg_begin + sgi].k;
-      for (int k0 = 0; k0 < kk; k0 += XKC, ++it) {
-        const int s = it % XSTAGES;
-        if (!mbar_wait(&full_bar[s], (it / XSTAGES) & 1, verr)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t st = smem_u32(stage_base + (size_t)s * XSTAGE);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {  // 4 k-steps of 16 bf16 (32 bytes)
-          const uint32_t koff = q * 32;
-          uint64_t a[4], b[4];
-#pragma unroll
-          for (int p = 0; p < 4; ++p) {
-            a[p] = sw128_desc(st + p * PLANE_BYTES + koff);
-            b[p] = sw128_desc(st + 4 * PLANE_BYTES + p * (64 * 128) + koff);
-          }
-#pragma unroll
-          for (int o = 0; o < 4; ++o) {
-#pragma unroll
-            for (int i = 0; i <= o; ++i) {
-              mma<1>(tmem + o * XN, a[i], b[o - i], idesc, (started >> o) & 1);
-              started |= 1u << o;
-            }
-          }
-        }
-        mma_commit(&empty_bar[s]);
-      }
-    }
-    if (ok) mma_commit(&done_bar);
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * XACC) : "memory");
   }
   if (tid == 0 && err) atomicAdd(status, 1);
 }
@@ -663,7 +718,7 @@ int split_tile_m() { return TM; }
 int split_tile_n(int kind) { return kind == 0 ? TN : XN; }
 
 void launch_gemm_split(int kind, const GemmTask* tasks, const GemmSeg* segs, const int3* tiles, int ntiles,
-                       const Bases4& B, int* status, cudaStream_t s) {
+                       const int* exps, const Bases4& B, int* status, cudaStream_t s) {
   if (ntiles <= 0) return;
   if (kind == 0) {
     static bool init = false;
@@ -675,15 +730,32 @@ void launch_gemm_split(int kind, const GemmTask* tasks, const GemmSeg* segs, con
     note_launch();
     gemm_split_kernel<0><<<ntiles, NTHREADS, sm, s>>>(tasks, segs, tiles, B, status);
   } else {
-    static bool init = false;
+    static int nsm = 0;
     size_t sm = (size_t)XSTAGES * XSTAGE + 1024;
-    if (!init) {
+    if (!nsm) {
       cudaFuncSetAttribute(gemm_exact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      init = true;
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      if (nsm < 1) nsm = 1;
     }
     note_launch();
-    gemm_exact_kernel<<<ntiles, NTHREADS, sm, s>>>(tasks, segs, tiles, B, status);
+    gemm_exact_kernel<<<ntiles < nsm ? ntiles : nsm, XTHREADS, sm, s>>>(tasks, segs, tiles, ntiles, B, exps, status);
   }
+}
+
+int digit_job_size() { return DIGIT_JOB; }
+
+void launch_digits(const DigitOp* ops, int nops, const int2* jobs, int njobs, unsigned long long* maxv, int* exps,
+                   int ngrp, const Bases4& B, cudaStream_t s) {
+  if (nops <= 0) return;
+  cudaMemsetAsync(maxv, 0, (size_t)ngrp * sizeof(unsigned long long), s);
+  note_launch();
+  digit_max_kernel<<<nops, 256, 0, s>>>(ops, B, maxv);
+  note_launch();
+  digit_exp_kernel<<<(ngrp + 255) / 256 < 1184 ? (ngrp + 255) / 256 : 1184, 256, 0, s>>>(maxv, exps, ngrp);
+  note_launch();
+  digit_convert_kernel<<<njobs, 256, 0, s>>>(ops, jobs, B, exps);
 }
 
 }  // namespace tdvp
