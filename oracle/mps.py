@@ -175,6 +175,14 @@ def heff1(Lenv, W, Renv, M):
     return X
 
 
+def heff0(Lenv, Renv, C):
+    """Zero-site effective Hamiltonian on the bond matrix between two sites:
+    C'[a',b'] = sum L[a',w,a] C[a,b] R[b,w,b'] (the projector term of the bond in
+    the one-site projector-splitting integrator, Sec. S2.2)."""
+    X = np.tensordot(Lenv, C, axes=([2], [0]))             # [a', w, b]
+    return np.tensordot(X, Renv, axes=([1, 2], [1, 0]))    # [a', b']
+
+
 def energy(mps, W) -> float:
     E = left_edge(W)
     for A in mps:
@@ -331,6 +339,51 @@ class DenseTDVP:
             self.bond_lr(i, tau, chi_max, eps, i < L - 2)
         for i in range(L - 2, -1, -1):
             self.bond_rl(i, tau, chi_max, eps, i > 0)
+
+    # ----- one-site TDVP (Sec. S2.2: after the bond dimension saturates) -----
+    # Left to right with tau: the centre site is evolved forward, QR-split into a
+    # left-orthonormal A and a bond matrix C, C is evolved backward with the
+    # zero-site H_eff and absorbed into the next site; the last site of the half
+    # sweep is evolved forward only.  Right to left mirrors it with an LQ split.
+    # The bond dimensions never change (QR keeps min(rows, cols) columns).
+
+    def site_lr(self, i, tau, shift):
+        mps, W = self.mps, self.W
+        Le, Re = self.Lenv[i], self.R[i + 1]
+        mps[i] = self._expm(lambda x: heff1(Le, W, Re, x), mps[i], tau)
+        if not shift:
+            return
+        a, d, b = mps[i].shape
+        Q, C = np.linalg.qr(mps[i].reshape(a * d, b))
+        mps[i] = Q.reshape(a, d, Q.shape[1])
+        self.Lenv[i + 1] = update_left(Le, mps[i], W)
+        L1 = self.Lenv[i + 1]
+        C = self._expm(lambda x: heff0(L1, Re, x), C, -tau)
+        mps[i + 1] = np.tensordot(C, mps[i + 1], axes=([1], [0]))
+
+    def site_rl(self, i, tau, shift):
+        mps, W = self.mps, self.W
+        Le, Re = self.Lenv[i], self.R[i + 1]
+        mps[i] = self._expm(lambda x: heff1(Le, W, Re, x), mps[i], tau)
+        if not shift:
+            return
+        a, d, b = mps[i].shape
+        Q, C = np.linalg.qr(mps[i].reshape(a, d * b).conj().T)  # M = C^H Q^H
+        B = Q.conj().T
+        mps[i] = B.reshape(B.shape[0], d, b)
+        self.R[i] = update_right(Re, mps[i], W)
+        R1 = self.R[i]
+        Cl = self._expm(lambda x: heff0(Le, R1, x), C.conj().T, -tau)
+        mps[i - 1] = np.tensordot(mps[i - 1], Cl, axes=([2], [0]))
+
+    def step1(self, dt):
+        """One second-order one-site TDVP time step (centre on site 0 before and after)."""
+        L = self.L
+        tau = dt / 2
+        for i in range(L):
+            self.site_lr(i, tau, i < L - 1)
+        for i in range(L - 1, -1, -1):
+            self.site_rl(i, tau, i > 0)
 
     def bond_dims(self):
         return [A.shape[2] for A in self.mps[:-1]]

@@ -145,3 +145,91 @@ def test_dense_tdvp_truncated_run_stays_physical():
     assert max(sim.bond_dims()) <= 4
     assert abs(o["norm"] - 1) < 1e-12
     assert np.abs(o["n"] - 1).max() < 1e-3
+
+
+# ---------------------------------------------------------------------------
+# one-site TDVP (Sec. S2.2, used once the bond dimension has saturated)
+# ---------------------------------------------------------------------------
+
+def _copy_sim(sim, L, J, U):
+    c = mps.DenseTDVP(L, J, U, kmax=30, krylov_tol=1e-14)
+    c.mps = [A.copy() for A in sim.mps]
+    c._build_right_envs()
+    return c
+
+
+def test_dense_tdvp1_full_rank_is_exact():
+    """At full bond dimension the one-site tangent space is the whole Hilbert space, so
+    the one-site projector-splitting integrator reproduces exact evolution."""
+    for L, steps in ((4, 10), (6, 12)):
+        J, U = 1.0, 4.0
+        sim = mps.DenseTDVP(L, J, U, kmax=30, krylov_tol=1e-14)
+        for _ in range(steps):
+            sim.step(0.05, 10**6, 0.0)
+        full = [min(4 ** (i + 1), 4 ** (L - i - 1)) for i in range(L - 1)]
+        assert sim.bond_dims() == full
+        one = _copy_sim(sim, L, J, U)
+        psi0 = mps.full_state(one.mps)
+        ref = ed.evolve(ed.fock_hamiltonian(L, J, U), psi0, [0.4])[0]
+        for _ in range(4):
+            one.step1(0.1)
+        assert np.abs(mps.full_state(one.mps) - ref).max() < 1e-11
+
+
+def test_dense_tdvp1_conserves_energy_norm_and_bonds():
+    """Below full rank the one-site integrator still conserves energy and norm exactly
+    (up to the Krylov tolerance) and never changes a bond dimension."""
+    L, J, U = 8, 1.0, 4.0
+    sim = mps.DenseTDVP(L, J, U, kmax=30, krylov_tol=1e-14)
+    for _ in range(6):
+        sim.step(0.05, 16, 1e-12)
+    dims = sim.bond_dims()
+    assert max(dims) == 16
+    one = _copy_sim(sim, L, J, U)
+    E0 = one.observables()["energy"]
+    for _ in range(4):
+        one.step1(0.05)
+    o = one.observables()
+    assert abs(o["energy"] - E0) < 1e-11
+    assert abs(np.linalg.norm(mps.full_state(one.mps)) - 1.0) < 1e-12
+    assert one.bond_dims() == dims
+
+
+def test_heff0_is_the_projected_hamiltonian():
+    """H_eff^0 on the bond matrix equals <psi(C1)| H |psi(C2)> for the mixed-canonical
+    embedding psi(C) = A_0..A_i C B_{i+1}..B_{L-1}, computed with the dense H."""
+    L, J, U = 4, 1.0, 4.0
+    rng = np.random.default_rng(5)
+    sim = mps.DenseTDVP(L, J, U)
+    for _ in range(3):
+        sim.step(0.1, 16, 0.0)
+    W = sim.W
+    # left-orthonormal A_0, A_1 by QR sweeps; B_2, B_3 right-orthonormal already
+    A = [x.copy() for x in sim.mps]
+    for i in range(2):
+        a, d, b = A[i].shape
+        Q, R = np.linalg.qr(A[i].reshape(a * d, b))
+        A[i] = Q.reshape(a, d, Q.shape[1])
+        A[i + 1] = np.tensordot(R, A[i + 1], axes=([1], [0]))
+    Le = mps.left_edge(W)
+    for i in range(2):
+        Le = mps.update_left(Le, A[i], W)
+    Re = mps.right_edge(W)
+    for i in (3, 2):
+        a, d, b = A[i].shape
+        if i == 2:  # make B_2 right-orthonormal (A[2] carries the centre after the QR sweep)
+            Q, R = np.linalg.qr(A[2].reshape(a, d * b).conj().T)
+            A[2] = Q.conj().T.reshape(Q.shape[1], d, b)
+        Re = mps.update_right(Re, A[i], W)
+    k = A[1].shape[2]
+    C1 = rng.normal(size=(k, k)) + 1j * rng.normal(size=(k, k))
+    C2 = rng.normal(size=(k, k)) + 1j * rng.normal(size=(k, k))
+
+    def embed(C):
+        t = [A[0], np.tensordot(A[1], C, axes=([2], [0])), A[2], A[3]]
+        return mps.full_state(t)
+
+    H = ed.fock_hamiltonian(L, J, U)
+    want = np.vdot(embed(C1), H @ embed(C2))
+    got = np.vdot(C1, mps.heff0(Le, Re, C2))
+    assert abs(got - want) < 1e-10 * abs(want)
