@@ -101,6 +101,25 @@ int tdvp_create_random(int L, double J, double U, int symmetry, long long chi_ta
  * TDVP_ENUMERIC, TDVP_ECUDA, TDVP_ENOMEM. */
 int tdvp_step(tdvp_ctx* ctx, double dt, long long chi_max, double eps_trunc);
 
+/* Integrator of tdvp_step_mode. */
+enum { TDVP_SWEEP_TWO_SITE = 0, TDVP_SWEEP_ONE_SITE = 1, TDVP_SWEEP_ADAPTIVE = 2 };
+
+/* One time step dt with the chosen integrator (Sec. S2.2).
+ *   TDVP_SWEEP_TWO_SITE: exactly tdvp_step.
+ *   TDVP_SWEEP_ONE_SITE: the second-order one-site sweep: left to right with
+ *     tau = dt/2 every site is evolved forward with the one-site H_eff, split as
+ *     M = A C (repeated Cholesky QR in FP64), C is evolved backward with the
+ *     zero-site H_eff and absorbed into the next site; right to left mirrors it
+ *     with M = C Q.  Bond dimensions never change; chi_max and eps_trunc are not
+ *     used; energy and norm are conserved up to the Krylov tolerance.
+ *   TDVP_SWEEP_ADAPTIVE: two-site steps until a step in which the chi_max cap
+ *     (rather than the discarded-weight rule) set the kept set at some bond; from
+ *     then on one-site steps ("switch once the bond dimension has saturated").
+ * used (nullable) receives the integrator this step used (0 or 1).  The centre
+ * must be on site 0 (it is again afterwards).  Errors: as tdvp_step; a
+ * non-positive Cholesky pivot (rank-deficient site tensor) gives TDVP_ENUMERIC. */
+int tdvp_step_mode(tdvp_ctx* ctx, double dt, long long chi_max, double eps_trunc, int mode, int* used);
+
 /* One two-site update of the sweep (Sec. S2.2) at bond (bond, bond+1), the unit
  * the full step repeats L-1 times per half sweep: theta formation, the Krylov
  * exponential exp(-i dt/2 H_eff), the per-sector SVD with truncation (same rule
@@ -141,7 +160,9 @@ int tdvp_bond_dims(tdvp_ctx* ctx, long long* chi, long long* chi_red);
  * boundaries), out[13] number of steps, out[14] number of SVD splits, out[15]
  * FP64 Jacobi sweeps summed over the splits (counting the final sweep that found
  * nothing left to rotate), out[16] FP32 preconditioner sweeps (split-precision
- * modes).  n = length of out (at most 17). */
+ * modes), out[17] one-site steps.  In one-site steps the phase timers hold:
+ * out[9] forward one-site Krylov, out[10] gauge shift, out[11] environment update,
+ * out[12] zero-site Krylov and absorption.  n = length of out (at most 18). */
 int tdvp_stats(tdvp_ctx* ctx, double* out, int n);
 
 /* ---- single-bond problems (the effective-Hamiltonian benchmark) ------------

@@ -46,6 +46,7 @@ def lib():
             "tdvp_opts_default": (None, [P(Opts)]),
             "tdvp_create": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_int, P(Opts), P(vp)]),
             "tdvp_step": (C.c_int, [vp, C.c_double, C.c_longlong, C.c_double]),
+            "tdvp_step_mode": (C.c_int, [vp, C.c_double, C.c_longlong, C.c_double, C.c_int, P(C.c_int)]),
             "tdvp_create_random": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_int, C.c_longlong, C.c_ulonglong,
                                              C.c_int, P(Opts), P(vp)]),
             "tdvp_bond_update": (C.c_int, [vp, C.c_int, C.c_int, C.c_double, C.c_longlong, C.c_double, vp]),
@@ -204,8 +205,14 @@ class Chain(_Ctx):
             check(lib().tdvp_create_random(L, J, U, SYM[symmetry], int(random_chi), int(seed), int(center),
                                            C.byref(o), C.byref(self.h)))
 
-    def step(self, dt, chi_max, eps):
-        check(lib().tdvp_step(self.h, dt, int(chi_max), eps))
+    def step(self, dt, chi_max, eps, mode="two"):
+        """One time step; mode "two" (two-site), "one" (one-site, bond dimensions
+        fixed) or "adaptive" (two-site until the chi cap binds, then one-site).
+        Returns the integrator used ("two" or "one")."""
+        m = {"two": 0, "one": 1, "adaptive": 2}[mode]
+        used = C.c_int()
+        check(lib().tdvp_step_mode(self.h, dt, int(chi_max), eps, m, C.byref(used)))
+        return "one" if used.value == 1 else "two"
 
     def measure(self, entropy=True, energy=True):
         L = self.L
@@ -241,11 +248,11 @@ class Chain(_Ctx):
         return chi, red
 
     def stats(self):
-        v = np.zeros(17)
-        check(lib().tdvp_stats(self.h, v.ctypes.data, 17))
+        v = np.zeros(18)
+        check(lib().tdvp_stats(self.h, v.ctypes.data, 18))
         keys = ["seconds", "heff_flops", "env_flops", "matvecs", "max_krylov", "max_discarded", "chi_max_seen",
                 "t_theta", "t_plan", "t_krylov2", "t_split", "t_env", "t_krylov1", "steps", "splits", "sweeps64",
-                "sweeps32"]
+                "sweeps32", "one_site_steps"]
         return dict(zip(keys, v.tolist()))
 
 

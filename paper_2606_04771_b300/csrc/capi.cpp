@@ -130,6 +130,15 @@ int tdvp_step(tdvp_ctx* ctx, double dt, long long chi_max, double eps_trunc) {
   return guarded([&] { ctx->eng->step(dt, chi_max, eps_trunc); });
 }
 
+int tdvp_step_mode(tdvp_ctx* ctx, double dt, long long chi_max, double eps_trunc, int mode, int* used) {
+  if (!ctx) return fail(TDVP_EINVAL, "ctx is NULL");
+  if (mode < 0 || mode > 2) return fail(TDVP_EINVAL, "mode must be 0, 1 or 2");
+  return guarded([&] {
+    int u = ctx->eng->step_mode(dt, chi_max, eps_trunc, mode);
+    if (used) *used = u;
+  });
+}
+
 int tdvp_bond_update(tdvp_ctx* ctx, int bond, int direction, double dt, long long chi_max, double eps_trunc,
                      double* s_ent) {
   if (!ctx) return fail(TDVP_EINVAL, "ctx is NULL");
@@ -175,11 +184,11 @@ int tdvp_stats(tdvp_ctx* ctx, double* out, int n) {
   if (!ctx || !out) return fail(TDVP_EINVAL, "NULL argument");
   return guarded([&] {
     const tdvp::StepStats& s = ctx->eng->stats();
-    double v[17] = {s.seconds, (double)s.heff_flops, (double)s.env_flops, (double)s.matvecs, (double)s.max_krylov,
+    double v[18] = {s.seconds, (double)s.heff_flops, (double)s.env_flops, (double)s.matvecs, (double)s.max_krylov,
                     s.max_discarded, (double)s.chi_max_seen, s.phase[0], s.phase[1], s.phase[2], s.phase[3],
                     s.phase[4], s.phase[5], (double)s.steps, (double)s.splits, (double)s.sweeps64,
-                    (double)s.sweeps32};
-    for (int i = 0; i < n && i < 17; ++i) out[i] = v[i];
+                    (double)s.sweeps32, (double)s.one_site_steps};
+    for (int i = 0; i < n && i < 18; ++i) out[i] = v[i];
   });
 }
 

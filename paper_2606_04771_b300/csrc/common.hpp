@@ -134,6 +134,14 @@ struct BasisTask {  // x[i][kk] = g[i, perm[kk]] / sv[kk] (or / sv[kk]^2); g col
   int pow2;
 };
 
+// One Cholesky factorisation K = R^H R of a Hermitian positive definite q x q matrix
+// (row-major, overwritten by R, upper triangular) and the inverse rinv = R^-1.
+struct CholTask {
+  cplx* k;
+  cplx* rinv;
+  int q;
+};
+
 struct NsTask {  // g <- 1.5 I - 0.5 g (k x k)
   cplx* g;
   int k;

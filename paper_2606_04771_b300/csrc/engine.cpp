@@ -641,11 +641,12 @@ Engine::~Engine() {
 }
 
 void Engine::check_status() {
-  int hs[2] = {0, 0};
-  TDVP_CUDA(cudaMemcpyAsync(hs, dstatus_, 2 * sizeof(int), cudaMemcpyDeviceToHost, stream_));
+  int hs[3] = {0, 0, 0};
+  TDVP_CUDA(cudaMemcpyAsync(hs, dstatus_, 3 * sizeof(int), cudaMemcpyDeviceToHost, stream_));
   TDVP_CUDA(cudaStreamSynchronize(stream_));
   if (hs[1] != 0) throw Error(-7, "a tensor-core GEMM gave up waiting on a pipeline barrier");
   if (hs[0] != 0) throw Error(-4, "Jacobi iteration did not converge");
+  if (hs[2] != 0) throw Error(-4, "Cholesky QR met a non-positive pivot (rank-deficient site tensor)");
 }
 
 void Engine::alloc(BTensor& t, bool zero) {
@@ -1420,8 +1421,9 @@ double Engine::split(BTensor& theta, const BondSpace& bl, const BondSpace& br, l
   std::vector<int> kept(ng);
   double hstats[8];
   TDVP_CUDA(cudaMemcpyAsync(kept.data(), dkept.p, ng * sizeof(int), cudaMemcpyDeviceToHost, stream_));
-  TDVP_CUDA(cudaMemcpyAsync(hstats, dstats.p, 5 * sizeof(double), cudaMemcpyDeviceToHost, stream_));
+  TDVP_CUDA(cudaMemcpyAsync(hstats, dstats.p, 6 * sizeof(double), cudaMemcpyDeviceToHost, stream_));
   TDVP_CUDA(cudaStreamSynchronize(stream_));
+  if (hstats[5] != 0.0) cap_hit_ = true;
   // new bond: kept sectors sorted by (n, t)
   std::vector<std::pair<std::pair<int, int>, int>> ns;
   for (int g = 0; g < ng; ++g)
@@ -1690,8 +1692,9 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
   std::vector<int> kept(ng);
   double hstats[8];
   TDVP_CUDA(cudaMemcpyAsync(kept.data(), dkept.p, ng * sizeof(int), cudaMemcpyDeviceToHost, stream_));
-  TDVP_CUDA(cudaMemcpyAsync(hstats, dstats.p, 5 * sizeof(double), cudaMemcpyDeviceToHost, stream_));
+  TDVP_CUDA(cudaMemcpyAsync(hstats, dstats.p, 6 * sizeof(double), cudaMemcpyDeviceToHost, stream_));
   TDVP_CUDA(cudaStreamSynchronize(stream_));
+  if (hstats[5] != 0.0) cap_hit_ = true;
   std::vector<std::pair<std::pair<int, int>, int>> ns;
   for (int g = 0; g < ng; ++g)
     if (kept[g] > 0) ns.push_back({{groups[g].n, groups[g].t}, g});
@@ -2027,6 +2030,403 @@ void Engine::step(double dt, long long chi_max, double eps) {
   check_status();
   stats_.seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   stats_.steps += 1;
+}
+
+// ---------------------------------------------------------------------------
+// one-site TDVP (Sec. S2.2: after the bond dimension has saturated the sweep
+// updates one site at a time and needs no truncated SVD)
+// ---------------------------------------------------------------------------
+
+// bond matrix on a bond: one d x d block per sector (it is an SU(2) scalar)
+void Engine::build_bond_layout(BTensor& t, const BondSpace& b) const {
+  t = BTensor();
+  t.kind = OMEGA;
+  for (int c = 0; c < (int)b.s.size(); ++c) t.add(bkey(c, 0, c), c, 0, c, 0, 0, b.s[c].d, b.s[c].d);
+}
+
+// Zero-site H_eff on the bond matrix: C'(a') = sum_{w,a} L(a',w,a) C(a) R(a,w,a').
+// In the reduced form every recoupling factor is 1: C is a scalar, so the Clebsch-
+// Gordan structure of L, C(a w|a'), meets the identical structure of R and
+// contracts to the identity by orthonormality.
+void Engine::plan_heff0(HeffPlan& p, const BTensor& Lenv, const BTensor& Renv, const BTensor& C) {
+  p = HeffPlan();
+  p.n = C.size;
+  p.t1.kind = THETA;
+  std::vector<int> t1l;                      // L block of each T1 block
+  std::map<int, std::vector<int>> by_out;    // a' -> T1 blocks
+  for (int lb = 0; lb < (int)Lenv.blocks.size(); ++lb) {
+    const Block& lk = Lenv.blocks[lb];
+    const int ap = lk.key[0], w = lk.key[1], a = lk.key[2];
+    if (C.find(bkey(a, 0, a)) < 0 || C.find(bkey(ap, 0, ap)) < 0) continue;
+    if (Renv.find(bkey(a, w, ap)) < 0) continue;
+    const int id = (int)t1l.size();
+    p.t1.add((uint64_t)id, ap, w, a, 0, 0, lk.rows, lk.cols);
+    t1l.push_back(lb);
+    by_out[ap].push_back(id);
+  }
+  alloc(p.t1, false);
+  for (int i = 0; i < (int)t1l.size(); ++i) {
+    const Block& lk = Lenv.blocks[t1l[i]];
+    const Block& cb = C.blocks[C.find(bkey(lk.key[2], 0, lk.key[2]))];
+    GemmTask t{};
+    t.c = p.t1.ptr(i);
+    t.rows = lk.rows;
+    t.cols = cb.cols;
+    t.ldc = cb.cols;
+    t.seg_begin = (int)p.g1.segs.size();
+    t.seg_count = 1;
+    GemmSeg sg{};
+    sg.a = Lenv.ptr(t1l[i]);
+    sg.lda = lk.cols;
+    sg.b = as_off(cb.off);
+    sg.b_base = 1;
+    sg.ldb = cb.cols;
+    sg.k = lk.cols;
+    sg.alpha = 1.0;
+    p.g1.segs.push_back(sg);
+    p.g1.tasks.push_back(t);
+    p.g1.flops += 8LL * lk.rows * lk.cols * cb.cols;
+  }
+  for (int ob = 0; ob < (int)C.blocks.size(); ++ob) {
+    const Block& o = C.blocks[ob];
+    GemmTask t{};
+    t.c = as_off(o.off);
+    t.c_base = 2;
+    t.rows = o.rows;
+    t.cols = o.cols;
+    t.ldc = o.cols;
+    t.seg_begin = (int)p.g3.segs.size();
+    int cnt = 0;
+    auto it = by_out.find(o.key[0]);
+    if (it != by_out.end())
+      for (int id : it->second) {
+        const Block& tb = p.t1.blocks[id];
+        const int rb = Renv.find(bkey(tb.key[2], tb.key[1], o.key[0]));
+        const Block& rk = Renv.blocks[rb];
+        GemmSeg sg{};
+        sg.a = p.t1.ptr(id);
+        sg.lda = tb.cols;
+        sg.b = Renv.ptr(rb);
+        sg.ldb = rk.cols;
+        sg.k = rk.rows;
+        sg.alpha = 1.0;
+        p.g3.segs.push_back(sg);
+        p.g3.flops += 8LL * o.rows * rk.rows * rk.cols;
+        ++cnt;
+      }
+    t.seg_count = cnt;
+    p.g3.tasks.push_back(t);
+  }
+  p.g1.finalize(stream_, gemm_kind_, dstatus_ + 1);
+  p.lc.finalize(stream_);
+  p.g3.finalize(stream_, gemm_kind_, dstatus_ + 1);
+}
+
+// Gauge shift by repeated Cholesky QR in FP64, three passes, the first with a
+// diagonal shift of 1e-14 tr(K)/q so that a numerically rank-deficient sector still
+// factorises (the later passes restore orthonormality).  right: per right-bond
+// sector c the matrix M_c (rows (a,s), q = d_c columns) becomes A_c with M_c = A_c C_c,
+// C_c = R3 R2 R1.  left: per left-bond sector a, M_a (p = d_a rows, columns (s,b)) =
+// R^H Q via the Gram matrix M_a M_a^H; C_a = (R3 R2 R1)^H so that M_a = C_a Q_a.
+void Engine::gauge_shift(BTensor& M, const BondSpace& b, BTensor& C, bool right) {
+  std::map<int, std::vector<int>> by;  // bond sector -> blocks of M
+  for (int bi = 0; bi < (int)M.blocks.size(); ++bi) by[M.blocks[bi].key[right ? 2 : 0]].push_back(bi);
+  build_bond_layout(C, b);
+  alloc(C, true);
+  std::vector<long long> off(b.s.size(), 0);
+  long long tot = 0;
+  for (int c = 0; c < (int)b.s.size(); ++c) {
+    off[c] = tot;
+    tot += (long long)b.s[c].d * b.s[c].d;
+  }
+  DevBuf dK(std::max<long long>(tot, 1) * sizeof(cplx), stream_), dRi(std::max<long long>(tot, 1) * sizeof(cplx), stream_);
+  DevBuf dT(std::max<long long>(tot, 1) * sizeof(cplx), stream_);
+  cplx *Kb = dK.as<cplx>(), *Ri = dRi.as<cplx>(), *Tb = dT.as<cplx>();
+  BTensor other;
+  other.kind = M.kind;
+  other.blocks = M.blocks;
+  other.map = M.map;
+  other.size = M.size;
+  alloc(other, false);
+  BTensor* cur = &M;
+  BTensor* nxt = &other;
+  std::vector<CholTask> ct;
+  for (auto& e : by) ct.push_back({Kb + off[e.first], Ri + off[e.first], b.s[e.first].d});
+  DevBuf dct = upload(ct, stream_);
+  for (int pass = 0; pass < 3; ++pass) {
+    GemmPlan gk, ga, gr;
+    for (auto& e : by) {
+      const int c = e.first, q = b.s[c].d;
+      GemmTask t{};
+      t.c = Kb + off[c];
+      t.rows = q;
+      t.cols = q;
+      t.ldc = q;
+      t.seg_begin = (int)gk.segs.size();
+      for (int bi : e.second) {
+        const Block& bk = M.blocks[bi];
+        GemmSeg sg{};
+        sg.alpha = 1.0;
+        sg.a = cur->ptr(bi);
+        sg.b = cur->ptr(bi);
+        sg.lda = bk.cols;
+        sg.ldb = bk.cols;
+        if (right) {  // K = sum blk^H blk
+          sg.op_a = OP_C;
+          sg.k = bk.rows;
+        } else {  // K = sum blk blk^H
+          sg.op_b = OP_C;
+          sg.k = bk.cols;
+        }
+        gk.segs.push_back(sg);
+      }
+      t.seg_count = (int)e.second.size();
+      gk.tasks.push_back(t);
+    }
+    gk.finalize(stream_);
+    gk.launch(stream_, Bases4{{0, 0, 0, 0}});
+    launch_chol_inv(dct.as<CholTask>(), (int)ct.size(), pass == 0 ? 1e-14 : 0.0, dstatus_ + 2, stream_);
+    // A = M R^-1 (right) or Q = R^-H M (left), block by block
+    for (auto& e : by) {
+      const int c = e.first, q = b.s[c].d;
+      for (int bi : e.second) {
+        const Block& bk = M.blocks[bi];
+        GemmTask t{};
+        t.c = nxt->ptr(bi);
+        t.rows = bk.rows;
+        t.cols = bk.cols;
+        t.ldc = bk.cols;
+        t.seg_begin = (int)ga.segs.size();
+        t.seg_count = 1;
+        GemmSeg sg{};
+        sg.alpha = 1.0;
+        if (right) {
+          sg.a = cur->ptr(bi);
+          sg.lda = bk.cols;
+          sg.b = Ri + off[c];
+          sg.ldb = q;
+          sg.k = q;
+        } else {
+          sg.a = Ri + off[c];
+          sg.lda = q;
+          sg.op_a = OP_C;
+          sg.b = cur->ptr(bi);
+          sg.ldb = bk.cols;
+          sg.k = q;
+        }
+        ga.segs.push_back(sg);
+        ga.tasks.push_back(t);
+      }
+    }
+    ga.finalize(stream_);
+    ga.launch(stream_, Bases4{{0, 0, 0, 0}});
+    // accumulated factor: C = R (first pass) or C <- R C
+    if (pass > 0)
+      for (auto& e : by) {
+        const int c = e.first, q = b.s[c].d;
+        GemmTask t{};
+        t.c = Tb + off[c];
+        t.rows = q;
+        t.cols = q;
+        t.ldc = q;
+        t.seg_begin = (int)gr.segs.size();
+        t.seg_count = 1;
+        GemmSeg sg{};
+        sg.alpha = 1.0;
+        sg.a = Kb + off[c];  // R: the upper triangle of K after the factorisation
+        sg.lda = q;
+        sg.b = C.ptr(C.find(bkey(c, 0, c)));
+        sg.ldb = q;
+        sg.k = q;
+        gr.segs.push_back(sg);
+        gr.tasks.push_back(t);
+      }
+    if (pass == 0) {
+      CopyPlan cp;  // C = R
+      for (auto& e : by) {
+        const int c = e.first, q = b.s[c].d;
+        CopyTask t{};
+        t.src = Kb + off[c];
+        t.dst = C.ptr(C.find(bkey(c, 0, c)));
+        t.rows = q;
+        t.cols = q;
+        t.src_rs = q;
+        t.src_cs = 1;
+        t.dst_rs = q;
+        t.dst_cs = 1;
+        cp.tasks.push_back(t);
+      }
+      cp.finalize(stream_);
+      cp.launch(stream_);
+    } else {
+      gr.finalize(stream_);
+      gr.launch(stream_, Bases4{{0, 0, 0, 0}});
+      CopyPlan cp;  // C = T
+      for (auto& e : by) {
+        const int c = e.first, q = b.s[c].d;
+        CopyTask t{};
+        t.src = Tb + off[c];
+        t.dst = C.ptr(C.find(bkey(c, 0, c)));
+        t.rows = q;
+        t.cols = q;
+        t.src_rs = q;
+        t.src_cs = 1;
+        t.dst_rs = q;
+        t.dst_cs = 1;
+        cp.tasks.push_back(t);
+      }
+      cp.finalize(stream_);
+      cp.launch(stream_);
+    }
+    std::swap(cur, nxt);
+  }
+  if (cur != &M) std::swap(M.buf, other.buf);
+  if (!right) {  // C_a = (R3 R2 R1)^H
+    CopyPlan cp;
+    for (auto& e : by) {
+      const int c = e.first, q = b.s[c].d;
+      CopyTask t{};
+      t.src = C.ptr(C.find(bkey(c, 0, c)));
+      t.dst = Tb + off[c];
+      t.rows = q;
+      t.cols = q;
+      t.src_rs = 1;
+      t.src_cs = q;
+      t.dst_rs = q;
+      t.dst_cs = 1;
+      t.conj = 1;
+      cp.tasks.push_back(t);
+    }
+    cp.finalize(stream_);
+    cp.launch(stream_);
+    TDVP_CUDA(cudaMemcpyAsync(C.data(), Tb, std::max<long long>(tot, 1) * sizeof(cplx), cudaMemcpyDeviceToDevice,
+                              stream_));
+  }
+}
+
+// M <- C M (blocks (c, s, b) of the site to the right of the bond) or M <- M C
+// (blocks (a, s, c) of the site to the left)
+void Engine::absorb(const BTensor& C, BTensor& M, bool from_left) {
+  BTensor out;
+  out.kind = M.kind;
+  out.blocks = M.blocks;
+  out.map = M.map;
+  out.size = M.size;
+  alloc(out, false);
+  GemmPlan g;
+  for (int bi = 0; bi < (int)M.blocks.size(); ++bi) {
+    const Block& bk = M.blocks[bi];
+    const int c = from_left ? bk.key[0] : bk.key[2];
+    const int cb = C.find(bkey(c, 0, c));
+    if (cb < 0) throw Error(-5, "bond matrix block missing");
+    const Block& ck = C.blocks[cb];
+    GemmTask t{};
+    t.c = out.ptr(bi);
+    t.rows = bk.rows;
+    t.cols = bk.cols;
+    t.ldc = bk.cols;
+    t.seg_begin = (int)g.segs.size();
+    t.seg_count = 1;
+    GemmSeg sg{};
+    sg.alpha = 1.0;
+    if (from_left) {
+      sg.a = C.ptr(cb);
+      sg.lda = ck.cols;
+      sg.b = M.ptr(bi);
+      sg.ldb = bk.cols;
+      sg.k = ck.cols;
+    } else {
+      sg.a = M.ptr(bi);
+      sg.lda = bk.cols;
+      sg.b = C.ptr(cb);
+      sg.ldb = ck.cols;
+      sg.k = bk.cols;
+    }
+    g.segs.push_back(sg);
+    g.tasks.push_back(t);
+    g.flops += 8LL * bk.rows * bk.cols * sg.k;
+  }
+  g.finalize(stream_, gemm_kind_, dstatus_ + 1);
+  g.launch(stream_, Bases4{{0, 0, 0, 0}});
+  stats_.env_flops += g.flops;
+  std::swap(M.buf, out.buf);
+}
+
+// one site of the one-site sweep: forward evolution of the centre by tau, then (if
+// shift) the gauge shift towards the sweep direction, the environment update, the
+// backward evolution of the bond matrix by tau and its absorption into the next site
+void Engine::site_update1(int i, bool left_to_right, double tau, bool shift) {
+  auto tp = std::chrono::steady_clock::now();
+  auto mark = [&](int ph) {
+    if (!profile_) return;
+    cudaStreamSynchronize(stream_);
+    auto now = std::chrono::steady_clock::now();
+    stats_.phase[ph] += std::chrono::duration<double>(now - tp).count();
+    tp = now;
+  };
+  {
+    HeffPlan H1;
+    plan_heff1(H1, Lenv_[i], Renv_[i + 1], site_[i], bonds_[i], bonds_[i + 1]);
+    mark(1);
+    expm(H1, site_[i].data(), tau);
+    mark(2);
+  }
+  if (!shift) return;
+  BTensor C;
+  if (left_to_right) {
+    gauge_shift(site_[i], bonds_[i + 1], C, true);
+    mark(3);
+    update_left_env(Lenv_[i], site_[i], Lenv_[i + 1], bonds_[i], bonds_[i + 1]);
+    mark(4);
+    HeffPlan H0;
+    plan_heff0(H0, Lenv_[i + 1], Renv_[i + 1], C);
+    mark(1);
+    expm(H0, C.data(), -tau);
+    absorb(C, site_[i + 1], true);
+    mark(5);
+    center_ = i + 1;
+  } else {
+    gauge_shift(site_[i], bonds_[i], C, false);
+    mark(3);
+    update_right_env(Renv_[i + 1], site_[i], Renv_[i], bonds_[i], bonds_[i + 1]);
+    mark(4);
+    HeffPlan H0;
+    plan_heff0(H0, Lenv_[i], Renv_[i], C);
+    mark(1);
+    expm(H0, C.data(), -tau);
+    absorb(C, site_[i - 1], false);
+    mark(5);
+    center_ = i - 1;
+  }
+}
+
+void Engine::step1(double dt) {
+  if (bond_only_) throw Error(-2, "a bond problem has no chain to evolve");
+  if (!(dt > 0)) throw Error(-1, "invalid step arguments");
+  if (center_ != 0) throw Error(-2, "a full time step starts with the orthogonality centre on site 0");
+  chain_heff_.reset();
+  auto t0 = std::chrono::steady_clock::now();
+  const double tau = dt / 2;
+  const int L = L_;
+  for (int i = 0; i < L; ++i) site_update1(i, true, tau, i + 1 < L);
+  for (int i = L - 1; i >= 0; --i) site_update1(i, false, tau, i > 0);
+  TDVP_CUDA(cudaStreamSynchronize(stream_));
+  check_status();
+  stats_.seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  stats_.steps += 1;
+  stats_.one_site_steps += 1;
+}
+
+int Engine::step_mode(double dt, long long chi_max, double eps, int mode) {
+  if (mode < 0 || mode > 2) throw Error(-1, "mode must be 0 (two-site), 1 (one-site) or 2 (adaptive)");
+  if (mode == 1 || (mode == 2 && saturated_)) {
+    step1(dt);
+    return 1;
+  }
+  cap_hit_ = false;
+  step(dt, chi_max, eps);
+  if (mode == 2 && cap_hit_) saturated_ = true;
+  return 0;
 }
 
 void Engine::single_bond(int i, int direction, double dt, long long chi_max, double eps, double* s_ent) {

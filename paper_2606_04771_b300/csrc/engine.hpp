@@ -148,6 +148,7 @@ struct StepStats {
   // Jacobi sweeps summed over the splits: FP64 (the FP64 split, or the FP64 finish
   // of the mixed split) and FP32 (the preconditioner of the mixed split)
   long long sweeps64 = 0, sweeps32 = 0, splits = 0;
+  long long one_site_steps = 0;
 };
 
 class Engine {
@@ -157,6 +158,11 @@ class Engine {
 
   // chain evolution
   void step(double dt, long long chi_max, double eps);
+  // one-site second-order step (bond dimensions fixed), Sec. S2.2
+  void step1(double dt);
+  // mode 0: two-site, 1: one-site, 2: adaptive (two-site until the chi cap binds in a
+  // step's truncation, one-site from then on); returns the mode used (0 or 1)
+  int step_mode(double dt, long long chi_max, double eps, int mode);
   // one bond update of the sweep at bond (i, i+1); direction 0: left to right (centre on i),
   // 1: right to left (centre on i+1); s_ent (nullable) receives the new bond's entropy
   void single_bond(int i, int direction, double dt, long long chi_max, double eps, double* s_ent);
@@ -215,6 +221,14 @@ class Engine {
                      bool absorb_right, BondSpace& bm, BTensor& X, BTensor& Y, double* s_ent, bool& ok);
   void bond_update(int i, bool left_to_right, double tau, long long chi_max, double eps, bool backward,
                    double* s_ent);
+  // one-site sweep pieces
+  void build_bond_layout(BTensor& t, const BondSpace& b) const;
+  void plan_heff0(HeffPlan& p, const BTensor& Lenv, const BTensor& Renv, const BTensor& C);
+  // Cholesky QR gauge shift: right: M (blocks (a,s,c)) = A C with A left-orthonormal;
+  // left: M (blocks (a,s,b)) = C Q with Q right-orthonormal; M is overwritten by A or Q
+  void gauge_shift(BTensor& M, const BondSpace& b, BTensor& C, bool right);
+  void absorb(const BTensor& C, BTensor& M, bool from_left);  // M <- C M (from_left) or M C
+  void site_update1(int i, bool left_to_right, double tau, bool shift);
   int expm(HeffPlan& H, cplx* x, double tau);  // returns the Krylov dimension used
 
   int L_ = 0;
@@ -231,6 +245,8 @@ class Engine {
   bool bond_only_ = false;
   bool profile_ = false;
   int center_ = 0;  // orthogonality centre
+  bool cap_hit_ = false;    // the chi cap set a truncation in the current two-site step
+  bool saturated_ = false;  // adaptive mode: one-site steps from now on
   // Krylov workspace
   DevBuf kv_, kw_, kpart_, kh1_, kh2_, knrm_, kstate_;
   long long kcap_ = 0;

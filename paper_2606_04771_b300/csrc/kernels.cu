@@ -1155,6 +1155,7 @@ __global__ void __launch_bounds__(TRUNC_THREADS) truncate_kernel(const TruncSect
     stats[2] = kw > 0 ? 1.0 / sqrt(kw) : 0.0;  // renormalisation of the kept values
     stats[3] = (double)K;
     stats[4] = (double)kchi;
+    stats[5] = keep_chi < keep_eps ? 1.0 : 0.0;  // the chi cap, not the tail rule, set K
   }
 }
 
@@ -1165,6 +1166,92 @@ void launch_truncate(const TruncSector* secs, int nsec, const int* offs, int n, 
   note_launch();
   truncate_kernel<<<1, TRUNC_THREADS, 0, s>>>(secs, nsec, offs, n, eps, chi_max, owner, order, kept, stats, vals);
   cudaFreeAsync(vals, s);
+}
+
+// ---------------------------------------------------------------------------
+// Gauge shift of the one-site sweep: Cholesky QR.  One CTA per matrix, in place,
+// right-looking: for each pivot j the row j is scaled by 1/sqrt(K_jj) and the
+// trailing upper triangle is updated, K_ik -= conj(R_ji) R_jk; then R^-1 by back
+// substitution, one column per thread.  shift_rel > 0 adds shift_rel * tr(K) / q to
+// the diagonal first (the shifted first pass of a repeated Cholesky QR, which keeps
+// a numerically rank-deficient K factorisable).  A non-positive pivot sets *status.
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) chol_inv_kernel(const CholTask* __restrict__ tasks, double shift_rel,
+                                                       int* __restrict__ status) {
+  const CholTask t = tasks[blockIdx.x];
+  const int q = t.q;
+  cplx* K = t.k;
+  __shared__ double sdiag;
+  __shared__ int bad;
+  if (threadIdx.x == 0) {
+    bad = 0;
+    double tr = 0.0;
+    for (int j = 0; j < q; ++j) tr += K[(long long)j * q + j].x;
+    sdiag = shift_rel > 0.0 ? shift_rel * tr / (q > 0 ? q : 1) : 0.0;
+  }
+  __syncthreads();
+  if (sdiag > 0.0)
+    for (int j = threadIdx.x; j < q; j += blockDim.x) K[(long long)j * q + j].x += sdiag;
+  __syncthreads();
+  for (int j = 0; j < q; ++j) {
+    const double d = K[(long long)j * q + j].x;
+    if (!(d > 0.0)) {
+      if (threadIdx.x == 0) bad = 1;
+      break;  // uniform: every thread read the same d
+    }
+    const double r = sqrt(d), ir = 1.0 / r;
+    __syncthreads();
+    for (int k = j + threadIdx.x; k < q; k += blockDim.x) {
+      cplx v = K[(long long)j * q + k];
+      K[(long long)j * q + k] = k == j ? cplx{r, 0.0} : cplx{v.x * ir, v.y * ir};
+    }
+    __syncthreads();
+    const int m = q - j - 1;  // trailing block rows/cols j+1..q-1, upper triangle
+    for (long long e = threadIdx.x; e < (long long)m * m; e += blockDim.x) {
+      const int i = j + 1 + (int)(e / m), k = j + 1 + (int)(e % m);
+      if (k < i) continue;
+      const cplx a = K[(long long)j * q + i], b = K[(long long)j * q + k];  // R_ji, R_jk
+      cplx& c = K[(long long)i * q + k];
+      c.x -= a.x * b.x + a.y * b.y;  // conj(a) b
+      c.y -= a.x * b.y - a.y * b.x;
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  if (bad) {
+    if (threadIdx.x == 0) atomicAdd(status, 1);
+    return;
+  }
+  // zero the strict lower triangle, then X = R^-1 column by column (upper triangular)
+  for (long long e = threadIdx.x; e < (long long)q * q; e += blockDim.x) {
+    const int i = (int)(e / q), k = (int)(e % q);
+    if (k < i) K[e] = {0.0, 0.0};
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < q; k += blockDim.x) {
+    cplx* X = t.rinv;
+    for (int i = q - 1; i >= 0; --i) {
+      cplx acc = {i == k ? 1.0 : 0.0, 0.0};
+      if (i <= k) {
+        for (int j = i + 1; j <= k; ++j) {
+          const cplx a = K[(long long)i * q + j], x = X[(long long)j * q + k];
+          acc.x -= a.x * x.x - a.y * x.y;
+          acc.y -= a.x * x.y + a.y * x.x;
+        }
+        const double ir = 1.0 / K[(long long)i * q + i].x;
+        X[(long long)i * q + k] = {acc.x * ir, acc.y * ir};
+      } else {
+        X[(long long)i * q + k] = {0.0, 0.0};
+      }
+    }
+  }
+}
+
+void launch_chol_inv(const CholTask* tasks, int n, double shift_rel, int* status, cudaStream_t s) {
+  if (n <= 0) return;
+  note_launch();
+  chol_inv_kernel<<<n, 256, 0, s>>>(tasks, shift_rel, status);
 }
 
 // ---------------------------------------------------------------------------

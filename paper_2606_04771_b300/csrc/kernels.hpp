@@ -71,6 +71,9 @@ void launch_narrow(const cplx* src, float2* dst, long long n, cudaStream_t s);
 void launch_widen(const float2* src, cplx* dst, long long n, cudaStream_t s);
 void launch_basis64(const BasisTask* tasks, int n, cudaStream_t s);
 void launch_ns_coeff(const NsTask* tasks, int n, cudaStream_t s);
+// in-place Cholesky K = R^H R (upper R) and R^-1 for each task; a non-positive pivot
+// adds 1 to *status
+void launch_chol_inv(const CholTask* tasks, int n, double shift_rel, int* status, cudaStream_t s);
 // round-robin one-sided Jacobi over all tasks at once, one warp per column pair
 // (same result layout as launch_jacobi_svd; v may be NULL); returns the sweeps run
 int run_jacobi_rounds(const SvdTask* d_tasks, const std::vector<SvdTask>& h_tasks, int max_sweeps, double tol,
