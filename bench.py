@@ -120,12 +120,15 @@ def init_dist():
 
 
 def max_over_ranks(x, ws):
+    """The largest value over the ranks (the slowest rank's time); NCCL reduces a
+    device tensor, gloo a host one."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 

@@ -270,6 +270,14 @@ int tdvp_svd_noalloc(int p, int q, const double* a, double* s, double* u, double
  * when it enqueues the kernel).  out must be non-NULL.  Errors: TDVP_EINVAL. */
 int tdvp_launch_count(long long* out);
 
+/* Self-test of failure detection: a kernel waits on an mbarrier that nothing
+ * arrives at, gives up after `polls` polls (the same bounded wait the GEMM
+ * pipelines use, which there runs 2^24 polls) and reports the expiry.  Returns
+ * TDVP_ETIMEOUT when the wait expired -- the expected outcome -- after which the
+ * CUDA context stays usable; TDVP_ECUDA on a CUDA error.  stream: cudaStream_t or
+ * NULL. */
+int tdvp_selftest_wait(unsigned int polls, void* stream);
+
 /* Destroy a context and free its device memory.  NULL is accepted. */
 int tdvp_destroy(tdvp_ctx* ctx);
 

@@ -3,4 +3,4 @@
 The compute path is the CUDA library ``libtdvp.so`` (sources in ``csrc/``,
 C ABI in ``include/tdvp.h``); this package only marshals arguments to it.
 """
-from ._lib import BondProblem, Chain, TdvpError, launch_count, lib  # noqa: F401
+from ._lib import BondProblem, Chain, TdvpError, launch_count, lib, svd  # noqa: F401

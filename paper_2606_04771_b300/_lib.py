@@ -66,6 +66,7 @@ def lib():
             "tdvp_svd": (C.c_int, [C.c_int, C.c_int, vp, vp, vp, vp, C.c_int, vp]),
             "tdvp_svd_noalloc": (C.c_int, [C.c_int, C.c_int, vp, vp, vp, vp, vp]),
             "tdvp_launch_count": (C.c_int, [P(C.c_longlong)]),
+            "tdvp_selftest_wait": (C.c_int, [C.c_uint, vp]),
             "tdvp_destroy": (C.c_int, [vp]),
             "tdvp_strerror": (C.c_char_p, [C.c_int]),
             "tdvp_last_error": (C.c_char_p, []),

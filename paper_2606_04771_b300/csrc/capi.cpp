@@ -174,6 +174,24 @@ int tdvp_bond_dims(tdvp_ctx* ctx, long long* chi, long long* chi_red) {
   });
 }
 
+int tdvp_selftest_wait(unsigned int polls, void* stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int* d = nullptr;
+  int h = 0;
+  cudaError_t e = cudaMallocAsync(&d, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d, 0, sizeof(int), st);
+  if (e == cudaSuccess) {
+    tdvp::launch_wait_selftest(polls, d, st);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaFreeAsync(d, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(TDVP_ECUDA, cudaGetErrorString(e));
+  if (h) return fail(TDVP_ETIMEOUT, "self-test wait expired as intended");
+  return TDVP_OK;
+}
+
 int tdvp_launch_count(long long* out) {
   if (!out) return fail(TDVP_EINVAL, "NULL argument");
   *out = tdvp::launch_count();

@@ -46,6 +46,8 @@ void launch_gemm_split(int kind, const GemmTask* tasks, const GemmSeg* segs, con
 // BF16x4 operand splitting (once per launch): group maxima, exponents, digit records.
 // jobs = (operand, first element) in steps of digit_job_size() elements.
 int digit_job_size();
+// one bounded wait on an mbarrier that never completes; adds 1 to *status on expiry
+void launch_wait_selftest(unsigned polls, int* status, cudaStream_t s);
 void launch_digits(const DigitOp* ops, int nops, const int2* jobs, int njobs, unsigned long long* maxv, int* exps,
                    int ngrp, const Bases4& B, cudaStream_t s);
 

@@ -712,6 +712,23 @@ size_t smem_bytes() {
   return (size_t)STAGES * 2 * Cfg<KIND>::PLANES * PLANE_BYTES + 1024;
 }
 
+// Self-test of the bounded-wait path: one thread waits on an mbarrier that nothing
+// arrives at, polls it `polls` times, gives up and records the expiry -- the same
+// give-up-and-report sequence every pipeline wait of the GEMM kernels follows.
+__global__ void wait_selftest_kernel(uint32_t polls, int* __restrict__ status) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bool done = false;
+    for (uint32_t it = 0; it < polls && !done; ++it) done = mbar_try(&bar, 0);
+    if (!done) atomicAdd(status, 1);
+  }
+}
+
 }  // namespace
 
 int split_tile_m() { return TM; }
@@ -745,6 +762,11 @@ void launch_gemm_split(int kind, const GemmTask* tasks, const GemmSeg* segs, con
 }
 
 int digit_job_size() { return DIGIT_JOB; }
+
+void launch_wait_selftest(unsigned polls, int* status, cudaStream_t s) {
+  note_launch();
+  wait_selftest_kernel<<<1, 32, 0, s>>>(polls, status);
+}
 
 void launch_digits(const DigitOp* ops, int nops, const int2* jobs, int njobs, unsigned long long* maxv, int* exps,
                    int ngrp, const Bases4& B, cudaStream_t s) {
