@@ -168,7 +168,11 @@ def heff_kernel_profile(args, dev, stream):
     bp.set_env(2, normed(nr))
     flops_mv = bp.heff_flops()
     pms, pfl, pby = (C.c_double * 3)(), (C.c_longlong * 3)(), (C.c_longlong * 3)()
+    import torch
+
+    torch.cuda.nvtx.range_push("heff_profile")
     check(lib().tdvp_heff_profile(bp.h, 5, pms, pfl, pby))
+    torch.cuda.nvtx.range_pop()
     stage_ms = list(pms)
     gemm_ms = stage_ms[0] + stage_ms[2]
     gemm_flops = pfl[0] + pfl[2]

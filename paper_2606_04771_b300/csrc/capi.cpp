@@ -246,6 +246,7 @@ int tdvp_set_tensor(tdvp_ctx* ctx, int which, const double* data, long long n, i
     TDVP_CUDA(cudaMemcpyAsync(t->data(), data, n * sizeof(tdvp::cplx),
                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
     TDVP_CUDA(cudaStreamSynchronize(s));
+    ctx->eng->environments_changed();
   });
 }
 

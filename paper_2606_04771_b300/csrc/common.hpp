@@ -49,6 +49,9 @@ struct GemmSeg {
   // B: k x cols, row-major, 8 bytes per complex element), filled per launch
   const unsigned long long* a_dig;
   const unsigned long long* b_dig;
+  // operand unchanged between launches of its plan (environment blocks): BF16x4
+  // splits it at the first launch only
+  int a_static, b_static;
 };
 
 // BF16x4: one distinct operand block split into digit records.  A operands get a

@@ -90,7 +90,8 @@ void GemmPlan::finalize(cudaStream_t s, int kind_, int* status_) {
 // across its B operands, so operands that meet in a task are merged (union-find)
 // into scale groups; a group's scales are the maxima over all of its operands.
 void GemmPlan::plan_digits(cudaStream_t s) {
-  typedef std::tuple<int, int, uintptr_t, int, int, int, int, double> Key;  // side, base, ptr, rows, cols, ld, op, alpha
+  // side, base, ptr, rows, cols, ld, op, alpha, static
+  typedef std::tuple<int, int, uintptr_t, int, int, int, int, double, int> Key;
   std::map<Key, int> idx;
   std::vector<Key> keys;
   std::vector<int> parent;
@@ -115,8 +116,10 @@ void GemmPlan::plan_digits(cudaStream_t s) {
       const int si = t.seg_begin + k;
       const GemmSeg& g = segs[si];
       if (g.k <= 0) continue;
-      const int ia = get(Key(0, g.a_base, reinterpret_cast<uintptr_t>(g.a), t.rows, g.k, g.lda, g.op_a, g.alpha));
-      const int ib = get(Key(1, g.b_base, reinterpret_cast<uintptr_t>(g.b), g.k, t.cols, g.ldb, g.op_b, 1.0));
+      const int ia = get(Key(0, g.a_base, reinterpret_cast<uintptr_t>(g.a), t.rows, g.k, g.lda, g.op_a, g.alpha,
+                             g.a_static != 0));
+      const int ib = get(Key(1, g.b_base, reinterpret_cast<uintptr_t>(g.b), g.k, t.cols, g.ldb, g.op_b, 1.0,
+                             g.b_static != 0));
       segop[si] = {ia, ib};
       if (first_a[i] < 0) first_a[i] = ia;
       else parent[find(ia)] = find(first_a[i]);
@@ -124,14 +127,26 @@ void GemmPlan::plan_digits(cudaStream_t s) {
       else parent[find(ib)] = find(first_b[i]);
     }
   }
-  // group offsets: A groups take rows entries, B groups cols entries
-  std::map<int, int> goff;
-  long long ng = 0;
+  // a group is static only if every operand in it is; static groups take the first
+  // offsets so that the per-launch maxima reset covers the dynamic range only
+  std::map<int, int> gstat;
   for (int i = 0; i < (int)keys.size(); ++i) {
     const int r = find(i);
-    if (goff.count(r)) continue;
-    goff[r] = (int)ng;
-    ng += std::get<0>(keys[r]) == 0 ? std::get<3>(keys[r]) : std::get<4>(keys[r]);
+    auto it = gstat.find(r);
+    const int st = std::get<8>(keys[i]);
+    if (it == gstat.end()) gstat[r] = st;
+    else it->second &= st;
+  }
+  std::map<int, int> goff;
+  long long ng = 0;
+  for (int pass = 1; pass >= 0; --pass) {
+    if (pass == 0) ngrp_static = (int)ng;
+    for (int i = 0; i < (int)keys.size(); ++i) {
+      const int r = find(i);
+      if (goff.count(r) || gstat[r] != pass) continue;
+      goff[r] = (int)ng;
+      ng += std::get<0>(keys[r]) == 0 ? std::get<3>(keys[r]) : std::get<4>(keys[r]);
+    }
   }
   if (ng > INT32_MAX) throw Error(-5, "GEMM plan too large for 32-bit scale offsets");
   ngrp = (int)ng;
@@ -145,35 +160,46 @@ void GemmPlan::plan_digits(cudaStream_t s) {
   dmax = DevBuf(std::max(ngrp, 1) * sizeof(unsigned long long), s);
   dexp = DevBuf(std::max(ngrp, 1) * sizeof(int), s);
   unsigned long long* dig = ddig.as<unsigned long long>();
-  dops.assign(keys.size(), DigitOp{});
-  djobs.clear();
+  std::vector<DigitOp> all(keys.size());
   const int job = digit_job_size();
-  for (int i = 0; i < (int)keys.size(); ++i) {
-    const Key& k = keys[i];
-    DigitOp& o = dops[i];
-    o.side = std::get<0>(k);
-    o.base = std::get<1>(k);
-    o.src = reinterpret_cast<const cplx*>(std::get<2>(k));
-    o.rows = std::get<3>(k);
-    o.cols = std::get<4>(k);
-    o.ld = std::get<5>(k);
-    o.op = std::get<6>(k);
-    o.alpha = std::get<7>(k);
-    o.grp = goff[find(i)];
-    o.dig = dig + roff[i];
-    const long long n = (long long)o.rows * o.cols;
-    for (long long e = 0; e < n; e += job) djobs.push_back(make_int2(i, (int)e));
+  for (int part = 0; part < 2; ++part) {  // 0: static operands, 1: dynamic
+    std::vector<DigitOp>& ops = part == 0 ? dops_s : dops_d;
+    std::vector<int2>& jobs = part == 0 ? djobs_s : djobs_d;
+    ops.clear();
+    jobs.clear();
+    for (int i = 0; i < (int)keys.size(); ++i) {
+      if ((gstat[find(i)] != 0) != (part == 0)) continue;
+      const Key& k = keys[i];
+      DigitOp o{};
+      o.side = std::get<0>(k);
+      o.base = std::get<1>(k);
+      o.src = reinterpret_cast<const cplx*>(std::get<2>(k));
+      o.rows = std::get<3>(k);
+      o.cols = std::get<4>(k);
+      o.ld = std::get<5>(k);
+      o.op = std::get<6>(k);
+      o.alpha = std::get<7>(k);
+      o.grp = goff[find(i)];
+      o.dig = dig + roff[i];
+      all[i] = o;
+      const long long n = (long long)o.rows * o.cols;
+      for (long long e = 0; e < n; e += job) jobs.push_back(make_int2((int)ops.size(), (int)e));
+      ops.push_back(o);
+    }
   }
   for (int i = 0; i < (int)tasks.size(); ++i) {
     if (first_a[i] >= 0) tasks[i].roff = goff[find(first_a[i])];
     if (first_b[i] >= 0) tasks[i].coff = goff[find(first_b[i])];
   }
   for (int si = 0; si < (int)segs.size(); ++si) {
-    segs[si].a_dig = segop[si].first >= 0 ? dops[segop[si].first].dig : nullptr;
-    segs[si].b_dig = segop[si].second >= 0 ? dops[segop[si].second].dig : nullptr;
+    segs[si].a_dig = segop[si].first >= 0 ? all[segop[si].first].dig : nullptr;
+    segs[si].b_dig = segop[si].second >= 0 ? all[segop[si].second].dig : nullptr;
   }
-  ddops = upload(dops, s);
-  djb = upload(djobs, s);
+  ddops_s = upload(dops_s, s);
+  djb_s = upload(djobs_s, s);
+  ddops_d = upload(dops_d, s);
+  djb_d = upload(djobs_d, s);
+  static_done = false;
   // the persistent kernel walks the tiles with a stride of the grid: the most
   // expensive (most K chunks) first balances the SMs
   std::vector<int> cost(tasks.size(), 0);
@@ -186,9 +212,15 @@ void GemmPlan::launch(cudaStream_t s, const Bases4& B) const {
   if (kind < 0)
     launch_gemm_fp64(dt.as<GemmTask>(), ds.as<GemmSeg>(), dti.as<int3>(), (int)tiles.size(), B, s);
   else {
-    if (kind == 1)
-      launch_digits(ddops.as<DigitOp>(), (int)dops.size(), djb.as<int2>(), (int)djobs.size(),
-                    dmax.as<unsigned long long>(), dexp.as<int>(), ngrp, B, s);
+    if (kind == 1) {
+      if (!static_done) {  // environment operands: split once per plan
+        launch_digits(ddops_s.as<DigitOp>(), (int)dops_s.size(), djb_s.as<int2>(), (int)djobs_s.size(),
+                      dmax.as<unsigned long long>(), dexp.as<int>(), 0, ngrp_static, B, s);
+        static_done = true;
+      }
+      launch_digits(ddops_d.as<DigitOp>(), (int)dops_d.size(), djb_d.as<int2>(), (int)djobs_d.size(),
+                    dmax.as<unsigned long long>(), dexp.as<int>(), ngrp_static, ngrp, B, s);
+    }
     launch_gemm_split(kind, dt.as<GemmTask>(), ds.as<GemmSeg>(), dti.as<int3>(), (int)tiles.size(), dexp.as<int>(),
                       B, status, s);
   }
@@ -787,6 +819,7 @@ void Engine::plan_heff2(HeffPlan& p, const BTensor& Lenv, const BTensor& Renv, c
     t.seg_count = 1;
     GemmSeg sg{};
     sg.a = Lenv.ptr(t1info[i].lb);
+    sg.a_static = 1;
     sg.a_base = 0;
     sg.lda = lk.cols;
     sg.b = as_off(th.off);
@@ -871,6 +904,7 @@ void Engine::plan_heff2(HeffPlan& p, const BTensor& Lenv, const BTensor& Renv, c
         sg.a_base = 0;
         sg.lda = p.t2.blocks[id].cols;
         sg.b = Renv.ptr(rb);
+        sg.b_static = 1;
         sg.b_base = 0;
         sg.ldb = rk.cols;
         sg.k = rk.rows;
@@ -922,6 +956,7 @@ static void plan_l_w(Engine* eng, const Model& M, Recoupler& rec, HeffPlan& p, c
     t.seg_count = 1;
     GemmSeg sg{};
     sg.a = Lenv.ptr(info[i].first);
+    sg.a_static = 1;
     sg.lda = lk.cols;
     sg.b = as_off(x.off);
     sg.b_base = 1;
@@ -1008,6 +1043,7 @@ void Engine::plan_heff1(HeffPlan& p, const BTensor& Lenv, const BTensor& Renv, c
         sg.a = p.t2.ptr(id);
         sg.lda = p.t2.blocks[id].cols;
         sg.b = Renv.ptr(rb);
+        sg.b_static = 1;
         sg.ldb = rk.cols;
         sg.k = rk.rows;
         sg.alpha = 1.0;
@@ -2077,6 +2113,7 @@ void Engine::plan_heff0(HeffPlan& p, const BTensor& Lenv, const BTensor& Renv, c
     t.seg_count = 1;
     GemmSeg sg{};
     sg.a = Lenv.ptr(t1l[i]);
+    sg.a_static = 1;
     sg.lda = lk.cols;
     sg.b = as_off(cb.off);
     sg.b_base = 1;
@@ -2107,6 +2144,7 @@ void Engine::plan_heff0(HeffPlan& p, const BTensor& Lenv, const BTensor& Renv, c
         sg.a = p.t1.ptr(id);
         sg.lda = tb.cols;
         sg.b = Renv.ptr(rb);
+        sg.b_static = 1;
         sg.ldb = rk.cols;
         sg.k = rk.rows;
         sg.alpha = 1.0;

@@ -85,11 +85,13 @@ struct GemmPlan {
   std::vector<GemmSeg> segs;
   std::vector<int3> tiles;
   DevBuf dt, ds, dti;
-  // BF16x4: distinct operands, their split jobs, digit records, group maxima and exponents
-  std::vector<DigitOp> dops;
-  std::vector<int2> djobs;
-  DevBuf ddops, djb, ddig, dmax, dexp;
-  int ngrp = 0;
+  // BF16x4: distinct operands (static: split at the first launch; dynamic: every
+  // launch), their split jobs, digit records, group maxima and exponents
+  std::vector<DigitOp> dops_s, dops_d;
+  std::vector<int2> djobs_s, djobs_d;
+  DevBuf ddops_s, djb_s, ddops_d, djb_d, ddig, dmax, dexp;
+  int ngrp = 0, ngrp_static = 0;
+  mutable bool static_done = false;
   long long flops = 0;  // algorithmic real flops (8 per complex MAC)
   long long bytes = 0;  // algorithmic bytes: every operand block read once, output written once
   int kind = -1;        // -1 FP64 CUDA cores, 0 3xTF32, 1 BF16x3 tensor cores
@@ -188,6 +190,11 @@ class Engine {
   BTensor& right_env_bp() { return Renv_[2]; }
   void heff_apply_bond(const cplx* in, cplx* out);  // device pointers, bond problem only
   HeffPlan& heff_plan_bond() { return *bp_heff_; }
+  // the caller rewrote an environment: operands split once per plan are stale
+  void environments_changed() {
+    if (bp_heff_) bp_heff_->g1.static_done = bp_heff_->g3.static_done = false;
+    chain_heff_.reset();
+  }
   HeffPlan& chain_heff0();  // two-site H_eff at bond (0,1) of a chain (centre at site 0)
   // x <- exp(-i tau H) x; *k = matvecs used, *launches = kernel launches
   void krylov(HeffPlan& H, cplx* x, double tau, int* k, int* launches);

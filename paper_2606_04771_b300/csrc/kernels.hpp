@@ -48,8 +48,9 @@ void launch_gemm_split(int kind, const GemmTask* tasks, const GemmSeg* segs, con
 int digit_job_size();
 // one bounded wait on an mbarrier that never completes; adds 1 to *status on expiry
 void launch_wait_selftest(unsigned polls, int* status, cudaStream_t s);
+// the groups [g0, g1) are reset and recomputed (the operands' groups lie in that range)
 void launch_digits(const DigitOp* ops, int nops, const int2* jobs, int njobs, unsigned long long* maxv, int* exps,
-                   int ngrp, const Bases4& B, cudaStream_t s);
+                   int g0, int g1, const Bases4& B, cudaStream_t s);
 
 int dots_grid(long long n);
 void launch_dots(const cplx* V, long long pitch, int nv, const cplx* w, long long n, cplx* partial, int G, cplx* out,

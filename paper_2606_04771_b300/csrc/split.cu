@@ -351,9 +351,10 @@ constexpr int XN = 64;                  // complex columns per tile
 constexpr int XSTAGE = 4 * PLANE_BYTES + 4 * (64 * 128);  // 4 A planes (128 rows) + 4 B planes (64 rows)
 constexpr int XSTAGES = 2;              // 192 KB of stages: one persistent CTA per SM
 constexpr int XKC = 32;                 // complex k per chunk (64 bf16 = one 128-byte row)
-constexpr int XPROD = 256;              // producer threads (warps 0-7)
-constexpr int XMMA_WARP = 8;            // MMA issuer warp
-constexpr int XTHREADS = XPROD + 32 + 128;  // + MMA warp + four epilogue warps (9-12)
+constexpr int XPROD = 128;              // producer threads (warps 0-3)
+constexpr int XMMA_WARP = 4;            // MMA issuer warp
+constexpr int XEPI = 256;               // epilogue threads (warps 5-12, two per TMEM lane quarter)
+constexpr int XTHREADS = XPROD + 32 + XEPI;
 constexpr int XACC = 4 * XN;            // TMEM columns of one accumulator set (four orders)
 
 __device__ __forceinline__ int exp_of_max(double m) {
@@ -378,6 +379,31 @@ __device__ __forceinline__ int fixed30(double x, int e) {
   else if (r <= 0) X = (long long)(mant << (-r));  // cannot happen for |x| <= 2^e (r >= 22)
   else X = (long long)((mant + (1ull << (r - 1))) >> r);
   return (b >> 63) ? -(int)X : (int)X;
+}
+
+// Bit pattern of the double V * 2^ee, built with integer operations only (64-bit
+// int-to-float conversions run on the FP64-rate pipe of this part): exact for
+// |V| < 2^53, rounded to nearest (ties away) above; 0 when V = 0 or the result falls
+// below the normal range.
+__device__ __forceinline__ long long scaled_double_bits(long long V, int ee) {
+  if (V == 0) return 0;
+  const unsigned long long sgn = V < 0 ? (1ull << 63) : 0ull;
+  unsigned long long u = V < 0 ? 0ull - (unsigned long long)V : (unsigned long long)V;
+  int msb = 63 - __clzll((long long)u);
+  if (msb > 52) {  // keep 53 significant bits
+    int sh = msb - 52;
+    u = (u + (1ull << (sh - 1))) >> sh;
+    if (u >> 53) {  // the rounding carried into a new bit
+      u >>= 1;
+      ++sh;
+    }
+    ee += sh;
+    msb = 52;
+  }
+  const int ex = msb + 1023 + ee;
+  if (ex <= 0) return (long long)sgn;
+  const unsigned long long mant = (u << (52 - msb)) & ((1ull << 52) - 1);
+  return (long long)(sgn | ((unsigned long long)ex << 52) | mant);
 }
 
 __device__ __forceinline__ void digits4(int X, float* d) {
@@ -411,39 +437,50 @@ __device__ __forceinline__ void tmem_ld16(uint32_t addr, uint32_t* v) {
 
 // ---- operand splitting, once per launch --------------------------------------
 // pass 1: per-row (A) / per-column (B) maxima of |Re|, |Im| into the operand's
-// scale group (bit patterns of non-negative doubles order like the values)
+// scale group (bit patterns of non-negative doubles order like the values).  One
+// CTA per operand walks all elements in storage order (coalesced) and reduces into
+// shared-memory slots with 64-bit atomics, then merges the slots into the group.
+constexpr int DIGIT_SLOTS = 6144;  // 48 KB of slots; longer rows/columns go to global atomics
 __global__ void __launch_bounds__(256) digit_max_kernel(const DigitOp* __restrict__ ops, const Bases4 B,
                                                         unsigned long long* __restrict__ maxv) {
   const DigitOp o = ops[blockIdx.x];
   const cplx* src = rebase(B, o.base, o.src);
   const unsigned long long ABS = 0x7FFFFFFFFFFFFFFFull;
-  auto at = [&](int r, int c) -> cplx {  // logical element (r, c)
-    return o.op == OP_N ? src[(long long)r * o.ld + c] : src[(long long)c * o.ld + r];
-  };
-  if (o.side == 0) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int r = warp; r < o.rows; r += 8) {
-      unsigned long long m = 0;
-      for (int c = lane; c < o.cols; c += 32) {
-        const cplx v = at(r, c);
-        m = max(m, max((unsigned long long)__double_as_longlong(v.x) & ABS,
-                       (unsigned long long)__double_as_longlong(v.y) & ABS));
-      }
-      for (int d = 16; d > 0; d >>= 1) m = max(m, (unsigned long long)__shfl_xor_sync(0xffffffffu, m, d));
-      if (m && o.alpha != 1.0) m = (unsigned long long)__double_as_longlong(fabs(o.alpha) * __longlong_as_double(m));
-      if (lane == 0 && m) atomicMax(&maxv[o.grp + r], m);
-    }
-  } else {
-    for (int c = threadIdx.x; c < o.cols; c += 256) {
-      unsigned long long m = 0;
-      for (int r = 0; r < o.rows; ++r) {
-        const cplx v = at(r, c);
-        m = max(m, max((unsigned long long)__double_as_longlong(v.x) & ABS,
-                       (unsigned long long)__double_as_longlong(v.y) & ABS));
-      }
-      if (m) atomicMax(&maxv[o.grp + c], m);
+  extern __shared__ unsigned long long slot[];
+  const int nslot = o.side == 0 ? o.rows : o.cols;
+  const bool local = nslot <= DIGIT_SLOTS;
+  if (local)
+    for (int i = threadIdx.x; i < nslot; i += 256) slot[i] = 0ull;
+  __syncthreads();
+  const long long n = (long long)o.rows * o.cols;
+  // storage order: OP_N stores rows of length cols, OP_C stores columns of length rows
+  const int inner = o.op == OP_N ? o.cols : o.rows;
+#pragma unroll 4
+  for (long long e = threadIdx.x; e < n; e += 256) {
+    const int outer = (int)(e / inner), in = (int)(e - (long long)outer * inner);
+    const cplx v = src[(long long)outer * o.ld + in];
+    const int r = o.op == OP_N ? outer : in, c = o.op == OP_N ? in : outer;
+    const unsigned long long m = max((unsigned long long)__double_as_longlong(v.x) & ABS,
+                                     (unsigned long long)__double_as_longlong(v.y) & ABS);
+    if (!m) continue;
+    const int sidx = o.side == 0 ? r : c;
+    if (local) {
+      atomicMax(&slot[sidx], m);
+    } else {
+      const unsigned long long ms = (o.side == 0 && o.alpha != 1.0)
+                                        ? (unsigned long long)__double_as_longlong(fabs(o.alpha) * __longlong_as_double(m))
+                                        : m;
+      atomicMax(&maxv[o.grp + sidx], ms);
     }
   }
+  __syncthreads();
+  if (local)
+    for (int i = threadIdx.x; i < nslot; i += 256) {
+      unsigned long long m = slot[i];
+      if (m && o.side == 0 && o.alpha != 1.0)
+        m = (unsigned long long)__double_as_longlong(fabs(o.alpha) * __longlong_as_double(m));
+      if (m) atomicMax(&maxv[o.grp + i], m);
+    }
 }
 
 // pass 2: the exponent of every group row/column
@@ -475,6 +512,7 @@ __global__ void __launch_bounds__(256) digit_convert_kernel(const DigitOp* __res
   const cplx* src = rebase(B, o.base, o.src);
   const long long n = (long long)o.rows * o.cols;
   const long long e1 = min(n, (long long)jb.y + DIGIT_JOB);
+#pragma unroll 4
   for (long long e = jb.y + threadIdx.x; e < e1; e += 256) {
     const int r = (int)(e / o.cols), c = (int)(e - (long long)r * o.cols);
     cplx v = o.op == OP_N ? src[(long long)r * o.ld + c] : src[(long long)c * o.ld + r];
@@ -496,9 +534,9 @@ __device__ __forceinline__ int task_chunks(const GemmTask& t, const GemmSeg* __r
 }
 
 // Persistent, warp-specialised BF16x4 kernel: one CTA per SM walks the tile list
-// (sorted by cost) with stride gridDim.x.  Warps 0-7 split FP64 operand chunks into
-// digit planes in a two-stage ring, warp 8 issues the MMAs into one of two TMEM
-// accumulator sets, warps 9-12 drain the other set (exact combination, scaling,
+// (sorted by cost) with stride gridDim.x.  Warps 0-3 unpack digit records into BF16
+// planes of a two-stage ring, warp 4 issues the MMAs into one of two TMEM
+// accumulator sets, warps 5-12 drain the other set (exact combination, scaling,
 // FP64 stores) while the next tile accumulates.
 __global__ void __launch_bounds__(XTHREADS, 1)
     gemm_exact_kernel(const GemmTask* __restrict__ tasks, const GemmSeg* __restrict__ segs,
@@ -518,7 +556,7 @@ __global__ void __launch_bounds__(XTHREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 4);
+      mbar_init(&tempty[b], XEPI / 32);
     }
     err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -537,6 +575,7 @@ __global__ void __launch_bounds__(XTHREADS, 1)
 
   if (warp < XPROD / 32) {
     // ---------------- producers ----------------
+    const int gtid = tid;
     int it = 0;
     for (int ti = blockIdx.x; ti < ntiles && !*verr; ti += gridDim.x) {
       const int3 tr = tiles[ti];
@@ -550,26 +589,27 @@ __global__ void __launch_bounds__(XTHREADS, 1)
           const int s = it % XSTAGES;
           if (!mbar_wait(&empty_bar[s], ((it / XSTAGES) & 1) ^ 1, verr)) break;
           uint8_t* st = stage_base + (size_t)s * XSTAGE;
-          // all 16 records of this thread first (loads in flight together), then
+          // all 32 records of this thread first (loads in flight together), then
           // A: 64 complex rows x 32 complex k -> 4 digit planes of 128 rows x 64 bf16,
           // B: 32 complex k x 64 complex n -> 4 digit planes of 64 rows x 64 bf16
-          constexpr int NA = TM * XKC / XPROD, NB = XN * XKC / XPROD;
+          constexpr int GT = XPROD;
+          constexpr int NA = TM * XKC / GT, NB = XN * XKC / GT;
           unsigned long long wa[NA], wb[NB];
 #pragma unroll
           for (int j = 0; j < NA; ++j) {
-            const int e = tid + j * XPROD, m = e / XKC, k = e % XKC;
+            const int e = gtid + j * GT, m = e / XKC, k = e % XKC;
             const int gr = m0 + m, gk = k0 + k;
             wa[j] = (gr < t.rows && gk < sg.k) ? __ldg(ad + (long long)gr * sg.k + gk) : 0ull;
           }
 #pragma unroll
           for (int j = 0; j < NB; ++j) {
-            const int e = tid + j * XPROD, n = e % XN, k = e / XN;
+            const int e = gtid + j * GT, n = e % XN, k = e / XN;
             const int gc = n0 + n, gk = k0 + k;
             wb[j] = (gc < t.cols && gk < sg.k) ? __ldg(bd + (long long)gk * t.cols + gc) : 0ull;
           }
 #pragma unroll
           for (int j = 0; j < NA; ++j) {
-            const int e = tid + j * XPROD, m = e / XKC, k = e % XKC;
+            const int e = gtid + j * GT, m = e / XKC, k = e % XKC;
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
               const float re = sbyte(wa[j], p), im = sbyte(wa[j], 4 + p);
@@ -580,7 +620,7 @@ __global__ void __launch_bounds__(XTHREADS, 1)
           }
 #pragma unroll
           for (int j = 0; j < NB; ++j) {
-            const int e = tid + j * XPROD, n = e % XN, k = e / XN;
+            const int e = gtid + j * GT, n = e % XN, k = e / XN;
 #pragma unroll
             for (int p = 0; p < 4; ++p)
               st_bf2(st + 4 * PLANE_BYTES + p * (64 * 128), n, 2 * k, sbyte(wb[j], p), sbyte(wb[j], 4 + p));
@@ -641,9 +681,11 @@ __global__ void __launch_bounds__(XTHREADS, 1)
       }
     }
   } else {
-    // ---------------- epilogue (warps 9-12: TMEM lane quarters 1, 2, 3, 0) ----------------
+    // ---------------- epilogue (warps 5-12: warp w reads TMEM lane quarter w mod 4;
+    // the two warps of a quarter take one half of the 64 columns each) ----------------
     const int quarter = warp & 3;
-    const int etid = tid - (XPROD + 32);  // 0..127
+    const int half = (warp - XMMA_WARP - 1) >> 2;
+    const int etid = tid - (XPROD + 32);  // 0..255
     int j = 0;
     for (int ti = blockIdx.x; ti < ntiles && !*verr; ti += gridDim.x) {
       const int3 tr = tiles[ti];
@@ -651,7 +693,7 @@ __global__ void __launch_bounds__(XTHREADS, 1)
       cplx* const cptr = rebase(B, t.c_base, t.c);
       const int m0 = tr.y * TM, n0 = tr.z * XN;
       if (task_chunks(t, segs) == 0) {  // no contribution: the output tile is zero
-        for (int e = etid; e < TM * XN; e += 128) {
+        for (int e = etid; e < TM * XN; e += XEPI) {
           const int r = m0 + e / XN, c = n0 + e % XN;
           if (r < t.rows && c < t.cols) cptr[(long long)r * t.ldc + c] = {0.0, 0.0};
         }
@@ -665,7 +707,7 @@ __global__ void __launch_bounds__(XTHREADS, 1)
       const int gr = m0 + m;
       const int re_m = gr < t.rows ? exps[t.roff + gr] : 0;
       const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) + buf * XACC;
-      for (int c0 = 0; c0 < XN; c0 += 16) {
+      for (int c0 = half * (XN / 2); c0 < (half + 1) * (XN / 2); c0 += 16) {
         uint32_t a0[16], a1[16], a2[16], a3[16];
         tmem_ld16<16>(lane_addr + 0 * XN + c0, a0);
         tmem_ld16<16>(lane_addr + 1 * XN + c0, a1);
@@ -678,17 +720,13 @@ __global__ void __launch_bounds__(XTHREADS, 1)
           for (int jj = 0; jj < 16; ++jj) {
             const int gc = n0 + c0 + jj;
             if (gc >= t.cols) continue;
-            long long V = (long long)__float2ll_rn(__uint_as_float(a0[jj]));
-            V = (V << 8) + (long long)__float2ll_rn(__uint_as_float(a1[jj]));
-            V = (V << 8) + (long long)__float2ll_rn(__uint_as_float(a2[jj]));
-            V = (V << 8) + (long long)__float2ll_rn(__uint_as_float(a3[jj]));
+            // the accumulators hold exact integers below 2^24: 32-bit conversions
+            long long V = __float2int_rn(__uint_as_float(a0[jj]));
+            V = (V << 8) + __float2int_rn(__uint_as_float(a1[jj]));
+            V = (V << 8) + __float2int_rn(__uint_as_float(a2[jj]));
+            V = (V << 8) + __float2int_rn(__uint_as_float(a3[jj]));
             const int ee = re_m + exps[t.coff + gc] - 36;
-            double r = 0.0;
-            if (V != 0 && ee > -900) {
-              // exact power-of-two scaling by adding to the exponent field of (double)V
-              r = __longlong_as_double(__double_as_longlong((double)V) + ((long long)ee << 52));
-            }
-            out[2 * gc + part] = r;
+            out[2 * gc + part] = __longlong_as_double(scaled_double_bits(V, ee));
           }
         }
       }
@@ -769,13 +807,22 @@ void launch_wait_selftest(unsigned polls, int* status, cudaStream_t s) {
 }
 
 void launch_digits(const DigitOp* ops, int nops, const int2* jobs, int njobs, unsigned long long* maxv, int* exps,
-                   int ngrp, const Bases4& B, cudaStream_t s) {
+                   int g0, int g1, const Bases4& B, cudaStream_t s) {
   if (nops <= 0) return;
-  cudaMemsetAsync(maxv, 0, (size_t)ngrp * sizeof(unsigned long long), s);
+  static bool init = false;
+  const size_t sm = DIGIT_SLOTS * sizeof(unsigned long long);
+  if (!init) {
+    cudaFuncSetAttribute(digit_max_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    init = true;
+  }
+  const int n = g1 - g0;
+  if (n > 0) cudaMemsetAsync(maxv + g0, 0, (size_t)n * sizeof(unsigned long long), s);
   note_launch();
-  digit_max_kernel<<<nops, 256, 0, s>>>(ops, B, maxv);
-  note_launch();
-  digit_exp_kernel<<<(ngrp + 255) / 256 < 1184 ? (ngrp + 255) / 256 : 1184, 256, 0, s>>>(maxv, exps, ngrp);
+  digit_max_kernel<<<nops, 256, sm, s>>>(ops, B, maxv);
+  if (n > 0) {
+    note_launch();
+    digit_exp_kernel<<<(n + 255) / 256 < 1184 ? (n + 255) / 256 : 1184, 256, 0, s>>>(maxv + g0, exps + g0, n);
+  }
   note_launch();
   digit_convert_kernel<<<njobs, 256, 0, s>>>(ops, jobs, B, exps);
 }
