@@ -2162,9 +2162,10 @@ void Engine::plan_heff0(HeffPlan& p, const BTensor& Lenv, const BTensor& Renv, c
   p.g3.finalize(stream_, gemm_kind_, dstatus_ + 1);
 }
 
-// Gauge shift by repeated Cholesky QR in FP64, three passes, the first with a
-// diagonal shift of 1e-14 tr(K)/q so that a numerically rank-deficient sector still
-// factorises (the later passes restore orthonormality).  right: per right-bond
+// Gauge shift by repeated Cholesky QR in FP64: two passes; if the first factorisation
+// meets a non-positive pivot (numerically rank-deficient sector) three passes, the
+// first with a diagonal shift of 1e-14 tr(K)/q (the later passes restore
+// orthonormality).  right: per right-bond
 // sector c the matrix M_c (rows (a,s), q = d_c columns) becomes A_c with M_c = A_c C_c,
 // C_c = R3 R2 R1.  left: per left-bond sector a, M_a (p = d_a rows, columns (s,b)) =
 // R^H Q via the Gram matrix M_a M_a^H; C_a = (R3 R2 R1)^H so that M_a = C_a Q_a.
@@ -2193,7 +2194,12 @@ void Engine::gauge_shift(BTensor& M, const BondSpace& b, BTensor& C, bool right)
   std::vector<CholTask> ct;
   for (auto& e : by) ct.push_back({Kb + off[e.first], Ri + off[e.first], b.s[e.first].d});
   DevBuf dct = upload(ct, stream_);
-  for (int pass = 0; pass < 3; ++pass) {
+  // CholQR2 (two unshifted passes, orthonormal to rounding whenever the first
+  // factorisation succeeds); a non-positive pivot in the first pass restarts with
+  // the shifted three-pass form
+  int npass = 2;
+  double shift0 = 0.0;
+  for (int pass = 0; pass < npass; ++pass) {
     GemmPlan gk, ga, gr;
     for (auto& e : by) {
       const int c = e.first, q = b.s[c].d;
@@ -2225,7 +2231,19 @@ void Engine::gauge_shift(BTensor& M, const BondSpace& b, BTensor& C, bool right)
     }
     gk.finalize(stream_);
     gk.launch(stream_, Bases4{{0, 0, 0, 0}});
-    launch_chol_inv(dct.as<CholTask>(), (int)ct.size(), pass == 0 ? 1e-14 : 0.0, dstatus_ + 2, stream_);
+    launch_chol_inv(dct.as<CholTask>(), (int)ct.size(), pass == 0 ? shift0 : 0.0, dstatus_ + 2, stream_);
+    if (pass == 0 && shift0 == 0.0) {
+      int bad = 0;
+      TDVP_CUDA(cudaMemcpyAsync(&bad, dstatus_ + 2, sizeof(int), cudaMemcpyDeviceToHost, stream_));
+      TDVP_CUDA(cudaStreamSynchronize(stream_));
+      if (bad) {
+        TDVP_CUDA(cudaMemsetAsync(dstatus_ + 2, 0, sizeof(int), stream_));
+        shift0 = 1e-14;
+        npass = 3;
+        pass = -1;  // M (= cur) is untouched until the first swap
+        continue;
+      }
+    }
     // A = M R^-1 (right) or Q = R^-H M (left), block by block
     for (auto& e : by) {
       const int c = e.first, q = b.s[c].d;
