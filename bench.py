@@ -303,8 +303,13 @@ def run_engine(args):
         peak, bound, issued = peaks["bf16_tflops"], "tensor", 10
         pnote = f"{peak_kind} bf16 burst (BF16X4 issues 10 digit products per complex-embedded MAC)"
     achieved = heff["tflops"]
+    # DRAM bytes of one matvec (stage 1 + stage 3 launches) from the ncu capture of the
+    # current BF16x4 kernel on this bond (dram__bytes_read.sum + dram__bytes_write.sum)
+    traffic = 52.2e6 if args.precision == "bf16x4" else None
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "grouped block GEMM of H_eff.psi (stages 1+3), chi=4096 bond",
+                "traffic": traffic, "traffic_unit": "bytes per matvec",
+                "alg_bytes_per_matvec": heff["stage_alg_bytes"][0] + heff["stage_alg_bytes"][2],
+                "kernel": "grouped block GEMM of H_eff.psi (stages 1+3), chi=4096 bond",
                 "peak_source": pnote, "stage_ms": heff["stage_ms"],
                 "tensor_pipe_frac_upper": achieved * issued / peak}
     line = {
