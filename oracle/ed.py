@@ -98,6 +98,28 @@ def neel_state(L: int, basis: list[int]) -> np.ndarray:
     return psi
 
 
+def product_state(L: int, occ, basis: list[int]) -> np.ndarray:
+    """A Fock product state: occ[i] in {0: empty, 1: up, 2: down, 3: up and down}.
+    The creators are applied right to left in increasing mode order (a global sign
+    only)."""
+    ops = [mode(i, sg) for i in range(L) for sg in (0, 1) if (occ[i] >> sg) & 1]
+    sign, s = 1, 0
+    for p in reversed(ops):
+        sg, s = apply_cdag(p, s)
+        sign *= sg
+    psi = np.zeros(len(basis), dtype=complex)
+    psi[basis.index(s)] = sign
+    return psi
+
+
+def vacancy_occupations(L: int) -> list[int]:
+    """The second initial state of the benchmark (Sec. S1): the Neel pattern (up on even
+    sites, down on odd sites) with the centre site L // 2 empty (L odd)."""
+    occ = [1 if i % 2 == 0 else 2 for i in range(L)]
+    occ[L // 2] = 0
+    return occ
+
+
 def evolve(H: np.ndarray, psi0: np.ndarray, times) -> list[np.ndarray]:
     """psi(t) = V exp(-i E t) V^dag psi0 from the full spectrum of H."""
     E, V = np.linalg.eigh(H)

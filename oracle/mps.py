@@ -95,6 +95,17 @@ def neel_mps(L: int) -> list[np.ndarray]:
     return out
 
 
+def product_mps(occ) -> list[np.ndarray]:
+    """A Fock product state as a bond-dimension-1 MPS; occ[i] in {0, 1 (up), 2 (down),
+    3 (both)} is the local basis index s = n_up + 2 n_dn."""
+    out = []
+    for o in occ:
+        A = np.zeros((1, D, 1), dtype=complex)
+        A[0, o, 0] = 1.0
+        out.append(A)
+    return out
+
+
 def full_state(mps: list[np.ndarray]) -> np.ndarray:
     """Contract the MPS to the full vector indexed by the Fock integer sum_i s_i 4^i."""
     psi = mps[0][0]  # [s0, b]
@@ -278,11 +289,12 @@ def split_svd(theta, chi_max, eps, absorb):
 class DenseTDVP:
     """Two-site TDVP on a dense MPS; the orthogonality centre rests on site 0."""
 
-    def __init__(self, L, J, U, kmax=20, krylov_tol=1e-12):
+    def __init__(self, L, J, U, kmax=20, krylov_tol=1e-12, occ=None):
         self.L, self.J, self.U = L, J, U
         self.W = mpo_tensor(J, U)
         self.kmax, self.tol = kmax, krylov_tol
-        self.mps = neel_mps(L)  # product state: every tensor is both left- and right-canonical
+        # product state (Neel by default): every tensor is both left- and right-canonical
+        self.mps = neel_mps(L) if occ is None else product_mps(occ)
         self.max_discarded = 0.0
         self.krylov_dims = []
         self._build_right_envs()

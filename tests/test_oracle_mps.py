@@ -233,3 +233,37 @@ def test_heff0_is_the_projected_hamiltonian():
     want = np.vdot(embed(C1), H @ embed(C2))
     got = np.vdot(C1, mps.heff0(Le, Re, C2))
     assert abs(got - want) < 1e-10 * abs(want)
+
+
+# ---------------------------------------------------------------------------
+# the second initial state (Sec. S1): the Neel pattern with a central vacancy
+# ---------------------------------------------------------------------------
+
+def test_vacancy_state_and_full_rank_evolution():
+    """The vacancy product state is the same in the ED and MPS oracles; once the
+    bond dimensions are full, both integrators reproduce exact evolution, and the
+    charge N = L - 1 and the S^z of the state are conserved."""
+    L, J, U = 5, 1.0, 4.0
+    occ = ed.vacancy_occupations(L)
+    assert occ == [1, 2, 0, 2, 1]
+    nu, nd = sum(o & 1 for o in occ), sum(o >> 1 & 1 for o in occ)
+    basis = ed.sector_basis(L, nu, nd)
+    H = ed.hamiltonian(L, J, U, basis)
+    sim = mps.DenseTDVP(L, J, U, kmax=30, krylov_tol=1e-14, occ=occ)
+    r0 = ed.observables(ed.product_state(L, occ, basis), basis, L, H)
+    o0 = sim.observables()
+    for key in ("n_up", "n_dn", "docc"):
+        assert np.abs(o0[key] - r0[key]).max() < 1e-14
+    for _ in range(12):
+        sim.step(0.05, 10**6, 0.0)
+    assert sim.bond_dims() == [4, 16, 16, 4]
+    for method in ("two", "one"):
+        c = _copy_sim(sim, L, J, U)
+        psi0 = mps.full_state(c.mps)
+        ref = ed.evolve(ed.fock_hamiltonian(L, J, U), psi0, [0.3])[0]
+        for _ in range(3):
+            c.step(0.1, 10**6, 0.0) if method == "two" else c.step1(0.1)
+        assert np.abs(mps.full_state(c.mps) - ref).max() < 1e-10, method
+        o = c.observables()
+        assert abs(o["n"].sum() - (L - 1)) < 1e-10
+        assert abs(0.5 * (o["n_up"] - o["n_dn"]).sum() - 0.5 * (nu - nd)) < 1e-10
