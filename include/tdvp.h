@@ -77,6 +77,18 @@ void tdvp_opts_default(tdvp_opts* o);
  * Errors: TDVP_EINVAL, TDVP_ENOMEM, TDVP_ECUDA. */
 int tdvp_create(int L, double J, double U, int symmetry, const tdvp_opts* opts, tdvp_ctx** out);
 
+/* A chain in a Fock product state instead of the Neel state: occ[i] (i = 0..L-1)
+ * is 0 (empty), 1 (up), 2 (down) or 3 (up and down) in the frame of Eq. (FHM).
+ * Used for the benchmark's second initial state (Sec. S1: the Neel pattern with a
+ * single central vacancy, L odd).  Any L >= 2 and any occupations with
+ * TDVP_SYM_U1U1.  TDVP_SYM_U1SU2 accepts only states whose sites are all singly
+ * occupied (the engine's particle-hole frame then holds a spin singlet, the sector
+ * its U(1)xSU(2) measurement assumes); others give TDVP_EINVAL.  The energy that
+ * tdvp_measure reports is that of Eq. (FHM) for any filling.  Errors: TDVP_EINVAL,
+ * TDVP_ENOMEM, TDVP_ECUDA. */
+int tdvp_create_product(int L, double J, double U, int symmetry, const int* occ, const tdvp_opts* opts,
+                        tdvp_ctx** out);
+
 /* Create a chain in a synthetic random state for benchmarking: a right-canonical
  * MPS of L sites (half filling, total spin singlet in the engine frame) whose
  * bond k holds the multiplets (n, t) of k sites that can couple to the total

@@ -49,6 +49,7 @@ def lib():
             "tdvp_step_mode": (C.c_int, [vp, C.c_double, C.c_longlong, C.c_double, C.c_int, P(C.c_int)]),
             "tdvp_create_random": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_int, C.c_longlong, C.c_ulonglong,
                                              C.c_int, P(Opts), P(vp)]),
+            "tdvp_create_product": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_int, vp, P(Opts), P(vp)]),
             "tdvp_bond_update": (C.c_int, [vp, C.c_int, C.c_int, C.c_double, C.c_longlong, C.c_double, vp]),
             "tdvp_measure_center": (C.c_int, [vp, vp, vp, vp, vp]),
             "tdvp_measure": (C.c_int, [vp, vp, vp, vp, vp, vp]),
@@ -191,16 +192,31 @@ class _Ctx:
         return f.value
 
 
+def vacancy_occupations(L):
+    """The benchmark's second initial state: the Neel pattern (up on even sites, down on
+    odd sites) with the centre site L // 2 empty."""
+    occ = [1 if i % 2 == 0 else 2 for i in range(L)]
+    occ[L // 2] = 0
+    return occ
+
+
 class Chain(_Ctx):
     """An L-site chain in the Neel state (or, with random_chi, a synthetic random
     right-canonical state of that bond dimension), evolved with tdvp_step."""
 
-    def __init__(self, L, J=1.0, U=4.0, symmetry="su2", random_chi=None, seed=1, center=0, **opts):
+    def __init__(self, L, J=1.0, U=4.0, symmetry="su2", random_chi=None, seed=1, center=0, occupations=None,
+                 **opts):
+        """occupations: per site 0 (empty), 1 (up), 2 (down), 3 (both) -- a product initial
+        state instead of the Neel state (e.g. the central-vacancy state)."""
         super().__init__()
         self.L = L
         self.sym = symmetry
         o = make_opts(**opts)
-        if random_chi is None:
+        if occupations is not None:
+            occ = np.ascontiguousarray(np.array(occupations, dtype=np.int32))
+            assert occ.shape == (L,)
+            check(lib().tdvp_create_product(L, J, U, SYM[symmetry], occ.ctypes.data, C.byref(o), C.byref(self.h)))
+        elif random_chi is None:
             check(lib().tdvp_create(L, J, U, SYM[symmetry], C.byref(o), C.byref(self.h)))
         else:
             check(lib().tdvp_create_random(L, J, U, SYM[symmetry], int(random_chi), int(seed), int(center),

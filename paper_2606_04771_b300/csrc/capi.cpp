@@ -5,6 +5,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/tdvp.h"
 #include "engine.hpp"
@@ -92,6 +93,21 @@ int tdvp_create(int L, double J, double U, int symmetry, const tdvp_opts* opts, 
     tdvp_opts d;
     tdvp_opts_default(&d);
     auto* e = new tdvp::Engine(L, J, U, symmetry == TDVP_SYM_U1SU2, to_opts(opts ? opts : &d));
+    *out = new tdvp_ctx{e};
+  });
+}
+
+int tdvp_create_product(int L, double J, double U, int symmetry, const int* occ, const tdvp_opts* opts,
+                        tdvp_ctx** out) {
+  if (!out || !occ) return fail(TDVP_EINVAL, "NULL argument");
+  *out = nullptr;
+  if (symmetry != TDVP_SYM_U1U1 && symmetry != TDVP_SYM_U1SU2) return fail(TDVP_EINVAL, "unknown symmetry");
+  if (L < 2) return fail(TDVP_EINVAL, "L must be >= 2");
+  return guarded([&] {
+    tdvp_opts d;
+    tdvp_opts_default(&d);
+    std::vector<int> o(occ, occ + L);
+    auto* e = tdvp::Engine::product_state(L, J, U, symmetry == TDVP_SYM_U1SU2, o, to_opts(opts ? opts : &d));
     *out = new tdvp_ctx{e};
   });
 }

@@ -341,6 +341,15 @@ Engine* Engine::bond_problem(bool su2, double J, double U, const std::vector<Sec
 // the middle bond reaches chi_target; then every sector is made reachable and every
 // right-canonical row space feasible, blocks are filled with counter-based normal
 // numbers and sites 1..L-1 are right-orthonormalised per left sector.
+Engine* Engine::product_state(int L, double J, double U, bool su2, const std::vector<int>& occ, const Opts& o) {
+  if (L < 2) throw Error(-1, "L must be >= 2");
+  std::unique_ptr<Engine> e(new Engine());
+  e->L_ = L;
+  e->init_common(su2, J, U, o);
+  e->init_product(occ);
+  return e.release();
+}
+
 Engine* Engine::random_state(int L, double J, double U, bool su2, long long chi_target, unsigned long long seed,
                              int center, const Opts& o) {
   if (L < 2 || (L % 2)) throw Error(-1, "L must be even and >= 2");
@@ -747,20 +756,50 @@ void Engine::build_renv_layout(BTensor& t, const BondSpace& ket, const BondSpace
 }
 
 void Engine::init_neel() {
-  // particle-hole frame: the Neel state of Eq. (neel) becomes |2,0,2,0,...>
+  // Eq. (neel): up on even sites, down on odd sites
+  std::vector<int> occ(L_);
+  for (int i = 0; i < L_; ++i) occ[i] = (i % 2 == 0) ? 1 : 2;
+  init_product(occ);
+}
+
+// A Fock product state, occ[i] in {0 empty, 1 up, 2 down, 3 both} (original frame).
+// In the particle-hole frame c_dn -> (-1)^i c_dn^dag an up site is doubly occupied,
+// a down site empty, an empty site holds a down spin and a doubly occupied site an
+// up spin; U(1)xSU(2) takes only states whose frame sites are all singlets (the
+// measurement there assumes a total spin 0).  Bond dimension 1 everywhere.
+void Engine::init_product(const std::vector<int>& occ) {
+  if ((int)occ.size() != L_) throw Error(-1, "one occupation per site");
+  const bool su2 = model_.su2;
   bonds_.assign(L_ + 1, BondSpace());
-  int n = 0;
+  int n = 0, t = 0;
+  std::vector<int> sidx(L_);
   for (int k = 0; k <= L_; ++k) {
-    bonds_[k].s = {{n, 0, 1}};
+    bonds_[k].s = {{n, t, 1}};
     bonds_[k].build_index();
-    if (k < L_) n += (k % 2 == 0) ? 2 : 0;
+    if (k == L_) break;
+    int o = occ[k];
+    if (o < 0 || o > 3) throw Error(-1, "occupation codes are 0 (empty), 1 (up), 2 (down), 3 (both)");
+    int nn, tt, si;
+    switch (o) {
+      case 1: nn = 2; tt = 0; si = su2 ? 2 : 3; break;  // up -> doubly occupied
+      case 2: nn = 0; tt = 0; si = 0; break;              // down -> empty
+      case 0: nn = 1; tt = -1; si = 2; break;             // empty -> down spin
+      default: nn = 1; tt = 1; si = 1; break;             // both -> up spin
+    }
+    if (su2 && nn == 1)
+      throw Error(-1, "U(1)xSU(2) needs a spin singlet in the particle-hole frame: every site singly "
+                      "occupied (an empty or doubly occupied site breaks it); use U(1)xU(1)");
+    sidx[k] = si;
+    n += nn;
+    t += tt;
   }
   site_.clear();
   site_.resize(L_);
   std::vector<cplx> one(1, cplx{1.0, 0.0});
   for (int i = 0; i < L_; ++i) {
     build_site_layout(site_[i], bonds_[i], bonds_[i + 1]);
-    if (site_[i].blocks.size() != 1) throw Error(-5, "Neel layout must have one block per site");
+    if (site_[i].blocks.size() != 1 || site_[i].blocks[0].key[1] != sidx[i])
+      throw Error(-5, "product-state layout must have the one block of the site's state");
     alloc(site_[i], false);
     TDVP_CUDA(cudaMemcpyAsync(site_[i].data(), one.data(), sizeof(cplx), cudaMemcpyHostToDevice, stream_));
   }
@@ -2680,7 +2719,10 @@ void Engine::measure(double* n_out, double* sz_out, double* docc_out, double* s_
     cplx he;
     TDVP_CUDA(cudaMemcpyAsync(&he, e.p, sizeof(cplx), cudaMemcpyDeviceToHost, stream_));
     TDVP_CUDA(cudaStreamSynchronize(stream_));
-    *energy = he.x;
+    // the MPO's on-site term -U n'_up n'_dn + (U/2) n' differs from U n_up n_dn of Eq.
+    // (FHM) by U S'^z per site, i.e. by U (N - L)/2 in total = U t_L / 2 with t_L the
+    // 2S'^z of the last bond (zero at half filling and for every U(1)xSU(2) state)
+    *energy = he.x + (model_.su2 ? 0.0 : 0.5 * model_.U * bonds_[L_].s[0].t);
   }
   TDVP_CUDA(cudaStreamSynchronize(stream_));
   check_status();

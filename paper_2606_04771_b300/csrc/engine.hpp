@@ -182,6 +182,8 @@ class Engine {
   // synthetic right-canonical random state of L sites with bond dimension about chi_target
   static Engine* random_state(int L, double J, double U, bool su2, long long chi_target, unsigned long long seed,
                               int center, const Opts& o);
+  // a Fock product state, occ[i] in {0 empty, 1 up, 2 down, 3 both}
+  static Engine* product_state(int L, double J, double U, bool su2, const std::vector<int>& occ, const Opts& o);
   static Engine* bond_problem(bool su2, double J, double U, const std::vector<Sector>& left,
                               const std::vector<Sector>& right, const Opts& o);
   bool bond_only() const { return bond_only_; }
@@ -203,6 +205,7 @@ class Engine {
   Engine() = default;
   void init_common(bool su2, double J, double U, const Opts& o);
   void init_neel();
+  void init_product(const std::vector<int>& occ);
   void build_site_layout(BTensor& t, const BondSpace& l, const BondSpace& r) const;
   void build_theta_layout(BTensor& t, const BondSpace& l, const BondSpace& r) const;
   void build_lenv_layout(BTensor& t, const BondSpace& bra, const BondSpace& ket) const;

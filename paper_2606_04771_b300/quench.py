@@ -3,6 +3,7 @@ with TDVP (Sec. S2.2) to a final time, one JSON line per time step.
 
     python -m paper_2606_04771_b300.quench --L 60 --U 4 --dt 0.05 --t 3 --chi 4096 \
         --eps 1e-9 --mode adaptive --precision bf16x4 --out run.npz
+    python -m paper_2606_04771_b300.quench --L 31 --vacancy --symmetry u1u1 ...
 
 Every step prints t, the integrator used, the largest bond dimension (U(1)-equivalent
 and reduced), the largest discarded weight and Krylov dimension so far, and the
@@ -20,12 +21,13 @@ import time
 
 import numpy as np
 
-from ._lib import Chain
+from ._lib import Chain, vacancy_occupations
 
 
 def run(L=60, J=1.0, U=4.0, dt=0.05, t_final=3.0, chi=4096, eps=1e-9, mode="adaptive", precision="bf16x4",
-        symmetry="su2", measure_every=10, entropy=True, out=None, stream=None, log=sys.stdout):
-    ch = Chain(L, J, U, symmetry=symmetry, precision=precision, stream=stream)
+        symmetry="su2", measure_every=10, entropy=True, out=None, stream=None, log=sys.stdout, vacancy=False):
+    ch = Chain(L, J, U, symmetry=symmetry, precision=precision, stream=stream,
+               occupations=vacancy_occupations(L) if vacancy else None)
     nsteps = int(round(t_final / dt))
     rec = {"t": [], "n_up": [], "n_dn": [], "docc": [], "s_ent": [], "energy": []}
     t0 = time.perf_counter()
@@ -79,8 +81,10 @@ def main(argv=None):
     ap.add_argument("--measure-every", type=int, default=10)
     ap.add_argument("--entropy", action="store_true")
     ap.add_argument("--out", default=None)
+    ap.add_argument("--vacancy", action="store_true", help="Neel state with the centre site empty (use u1u1)")
     a = ap.parse_args(argv)
-    run(a.L, a.J, a.U, a.dt, a.t, a.chi, a.eps, a.mode, a.precision, a.symmetry, a.measure_every, a.entropy, a.out)
+    run(a.L, a.J, a.U, a.dt, a.t, a.chi, a.eps, a.mode, a.precision, a.symmetry, a.measure_every, a.entropy, a.out,
+        vacancy=a.vacancy)
 
 
 if __name__ == "__main__":
