@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 
 #include <cstdio>
 #include <vector>
@@ -806,6 +807,41 @@ static int rows_per_lane(int pmax) {
   return 0;
 }
 
+// Cooperative grids launched from different streams never overlap on the device.
+// A grid-wide barrier needs every CTA of its grid resident at once; two such grids
+// sharing the SMs (two chains evolved on two streams) could each hold SMs that the
+// other's missing CTAs wait for.  Every cooperative launch therefore first waits
+// for the previous cooperative launch of any other stream on the same device (one
+// event per device, re-recorded under a lock).  Kernels that are not cooperative
+// keep overlapping freely: they never wait on other CTAs, so a cooperative grid
+// that has to wait for SMs they hold gets them when they finish.
+struct CoopOrder {
+  std::mutex m;
+  cudaEvent_t ev = nullptr;
+  cudaStream_t last = nullptr;
+  bool any = false;
+};
+static CoopOrder g_coop_order[64];
+
+template <class Launch>
+static int coop_ordered(cudaStream_t s, Launch launch) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (dev < 0 || dev >= 64 || cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+    return launch();  // a captured graph replays in the order it was captured
+  CoopOrder& o = g_coop_order[dev];
+  std::lock_guard<std::mutex> lk(o.m);
+  if (!o.ev && cudaEventCreateWithFlags(&o.ev, cudaEventDisableTiming) != cudaSuccess) return -1;
+  if (o.any && o.last != s && cudaStreamWaitEvent(s, o.ev, 0) != cudaSuccess) return -1;
+  const int rc = launch();
+  if (rc != 0) return rc;
+  if (cudaEventRecord(o.ev, s) != cudaSuccess) return -1;
+  o.last = s;
+  o.any = true;
+  return 0;
+}
+
 template <class Task, class S, class C2, int R>
 static int coop_launch(const Task* d_tasks, int nt, const int2* d_work, const int* d_active, int nrounds,
                        int max_sweeps, S tol, S tol_flag, S abs_flag, int* flags, int* out, cudaStream_t s) {
@@ -818,8 +854,10 @@ static int coop_launch(const Task* d_tasks, int nt, const int2* d_work, const in
   const int grid = nsm * (per < 4 ? per : 4);
   void* args[] = {(void*)&d_tasks, (void*)&nt,  (void*)&d_work,   (void*)&d_active, (void*)&nrounds, (void*)&max_sweeps,
                   (void*)&tol,     (void*)&tol_flag, (void*)&abs_flag, (void*)&flags,    (void*)&out};
-  note_launch();
-  return cudaLaunchCooperativeKernel((void*)kern, dim3(grid), dim3(JT), args, 0, s) == cudaSuccess ? 0 : -1;
+  return coop_ordered(s, [&] {
+    note_launch();
+    return cudaLaunchCooperativeKernel((void*)kern, dim3(grid), dim3(JT), args, 0, s) == cudaSuccess ? 0 : -1;
+  });
 }
 
 template <class Task, class S, class C2>

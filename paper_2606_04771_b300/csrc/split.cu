@@ -776,24 +776,23 @@ void launch_gemm_split(int kind, const GemmTask* tasks, const GemmSeg* segs, con
                        const int* exps, const Bases4& B, int* status, cudaStream_t s) {
   if (ntiles <= 0) return;
   if (kind == 0) {
-    static bool init = false;
-    size_t sm = smem_bytes<0>();
-    if (!init) {
+    const size_t sm = smem_bytes<0>();
+    static const bool init = [sm] {  // once per process, thread-safe (function-local static)
       cudaFuncSetAttribute(gemm_split_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      init = true;
-    }
+      return true;
+    }();
+    (void)init;
     note_launch();
     gemm_split_kernel<0><<<ntiles, NTHREADS, sm, s>>>(tasks, segs, tiles, B, status);
   } else {
-    static int nsm = 0;
-    size_t sm = (size_t)XSTAGES * XSTAGE + 1024;
-    if (!nsm) {
+    const size_t sm = (size_t)XSTAGES * XSTAGE + 1024;
+    static const int nsm = [sm] {  // once per process, thread-safe (function-local static)
       cudaFuncSetAttribute(gemm_exact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      int dev = 0;
+      int dev = 0, n = 0;
       cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-      if (nsm < 1) nsm = 1;
-    }
+      cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+      return n < 1 ? 1 : n;
+    }();
     note_launch();
     gemm_exact_kernel<<<ntiles < nsm ? ntiles : nsm, XTHREADS, sm, s>>>(tasks, segs, tiles, ntiles, B, exps, status);
   }
@@ -809,12 +808,12 @@ void launch_wait_selftest(unsigned polls, int* status, cudaStream_t s) {
 void launch_digits(const DigitOp* ops, int nops, const int2* jobs, int njobs, unsigned long long* maxv, int* exps,
                    int g0, int g1, const Bases4& B, cudaStream_t s) {
   if (nops <= 0) return;
-  static bool init = false;
   const size_t sm = DIGIT_SLOTS * sizeof(unsigned long long);
-  if (!init) {
+  static const bool init = [sm] {  // once per process, thread-safe (function-local static)
     cudaFuncSetAttribute(digit_max_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    init = true;
-  }
+    return true;
+  }();
+  (void)init;
   const int n = g1 - g0;
   if (n > 0) cudaMemsetAsync(maxv + g0, 0, (size_t)n * sizeof(unsigned long long), s);
   note_launch();
