@@ -55,7 +55,8 @@ enum {
   TDVP_ENUMERIC = -4, /* an iteration did not converge or produced NaN */
   TDVP_EINTERNAL = -5,/* inconsistent internal bookkeeping */
   TDVP_ECUDA = -6,    /* a CUDA runtime call failed (including "no device") */
-  TDVP_ETIMEOUT = -7  /* a bounded device wait gave up */
+  TDVP_ETIMEOUT = -7, /* a bounded device wait gave up (or tdvp_server_wait ran out) */
+  TDVP_ECANCELED = -8 /* a served request was cancelled */
 };
 
 typedef struct {
@@ -174,7 +175,10 @@ int tdvp_bond_dims(tdvp_ctx* ctx, long long* chi, long long* chi_red);
  * nothing left to rotate), out[16] FP32 preconditioner sweeps (split-precision
  * modes), out[17] one-site steps.  In one-site steps the phase timers hold:
  * out[9] forward one-site Krylov, out[10] gauge shift, out[11] environment update,
- * out[12] zero-site Krylov and absorption.  n = length of out (at most 18). */
+ * out[12] zero-site Krylov and absorption.  out[18] device bytes the context
+ * holds now and out[19] the most it has held (the buffers of the context's own
+ * tensors, plans and workspaces; the few-KB scratch of single launches is not
+ * counted).  n = length of out (at most 20). */
 int tdvp_stats(tdvp_ctx* ctx, double* out, int n);
 
 /* ---- single-bond problems (the effective-Hamiltonian benchmark) ------------
@@ -289,6 +293,98 @@ int tdvp_launch_count(long long* out);
  * CUDA context stays usable; TDVP_ECUDA on a CUDA error.  stream: cudaStream_t or
  * NULL. */
 int tdvp_selftest_wait(unsigned int polls, void* stream);
+
+/* ---- serving: independent quench requests on one GPU ---------------------
+ * A server runs up to max_active requests at once, each on its own worker
+ * thread and CUDA stream with its own context (MPS, environments, plans and
+ * workspaces resident on the device for the whole run), so the kernels of
+ * different requests overlap on the device.  Admission is first in, first out:
+ * the oldest queued request starts when a worker is free, its footprint estimate
+ * (tdvp_server_footprint) fits beside those of the running requests within
+ * hbm_budget_bytes, and the device reports at least that much free memory; a
+ * request whose estimate alone exceeds the budget runs when nothing else does.
+ * A finished request frees its worker and its share of the budget at once and
+ * the next one is admitted while the others keep running.  A request is
+ * round(t_final / dt) steps of tdvp_step_mode(dt, chi_max, eps, mode) from the
+ * Neel state (Eq. neel) or from the product state `occupations` (as in
+ * tdvp_create_product), then one tdvp_measure.  Requests share no state and
+ * every kernel is deterministic: a result is the same alone and beside others.
+ * Calls on one server may come from any threads; tdvp_server_destroy must not
+ * overlap other calls on the same server. */
+typedef struct tdvp_server tdvp_server;
+
+typedef struct {
+  int L;                  /* sites, >= 2 */
+  double J, U;            /* hopping and interaction of Eq. (FHM) */
+  int symmetry;           /* TDVP_SYM_* */
+  int precision;          /* TDVP_PREC_* of this request's contractions */
+  int mode;               /* TDVP_SWEEP_* */
+  double dt, t_final;     /* dt > 0, t_final >= 0 */
+  long long chi_max;      /* U(1)-equivalent bond dimension cap, >= 1 */
+  double eps;             /* truncation threshold, >= 0 (Sec. S2.4) */
+  const int* occupations; /* [L] in {0,1,2,3} (empty, up, down, both), or NULL for
+                             the Neel state; copied at submission */
+} tdvp_request;
+
+enum { TDVP_REQ_QUEUED = 0, TDVP_REQ_RUNNING = 1, TDVP_REQ_DONE = 2, TDVP_REQ_FAILED = 3, TDVP_REQ_CANCELLED = 4 };
+
+/* Start a server: hbm_budget_bytes > 0, 1 <= max_active <= 256.  opts gives the
+ * Krylov settings and the device (its precision and stream are ignored: each
+ * request names its precision and each worker owns a stream); NULL = defaults.
+ * No device work happens until the first request is admitted.  Errors:
+ * TDVP_EINVAL, TDVP_ENOMEM, TDVP_EINTERNAL. */
+int tdvp_server_create(double hbm_budget_bytes, int max_active, const tdvp_opts* opts, tdvp_server** out);
+
+/* The admission estimate of a request, in bytes, for Krylov dimension krylov_max
+ * (<= 0: 20): 16 chi_max^2 (2 L + 2.5 (krylov_max + 8)) + 64e6, a bound with a
+ * factor of two to spare on the device bytes measured for Neel quenches whose
+ * largest bond reached chi_max.  Errors: TDVP_EINVAL. */
+int tdvp_server_footprint(const tdvp_request* req, int krylov_max, double* bytes);
+
+/* Queue a request (copied, occupations included); *id receives its id (> 0).
+ * Errors: TDVP_EINVAL (see tdvp_request), TDVP_ESTATE (shutting down). */
+int tdvp_server_submit(tdvp_server* s, const tdvp_request* req, long long* id);
+
+/* Current state of a request (TDVP_REQ_*).  Errors: TDVP_EINVAL (unknown id). */
+int tdvp_server_poll(tdvp_server* s, long long id, int* state);
+
+/* Block until the request has ended (DONE, FAILED or CANCELLED) or timeout_ms
+ * has passed (< 0: no limit).  Returns TDVP_OK when it ended (its state in
+ * *state, which may be NULL), TDVP_ETIMEOUT otherwise, TDVP_EINVAL for an
+ * unknown id. */
+int tdvp_server_wait(tdvp_server* s, long long id, int timeout_ms, int* state);
+
+/* Results of an ended request: n, sz, docc [L] and s_ent [L-1] as tdvp_measure
+ * (each may be NULL), and info[0..ninfo) with info[0] energy, [1] largest bond
+ * dimension reached, [2] steps done, [3] effective-Hamiltonian flops, [4] submit,
+ * [5] admission and [6] end time (seconds since the server started), [7] peak
+ * device bytes of its context, [8] its footprint estimate, [9] its status code.
+ * info is filled in every state.  Returns TDVP_OK for a DONE request, the
+ * request's own error code for a FAILED or CANCELLED one (message in
+ * tdvp_last_error), TDVP_ESTATE while it is queued or running, TDVP_EINVAL for
+ * an unknown id. */
+int tdvp_server_result(tdvp_server* s, long long id, double* n, double* sz, double* docc, double* s_ent,
+                       double* info, int ninfo);
+
+/* Cancel a request: a queued one ends at once, a running one at its next step
+ * boundary (state CANCELLED, code TDVP_ECANCELED); an ended one is left as is.
+ * Errors: TDVP_EINVAL (unknown id). */
+int tdvp_server_cancel(tdvp_server* s, long long id);
+
+/* Stop (paused != 0) or resume admission; running requests continue. */
+int tdvp_server_pause(tdvp_server* s, int paused);
+
+/* Counters: out[0] submitted, [1] done, [2] failed, [3] cancelled, [4] queued,
+ * [5] running, [6] p50 and [7] p99 latency in seconds (submission to end, over
+ * the DONE requests, linear between closest ranks), [8] seconds since the server
+ * started, [9] most requests running at once, [10] most bytes of estimates
+ * admitted at once, [11] steps and [12] effective-Hamiltonian flops of the DONE
+ * requests.  n = length of out (at most 13). */
+int tdvp_server_stats(tdvp_server* s, double* out, int n);
+
+/* Cancel the queued requests, let the running ones stop at their next step
+ * boundary, join the workers and free the server.  NULL is accepted. */
+int tdvp_server_destroy(tdvp_server* s);
 
 /* Destroy a context and free its device memory.  NULL is accepted. */
 int tdvp_destroy(tdvp_ctx* ctx);

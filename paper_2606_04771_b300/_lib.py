@@ -17,7 +17,8 @@ LIB_PATH = os.path.join(HERE, "libtdvp.so")
 SYM = {"u1u1": 0, "u1su2": 1, "su2": 1}
 PREC = {"fp64": 0, "3xtf32": 1, "bf16x4": 2}
 ERRORS = {0: "ok", -1: "EINVAL", -2: "ESTATE", -3: "ENOMEM", -4: "ENUMERIC", -5: "EINTERNAL", -6: "ECUDA",
-          -7: "ETIMEOUT"}
+          -7: "ETIMEOUT", -8: "ECANCELED"}
+MODE = {"two": 0, "one": 1, "adaptive": 2}
 
 
 class TdvpError(RuntimeError):
@@ -29,6 +30,12 @@ class TdvpError(RuntimeError):
 class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("krylov_max", C.c_int), ("krylov_tol", C.c_double),
                 ("timeout_ms", C.c_int), ("cuda_stream", C.c_void_p), ("device", C.c_int)]
+
+
+class RequestC(C.Structure):
+    _fields_ = [("L", C.c_int), ("J", C.c_double), ("U", C.c_double), ("symmetry", C.c_int),
+                ("precision", C.c_int), ("mode", C.c_int), ("dt", C.c_double), ("t_final", C.c_double),
+                ("chi_max", C.c_longlong), ("eps", C.c_double), ("occupations", C.c_void_p)]
 
 
 _lib = None
@@ -69,6 +76,16 @@ def lib():
             "tdvp_launch_count": (C.c_int, [P(C.c_longlong)]),
             "tdvp_selftest_wait": (C.c_int, [C.c_uint, vp]),
             "tdvp_destroy": (C.c_int, [vp]),
+            "tdvp_server_create": (C.c_int, [C.c_double, C.c_int, P(Opts), P(vp)]),
+            "tdvp_server_footprint": (C.c_int, [P(RequestC), C.c_int, P(C.c_double)]),
+            "tdvp_server_submit": (C.c_int, [vp, P(RequestC), P(C.c_longlong)]),
+            "tdvp_server_poll": (C.c_int, [vp, C.c_longlong, P(C.c_int)]),
+            "tdvp_server_wait": (C.c_int, [vp, C.c_longlong, C.c_int, P(C.c_int)]),
+            "tdvp_server_result": (C.c_int, [vp, C.c_longlong, vp, vp, vp, vp, vp, C.c_int]),
+            "tdvp_server_cancel": (C.c_int, [vp, C.c_longlong]),
+            "tdvp_server_pause": (C.c_int, [vp, C.c_int]),
+            "tdvp_server_stats": (C.c_int, [vp, vp, C.c_int]),
+            "tdvp_server_destroy": (C.c_int, [vp]),
             "tdvp_strerror": (C.c_char_p, [C.c_int]),
             "tdvp_last_error": (C.c_char_p, []),
         }
@@ -226,7 +243,7 @@ class Chain(_Ctx):
         """One time step; mode "two" (two-site), "one" (one-site, bond dimensions
         fixed) or "adaptive" (two-site until the chi cap binds, then one-site).
         Returns the integrator used ("two" or "one")."""
-        m = {"two": 0, "one": 1, "adaptive": 2}[mode]
+        m = MODE[mode]
         used = C.c_int()
         check(lib().tdvp_step_mode(self.h, dt, int(chi_max), eps, m, C.byref(used)))
         return "one" if used.value == 1 else "two"
@@ -265,11 +282,11 @@ class Chain(_Ctx):
         return chi, red
 
     def stats(self):
-        v = np.zeros(18)
-        check(lib().tdvp_stats(self.h, v.ctypes.data, 18))
+        v = np.zeros(20)
+        check(lib().tdvp_stats(self.h, v.ctypes.data, 20))
         keys = ["seconds", "heff_flops", "env_flops", "matvecs", "max_krylov", "max_discarded", "chi_max_seen",
                 "t_theta", "t_plan", "t_krylov2", "t_split", "t_env", "t_krylov1", "steps", "splits", "sweeps64",
-                "sweeps32", "one_site_steps"]
+                "sweeps32", "one_site_steps", "device_bytes", "device_bytes_peak"]
         return dict(zip(keys, v.tolist()))
 
 

@@ -11,7 +11,8 @@
 #include "engine.hpp"
 
 struct tdvp_ctx {
-  tdvp::Engine* eng;
+  tdvp::Engine* eng = nullptr;
+  tdvp::DevAcct acct;  // device bytes of this context (live and peak)
 };
 
 namespace {
@@ -34,6 +35,27 @@ int guarded(F f) {
   } catch (const std::exception& e) {
     return fail(TDVP_EINTERNAL, e.what());
   }
+}
+
+// a call on a context: its device allocations are charged to the context
+template <class F>
+int guarded(tdvp_ctx* ctx, F f) {
+  tdvp::DevAcctScope scope(&ctx->acct);
+  return guarded(f);
+}
+
+// a new context around the engine that make() builds
+template <class Make>
+int create_ctx(tdvp_ctx** out, Make make) {
+  auto* c = new (std::nothrow) tdvp_ctx;
+  if (!c) return fail(TDVP_ENOMEM, "host allocation failed");
+  const int rc = guarded(c, [&] { c->eng = make(); });
+  if (rc != TDVP_OK) {
+    delete c;
+    return rc;
+  }
+  *out = c;
+  return TDVP_OK;
 }
 
 tdvp::Opts to_opts(const tdvp_opts* o) {
@@ -89,11 +111,10 @@ int tdvp_create(int L, double J, double U, int symmetry, const tdvp_opts* opts, 
   if (!out) return fail(TDVP_EINVAL, "out is NULL");
   *out = nullptr;
   if (symmetry != TDVP_SYM_U1U1 && symmetry != TDVP_SYM_U1SU2) return fail(TDVP_EINVAL, "unknown symmetry");
-  return guarded([&] {
+  return create_ctx(out, [&] {
     tdvp_opts d;
     tdvp_opts_default(&d);
-    auto* e = new tdvp::Engine(L, J, U, symmetry == TDVP_SYM_U1SU2, to_opts(opts ? opts : &d));
-    *out = new tdvp_ctx{e};
+    return new tdvp::Engine(L, J, U, symmetry == TDVP_SYM_U1SU2, to_opts(opts ? opts : &d));
   });
 }
 
@@ -103,12 +124,11 @@ int tdvp_create_product(int L, double J, double U, int symmetry, const int* occ,
   *out = nullptr;
   if (symmetry != TDVP_SYM_U1U1 && symmetry != TDVP_SYM_U1SU2) return fail(TDVP_EINVAL, "unknown symmetry");
   if (L < 2) return fail(TDVP_EINVAL, "L must be >= 2");
-  return guarded([&] {
+  return create_ctx(out, [&] {
     tdvp_opts d;
     tdvp_opts_default(&d);
     std::vector<int> o(occ, occ + L);
-    auto* e = tdvp::Engine::product_state(L, J, U, symmetry == TDVP_SYM_U1SU2, o, to_opts(opts ? opts : &d));
-    *out = new tdvp_ctx{e};
+    return tdvp::Engine::product_state(L, J, U, symmetry == TDVP_SYM_U1SU2, o, to_opts(opts ? opts : &d));
   });
 }
 
@@ -117,12 +137,11 @@ int tdvp_create_random(int L, double J, double U, int symmetry, long long chi_ta
   if (!out) return fail(TDVP_EINVAL, "out is NULL");
   *out = nullptr;
   if (symmetry != TDVP_SYM_U1U1 && symmetry != TDVP_SYM_U1SU2) return fail(TDVP_EINVAL, "unknown symmetry");
-  return guarded([&] {
+  return create_ctx(out, [&] {
     tdvp_opts d;
     tdvp_opts_default(&d);
-    auto* e = tdvp::Engine::random_state(L, J, U, symmetry == TDVP_SYM_U1SU2, chi_target, seed, center,
-                                         to_opts(opts ? opts : &d));
-    *out = new tdvp_ctx{e};
+    return tdvp::Engine::random_state(L, J, U, symmetry == TDVP_SYM_U1SU2, chi_target, seed, center,
+                                      to_opts(opts ? opts : &d));
   });
 }
 
@@ -132,24 +151,23 @@ int tdvp_bond_create(int symmetry, double J, double U, int nl, const int* left, 
   *out = nullptr;
   if (symmetry != TDVP_SYM_U1U1 && symmetry != TDVP_SYM_U1SU2) return fail(TDVP_EINVAL, "unknown symmetry");
   if (nl < 1 || nr < 1 || !left || !right) return fail(TDVP_EINVAL, "empty sector table");
-  return guarded([&] {
+  return create_ctx(out, [&] {
     tdvp_opts d;
     tdvp_opts_default(&d);
-    auto* e = tdvp::Engine::bond_problem(symmetry == TDVP_SYM_U1SU2, J, U, sectors(nl, left), sectors(nr, right),
-                                         to_opts(opts ? opts : &d));
-    *out = new tdvp_ctx{e};
+    return tdvp::Engine::bond_problem(symmetry == TDVP_SYM_U1SU2, J, U, sectors(nl, left), sectors(nr, right),
+                                      to_opts(opts ? opts : &d));
   });
 }
 
 int tdvp_step(tdvp_ctx* ctx, double dt, long long chi_max, double eps_trunc) {
   if (!ctx) return fail(TDVP_EINVAL, "ctx is NULL");
-  return guarded([&] { ctx->eng->step(dt, chi_max, eps_trunc); });
+  return guarded(ctx, [&] { ctx->eng->step(dt, chi_max, eps_trunc); });
 }
 
 int tdvp_step_mode(tdvp_ctx* ctx, double dt, long long chi_max, double eps_trunc, int mode, int* used) {
   if (!ctx) return fail(TDVP_EINVAL, "ctx is NULL");
   if (mode < 0 || mode > 2) return fail(TDVP_EINVAL, "mode must be 0, 1 or 2");
-  return guarded([&] {
+  return guarded(ctx, [&] {
     int u = ctx->eng->step_mode(dt, chi_max, eps_trunc, mode);
     if (used) *used = u;
   });
@@ -159,22 +177,22 @@ int tdvp_bond_update(tdvp_ctx* ctx, int bond, int direction, double dt, long lon
                      double* s_ent) {
   if (!ctx) return fail(TDVP_EINVAL, "ctx is NULL");
   if (direction != 0 && direction != 1) return fail(TDVP_EINVAL, "direction must be 0 or 1");
-  return guarded([&] { ctx->eng->single_bond(bond, direction, dt, chi_max, eps_trunc, s_ent); });
+  return guarded(ctx, [&] { ctx->eng->single_bond(bond, direction, dt, chi_max, eps_trunc, s_ent); });
 }
 
 int tdvp_measure_center(tdvp_ctx* ctx, int* site, double* n, double* sz, double* docc) {
   if (!ctx) return fail(TDVP_EINVAL, "ctx is NULL");
-  return guarded([&] { ctx->eng->measure_center(site, n, sz, docc); });
+  return guarded(ctx, [&] { ctx->eng->measure_center(site, n, sz, docc); });
 }
 
 int tdvp_measure(tdvp_ctx* ctx, double* n, double* sz, double* docc, double* s_ent, double* energy) {
   if (!ctx) return fail(TDVP_EINVAL, "ctx is NULL");
-  return guarded([&] { ctx->eng->measure(n, sz, docc, s_ent, energy); });
+  return guarded(ctx, [&] { ctx->eng->measure(n, sz, docc, s_ent, energy); });
 }
 
 int tdvp_bond_dims(tdvp_ctx* ctx, long long* chi, long long* chi_red) {
   if (!ctx) return fail(TDVP_EINVAL, "ctx is NULL");
-  return guarded([&] {
+  return guarded(ctx, [&] {
     tdvp::Engine* e = ctx->eng;
     if (e->bond_only()) throw tdvp::Error(TDVP_ESTATE, "bond problem has no chain");
     for (int k = 0; k <= e->L(); ++k) {
@@ -216,19 +234,20 @@ int tdvp_launch_count(long long* out) {
 
 int tdvp_stats(tdvp_ctx* ctx, double* out, int n) {
   if (!ctx || !out) return fail(TDVP_EINVAL, "NULL argument");
-  return guarded([&] {
+  return guarded(ctx, [&] {
     const tdvp::StepStats& s = ctx->eng->stats();
-    double v[18] = {s.seconds, (double)s.heff_flops, (double)s.env_flops, (double)s.matvecs, (double)s.max_krylov,
+    double v[20] = {s.seconds, (double)s.heff_flops, (double)s.env_flops, (double)s.matvecs, (double)s.max_krylov,
                     s.max_discarded, (double)s.chi_max_seen, s.phase[0], s.phase[1], s.phase[2], s.phase[3],
                     s.phase[4], s.phase[5], (double)s.steps, (double)s.splits, (double)s.sweeps64,
-                    (double)s.sweeps32, (double)s.one_site_steps};
-    for (int i = 0; i < n && i < 18; ++i) out[i] = v[i];
+                    (double)s.sweeps32, (double)s.one_site_steps, (double)ctx->acct.live.load(),
+                    (double)ctx->acct.peak.load()};
+    for (int i = 0; i < n && i < 20; ++i) out[i] = v[i];
   });
 }
 
 int tdvp_block_count(tdvp_ctx* ctx, int which, long long* nblocks, long long* nelems) {
   if (!ctx) return fail(TDVP_EINVAL, "ctx is NULL");
-  return guarded([&] {
+  return guarded(ctx, [&] {
     tdvp::BTensor* t = tensor_of(ctx, which);
     if (nblocks) *nblocks = (long long)t->blocks.size();
     if (nelems) *nelems = t->size;
@@ -237,7 +256,7 @@ int tdvp_block_count(tdvp_ctx* ctx, int which, long long* nblocks, long long* ne
 
 int tdvp_block_list(tdvp_ctx* ctx, int which, int* keys, int* dims, long long* offsets) {
   if (!ctx) return fail(TDVP_EINVAL, "ctx is NULL");
-  return guarded([&] {
+  return guarded(ctx, [&] {
     tdvp::BTensor* t = tensor_of(ctx, which);
     for (size_t i = 0; i < t->blocks.size(); ++i) {
       const tdvp::Block& b = t->blocks[i];
@@ -255,7 +274,7 @@ int tdvp_block_list(tdvp_ctx* ctx, int which, int* keys, int* dims, long long* o
 int tdvp_set_tensor(tdvp_ctx* ctx, int which, const double* data, long long n, int on_device) {
   if (!ctx || !data) return fail(TDVP_EINVAL, "NULL argument");
   if (which != 1 && which != 2) return fail(TDVP_EINVAL, "which must be 1 (L) or 2 (R)");
-  return guarded([&] {
+  return guarded(ctx, [&] {
     tdvp::BTensor* t = tensor_of(ctx, which);
     if (n != t->size) throw tdvp::Error(TDVP_EINVAL, "size mismatch");
     cudaStream_t s = ctx->eng->stream();
@@ -269,7 +288,7 @@ int tdvp_set_tensor(tdvp_ctx* ctx, int which, const double* data, long long n, i
 int tdvp_heff_apply(tdvp_ctx* ctx, int bond, const double* psi_in, double* psi_out, int on_device) {
   if (!ctx || !psi_in || !psi_out) return fail(TDVP_EINVAL, "NULL argument");
   if (bond != 0) return fail(TDVP_EINVAL, "bond must be 0");
-  return guarded([&] {
+  return guarded(ctx, [&] {
     tdvp::Engine* e = ctx->eng;
     tdvp::HeffPlan& H = e->bond_only() ? e->heff_plan_bond() : e->chain_heff0();
     cudaStream_t s = e->stream();
@@ -294,7 +313,7 @@ int tdvp_krylov_expm(tdvp_ctx* ctx, int bond, const double* psi_in, double* psi_
                      int* krylov_dim, int* launches) {
   if (!ctx || !psi_in || !psi_out) return fail(TDVP_EINVAL, "NULL argument");
   if (bond != 0) return fail(TDVP_EINVAL, "bond must be 0");
-  return guarded([&] {
+  return guarded(ctx, [&] {
     tdvp::Engine* e = ctx->eng;
     tdvp::HeffPlan& H = e->bond_only() ? e->heff_plan_bond() : e->chain_heff0();
     cudaStream_t s = e->stream();
@@ -315,7 +334,7 @@ int tdvp_krylov_expm(tdvp_ctx* ctx, int bond, const double* psi_in, double* psi_
 
 int tdvp_heff_flops(tdvp_ctx* ctx, long long* flops) {
   if (!ctx || !flops) return fail(TDVP_EINVAL, "NULL argument");
-  return guarded([&] {
+  return guarded(ctx, [&] {
     tdvp::Engine* e = ctx->eng;
     *flops = (e->bond_only() ? e->heff_plan_bond() : e->chain_heff0()).flops();
   });
@@ -323,7 +342,7 @@ int tdvp_heff_flops(tdvp_ctx* ctx, long long* flops) {
 
 int tdvp_heff_profile(tdvp_ctx* ctx, int iters, double* ms, long long* flops, long long* bytes) {
   if (!ctx || iters < 1) return fail(TDVP_EINVAL, "bad argument");
-  return guarded([&] {
+  return guarded(ctx, [&] {
     tdvp::Engine* e = ctx->eng;
     tdvp::HeffPlan& H = e->bond_only() ? e->heff_plan_bond() : e->chain_heff0();
     cudaStream_t s = e->stream();
@@ -466,7 +485,7 @@ int tdvp_svd(int p, int q, const double* a, double* s, double* u, double* vh, in
 
 int tdvp_destroy(tdvp_ctx* ctx) {
   if (!ctx) return TDVP_OK;
-  int rc = guarded([&] { delete ctx->eng; });
+  int rc = guarded(ctx, [&] { delete ctx->eng; });
   delete ctx;
   return rc;
 }
@@ -481,6 +500,7 @@ const char* tdvp_strerror(int code) {
     case TDVP_EINTERNAL: return "internal error";
     case TDVP_ECUDA: return "CUDA error";
     case TDVP_ETIMEOUT: return "device wait timed out";
+    case TDVP_ECANCELED: return "request cancelled";
     default: return "unknown error";
   }
 }

@@ -25,8 +25,17 @@ namespace tdvp {
 // device buffers and plan uploads
 // ---------------------------------------------------------------------------
 
+DevAcct*& current_acct() {
+  thread_local DevAcct* a = nullptr;
+  return a;
+}
+
 DevBuf::DevBuf(size_t b, cudaStream_t st) : bytes(b), s(st) {
-  if (b) TDVP_CUDA(cudaMallocAsync(&p, b, st));
+  if (b) {
+    TDVP_CUDA(cudaMallocAsync(&p, b, st));
+    acct = current_acct();
+    if (acct) acct->add((long long)b);
+  }
 }
 DevBuf::~DevBuf() { reset(); }
 DevBuf& DevBuf::operator=(DevBuf&& o) noexcept {
@@ -35,15 +44,21 @@ DevBuf& DevBuf::operator=(DevBuf&& o) noexcept {
     p = o.p;
     bytes = o.bytes;
     s = o.s;
+    acct = o.acct;
     o.p = nullptr;
     o.bytes = 0;
+    o.acct = nullptr;
   }
   return *this;
 }
 void DevBuf::reset() {
-  if (p) cudaFreeAsync(p, s);
+  if (p) {
+    cudaFreeAsync(p, s);
+    if (acct) acct->add(-(long long)bytes);
+  }
   p = nullptr;
   bytes = 0;
+  acct = nullptr;
 }
 
 template <class T>

@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <cstdint>
 #include <memory>
 #include <stdexcept>
@@ -29,10 +31,30 @@ struct Error : std::runtime_error {
   } while (0)
 
 // stream-ordered device buffer
+// Live and peak device bytes of one context.  Every DevBuf allocated while a
+// context's accountant is current on the thread (DevAcctScope, set by the C entry
+// points for the duration of a call) is charged to it until it is freed.
+struct DevAcct {
+  std::atomic<long long> live{0}, peak{0};
+  void add(long long b) {
+    const long long v = live.fetch_add(b) + b;
+    long long p = peak.load();
+    while (v > p && !peak.compare_exchange_weak(p, v)) {
+    }
+  }
+};
+DevAcct*& current_acct();  // thread-local
+struct DevAcctScope {
+  DevAcct* prev;
+  explicit DevAcctScope(DevAcct* a) : prev(current_acct()) { current_acct() = a; }
+  ~DevAcctScope() { current_acct() = prev; }
+};
+
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
   cudaStream_t s = nullptr;
+  DevAcct* acct = nullptr;
   DevBuf() = default;
   DevBuf(size_t b, cudaStream_t st);
   ~DevBuf();
