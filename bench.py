@@ -306,12 +306,42 @@ def run_engine(args):
     # DRAM bytes of one matvec (stage 1 + stage 3 launches) from the ncu capture of the
     # current BF16x4 kernel on this bond (dram__bytes_read.sum + dram__bytes_write.sum)
     traffic = 52.2e6 if args.precision == "bf16x4" else None
-    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "traffic_unit": "bytes per matvec",
-                "alg_bytes_per_matvec": heff["stage_alg_bytes"][0] + heff["stage_alg_bytes"][2],
-                "kernel": "grouped block GEMM of H_eff.psi (stages 1+3), chi=4096 bond",
-                "peak_source": pnote, "stage_ms": heff["stage_ms"],
-                "tensor_pipe_frac_upper": achieved * issued / peak}
+    roofline_heff = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": traffic, "traffic_unit": "bytes per matvec",
+                     "alg_bytes_per_matvec": heff["stage_alg_bytes"][0] + heff["stage_alg_bytes"][2],
+                     "kernel": "grouped block GEMM of H_eff.psi (stages 1+3), chi=4096 bond",
+                     "peak_source": pnote, "stage_ms": heff["stage_ms"],
+                     "tensor_pipe_frac_upper": achieved * issued / peak}
+    # the step's kernels by device time: the two Jacobi stages of the split are timed
+    # with CUDA events around each cooperative launch inside the timed steps; the
+    # H_eff GEMMs of the step are its matvecs x the GEMM time of one matvec
+    d = {k: (st1[k] - st0[k]) / args.steps for k in ("jacobi32_ms", "jacobi32_flops", "jacobi64_ms", "jacobi64_flops",
+                                                       "matvecs")}
+    shares = {"jacobi_fp32": d["jacobi32_ms"], "jacobi_fp64": d["jacobi64_ms"],
+              "heff_gemm": d["matvecs"] * heff["gemm_ms"]}
+    top = max(shares, key=shares.get)
+    clock_ghz = 2.032  # maximum SM clock of the B300
+    if top == "jacobi_fp32":
+        a = d["jacobi32_flops"] / (d["jacobi32_ms"] * 1e-3) / 1e12
+        p32 = 148 * 128 * 2 * clock_ghz / 1e3  # 148 SMs x 128 FP32 FMA lanes x 2 flops x clock
+        roofline = {"bound": "alu", "achieved": a, "peak": p32, "unit": "TFLOP/s", "frac": a / p32,
+                    "traffic": None, "kernel": "jacobi_coop_kernel<Svd32Task> (FP32 preconditioner of the split)",
+                    "peak_source": "FP32 FMA: 148 SMs x 128 lanes x 2 flops x 2.032 GHz (recipe unit counts, max clock)",
+                    "alg_flops_per_step": d["jacobi32_flops"], "ms_per_step": d["jacobi32_ms"]}
+    elif top == "jacobi_fp64":
+        a = d["jacobi64_flops"] / (d["jacobi64_ms"] * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": a, "peak": 1.25, "unit": "TFLOP/s", "frac": a / 1.25,
+                    "traffic": None, "kernel": "jacobi_coop_kernel<SvdTask> (FP64 Jacobi of the split)",
+                    "peak_source": "FP64 nominal 1.25 TFLOP/s (recipe table)",
+                    "alg_flops_per_step": d["jacobi64_flops"], "ms_per_step": d["jacobi64_ms"]}
+    else:
+        roofline = dict(roofline_heff)
+    roofline["step_kernel_ms"] = shares
+    roofline["step_ms"] = ms_step
+    wk = st1["split_work"] - st0["split_work"]
+    roofline["split_sectors"] = {"pmax": st1["split_pmax"], "qmax": st1["split_qmax"],
+                                 "work_frac_fits_192KiB": (st1["split_work_small"] - st0["split_work_small"]) / wk
+                                 if wk > 0 else None}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -328,6 +358,7 @@ def run_engine(args):
         "sweep": sweep,
         "heff_kernel": heff,
         "roofline": roofline,
+        "roofline_heff": roofline_heff,
         "e2e": {"value": heff["e2e_tflops"], "unit": UNIT, "h2d_bytes_per_step": heff["h2d_bytes"],
                 "d2h_bytes_per_step": heff["d2h_bytes"],
                 "path": "tdvp_krylov_expm with host buffers on the chi=4096 bond (H2D theta, D2H result)"},

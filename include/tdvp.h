@@ -69,6 +69,15 @@ typedef struct {
   int device;        /* CUDA device ordinal, or -1 for the current device */
 } tdvp_opts;
 
+/* Environment: when every sector of a split has at most 32 columns and a working
+ * copy within TDVP_JACOBI_RESIDENT_BYTES (read at every split; default and maximum
+ * 196608 bytes), each sector's Jacobi runs inside one CTA's shared memory;
+ * otherwise all sectors share the cooperative grid-wide kernel (0 forces that).
+ * Both paths give the same result, bit for bit.
+ * TDVP_JACOBI_CTAS_PER_SM (1..8, default 4, read at every launch) sets the CTAs
+ * per SM of the cooperative Jacobi grid (bounded by its occupancy); results do
+ * not depend on it. */
+
 /* Fill *o with the defaults listed above. */
 void tdvp_opts_default(tdvp_opts* o);
 
@@ -178,7 +187,16 @@ int tdvp_bond_dims(tdvp_ctx* ctx, long long* chi, long long* chi_red);
  * out[12] zero-site Krylov and absorption.  out[18] device bytes the context
  * holds now and out[19] the most it has held (the buffers of the context's own
  * tensors, plans and workspaces; the few-KB scratch of single launches is not
- * counted).  n = length of out (at most 20). */
+ * counted).  out[20] milliseconds and out[21] algorithmic flops of the FP32
+ * Jacobi launches of the splits, out[22], out[23] the same for the FP64 Jacobi
+ * launches (CUDA events around each cooperative launch; flops = over the
+ * sectors, sweeps in which the sector was still rotating x q(q-1)/2 column pairs
+ * x (48 p + 32 q when the right vectors are accumulated, else 48 p) for a p x q
+ * sector, p >= q).  out[24] largest P = max(p, q) and out[25] largest
+ * Q = min(p, q) of a sector in the split-precision splits, out[26] the sum of
+ * P Q^2 over those sectors and out[27] the same sum over the sectors whose
+ * complex64 copy fits in 192 KiB.  out[28] Jacobi calls of the splits and
+ * out[29] those that ran CTA-resident.  n = length of out (at most 30). */
 int tdvp_stats(tdvp_ctx* ctx, double* out, int n);
 
 /* ---- single-bond problems (the effective-Hamiltonian benchmark) ------------

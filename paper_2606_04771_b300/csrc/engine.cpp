@@ -1499,7 +1499,8 @@ double Engine::split(BTensor& theta, const BondSpace& bl, const BondSpace& br, l
     ts[g] = {Sp + soff[g], Q, M.mult_dim(groups[g].t)};
   }
   DevBuf dst = upload(st, stream_);
-  stats_.sweeps64 += jacobi(run_jacobi_rounds(dst.as<SvdTask>(), st, 40, 1e-14, dstatus_, stream_));
+  stats_.sweeps64 +=
+      jacobi(run_jacobi_rounds(dst.as<SvdTask>(), st, 40, 1e-14, dstatus_, stream_, 0.0, 0.0, &stats_.jacobi64));
   stats_.splits += 1;
   // truncation
   DevBuf dts = upload(ts, stream_);
@@ -1730,10 +1731,18 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
   launch_narrow(W64, W32, ttot, stream_);
   std::vector<Svd32Task> st32(ng);
   for (int g = 0; g < ng; ++g) st32[g] = {W32 + toff[g], V32 + voff[g], bigP(groups[g]), smallQ(groups[g])};
+  for (int g = 0; g < ng; ++g) {
+    const double P = bigP(groups[g]), Q = smallQ(groups[g]);
+    stats_.split_pmax = std::max<long long>(stats_.split_pmax, (long long)P);
+    stats_.split_qmax = std::max<long long>(stats_.split_qmax, (long long)Q);
+    stats_.split_work += P * Q * Q;
+    if (P * Q * 8.0 <= 192.0 * 1024.0) stats_.split_work_small += P * Q * Q;
+  }
   DevBuf dst32 = upload(st32, stream_);
   // FP32 stage: rotate while |g_i^H g_j| > 2e-5 |g_i||g_j|, at most 24 sweeps (it
   // need not converge: the FP64 stage finishes whatever is left)
-  const int sw32 = jacobi(run_jacobi_rounds32(dst32.as<Svd32Task>(), st32, 24, 2e-5f, 0.0f, stream_));
+  const int sw32 =
+      jacobi(run_jacobi_rounds32(dst32.as<Svd32Task>(), st32, 24, 2e-5f, 0.0f, stream_, &stats_.jacobi32));
   ok = true;
   stats_.sweeps32 += sw32;
   stats_.splits += 1;
@@ -1775,7 +1784,8 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
   // absolute terms (theta has unit norm, so that is a weight a decade below the
   // smallest truncation threshold in use; on the L=60 quench the observables do not
   // move against tighter settings while the stage needs fewer sweeps)
-  stats_.sweeps64 += jacobi(run_jacobi_rounds(dst.as<SvdTask>(), st, 30, 1e-13, dstatus_, stream_, 1e-6, 1e-10));
+  stats_.sweeps64 += jacobi(
+      run_jacobi_rounds(dst.as<SvdTask>(), st, 30, 1e-13, dstatus_, stream_, 1e-6, 1e-10, &stats_.jacobi64));
   DevBuf dts = upload(ts, stream_), doffs = upload(soff, stream_);
   DevBuf downer(std::max(stot, 1) * sizeof(int), stream_), dorder(std::max(stot, 1) * sizeof(int), stream_);
   DevBuf dkept(std::max(ng, 1) * sizeof(int), stream_), dstats(8 * sizeof(double), stream_);

@@ -173,6 +173,14 @@ struct StepStats {
   // of the mixed split) and FP32 (the preconditioner of the mixed split)
   long long sweeps64 = 0, sweeps32 = 0, splits = 0;
   long long one_site_steps = 0;
+  // the cooperative Jacobi launches of the splits (CUDA-event time and algorithmic
+  // flops, as JacobiProfile): FP32 preconditioner and FP64 stage
+  JacobiProfile jacobi32, jacobi64;
+  // sector shapes of the splits: largest P = max(p, q) and Q = min(p, q) seen, and the
+  // one-sided Jacobi work sum P Q^2 over all sectors and over those whose complex64
+  // copy (P Q x 8 bytes) fits in 192 KiB of shared memory
+  long long split_pmax = 0, split_qmax = 0;
+  double split_work = 0, split_work_small = 0;
 };
 
 class Engine {

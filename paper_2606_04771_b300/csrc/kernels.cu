@@ -14,6 +14,8 @@
 #include <mutex>
 
 #include <cstdio>
+#include <cstdlib>
+#include <type_traits>
 #include <vector>
 
 #include "common.hpp"
@@ -578,14 +580,17 @@ __device__ __forceinline__ void tourney(int r, int k, int n, int& i, int& j) {
 
 constexpr int JT = 256;  // threads per CTA of the cooperative Jacobi
 
-// x' = cs x - sn conj(e) y ; y' = sn e x + cs y
+// x' = cs x - sn conj(e) y ; y' = sn e x + cs y.  Written with explicit fma so that
+// every instantiation (registers or memory, global or shared) rounds the same way.
 template <class S, class C2>
 __device__ __forceinline__ void rot2(C2& x, C2& y, S cs, S sn, S ex, S ey) {
   const C2 a = x, b = y;
-  x.x = cs * a.x - sn * (ex * b.x + ey * b.y);
-  x.y = cs * a.y - sn * (ex * b.y - ey * b.x);
-  y.x = sn * (ex * a.x - ey * a.y) + cs * b.x;
-  y.y = sn * (ex * a.y + ey * a.x) + cs * b.y;
+  const S u = fma(ex, b.x, ey * b.y), w = fma(ex, b.y, -(ey * b.x));   // conj(e) y
+  const S f = fma(ex, a.x, -(ey * a.y)), h = fma(ex, a.y, ey * a.x);   // e x
+  x.x = fma(cs, a.x, -(sn * u));
+  x.y = fma(cs, a.y, -(sn * w));
+  y.x = fma(sn, f, cs * b.x);
+  y.y = fma(sn, h, cs * b.y);
 }
 
 // one column pair (i, j) by one warp; R > 0: rows lane + 32 k (k < R) in registers
@@ -632,11 +637,11 @@ __device__ __forceinline__ void warp_pair(C2* __restrict__ g, C2* __restrict__ v
     cx += __shfl_xor_sync(0xffffffffu, cx, o);
     cy += __shfl_xor_sync(0xffffffffu, cy, o);
   }
-  const S ac = sqrt(cx * cx + cy * cy);
+  const S ac = sqrt(fma(cx, cx, cy * cy));
   if (ac == S(0) || ac <= tol * sqrt(sa * sb)) return;  // warp-uniform
   const S zeta = (sb - sa) / (S(2) * ac);
-  const S tt = (zeta >= 0 ? S(1) : S(-1)) / (fabs(zeta) + sqrt(S(1) + zeta * zeta));
-  const S cs = S(1) / sqrt(S(1) + tt * tt), sn = cs * tt;
+  const S tt = (zeta >= 0 ? S(1) : S(-1)) / (fabs(zeta) + sqrt(fma(zeta, zeta, S(1))));
+  const S cs = S(1) / sqrt(fma(tt, tt, S(1))), sn = cs * tt;
   const S ex = cx / ac, ey = cy / ac;
   if (R > 0) {
 #pragma unroll
@@ -675,7 +680,8 @@ template <class Task, class S, class C2, int R>
 __global__ void __launch_bounds__(JT) jacobi_coop_kernel(const Task* __restrict__ tasks, int nt,
                                                          const int2* __restrict__ work, const int* __restrict__ active,
                                                          int nrounds, int max_sweeps, S tol, S tol_flag, S abs_flag,
-                                                         int* __restrict__ flags, int* __restrict__ out) {
+                                                         int* __restrict__ flags, int* __restrict__ out,
+                                                         int* __restrict__ task_sweeps) {
   cg::grid_group grid = cg::this_grid();
   // pair w goes to CTA w mod G (warp w div G there): consecutive pairs -- the pairs of
   // one large sector -- land on different SMs instead of sharing one SM's pipes
@@ -688,7 +694,10 @@ __global__ void __launch_bounds__(JT) jacobi_coop_kernel(const Task* __restrict_
   bool conv = false;
   for (; sweep < max_sweeps; ++sweep) {
     if (blockIdx.x == 0)
-      for (int e = threadIdx.x; e < nt; e += JT) now[e] = 0;
+      for (int e = threadIdx.x; e < nt; e += JT) {
+        now[e] = 0;
+        if (!prev || prev[e]) ++task_sweeps[e];  // the task takes part in this sweep
+      }
     grid.sync();
     for (int r = 0; r < nrounds; ++r) {
       const int na = active[r];
@@ -724,6 +733,62 @@ __global__ void __launch_bounds__(JT) jacobi_coop_kernel(const Task* __restrict_
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     out[0] = sweep;
     out[1] = conv ? 0 : 1;
+  }
+}
+
+// The same Jacobi for sectors small enough to live in one CTA's shared memory (used
+// when every sector of a call is that small): the
+// CTA loads its p x q working copy once, runs the sweeps with the same tournament,
+// the same pair arithmetic (warp_pair on the shared copy) and the same stopping rule,
+// with a CTA barrier per round instead of a grid barrier, and writes the copy back.
+// V stays in global memory.  Per sector the result is the one the cooperative
+// kernel gives: the rounds see the same pairs in the same order and each pair the
+// same operations.
+constexpr int RJT = 512;                     // threads per CTA of the resident Jacobi
+constexpr int RJ_SMEM = 192 * 1024;          // bytes of the largest resident working copy
+constexpr int RJ_QMAX = 2 * (RJT / 32);      // columns: one pair per warp and round
+
+template <class Task, class S, class C2>
+__global__ void __launch_bounds__(RJT) jacobi_resident_kernel(const Task* __restrict__ tasks,
+                                                              const int* __restrict__ ids, int max_sweeps, S tol,
+                                                              S tol_flag, S abs_flag, int* __restrict__ task_sweeps,
+                                                              int* __restrict__ nonconv) {
+  extern __shared__ __align__(16) unsigned char rj_smem[];
+  C2* g = reinterpret_cast<C2*>(rj_smem);
+  __shared__ int flag_s;
+  const int id = ids[blockIdx.x];
+  const Task t = tasks[id];
+  const int p = t.p, q = t.q;
+  const long long pq = (long long)p * q;
+  for (long long e = threadIdx.x; e < pq; e += RJT) g[e] = t.g[e];
+  const int warp = threadIdx.x >> 5, nw = RJT >> 5;
+  const int n = q + (q & 1);
+  int sweep = 0;
+  bool conv = false;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) flag_s = 0;
+    __syncthreads();
+    for (int r = 0; r < n - 1; ++r) {
+      for (int k = warp; k < n / 2; k += nw) {
+        int i, j;
+        tourney(r, k, n, i, j);
+        if (j >= q) continue;
+        warp_pair<S, C2, 0>(g, t.v, p, q, i, j, tol, tol_flag, abs_flag, &flag_s);
+      }
+      __syncthreads();
+    }
+    const int f = flag_s;
+    __syncthreads();
+    if (!f) {
+      conv = true;
+      ++sweep;
+      break;
+    }
+  }
+  for (long long e = threadIdx.x; e < pq; e += RJT) t.g[e] = g[e];
+  if (threadIdx.x == 0) {
+    task_sweeps[id] = sweep;
+    if (!conv) atomicOr(nonconv, 1);
   }
 }
 
@@ -774,7 +839,8 @@ __global__ void svd32_init_v_kernel(const Svd32Task* __restrict__ tasks) {
 // Pairs (task, k) sorted by task size descending, and per round the number of
 // leading pairs whose task still has that round.
 template <class Task>
-static void pair_schedule(const std::vector<Task>& h_tasks, std::vector<int2>& work, std::vector<int>& active) {
+static void pair_schedule(const std::vector<Task>& h_tasks, const std::vector<char>& skip, std::vector<int2>& work,
+                          std::vector<int>& active) {
   std::vector<int> ord(h_tasks.size());
   for (size_t i = 0; i < ord.size(); ++i) ord[i] = (int)i;
   std::sort(ord.begin(), ord.end(), [&](int x, int y) {
@@ -784,7 +850,7 @@ static void pair_schedule(const std::vector<Task>& h_tasks, std::vector<int2>& w
   std::vector<int> nround;  // rounds of the task of each work item
   for (int i : ord) {
     const int q = h_tasks[i].q;
-    if (q < 2) continue;
+    if (q < 2 || skip[i]) continue;
     const int n = q + (q & 1);
     for (int k = 0; k < n / 2; ++k) {
       work.push_back(make_int2(i, k));
@@ -842,62 +908,165 @@ static int coop_ordered(cudaStream_t s, Launch launch) {
   return 0;
 }
 
+// CTAs per SM of the cooperative Jacobi grid: 4, or TDVP_JACOBI_CTAS_PER_SM (1..8,
+// read at every launch; the occupancy limit still applies).  Only the pairs'
+// distribution over warps changes; every pair's arithmetic and order do not.
+static int coop_ctas_per_sm() {
+  const char* e = std::getenv("TDVP_JACOBI_CTAS_PER_SM");
+  if (!e || !*e) return 4;
+  const int v = std::atoi(e);
+  return v < 1 ? 1 : (v > 8 ? 8 : v);
+}
+
 template <class Task, class S, class C2, int R>
 static int coop_launch(const Task* d_tasks, int nt, const int2* d_work, const int* d_active, int nrounds,
-                       int max_sweeps, S tol, S tol_flag, S abs_flag, int* flags, int* out, cudaStream_t s) {
+                       int max_sweeps, S tol, S tol_flag, S abs_flag, int* flags, int* out, cudaStream_t s,
+                       int* task_sweeps) {
   auto kern = jacobi_coop_kernel<Task, S, C2, R>;
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, JT, 0);
   if (per < 1 || nsm < 1) return -1;
-  const int grid = nsm * (per < 4 ? per : 4);
-  void* args[] = {(void*)&d_tasks, (void*)&nt,  (void*)&d_work,   (void*)&d_active, (void*)&nrounds, (void*)&max_sweeps,
-                  (void*)&tol,     (void*)&tol_flag, (void*)&abs_flag, (void*)&flags,    (void*)&out};
+  const int grid = nsm * std::min(per, coop_ctas_per_sm());
+  void* args[] = {(void*)&d_tasks,    (void*)&nt,  (void*)&d_work,   (void*)&d_active, (void*)&nrounds,
+                  (void*)&max_sweeps, (void*)&tol, (void*)&tol_flag, (void*)&abs_flag, (void*)&flags,
+                  (void*)&out,        (void*)&task_sweeps};
   return coop_ordered(s, [&] {
     note_launch();
     return cudaLaunchCooperativeKernel((void*)kern, dim3(grid), dim3(JT), args, 0, s) == cudaSuccess ? 0 : -1;
   });
 }
 
+// Largest working copy (bytes) that may run CTA-resident: RJ_SMEM, or the value of
+// the environment variable TDVP_JACOBI_RESIDENT_BYTES (read at every call, clamped to
+// [0, RJ_SMEM]; 0 sends every sector to the cooperative kernel).  Both paths give
+// the same result; the variable only selects where a sector runs.
+static long long resident_limit() {
+  const char* e = std::getenv("TDVP_JACOBI_RESIDENT_BYTES");
+  if (!e || !*e) return RJ_SMEM;
+  const long long v = std::atoll(e);
+  return v < 0 ? 0 : (v > RJ_SMEM ? RJ_SMEM : v);
+}
+
 template <class Task, class S, class C2>
 static int coop_run(const Task* d_tasks, const std::vector<Task>& h_tasks, int max_sweeps, S tol, S tol_flag,
-                    S abs_flag, int* nonconv, cudaStream_t s) {
+                    S abs_flag, int* nonconv, bool with_v, JacobiProfile* prof, cudaStream_t s) {
   const int nt = (int)h_tasks.size();
   int pmax = 1;
-  for (auto& t : h_tasks) pmax = max(pmax, t.p);
+  // All sectors run CTA-resident when every one of them fits: q <= RJ_QMAX columns
+  // (each round is one parallel step of the CTA's warps) and a working copy within the
+  // shared-memory limit.  Otherwise all of them share the cooperative grid: a resident
+  // launch beside it would add its own rounds to the critical path, and a large sector
+  // inside one SM runs its pairs one after another on one SM's FP64 units.
+  const long long limit = resident_limit();
+  bool all_fit = true;
+  for (const Task& t : h_tasks)
+    if (t.q >= 2 && (t.q > RJ_QMAX || (long long)t.p * t.q * (long long)sizeof(C2) > limit)) all_fit = false;
+  std::vector<char> resident(nt, 0);
+  std::vector<int> rid;
+  for (int e = 0; e < nt; ++e) {
+    const Task& t = h_tasks[e];
+    if (t.q < 2) continue;
+    if (all_fit) {
+      resident[e] = 1;
+      rid.push_back(e);
+    } else {
+      pmax = max(pmax, t.p);
+    }
+  }
   std::vector<int2> work;
   std::vector<int> active;
-  pair_schedule(h_tasks, work, active);
-  if (work.empty()) return 1;
+  pair_schedule(h_tasks, resident, work, active);
+  if (work.empty() && rid.empty()) return 1;
   int2* d_work = nullptr;
-  int *d_active = nullptr, *flags = nullptr, *out = nullptr;
-  cudaMallocAsync(&d_work, work.size() * sizeof(int2), s);
-  cudaMallocAsync(&d_active, active.size() * sizeof(int), s);
-  cudaMallocAsync(&flags, (2 * nt + 2) * sizeof(int), s);
+  int *d_active = nullptr, *flags = nullptr, *out = nullptr, *d_rid = nullptr;
+  if (!work.empty()) {
+    cudaMallocAsync(&d_work, work.size() * sizeof(int2), s);
+    cudaMallocAsync(&d_active, active.size() * sizeof(int), s);
+    cudaMemcpyAsync(d_work, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(d_active, active.data(), active.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+  }
+  if (!rid.empty()) {
+    cudaMallocAsync(&d_rid, rid.size() * sizeof(int), s);
+    cudaMemcpyAsync(d_rid, rid.data(), rid.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+  }
+  // flags: two sweep buffers [2 nt], out [2] (cooperative sweeps, non-convergence),
+  // per-task active sweeps of the cooperative kernel [nt], non-convergence of the
+  // resident sectors [1], sweeps of the resident sectors [nt]
+  cudaMallocAsync(&flags, (4 * nt + 3) * sizeof(int), s);
   out = flags + 2 * nt;
-  cudaMemcpyAsync(d_work, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
-  cudaMemcpyAsync(d_active, active.data(), active.size() * sizeof(int), cudaMemcpyHostToDevice, s);
-  const int nr = (int)active.size();
-  int rc;
-  switch (rows_per_lane(pmax)) {
-    case 1: rc = coop_launch<Task, S, C2, 1>(d_tasks, nt, d_work, d_active, nr, max_sweeps, tol, tol_flag, abs_flag, flags, out, s); break;
-    case 2: rc = coop_launch<Task, S, C2, 2>(d_tasks, nt, d_work, d_active, nr, max_sweeps, tol, tol_flag, abs_flag, flags, out, s); break;
-    case 4: rc = coop_launch<Task, S, C2, 4>(d_tasks, nt, d_work, d_active, nr, max_sweeps, tol, tol_flag, abs_flag, flags, out, s); break;
-    case 8: rc = coop_launch<Task, S, C2, 8>(d_tasks, nt, d_work, d_active, nr, max_sweeps, tol, tol_flag, abs_flag, flags, out, s); break;
-    case 16: rc = coop_launch<Task, S, C2, 16>(d_tasks, nt, d_work, d_active, nr, max_sweeps, tol, tol_flag, abs_flag, flags, out, s); break;
-    default: rc = coop_launch<Task, S, C2, 0>(d_tasks, nt, d_work, d_active, nr, max_sweeps, tol, tol_flag, abs_flag, flags, out, s); break;
+  int* tsw = out + 2;
+  int* rnc = tsw + nt;
+  int* rsw = rnc + 1;
+  cudaMemsetAsync(out, 0, (2 * nt + 3) * sizeof(int), s);
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  if (prof) {
+    cudaEventCreate(&ev[0]);
+    cudaEventCreate(&ev[1]);
+    cudaEventRecord(ev[0], s);
   }
-  int h[2] = {max_sweeps, 1};
+  int rc = 0;
+  if (!rid.empty()) {
+    static const bool attr = [] {  // once per process, thread-safe (function-local static)
+      cudaFuncSetAttribute(jacobi_resident_kernel<Task, S, C2>, cudaFuncAttributeMaxDynamicSharedMemorySize, RJ_SMEM);
+      return true;
+    }();
+    (void)attr;
+    size_t sm = 0;
+    for (int e : rid) sm = std::max(sm, (size_t)h_tasks[e].p * h_tasks[e].q * sizeof(C2));
+    note_launch();
+    jacobi_resident_kernel<Task, S, C2><<<(int)rid.size(), RJT, sm, s>>>(d_tasks, d_rid, max_sweeps, tol, tol_flag,
+                                                                         abs_flag, rsw, rnc);
+    if (cudaGetLastError() != cudaSuccess) rc = -1;
+  }
+  if (rc == 0 && !work.empty()) {
+    const int nr = (int)active.size();
+    auto go = [&](auto r_tag) {
+      constexpr int R = decltype(r_tag)::value;
+      return coop_launch<Task, S, C2, R>(d_tasks, nt, d_work, d_active, nr, max_sweeps, tol, tol_flag, abs_flag,
+                                         flags, out, s, tsw);
+    };
+    switch (rows_per_lane(pmax)) {
+      case 1: rc = go(std::integral_constant<int, 1>()); break;
+      case 2: rc = go(std::integral_constant<int, 2>()); break;
+      case 4: rc = go(std::integral_constant<int, 4>()); break;
+      case 8: rc = go(std::integral_constant<int, 8>()); break;
+      case 16: rc = go(std::integral_constant<int, 16>()); break;
+      default: rc = go(std::integral_constant<int, 0>()); break;
+    }
+  }
+  if (prof) cudaEventRecord(ev[1], s);
+  std::vector<int> h(3 + 2 * nt, 0);
+  int sweeps = -1, nc = 1;
   if (rc == 0) {
-    cudaMemcpyAsync(h, out, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(h.data(), out, (3 + 2 * nt) * sizeof(int), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
+    auto task_sweeps = [&](int e) { return resident[e] ? h[3 + nt + e] : h[2 + e]; };
+    sweeps = h[0];  // the cooperative launch's sweeps (0 when it did not run)
+    for (int e : rid) sweeps = max(sweeps, task_sweeps(e));
+    nc = (h[1] | h[2 + nt]) ? 1 : 0;
+    if (prof) {
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess) prof->ms += ms;
+      for (int e = 0; e < nt; ++e) {
+        const double p = h_tasks[e].p, q = h_tasks[e].q;
+        prof->flops += (double)task_sweeps(e) * 0.5 * q * (q - 1) * (48.0 * p + (with_v ? 32.0 * q : 0.0));
+      }
+      prof->launches += 1;
+      if (!rid.empty()) prof->resident += 1;
+    }
   }
-  cudaFreeAsync(d_work, s);
-  cudaFreeAsync(d_active, s);
+  if (prof) {
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+  }
+  if (d_work) cudaFreeAsync(d_work, s);
+  if (d_active) cudaFreeAsync(d_active, s);
+  if (d_rid) cudaFreeAsync(d_rid, s);
   cudaFreeAsync(flags, s);
-  if (nonconv) *nonconv = h[1];
-  return rc == 0 ? h[0] : -1;
+  if (nonconv) *nonconv = nc;
+  return rc == 0 ? sweeps : -1;
 }
 
 // Jacobi driver: returns the number of sweeps run, or -1 when the cooperative launch
@@ -912,7 +1081,7 @@ static int coop_run(const Task* d_tasks, const std::vector<Task>& h_tasks, int m
 // unit-norm theta, so abs_flag is a weight).  Non-convergence within max_sweeps
 // sets *status to 1.
 int run_jacobi_rounds(const SvdTask* d_tasks, const std::vector<SvdTask>& h_tasks, int max_sweeps, double tol,
-                      int* status, cudaStream_t s, double tol_flag, double abs_flag) {
+                      int* status, cudaStream_t s, double tol_flag, double abs_flag, JacobiProfile* prof) {
   const int nt = (int)h_tasks.size();
   if (nt == 0) return 0;
   if (!(tol_flag >= tol)) tol_flag = tol;
@@ -921,7 +1090,9 @@ int run_jacobi_rounds(const SvdTask* d_tasks, const std::vector<SvdTask>& h_task
   note_launch();
   svd_init_v_kernel<<<nt, 256, 0, s>>>(d_tasks);
   int nonconv = 0;
-  const int sweeps = coop_run<SvdTask, double, cplx>(d_tasks, h_tasks, max_sweeps, tol, tol_flag, abs_flag, &nonconv, s);
+  const bool with_v = h_tasks[0].v != nullptr;
+  const int sweeps =
+      coop_run<SvdTask, double, cplx>(d_tasks, h_tasks, max_sweeps, tol, tol_flag, abs_flag, &nonconv, with_v, prof, s);
   if (sweeps > 0 && nonconv) {
     int one = 1;
     cudaMemcpyAsync(status, &one, sizeof(int), cudaMemcpyHostToDevice, s);  // reported by the caller's check
@@ -944,12 +1115,13 @@ int run_jacobi_rounds(const SvdTask* d_tasks, const std::vector<SvdTask>& h_task
 // ---------------------------------------------------------------------------
 
 int run_jacobi_rounds32(const Svd32Task* d_tasks, const std::vector<Svd32Task>& h_tasks, int max_sweeps, float tol,
-                        float abs_flag, cudaStream_t s) {
+                        float abs_flag, cudaStream_t s, JacobiProfile* prof) {
   const int nt = (int)h_tasks.size();
   if (nt == 0) return 0;
   note_launch();
   svd32_init_v_kernel<<<nt, 256, 0, s>>>(d_tasks);
-  return coop_run<Svd32Task, float, float2>(d_tasks, h_tasks, max_sweeps, tol, 0.0f, abs_flag, nullptr, s);
+  return coop_run<Svd32Task, float, float2>(d_tasks, h_tasks, max_sweeps, tol, 0.0f, abs_flag, nullptr, true, prof,
+                                            s);
 }
 
 

@@ -66,10 +66,20 @@ void launch_krylov_step(KrylovState* st, const cplx* h1, const cplx* nrm2, doubl
 
 void launch_jacobi_svd(const SvdTask* tasks, int ntasks, int max_q, int max_sweeps, double tol, int* status,
                        cudaStream_t s);
+// Time and algorithmic work of the cooperative Jacobi launches a caller asks to be
+// profiled: ms summed over the launches (CUDA events around each launch on its
+// stream), flops = sum over tasks of (sweeps in which the task was active) x
+// q(q-1)/2 pairs x (16p for the two squared norms and the inner product of a column
+// pair, 32p for rotating the pair, 32q for rotating the pair's columns of V when V
+// is accumulated).  Every visited pair is counted as rotated.
+struct JacobiProfile {
+  double ms = 0, flops = 0;
+  long long launches = 0, resident = 0;  // calls, and calls that ran CTA-resident
+};
 // FP32 round-robin Jacobi on complex64 working copies (p >= q), accumulating V
 // (from the identity); returns the sweeps run
 int run_jacobi_rounds32(const Svd32Task* d_tasks, const std::vector<Svd32Task>& h_tasks, int max_sweeps, float tol,
-                        float abs_flag, cudaStream_t s);
+                        float abs_flag, cudaStream_t s, JacobiProfile* prof = nullptr);
 void launch_narrow(const cplx* src, float2* dst, long long n, cudaStream_t s);
 void launch_widen(const float2* src, cplx* dst, long long n, cudaStream_t s);
 void launch_basis64(const BasisTask* tasks, int n, cudaStream_t s);
@@ -80,7 +90,8 @@ void launch_chol_inv(const CholTask* tasks, int n, double shift_rel, int* status
 // round-robin one-sided Jacobi over all tasks at once, one warp per column pair
 // (same result layout as launch_jacobi_svd; v may be NULL); returns the sweeps run
 int run_jacobi_rounds(const SvdTask* d_tasks, const std::vector<SvdTask>& h_tasks, int max_sweeps, double tol,
-                      int* status, cudaStream_t s, double tol_flag = 0.0, double abs_flag = 0.0);
+                      int* status, cudaStream_t s, double tol_flag = 0.0, double abs_flag = 0.0,
+                      JacobiProfile* prof = nullptr);
 void launch_truncate(const TruncSector* secs, int nsec, const int* offs, int n, double eps, long long chi_max,
                      int* owner, int* order, int* kept, double* stats, cudaStream_t s);
 void launch_wdot(const DotTask* tasks, int ntasks, double* partial, double* out, int nslots, cudaStream_t s);
