@@ -72,8 +72,12 @@ typedef struct {
 /* Environment: when every sector of a split has at most 32 columns and a working
  * copy within TDVP_JACOBI_RESIDENT_BYTES (read at every split; default and maximum
  * 196608 bytes), each sector's Jacobi runs inside one CTA's shared memory;
- * otherwise all sectors share the cooperative grid-wide kernel (0 forces that).
- * Both paths give the same result, bit for bit.
+ * otherwise all sectors share the cooperative grid-wide kernel
+ * (TDVP_JACOBI_RESIDENT_BYTES=0 skips the first form).  With
+ * TDVP_JACOBI_CLUSTER=1, splits whose sectors each fit in the shared memory of a
+ * cluster of at most 8 CTAs run one thread-block cluster per sector instead of
+ * the cooperative kernel (off by default: slower on the measured workloads).
+ * All forms give the same result, bit for bit.
  * TDVP_JACOBI_CTAS_PER_SM (1..8, default 4, read at every launch) sets the CTAs
  * per SM of the cooperative Jacobi grid (bounded by its occupancy); results do
  * not depend on it. */
@@ -196,7 +200,8 @@ int tdvp_bond_dims(tdvp_ctx* ctx, long long* chi, long long* chi_red);
  * Q = min(p, q) of a sector in the split-precision splits, out[26] the sum of
  * P Q^2 over those sectors and out[27] the same sum over the sectors whose
  * complex64 copy fits in 192 KiB.  out[28] Jacobi calls of the splits and
- * out[29] those that ran CTA-resident.  n = length of out (at most 30). */
+ * out[29] those that ran CTA-resident, out[30] those that ran in thread-block
+ * clusters.  n = length of out (at most 31). */
 int tdvp_stats(tdvp_ctx* ctx, double* out, int n);
 
 /* ---- single-bond problems (the effective-Hamiltonian benchmark) ------------

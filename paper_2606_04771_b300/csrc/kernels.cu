@@ -593,13 +593,14 @@ __device__ __forceinline__ void rot2(C2& x, C2& y, S cs, S sn, S ex, S ey) {
   y.y = fma(sn, h, cs * b.y);
 }
 
-// one column pair (i, j) by one warp; R > 0: rows lane + 32 k (k < R) in registers
+// one column pair by one warp, given the two columns of G (p rows) and, when V is
+// accumulated, of V (q rows); any address space (global, shared, a cluster peer's
+// shared memory).  R > 0: rows lane + 32 k (k < R) in registers.
 template <class S, class C2, int R>
-__device__ __forceinline__ void warp_pair(C2* __restrict__ g, C2* __restrict__ v, int p, int q, int i, int j, S tol,
-                                          S tol_flag, S abs_flag, int* __restrict__ flag) {
+__device__ __forceinline__ void warp_pair_cols(C2* __restrict__ gi, C2* __restrict__ gj, C2* __restrict__ vi,
+                                               C2* __restrict__ vj, int p, int q, S tol, S tol_flag, S abs_flag,
+                                               int* __restrict__ flag) {
   const int lane = threadIdx.x & 31;
-  C2* gi = g + (long long)i * p;
-  C2* gj = g + (long long)j * p;
   S sa = 0, sb = 0, cx = 0, cy = 0;
   constexpr int RR = R > 0 ? R : 1;
   C2 x[RR], y[RR];
@@ -662,9 +663,7 @@ __device__ __forceinline__ void warp_pair(C2* __restrict__ g, C2* __restrict__ v
       gj[r] = b;
     }
   }
-  if (v) {
-    C2* vi = v + (long long)i * q;
-    C2* vj = v + (long long)j * q;
+  if (vi) {
 #pragma unroll 4
     for (int r = lane; r < q; r += 32) {
       C2 a = vi[r], b = vj[r];
@@ -674,6 +673,14 @@ __device__ __forceinline__ void warp_pair(C2* __restrict__ g, C2* __restrict__ v
     }
   }
   if (lane == 0 && ac > tol_flag * sqrt(sa * sb) && ac > abs_flag) atomicOr(flag, 1);
+}
+
+// column pair (i, j) of a column-major p x q G (and q x q V, or none)
+template <class S, class C2, int R>
+__device__ __forceinline__ void warp_pair(C2* __restrict__ g, C2* __restrict__ v, int p, int q, int i, int j, S tol,
+                                          S tol_flag, S abs_flag, int* __restrict__ flag) {
+  warp_pair_cols<S, C2, R>(g + (long long)i * p, g + (long long)j * p, v ? v + (long long)i * q : nullptr,
+                           v ? v + (long long)j * q : nullptr, p, q, tol, tol_flag, abs_flag, flag);
 }
 
 template <class Task, class S, class C2, int R>
@@ -787,6 +794,79 @@ __global__ void __launch_bounds__(RJT) jacobi_resident_kernel(const Task* __rest
   }
   for (long long e = threadIdx.x; e < pq; e += RJT) t.g[e] = g[e];
   if (threadIdx.x == 0) {
+    task_sweeps[id] = sweep;
+    if (!conv) atomicOr(nonconv, 1);
+  }
+}
+
+// The same Jacobi with each sector held in the shared memory of one thread-block
+// cluster (C CTAs): column c of G (and of V) lives in CTA c mod C, slot c div C.  A
+// round's pairs are spread over the cluster's warps, which read and rotate the two
+// columns where they live (distributed shared memory); a cluster barrier ends each
+// round.  Same tournament, pair arithmetic and stopping rule as the other forms.
+constexpr int CJT = 1024;           // threads per CTA of the cluster Jacobi
+constexpr int CJ_SMEM = 200 * 1024; // bytes of one CTA's slice
+
+template <class Task, class S, class C2>
+__global__ void __launch_bounds__(CJT) jacobi_cluster_kernel(const Task* __restrict__ tasks,
+                                                             const int* __restrict__ ids, int max_sweeps, S tol,
+                                                             S tol_flag, S abs_flag, int* __restrict__ task_sweeps,
+                                                             int* __restrict__ nonconv) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const int id = ids[blockIdx.x / C];
+  extern __shared__ __align__(16) unsigned char cj_smem[];
+  __shared__ int flag_s;
+  const Task t = tasks[id];
+  const int p = t.p, q = t.q;
+  const bool with_v = t.v != nullptr;
+  const int slots = (q + C - 1) / C;  // column slots per CTA
+  C2* gl = reinterpret_cast<C2*>(cj_smem);
+  C2* vl = gl + (long long)slots * p;
+  for (int l = 0; rank + C * l < q; ++l) {
+    const int c = rank + C * l;
+    for (int r = threadIdx.x; r < p; r += CJT) gl[(long long)l * p + r] = t.g[(long long)c * p + r];
+    if (with_v)
+      for (int r = threadIdx.x; r < q; r += CJT) vl[(long long)l * q + r] = t.v[(long long)c * q + r];
+  }
+  int* flag0 = cl.map_shared_rank(&flag_s, 0);
+  const int warp = threadIdx.x >> 5, nw = CJT >> 5;
+  const int gw = rank * nw + warp, W = C * nw;
+  const int n = q + (q & 1);
+  int sweep = 0;
+  bool conv = false;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (rank == 0 && threadIdx.x == 0) flag_s = 0;
+    cl.sync();  // slices loaded (first sweep), flag reset
+    for (int r = 0; r < n - 1; ++r) {
+      for (int k = gw; k < n / 2; k += W) {
+        int i, j;
+        tourney(r, k, n, i, j);
+        if (j >= q) continue;
+        C2* gi = cl.map_shared_rank(gl + (long long)(i / C) * p, i % C);
+        C2* gj = cl.map_shared_rank(gl + (long long)(j / C) * p, j % C);
+        C2* vi = with_v ? cl.map_shared_rank(vl + (long long)(i / C) * q, i % C) : nullptr;
+        C2* vj = with_v ? cl.map_shared_rank(vl + (long long)(j / C) * q, j % C) : nullptr;
+        warp_pair_cols<S, C2, 0>(gi, gj, vi, vj, p, q, tol, tol_flag, abs_flag, flag0);
+      }
+      cl.sync();
+    }
+    const int f = *reinterpret_cast<volatile int*>(flag0);
+    cl.sync();  // every CTA has read the flag before it is reset
+    if (!f) {
+      conv = true;
+      ++sweep;
+      break;
+    }
+  }
+  for (int l = 0; rank + C * l < q; ++l) {
+    const int c = rank + C * l;
+    for (int r = threadIdx.x; r < p; r += CJT) t.g[(long long)c * p + r] = gl[(long long)l * p + r];
+    if (with_v)
+      for (int r = threadIdx.x; r < q; r += CJT) t.v[(long long)c * q + r] = vl[(long long)l * q + r];
+  }
+  if (rank == 0 && threadIdx.x == 0) {
     task_sweeps[id] = sweep;
     if (!conv) atomicOr(nonconv, 1);
   }
@@ -949,6 +1029,42 @@ static long long resident_limit() {
   return v < 0 ? 0 : (v > RJ_SMEM ? RJ_SMEM : v);
 }
 
+// Whether the cluster form may run: only when TDVP_JACOBI_CLUSTER=1 (read at every
+// call).  It is off by default because it is slower on the workloads measured: a
+// sector's pairs then run on the C SMs of its cluster, and clusters of 200 KiB CTAs
+// run in waves, while the cooperative form spreads every round's pairs over all SMs
+// (the FP64 stage suffers most, the B300's FP64 rate per SM being low).
+static bool cluster_enabled() {
+  const char* e = std::getenv("TDVP_JACOBI_CLUSTER");
+  return e && e[0] == '1';
+}
+
+// Smallest cluster size (2, 4 or 8 CTAs) whose slices hold every sector of the call
+// (G, and V when accumulated), with the largest slice in *smem; 0 when a sector does
+// not fit in 8 CTAs.
+template <class Task, class C2>
+static int cluster_size_for(const std::vector<Task>& h_tasks, size_t* smem) {
+  for (int C = 2; C <= 8; C *= 2) {
+    size_t need = 0;
+    bool ok = true;
+    for (const Task& t : h_tasks) {
+      if (t.q < 2) continue;
+      const size_t slots = (size_t)(t.q + C - 1) / C;
+      const size_t b = slots * ((size_t)t.p + (t.v ? (size_t)t.q : 0)) * sizeof(C2);
+      if (b > (size_t)CJ_SMEM) {
+        ok = false;
+        break;
+      }
+      need = std::max(need, b);
+    }
+    if (ok) {
+      *smem = need;
+      return C;
+    }
+  }
+  return 0;
+}
+
 template <class Task, class S, class C2>
 static int coop_run(const Task* d_tasks, const std::vector<Task>& h_tasks, int max_sweeps, S tol, S tol_flag,
                     S abs_flag, int* nonconv, bool with_v, JacobiProfile* prof, cudaStream_t s) {
@@ -959,21 +1075,62 @@ static int coop_run(const Task* d_tasks, const std::vector<Task>& h_tasks, int m
   // shared-memory limit.  Otherwise all of them share the cooperative grid: a resident
   // launch beside it would add its own rounds to the critical path, and a large sector
   // inside one SM runs its pairs one after another on one SM's FP64 units.
+  // Failing that, all sectors run in thread-block clusters when every one fits in the
+  // distributed shared memory of 8 CTAs; otherwise on the cooperative grid.
   const long long limit = resident_limit();
   bool all_fit = true;
   for (const Task& t : h_tasks)
     if (t.q >= 2 && (t.q > RJ_QMAX || (long long)t.p * t.q * (long long)sizeof(C2) > limit)) all_fit = false;
+  size_t cl_smem = 0;
+  int cl_size = 0;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute cl_attr[1];
+  auto cl_kern = jacobi_cluster_kernel<Task, S, C2>;
+  if (!all_fit && cluster_enabled()) {
+    cl_size = cluster_size_for<Task, C2>(h_tasks, &cl_smem);
+    if (cl_size > 0) {
+      static const bool attr = [] {  // once per process, thread-safe (function-local static)
+        cudaFuncSetAttribute(jacobi_cluster_kernel<Task, S, C2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             CJ_SMEM);
+        return true;
+      }();
+      (void)attr;
+      int nsec = 0;
+      for (const Task& t : h_tasks) nsec += t.q >= 2 ? 1 : 0;
+      cfg.gridDim = dim3((unsigned)(nsec * cl_size));
+      cfg.blockDim = dim3(CJT);
+      cfg.dynamicSmemBytes = cl_smem;
+      cfg.stream = s;
+      cl_attr[0].id = cudaLaunchAttributeClusterDimension;
+      cl_attr[0].val.clusterDim.x = (unsigned)cl_size;
+      cl_attr[0].val.clusterDim.y = 1;
+      cl_attr[0].val.clusterDim.z = 1;
+      cfg.attrs = cl_attr;
+      cfg.numAttrs = 1;
+      int ncl = 0;  // clusters of this shape that fit on the device at once
+      if (cudaOccupancyMaxActiveClusters(&ncl, (void*)cl_kern, &cfg) != cudaSuccess || ncl < 1) {
+        cudaGetLastError();
+        cl_size = 0;
+      }
+    }
+  }
+  const bool own_launch = all_fit || cl_size > 0;  // resident or cluster form
   std::vector<char> resident(nt, 0);
   std::vector<int> rid;
   for (int e = 0; e < nt; ++e) {
     const Task& t = h_tasks[e];
     if (t.q < 2) continue;
-    if (all_fit) {
+    if (own_launch) {
       resident[e] = 1;
       rid.push_back(e);
     } else {
       pmax = max(pmax, t.p);
     }
+  }
+  if (cl_size > 0) {  // largest sectors first, so that their clusters start first
+    std::stable_sort(rid.begin(), rid.end(), [&](int a, int b) {
+      return (long long)h_tasks[a].p * h_tasks[a].q > (long long)h_tasks[b].p * h_tasks[b].q;
+    });
   }
   std::vector<int2> work;
   std::vector<int> active;
@@ -1007,7 +1164,12 @@ static int coop_run(const Task* d_tasks, const std::vector<Task>& h_tasks, int m
     cudaEventRecord(ev[0], s);
   }
   int rc = 0;
-  if (!rid.empty()) {
+  if (!rid.empty() && cl_size > 0) {
+    note_launch();
+    if (cudaLaunchKernelEx(&cfg, cl_kern, (const Task*)d_tasks, (const int*)d_rid, max_sweeps, tol, tol_flag, abs_flag,
+                           rsw, rnc) != cudaSuccess)
+      rc = -1;
+  } else if (!rid.empty()) {
     static const bool attr = [] {  // once per process, thread-safe (function-local static)
       cudaFuncSetAttribute(jacobi_resident_kernel<Task, S, C2>, cudaFuncAttributeMaxDynamicSharedMemorySize, RJ_SMEM);
       return true;
@@ -1054,7 +1216,8 @@ static int coop_run(const Task* d_tasks, const std::vector<Task>& h_tasks, int m
         prof->flops += (double)task_sweeps(e) * 0.5 * q * (q - 1) * (48.0 * p + (with_v ? 32.0 * q : 0.0));
       }
       prof->launches += 1;
-      if (!rid.empty()) prof->resident += 1;
+      if (!rid.empty() && cl_size == 0) prof->resident += 1;
+      if (!rid.empty() && cl_size > 0) prof->cluster += 1;
     }
   }
   if (prof) {

@@ -74,7 +74,7 @@ void launch_jacobi_svd(const SvdTask* tasks, int ntasks, int max_q, int max_swee
 // is accumulated).  Every visited pair is counted as rotated.
 struct JacobiProfile {
   double ms = 0, flops = 0;
-  long long launches = 0, resident = 0;  // calls, and calls that ran CTA-resident
+  long long launches = 0, resident = 0, cluster = 0;  // calls; calls that ran CTA-resident, in clusters
 };
 // FP32 round-robin Jacobi on complex64 working copies (p >= q), accumulating V
 // (from the identity); returns the sweeps run
