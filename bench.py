@@ -325,7 +325,10 @@ def run_engine(args):
         a = d["jacobi32_flops"] / (d["jacobi32_ms"] * 1e-3) / 1e12
         p32 = 148 * 128 * 2 * clock_ghz / 1e3  # 148 SMs x 128 FP32 FMA lanes x 2 flops x clock
         roofline = {"bound": "alu", "achieved": a, "peak": p32, "unit": "TFLOP/s", "frac": a / p32,
-                    "traffic": None, "kernel": "jacobi_coop_kernel<Svd32Task> (FP32 preconditioner of the split)",
+                    "traffic": None,
+                    "traffic_note": "ncu at chi=2048: 5.4 MB DRAM (the working set once) and 10.3 GB L2 per launch; "
+                                    "DRAM bytes follow the matrices, not the flops, so no scaled figure",
+                    "kernel": "jacobi_coop_kernel<Svd32Task> (FP32 preconditioner of the split)",
                     "peak_source": "FP32 FMA: 148 SMs x 128 lanes x 2 flops x 2.032 GHz (recipe unit counts, max clock)",
                     "alg_flops_per_step": d["jacobi32_flops"], "ms_per_step": d["jacobi32_ms"]}
     elif top == "jacobi_fp64":
