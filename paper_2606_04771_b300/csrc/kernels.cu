@@ -664,12 +664,36 @@ __device__ __forceinline__ void warp_pair_cols(C2* __restrict__ gi, C2* __restri
     }
   }
   if (vi) {
+    if constexpr (R > 0 && sizeof(S) == 4) {
+      // FP32 (the preconditioner, which accumulates V): q <= p <= 32 R, so every load of
+      // the two V columns is issued before the rotation (one memory latency instead of
+      // one per four rows; the FP64 instances keep the loop for their register budget)
+      C2 va[RR], vb[RR];
+#pragma unroll
+      for (int k = 0; k < RR; ++k) {
+        const int r = lane + 32 * k;
+        if (r < q) {
+          va[k] = vi[r];
+          vb[k] = vj[r];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < RR; ++k) {
+        const int r = lane + 32 * k;
+        if (r < q) {
+          rot2(va[k], vb[k], cs, sn, ex, ey);
+          vi[r] = va[k];
+          vj[r] = vb[k];
+        }
+      }
+    } else {
 #pragma unroll 4
-    for (int r = lane; r < q; r += 32) {
-      C2 a = vi[r], b = vj[r];
-      rot2(a, b, cs, sn, ex, ey);
-      vi[r] = a;
-      vj[r] = b;
+      for (int r = lane; r < q; r += 32) {
+        C2 a = vi[r], b = vj[r];
+        rot2(a, b, cs, sn, ex, ey);
+        vi[r] = a;
+        vj[r] = b;
+      }
     }
   }
   if (lane == 0 && ac > tol_flag * sqrt(sa * sb) && ac > abs_flag) atomicOr(flag, 1);
