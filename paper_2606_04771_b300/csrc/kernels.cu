@@ -603,7 +603,9 @@ __device__ __forceinline__ void warp_pair_cols(C2* __restrict__ gi, C2* __restri
   const int lane = threadIdx.x & 31;
   S sa = 0, sb = 0, cx = 0, cy = 0;
   constexpr int RR = R > 0 ? R : 1;
+  constexpr bool kPrefetchV = R > 0 && sizeof(S) == 4;
   C2 x[RR], y[RR];
+  C2 va[kPrefetchV ? RR : 1], vb[kPrefetchV ? RR : 1];
   if (R > 0) {
 #pragma unroll
     for (int k = 0; k < RR; ++k) {
@@ -613,6 +615,21 @@ __device__ __forceinline__ void warp_pair_cols(C2* __restrict__ gi, C2* __restri
         y[k] = gj[r];
       } else {
         x[k].x = x[k].y = y[k].x = y[k].y = S(0);
+      }
+    }
+    if constexpr (kPrefetchV) {
+      // FP32 (the preconditioner, which accumulates V): q <= p <= 32 R.  The two V
+      // columns are loaded together with G, so their latency overlaps G's instead of
+      // following the rotation decision; unused when the pair does not rotate.
+      if (vi) {
+#pragma unroll
+        for (int k = 0; k < RR; ++k) {
+          const int r = lane + 32 * k;
+          if (r < q) {
+            va[k] = vi[r];
+            vb[k] = vj[r];
+          }
+        }
       }
     }
 #pragma unroll
@@ -664,19 +681,8 @@ __device__ __forceinline__ void warp_pair_cols(C2* __restrict__ gi, C2* __restri
     }
   }
   if (vi) {
-    if constexpr (R > 0 && sizeof(S) == 4) {
-      // FP32 (the preconditioner, which accumulates V): q <= p <= 32 R, so every load of
-      // the two V columns is issued before the rotation (one memory latency instead of
-      // one per four rows; the FP64 instances keep the loop for their register budget)
-      C2 va[RR], vb[RR];
-#pragma unroll
-      for (int k = 0; k < RR; ++k) {
-        const int r = lane + 32 * k;
-        if (r < q) {
-          va[k] = vi[r];
-          vb[k] = vj[r];
-        }
-      }
+    if constexpr (kPrefetchV) {  // V rows loaded above (the FP64 instances keep the
+                                 // loop below for their register budget)
 #pragma unroll
       for (int k = 0; k < RR; ++k) {
         const int r = lane + 32 * k;
