@@ -369,7 +369,7 @@ def run_engine(args):
         "clocks": clk.summary(),
     }
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(budget_s=args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(budget_s=args.cpu_seconds, single_thread_s=args.cpu_seconds / 4)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -394,28 +394,54 @@ def oracle_problem(seed):
     return tab, lb, rb, keys, th, lk, Lb, rk, Rb
 
 
-def cpu_baseline(budget_s=20.0, seed=synth.SEED_BOND):
-    """Oracle timed on the host cores on a bounded sample of output blocks."""
+def _blas_threads():
+    """Threads of the BLAS pool numpy uses (what the oracle's block products run on)."""
+    try:
+        import threadpoolctl
+
+        n = [p["num_threads"] for p in threadpoolctl.threadpool_info() if p.get("user_api") == "blas"]
+        return max(n) if n else 1
+    except Exception:
+        return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def cpu_baseline(budget_s=20.0, seed=synth.SEED_BOND, single_thread_s=None):
+    """Oracle timed on the host cores on a bounded sample of output blocks; with
+    single_thread_s, also on one BLAS thread for that many seconds."""
     from oracle import blockwise, heff
 
     tab, lb, rb, keys, th, lk, Lb, rk, Rb = oracle_problem(seed)
     W = heff.shiba_mpo_tensor(1.0, 4.0)
     order = synth.rng(seed + 99).permutation(len(keys))
-    t0 = time.perf_counter()
-    flops, done = 0, 0
-    for i in order:
-        _, f = blockwise.heff2_u1_blocks(lb, rb, keys, th, lk, Lb, rk, Rb, W, [keys[i]])
-        flops += f
-        done += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
-    dt = time.perf_counter() - t0
     total_u1 = sum(1 for _ in keys)
+
+    def timed(budget):
+        t0 = time.perf_counter()
+        flops, done = 0, 0
+        for i in order:
+            _, f = blockwise.heff2_u1_blocks(lb, rb, keys, th, lk, Lb, rk, Rb, W, [keys[i]])
+            flops += f
+            done += 1
+            if time.perf_counter() - t0 > budget:
+                break
+        return flops, done, time.perf_counter() - t0
+
+    flops, done, dt = timed(budget_s)
     rate = flops / dt / 1e12  # TFLOP/s of U(1)xU(1) algorithmic work
-    return {"value": rate, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)),
-            "kind": "oracle",
-            "sample": f"{done} of {total_u1} U(1)xU(1) output blocks of the chi=4096 bond "
-                      f"({flops / 1e9:.1f} GFLOP of U(1)xU(1) block products in {dt:.1f} s, numpy/OpenBLAS FP64)"}
+    out = {"value": rate, "unit": UNIT, "cores": _blas_threads(), "kind": "oracle",
+           "sample": f"{done} of {total_u1} U(1)xU(1) output blocks of the chi=4096 bond "
+                     f"({flops / 1e9:.1f} GFLOP of U(1)xU(1) block products in {dt:.1f} s, numpy/OpenBLAS FP64)"}
+    if single_thread_s:
+        try:
+            import threadpoolctl
+
+            with threadpoolctl.threadpool_limits(limits=1, user_api="blas"):
+                f1, d1, t1 = timed(single_thread_s)
+            out["single_thread"] = {"value": f1 / t1 / 1e12, "unit": UNIT, "cores": 1,
+                                    "sample": f"{d1} output blocks ({f1 / 1e9:.1f} GFLOP in {t1:.1f} s)"}
+        except Exception as e:  # the all-cores figure stands on its own
+            out["single_thread"] = {"unavailable": str(e)}
+    return out
 
 
 def run_reference(args):
