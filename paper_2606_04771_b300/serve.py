@@ -91,8 +91,11 @@ class QuenchServer:
         return STATES[st.value]
 
     def info(self, rid):
+        """Timings, bond dimension, device bytes and status of a request, in any state."""
         v = np.zeros(10)
-        lib().tdvp_server_result(self.h, rid, None, None, None, None, v.ctypes.data, 10)
+        rc = lib().tdvp_server_result(self.h, rid, None, None, None, None, v.ctypes.data, 10)
+        if rc == -1:  # unknown id (other codes are the request's own state or error)
+            check(rc)
         keys = ["energy", "chi", "steps", "heff_flops", "t_submit", "t_admit", "t_done", "device_bytes_peak",
                 "footprint", "status"]
         return dict(zip(keys, v.tolist()))

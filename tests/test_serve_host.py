@@ -37,6 +37,8 @@ def test_invalid_arguments_are_rejected():
         assert lib().tdvp_server_submit(s.h, C.byref(r), C.byref(i)) == -1
         with pytest.raises(TdvpError, match="EINVAL"):
             s.poll(12345)
+        with pytest.raises(TdvpError, match="EINVAL"):
+            s.info(12345)
 
 
 def test_queue_pause_cancel_and_timeouts():
