@@ -56,7 +56,8 @@ enum {
   TDVP_EINTERNAL = -5,/* inconsistent internal bookkeeping */
   TDVP_ECUDA = -6,    /* a CUDA runtime call failed (including "no device") */
   TDVP_ETIMEOUT = -7, /* a bounded device wait gave up (or tdvp_server_wait ran out) */
-  TDVP_ECANCELED = -8 /* a served request was cancelled */
+  TDVP_ECANCELED = -8,/* a served request was cancelled */
+  TDVP_EIO = -9       /* a checkpoint file could not be opened, written or renamed */
 };
 
 typedef struct {
@@ -408,6 +409,25 @@ int tdvp_server_stats(tdvp_server* s, double* out, int n);
 /* Cancel the queued requests, let the running ones stop at their next step
  * boundary, join the workers and free the server.  NULL is accepted. */
 int tdvp_server_destroy(tdvp_server* s);
+
+/* ---- checkpoint / resume --------------------------------------------------
+ * tdvp_save writes a chain context's state to `path`: the bond sector tables,
+ * the site tensors (complex128), the orthogonality centre and the adaptive
+ * switch's state, with the caller's time t.  It writes `path`.part and renames
+ * it, so an interrupted save leaves any older file intact.  tdvp_load creates a
+ * context from such a file (opts as in tdvp_create: the precision and stream of
+ * the resumed run) and rebuilds the environments from the sites with the same
+ * kernels in the same order, so an FP64 run resumed from a checkpoint repeats
+ * the uninterrupted run bit for bit; *t (nullable) receives the stored time.
+ * The file is read and checked completely before any device work.  Format
+ * (little-endian): "TDVPCKP1"; int32 version (1), L, su2, centre, cap_hit,
+ * saturated; float64 J, U, t; per bond k = 0..L an int32 count and count int32
+ * triples (n, t, d); per site an int64 element count and the elements;
+ * "TDVPEND1".  Errors: TDVP_EINVAL (NULL argument, not a checkpoint, truncated or
+ * inconsistent file), TDVP_ESTATE (a bond-problem context), TDVP_EIO (file
+ * could not be opened, written or renamed), TDVP_ENOMEM, TDVP_ECUDA. */
+int tdvp_save(tdvp_ctx* ctx, const char* path, double t);
+int tdvp_load(const char* path, const tdvp_opts* opts, tdvp_ctx** out, double* t);
 
 /* Destroy a context and free its device memory.  NULL is accepted. */
 int tdvp_destroy(tdvp_ctx* ctx);

@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import struct
 
 import numpy as np
 
@@ -17,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libtdvp.so")
 SYM = {"u1u1": 0, "u1su2": 1, "su2": 1}
 PREC = {"fp64": 0, "3xtf32": 1, "bf16x4": 2}
 ERRORS = {0: "ok", -1: "EINVAL", -2: "ESTATE", -3: "ENOMEM", -4: "ENUMERIC", -5: "EINTERNAL", -6: "ECUDA",
-          -7: "ETIMEOUT", -8: "ECANCELED"}
+          -7: "ETIMEOUT", -8: "ECANCELED", -9: "EIO"}
 MODE = {"two": 0, "one": 1, "adaptive": 2}
 
 
@@ -76,6 +77,8 @@ def lib():
             "tdvp_launch_count": (C.c_int, [P(C.c_longlong)]),
             "tdvp_selftest_wait": (C.c_int, [C.c_uint, vp]),
             "tdvp_destroy": (C.c_int, [vp]),
+            "tdvp_save": (C.c_int, [vp, C.c_char_p, C.c_double]),
+            "tdvp_load": (C.c_int, [C.c_char_p, P(Opts), P(vp), P(C.c_double)]),
             "tdvp_server_create": (C.c_int, [C.c_double, C.c_int, P(Opts), P(vp)]),
             "tdvp_server_footprint": (C.c_int, [P(RequestC), C.c_int, P(C.c_double)]),
             "tdvp_server_submit": (C.c_int, [vp, P(RequestC), P(C.c_longlong)]),
@@ -238,6 +241,24 @@ class Chain(_Ctx):
         else:
             check(lib().tdvp_create_random(L, J, U, SYM[symmetry], int(random_chi), int(seed), int(center),
                                            C.byref(o), C.byref(self.h)))
+
+    def save(self, path, t=0.0):
+        """Checkpoint the chain (bond tables, site tensors, centre, adaptive state) and t."""
+        check(lib().tdvp_save(self.h, os.fsencode(path), float(t)))
+
+    @classmethod
+    def load(cls, path, **opts):
+        """A chain resumed from a checkpoint; returns (chain, t).  opts as for Chain
+        (precision, krylov_max, krylov_tol, stream, device)."""
+        ch = cls.__new__(cls)
+        _Ctx.__init__(ch)
+        o = make_opts(**opts)
+        t = C.c_double()
+        check(lib().tdvp_load(os.fsencode(path), C.byref(o), C.byref(ch.h), C.byref(t)))
+        with open(path, "rb") as f:  # header: magic, int32 version, L, su2, ...
+            _, _, L, su2 = struct.unpack("<8s3i", f.read(20))
+        ch.L, ch.sym = L, ("su2" if su2 else "u1u1")
+        return ch, t.value
 
     def step(self, dt, chi_max, eps, mode="two"):
         """One time step; mode "two" (two-site), "one" (one-site, bond dimensions

@@ -159,6 +159,21 @@ int tdvp_bond_create(int symmetry, double J, double U, int nl, const int* left, 
   });
 }
 
+int tdvp_save(tdvp_ctx* ctx, const char* path, double t) {
+  if (!ctx || !path) return fail(TDVP_EINVAL, "NULL argument");
+  return guarded(ctx, [&] { ctx->eng->save(path, t); });
+}
+
+int tdvp_load(const char* path, const tdvp_opts* opts, tdvp_ctx** out, double* t) {
+  if (!out || !path) return fail(TDVP_EINVAL, "NULL argument");
+  *out = nullptr;
+  return create_ctx(out, [&] {
+    tdvp_opts d;
+    tdvp_opts_default(&d);
+    return tdvp::Engine::load(path, to_opts(opts ? opts : &d), t);
+  });
+}
+
 int tdvp_step(tdvp_ctx* ctx, double dt, long long chi_max, double eps_trunc) {
   if (!ctx) return fail(TDVP_EINVAL, "ctx is NULL");
   return guarded(ctx, [&] { ctx->eng->step(dt, chi_max, eps_trunc); });
@@ -505,6 +520,7 @@ const char* tdvp_strerror(int code) {
     case TDVP_ECUDA: return "CUDA error";
     case TDVP_ETIMEOUT: return "device wait timed out";
     case TDVP_ECANCELED: return "request cancelled";
+    case TDVP_EIO: return "checkpoint file error";
     default: return "unknown error";
   }
 }

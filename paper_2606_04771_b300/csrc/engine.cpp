@@ -10,9 +10,13 @@
 // MPO applied as an FP64-weighted linear combination of blocks in between.
 #include "engine.hpp"
 
+#include "../../include/tdvp.h"
+
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdint>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <functional>
@@ -500,25 +504,157 @@ Engine* Engine::random_state(int L, double J, double U, bool su2, long long chi_
     cp.launch(e->stream_);
     TDVP_CUDA(cudaStreamSynchronize(e->stream_));
   }
-  e->Lenv_.clear();
-  e->Renv_.clear();
-  e->Lenv_.resize(L + 1);
-  e->Renv_.resize(L + 1);
+  e->build_environments();
+  return e.release();
+}
+
+void Engine::build_environments() {
+  const int L = L_;
+  const Model& M = model_;
+  Lenv_.clear();
+  Renv_.clear();
+  Lenv_.resize(L + 1);
+  Renv_.resize(L + 1);
   std::vector<cplx> one(1, cplx{1.0, 0.0});
-  e->build_lenv_layout(e->Lenv_[0], e->bonds_[0], e->bonds_[0]);
-  e->alloc(e->Lenv_[0], true);
-  int bi = e->Lenv_[0].find(bkey(0, M.chB, 0));
-  TDVP_CUDA(cudaMemcpyAsync(e->Lenv_[0].ptr(bi), one.data(), sizeof(cplx), cudaMemcpyHostToDevice, e->stream_));
-  e->build_renv_layout(e->Renv_[L], e->bonds_[L], e->bonds_[L]);
-  e->alloc(e->Renv_[L], true);
-  bi = e->Renv_[L].find(bkey(0, M.chE, 0));
-  TDVP_CUDA(cudaMemcpyAsync(e->Renv_[L].ptr(bi), one.data(), sizeof(cplx), cudaMemcpyHostToDevice, e->stream_));
-  for (int k = L - 1; k >= center + 1; --k)
-    e->update_right_env(e->Renv_[k + 1], e->site_[k], e->Renv_[k], e->bonds_[k], e->bonds_[k + 1]);
-  for (int k = 0; k < center; ++k)
-    e->update_left_env(e->Lenv_[k], e->site_[k], e->Lenv_[k + 1], e->bonds_[k], e->bonds_[k + 1]);
-  TDVP_CUDA(cudaStreamSynchronize(e->stream_));
-  e->check_status();
+  build_lenv_layout(Lenv_[0], bonds_[0], bonds_[0]);
+  alloc(Lenv_[0], true);
+  int bi = Lenv_[0].find(bkey(0, M.chB, 0));
+  TDVP_CUDA(cudaMemcpyAsync(Lenv_[0].ptr(bi), one.data(), sizeof(cplx), cudaMemcpyHostToDevice, stream_));
+  build_renv_layout(Renv_[L], bonds_[L], bonds_[L]);
+  alloc(Renv_[L], true);
+  bi = Renv_[L].find(bkey(0, M.chE, 0));
+  TDVP_CUDA(cudaMemcpyAsync(Renv_[L].ptr(bi), one.data(), sizeof(cplx), cudaMemcpyHostToDevice, stream_));
+  for (int k = L - 1; k >= center_ + 1; --k)
+    update_right_env(Renv_[k + 1], site_[k], Renv_[k], bonds_[k], bonds_[k + 1]);
+  for (int k = 0; k < center_; ++k) update_left_env(Lenv_[k], site_[k], Lenv_[k + 1], bonds_[k], bonds_[k + 1]);
+  TDVP_CUDA(cudaStreamSynchronize(stream_));
+  check_status();
+}
+
+// ---------------------------------------------------------------------------
+// checkpoint / resume
+// ---------------------------------------------------------------------------
+// File (little-endian): "TDVPCKP1"; int32 version = 1, L, su2, centre, cap_hit,
+// saturated; float64 J, U, t; per bond k = 0..L: int32 count, then count x int32
+// (n, t, d); per site i = 0..L-1: int64 element count, then the site tensor's blocks
+// as complex128 in the engine's block order (which the bond tables determine);
+// "TDVPEND1".  The environments are not stored: they are rebuilt from the sites with
+// the same kernels in the same order as when they were made, so a resumed FP64 run
+// repeats the uninterrupted one bit for bit.
+namespace {
+const char kCkptHead[8] = {'T', 'D', 'V', 'P', 'C', 'K', 'P', '1'};
+const char kCkptTail[8] = {'T', 'D', 'V', 'P', 'E', 'N', 'D', '1'};
+
+struct CkptHeader {
+  int32_t version, L, su2, center, cap_hit, saturated;
+  double J, U, t;
+};
+
+void put(std::FILE* f, const void* p, size_t n, const std::string& path) {
+  if (n && std::fwrite(p, 1, n, f) != n) throw Error(TDVP_EIO, "checkpoint: write failed: " + path);
+}
+void get(std::FILE* f, void* p, size_t n, const std::string& path) {
+  if (n && std::fread(p, 1, n, f) != n) throw Error(TDVP_EINVAL, "checkpoint: truncated file: " + path);
+}
+struct FileCloser {
+  std::FILE* f;
+  ~FileCloser() {
+    if (f) std::fclose(f);
+  }
+};
+}  // namespace
+
+void Engine::save(const std::string& path, double t) {
+  if (bond_only_) throw Error(TDVP_ESTATE, "checkpoint: a bond-problem context has no chain");
+  const std::string tmp = path + ".part";
+  {
+    FileCloser fc{std::fopen(tmp.c_str(), "wb")};
+    if (!fc.f) throw Error(TDVP_EIO, "checkpoint: cannot open " + tmp);
+    CkptHeader h{1, L_, model_.su2 ? 1 : 0, center_, cap_hit_ ? 1 : 0, saturated_ ? 1 : 0, model_.J, model_.U, t};
+    put(fc.f, kCkptHead, 8, tmp);
+    put(fc.f, &h, sizeof(h), tmp);
+    for (int k = 0; k <= L_; ++k) {
+      const int32_t c = (int32_t)bonds_[k].s.size();
+      put(fc.f, &c, sizeof(c), tmp);
+      for (const Sector& x : bonds_[k].s) {
+        const int32_t v[3] = {x.n, x.t, x.d};
+        put(fc.f, v, sizeof(v), tmp);
+      }
+    }
+    std::vector<cplx> host;
+    for (int i = 0; i < L_; ++i) {
+      const int64_t n = site_[i].size;
+      host.resize((size_t)n);
+      if (n) {
+        TDVP_CUDA(cudaMemcpyAsync(host.data(), site_[i].data(), (size_t)n * sizeof(cplx), cudaMemcpyDeviceToHost,
+                                  stream_));
+        TDVP_CUDA(cudaStreamSynchronize(stream_));
+      }
+      put(fc.f, &n, sizeof(n), tmp);
+      put(fc.f, host.data(), (size_t)n * sizeof(cplx), tmp);
+    }
+    put(fc.f, kCkptTail, 8, tmp);
+    if (std::fflush(fc.f) != 0) throw Error(TDVP_EIO, "checkpoint: write failed: " + tmp);
+  }
+  if (std::rename(tmp.c_str(), path.c_str()) != 0) throw Error(TDVP_EIO, "checkpoint: cannot rename to " + path);
+}
+
+Engine* Engine::load(const std::string& path, const Opts& o, double* t) {
+  FileCloser fc{std::fopen(path.c_str(), "rb")};
+  if (!fc.f) throw Error(TDVP_EIO, "checkpoint: cannot open " + path);
+  char head[8];
+  get(fc.f, head, 8, path);
+  if (std::memcmp(head, kCkptHead, 8) != 0) throw Error(TDVP_EINVAL, "checkpoint: not a checkpoint file: " + path);
+  CkptHeader h;
+  get(fc.f, &h, sizeof(h), path);
+  if (h.version != 1 || h.L < 2 || h.L > 100000 || h.center < 0 || h.center >= h.L)
+    throw Error(TDVP_EINVAL, "checkpoint: bad header: " + path);
+  // read and check everything on the host before any device work
+  std::vector<BondSpace> bonds(h.L + 1);
+  for (int k = 0; k <= h.L; ++k) {
+    int32_t c = 0;
+    get(fc.f, &c, sizeof(c), path);
+    if (c < 1 || c > 1000000) throw Error(TDVP_EINVAL, "checkpoint: bad sector count: " + path);
+    for (int j = 0; j < c; ++j) {
+      int32_t v[3];
+      get(fc.f, v, sizeof(v), path);
+      if (v[2] < 1) throw Error(TDVP_EINVAL, "checkpoint: bad sector degeneracy: " + path);
+      bonds[k].s.push_back({v[0], v[1], v[2]});
+    }
+    bonds[k].build_index();
+    if (bonds[k].idx.size() != bonds[k].s.size()) throw Error(TDVP_EINVAL, "checkpoint: duplicate sector: " + path);
+  }
+  std::vector<std::vector<cplx>> sites(h.L);
+  for (int i = 0; i < h.L; ++i) {
+    int64_t n = 0;
+    get(fc.f, &n, sizeof(n), path);
+    if (n < 0 || n > (int64_t)1 << 36) throw Error(TDVP_EINVAL, "checkpoint: bad site size: " + path);
+    sites[i].resize((size_t)n);
+    get(fc.f, sites[i].data(), (size_t)n * sizeof(cplx), path);
+  }
+  char tail[8];
+  get(fc.f, tail, 8, path);
+  if (std::memcmp(tail, kCkptTail, 8) != 0) throw Error(TDVP_EINVAL, "checkpoint: bad trailer: " + path);
+
+  std::unique_ptr<Engine> e(new Engine());
+  e->L_ = h.L;
+  e->init_common(h.su2 != 0, h.J, h.U, o);
+  e->bonds_ = std::move(bonds);
+  e->site_.resize(h.L);
+  for (int i = 0; i < h.L; ++i) {
+    e->build_site_layout(e->site_[i], e->bonds_[i], e->bonds_[i + 1]);
+    if (e->site_[i].size != (long long)sites[i].size())
+      throw Error(TDVP_EINVAL, "checkpoint: site tensor does not match its bond tables: " + path);
+    e->alloc(e->site_[i], false);
+    if (!sites[i].empty())
+      TDVP_CUDA(cudaMemcpyAsync(e->site_[i].data(), sites[i].data(), sites[i].size() * sizeof(cplx),
+                                cudaMemcpyHostToDevice, e->stream_));
+  }
+  e->center_ = h.center;
+  e->cap_hit_ = h.cap_hit != 0;
+  e->saturated_ = h.saturated != 0;
+  e->build_environments();
+  if (t) *t = h.t;
   return e.release();
 }
 

@@ -216,6 +216,10 @@ class Engine {
   static Engine* product_state(int L, double J, double U, bool su2, const std::vector<int>& occ, const Opts& o);
   static Engine* bond_problem(bool su2, double J, double U, const std::vector<Sector>& left,
                               const std::vector<Sector>& right, const Opts& o);
+  // checkpoint: the chain's bond tables, site tensors, orthogonality centre and the
+  // adaptive-switch state, with the caller's time t; load rebuilds the environments
+  void save(const std::string& path, double t);
+  static Engine* load(const std::string& path, const Opts& o, double* t);
   bool bond_only() const { return bond_only_; }
   BTensor& theta_layout() { return theta_; }
   BTensor& left_env_bp() { return Lenv_[0]; }
@@ -242,6 +246,8 @@ class Engine {
   void build_renv_layout(BTensor& t, const BondSpace& ket, const BondSpace& bra) const;
   void alloc(BTensor& t, bool zero);
   void orthonormalize_rows(BTensor& T, const BondSpace& l, const BondSpace& r);
+  // boundary environments, then L_1..L_centre and R_{L-1}..R_{centre+1} from the sites
+  void build_environments();
   void orthonormalize_cols(BTensor& T, const BondSpace& l, const BondSpace& r);
 
   void plan_heff2(HeffPlan& p, const BTensor& Lenv, const BTensor& Renv, const BTensor& theta,
