@@ -4,6 +4,8 @@ with TDVP (Sec. S2.2) to a final time, one JSON line per time step.
     python -m paper_2606_04771_b300.quench --L 60 --U 4 --dt 0.05 --t 3 --chi 4096 \
         --eps 1e-9 --mode adaptive --precision bf16x4 --out run.npz
     python -m paper_2606_04771_b300.quench --L 31 --vacancy --symmetry u1u1 ...
+    python -m paper_2606_04771_b300.quench ... --checkpoint run.ckpt --checkpoint-every 20
+    python -m paper_2606_04771_b300.quench --resume run.ckpt --t 6 ...
 
 Every step prints t, the integrator used, the largest bond dimension (U(1)-equivalent
 and reduced), the largest discarded weight and Krylov dimension so far, and the
@@ -25,9 +27,19 @@ from ._lib import Chain, vacancy_occupations
 
 
 def run(L=60, J=1.0, U=4.0, dt=0.05, t_final=3.0, chi=4096, eps=1e-9, mode="adaptive", precision="bf16x4",
-        symmetry="su2", measure_every=10, entropy=True, out=None, stream=None, log=sys.stdout, vacancy=False):
-    ch = Chain(L, J, U, symmetry=symmetry, precision=precision, stream=stream,
-               occupations=vacancy_occupations(L) if vacancy else None)
+        symmetry="su2", measure_every=10, entropy=True, out=None, stream=None, log=sys.stdout, vacancy=False,
+        checkpoint=None, checkpoint_every=0, resume=None):
+    """checkpoint: file written every checkpoint_every steps (if > 0) and at the end;
+    resume: a checkpoint to continue from (its chain replaces L, J, U, symmetry and
+    the initial state; the run goes on from its stored time to t_final)."""
+    k0 = 0
+    if resume:
+        ch, t_start = Chain.load(resume, precision=precision, stream=stream)
+        L = ch.L
+        k0 = int(round(t_start / dt))
+    else:
+        ch = Chain(L, J, U, symmetry=symmetry, precision=precision, stream=stream,
+                   occupations=vacancy_occupations(L) if vacancy else None)
     nsteps = int(round(t_final / dt))
     rec = {"t": [], "n_up": [], "n_dn": [], "docc": [], "s_ent": [], "energy": []}
     t0 = time.perf_counter()
@@ -41,8 +53,8 @@ def run(L=60, J=1.0, U=4.0, dt=0.05, t_final=3.0, chi=4096, eps=1e-9, mode="adap
         rec["energy"].append(o["energy"])
         return o
 
-    measure(0.0)
-    for k in range(1, nsteps + 1):
+    measure(k0 * dt)
+    for k in range(k0 + 1, nsteps + 1):
         ts = time.perf_counter()
         used = ch.step(dt, chi, eps, mode=mode)
         sec = time.perf_counter() - ts
@@ -57,6 +69,9 @@ def run(L=60, J=1.0, U=4.0, dt=0.05, t_final=3.0, chi=4096, eps=1e-9, mode="adap
                          "docc_mean": float(np.mean(o["docc"]))})
             if entropy:
                 line["s_half"] = float(o["s_ent"][L // 2 - 1])
+        if checkpoint and ((checkpoint_every > 0 and k % checkpoint_every == 0) or k == nsteps):
+            ch.save(checkpoint, t=k * dt)
+            line["checkpoint"] = checkpoint
         if log is not None:
             print(json.dumps(line), file=log, flush=True)
     ch.close()
@@ -82,9 +97,12 @@ def main(argv=None):
     ap.add_argument("--entropy", action="store_true")
     ap.add_argument("--out", default=None)
     ap.add_argument("--vacancy", action="store_true", help="Neel state with the centre site empty (use u1u1)")
+    ap.add_argument("--checkpoint", default=None, help="checkpoint file, written at the end and every --checkpoint-every")
+    ap.add_argument("--checkpoint-every", type=int, default=0)
+    ap.add_argument("--resume", default=None, help="continue from this checkpoint to --t")
     a = ap.parse_args(argv)
     run(a.L, a.J, a.U, a.dt, a.t, a.chi, a.eps, a.mode, a.precision, a.symmetry, a.measure_every, a.entropy, a.out,
-        vacancy=a.vacancy)
+        vacancy=a.vacancy, checkpoint=a.checkpoint, checkpoint_every=a.checkpoint_every, resume=a.resume)
 
 
 if __name__ == "__main__":

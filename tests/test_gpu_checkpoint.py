@@ -51,3 +51,16 @@ def test_bond_problem_cannot_be_saved(tmp_path):
     bp = BondProblem([(3, 1, 2), (4, 0, 1)], [(5, 1, 2), (4, 0, 1)], symmetry="su2")
     assert lib().tdvp_save(bp.h, str(tmp_path / "x").encode(), 0.0) == -2
     bp.close()
+
+
+def test_quench_driver_resumes_from_its_checkpoint(tmp_path):
+    from paper_2606_04771_b300 import quench
+
+    ck = str(tmp_path / "q.ckpt")
+    kw = dict(L=8, U=4.0, dt=0.05, chi=64, eps=1e-10, mode="two", precision="fp64", measure_every=2, log=None)
+    full = quench.run(t_final=0.4, **kw)
+    quench.run(t_final=0.2, checkpoint=ck, **kw)
+    rest = quench.run(t_final=0.4, resume=ck, **kw)
+    assert rest["t"][0] == pytest.approx(0.2) and rest["t"][-1] == pytest.approx(0.4)
+    assert np.array_equal(rest["n_up"][-1], full["n_up"][-1])
+    assert np.array_equal(rest["s_ent"][-1], full["s_ent"][-1])
