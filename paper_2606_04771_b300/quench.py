@@ -8,10 +8,11 @@ with TDVP (Sec. S2.2) to a final time, one JSON line per time step.
     python -m paper_2606_04771_b300.quench --resume run.ckpt --t 6 ...
 
 Every step prints t, the integrator used, the largest bond dimension (U(1)-equivalent
-and reduced), the largest discarded weight and Krylov dimension so far, and the
-seconds of the step; every --measure-every steps (and at the end) it also measures
-n_i, S^z_i, docc_i, the energy and (with --entropy) every bond's entanglement
-entropy, and stores them in --out (numpy .npz: t, n_up, n_dn, docc, s_ent, energy).
+and reduced) and every bond's, the largest discarded weight and Krylov dimension so
+far, the seconds and H_eff TFLOP/s of the step and the device memory held.  Every
+--measure-every steps (and at the end) it also measures n_i, S^z_i, docc_i, the
+energy and (with --entropy) every bond's entanglement entropy, and stores them in
+--out (numpy .npz: t, n_up, n_dn, docc, s_ent, energy).
 All arithmetic runs in the CUDA library; this module only drives it.
 """
 from __future__ import annotations
@@ -54,6 +55,7 @@ def run(L=60, J=1.0, U=4.0, dt=0.05, t_final=3.0, chi=4096, eps=1e-9, mode="adap
         return o
 
     measure(k0 * dt)
+    flops0 = ch.stats()["heff_flops"]
     for k in range(k0 + 1, nsteps + 1):
         ts = time.perf_counter()
         used = ch.step(dt, chi, eps, mode=mode)
@@ -62,7 +64,9 @@ def run(L=60, J=1.0, U=4.0, dt=0.05, t_final=3.0, chi=4096, eps=1e-9, mode="adap
         st = ch.stats()
         line = {"step": k, "t": round(k * dt, 10), "mode": used, "chi": int(chis.max()), "chi_red": int(red.max()),
                 "max_discarded": st["max_discarded"], "max_krylov": int(st["max_krylov"]), "seconds": sec,
-                "elapsed": time.perf_counter() - t0}
+                "heff_tflops": (st["heff_flops"] - flops0) / sec / 1e12, "elapsed": time.perf_counter() - t0,
+                "device_gb": st["device_bytes"] / 1e9, "chi_bonds": chis.tolist()}
+        flops0 = st["heff_flops"]
         if k % measure_every == 0 or k == nsteps:
             o = measure(k * dt)
             line.update({"energy": o["energy"], "n_up_mid": float(o["n_up"][L // 2]),
