@@ -12,6 +12,8 @@
 
 #include "../../include/tdvp.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -24,6 +26,15 @@
 #include <tuple>
 
 namespace tdvp {
+
+// NVTX range for the duration of a scope (a no-op unless a profiler is attached):
+// tdvp_step, tdvp_step_one_site, bond_update, site_update1, krylov, split, env_update
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ---------------------------------------------------------------------------
 // device buffers and plan uploads
@@ -1251,6 +1262,7 @@ void Engine::plan_heff1(HeffPlan& p, const BTensor& Lenv, const BTensor& Renv, c
 
 void Engine::update_left_env(const BTensor& Lin, const BTensor& A, BTensor& Lout, const BondSpace& bl,
                              const BondSpace& br) {
+  NvtxRange nvtx_range("env_update");
   build_lenv_layout(Lout, br, br);
   alloc(Lout, false);
   HeffPlan p;
@@ -1304,6 +1316,7 @@ void Engine::update_left_env(const BTensor& Lin, const BTensor& A, BTensor& Lout
 
 void Engine::update_right_env(const BTensor& Rin, const BTensor& Bt, BTensor& Rout, const BondSpace& bl,
                               const BondSpace& br) {
+  NvtxRange nvtx_range("env_update");
   const Model& M = model_;
   build_renv_layout(Rout, bl, bl);
   alloc(Rout, false);
@@ -1476,6 +1489,7 @@ void Engine::krylov(HeffPlan& H, cplx* x, double tau, int* k, int* launches) {
 }
 
 int Engine::expm(HeffPlan& H, cplx* x, double tau) {
+  NvtxRange nvtx_range("krylov");
   const long long n = H.n;
   const int kmax = opt_.krylov_max;
   if (kcap_ < n) {
@@ -1534,6 +1548,7 @@ int Engine::expm(HeffPlan& H, cplx* x, double tau) {
 
 double Engine::split(BTensor& theta, const BondSpace& bl, const BondSpace& br, long long chi_max, double eps,
                      bool absorb_right, BondSpace& bm, BTensor& X, BTensor& Y, double* s_ent) {
+  NvtxRange nvtx_range("split");
   if (gemm_kind_ >= 0) {
     bool ok = false;
     double r = split_mixed(theta, bl, br, chi_max, eps, absorb_right, bm, X, Y, s_ent, ok);
@@ -1769,6 +1784,7 @@ double Engine::split(BTensor& theta, const BondSpace& bl, const BondSpace& br, l
 
 double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace& br, long long chi_max, double eps,
                            bool absorb_right, BondSpace& bm, BTensor& X, BTensor& Y, double* s_ent, bool& ok) {
+  NvtxRange nvtx_range("split");
   const Model& M = model_;
   ok = false;
   struct Grp {
@@ -2203,6 +2219,7 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
 // centre by +tau.  left_to_right: centre i -> i+1, otherwise i+1 -> i.
 void Engine::bond_update(int i, bool left_to_right, double tau, long long chi_max, double eps, bool backward,
                          double* s_ent) {
+  NvtxRange nvtx_range("bond_update");
   auto tp = std::chrono::steady_clock::now();
   auto mark = [&](int ph) {
     if (!profile_) return;
@@ -2255,6 +2272,7 @@ void Engine::bond_update(int i, bool left_to_right, double tau, long long chi_ma
 }
 
 void Engine::step(double dt, long long chi_max, double eps) {
+  NvtxRange nvtx_range("tdvp_step");
   if (bond_only_) throw Error(-2, "a bond problem has no chain to evolve");
   if (!(dt > 0) || chi_max < 1 || !(eps >= 0)) throw Error(-1, "invalid step arguments");
   if (center_ != 0) throw Error(-2, "a full time step starts with the orthogonality centre on site 0");
@@ -2614,6 +2632,7 @@ void Engine::absorb(const BTensor& C, BTensor& M, bool from_left) {
 // shift) the gauge shift towards the sweep direction, the environment update, the
 // backward evolution of the bond matrix by tau and its absorption into the next site
 void Engine::site_update1(int i, bool left_to_right, double tau, bool shift) {
+  NvtxRange nvtx_range("site_update1");
   auto tp = std::chrono::steady_clock::now();
   auto mark = [&](int ph) {
     if (!profile_) return;
@@ -2659,6 +2678,7 @@ void Engine::site_update1(int i, bool left_to_right, double tau, bool shift) {
 }
 
 void Engine::step1(double dt) {
+  NvtxRange nvtx_range("tdvp_step_one_site");
   if (bond_only_) throw Error(-2, "a bond problem has no chain to evolve");
   if (!(dt > 0)) throw Error(-1, "invalid step arguments");
   if (center_ != 0) throw Error(-2, "a full time step starts with the orthogonality centre on site 0");
