@@ -42,3 +42,20 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(cname, "size")] == C.sizeof(cls), cname
         for f in fields:
             assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
+
+
+def test_binding_argument_counts_match_the_prototypes():
+    import re
+
+    from paper_2606_04771_b300._lib import lib
+
+    text = open(os.path.join(ROOT, "include", "tdvp.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    protos = re.findall(r"\b(?:int|void|const char\s*\*)\s+(tdvp_\w+)\s*\(([^)]*)\)\s*;", text)
+    assert len(protos) > 30
+    L = lib()
+    for name, args in protos:
+        args = args.strip()
+        n = 0 if args in ("", "void") else args.count(",") + 1
+        f = getattr(L, name)
+        assert f.argtypes is not None and len(f.argtypes) == n, (name, n, f.argtypes)
