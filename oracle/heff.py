@@ -81,11 +81,13 @@ def shiba_mpo_tensor(J: float, U: float) -> np.ndarray:
 
 
 def heff2_dense(Lenv, W1, W2, Renv, theta):
-    """The two-site definition as one plain einsum (no contraction-order optimisation)."""
-    X = np.einsum("xwa,asqb->xwsqb", Lenv, theta)
-    X = np.einsum("xwsqb,wuts->xutqb", X, W1)
-    X = np.einsum("xutqb,uvrq->xvtrb", X, W2)
-    return np.einsum("xvtrb,bvy->xtry", X, Renv)
+    """The two-site definition as four pairwise contractions in the stated order
+    (L, then W1, then W2, then R); each pairwise contraction is handed to BLAS
+    (``optimize=True`` only routes a two-operand einsum through tensordot)."""
+    X = np.einsum("xwa,asqb->xwsqb", Lenv, theta, optimize=True)
+    X = np.einsum("xwsqb,wuts->xutqb", X, W1, optimize=True)
+    X = np.einsum("xutqb,uvrq->xvtrb", X, W2, optimize=True)
+    return np.einsum("xvtrb,bvy->xtry", X, Renv, optimize=True)
 
 
 def heff1_dense(Lenv, W, Renv, M):

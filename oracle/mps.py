@@ -27,6 +27,8 @@ from __future__ import annotations
 
 import numpy as np
 
+from . import truncation
+
 D = 4  # local dimension
 
 
@@ -267,11 +269,18 @@ def truncation_count(s: np.ndarray, chi_max: int, eps: float) -> int:
     return max(1, min(keep, chi_max))
 
 
-def split_svd(theta, chi_max, eps, absorb):
-    """theta[a,s1,s2,b] -> (X[a,s1,c], Y[c,s2,b]); absorb = 'right' puts S into Y, 'left' into X."""
+def split_svd(theta, chi_max, eps, absorb, degeneracy=0.0):
+    """theta[a,s1,s2,b] -> (X[a,s1,c], Y[c,s2,b]); absorb = 'right' puts S into Y, 'left' into X.
+
+    degeneracy > 0: the cut never separates singular values whose squares agree to
+    that relative tolerance (degenerate symmetry multiplets are kept or dropped
+    together, ``truncation.select_multiplets``)."""
     a, d1, d2, b = theta.shape
     U, s, Vh = np.linalg.svd(theta.reshape(a * d1, d2 * b), full_matrices=False)
-    n = truncation_count(s, chi_max, eps)
+    if degeneracy > 0.0:
+        n = truncation.dense_keep_count(s, chi_max, eps, degeneracy)
+    else:
+        n = truncation_count(s, chi_max, eps)
     discarded = float(np.sum(s[n:] ** 2))
     U, s, Vh = U[:, :n], s[:n], Vh[:n]
     s = s / np.linalg.norm(s)
@@ -289,8 +298,9 @@ def split_svd(theta, chi_max, eps, absorb):
 class DenseTDVP:
     """Two-site TDVP on a dense MPS; the orthogonality centre rests on site 0."""
 
-    def __init__(self, L, J, U, kmax=20, krylov_tol=1e-12, occ=None):
+    def __init__(self, L, J, U, kmax=20, krylov_tol=1e-12, occ=None, degeneracy=0.0):
         self.L, self.J, self.U = L, J, U
+        self.degeneracy = degeneracy  # > 0: degenerate singular values are cut together
         self.W = mpo_tensor(J, U)
         self.kmax, self.tol = kmax, krylov_tol
         # product state (Neel by default): every tensor is both left- and right-canonical
@@ -320,7 +330,7 @@ class DenseTDVP:
         theta = np.einsum("asc,ctb->astb", mps[i], mps[i + 1])
         Le, Re = self.Lenv[i], self.R[i + 2]
         theta = self._expm(lambda x: heff2(Le, W, W, Re, x), theta, tau)
-        A, M, disc, s = split_svd(theta, chi_max, eps, "right")
+        A, M, disc, s = split_svd(theta, chi_max, eps, "right", self.degeneracy)
         self.max_discarded = max(self.max_discarded, disc)
         self.last_s = s
         mps[i], mps[i + 1] = A, M
@@ -335,7 +345,7 @@ class DenseTDVP:
         theta = np.einsum("asc,ctb->astb", mps[i], mps[i + 1])
         Le, Re = self.Lenv[i], self.R[i + 2]
         theta = self._expm(lambda x: heff2(Le, W, W, Re, x), theta, tau)
-        M, B, disc, s = split_svd(theta, chi_max, eps, "left")
+        M, B, disc, s = split_svd(theta, chi_max, eps, "left", self.degeneracy)
         self.max_discarded = max(self.max_discarded, disc)
         self.last_s = s
         mps[i], mps[i + 1] = M, B
