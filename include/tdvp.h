@@ -68,6 +68,10 @@ typedef struct {
   int timeout_ms;    /* reserved for bounded device waits; 0 = default */
   void* cuda_stream; /* cudaStream_t to run on, or NULL for an engine-owned stream */
   int device;        /* CUDA device ordinal, or -1 for the current device */
+  double trunc_degeneracy; /* truncation (Sec. S2.4): the cut never separates two multiplets
+                              whose per-state weights s^2 agree to this relative tolerance
+                              (degenerate multiplets are kept or dropped together; see
+                              tdvp_truncate); 0 = off; default 1e-8 */
 } tdvp_opts;
 
 /* Environment: when every sector of a split has at most 32 columns and a working
@@ -202,7 +206,11 @@ int tdvp_bond_dims(tdvp_ctx* ctx, long long* chi, long long* chi_red);
  * P Q^2 over those sectors and out[27] the same sum over the sectors whose
  * complex64 copy fits in 192 KiB.  out[28] Jacobi calls of the splits and
  * out[29] those that ran CTA-resident, out[30] those that ran in thread-block
- * clusters.  n = length of out (at most 31). */
+ * clusters.  out[31] milliseconds of the environment updates of the two-site
+ * bond updates (CUDA events around each update) and out[32] their algorithmic
+ * bytes (every operand block read once and every result block written once, over
+ * the block-GEMM and MPO linear-combination stages).  n = length of out (at most
+ * 33). */
 int tdvp_stats(tdvp_ctx* ctx, double* out, int n);
 
 /* ---- single-bond problems (the effective-Hamiltonian benchmark) ------------
@@ -281,6 +289,38 @@ int tdvp_heff_profile(tdvp_ctx* ctx, int iters, double* ms, long long* flops, lo
  * Errors: TDVP_EINVAL (p<1, q<1, NULL), TDVP_ENUMERIC (no convergence),
  * TDVP_ENOMEM, TDVP_ECUDA. */
 int tdvp_svd(int p, int q, const double* a, double* s, double* u, double* vh, int on_device, void* stream);
+
+/* The truncation's multiplet selection on its own (Sec. S2.4, Sec. S2.1): the
+ * step that tdvp_step runs after every two-site SVD, exposed so that callers can
+ * check it against a restatement of the rule.  Sector k (k = 0..nsec-1) holds
+ * r[k] >= 0 reduced singular values in descending order, stored back to back in
+ * sv (sector 0 first, sum r[k] >= 1 values), each the value of one multiplet of
+ * mult[k] = 2S+1 states (1 without SU(2)), normalised so that sv^2 is the weight
+ * of the whole multiplet (mult[k] s^2 for the singular value s of each of its
+ * states).  The rule:
+ *   - order all multiplets by the per-state weight sv^2 / mult, descending; ties
+ *     go to the lower sector index, then the lower index within the sector;
+ *   - K_eps = the smallest K >= 1 such that the weights of the multiplets ranked
+ *     K, K+1, ... sum to at most eps times the total weight (whole multiplets
+ *     are kept or dropped);
+ *   - K_chi = the largest K >= 1 whose first K multiplets hold at most chi_max
+ *     states (sum of mult), or 1 if the first alone holds more;
+ *   - the first K = min(K_eps, K_chi) ranked multiplets are kept;
+ *   - with degeneracy > 0, a head may not end between two ranked multiplets whose
+ *     per-state weights a >= b satisfy a - b <= degeneracy * a: K_eps and K_chi
+ *     are taken over the allowed heads only (K = all multiplets is always
+ *     allowed), and when no allowed head fits under the cap, K_chi is the first
+ *     allowed head (tdvp_step uses tdvp_opts.trunc_degeneracy here).
+ * kept[k] receives the number of sector k's values kept (always a prefix of the
+ * sector).  stats (nullable, 6 doubles): total weight, discarded weight,
+ * 1/sqrt(kept weight) (the renormalisation factor of the kept values), K, the
+ * states kept (sum of mult), and 1.0 when K_chi < K_eps (the cap set K) else 0.
+ * Host pointers; NaN or negative values rank last with weight 0.  stream is a
+ * cudaStream_t or NULL; the call returns when the result is on the host.
+ * Errors: TDVP_EINVAL (nsec < 1, NULL, r[k] < 0, mult[k] < 1, no values, eps < 0,
+ * chi_max < 1, degeneracy < 0), TDVP_ENOMEM, TDVP_ECUDA. */
+int tdvp_truncate(int nsec, const int* r, const int* mult, const double* sv, double eps, long long chi_max,
+                  double degeneracy, int* kept, double* stats, void* stream);
 
 /* Largest p or q accepted by tdvp_svd_noalloc. */
 #define TDVP_SVD_NOALLOC_MAX 512

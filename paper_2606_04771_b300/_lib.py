@@ -30,7 +30,8 @@ class TdvpError(RuntimeError):
 
 class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("krylov_max", C.c_int), ("krylov_tol", C.c_double),
-                ("timeout_ms", C.c_int), ("cuda_stream", C.c_void_p), ("device", C.c_int)]
+                ("timeout_ms", C.c_int), ("cuda_stream", C.c_void_p), ("device", C.c_int),
+                ("trunc_degeneracy", C.c_double)]
 
 
 class RequestC(C.Structure):
@@ -74,6 +75,7 @@ def lib():
             "tdvp_heff_profile": (C.c_int, [vp, C.c_int, vp, vp, vp]),
             "tdvp_svd": (C.c_int, [C.c_int, C.c_int, vp, vp, vp, vp, C.c_int, vp]),
             "tdvp_svd_noalloc": (C.c_int, [C.c_int, C.c_int, vp, vp, vp, vp, vp]),
+            "tdvp_truncate": (C.c_int, [C.c_int, vp, vp, vp, C.c_double, C.c_longlong, C.c_double, vp, vp, vp]),
             "tdvp_launch_count": (C.c_int, [P(C.c_longlong)]),
             "tdvp_selftest_wait": (C.c_int, [C.c_uint, vp]),
             "tdvp_destroy": (C.c_int, [vp]),
@@ -105,9 +107,11 @@ def check(rc):
         raise TdvpError(rc, lib().tdvp_last_error().decode())
 
 
-def make_opts(precision="fp64", krylov_max=20, krylov_tol=1e-12, stream=None, device=-1):
+def make_opts(precision="fp64", krylov_max=20, krylov_tol=1e-12, stream=None, device=-1, trunc_degeneracy=None):
     o = Opts()
     lib().tdvp_opts_default(C.byref(o))
+    if trunc_degeneracy is not None:
+        o.trunc_degeneracy = float(trunc_degeneracy)
     o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
     o.krylov_max = krylov_max
     o.krylov_tol = krylov_tol
@@ -146,6 +150,24 @@ def svd(a, stream=None):
     s = torch.empty(r, dtype=torch.float64, device=a.device)
     check(lib().tdvp_svd(p, q, a.data_ptr(), s.data_ptr(), u.data_ptr(), vh.data_ptr(), 1, stream))
     return u, s, vh
+
+
+def truncate(values, mults, eps, chi_max, degeneracy=0.0, stream=None):
+    """The truncation's multiplet selection through tdvp_truncate.
+
+    values: one descending 1-D array of reduced singular values per sector (sv^2 is
+    the weight of a whole multiplet); mults: 2S+1 per sector.  Returns (kept per
+    sector, stats) with stats = (total weight, discarded weight, 1/sqrt(kept
+    weight), K, states kept, 1.0 when the chi cap set K)."""
+    nsec = len(values)
+    r = np.array([len(v) for v in values], dtype=np.int32)
+    m = np.ascontiguousarray(mults, dtype=np.int32)
+    sv = np.ascontiguousarray(np.concatenate([np.asarray(v, dtype=np.float64) for v in values]))
+    kept = np.zeros(nsec, dtype=np.int32)
+    stats = np.zeros(6)
+    check(lib().tdvp_truncate(nsec, r.ctypes.data, m.ctypes.data, sv.ctypes.data, float(eps), int(chi_max),
+                              float(degeneracy), kept.ctypes.data, stats.ctypes.data, stream))
+    return kept, stats
 
 
 def launch_count():
@@ -303,13 +325,13 @@ class Chain(_Ctx):
         return chi, red
 
     def stats(self):
-        v = np.zeros(31)
-        check(lib().tdvp_stats(self.h, v.ctypes.data, 31))
+        v = np.zeros(33)
+        check(lib().tdvp_stats(self.h, v.ctypes.data, 33))
         keys = ["seconds", "heff_flops", "env_flops", "matvecs", "max_krylov", "max_discarded", "chi_max_seen",
                 "t_theta", "t_plan", "t_krylov2", "t_split", "t_env", "t_krylov1", "steps", "splits", "sweeps64",
                 "sweeps32", "one_site_steps", "device_bytes", "device_bytes_peak", "jacobi32_ms", "jacobi32_flops",
                 "jacobi64_ms", "jacobi64_flops", "split_pmax", "split_qmax", "split_work", "split_work_small",
-                "jacobi_calls", "jacobi_resident_calls", "jacobi_cluster_calls"]
+                "jacobi_calls", "jacobi_resident_calls", "jacobi_cluster_calls", "env_ms", "env_bytes"]
         return dict(zip(keys, v.tolist()))
 
 

@@ -67,6 +67,7 @@ tdvp::Opts to_opts(const tdvp_opts* o) {
     r.timeout_ms = o->timeout_ms;
     r.stream = reinterpret_cast<cudaStream_t>(o->cuda_stream);
     r.device = o->device;
+    r.trunc_degen = o->trunc_degeneracy;
   }
   return r;
 }
@@ -105,6 +106,7 @@ void tdvp_opts_default(tdvp_opts* o) {
   o->timeout_ms = 0;
   o->cuda_stream = nullptr;
   o->device = -1;
+  o->trunc_degeneracy = 1e-8;
 }
 
 int tdvp_create(int L, double J, double U, int symmetry, const tdvp_opts* opts, tdvp_ctx** out) {
@@ -251,7 +253,7 @@ int tdvp_stats(tdvp_ctx* ctx, double* out, int n) {
   if (!ctx || !out) return fail(TDVP_EINVAL, "NULL argument");
   return guarded(ctx, [&] {
     const tdvp::StepStats& s = ctx->eng->stats();
-    double v[31] = {s.seconds, (double)s.heff_flops, (double)s.env_flops, (double)s.matvecs, (double)s.max_krylov,
+    double v[33] = {s.seconds, (double)s.heff_flops, (double)s.env_flops, (double)s.matvecs, (double)s.max_krylov,
                     s.max_discarded, (double)s.chi_max_seen, s.phase[0], s.phase[1], s.phase[2], s.phase[3],
                     s.phase[4], s.phase[5], (double)s.steps, (double)s.splits, (double)s.sweeps64,
                     (double)s.sweeps32, (double)s.one_site_steps, (double)ctx->acct.live.load(),
@@ -259,8 +261,8 @@ int tdvp_stats(tdvp_ctx* ctx, double* out, int n) {
                     (double)s.split_pmax, (double)s.split_qmax, s.split_work, s.split_work_small,
                     (double)(s.jacobi32.launches + s.jacobi64.launches),
                     (double)(s.jacobi32.resident + s.jacobi64.resident),
-                    (double)(s.jacobi32.cluster + s.jacobi64.cluster)};
-    for (int i = 0; i < n && i < 31; ++i) out[i] = v[i];
+                    (double)(s.jacobi32.cluster + s.jacobi64.cluster), s.env_ms, s.env_bytes};
+    for (int i = 0; i < n && i < 33; ++i) out[i] = v[i];
   });
 }
 
@@ -499,6 +501,47 @@ int tdvp_svd(int p, int q, const double* a, double* s, double* u, double* vh, in
     TDVP_CUDA(cudaStreamSynchronize(st));
     TDVP_CUDA(cudaGetLastError());
     if (status) throw tdvp::Error(TDVP_ENUMERIC, "Jacobi SVD did not converge");
+  });
+}
+
+int tdvp_truncate(int nsec, const int* r, const int* mult, const double* sv, double eps, long long chi_max,
+                  double degeneracy, int* kept, double* stats, void* stream) {
+  if (nsec < 1 || !r || !mult || !sv || !kept) return fail(TDVP_EINVAL, "tdvp_truncate: NULL argument or nsec < 1");
+  if (!(eps >= 0.0) || chi_max < 1 || !(degeneracy >= 0.0))
+    return fail(TDVP_EINVAL, "tdvp_truncate: eps < 0, chi_max < 1 or degeneracy < 0");
+  long long n = 0;
+  for (int k = 0; k < nsec; ++k) {
+    if (r[k] < 0 || mult[k] < 1) return fail(TDVP_EINVAL, "tdvp_truncate: r[k] < 0 or mult[k] < 1");
+    n += r[k];
+  }
+  if (n < 1 || n > (1LL << 30)) return fail(TDVP_EINVAL, "tdvp_truncate: total number of values out of range");
+  return guarded([&] {
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int ni = (int)n;
+    tdvp::DevBuf dsv(n * sizeof(double), st), dsec(nsec * sizeof(tdvp::TruncSector), st);
+    tdvp::DevBuf doffs(nsec * sizeof(int), st), downer(n * sizeof(int), st), dorder(n * sizeof(int), st);
+    tdvp::DevBuf dkept(nsec * sizeof(int), st), dstats(8 * sizeof(double), st), dvals(2 * n * sizeof(double), st);
+    std::vector<tdvp::TruncSector> secs(nsec);
+    std::vector<int> offs(nsec);
+    int o = 0;
+    for (int k = 0; k < nsec; ++k) {
+      offs[k] = o;
+      secs[k] = {dsv.as<double>() + o, r[k], mult[k]};
+      o += r[k];
+    }
+    TDVP_CUDA(cudaMemcpyAsync(dsv.p, sv, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    TDVP_CUDA(cudaMemcpyAsync(dsec.p, secs.data(), nsec * sizeof(tdvp::TruncSector), cudaMemcpyHostToDevice, st));
+    TDVP_CUDA(cudaMemcpyAsync(doffs.p, offs.data(), nsec * sizeof(int), cudaMemcpyHostToDevice, st));
+    tdvp::launch_truncate(dsec.as<tdvp::TruncSector>(), nsec, doffs.as<int>(), ni, eps, chi_max, degeneracy,
+                          downer.as<int>(),
+                          dorder.as<int>(), dkept.as<int>(), dstats.as<double>(), dvals.as<double>(), st);
+    double hs[6];
+    TDVP_CUDA(cudaMemcpyAsync(kept, dkept.p, nsec * sizeof(int), cudaMemcpyDeviceToHost, st));
+    TDVP_CUDA(cudaMemcpyAsync(hs, dstats.p, 6 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    TDVP_CUDA(cudaStreamSynchronize(st));
+    TDVP_CUDA(cudaGetLastError());
+    if (stats)
+      for (int i = 0; i < 6; ++i) stats[i] = hs[i];
   });
 }
 

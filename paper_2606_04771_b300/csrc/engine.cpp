@@ -292,6 +292,7 @@ void HeffPlan::apply(const cplx* in, cplx* out, cudaStream_t s) const {
 
 // a Jacobi driver's sweep count, or the CUDA error of a failed cooperative launch
 static int jacobi(int sweeps) {
+  if (sweeps == JACOBI_ENOMEM) throw Error(-3, "Jacobi work lists: device allocation failed");
   if (sweeps < 0) {
     cudaError_t e = cudaGetLastError();
     throw Error(-6, std::string("cooperative Jacobi launch failed: ") + cudaGetErrorString(e));
@@ -731,7 +732,7 @@ void Engine::orthonormalize_cols(BTensor& T, const BondSpace& l, const BondSpace
   gather.finalize(stream_);
   gather.launch(stream_);
   DevBuf dt = upload(tasks, stream_);
-  jacobi(run_jacobi_rounds(dt.as<SvdTask>(), tasks, 40, 1e-14, dstatus_, stream_));
+  jacobi(run_jacobi_rounds(dt.as<SvdTask>(), tasks, 40, 1e-14, dstatus_, stream_, 0.0, 0.0, nullptr, jscratch()));
   scatter.finalize(stream_);
   scatter.launch(stream_);
   TDVP_CUDA(cudaStreamSynchronize(stream_));
@@ -801,7 +802,7 @@ void Engine::orthonormalize_rows(BTensor& T, const BondSpace& l, const BondSpace
   gather.finalize(stream_);
   gather.launch(stream_);
   DevBuf dt = upload(tasks, stream_);
-  jacobi(run_jacobi_rounds(dt.as<SvdTask>(), tasks, 40, 1e-14, dstatus_, stream_));
+  jacobi(run_jacobi_rounds(dt.as<SvdTask>(), tasks, 40, 1e-14, dstatus_, stream_, 0.0, 0.0, nullptr, jscratch()));
   scatter.finalize(stream_);
   scatter.launch(stream_);
   TDVP_CUDA(cudaStreamSynchronize(stream_));
@@ -837,10 +838,27 @@ Engine::~Engine() {
   kh2_.reset();
   knrm_.reset();
   kstate_.reset();
+  jscratch_.reset();
   if (stream_) cudaStreamSynchronize(stream_);
+  for (cudaEvent_t& e : env_ev_)
+    if (e) cudaEventDestroy(e);
   if (pinned_) cudaFreeHost(pinned_);
   if (dstatus_) cudaFree(dstatus_);
   if (own_stream_) cudaStreamDestroy(stream_);
+}
+
+ScratchFn Engine::jscratch() {
+  return [this](size_t bytes) -> void* {
+    if (jscratch_.bytes < bytes) {
+      try {
+        jscratch_ = DevBuf(std::max(bytes, (size_t)64 << 10), stream_);
+      } catch (const Error&) {
+        cudaGetLastError();
+        return nullptr;
+      }
+    }
+    return jscratch_.p;
+  };
 }
 
 void Engine::check_status() {
@@ -1312,6 +1330,7 @@ void Engine::update_left_env(const BTensor& Lin, const BTensor& A, BTensor& Lout
   p.lc.launch(stream_);
   p.g3.launch(stream_, B);
   stats_.env_flops += p.g1.flops + p.g3.flops;
+  stats_.env_bytes += (double)(p.g1.bytes + p.lc.bytes + p.g3.bytes);
 }
 
 void Engine::update_right_env(const BTensor& Rin, const BTensor& Bt, BTensor& Rout, const BondSpace& bl,
@@ -1439,6 +1458,7 @@ void Engine::update_right_env(const BTensor& Rin, const BTensor& Bt, BTensor& Ro
   p.lc.launch(stream_);
   p.g3.launch(stream_, B);
   stats_.env_flops += p.g1.flops + p.g3.flops;
+  stats_.env_bytes += (double)(p.g1.bytes + p.lc.bytes + p.g3.bytes);
 }
 
 void Engine::form_theta(const BTensor& X, const BTensor& Y, BTensor& theta, const BondSpace& bl, const BondSpace& bm,
@@ -1651,15 +1671,17 @@ double Engine::split(BTensor& theta, const BondSpace& bl, const BondSpace& br, l
   }
   DevBuf dst = upload(st, stream_);
   stats_.sweeps64 +=
-      jacobi(run_jacobi_rounds(dst.as<SvdTask>(), st, 40, 1e-14, dstatus_, stream_, 0.0, 0.0, &stats_.jacobi64));
+      jacobi(run_jacobi_rounds(dst.as<SvdTask>(), st, 40, 1e-14, dstatus_, stream_, 0.0, 0.0, &stats_.jacobi64,
+                               jscratch()));
   stats_.splits += 1;
   // truncation
   DevBuf dts = upload(ts, stream_);
   DevBuf doffs = upload(soff, stream_);
   DevBuf downer(std::max(stot, 1) * sizeof(int), stream_), dorder(std::max(stot, 1) * sizeof(int), stream_);
   DevBuf dkept(std::max(ng, 1) * sizeof(int), stream_), dstats(8 * sizeof(double), stream_);
-  launch_truncate(dts.as<TruncSector>(), ng, doffs.as<int>(), stot, eps, chi_max, downer.as<int>(), dorder.as<int>(),
-                  dkept.as<int>(), dstats.as<double>(), stream_);
+  DevBuf dvals(2 * std::max(stot, 1) * sizeof(double), stream_);
+  launch_truncate(dts.as<TruncSector>(), ng, doffs.as<int>(), stot, eps, chi_max, opt_.trunc_degen, downer.as<int>(),
+                  dorder.as<int>(), dkept.as<int>(), dstats.as<double>(), dvals.as<double>(), stream_);
   std::vector<int> kept(ng);
   double hstats[8];
   TDVP_CUDA(cudaMemcpyAsync(kept.data(), dkept.p, ng * sizeof(int), cudaMemcpyDeviceToHost, stream_));
@@ -1894,7 +1916,7 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
   // FP32 stage: rotate while |g_i^H g_j| > 2e-5 |g_i||g_j|, at most 24 sweeps (it
   // need not converge: the FP64 stage finishes whatever is left)
   const int sw32 =
-      jacobi(run_jacobi_rounds32(dst32.as<Svd32Task>(), st32, 24, 2e-5f, 0.0f, stream_, &stats_.jacobi32));
+      jacobi(run_jacobi_rounds32(dst32.as<Svd32Task>(), st32, 24, 2e-5f, 0.0f, stream_, &stats_.jacobi32, jscratch()));
   ok = true;
   stats_.sweeps32 += sw32;
   stats_.splits += 1;
@@ -1937,12 +1959,14 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
   // smallest truncation threshold in use; on the L=60 quench the observables do not
   // move against tighter settings while the stage needs fewer sweeps)
   stats_.sweeps64 += jacobi(
-      run_jacobi_rounds(dst.as<SvdTask>(), st, 30, 1e-13, dstatus_, stream_, 1e-6, 1e-10, &stats_.jacobi64));
+      run_jacobi_rounds(dst.as<SvdTask>(), st, 30, 1e-13, dstatus_, stream_, 1e-6, 1e-10, &stats_.jacobi64,
+                        jscratch()));
   DevBuf dts = upload(ts, stream_), doffs = upload(soff, stream_);
   DevBuf downer(std::max(stot, 1) * sizeof(int), stream_), dorder(std::max(stot, 1) * sizeof(int), stream_);
   DevBuf dkept(std::max(ng, 1) * sizeof(int), stream_), dstats(8 * sizeof(double), stream_);
-  launch_truncate(dts.as<TruncSector>(), ng, doffs.as<int>(), stot, eps, chi_max, downer.as<int>(), dorder.as<int>(),
-                  dkept.as<int>(), dstats.as<double>(), stream_);
+  DevBuf dvals(2 * std::max(stot, 1) * sizeof(double), stream_);
+  launch_truncate(dts.as<TruncSector>(), ng, doffs.as<int>(), stot, eps, chi_max, opt_.trunc_degen, downer.as<int>(),
+                  dorder.as<int>(), dkept.as<int>(), dstats.as<double>(), dvals.as<double>(), stream_);
   std::vector<int> kept(ng);
   double hstats[8];
   TDVP_CUDA(cudaMemcpyAsync(kept.data(), dkept.p, ng * sizeof(int), cudaMemcpyDeviceToHost, stream_));
@@ -2246,8 +2270,14 @@ void Engine::bond_update(int i, bool left_to_right, double tau, long long chi_ma
   site_[i] = std::move(X);
   site_[i + 1] = std::move(Y);
   mark(3);
+  if (!env_ev_[0]) {
+    TDVP_CUDA(cudaEventCreate(&env_ev_[0]));
+    TDVP_CUDA(cudaEventCreate(&env_ev_[1]));
+  }
+  TDVP_CUDA(cudaEventRecord(env_ev_[0], stream_));
   if (left_to_right) {
     update_left_env(Lenv_[i], site_[i], Lenv_[i + 1], bonds_[i], bonds_[i + 1]);
+    TDVP_CUDA(cudaEventRecord(env_ev_[1], stream_));
     mark(4);
     center_ = i + 1;
     if (backward) {
@@ -2259,6 +2289,7 @@ void Engine::bond_update(int i, bool left_to_right, double tau, long long chi_ma
     }
   } else {
     update_right_env(Renv_[i + 2], site_[i + 1], Renv_[i + 1], bonds_[i + 1], bonds_[i + 2]);
+    TDVP_CUDA(cudaEventRecord(env_ev_[1], stream_));
     mark(4);
     center_ = i;
     if (backward) {
@@ -2269,6 +2300,11 @@ void Engine::bond_update(int i, bool left_to_right, double tau, long long chi_ma
       mark(5);
     }
   }
+  // device time of the environment update (the backward Krylov step has usually
+  // synchronised the stream already)
+  float ms = 0.f;
+  TDVP_CUDA(cudaEventSynchronize(env_ev_[1]));
+  if (cudaEventElapsedTime(&ms, env_ev_[0], env_ev_[1]) == cudaSuccess) stats_.env_ms += ms;
 }
 
 void Engine::step(double dt, long long chi_max, double eps) {
@@ -2877,7 +2913,7 @@ void Engine::measure(double* n_out, double* sz_out, double* docc_out, double* s_
         ts[b] = {dS.as<double>() + so[b], br.s[b].d, M.mult_dim(br.s[b].t)};
       }
       DevBuf dst = upload(st, stream_), dts2 = upload(ts, stream_);
-      jacobi(run_jacobi_rounds(dst.as<SvdTask>(), st, 40, 1e-14, dstatus_, stream_));
+      jacobi(run_jacobi_rounds(dst.as<SvdTask>(), st, 40, 1e-14, dstatus_, stream_, 0.0, 0.0, nullptr, jscratch()));
       launch_entropy(dts2.as<TruncSector>(), ns, dent.as<double>() + i, stream_);
       TDVP_CUDA(cudaStreamSynchronize(stream_));
     }

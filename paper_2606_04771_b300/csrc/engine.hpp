@@ -158,6 +158,7 @@ struct Opts {
   int timeout_ms = 0;
   cudaStream_t stream = nullptr;
   int device = -1;
+  double trunc_degen = 1e-8;  // degenerate multiplets are cut together (relative, per-state weight)
 };
 
 struct StepStats {
@@ -181,6 +182,10 @@ struct StepStats {
   // copy (P Q x 8 bytes) fits in 192 KiB of shared memory
   long long split_pmax = 0, split_qmax = 0;
   double split_work = 0, split_work_small = 0;
+  // environment updates of the two-site bond updates: device milliseconds (CUDA events
+  // around each update) and algorithmic bytes (every operand block read once, every
+  // result block written once, over the GEMM and linear-combination stages)
+  double env_ms = 0, env_bytes = 0;
 };
 
 class Engine {
@@ -299,6 +304,10 @@ class Engine {
   void* pinned_ = nullptr;
   StepStats stats_;
   int* dstatus_ = nullptr;
+  // device scratch of the Jacobi drivers' work lists, grown on demand (stream-ordered)
+  DevBuf jscratch_;
+  ScratchFn jscratch();
+  cudaEvent_t env_ev_[2] = {nullptr, nullptr};
   int gemm_kind_ = -1;  // block-GEMM precision of H_eff, environment updates and theta formation
 
   friend struct BondAccess;

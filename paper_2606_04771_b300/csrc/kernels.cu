@@ -15,6 +15,7 @@
 
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <type_traits>
 #include <vector>
 
@@ -1097,7 +1098,8 @@ static int cluster_size_for(const std::vector<Task>& h_tasks, size_t* smem) {
 
 template <class Task, class S, class C2>
 static int coop_run(const Task* d_tasks, const std::vector<Task>& h_tasks, int max_sweeps, S tol, S tol_flag,
-                    S abs_flag, int* nonconv, bool with_v, JacobiProfile* prof, cudaStream_t s) {
+                    S abs_flag, int* nonconv, bool with_v, JacobiProfile* prof, cudaStream_t s,
+                    const ScratchFn& scratch) {
   const int nt = (int)h_tasks.size();
   int pmax = 1;
   // All sectors run CTA-resident when every one of them fits: q <= RJ_QMAX columns
@@ -1166,23 +1168,39 @@ static int coop_run(const Task* d_tasks, const std::vector<Task>& h_tasks, int m
   std::vector<int> active;
   pair_schedule(h_tasks, resident, work, active);
   if (work.empty() && rid.empty()) return 1;
-  int2* d_work = nullptr;
-  int *d_active = nullptr, *flags = nullptr, *out = nullptr, *d_rid = nullptr;
+  // one device region for the work lists and the flags: [work | active | rid | flags],
+  // each part 16-byte aligned; flags: two sweep buffers [2 nt], out [2] (cooperative
+  // sweeps, non-convergence), per-task active sweeps of the cooperative kernel [nt],
+  // non-convergence of the resident sectors [1], sweeps of the resident sectors [nt]
+  auto up16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
+  const size_t b_work = up16(work.size() * sizeof(int2)), b_act = up16(active.size() * sizeof(int)),
+               b_rid = up16(rid.size() * sizeof(int)), b_flags = up16((4 * (size_t)nt + 3) * sizeof(int));
+  const size_t b_lists = b_work + b_act + b_rid;
+  char* region = nullptr;
+  bool owned = false;
+  if (scratch) {
+    region = static_cast<char*>(scratch(b_lists + b_flags));
+  } else if (cudaMallocAsync((void**)&region, b_lists + b_flags, s) == cudaSuccess) {
+    owned = true;
+  } else {
+    region = nullptr;
+  }
+  if (!region) {
+    cudaGetLastError();
+    return JACOBI_ENOMEM;
+  }
+  std::vector<char> host(b_lists, 0);
   if (!work.empty()) {
-    cudaMallocAsync(&d_work, work.size() * sizeof(int2), s);
-    cudaMallocAsync(&d_active, active.size() * sizeof(int), s);
-    cudaMemcpyAsync(d_work, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(d_active, active.data(), active.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+    std::memcpy(host.data(), work.data(), work.size() * sizeof(int2));
+    std::memcpy(host.data() + b_work, active.data(), active.size() * sizeof(int));
   }
-  if (!rid.empty()) {
-    cudaMallocAsync(&d_rid, rid.size() * sizeof(int), s);
-    cudaMemcpyAsync(d_rid, rid.data(), rid.size() * sizeof(int), cudaMemcpyHostToDevice, s);
-  }
-  // flags: two sweep buffers [2 nt], out [2] (cooperative sweeps, non-convergence),
-  // per-task active sweeps of the cooperative kernel [nt], non-convergence of the
-  // resident sectors [1], sweeps of the resident sectors [nt]
-  cudaMallocAsync(&flags, (4 * nt + 3) * sizeof(int), s);
-  out = flags + 2 * nt;
+  if (!rid.empty()) std::memcpy(host.data() + b_work + b_act, rid.data(), rid.size() * sizeof(int));
+  if (b_lists) cudaMemcpyAsync(region, host.data(), b_lists, cudaMemcpyHostToDevice, s);
+  int2* d_work = work.empty() ? nullptr : reinterpret_cast<int2*>(region);
+  int* d_active = work.empty() ? nullptr : reinterpret_cast<int*>(region + b_work);
+  int* d_rid = rid.empty() ? nullptr : reinterpret_cast<int*>(region + b_work + b_act);
+  int* flags = reinterpret_cast<int*>(region + b_lists);
+  int* out = flags + 2 * nt;
   int* tsw = out + 2;
   int* rnc = tsw + nt;
   int* rsw = rnc + 1;
@@ -1254,10 +1272,7 @@ static int coop_run(const Task* d_tasks, const std::vector<Task>& h_tasks, int m
     cudaEventDestroy(ev[0]);
     cudaEventDestroy(ev[1]);
   }
-  if (d_work) cudaFreeAsync(d_work, s);
-  if (d_active) cudaFreeAsync(d_active, s);
-  if (d_rid) cudaFreeAsync(d_rid, s);
-  cudaFreeAsync(flags, s);
+  if (owned) cudaFreeAsync(region, s);
   if (nonconv) *nonconv = nc;
   return rc == 0 ? sweeps : -1;
 }
@@ -1274,7 +1289,8 @@ static int coop_run(const Task* d_tasks, const std::vector<Task>& h_tasks, int m
 // unit-norm theta, so abs_flag is a weight).  Non-convergence within max_sweeps
 // sets *status to 1.
 int run_jacobi_rounds(const SvdTask* d_tasks, const std::vector<SvdTask>& h_tasks, int max_sweeps, double tol,
-                      int* status, cudaStream_t s, double tol_flag, double abs_flag, JacobiProfile* prof) {
+                      int* status, cudaStream_t s, double tol_flag, double abs_flag, JacobiProfile* prof,
+                      const ScratchFn& scratch) {
   const int nt = (int)h_tasks.size();
   if (nt == 0) return 0;
   if (!(tol_flag >= tol)) tol_flag = tol;
@@ -1285,7 +1301,9 @@ int run_jacobi_rounds(const SvdTask* d_tasks, const std::vector<SvdTask>& h_task
   int nonconv = 0;
   const bool with_v = h_tasks[0].v != nullptr;
   const int sweeps =
-      coop_run<SvdTask, double, cplx>(d_tasks, h_tasks, max_sweeps, tol, tol_flag, abs_flag, &nonconv, with_v, prof, s);
+      coop_run<SvdTask, double, cplx>(d_tasks, h_tasks, max_sweeps, tol, tol_flag, abs_flag, &nonconv, with_v, prof, s,
+                                      scratch);
+  if (sweeps == JACOBI_ENOMEM) return sweeps;
   if (sweeps > 0 && nonconv) {
     int one = 1;
     cudaMemcpyAsync(status, &one, sizeof(int), cudaMemcpyHostToDevice, s);  // reported by the caller's check
@@ -1308,13 +1326,13 @@ int run_jacobi_rounds(const SvdTask* d_tasks, const std::vector<SvdTask>& h_task
 // ---------------------------------------------------------------------------
 
 int run_jacobi_rounds32(const Svd32Task* d_tasks, const std::vector<Svd32Task>& h_tasks, int max_sweeps, float tol,
-                        float abs_flag, cudaStream_t s, JacobiProfile* prof) {
+                        float abs_flag, cudaStream_t s, JacobiProfile* prof, const ScratchFn& scratch) {
   const int nt = (int)h_tasks.size();
   if (nt == 0) return 0;
   note_launch();
   svd32_init_v_kernel<<<nt, 256, 0, s>>>(d_tasks);
   return coop_run<Svd32Task, float, float2>(d_tasks, h_tasks, max_sweeps, tol, 0.0f, abs_flag, nullptr, true, prof,
-                                            s);
+                                            s, scratch);
 }
 
 
@@ -1396,12 +1414,20 @@ void launch_jacobi_svd(const SvdTask* tasks, int ntasks, int max_q, int max_swee
 // ---------------------------------------------------------------------------
 
 // One CTA of TRUNC_THREADS threads.  Flat entry e of sector s is e = offs[s] + i.
-// 1. stage value, sector and multiplet size of every entry (NaN ranks last, weight 0);
-// 2. rank every entry (descending value, ties by flat index) against shared-memory
-//    tiles of the values, order[rank] = e;
+// A sector's values r are reduced singular values normalised so that r^2 is the
+// weight of the whole multiplet, (2S+1) s^2 with s the singular value of each of its
+// 2S+1 states (Sec. S2.1, S2.4); mult = 2S+1 (1 without SU(2)).
+// 1. stage value, sector and multiplet size of every entry (NaN ranks last, weight 0),
+//    and the per-state weight lambda = r^2 / mult, the ranking key;
+// 2. rank every entry (descending lambda, i.e. descending per-state singular value,
+//    ties by flat index = sector, then in-sector index) against shared-memory tiles
+//    of the keys, order[rank] = e;
 // 3. block scans over the sorted list: suffix sums of the weights s^2 (the tail
 //    rule) and prefix sums of the multiplet sizes (the chi cap);
-// 4. K = max(1, min(longest tail with weight <= eps * total, largest chi <= cap)),
+// 4. K = min(shortest head whose dropped tail weighs <= eps * total, longest head with
+//    at most chi_max states), both taken over the allowed heads (with degen > 0 a head
+//    may not end between two entries whose per-state weights agree to within degen,
+//    relative); if no allowed head fits under the cap the first allowed head is kept;
 //    kept[s] = number of the first K sorted entries that belong to sector s.
 constexpr int TRUNC_THREADS = 1024;
 constexpr int TRUNC_TILE = 2048;
@@ -1436,7 +1462,8 @@ __device__ T block_exclusive_scan(T v, T* sh, T& total) {
 
 __global__ void __launch_bounds__(TRUNC_THREADS) truncate_kernel(const TruncSector* __restrict__ secs, int nsec,
                                                                  const int* __restrict__ offs, int n, double eps,
-                                                                 long long chi_max, int* __restrict__ owner,
+                                                                 long long chi_max, double degen,
+                                                                 int* __restrict__ owner,
                                                                  int* __restrict__ order, int* __restrict__ kept,
                                                                  double* __restrict__ stats,
                                                                  double* __restrict__ vals) {
@@ -1445,8 +1472,10 @@ __global__ void __launch_bounds__(TRUNC_THREADS) truncate_kernel(const TruncSect
     const TruncSector t = secs[sct];
     for (int i = lane; i < t.r; i += 32) {
       double v = t.sv[i];
+      const bool ok = v == v && v >= 0.0;
       owner[offs[sct] + i] = sct;
-      vals[offs[sct] + i] = (v == v && v >= 0.0) ? v : -1.0;
+      vals[offs[sct] + i] = ok ? v : -1.0;
+      vals[n + offs[sct] + i] = ok ? v * v / (double)t.mult : -1.0;
     }
     if (lane == 0) kept[sct] = 0;
   }
@@ -1464,13 +1493,13 @@ __global__ void __launch_bounds__(TRUNC_THREADS) truncate_kernel(const TruncSect
 #pragma unroll
     for (int j = 0; j < TRUNC_PER; ++j) {
       int e = e0 + j * TRUNC_THREADS + tid;
-      mine[j] = e < n ? key(vals[e]) : 0ull;
+      mine[j] = e < n ? key(vals[n + e]) : 0ull;
       rank[j] = 0;
     }
     for (int f0 = 0; f0 < n; f0 += TRUNC_TILE) {
       const int m = min(TRUNC_TILE, n - f0);
       __syncthreads();
-      for (int f = tid; f < m; f += TRUNC_THREADS) tile[f] = key(vals[f0 + f]);
+      for (int f = tid; f < m; f += TRUNC_THREADS) tile[f] = key(vals[n + f0 + f]);
       __syncthreads();
       for (int f = 0; f < m; ++f) {
         const unsigned long long vf = tile[f];
@@ -1506,13 +1535,35 @@ __global__ void __launch_bounds__(TRUNC_THREADS) truncate_kernel(const TruncSect
   const double wbefore = block_exclusive_scan(wloc, shd, total);
   const long long mbefore = block_exclusive_scan(mloc, shl, mtot);
   (void)mtot;
-  __shared__ int keep_eps, keep_chi;
+  (void)wbefore;
+  // weight of all runs after this thread's run, summed as a scan in reverse thread
+  // order (a sum of positive terms, not total minus a prefix, so small tails keep
+  // their relative accuracy)
+  __shared__ double shw[TRUNC_THREADS];
+  shw[tid] = wloc;
+  __syncthreads();
+  double wrev_total;
+  const double wafter_mirror = block_exclusive_scan(shw[TRUNC_THREADS - 1 - tid], shd, wrev_total);
+  __syncthreads();
+  shw[TRUNC_THREADS - 1 - tid] = wafter_mirror;
+  __syncthreads();
+  const double wafter = shw[tid];
+  // a head of K ranked entries may end there unless the entries K-1 and K are
+  // degenerate: per-state weights equal to within the relative tolerance degen
+  auto cut_ok = [&](int K) -> bool {
+    if (K >= n || degen <= 0.0) return true;
+    const double a = vals[n + order[K - 1]], b = vals[n + order[K]];
+    return !(a - b <= degen * a);
+  };
+  __shared__ int keep_eps, keep_chi, first_ok;
   if (tid == 0) {
     keep_eps = n;
-    keep_chi = 1;
+    keep_chi = 0;
+    first_ok = n;
   }
   __syncthreads();
-  // tail rule: the smallest r >= 1 whose suffix sum sum_{r' >= r} w is <= eps * total
+  // tail rule: the smallest allowed head r >= 1 whose dropped tail sum_{r' >= r} w is
+  // <= eps * total
   {
     // suffix within the run accumulated from the run's end, plus everything after the run
     double run_tail = 0.0;
@@ -1520,21 +1571,27 @@ __global__ void __launch_bounds__(TRUNC_THREADS) truncate_kernel(const TruncSect
     for (int r = r1 - 1; r >= r0; --r) {
       double v = vals[order[r]];
       run_tail += v > 0.0 ? v * v : 0.0;
-      double suf = (total - wbefore - wloc) + run_tail;  // sum over r' >= r
-      if (r >= 1 && suf <= eps * total) best = r;
+      double suf = wafter + run_tail;  // sum over r' >= r
+      if (r >= 1 && suf <= eps * total && cut_ok(r)) best = r;
     }
     if (best < n) atomicMin(&keep_eps, best);
   }
-  // chi cap: the largest K with sum_{r < K} mult <= chi_max (K >= 1)
+  // chi cap: the largest allowed head K with sum_{r < K} mult <= chi_max; failing
+  // that, the first allowed head (at least one multiplet is kept)
   {
     long long pre = mbefore;
-    int best = 0;
+    int best = 0, first = n;
     for (int r = r0; r < r1; ++r) {
       pre += secs[owner[order[r]]].mult;
-      if (pre <= chi_max) best = r + 1;
+      const bool ok = cut_ok(r + 1);
+      if (ok && r + 1 < first) first = r + 1;
+      if (pre <= chi_max && ok) best = r + 1;
     }
     if (best > 0) atomicMax(&keep_chi, best);
+    if (first < n) atomicMin(&first_ok, first);
   }
+  __syncthreads();
+  if (tid == 0 && keep_chi == 0) keep_chi = first_ok;
   __syncthreads();
   int K = keep_eps < keep_chi ? keep_eps : keep_chi;
   if (K < 1) K = 1;
@@ -1563,12 +1620,10 @@ __global__ void __launch_bounds__(TRUNC_THREADS) truncate_kernel(const TruncSect
 }
 
 void launch_truncate(const TruncSector* secs, int nsec, const int* offs, int n, double eps, long long chi_max,
-                     int* owner, int* order, int* kept, double* stats, cudaStream_t s) {
-  double* vals = nullptr;
-  cudaMallocAsync(&vals, (size_t)(n > 0 ? n : 1) * sizeof(double), s);
+                     double degen, int* owner, int* order, int* kept, double* stats, double* vals, cudaStream_t s) {
   note_launch();
-  truncate_kernel<<<1, TRUNC_THREADS, 0, s>>>(secs, nsec, offs, n, eps, chi_max, owner, order, kept, stats, vals);
-  cudaFreeAsync(vals, s);
+  truncate_kernel<<<1, TRUNC_THREADS, 0, s>>>(secs, nsec, offs, n, eps, chi_max, degen, owner, order, kept, stats,
+                                              vals);
 }
 
 // ---------------------------------------------------------------------------

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <functional>
 #include <vector>
 
 #include "common.hpp"
@@ -76,10 +77,18 @@ struct JacobiProfile {
   double ms = 0, flops = 0;
   long long launches = 0, resident = 0, cluster = 0;  // calls; calls that ran CTA-resident, in clusters
 };
+// Device scratch for the small per-call work lists and flags of the Jacobi drivers:
+// returns at least `bytes` bytes of device memory, usable in stream order on the
+// driver's stream until the next request, or nullptr.  An empty function makes the
+// driver allocate (and free) the region itself with cudaMallocAsync.  When no
+// region can be had the drivers launch nothing and return JACOBI_ENOMEM.
+using ScratchFn = std::function<void*(size_t)>;
+constexpr int JACOBI_ENOMEM = -3;
 // FP32 round-robin Jacobi on complex64 working copies (p >= q), accumulating V
 // (from the identity); returns the sweeps run
 int run_jacobi_rounds32(const Svd32Task* d_tasks, const std::vector<Svd32Task>& h_tasks, int max_sweeps, float tol,
-                        float abs_flag, cudaStream_t s, JacobiProfile* prof = nullptr);
+                        float abs_flag, cudaStream_t s, JacobiProfile* prof = nullptr,
+                        const ScratchFn& scratch = ScratchFn());
 void launch_narrow(const cplx* src, float2* dst, long long n, cudaStream_t s);
 void launch_widen(const float2* src, cplx* dst, long long n, cudaStream_t s);
 void launch_basis64(const BasisTask* tasks, int n, cudaStream_t s);
@@ -91,9 +100,14 @@ void launch_chol_inv(const CholTask* tasks, int n, double shift_rel, int* status
 // (same result layout as launch_jacobi_svd; v may be NULL); returns the sweeps run
 int run_jacobi_rounds(const SvdTask* d_tasks, const std::vector<SvdTask>& h_tasks, int max_sweeps, double tol,
                       int* status, cudaStream_t s, double tol_flag = 0.0, double abs_flag = 0.0,
-                      JacobiProfile* prof = nullptr);
+                      JacobiProfile* prof = nullptr, const ScratchFn& scratch = ScratchFn());
+// Multiplet selection of the truncation over nsec sectors (n values in all, sector k's
+// at offs[k]); degen > 0 keeps degenerate entries (per-state weights equal to that
+// relative tolerance) on the same side of the cut; owner, order (n ints), kept (nsec
+// ints), stats (6 doubles) and vals (2n doubles, scratch) are device buffers of the
+// caller.
 void launch_truncate(const TruncSector* secs, int nsec, const int* offs, int n, double eps, long long chi_max,
-                     int* owner, int* order, int* kept, double* stats, cudaStream_t s);
+                     double degen, int* owner, int* order, int* kept, double* stats, double* vals, cudaStream_t s);
 void launch_wdot(const DotTask* tasks, int ntasks, double* partial, double* out, int nslots, cudaStream_t s);
 void launch_entropy(const TruncSector* secs, int nsec, double* out, cudaStream_t s);
 void launch_entropy_sv(const TruncSector* secs, int nsec, const double* g, double* out, cudaStream_t s);

@@ -162,9 +162,15 @@ extern "C" int tdvp_svd_noalloc(int p, int q, const double* a, double* s, double
     c[2].scale = s;
     c[2].scale_mode = 4;
   }
-  if (add_chunks(0, p * q, chunks, nc)) return TDVP_EINTERNAL;
+  if (add_chunks(0, p * q, chunks, nc)) {
+    set_last_error("tdvp_svd_noalloc: copy work list exceeds its static capacity");
+    return TDVP_EINTERNAL;
+  }
   const int ng = nc;
-  if (add_chunks(1, p * r, chunks, nc) || add_chunks(2, r * q, chunks, nc)) return TDVP_EINTERNAL;
+  if (add_chunks(1, p * r, chunks, nc) || add_chunks(2, r * q, chunks, nc)) {
+    set_last_error("tdvp_svd_noalloc: copy work list exceeds its static capacity");
+    return TDVP_EINTERNAL;
+  }
   for (int k = ng; k < nc; ++k) chunks[k].x -= 1;  // scatter chunks index copies[1..2] as tasks 0..1
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&S->task, &task, sizeof(task), cudaMemcpyHostToDevice, st);

@@ -14,7 +14,8 @@ from paper_2606_04771_b300._lib import Opts, RequestC
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 FIELDS = {
-    "tdvp_opts": (Opts, ["precision", "krylov_max", "krylov_tol", "timeout_ms", "cuda_stream", "device"]),
+    "tdvp_opts": (Opts, ["precision", "krylov_max", "krylov_tol", "timeout_ms", "cuda_stream", "device",
+                         "trunc_degeneracy"]),
     "tdvp_request": (RequestC, ["L", "J", "U", "symmetry", "precision", "mode", "dt", "t_final", "chi_max", "eps",
                                 "occupations"]),
 }
