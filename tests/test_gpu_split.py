@@ -21,6 +21,14 @@ CASES = {
                   [(5, 1, 66), (6, 0, 1), (4, 0, 67), (5, 3, 2)]),
     "u1_tiles": (False, [(3, 1, 70), (4, 0, 130), (3, -1, 5)], [(5, 1, 66), (6, 0, 1), (5, -1, 129)]),
     "one_block": (True, [(4, 0, 1)], [(6, 0, 1)]),
+    # 119 theta blocks of d = 12..75 (328 output tiles of 64 x 64 in the last stage,
+    # more in the first): more tiles than SMs, so each persistent CTA takes several
+    # tiles (both TMEM accumulator sets, the operand ring wrapping, the epilogue of
+    # one tile beside the MMAs of the next)
+    "su2_many_tiles": (True, [(1, 1, 66), (2, 0, 70), (2, 2, 20), (3, 1, 72), (3, 3, 12), (4, 0, 75), (4, 2, 30),
+                              (5, 1, 68), (6, 0, 66), (6, 2, 16), (7, 1, 65)],
+                       [(3, 1, 66), (4, 0, 70), (4, 2, 20), (5, 1, 72), (5, 3, 12), (6, 0, 75), (6, 2, 30),
+                        (7, 1, 68), (8, 0, 66), (8, 2, 16), (9, 1, 65)]),
 }
 TOL = {"bf16x4": 2e-7, "3xtf32": 3e-5}
 
@@ -32,7 +40,10 @@ def test_split_heff_matches_oracle(name, prec):
 
     su2, left, right = CASES[name]
     bp = BondProblem(left, right, symmetry="su2" if su2 else "u1u1", precision=prec)
-    lb, rb, keys, theta, th, Ld, Rd, _ = fill_bond_problem(bp, left, right, su2, seed=4321)
+    lb, rb, keys, theta, th, Ld, Rd, (dims, _) = fill_bond_problem(bp, left, right, su2, seed=4321)
+    if name == "su2_many_tiles":
+        tiles = sum(-(-int(r) // 64) * -(-int(c) // 64) for r, c in dims)
+        assert tiles > 2 * 148, tiles
     got = bp.heff_apply(theta)
     ref = oracle_heff(lb, rb, keys, th, Ld, Rd, 1.0, 4.0)
     err = np.abs(got - ref).max() / np.abs(ref).max()
