@@ -33,6 +33,11 @@ struct GemmTask {
   int seg_begin, seg_count;
   int tiles_m, tiles_n;  // filled by the planner for the tile size in use
   int roff, coff;        // BF16x4: scale-group offsets of this task's rows and columns
+  // BF16x4 packed tasks: output row r starts at element c + rowoff[r] (rows of
+  // several output blocks stacked in one task) when rowoff is set, else at c + r ldc;
+  // tn = complex columns per output tile (a multiple of 16, at most 64; 0 = default)
+  const long long* rowoff;
+  int tn;
 };
 
 // op flags
@@ -66,6 +71,10 @@ struct DigitOp {
   int side;        // 0: A (row scales), 1: B (column scales)
   int grp;
   unsigned long long* dig;
+  // placement in the digit records: element (r, c) goes to dig[(row0 + r) dig_ld +
+  // col0 + c] and takes the scale of group row grp + row0 + r (A) or column grp +
+  // col0 + c (B); an operand of its own has row0 = col0 = 0 and dig_ld = cols
+  int dig_ld, row0, col0;
 };
 
 template <class T>

@@ -86,11 +86,18 @@ static DevBuf upload(const std::vector<T>& v, cudaStream_t s) {
 void GemmPlan::finalize(cudaStream_t s, int kind_, int* status_) {
   kind = kind_;
   status = status_;
+  if (!packed.empty() && kind != 1) throw Error(-5, "packed GEMM plans need the BF16x4 kernel");
   // algorithmic bytes: each distinct operand block read once, each output written once
   std::map<std::pair<int, uintptr_t>, long long> seen;
   bytes = 0;
-  for (const GemmTask& t : tasks) {
+  for (int i = 0; i < (int)tasks.size(); ++i) {
+    const GemmTask& t = tasks[i];
     bytes += (long long)t.rows * t.cols * (long long)sizeof(cplx);
+    if (!packed.empty()) {
+      for (const PackedSrc& q : packed[i].a) seen[{q.base, reinterpret_cast<uintptr_t>(q.src)}] = (long long)q.rows * q.cols;
+      for (const PackedSrc& q : packed[i].b) seen[{q.base, reinterpret_cast<uintptr_t>(q.src)}] = (long long)q.rows * q.cols;
+      continue;
+    }
     for (int k = 0; k < t.seg_count; ++k) {
       const GemmSeg& g = segs[t.seg_begin + k];
       seen[{g.a_base, reinterpret_cast<uintptr_t>(g.a)}] = (long long)t.rows * g.k;
@@ -99,16 +106,23 @@ void GemmPlan::finalize(cudaStream_t s, int kind_, int* status_) {
   }
   for (auto& e : seen) bytes += e.second * (long long)sizeof(cplx);
   tiles.clear();
-  const int tm = kind < 0 ? 64 : split_tile_m(), tn = kind < 0 ? 64 : split_tile_n(kind);
+  const int tm = kind < 0 ? 64 : split_tile_m(), tn0 = kind < 0 ? 64 : split_tile_n(kind);
   for (int i = 0; i < (int)tasks.size(); ++i) {
     GemmTask& t = tasks[i];
+    const int tn = (kind == 1 && t.tn > 0) ? t.tn : tn0;
     t.tiles_m = (t.rows + tm - 1) / tm;
     t.tiles_n = (t.cols + tn - 1) / tn;
     t.roff = t.coff = 0;
     for (int a = 0; a < t.tiles_m; ++a)
       for (int b = 0; b < t.tiles_n; ++b) tiles.push_back(make_int3(i, a, b));
   }
-  if (kind == 1) plan_digits(s);
+  if (!rowoffs.empty()) {
+    drow = upload(rowoffs, s);
+    for (int i = 0; i < (int)tasks.size(); ++i)
+      tasks[i].rowoff = (i < (int)row_start.size() && row_start[i] >= 0) ? drow.as<long long>() + row_start[i] : nullptr;
+  }
+  if (kind == 1 && !packed.empty()) plan_packed(s);
+  else if (kind == 1) plan_digits(s);
   dt = upload(tasks, s);
   ds = upload(segs, s);
   dti = upload(tiles, s);
@@ -211,6 +225,8 @@ void GemmPlan::plan_digits(cudaStream_t s) {
       o.alpha = std::get<7>(k);
       o.grp = goff[find(i)];
       o.dig = dig + roff[i];
+      o.dig_ld = o.cols;
+      o.row0 = o.col0 = 0;
       all[i] = o;
       const long long n = (long long)o.rows * o.cols;
       for (long long e = 0; e < n; e += job) jobs.push_back(make_int2((int)ops.size(), (int)e));
@@ -235,6 +251,92 @@ void GemmPlan::plan_digits(cudaStream_t s) {
   std::vector<int> cost(tasks.size(), 0);
   for (int i = 0; i < (int)tasks.size(); ++i)
     for (int k = 0; k < tasks[i].seg_count; ++k) cost[i] += (segs[tasks[i].seg_begin + k].k + 31) / 32;
+  std::stable_sort(tiles.begin(), tiles.end(), [&](const int3& x, const int3& y) { return cost[x.x] > cost[y.x]; });
+}
+
+// Packed BF16x4 plan: task i has one segment whose operands are private record
+// matrices (A: rows x K, B: K x cols, row-major) assembled from the source blocks of
+// packed[i]; every record position no source covers stays zero.  Each task side is
+// its own scale group (one scale per A row, one per B column): no operand is shared
+// between tasks, so no groups need merging.  Static sides take the first group
+// offsets (split once per plan), dynamic sides the rest (split every launch).
+void GemmPlan::plan_packed(cudaStream_t s) {
+  const int nt = (int)tasks.size();
+  std::vector<long long> ga(nt, -1), gb(nt, -1);
+  long long ng = 0;
+  for (int pass = 1; pass >= 0; --pass) {  // 1: static sides, 0: dynamic
+    if (pass == 0) ngrp_static = (int)ng;
+    for (int i = 0; i < nt; ++i) {
+      if ((int)packed[i].a_static == pass) {
+        ga[i] = ng;
+        ng += tasks[i].rows;
+      }
+      if ((int)packed[i].b_static == pass) {
+        gb[i] = ng;
+        ng += tasks[i].cols;
+      }
+    }
+  }
+  if (ng > INT32_MAX) throw Error(-5, "GEMM plan too large for 32-bit scale offsets");
+  ngrp = (int)ng;
+  std::vector<long long> aoff(nt), boff(nt);
+  long long nrec = 0;
+  for (int i = 0; i < nt; ++i) {
+    const long long K = segs[tasks[i].seg_begin].k;
+    aoff[i] = nrec;
+    nrec += (long long)tasks[i].rows * K;
+    boff[i] = nrec;
+    nrec += K * tasks[i].cols;
+  }
+  ddig = DevBuf(std::max<long long>(nrec, 1) * sizeof(unsigned long long), s);
+  TDVP_CUDA(cudaMemsetAsync(ddig.p, 0, std::max<long long>(nrec, 1) * sizeof(unsigned long long), s));
+  dmax = DevBuf(std::max(ngrp, 1) * sizeof(unsigned long long), s);
+  dexp = DevBuf(std::max(ngrp, 1) * sizeof(int), s);
+  unsigned long long* dig = ddig.as<unsigned long long>();
+  const int job = digit_job_size();
+  dops_s.clear();
+  dops_d.clear();
+  djobs_s.clear();
+  djobs_d.clear();
+  auto add = [&](const PackedSrc& q, int side, bool st, long long grp, unsigned long long* base, int ld) {
+    std::vector<DigitOp>& ops = st ? dops_s : dops_d;
+    std::vector<int2>& jobs = st ? djobs_s : djobs_d;
+    DigitOp o{};
+    o.side = side;
+    o.base = q.base;
+    o.src = q.src;
+    o.rows = q.rows;
+    o.cols = q.cols;
+    o.ld = q.ld;
+    o.op = q.op;
+    o.alpha = side == 0 ? q.alpha : 1.0;
+    o.grp = (int)grp;
+    o.dig = base;
+    o.dig_ld = ld;
+    o.row0 = q.row0;
+    o.col0 = q.col0;
+    const long long n = (long long)o.rows * o.cols;
+    for (long long e = 0; e < n; e += job) jobs.push_back(make_int2((int)ops.size(), (int)e));
+    ops.push_back(o);
+  };
+  for (int i = 0; i < nt; ++i) {
+    GemmTask& t = tasks[i];
+    GemmSeg& g = segs[t.seg_begin];
+    const int K = g.k;
+    for (const PackedSrc& q : packed[i].a) add(q, 0, packed[i].a_static, ga[i], dig + aoff[i], K);
+    for (const PackedSrc& q : packed[i].b) add(q, 1, packed[i].b_static, gb[i], dig + boff[i], t.cols);
+    t.roff = (int)ga[i];
+    t.coff = (int)gb[i];
+    g.a_dig = dig + aoff[i];
+    g.b_dig = dig + boff[i];
+  }
+  ddops_s = upload(dops_s, s);
+  djb_s = upload(djobs_s, s);
+  ddops_d = upload(dops_d, s);
+  djb_d = upload(djobs_d, s);
+  static_done = false;
+  std::vector<int> cost(nt, 0);
+  for (int i = 0; i < nt; ++i) cost[i] = (segs[tasks[i].seg_begin].k + 31) / 32;
   std::stable_sort(tiles.begin(), tiles.end(), [&](const int3& x, const int3& y) { return cost[x.x] > cost[y.x]; });
 }
 
@@ -1003,8 +1105,243 @@ void Engine::init_product(const std::vector<int>& occ) {
 // planners
 // ---------------------------------------------------------------------------
 
+// Whether BF16x4 two-site H_eff plans use packed tasks: unless TDVP_HEFF_PACKED=0
+// (read at every plan), which selects the per-block task lists instead.
+static bool heff_packed_enabled() {
+  const char* e = std::getenv("TDVP_HEFF_PACKED");
+  return !(e && e[0] == '0');
+}
+
+// BF16x4 output tile width for a task with n complex columns: n rounded up to 16 when
+// n <= 64, else 64
+static int packed_tile_n(int n) { return n >= 64 ? 64 : std::max(16, (n + 15) / 16 * 16); }
+
+// Two-site H_eff as packed BF16x4 tasks (same products and recoupling as plan_heff2,
+// regrouped into long GEMMs so that the tensor-core tiles are full):
+//   stage 1, one task per input sector a: the left-environment blocks L(a',w,a)
+//     stacked by rows (M_a = sum d_a') times the theta blocks (a,s1,c,s2,b) side by
+//     side (N_a = sum d_b), K = d_a; T1 of sector a is that M_a x N_a matrix and the
+//     intermediate T1(a',w,theta block) is its sub-block;
+//   stage 2, the recoupling linear combination, writes T2(o,w2,b) into the stage-3
+//     operand of its output column sector b' directly;
+//   stage 3, one task per output column sector b': the rows of every output block o =
+//     (a',s1',c',s2',b') stacked (M = sum d_a'), the (w2, b) channels of the sector
+//     side by side (K = sum d_b; blocks that no recoupling term reaches stay zero),
+//     times the right-environment blocks R(b,w2,b') stacked by rows (N = d_b'); the
+//     output rows go back to their blocks through a row-offset table.
+void Engine::plan_heff2_packed(HeffPlan& p, const BTensor& Lenv, const BTensor& Renv, const BTensor& theta,
+                               const BondSpace& bl, const BondSpace& br) {
+  p = HeffPlan();
+  p.n = theta.size;
+  const Model& M = model_;
+  const int nsl = (int)bl.s.size();
+  std::vector<std::vector<int>> lby(nsl), thby(nsl);
+  for (int i = 0; i < (int)Lenv.blocks.size(); ++i) lby[Lenv.blocks[i].key[2]].push_back(i);
+  for (int tb = 0; tb < (int)theta.blocks.size(); ++tb) thby[theta.blocks[tb].key[0]].push_back(tb);
+  // stage 1 layout: T1 block per input sector a
+  std::vector<long long> lrow(Lenv.blocks.size(), 0), tcol(theta.blocks.size(), 0);
+  std::vector<int> t1blk(nsl, -1), t1cols(nsl, 0);
+  p.t1.kind = THETA;
+  for (int a = 0; a < nsl; ++a) {
+    if (lby[a].empty() || thby[a].empty()) continue;
+    int m = 0, n = 0;
+    for (int lb : lby[a]) {
+      lrow[lb] = m;
+      m += Lenv.blocks[lb].rows;
+    }
+    for (int tb : thby[a]) {
+      tcol[tb] = n;
+      n += theta.blocks[tb].cols;
+    }
+    t1blk[a] = (int)p.t1.blocks.size();
+    t1cols[a] = n;
+    p.t1.add((uint64_t)a, a, 0, 0, 0, 0, m, n);
+  }
+  alloc(p.t1, false);
+  // T1 views, in the order of plan_heff2 (theta block, then L block)
+  struct T1View {
+    int lb, tb;
+    cplx* ptr;
+    int ld;
+  };
+  std::vector<T1View> t1v;
+  for (int tb = 0; tb < (int)theta.blocks.size(); ++tb) {
+    const int a = theta.blocks[tb].key[0];
+    if (t1blk[a] < 0) continue;
+    for (int lb : lby[a])
+      t1v.push_back({lb, tb, p.t1.ptr(t1blk[a]) + lrow[lb] * t1cols[a] + tcol[tb], t1cols[a]});
+  }
+  for (int a = 0; a < nsl; ++a) {
+    if (t1blk[a] < 0) continue;
+    const Block& tb1 = p.t1.blocks[t1blk[a]];
+    GemmTask t{};
+    t.c = p.t1.ptr(t1blk[a]);
+    t.c_base = 0;
+    t.rows = tb1.rows;
+    t.cols = tb1.cols;
+    t.ldc = tb1.cols;
+    t.tn = packed_tile_n(tb1.cols);
+    t.seg_begin = (int)p.g1.segs.size();
+    t.seg_count = 1;
+    GemmSeg sg{};
+    sg.k = bl.s[a].d;
+    sg.alpha = 1.0;
+    p.g1.segs.push_back(sg);
+    PackedTask pk;
+    pk.a_static = true;
+    pk.b_static = false;
+    for (int lb : lby[a]) {
+      const Block& lk = Lenv.blocks[lb];
+      pk.a.push_back({Lenv.ptr(lb), 0, lk.rows, lk.cols, lk.cols, OP_N, 1.0, (int)lrow[lb], 0});
+    }
+    for (int tb : thby[a]) {
+      const Block& th = theta.blocks[tb];
+      pk.b.push_back({as_off(th.off), 1, th.rows, th.cols, th.cols, OP_N, 1.0, 0, (int)tcol[tb]});
+      for (int lb : lby[a]) p.g1.flops += 8LL * Lenv.blocks[lb].rows * th.rows * th.cols;
+    }
+    p.g1.packed.push_back(std::move(pk));
+    p.g1.tasks.push_back(t);
+  }
+  // stage 2: recoupling terms (as plan_heff2)
+  std::map<std::tuple<int, int, int, int, int, int, int>, int> t2idx;
+  std::vector<std::vector<std::pair<int, double>>> t2terms;
+  std::vector<std::array<int, 7>> t2keys;
+  for (int i = 0; i < (int)t1v.size(); ++i) {
+    const Block& lk = Lenv.blocks[t1v[i].lb];
+    const Block& th = theta.blocks[t1v[i].tb];
+    int ap = lk.key[0], w = lk.key[1], a = th.key[0], s1 = th.key[1], tc = th.key[2], s2 = th.key[3], b = th.key[4];
+    const auto& rc = rec_->two_site(bl.s[ap].t, w, bl.s[a].t, s1, tc, s2, br.s[b].t);
+    for (const auto& e : rc) {
+      int nbp = br.s[b].n + M.chan[e.w2].n;
+      int bp = br.find(nbp, e.tbp);
+      if (bp < 0) continue;
+      if (Renv.find(bkey(b, e.w2, bp)) < 0) continue;
+      if (bl.s[ap].n + M.site[e.s1p].n + M.site[e.s2p].n != nbp) throw Error(-5, "charge mismatch in recoupling");
+      auto key = std::make_tuple(ap, e.s1p, e.tcp, e.s2p, bp, e.w2, b);
+      auto it = t2idx.find(key);
+      int id;
+      if (it == t2idx.end()) {
+        id = (int)t2keys.size();
+        t2idx[key] = id;
+        t2keys.push_back({ap, e.s1p, e.tcp, e.s2p, bp, e.w2, b});
+        t2terms.emplace_back();
+      } else {
+        id = it->second;
+      }
+      t2terms[id].push_back({i, e.f});
+    }
+  }
+  // stage 3 grouping by output column sector b'
+  const int nsr = (int)br.s.size();
+  std::vector<std::vector<int>> oby(nsr);  // output (theta) blocks by right sector
+  for (int ob = 0; ob < (int)theta.blocks.size(); ++ob) oby[theta.blocks[ob].key[4]].push_back(ob);
+  std::vector<long long> orow(theta.blocks.size(), 0);
+  std::vector<std::map<std::pair<int, int>, int>> segcol(nsr);  // (w2, b) -> column offset
+  std::vector<int> gk(nsr, 0), gm(nsr, 0), t2g(nsr, -1);
+  for (int bp = 0; bp < nsr; ++bp) {
+    int m = 0;
+    for (int ob : oby[bp]) {
+      orow[ob] = m;
+      m += theta.blocks[ob].rows;
+    }
+    gm[bp] = m;
+  }
+  for (const auto& k : t2keys) segcol[k[4]][{k[5], k[6]}] = 0;
+  for (int bp = 0; bp < nsr; ++bp) {
+    int kk = 0;
+    for (auto& e : segcol[bp]) {
+      e.second = kk;
+      kk += br.s[e.first.second].d;
+    }
+    gk[bp] = kk;
+  }
+  p.t2.kind = THETA;
+  for (int bp = 0; bp < nsr; ++bp)
+    if (gm[bp] > 0 && gk[bp] > 0) {
+      t2g[bp] = (int)p.t2.blocks.size();
+      p.t2.add((uint64_t)bp, bp, 0, 0, 0, 0, gm[bp], gk[bp]);
+    }
+  alloc(p.t2, true);  // (o, w2, b) blocks that no term reaches stay zero
+  std::vector<cplx*> t2ptr(t2keys.size());
+  for (int id = 0; id < (int)t2keys.size(); ++id) {
+    const auto& k = t2keys[id];
+    const int bp = k[4];
+    const int ob = theta.find(bkey(k[0], k[1], k[2], k[3], k[4]));
+    if (ob < 0) throw Error(-5, "recoupled block outside the two-site layout");
+    t2ptr[id] = p.t2.ptr(t2g[bp]) + orow[ob] * gk[bp] + segcol[bp].at({k[5], k[6]});
+    LincombTask t{};
+    t.out = t2ptr[id];
+    t.rows = bl.s[k[0]].d;
+    t.cols = br.s[k[6]].d;
+    t.ld_out = gk[bp];
+    t.term_begin = (int)p.lc.terms.size();
+    t.term_count = (int)t2terms[id].size();
+    for (auto& tm : t2terms[id]) p.lc.terms.push_back({t1v[tm.first].ptr, t1v[tm.first].ld, tm.second});
+    p.lc.tasks.push_back(t);
+    p.lc.bytes += (long long)sizeof(cplx) * t.rows * t.cols * (1 + t.term_count);
+  }
+  // stage 3 tasks
+  for (int bp = 0; bp < nsr; ++bp) {
+    if (oby[bp].empty()) continue;
+    GemmTask t{};
+    t.c = nullptr;
+    t.c_base = 2;
+    t.rows = gm[bp];
+    t.cols = br.s[bp].d;
+    t.ldc = t.cols;
+    t.tn = packed_tile_n(t.cols);
+    t.seg_begin = (int)p.g3.segs.size();
+    t.seg_count = 1;
+    p.g3.row_start.resize(p.g3.tasks.size() + 1, -1);
+    p.g3.row_start.back() = (long long)p.g3.rowoffs.size();
+    for (int ob : oby[bp]) {
+      const Block& o = theta.blocks[ob];
+      for (int r = 0; r < o.rows; ++r) p.g3.rowoffs.push_back(o.off + (long long)r * o.cols);
+    }
+    GemmSeg sg{};
+    sg.k = t2g[bp] >= 0 ? gk[bp] : 0;
+    sg.alpha = 1.0;
+    p.g3.segs.push_back(sg);
+    PackedTask pk;
+    pk.a_static = false;
+    pk.b_static = true;
+    if (t2g[bp] >= 0) {
+      for (auto& e : segcol[bp]) {
+        const int w2 = e.first.first, b = e.first.second;
+        const int rb = Renv.find(bkey(b, w2, bp));
+        const Block& rk = Renv.blocks[rb];
+        pk.b.push_back({Renv.ptr(rb), 0, rk.rows, rk.cols, rk.cols, OP_N, 1.0, e.second, 0});
+      }
+    }
+    p.g3.packed.push_back(std::move(pk));
+    p.g3.tasks.push_back(t);
+  }
+  {
+    std::map<int, int> task_of;  // output column sector -> stage-3 task
+    int ti = 0;
+    for (int bp = 0; bp < nsr; ++bp)
+      if (!oby[bp].empty()) task_of[bp] = ti++;
+    for (int id = 0; id < (int)t2keys.size(); ++id) {
+      const auto& k = t2keys[id];
+      const int bp = k[4];
+      const int ob = theta.find(bkey(k[0], k[1], k[2], k[3], k[4]));
+      const int rows = bl.s[k[0]].d, cols = br.s[k[6]].d;
+      p.g3.packed[task_of.at(bp)].a.push_back(
+          {t2ptr[id], 0, rows, cols, gk[bp], OP_N, 1.0, (int)orow[ob], segcol[bp].at({k[5], k[6]})});
+      p.g3.flops += 8LL * rows * cols * br.s[bp].d;
+    }
+  }
+  p.g1.finalize(stream_, gemm_kind_, dstatus_ + 1);
+  p.lc.finalize(stream_);
+  p.g3.finalize(stream_, gemm_kind_, dstatus_ + 1);
+}
+
 void Engine::plan_heff2(HeffPlan& p, const BTensor& Lenv, const BTensor& Renv, const BTensor& theta,
                         const BondSpace& bl, const BondSpace& br) {
+  if (gemm_kind_ == 1 && heff_packed_enabled()) {
+    plan_heff2_packed(p, Lenv, Renv, theta, bl, br);
+    return;
+  }
   p = HeffPlan();
   p.n = theta.size;
   const Model& M = model_;

@@ -102,11 +102,34 @@ struct BTensor {
   cplx* data() const { return buf.as<cplx>(); }
 };
 
+// BF16x4 packed task side: one source block of a task's A operand (rows x K) or B
+// operand (K x cols) and where it sits in that operand (first row, first column)
+struct PackedSrc {
+  const cplx* src;
+  int base;
+  int rows, cols, ld, op;  // logical shape after op
+  double alpha;            // A only
+  int row0, col0;
+};
+// One packed task: its operands are dense record matrices assembled from source
+// blocks (positions not covered by a source are zero); side static = every source
+// of that side is unchanged between launches of the plan
+struct PackedTask {
+  std::vector<PackedSrc> a, b;
+  bool a_static = false, b_static = false;
+};
+
 struct GemmPlan {
   std::vector<GemmTask> tasks;
   std::vector<GemmSeg> segs;
   std::vector<int3> tiles;
   DevBuf dt, ds, dti;
+  // packed BF16x4 plans (one segment per task, operands assembled from blocks):
+  // packed[i] describes task i; rowoffs holds the stacked-output row offsets that a
+  // task with row_start[i] >= 0 reads from index row_start[i] on
+  std::vector<PackedTask> packed;
+  std::vector<long long> rowoffs, row_start;
+  DevBuf drow;
   // BF16x4: distinct operands (static: split at the first launch; dynamic: every
   // launch), their split jobs, digit records, group maxima and exponents
   std::vector<DigitOp> dops_s, dops_d;
@@ -120,6 +143,7 @@ struct GemmPlan {
   int* status = nullptr;
   void finalize(cudaStream_t s, int kind_ = -1, int* status_ = nullptr);
   void plan_digits(cudaStream_t s);
+  void plan_packed(cudaStream_t s);
   void launch(cudaStream_t s, const Bases4& B) const;
 };
 
@@ -257,6 +281,8 @@ class Engine {
 
   void plan_heff2(HeffPlan& p, const BTensor& Lenv, const BTensor& Renv, const BTensor& theta,
                   const BondSpace& bl, const BondSpace& br);
+  void plan_heff2_packed(HeffPlan& p, const BTensor& Lenv, const BTensor& Renv, const BTensor& theta,
+                         const BondSpace& bl, const BondSpace& br);
   void plan_heff1(HeffPlan& p, const BTensor& Lenv, const BTensor& Renv, const BTensor& M, const BondSpace& bl,
                   const BondSpace& br);
   void update_left_env(const BTensor& Lin, const BTensor& A, BTensor& Lout, const BondSpace& bl,

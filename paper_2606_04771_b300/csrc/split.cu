@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             : "memory");
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (gr < t.rows) {
-          double* out = reinterpret_cast<double*>(cptr + (long long)gr * t.ldc);
+          double* out = reinterpret_cast<double*>(cptr + (t.rowoff ? t.rowoff[gr] : (long long)gr * t.ldc));
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const int gc = n0 + c0 + j;
@@ -351,9 +351,9 @@ constexpr int XN = 64;                  // complex columns per tile
 constexpr int XSTAGE = 4 * PLANE_BYTES + 4 * (64 * 128);  // 4 A planes (128 rows) + 4 B planes (64 rows)
 constexpr int XSTAGES = 2;              // 192 KB of stages: one persistent CTA per SM
 constexpr int XKC = 32;                 // complex k per chunk (64 bf16 = one 128-byte row)
-constexpr int XPROD = 128;              // producer threads (warps 0-3)
-constexpr int XMMA_WARP = 4;            // MMA issuer warp
-constexpr int XEPI = 256;               // epilogue threads (warps 5-12, two per TMEM lane quarter)
+constexpr int XPROD = 256;              // producer threads (warps 0-7)
+constexpr int XMMA_WARP = XPROD / 32;   // MMA issuer warp (8)
+constexpr int XEPI = 256;               // epilogue threads (warps 9-16, two per TMEM lane quarter)
 constexpr int XTHREADS = XPROD + 32 + XEPI;
 constexpr int XACC = 4 * XN;            // TMEM columns of one accumulator set (four orders)
 
@@ -448,6 +448,7 @@ __global__ void __launch_bounds__(256) digit_max_kernel(const DigitOp* __restric
   const unsigned long long ABS = 0x7FFFFFFFFFFFFFFFull;
   extern __shared__ unsigned long long slot[];
   const int nslot = o.side == 0 ? o.rows : o.cols;
+  const int goff = o.side == 0 ? o.row0 : o.col0;  // the operand's first row / column in its group
   const bool local = nslot <= DIGIT_SLOTS;
   if (local)
     for (int i = threadIdx.x; i < nslot; i += 256) slot[i] = 0ull;
@@ -470,7 +471,7 @@ __global__ void __launch_bounds__(256) digit_max_kernel(const DigitOp* __restric
       const unsigned long long ms = (o.side == 0 && o.alpha != 1.0)
                                         ? (unsigned long long)__double_as_longlong(fabs(o.alpha) * __longlong_as_double(m))
                                         : m;
-      atomicMax(&maxv[o.grp + sidx], ms);
+      atomicMax(&maxv[o.grp + goff + sidx], ms);
     }
   }
   __syncthreads();
@@ -479,7 +480,7 @@ __global__ void __launch_bounds__(256) digit_max_kernel(const DigitOp* __restric
       unsigned long long m = slot[i];
       if (m && o.side == 0 && o.alpha != 1.0)
         m = (unsigned long long)__double_as_longlong(fabs(o.alpha) * __longlong_as_double(m));
-      if (m) atomicMax(&maxv[o.grp + i], m);
+      if (m) atomicMax(&maxv[o.grp + goff + i], m);
     }
 }
 
@@ -521,7 +522,8 @@ __global__ void __launch_bounds__(256) digit_convert_kernel(const DigitOp* __res
       v.x *= o.alpha;
       v.y *= o.alpha;
     }
-    o.dig[e] = pack_digits(v.x, v.y, exps[o.grp + (o.side == 0 ? r : c)]);
+    o.dig[(long long)(o.row0 + r) * o.dig_ld + o.col0 + c] =
+        pack_digits(v.x, v.y, exps[o.grp + (o.side == 0 ? o.row0 + r : o.col0 + c)]);
   }
 }
 
@@ -534,9 +536,9 @@ __device__ __forceinline__ int task_chunks(const GemmTask& t, const GemmSeg* __r
 }
 
 // Persistent, warp-specialised BF16x4 kernel: one CTA per SM walks the tile list
-// (sorted by cost) with stride gridDim.x.  Warps 0-3 unpack digit records into BF16
-// planes of a two-stage ring, warp 4 issues the MMAs into one of two TMEM
-// accumulator sets, warps 5-12 drain the other set (exact combination, scaling,
+// (sorted by cost) with stride gridDim.x.  Warps 0-7 unpack digit records into BF16
+// planes of a two-stage ring, warp 8 issues the MMAs into one of two TMEM
+// accumulator sets, warps 9-16 drain the other set (exact combination, scaling,
 // FP64 stores) while the next tile accumulates.
 __global__ void __launch_bounds__(XTHREADS, 1)
     gemm_exact_kernel(const GemmTask* __restrict__ tasks, const GemmSeg* __restrict__ segs,
@@ -575,71 +577,100 @@ __global__ void __launch_bounds__(XTHREADS, 1)
 
   if (warp < XPROD / 32) {
     // ---------------- producers ----------------
+    // The CTA's chunks (tile, segment, k0) in order; the records of the next chunk are
+    // loaded into registers before the current chunk is unpacked, so the loads of one
+    // chunk overlap the shared-memory stores of the previous one.
     const int gtid = tid;
-    int it = 0;
-    for (int ti = blockIdx.x; ti < ntiles && !*verr; ti += gridDim.x) {
+    constexpr int GT = XPROD;
+    constexpr int NA = TM * XKC / GT, NB = XN * XKC / GT;
+    auto advance = [&](int& ti, int& sgi, int& k0) -> bool {
+      k0 += XKC;
+      while (ti < ntiles) {
+        const GemmTask& t = tasks[tiles[ti].x];
+        while (sgi < t.seg_count) {
+          if (k0 < segs[t.seg_begin + sgi].k) return true;
+          ++sgi;
+          k0 = 0;
+        }
+        ti += gridDim.x;
+        sgi = 0;
+        k0 = 0;
+      }
+      return false;
+    };
+    auto fetch = [&](int ti, int sgi, int k0, unsigned long long* wa, unsigned long long* wb) {
       const int3 tr = tiles[ti];
-      const GemmTask t = tasks[tr.x];
-      const int m0 = tr.y * TM, n0 = tr.z * XN;
-      for (int sgi = 0; sgi < t.seg_count && !*verr; ++sgi) {
-        const GemmSeg sg = segs[t.seg_begin + sgi];
-        const unsigned long long* ad = sg.a_dig;
-        const unsigned long long* bd = sg.b_dig;
-        for (int k0 = 0; k0 < sg.k; k0 += XKC, ++it) {
-          const int s = it % XSTAGES;
-          if (!mbar_wait(&empty_bar[s], ((it / XSTAGES) & 1) ^ 1, verr)) break;
-          uint8_t* st = stage_base + (size_t)s * XSTAGE;
-          // all 32 records of this thread first (loads in flight together), then
-          // A: 64 complex rows x 32 complex k -> 4 digit planes of 128 rows x 64 bf16,
-          // B: 32 complex k x 64 complex n -> 4 digit planes of 64 rows x 64 bf16
-          constexpr int GT = XPROD;
-          constexpr int NA = TM * XKC / GT, NB = XN * XKC / GT;
-          unsigned long long wa[NA], wb[NB];
+      const GemmTask& t = tasks[tr.x];
+      const GemmSeg& sg = segs[t.seg_begin + sgi];
+      const int tn = t.tn > 0 ? t.tn : XN;
+      const int m0 = tr.y * TM, n0 = tr.z * tn, kk = sg.k, rows = t.rows, cols = t.cols;
+      const unsigned long long* ad = sg.a_dig;
+      const unsigned long long* bd = sg.b_dig;
 #pragma unroll
-          for (int j = 0; j < NA; ++j) {
-            const int e = gtid + j * GT, m = e / XKC, k = e % XKC;
-            const int gr = m0 + m, gk = k0 + k;
-            wa[j] = (gr < t.rows && gk < sg.k) ? __ldg(ad + (long long)gr * sg.k + gk) : 0ull;
-          }
+      for (int j = 0; j < NA; ++j) {
+        const int e = gtid + j * GT, m = e / XKC, k = e % XKC;
+        const int gr = m0 + m, gk = k0 + k;
+        wa[j] = (gr < rows && gk < kk) ? __ldg(ad + (long long)gr * kk + gk) : 0ull;
+      }
 #pragma unroll
-          for (int j = 0; j < NB; ++j) {
-            const int e = gtid + j * GT, n = e % XN, k = e / XN;
-            const int gc = n0 + n, gk = k0 + k;
-            wb[j] = (gc < t.cols && gk < sg.k) ? __ldg(bd + (long long)gk * t.cols + gc) : 0ull;
-          }
+      for (int j = 0; j < NB; ++j) {
+        const int e = gtid + j * GT, n = e % XN, k = e / XN;
+        const int gc = n0 + n, gk = k0 + k;
+        wb[j] = (n < tn && gc < cols && gk < kk) ? __ldg(bd + (long long)gk * cols + gc) : 0ull;
+      }
+    };
+    int ti = blockIdx.x, sgi = 0, k0 = -XKC;
+    bool have = advance(ti, sgi, k0);
+    unsigned long long wa[NA], wb[NB], na_[NA], nb_[NB];
+    if (have) fetch(ti, sgi, k0, wa, wb);
+    for (int it = 0; have && !*verr; ++it) {
+      int ti2 = ti, sgi2 = sgi, k02 = k0;
+      const bool have2 = advance(ti2, sgi2, k02);
+      if (have2) fetch(ti2, sgi2, k02, na_, nb_);
+      const int s = it % XSTAGES;
+      if (!mbar_wait(&empty_bar[s], ((it / XSTAGES) & 1) ^ 1, verr)) break;
+      uint8_t* st = stage_base + (size_t)s * XSTAGE;
+      // A: 64 complex rows x 32 complex k -> 4 digit planes of 128 rows x 64 bf16,
+      // B: 32 complex k x 64 complex n -> 4 digit planes of 64 rows x 64 bf16
 #pragma unroll
-          for (int j = 0; j < NA; ++j) {
-            const int e = gtid + j * GT, m = e / XKC, k = e % XKC;
+      for (int j = 0; j < NA; ++j) {
+        const int e = gtid + j * GT, m = e / XKC, k = e % XKC;
 #pragma unroll
-            for (int p = 0; p < 4; ++p) {
-              const float re = sbyte(wa[j], p), im = sbyte(wa[j], 4 + p);
-              uint8_t* pl = st + p * PLANE_BYTES;
-              st_bf2(pl, 2 * m, 2 * k, re, -im);
-              st_bf2(pl, 2 * m + 1, 2 * k, im, re);
-            }
-          }
-#pragma unroll
-          for (int j = 0; j < NB; ++j) {
-            const int e = gtid + j * GT, n = e % XN, k = e / XN;
-#pragma unroll
-            for (int p = 0; p < 4; ++p)
-              st_bf2(st + 4 * PLANE_BYTES + p * (64 * 128), n, 2 * k, sbyte(wb[j], p), sbyte(wb[j], 4 + p));
-          }
-          fence_proxy_async();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&full_bar[s]);
+        for (int p = 0; p < 4; ++p) {
+          const float re = sbyte(wa[j], p), im = sbyte(wa[j], 4 + p);
+          uint8_t* pl = st + p * PLANE_BYTES;
+          st_bf2(pl, 2 * m, 2 * k, re, -im);
+          st_bf2(pl, 2 * m + 1, 2 * k, im, re);
         }
       }
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        const int e = gtid + j * GT, n = e % XN, k = e / XN;
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+          st_bf2(st + 4 * PLANE_BYTES + p * (64 * 128), n, 2 * k, sbyte(wb[j], p), sbyte(wb[j], 4 + p));
+      }
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&full_bar[s]);
+#pragma unroll
+      for (int j = 0; j < NA; ++j) wa[j] = na_[j];
+#pragma unroll
+      for (int j = 0; j < NB; ++j) wb[j] = nb_[j];
+      ti = ti2;
+      sgi = sgi2;
+      k0 = k02;
+      have = have2;
     }
   } else if (warp == XMMA_WARP) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      constexpr uint32_t idesc = make_idesc(1u, 128, XN);
       int it = 0, j = 0;
       bool ok = true;
       for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
         const GemmTask t = tasks[tiles[ti].x];
         if (task_chunks(t, segs) == 0) continue;
+        const uint32_t idesc = make_idesc(1u, 128, (uint32_t)(t.tn > 0 ? t.tn : XN));
         const int buf = j & 1;
         if (!mbar_wait(&tempty[buf], ((j >> 1) & 1) ^ 1, verr)) break;
         tc_fence_after();
@@ -655,8 +686,12 @@ __global__ void __launch_bounds__(XTHREADS, 1)
             }
             tc_fence_after();
             const uint32_t st = smem_u32(stage_base + (size_t)s * XSTAGE);
+            // 4 k-steps of 16 bf16 (8 complex k, 32 bytes); the last chunk of a
+            // segment issues only the steps that hold data
+            const int nks = min(4, (kk - k0 + 7) >> 3);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {  // 4 k-steps of 16 bf16 (32 bytes)
+            for (int q = 0; q < 4; ++q) {
+              if (q >= nks) break;
               const uint32_t koff = q * 32;
               uint64_t a[4], b[4];
 #pragma unroll
@@ -681,7 +716,7 @@ __global__ void __launch_bounds__(XTHREADS, 1)
       }
     }
   } else {
-    // ---------------- epilogue (warps 5-12: warp w reads TMEM lane quarter w mod 4;
+    // ---------------- epilogue (warps 9-16: warp w reads TMEM lane quarter w mod 4;
     // the two warps of a quarter take one half of the 64 columns each) ----------------
     const int quarter = warp & 3;
     const int half = (warp - XMMA_WARP - 1) >> 2;
@@ -691,11 +726,13 @@ __global__ void __launch_bounds__(XTHREADS, 1)
       const int3 tr = tiles[ti];
       const GemmTask t = tasks[tr.x];
       cplx* const cptr = rebase(B, t.c_base, t.c);
-      const int m0 = tr.y * TM, n0 = tr.z * XN;
+      const int tn = t.tn > 0 ? t.tn : XN;
+      const int m0 = tr.y * TM, n0 = tr.z * tn;
       if (task_chunks(t, segs) == 0) {  // no contribution: the output tile is zero
         for (int e = etid; e < TM * XN; e += XEPI) {
           const int r = m0 + e / XN, c = n0 + e % XN;
-          if (r < t.rows && c < t.cols) cptr[(long long)r * t.ldc + c] = {0.0, 0.0};
+          if (r < t.rows && e % XN < tn && c < t.cols)
+            cptr[t.rowoff ? t.rowoff[r] + c : (long long)r * t.ldc + c] = {0.0, 0.0};
         }
         continue;
       }
@@ -707,7 +744,8 @@ __global__ void __launch_bounds__(XTHREADS, 1)
       const int gr = m0 + m;
       const int re_m = gr < t.rows ? exps[t.roff + gr] : 0;
       const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) + buf * XACC;
-      for (int c0 = half * (XN / 2); c0 < (half + 1) * (XN / 2); c0 += 16) {
+      // the two warps of a lane quarter take alternate 16-column groups of the tile
+      for (int c0 = half * 16; c0 < tn; c0 += 32) {
         uint32_t a0[16], a1[16], a2[16], a3[16];
         tmem_ld16<16>(lane_addr + 0 * XN + c0, a0);
         tmem_ld16<16>(lane_addr + 1 * XN + c0, a1);
@@ -715,7 +753,7 @@ __global__ void __launch_bounds__(XTHREADS, 1)
         tmem_ld16<16>(lane_addr + 3 * XN + c0, a3);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (gr < t.rows) {
-          double* out = reinterpret_cast<double*>(cptr + (long long)gr * t.ldc);
+          double* out = reinterpret_cast<double*>(cptr + (t.rowoff ? t.rowoff[gr] : (long long)gr * t.ldc));
 #pragma unroll
           for (int jj = 0; jj < 16; ++jj) {
             const int gc = n0 + c0 + jj;

@@ -33,11 +33,16 @@ CASES = {
 TOL = {"bf16x4": 2e-7, "3xtf32": 3e-5}
 
 
-@pytest.mark.parametrize("prec", ["bf16x4", "3xtf32"])
+@pytest.mark.parametrize("prec", ["bf16x4", "bf16x4-blocks", "3xtf32"])
 @pytest.mark.parametrize("name", list(CASES))
-def test_split_heff_matches_oracle(name, prec):
+def test_split_heff_matches_oracle(name, prec, monkeypatch):
+    """bf16x4: the packed plan (long GEMMs per input / output sector); bf16x4-blocks:
+    the per-block task lists (TDVP_HEFF_PACKED=0); both to the BF16x4 bar."""
     from paper_2606_04771_b300 import BondProblem
 
+    if prec == "bf16x4-blocks":
+        monkeypatch.setenv("TDVP_HEFF_PACKED", "0")
+        prec = "bf16x4"
     su2, left, right = CASES[name]
     bp = BondProblem(left, right, symmetry="su2" if su2 else "u1u1", precision=prec)
     lb, rb, keys, theta, th, Ld, Rd, (dims, _) = fill_bond_problem(bp, left, right, su2, seed=4321)
