@@ -382,7 +382,8 @@ def run_engine(args):
     # with CUDA events around each cooperative launch inside the timed steps; the
     # H_eff GEMMs of the step are its matvecs x the GEMM time of one matvec
     d = {k: (st1[k] - st0[k]) / args.steps for k in ("jacobi32_ms", "jacobi32_flops", "jacobi64_ms", "jacobi64_flops",
-                                                       "matvecs", "env_ms", "env_bytes")}
+                                                       "matvecs", "env_ms", "env_bytes", "sweeps32", "sweeps64",
+                                                       "splits")}
     shares = {"jacobi_fp32": d["jacobi32_ms"], "jacobi_fp64": d["jacobi64_ms"],
               "heff_gemm": d["matvecs"] * heff["gemm_ms"], "env_update": d["env_ms"]}
     top = max(shares, key=shares.get)
@@ -414,7 +415,8 @@ def run_engine(args):
         ms_, fl_ = d[f"jacobi{tag[2:]}_ms"], d[f"jacobi{tag[2:]}_flops"]
         a_ = fl_ / (ms_ * 1e-3) / 1e12 if ms_ > 0 else None
         jac[tag] = {"ms_per_step": ms_, "alg_gflop_per_step": fl_ / 1e9, "achieved_tflops": a_,
-                    "frac_of_measured": a_ / alu[peak_k] if a_ else None}
+                    "frac_of_measured": a_ / alu[peak_k] if a_ else None,
+                    "sweeps_per_split": d[f"sweeps{tag[2:]}"] / d["splits"] if d["splits"] else None}
     env = {"ms_per_step": d["env_ms"], "alg_bytes_per_step": d["env_bytes"],
            "gbs": d["env_bytes"] / (d["env_ms"] * 1e-3) / 1e9 if d["env_ms"] > 0 else None}
     env["frac_hbm"] = env["gbs"] / peaks["hbm_gbs"] if env["gbs"] else None

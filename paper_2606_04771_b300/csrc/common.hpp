@@ -38,6 +38,7 @@ struct GemmTask {
   // tn = complex columns per output tile (a multiple of 16, at most 64; 0 = default)
   const long long* rowoff;
   int tn;
+  int b_kmajor;  // BF16x4: the B records are stored column by column (K contiguous)
 };
 
 // op flags
@@ -72,9 +73,10 @@ struct DigitOp {
   int grp;
   unsigned long long* dig;
   // placement in the digit records: element (r, c) goes to dig[(row0 + r) dig_ld +
-  // col0 + c] and takes the scale of group row grp + row0 + r (A) or column grp +
-  // col0 + c (B); an operand of its own has row0 = col0 = 0 and dig_ld = cols
-  int dig_ld, row0, col0;
+  // col0 + c] (kmajor: dig[(col0 + c) dig_ld + row0 + r]) and takes the scale of
+  // group row grp + row0 + r (A) or column grp + col0 + c (B); an operand of its own
+  // has row0 = col0 = 0, dig_ld = cols and kmajor = 0
+  int dig_ld, row0, col0, kmajor;
 };
 
 template <class T>

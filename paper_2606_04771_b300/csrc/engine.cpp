@@ -201,8 +201,10 @@ void GemmPlan::plan_digits(cudaStream_t s) {
     nrec += (long long)std::get<3>(keys[i]) * std::get<4>(keys[i]);
   }
   ddig = DevBuf(std::max<long long>(nrec, 1) * sizeof(unsigned long long), s);
-  dmax = DevBuf(std::max(ngrp, 1) * sizeof(unsigned long long), s);
+  dtag = DevBuf(std::max(ngrp, 1) * sizeof(unsigned), s);
+  TDVP_CUDA(cudaMemsetAsync(dtag.p, 0, std::max(ngrp, 1) * sizeof(unsigned), s));
   dexp = DevBuf(std::max(ngrp, 1) * sizeof(int), s);
+  epoch = 0;
   unsigned long long* dig = ddig.as<unsigned long long>();
   std::vector<DigitOp> all(keys.size());
   const int job = digit_job_size();
@@ -227,6 +229,7 @@ void GemmPlan::plan_digits(cudaStream_t s) {
       o.dig = dig + roff[i];
       o.dig_ld = o.cols;
       o.row0 = o.col0 = 0;
+      o.kmajor = 0;
       all[i] = o;
       const long long n = (long long)o.rows * o.cols;
       for (long long e = 0; e < n; e += job) jobs.push_back(make_int2((int)ops.size(), (int)e));
@@ -290,8 +293,10 @@ void GemmPlan::plan_packed(cudaStream_t s) {
   }
   ddig = DevBuf(std::max<long long>(nrec, 1) * sizeof(unsigned long long), s);
   TDVP_CUDA(cudaMemsetAsync(ddig.p, 0, std::max<long long>(nrec, 1) * sizeof(unsigned long long), s));
-  dmax = DevBuf(std::max(ngrp, 1) * sizeof(unsigned long long), s);
+  dtag = DevBuf(std::max(ngrp, 1) * sizeof(unsigned), s);
+  TDVP_CUDA(cudaMemsetAsync(dtag.p, 0, std::max(ngrp, 1) * sizeof(unsigned), s));
   dexp = DevBuf(std::max(ngrp, 1) * sizeof(int), s);
+  epoch = 0;
   unsigned long long* dig = ddig.as<unsigned long long>();
   const int job = digit_job_size();
   dops_s.clear();
@@ -315,6 +320,7 @@ void GemmPlan::plan_packed(cudaStream_t s) {
     o.dig_ld = ld;
     o.row0 = q.row0;
     o.col0 = q.col0;
+    o.kmajor = side == 1;  // B records column by column (K contiguous)
     const long long n = (long long)o.rows * o.cols;
     for (long long e = 0; e < n; e += job) jobs.push_back(make_int2((int)ops.size(), (int)e));
     ops.push_back(o);
@@ -324,7 +330,8 @@ void GemmPlan::plan_packed(cudaStream_t s) {
     GemmSeg& g = segs[t.seg_begin];
     const int K = g.k;
     for (const PackedSrc& q : packed[i].a) add(q, 0, packed[i].a_static, ga[i], dig + aoff[i], K);
-    for (const PackedSrc& q : packed[i].b) add(q, 1, packed[i].b_static, gb[i], dig + boff[i], t.cols);
+    for (const PackedSrc& q : packed[i].b) add(q, 1, packed[i].b_static, gb[i], dig + boff[i], K);
+    t.b_kmajor = 1;
     t.roff = (int)ga[i];
     t.coff = (int)gb[i];
     g.a_dig = dig + aoff[i];
@@ -345,13 +352,18 @@ void GemmPlan::launch(cudaStream_t s, const Bases4& B) const {
     launch_gemm_fp64(dt.as<GemmTask>(), ds.as<GemmSeg>(), dti.as<int3>(), (int)tiles.size(), B, s);
   else {
     if (kind == 1) {
+      if (epoch + 2 > DIGIT_EPOCH_MAX) {  // the tag counter wraps: clear every tag, split all again
+        TDVP_CUDA(cudaMemsetAsync(dtag.p, 0, std::max(ngrp, 1) * sizeof(unsigned), s));
+        epoch = 0;
+        static_done = false;
+      }
       if (!static_done) {  // environment operands: split once per plan
         launch_digits(ddops_s.as<DigitOp>(), (int)dops_s.size(), djb_s.as<int2>(), (int)djobs_s.size(),
-                      dmax.as<unsigned long long>(), dexp.as<int>(), 0, ngrp_static, B, s);
+                      dtag.as<unsigned>(), dexp.as<int>(), ++epoch, B, s);
         static_done = true;
       }
       launch_digits(ddops_d.as<DigitOp>(), (int)dops_d.size(), djb_d.as<int2>(), (int)djobs_d.size(),
-                    dmax.as<unsigned long long>(), dexp.as<int>(), ngrp_static, ngrp, B, s);
+                    dtag.as<unsigned>(), dexp.as<int>(), ++epoch, B, s);
     }
     launch_gemm_split(kind, dt.as<GemmTask>(), ds.as<GemmSeg>(), dti.as<int3>(), (int)tiles.size(), dexp.as<int>(),
                       B, status, s);

@@ -134,9 +134,10 @@ struct GemmPlan {
   // launch), their split jobs, digit records, group maxima and exponents
   std::vector<DigitOp> dops_s, dops_d;
   std::vector<int2> djobs_s, djobs_d;
-  DevBuf ddops_s, djb_s, ddops_d, djb_d, ddig, dmax, dexp;
+  DevBuf ddops_s, djb_s, ddops_d, djb_d, ddig, dtag, dexp;
   int ngrp = 0, ngrp_static = 0;
   mutable bool static_done = false;
+  mutable unsigned epoch = 0;  // of the last digit split (exponent tags of older epochs read as empty)
   long long flops = 0;  // algorithmic real flops (8 per complex MAC)
   long long bytes = 0;  // algorithmic bytes: every operand block read once, output written once
   int kind = -1;        // -1 FP64 CUDA cores, 0 3xTF32, 1 BF16x3 tensor cores

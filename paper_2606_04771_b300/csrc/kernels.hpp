@@ -44,14 +44,15 @@ int split_tile_m();
 int split_tile_n(int kind);
 void launch_gemm_split(int kind, const GemmTask* tasks, const GemmSeg* segs, const int3* tiles, int ntiles,
                        const int* exps, const Bases4& B, int* status, cudaStream_t s);
-// BF16x4 operand splitting (once per launch): group maxima, exponents, digit records.
-// jobs = (operand, first element) in steps of digit_job_size() elements.
+// BF16x4 operand splitting (once per launch): group exponent tags of this epoch, then
+// digit records and exponents.  jobs = (operand, first element) in steps of
+// digit_job_size() elements.  tags start at zero; epoch runs 1 .. 2^20 - 1.
 int digit_job_size();
+constexpr unsigned DIGIT_EPOCH_MAX = (1u << 20) - 1;
 // one bounded wait on an mbarrier that never completes; adds 1 to *status on expiry
 void launch_wait_selftest(unsigned polls, int* status, cudaStream_t s);
-// the groups [g0, g1) are reset and recomputed (the operands' groups lie in that range)
-void launch_digits(const DigitOp* ops, int nops, const int2* jobs, int njobs, unsigned long long* maxv, int* exps,
-                   int g0, int g1, const Bases4& B, cudaStream_t s);
+void launch_digits(const DigitOp* ops, int nops, const int2* jobs, int njobs, unsigned* tags, int* exps,
+                   unsigned epoch, const Bases4& B, cudaStream_t s);
 
 int dots_grid(long long n);
 void launch_dots(const cplx* V, long long pitch, int nv, const cplx* w, long long n, cplx* partial, int G, cplx* out,

@@ -357,13 +357,6 @@ constexpr int XEPI = 256;               // epilogue threads (warps 9-16, two per
 constexpr int XTHREADS = XPROD + 32 + XEPI;
 constexpr int XACC = 4 * XN;            // TMEM columns of one accumulator set (four orders)
 
-__device__ __forceinline__ int exp_of_max(double m) {
-  // smallest e with |x| <= 2^e for |x| <= m (m > 0); -2000 marks an all-zero row
-  if (!(m > 0.0)) return -2000;
-  const unsigned long long b = __double_as_longlong(m);
-  const int ex = (int)((b >> 52) & 0x7FF);
-  return ex - 1022;
-}
 
 // X = round(x 2^(30 - e)) as int (|X| <= 2^30); x must satisfy |x| <= 2^e
 __device__ __forceinline__ int fixed30(double x, int e) {
@@ -436,22 +429,31 @@ __device__ __forceinline__ void tmem_ld16(uint32_t addr, uint32_t* v) {
 }
 
 // ---- operand splitting, once per launch --------------------------------------
-// pass 1: per-row (A) / per-column (B) maxima of |Re|, |Im| into the operand's
-// scale group (bit patterns of non-negative doubles order like the values).  One
-// CTA per operand walks all elements in storage order (coalesced) and reduces into
-// shared-memory slots with 64-bit atomics, then merges the slots into the group.
-constexpr int DIGIT_SLOTS = 6144;  // 48 KB of slots; longer rows/columns go to global atomics
+// pass 1: per-row (A) / per-column (B) maxima of |Re|, |Im| into the operand's scale
+// group.  Only the binary exponent of a maximum matters (the scale is the power of two
+// just above it), so each group row / column holds a 32-bit tag: the launch's epoch in
+// bits 12-31 and the largest biased exponent seen in bits 0-11; an unsigned atomicMax
+// keeps the newest epoch's largest exponent, and a tag of an older epoch means "no
+// non-zero element in this launch" -- no reset pass is needed between launches.  One
+// CTA per operand walks its elements in storage order (coalesced) and reduces into
+// shared-memory slots, then merges the slots into the group.
+constexpr int DIGIT_SLOTS = 6144;  // 24 KB of slots; longer rows/columns go to global atomics
+
+__device__ __forceinline__ unsigned biased_exp(double x) {
+  return (unsigned)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FF);
+}
+
 __global__ void __launch_bounds__(256) digit_max_kernel(const DigitOp* __restrict__ ops, const Bases4 B,
-                                                        unsigned long long* __restrict__ maxv) {
+                                                        unsigned* __restrict__ tags, unsigned epoch) {
   const DigitOp o = ops[blockIdx.x];
   const cplx* src = rebase(B, o.base, o.src);
-  const unsigned long long ABS = 0x7FFFFFFFFFFFFFFFull;
-  extern __shared__ unsigned long long slot[];
+  extern __shared__ unsigned slot[];
   const int nslot = o.side == 0 ? o.rows : o.cols;
   const int goff = o.side == 0 ? o.row0 : o.col0;  // the operand's first row / column in its group
   const bool local = nslot <= DIGIT_SLOTS;
+  const double sa = (o.side == 0 && o.alpha != 1.0) ? fabs(o.alpha) : 1.0;
   if (local)
-    for (int i = threadIdx.x; i < nslot; i += 256) slot[i] = 0ull;
+    for (int i = threadIdx.x; i < nslot; i += 256) slot[i] = 0u;
   __syncthreads();
   const long long n = (long long)o.rows * o.cols;
   // storage order: OP_N stores rows of length cols, OP_C stores columns of length rows
@@ -461,32 +463,24 @@ __global__ void __launch_bounds__(256) digit_max_kernel(const DigitOp* __restric
     const int outer = (int)(e / inner), in = (int)(e - (long long)outer * inner);
     const cplx v = src[(long long)outer * o.ld + in];
     const int r = o.op == OP_N ? outer : in, c = o.op == OP_N ? in : outer;
-    const unsigned long long m = max((unsigned long long)__double_as_longlong(v.x) & ABS,
-                                     (unsigned long long)__double_as_longlong(v.y) & ABS);
-    if (!m) continue;
+    const unsigned ex = biased_exp(sa * fmax(fabs(v.x), fabs(v.y)));
+    if (!ex) continue;  // zero (or subnormal, which the split rounds to zero)
     const int sidx = o.side == 0 ? r : c;
-    if (local) {
-      atomicMax(&slot[sidx], m);
-    } else {
-      const unsigned long long ms = (o.side == 0 && o.alpha != 1.0)
-                                        ? (unsigned long long)__double_as_longlong(fabs(o.alpha) * __longlong_as_double(m))
-                                        : m;
-      atomicMax(&maxv[o.grp + goff + sidx], ms);
-    }
+    if (local) atomicMax(&slot[sidx], ex);
+    else atomicMax(&tags[o.grp + goff + sidx], (epoch << 12) | ex);
   }
   __syncthreads();
   if (local)
     for (int i = threadIdx.x; i < nslot; i += 256) {
-      unsigned long long m = slot[i];
-      if (m && o.side == 0 && o.alpha != 1.0)
-        m = (unsigned long long)__double_as_longlong(fabs(o.alpha) * __longlong_as_double(m));
-      if (m) atomicMax(&maxv[o.grp + goff + i], m);
+      const unsigned ex = slot[i];
+      if (ex) atomicMax(&tags[o.grp + goff + i], (epoch << 12) | ex);
     }
 }
 
-// pass 2: the exponent of every group row/column
-__global__ void digit_exp_kernel(const unsigned long long* __restrict__ maxv, int* __restrict__ exps, int n) {
-  for (int i = blockIdx.x * 256 + threadIdx.x; i < n; i += gridDim.x * 256) exps[i] = exp_of_max(__longlong_as_double(maxv[i]));
+// the scale exponent of a group row / column in this launch: the smallest e with
+// max|x| <= 2^e, or -2000 when the row / column holds no non-zero element
+__device__ __forceinline__ int tag_exp(unsigned tag, unsigned epoch) {
+  return (tag >> 12) == epoch ? (int)(tag & 0xFFF) - 1022 : -2000;
 }
 
 __device__ __forceinline__ unsigned long long pack_digits(double re, double im, int e) {
@@ -502,12 +496,15 @@ __device__ __forceinline__ unsigned long long pack_digits(double re, double im, 
   return w;
 }
 
-// pass 3: every element of every operand as one 8-byte record (Re digits 0-3, Im
-// digits 0-3, signed bytes), logical row-major; jobs = (operand, first element)
+// pass 2: every element of every operand as one 8-byte record (Re digits 0-3, Im
+// digits 0-3, signed bytes) at its place in the digit records (row-major, or column-
+// major for a K-major B operand); jobs = (operand, first element).  The thread of
+// column 0 (A) or row 0 (B) also stores the exponent for the GEMM's epilogue.
 constexpr int DIGIT_JOB = 4096;
 __global__ void __launch_bounds__(256) digit_convert_kernel(const DigitOp* __restrict__ ops,
                                                             const int2* __restrict__ jobs, const Bases4 B,
-                                                            const int* __restrict__ exps) {
+                                                            const unsigned* __restrict__ tags, unsigned epoch,
+                                                            int* __restrict__ exps) {
   const int2 jb = jobs[blockIdx.x];
   const DigitOp o = ops[jb.x];
   const cplx* src = rebase(B, o.base, o.src);
@@ -515,19 +512,47 @@ __global__ void __launch_bounds__(256) digit_convert_kernel(const DigitOp* __res
   const long long e1 = min(n, (long long)jb.y + DIGIT_JOB);
 #pragma unroll 4
   for (long long e = jb.y + threadIdx.x; e < e1; e += 256) {
-    const int r = (int)(e / o.cols), c = (int)(e - (long long)r * o.cols);
+    // K-major B operands are walked column by column (their records are contiguous
+    // along a column), everything else row by row
+    int r, c;
+    if (o.kmajor) {
+      c = (int)(e / o.rows);
+      r = (int)(e - (long long)c * o.rows);
+    } else {
+      r = (int)(e / o.cols);
+      c = (int)(e - (long long)r * o.cols);
+    }
     cplx v = o.op == OP_N ? src[(long long)r * o.ld + c] : src[(long long)c * o.ld + r];
     if (o.op != OP_N) v.y = -v.y;
     if (o.alpha != 1.0) {
       v.x *= o.alpha;
       v.y *= o.alpha;
     }
-    o.dig[(long long)(o.row0 + r) * o.dig_ld + o.col0 + c] =
-        pack_digits(v.x, v.y, exps[o.grp + (o.side == 0 ? o.row0 + r : o.col0 + c)]);
+    const int gi = o.grp + (o.side == 0 ? o.row0 + r : o.col0 + c);
+    const int ex = tag_exp(tags[gi], epoch);
+    if (o.side == 0 ? c == 0 : r == 0) exps[gi] = ex;
+    const long long at = o.kmajor ? (long long)(o.col0 + c) * o.dig_ld + o.row0 + r
+                                  : (long long)(o.row0 + r) * o.dig_ld + o.col0 + c;
+    o.dig[at] = pack_digits(v.x, v.y, ex);
   }
 }
 
 __device__ __forceinline__ float sbyte(unsigned long long w, int i) { return (float)(int)(signed char)(w >> (8 * i)); }
+
+// the B record a producer thread handles: element e of a chunk (XKC k x XN columns);
+// consecutive threads take consecutive columns of one k (row-major records, loads
+// coalesced along the row) or consecutive k of one column (K-major records, loads
+// coalesced along the column, and the bf16 stores of a warp fill one 128-byte row of
+// the swizzled plane, free of bank conflicts)
+__device__ __forceinline__ void b_coords(int e, int kmajor, int& n, int& k) {
+  if (kmajor) {
+    n = e / XKC;
+    k = e % XKC;
+  } else {
+    n = e % XN;
+    k = e / XN;
+  }
+}
 
 __device__ __forceinline__ int task_chunks(const GemmTask& t, const GemmSeg* __restrict__ segs) {
   int n = 0;
@@ -614,9 +639,12 @@ __global__ void __launch_bounds__(XTHREADS, 1)
       }
 #pragma unroll
       for (int j = 0; j < NB; ++j) {
-        const int e = gtid + j * GT, n = e % XN, k = e / XN;
+        int n, k;
+        b_coords(gtid + j * GT, t.b_kmajor, n, k);
         const int gc = n0 + n, gk = k0 + k;
-        wb[j] = (n < tn && gc < cols && gk < kk) ? __ldg(bd + (long long)gk * cols + gc) : 0ull;
+        wb[j] = (n < tn && gc < cols && gk < kk)
+                    ? __ldg(bd + (t.b_kmajor ? (long long)gc * kk + gk : (long long)gk * cols + gc))
+                    : 0ull;
       }
     };
     int ti = blockIdx.x, sgi = 0, k0 = -XKC;
@@ -624,6 +652,7 @@ __global__ void __launch_bounds__(XTHREADS, 1)
     unsigned long long wa[NA], wb[NB], na_[NA], nb_[NB];
     if (have) fetch(ti, sgi, k0, wa, wb);
     for (int it = 0; have && !*verr; ++it) {
+      const int bkm = tasks[tiles[ti].x].b_kmajor;
       int ti2 = ti, sgi2 = sgi, k02 = k0;
       const bool have2 = advance(ti2, sgi2, k02);
       if (have2) fetch(ti2, sgi2, k02, na_, nb_);
@@ -645,7 +674,8 @@ __global__ void __launch_bounds__(XTHREADS, 1)
       }
 #pragma unroll
       for (int j = 0; j < NB; ++j) {
-        const int e = gtid + j * GT, n = e % XN, k = e / XN;
+        int n, k;
+        b_coords(gtid + j * GT, bkm, n, k);
 #pragma unroll
         for (int p = 0; p < 4; ++p)
           st_bf2(st + 4 * PLANE_BYTES + p * (64 * 128), n, 2 * k, sbyte(wb[j], p), sbyte(wb[j], 4 + p));
@@ -843,25 +873,14 @@ void launch_wait_selftest(unsigned polls, int* status, cudaStream_t s) {
   wait_selftest_kernel<<<1, 32, 0, s>>>(polls, status);
 }
 
-void launch_digits(const DigitOp* ops, int nops, const int2* jobs, int njobs, unsigned long long* maxv, int* exps,
-                   int g0, int g1, const Bases4& B, cudaStream_t s) {
+void launch_digits(const DigitOp* ops, int nops, const int2* jobs, int njobs, unsigned* tags, int* exps,
+                   unsigned epoch, const Bases4& B, cudaStream_t s) {
   if (nops <= 0) return;
-  const size_t sm = DIGIT_SLOTS * sizeof(unsigned long long);
-  static const bool init = [sm] {  // once per process, thread-safe (function-local static)
-    cudaFuncSetAttribute(digit_max_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    return true;
-  }();
-  (void)init;
-  const int n = g1 - g0;
-  if (n > 0) cudaMemsetAsync(maxv + g0, 0, (size_t)n * sizeof(unsigned long long), s);
+  const size_t sm = DIGIT_SLOTS * sizeof(unsigned);
   note_launch();
-  digit_max_kernel<<<nops, 256, sm, s>>>(ops, B, maxv);
-  if (n > 0) {
-    note_launch();
-    digit_exp_kernel<<<(n + 255) / 256 < 1184 ? (n + 255) / 256 : 1184, 256, 0, s>>>(maxv + g0, exps + g0, n);
-  }
+  digit_max_kernel<<<nops, 256, sm, s>>>(ops, B, tags, epoch);
   note_launch();
-  digit_convert_kernel<<<njobs, 256, 0, s>>>(ops, jobs, B, exps);
+  digit_convert_kernel<<<njobs, 256, 0, s>>>(ops, jobs, B, tags, epoch, exps);
 }
 
 }  // namespace tdvp
