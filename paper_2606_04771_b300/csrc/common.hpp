@@ -89,6 +89,9 @@ struct LincombTask {
   cplx* out;
   int rows, cols, ld_out;
   int term_begin, term_count;
+  // optional: the BF16x4 exponent tags of the output's rows (one per row, row r at
+  // tags[r]), raised to the launch's epoch and the rows' largest binary exponents
+  unsigned* tags;
 };
 
 struct LincombTerm {

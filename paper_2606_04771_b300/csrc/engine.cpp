@@ -342,28 +342,43 @@ void GemmPlan::plan_packed(cudaStream_t s) {
   ddops_d = upload(dops_d, s);
   djb_d = upload(djobs_d, s);
   static_done = false;
+  // dynamic operands that each hold whole scale lines (an A source spanning all K
+  // columns, a B source all K rows) are split by one fused kernel
+  bool own = true;
+  for (const DigitOp& o : dops_d) {
+    const int K = o.dig_ld;  // row-major A and K-major B records: lines of length K
+    const bool whole = o.side == 0 ? (o.col0 == 0 && o.cols == K) : (o.row0 == 0 && o.rows == K);
+    if (!whole || (o.side == 0 ? o.rows : o.cols) > digit_slots()) own = false;
+  }
+  dyn_mode = dyn_tags_external ? 1 : (own ? 2 : 0);
   std::vector<int> cost(nt, 0);
   for (int i = 0; i < nt; ++i) cost[i] = (segs[tasks[i].seg_begin].k + 31) / 32;
   std::stable_sort(tiles.begin(), tiles.end(), [&](const int3& x, const int3& y) { return cost[x.x] > cost[y.x]; });
 }
 
-void GemmPlan::launch(cudaStream_t s, const Bases4& B) const {
+unsigned GemmPlan::begin_split(cudaStream_t s, const Bases4& B) const {
+  if (epoch + 2 > DIGIT_EPOCH_MAX) {  // the tag counter wraps: clear every tag, split all again
+    TDVP_CUDA(cudaMemsetAsync(dtag.p, 0, std::max(ngrp, 1) * sizeof(unsigned), s));
+    epoch = 0;
+    static_done = false;
+  }
+  if (!static_done) {  // environment operands: split once per plan
+    launch_digits(ddops_s.as<DigitOp>(), (int)dops_s.size(), djb_s.as<int2>(), (int)djobs_s.size(),
+                  dtag.as<unsigned>(), dexp.as<int>(), ++epoch, B, s);
+    static_done = true;
+  }
+  return ++epoch;
+}
+
+void GemmPlan::launch(cudaStream_t s, const Bases4& B, unsigned ep) const {
   if (kind < 0)
     launch_gemm_fp64(dt.as<GemmTask>(), ds.as<GemmSeg>(), dti.as<int3>(), (int)tiles.size(), B, s);
   else {
     if (kind == 1) {
-      if (epoch + 2 > DIGIT_EPOCH_MAX) {  // the tag counter wraps: clear every tag, split all again
-        TDVP_CUDA(cudaMemsetAsync(dtag.p, 0, std::max(ngrp, 1) * sizeof(unsigned), s));
-        epoch = 0;
-        static_done = false;
-      }
-      if (!static_done) {  // environment operands: split once per plan
-        launch_digits(ddops_s.as<DigitOp>(), (int)dops_s.size(), djb_s.as<int2>(), (int)djobs_s.size(),
-                      dtag.as<unsigned>(), dexp.as<int>(), ++epoch, B, s);
-        static_done = true;
-      }
+      const unsigned e = ep ? ep : begin_split(s, B);
+      const int mode = dyn_mode == 1 && !ep ? 0 : dyn_mode;  // no producer raised the tags: both passes
       launch_digits(ddops_d.as<DigitOp>(), (int)dops_d.size(), djb_d.as<int2>(), (int)djobs_d.size(),
-                    dtag.as<unsigned>(), dexp.as<int>(), ++epoch, B, s);
+                    dtag.as<unsigned>(), dexp.as<int>(), e, B, s, mode);
     }
     launch_gemm_split(kind, dt.as<GemmTask>(), ds.as<GemmSeg>(), dti.as<int3>(), (int)tiles.size(), dexp.as<int>(),
                       B, status, s);
@@ -381,8 +396,8 @@ void LincombPlan::finalize(cudaStream_t s) {
   dc = upload(chunks, s);
 }
 
-void LincombPlan::launch(cudaStream_t s) const {
-  launch_lincomb(dt.as<LincombTask>(), dm.as<LincombTerm>(), dc.as<int2>(), (int)chunks.size(), s);
+void LincombPlan::launch(cudaStream_t s, unsigned epoch) const {
+  launch_lincomb(dt.as<LincombTask>(), dm.as<LincombTerm>(), dc.as<int2>(), (int)chunks.size(), s, epoch);
 }
 
 void CopyPlan::finalize(cudaStream_t s) {
@@ -400,8 +415,14 @@ void CopyPlan::launch(cudaStream_t s) const { launch_copy(dt.as<CopyTask>(), dc.
 void HeffPlan::apply(const cplx* in, cplx* out, cudaStream_t s) const {
   Bases4 B{{0, reinterpret_cast<uintptr_t>(in), reinterpret_cast<uintptr_t>(out), 0}};
   g1.launch(s, B);
-  lc.launch(s);
-  g3.launch(s, B);
+  if (g3.dyn_mode == 1) {  // the linear combination raises the stage-3 operand's exponent tags
+    const unsigned e = g3.begin_split(s, B);
+    lc.launch(s, e);
+    g3.launch(s, B, e);
+  } else {
+    lc.launch(s);
+    g3.launch(s, B);
+  }
 }
 
 // a Jacobi driver's sweep count, or the CUDA error of a failed cooperative launch
@@ -1344,8 +1365,20 @@ void Engine::plan_heff2_packed(HeffPlan& p, const BTensor& Lenv, const BTensor& 
     }
   }
   p.g1.finalize(stream_, gemm_kind_, dstatus_ + 1);
-  p.lc.finalize(stream_);
+  p.g3.dyn_tags_external = true;
   p.g3.finalize(stream_, gemm_kind_, dstatus_ + 1);
+  {  // the linear combination raises the exponent tags of the stage-3 operand's rows
+    std::map<int, int> task_of;
+    int ti = 0;
+    for (int bp = 0; bp < nsr; ++bp)
+      if (!oby[bp].empty()) task_of[bp] = ti++;
+    for (int id = 0; id < (int)t2keys.size(); ++id) {
+      const auto& k = t2keys[id];
+      const int ob = theta.find(bkey(k[0], k[1], k[2], k[3], k[4]));
+      p.lc.tasks[id].tags = p.g3.tags() + p.g3.tasks[task_of.at(k[4])].roff + orow[ob];
+    }
+  }
+  p.lc.finalize(stream_);
 }
 
 void Engine::plan_heff2(HeffPlan& p, const BTensor& Lenv, const BTensor& Renv, const BTensor& theta,
@@ -1886,9 +1919,13 @@ int Engine::expm(HeffPlan& H, cplx* x, double tau) {
   launch_krylov_init(st, nrm, stream_);
   launch_scale(x, &st->beta0, V, n, done, stream_);
   KrylovState* hst = reinterpret_cast<KrylovState*>(pinned_);
-  int* hdone = &hst->done;
-  int k = 0;
-  for (; k < kmax; ++k) {
+  // For small problems the host's round trip per iteration costs more than the
+  // iteration itself, so up to KRYLOV_BATCH iterations are queued before the host reads
+  // the flags: iterations queued after convergence do nothing in the Lanczos kernels
+  // (they test the done flag) and their H_eff products only overwrite the scratch
+  // vector.  Large problems read the flags after every iteration.
+  const int batch = n <= KRYLOV_BATCH_N ? KRYLOV_BATCH : 1;
+  for (int k = 0; k < kmax; ++k) {
     cplx* vk = V + (long long)k * n;
     H.apply(vk, w, stream_);
     launch_dots(V, n, k + 1, w, n, part, G, h1, done, stream_);
@@ -1898,14 +1935,16 @@ int Engine::expm(HeffPlan& H, cplx* x, double tau) {
     launch_dots(w, 0, 1, w, n, part, G, nrm, done, stream_);
     launch_krylov_step(st, h1, nrm, tau, opt_.krylov_tol, kmax, stream_);
     launch_scale(w, &st->beta[k], V + (long long)(k + 1) * n, n, done, stream_);
-    TDVP_CUDA(cudaMemcpyAsync(hdone, done, 2 * sizeof(int), cudaMemcpyDeviceToHost, stream_));
+    if ((k + 1) % batch != 0 && k + 1 < kmax) continue;
+    // k, nv, done, bad
+    TDVP_CUDA(cudaMemcpyAsync(&hst->k, &st->k, 4 * sizeof(int), cudaMemcpyDeviceToHost, stream_));
     TDVP_CUDA(cudaStreamSynchronize(stream_));
-    stats_.matvecs += 1;
-    stats_.heff_flops += H.flops();
     if (hst->bad) throw Error(-4, "non-finite value in the Krylov recurrence");
-    if (*hdone) break;
+    if (hst->done) break;
   }
-  const int used = std::min(k + 1, kmax);
+  const int used = hst->k;  // matvecs whose results the recurrence took
+  stats_.matvecs += used;
+  stats_.heff_flops += (long long)used * H.flops();
   stats_.max_krylov = std::max(stats_.max_krylov, used);
   launch_combine(V, n, &st->nv, st->coef, &st->beta0, x, n, stream_);
   return used;

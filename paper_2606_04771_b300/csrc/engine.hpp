@@ -142,10 +142,20 @@ struct GemmPlan {
   long long bytes = 0;  // algorithmic bytes: every operand block read once, output written once
   int kind = -1;        // -1 FP64 CUDA cores, 0 3xTF32, 1 BF16x3 tensor cores
   int* status = nullptr;
+  // BF16x4 split of the dynamic operands: 0 two passes; 1 their exponent tags are set
+  // by the kernel that produces them (the caller passes the epoch of begin_split);
+  // 2 every dynamic operand holds whole scale lines (one fused kernel)
+  int dyn_mode = 0;
+  bool dyn_tags_external = false;  // set by the planner before finalize: mode 1
   void finalize(cudaStream_t s, int kind_ = -1, int* status_ = nullptr);
   void plan_digits(cudaStream_t s);
   void plan_packed(cudaStream_t s);
-  void launch(cudaStream_t s, const Bases4& B) const;
+  // BF16x4: split the static operands if not done yet and return the epoch of the
+  // next dynamic split (clearing the tags when the counter would wrap)
+  unsigned begin_split(cudaStream_t s, const Bases4& B) const;
+  // epoch: 0, or the value begin_split returned (dynamic tags raised by the producer)
+  void launch(cudaStream_t s, const Bases4& B, unsigned epoch = 0) const;
+  unsigned* tags() const { return dtag.as<unsigned>(); }
 };
 
 struct LincombPlan {
@@ -155,7 +165,7 @@ struct LincombPlan {
   DevBuf dt, dm, dc;
   long long bytes = 0;  // algorithmic bytes moved
   void finalize(cudaStream_t s);
-  void launch(cudaStream_t s) const;
+  void launch(cudaStream_t s, unsigned epoch = 0) const;
 };
 
 struct CopyPlan {

@@ -132,13 +132,24 @@ void launch_gemm_fp64(const GemmTask* tasks, const GemmSeg* segs, const int3* ti
 // K3: MPO linear combination  out = sum coef * in
 // ---------------------------------------------------------------------------
 
+// With tags, every chunk also raises the exponent tags of its rows for the BF16x4
+// split of the output (epoch in bits 12-31, the largest biased exponent of max(|Re|,
+// |Im|) in bits 0-11; zeros leave a row's tag alone): the rows of a chunk are reduced
+// in shared memory first, then merged with one atomicMax per row.
 __global__ void __launch_bounds__(256) lincomb_kernel(const LincombTask* __restrict__ tasks,
                                                       const LincombTerm* __restrict__ terms,
-                                                      const int2* __restrict__ chunks) {
+                                                      const int2* __restrict__ chunks, unsigned epoch) {
+  __shared__ unsigned rmax[LINCOMB_CHUNK];
   const int2 ch = chunks[blockIdx.x];
   const LincombTask t = tasks[ch.x];
   const int n = t.rows * t.cols;
-  for (int e = ch.y + threadIdx.x; e < min(n, ch.y + LINCOMB_CHUNK); e += 256) {
+  const int e1 = min(n, ch.y + LINCOMB_CHUNK);
+  const int r_first = ch.y / t.cols, r_last = (e1 - 1) / t.cols;
+  if (t.tags) {
+    for (int i = threadIdx.x; i <= r_last - r_first; i += 256) rmax[i] = 0u;
+    __syncthreads();
+  }
+  for (int e = ch.y + threadIdx.x; e < e1; e += 256) {
     int r = e / t.cols, c = e - r * t.cols;
     cplx acc = {0.0, 0.0};
     for (int k = 0; k < t.term_count; ++k) {
@@ -148,14 +159,24 @@ __global__ void __launch_bounds__(256) lincomb_kernel(const LincombTask* __restr
       acc.y = fma(tm.coef, v.y, acc.y);
     }
     t.out[(long long)r * t.ld_out + c] = acc;
+    if (t.tags) {
+      const unsigned ex =
+          (unsigned)(((unsigned long long)__double_as_longlong(fmax(fabs(acc.x), fabs(acc.y))) >> 52) & 0x7FF);
+      if (ex) atomicMax(&rmax[r - r_first], ex);
+    }
+  }
+  if (t.tags) {
+    __syncthreads();
+    for (int i = threadIdx.x; i <= r_last - r_first; i += 256)
+      if (rmax[i]) atomicMax(&t.tags[r_first + i], (epoch << 12) | rmax[i]);
   }
 }
 
 void launch_lincomb(const LincombTask* tasks, const LincombTerm* terms, const int2* chunks, int nchunks,
-                    cudaStream_t s) {
+                    cudaStream_t s, unsigned epoch) {
   if (nchunks <= 0) return;
   note_launch();
-  lincomb_kernel<<<nchunks, 256, 0, s>>>(tasks, terms, chunks);
+  lincomb_kernel<<<nchunks, 256, 0, s>>>(tasks, terms, chunks, epoch);
 }
 
 // ---------------------------------------------------------------------------
@@ -1065,9 +1086,13 @@ static long long resident_limit() {
 // sector's pairs then run on the C SMs of its cluster, and clusters of 200 KiB CTAs
 // run in waves, while the cooperative form spreads every round's pairs over all SMs
 // (the FP64 stage suffers most, the B300's FP64 rate per SM being low).
-static bool cluster_enabled() {
+// TDVP_JACOBI_CLUSTER=32 enables it for the FP32 preconditioner only (the FP64 stage
+// keeps the cooperative grid, whose rounds use every SM's FP64 units).
+static bool cluster_enabled(bool fp32) {
   const char* e = std::getenv("TDVP_JACOBI_CLUSTER");
-  return e && e[0] == '1';
+  if (!e) return false;
+  if (e[0] == '1') return true;
+  return fp32 && e[0] == '3' && e[1] == '2';
 }
 
 // Smallest cluster size (2, 4 or 8 CTAs) whose slices hold every sector of the call
@@ -1118,7 +1143,7 @@ static int coop_run(const Task* d_tasks, const std::vector<Task>& h_tasks, int m
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute cl_attr[1];
   auto cl_kern = jacobi_cluster_kernel<Task, S, C2>;
-  if (!all_fit && cluster_enabled()) {
+  if (!all_fit && cluster_enabled(sizeof(S) == 4)) {
     cl_size = cluster_size_for<Task, C2>(h_tasks, &cl_smem);
     if (cl_size > 0) {
       static const bool attr = [] {  // once per process, thread-safe (function-local static)

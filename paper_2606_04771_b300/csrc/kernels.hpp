@@ -16,6 +16,10 @@ long long launch_count();
 
 constexpr int LINCOMB_CHUNK = 1024;  // elements per CTA in lincomb / copy
 constexpr int KRYLOV_MAX = 32;       // one warp holds the Krylov coefficients
+// Krylov vectors of at most KRYLOV_BATCH_N complex elements: KRYLOV_BATCH iterations are
+// queued between two reads of the convergence flags by the host
+constexpr long long KRYLOV_BATCH_N = 1 << 16;
+constexpr int KRYLOV_BATCH = 4;
 
 // Device-resident Krylov state: the host launches the loop without reading it
 // until the end (kernels return immediately once done is set).
@@ -33,8 +37,9 @@ struct KrylovState {
 
 void launch_gemm_fp64(const GemmTask* tasks, const GemmSeg* segs, const int3* tiles, int ntiles, const Bases4& B,
                       cudaStream_t s);
+// epoch: the BF16x4 split epoch the output row tags are raised to (tasks with tags)
 void launch_lincomb(const LincombTask* tasks, const LincombTerm* terms, const int2* chunks, int nchunks,
-                    cudaStream_t s);
+                    cudaStream_t s, unsigned epoch = 0);
 void launch_copy(const CopyTask* tasks, const int2* chunks, int nchunks, cudaStream_t s);
 
 // split-precision tensor-core GEMM (split.cu); kind 0 = 3xTF32 (FP32 accumulation),
@@ -48,11 +53,15 @@ void launch_gemm_split(int kind, const GemmTask* tasks, const GemmSeg* segs, con
 // digit records and exponents.  jobs = (operand, first element) in steps of
 // digit_job_size() elements.  tags start at zero; epoch runs 1 .. 2^20 - 1.
 int digit_job_size();
+int digit_slots();  // longest scale line the fused split handles
 constexpr unsigned DIGIT_EPOCH_MAX = (1u << 20) - 1;
 // one bounded wait on an mbarrier that never completes; adds 1 to *status on expiry
 void launch_wait_selftest(unsigned polls, int* status, cudaStream_t s);
+// mode 0: both passes; 1: the tags of this epoch are already set (conversion only);
+// 2: every operand holds whole rows (A) / columns (B) of its group, so one kernel per
+// operand finds its exponents in shared memory and converts (the tags are not used)
 void launch_digits(const DigitOp* ops, int nops, const int2* jobs, int njobs, unsigned* tags, int* exps,
-                   unsigned epoch, const Bases4& B, cudaStream_t s);
+                   unsigned epoch, const Bases4& B, cudaStream_t s, int mode = 0);
 
 int dots_grid(long long n);
 void launch_dots(const cplx* V, long long pitch, int nv, const cplx* w, long long n, cplx* partial, int G, cplx* out,

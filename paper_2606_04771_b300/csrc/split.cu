@@ -348,9 +348,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // ---------------------------------------------------------------------------
 
 constexpr int XN = 64;                  // complex columns per tile
-constexpr int XSTAGE = 4 * PLANE_BYTES + 4 * (64 * 128);  // 4 A planes (128 rows) + 4 B planes (64 rows)
-constexpr int XSTAGES = 2;              // 192 KB of stages: one persistent CTA per SM
-constexpr int XKC = 32;                 // complex k per chunk (64 bf16 = one 128-byte row)
+constexpr int XKC = 16;                 // complex k per chunk (32 bf16 = one 64-byte row)
+constexpr int XA_PLANE = 128 * 64;      // one A digit plane: 128 embedded rows x 64 bytes
+constexpr int XB_PLANE = 64 * 64;       // one B digit plane: 64 rows x 64 bytes
+constexpr int XSTAGE = 4 * XA_PLANE + 4 * XB_PLANE;  // 48 KB: 4 A planes + 4 B planes
+constexpr int XSTAGES = 4;              // 192 KB of stages: one persistent CTA per SM
 constexpr int XPROD = 256;              // producer threads (warps 0-7)
 constexpr int XMMA_WARP = XPROD / 32;   // MMA issuer warp (8)
 constexpr int XEPI = 256;               // epilogue threads (warps 9-16, two per TMEM lane quarter)
@@ -416,6 +418,27 @@ __device__ __forceinline__ void digits4(int X, float* d) {
 
 __device__ __forceinline__ void st_bf2(uint8_t* plane, int row, int kk, float v0, float v1) {
   *reinterpret_cast<__nv_bfloat162*>(plane + sw_off2(row, kk)) = __floats2bfloat162_rn(v0, v1);
+}
+
+// K-major tiles with 64-byte rows (32 bf16) in the 64-byte swizzle: the 16-byte chunk
+// index of a row is XORed with (row / 2) mod 4 (the address bits 7-8 folded onto bits
+// 4-5); 8-row groups are 512 bytes apart
+__device__ __forceinline__ uint32_t sw64_off2(int row, int kk) {
+  return row * 64 + ((((kk >> 3) ^ (row >> 1)) & 3) << 4) + ((kk & 7) << 1);
+}
+
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;              // leading-dimension offset (unused for this layout)
+  d |= (uint64_t)(512 >> 4) << 32;     // stride between 8-row groups
+  d |= (uint64_t)1 << 46;              // descriptor version for this architecture
+  d |= (uint64_t)4 << 61;              // 64-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void st_bf2_64(uint8_t* plane, int row, int kk, float v0, float v1) {
+  *reinterpret_cast<__nv_bfloat162*>(plane + sw64_off2(row, kk)) = __floats2bfloat162_rn(v0, v1);
 }
 
 template <int NCOL>
@@ -534,6 +557,53 @@ __global__ void __launch_bounds__(256) digit_convert_kernel(const DigitOp* __res
     const long long at = o.kmajor ? (long long)(o.col0 + c) * o.dig_ld + o.row0 + r
                                   : (long long)(o.row0 + r) * o.dig_ld + o.col0 + c;
     o.dig[at] = pack_digits(v.x, v.y, ex);
+  }
+}
+
+// Both passes in one kernel for an operand that holds whole rows (A) / columns (B) of
+// its scale group (every element of such a line is in this operand): one CTA per
+// operand reduces the line exponents in shared memory, then converts every element
+// and stores the line exponents.  The lines have at most DIGIT_SLOTS entries.
+__global__ void __launch_bounds__(256) digit_split_own_kernel(const DigitOp* __restrict__ ops, const Bases4 B,
+                                                              int* __restrict__ exps) {
+  const DigitOp o = ops[blockIdx.x];
+  const cplx* src = rebase(B, o.base, o.src);
+  extern __shared__ unsigned slot[];
+  const int nslot = o.side == 0 ? o.rows : o.cols;
+  const double sa = (o.side == 0 && o.alpha != 1.0) ? fabs(o.alpha) : 1.0;
+  for (int i = threadIdx.x; i < nslot; i += 256) slot[i] = 0u;
+  __syncthreads();
+  const long long n = (long long)o.rows * o.cols;
+  const int inner = o.op == OP_N ? o.cols : o.rows;
+  for (long long e = threadIdx.x; e < n; e += 256) {
+    const int outer = (int)(e / inner), in = (int)(e - (long long)outer * inner);
+    const cplx v = src[(long long)outer * o.ld + in];
+    const int r = o.op == OP_N ? outer : in, c = o.op == OP_N ? in : outer;
+    const unsigned ex = biased_exp(sa * fmax(fabs(v.x), fabs(v.y)));
+    if (ex) atomicMax(&slot[o.side == 0 ? r : c], ex);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nslot; i += 256)
+    exps[o.grp + (o.side == 0 ? o.row0 : o.col0) + i] = slot[i] ? (int)slot[i] - 1022 : -2000;
+  for (long long e = threadIdx.x; e < n; e += 256) {
+    int r, c;
+    if (o.kmajor) {
+      c = (int)(e / o.rows);
+      r = (int)(e - (long long)c * o.rows);
+    } else {
+      r = (int)(e / o.cols);
+      c = (int)(e - (long long)r * o.cols);
+    }
+    cplx v = o.op == OP_N ? src[(long long)r * o.ld + c] : src[(long long)c * o.ld + r];
+    if (o.op != OP_N) v.y = -v.y;
+    if (o.alpha != 1.0) {
+      v.x *= o.alpha;
+      v.y *= o.alpha;
+    }
+    const unsigned ex = slot[o.side == 0 ? r : c];
+    const long long at = o.kmajor ? (long long)(o.col0 + c) * o.dig_ld + o.row0 + r
+                                  : (long long)(o.row0 + r) * o.dig_ld + o.col0 + c;
+    o.dig[at] = pack_digits(v.x, v.y, ex ? (int)ex - 1022 : -2000);
   }
 }
 
@@ -659,17 +729,23 @@ __global__ void __launch_bounds__(XTHREADS, 1)
       const int s = it % XSTAGES;
       if (!mbar_wait(&empty_bar[s], ((it / XSTAGES) & 1) ^ 1, verr)) break;
       uint8_t* st = stage_base + (size_t)s * XSTAGE;
-      // A: 64 complex rows x 32 complex k -> 4 digit planes of 128 rows x 64 bf16,
-      // B: 32 complex k x 64 complex n -> 4 digit planes of 64 rows x 64 bf16
+      // A: 64 complex rows x 16 complex k -> 4 digit planes of 128 rows x 32 bf16,
+      // B: 16 complex k x 64 complex n -> 4 digit planes of 64 rows x 32 bf16.  A half
+      // warp fills one 64-byte row; the upper half warp writes its two embedded rows in
+      // the other order, so that each store instruction touches two rows 3 apart (the
+      // two halves of the 128 banks' worth) rather than 2 apart (the same banks).
 #pragma unroll
       for (int j = 0; j < NA; ++j) {
         const int e = gtid + j * GT, m = e / XKC, k = e % XKC;
+        const bool up = (lane >> 4) & 1;
+        const int r0 = 2 * m + (up ? 1 : 0), r1 = 4 * m + 1 - r0;
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
           const float re = sbyte(wa[j], p), im = sbyte(wa[j], 4 + p);
-          uint8_t* pl = st + p * PLANE_BYTES;
-          st_bf2(pl, 2 * m, 2 * k, re, -im);
-          st_bf2(pl, 2 * m + 1, 2 * k, im, re);
+          uint8_t* pl = st + p * XA_PLANE;
+          // row 2m holds (re, -im), row 2m+1 holds (im, re)
+          st_bf2_64(pl, r0, 2 * k, up ? im : re, up ? re : -im);
+          st_bf2_64(pl, r1, 2 * k, up ? re : im, up ? -im : re);
         }
       }
 #pragma unroll
@@ -678,7 +754,7 @@ __global__ void __launch_bounds__(XTHREADS, 1)
         b_coords(gtid + j * GT, bkm, n, k);
 #pragma unroll
         for (int p = 0; p < 4; ++p)
-          st_bf2(st + 4 * PLANE_BYTES + p * (64 * 128), n, 2 * k, sbyte(wb[j], p), sbyte(wb[j], 4 + p));
+          st_bf2_64(st + 4 * XA_PLANE + p * XB_PLANE, n, 2 * k, sbyte(wb[j], p), sbyte(wb[j], 4 + p));
       }
       fence_proxy_async();
       __syncwarp();
@@ -716,18 +792,18 @@ __global__ void __launch_bounds__(XTHREADS, 1)
             }
             tc_fence_after();
             const uint32_t st = smem_u32(stage_base + (size_t)s * XSTAGE);
-            // 4 k-steps of 16 bf16 (8 complex k, 32 bytes); the last chunk of a
+            // 2 k-steps of 16 bf16 (8 complex k, 32 bytes); the last chunk of a
             // segment issues only the steps that hold data
-            const int nks = min(4, (kk - k0 + 7) >> 3);
+            const int nks = min(2, (kk - k0 + 7) >> 3);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < 2; ++q) {
               if (q >= nks) break;
               const uint32_t koff = q * 32;
               uint64_t a[4], b[4];
 #pragma unroll
               for (int p = 0; p < 4; ++p) {
-                a[p] = sw128_desc(st + p * PLANE_BYTES + koff);
-                b[p] = sw128_desc(st + 4 * PLANE_BYTES + p * (64 * 128) + koff);
+                a[p] = sw64_desc(st + p * XA_PLANE + koff);
+                b[p] = sw64_desc(st + 4 * XA_PLANE + p * XB_PLANE + koff);
               }
 #pragma unroll
               for (int o = 0; o < 4; ++o) {
@@ -867,6 +943,7 @@ void launch_gemm_split(int kind, const GemmTask* tasks, const GemmSeg* segs, con
 }
 
 int digit_job_size() { return DIGIT_JOB; }
+int digit_slots() { return DIGIT_SLOTS; }
 
 void launch_wait_selftest(unsigned polls, int* status, cudaStream_t s) {
   note_launch();
@@ -874,11 +951,18 @@ void launch_wait_selftest(unsigned polls, int* status, cudaStream_t s) {
 }
 
 void launch_digits(const DigitOp* ops, int nops, const int2* jobs, int njobs, unsigned* tags, int* exps,
-                   unsigned epoch, const Bases4& B, cudaStream_t s) {
+                   unsigned epoch, const Bases4& B, cudaStream_t s, int mode) {
   if (nops <= 0) return;
   const size_t sm = DIGIT_SLOTS * sizeof(unsigned);
-  note_launch();
-  digit_max_kernel<<<nops, 256, sm, s>>>(ops, B, tags, epoch);
+  if (mode == 2) {
+    note_launch();
+    digit_split_own_kernel<<<nops, 256, sm, s>>>(ops, B, exps);
+    return;
+  }
+  if (mode == 0) {
+    note_launch();
+    digit_max_kernel<<<nops, 256, sm, s>>>(ops, B, tags, epoch);
+  }
   note_launch();
   digit_convert_kernel<<<njobs, 256, 0, s>>>(ops, jobs, B, tags, epoch, exps);
 }
