@@ -72,6 +72,11 @@ typedef struct {
                               whose per-state weights s^2 agree to this relative tolerance
                               (degenerate multiplets are kept or dropped together; see
                               tdvp_truncate); 0 = off; default 1e-8 */
+  int merge_launches;      /* != 0: this context's BF16x4 block GEMMs go out in launches
+                              shared with the other merging contexts on the device that
+                              launch at the same moment (several served requests' H_eff
+                              stages in one grouped launch); results are unchanged, bit for
+                              bit; default 0 */
 } tdvp_opts;
 
 /* Environment: when every sector of a split has at most 32 columns and a working
@@ -254,6 +259,35 @@ int tdvp_set_tensor(tdvp_ctx* ctx, int which, const double* data, long long n, i
  * result is complete.  Errors: TDVP_EINVAL, TDVP_ESTATE, TDVP_ECUDA. */
 int tdvp_heff_apply(tdvp_ctx* ctx, int bond, const double* psi_in, double* psi_out, int on_device);
 
+/* ---- one H_eff.psi over several GPUs (Sec. S2.3, "GPU acceleration": the
+ * block products are spread over the GPUs with greedy load balancing) ---------
+ * The last GEMM stage of the product writes each output block from one task; the
+ * tasks (output groups) are the units that ranks share out.  Each rank computes the
+ * first stages in full and the output groups it owns (tdvp_heff_apply_owned); the
+ * ranks then exchange their output blocks (an all-gather), and every rank holds
+ * the whole psi_out for its replicated Lanczos recurrence.  The partition and the
+ * exchange are in the Python binding (paper_2606_04771_b300/shard.py).
+ *
+ * tdvp_heff_groups: *ngroups receives the number of output groups of the context's
+ * H_eff (which = 0 of a bond problem, or chain bond (0,1)); flops[g] (nullable,
+ * ngroups entries) their algorithmic flops; block_group[b] (nullable, one entry per
+ * block of the tdvp_block_list layout) the group that writes output block b.
+ * Errors: TDVP_EINVAL, TDVP_ESTATE. */
+int tdvp_heff_groups(tdvp_ctx* ctx, int* ngroups, long long* flops, int* block_group);
+
+/* Greedy longest-processing-time partition of n units with costs cost[0..n) over
+ * nranks ranks: units in descending cost (ties by index) each go to the rank with
+ * the least load so far (ties to the lowest rank).  owner[i] receives the rank of
+ * unit i; load (nullable, nranks entries) the summed cost per rank.  Host only (no
+ * device is touched).  Errors: TDVP_EINVAL (n < 0, nranks < 1, NULL, cost < 0). */
+int tdvp_partition(int n, const double* cost, int nranks, int* owner, double* load);
+
+/* psi_out = H_eff psi_in restricted to the output groups g with group_owner[g] ==
+ * rank: the blocks of the other groups in psi_out are left as they were.  Device
+ * pointers only (on_device must be 1); layout and errors as tdvp_heff_apply. */
+int tdvp_heff_apply_owned(tdvp_ctx* ctx, int bond, const int* group_owner, int rank, const double* psi_in,
+                          double* psi_out, int on_device);
+
 /* psi_out = exp(-i tau H_eff) psi_in with the engine's Krylov exponential
  * (Sec. S2.2): Lanczos with full re-orthogonalisation applied twice, FP64
  * vectors, exp(-i tau T_k) e_1 from a scaled Taylor series on the GPU, stopped
@@ -344,6 +378,12 @@ int tdvp_truncate(int nsec, const int* r, const int* mult, const double* sv, dou
  * stream is a cudaStream_t or NULL; the call returns after the result is
  * complete.  Errors: TDVP_EINVAL, TDVP_ENUMERIC, TDVP_ECUDA. */
 int tdvp_svd_noalloc(int p, int q, const double* a, double* s, double* u, double* vh, void* stream);
+
+/* Merged launches so far in the process (tdvp_opts.merge_launches): *launches
+ * receives the number of BF16x4 GEMM launches that carried more than one context's
+ * work, *slices the number of task lists they carried.  Either may be NULL (not
+ * both).  Errors: TDVP_EINVAL. */
+int tdvp_merge_count(long long* launches, long long* slices);
 
 /* Number of kernel launches this library has made in the process so far, over
  * every context and entry point (each launch site counts itself on the host

@@ -31,7 +31,7 @@ class TdvpError(RuntimeError):
 class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("krylov_max", C.c_int), ("krylov_tol", C.c_double),
                 ("timeout_ms", C.c_int), ("cuda_stream", C.c_void_p), ("device", C.c_int),
-                ("trunc_degeneracy", C.c_double)]
+                ("trunc_degeneracy", C.c_double), ("merge_launches", C.c_int)]
 
 
 class RequestC(C.Structure):
@@ -76,7 +76,11 @@ def lib():
             "tdvp_svd": (C.c_int, [C.c_int, C.c_int, vp, vp, vp, vp, C.c_int, vp]),
             "tdvp_svd_noalloc": (C.c_int, [C.c_int, C.c_int, vp, vp, vp, vp, vp]),
             "tdvp_truncate": (C.c_int, [C.c_int, vp, vp, vp, C.c_double, C.c_longlong, C.c_double, vp, vp, vp]),
+            "tdvp_heff_groups": (C.c_int, [vp, P(C.c_int), vp, vp]),
+            "tdvp_partition": (C.c_int, [C.c_int, vp, C.c_int, vp, vp]),
+            "tdvp_heff_apply_owned": (C.c_int, [vp, C.c_int, vp, C.c_int, vp, vp, C.c_int]),
             "tdvp_launch_count": (C.c_int, [P(C.c_longlong)]),
+            "tdvp_merge_count": (C.c_int, [P(C.c_longlong), P(C.c_longlong)]),
             "tdvp_selftest_wait": (C.c_int, [C.c_uint, vp]),
             "tdvp_destroy": (C.c_int, [vp]),
             "tdvp_save": (C.c_int, [vp, C.c_char_p, C.c_double]),
@@ -107,9 +111,11 @@ def check(rc):
         raise TdvpError(rc, lib().tdvp_last_error().decode())
 
 
-def make_opts(precision="fp64", krylov_max=20, krylov_tol=1e-12, stream=None, device=-1, trunc_degeneracy=None):
+def make_opts(precision="fp64", krylov_max=20, krylov_tol=1e-12, stream=None, device=-1, trunc_degeneracy=None,
+              merge_launches=False):
     o = Opts()
     lib().tdvp_opts_default(C.byref(o))
+    o.merge_launches = 1 if merge_launches else 0
     if trunc_degeneracy is not None:
         o.trunc_degeneracy = float(trunc_degeneracy)
     o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
@@ -170,6 +176,13 @@ def truncate(values, mults, eps, chi_max, degeneracy=0.0, stream=None):
     return kept, stats
 
 
+def merge_count():
+    """(launches that carried more than one context's GEMM work, task lists they carried)."""
+    a, b = C.c_longlong(), C.c_longlong()
+    check(lib().tdvp_merge_count(C.byref(a), C.byref(b)))
+    return a.value, b.value
+
+
 def launch_count():
     """Kernel launches this library has enqueued in the process so far."""
     n = C.c_longlong()
@@ -208,6 +221,29 @@ class _Ctx:
         po, do = _ptr(out)
         assert di == do
         check(lib().tdvp_heff_apply(self.h, 0, pi, po, di))
+        return out
+
+    def heff_groups(self):
+        """The output groups of the last GEMM stage: (flops per group, group of each
+        output block) as int64 / int32 arrays."""
+        ng = C.c_int()
+        check(lib().tdvp_heff_groups(self.h, C.byref(ng), None, None))
+        flops = np.zeros(ng.value, dtype=np.int64)
+        nb = C.c_longlong()
+        ne = C.c_longlong()
+        check(lib().tdvp_block_count(self.h, 0, C.byref(nb), C.byref(ne)))
+        bg = np.zeros(nb.value, dtype=np.int32)
+        check(lib().tdvp_heff_groups(self.h, C.byref(ng), flops.ctypes.data, bg.ctypes.data))
+        return flops, bg
+
+    def heff_apply_owned(self, owner, rank, psi, out):
+        """out = H_eff psi on the output groups g with owner[g] == rank (device tensors;
+        the other blocks of out are left as they were)."""
+        ow = np.ascontiguousarray(owner, dtype=np.int32)
+        pi, di = _ptr(psi)
+        po, do = _ptr(out)
+        assert di == 1 and do == 1, "device tensors"
+        check(lib().tdvp_heff_apply_owned(self.h, 0, ow.ctypes.data, int(rank), pi, po, 1))
         return out
 
     def krylov_expm(self, psi, out=None, tau=0.025):

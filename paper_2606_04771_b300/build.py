@@ -17,7 +17,7 @@ LIB = os.path.join(HERE, "libtdvp.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["kernels.cu", "split.cu", "noalloc.cu"]
-CPP_SOURCES = ["sym.cpp", "engine.cpp", "capi.cpp", "server.cpp"]
+CPP_SOURCES = ["sym.cpp", "engine.cpp", "capi.cpp", "server.cpp", "merge.cpp"]
 
 
 def sources():

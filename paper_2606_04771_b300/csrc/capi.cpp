@@ -2,6 +2,7 @@
 // marshalling and the translation of exceptions into status codes.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <string>
@@ -37,10 +38,17 @@ int guarded(F f) {
   }
 }
 
-// a call on a context: its device allocations are charged to the context
+// a call on a context: its device allocations are charged to the context, and its
+// BF16x4 GEMMs merge with other contexts' launches when the context asked for that
+struct MergeScope {
+  bool prev;
+  explicit MergeScope(bool on) : prev(tdvp::merge_launches_here()) { tdvp::merge_launches_here() = on; }
+  ~MergeScope() { tdvp::merge_launches_here() = prev; }
+};
 template <class F>
 int guarded(tdvp_ctx* ctx, F f) {
   tdvp::DevAcctScope scope(&ctx->acct);
+  MergeScope merge(ctx->eng && ctx->eng->opts().merge);
   return guarded(f);
 }
 
@@ -68,6 +76,7 @@ tdvp::Opts to_opts(const tdvp_opts* o) {
     r.stream = reinterpret_cast<cudaStream_t>(o->cuda_stream);
     r.device = o->device;
     r.trunc_degen = o->trunc_degeneracy;
+    r.merge = o->merge_launches != 0;
   }
   return r;
 }
@@ -107,6 +116,7 @@ void tdvp_opts_default(tdvp_opts* o) {
   o->cuda_stream = nullptr;
   o->device = -1;
   o->trunc_degeneracy = 1e-8;
+  o->merge_launches = 0;
 }
 
 int tdvp_create(int L, double J, double U, int symmetry, const tdvp_opts* opts, tdvp_ctx** out) {
@@ -243,6 +253,12 @@ int tdvp_selftest_wait(unsigned int polls, void* stream) {
   return TDVP_OK;
 }
 
+int tdvp_merge_count(long long* launches, long long* slices) {
+  if (!launches && !slices) return fail(TDVP_EINVAL, "NULL argument");
+  tdvp::merge_counts(launches, slices);
+  return TDVP_OK;
+}
+
 int tdvp_launch_count(long long* out) {
   if (!out) return fail(TDVP_EINVAL, "NULL argument");
   *out = tdvp::launch_count();
@@ -326,6 +342,64 @@ int tdvp_heff_apply(tdvp_ctx* ctx, int bond, const double* psi_in, double* psi_o
       TDVP_CUDA(cudaStreamSynchronize(s));
       e->check_status();
     }
+    TDVP_CUDA(cudaGetLastError());
+  });
+}
+
+int tdvp_heff_groups(tdvp_ctx* ctx, int* ngroups, long long* flops, int* block_group) {
+  if (!ctx || !ngroups) return fail(TDVP_EINVAL, "NULL argument");
+  return guarded(ctx, [&] {
+    tdvp::Engine* e = ctx->eng;
+    tdvp::HeffPlan& H = e->bond_only() ? e->heff_plan_bond() : e->chain_heff0();
+    const int ng = (int)H.g3.tasks.size();
+    *ngroups = ng;
+    if (flops)
+      for (int g = 0; g < ng; ++g) flops[g] = H.g3.task_flops[g];
+    if (block_group) {
+      const int nb = (int)e->theta_layout().blocks.size();
+      for (int b = 0; b < nb; ++b) block_group[b] = -1;
+      for (int g = 0; g < ng; ++g)
+        for (int b : H.g3.out_blocks[g]) block_group[b] = g;
+    }
+  });
+}
+
+int tdvp_partition(int n, const double* cost, int nranks, int* owner, double* load) {
+  if (n < 0 || nranks < 1 || (n > 0 && (!cost || !owner))) return fail(TDVP_EINVAL, "bad argument");
+  for (int i = 0; i < n; ++i)
+    if (!(cost[i] >= 0.0)) return fail(TDVP_EINVAL, "tdvp_partition: negative or NaN cost");
+  return guarded([&] {
+    // longest processing time first: units by cost descending (ties by index), each to
+    // the rank with the least load so far (ties to the lowest rank)
+    std::vector<int> ord(n);
+    for (int i = 0; i < n; ++i) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<double> l(nranks, 0.0);
+    for (int i : ord) {
+      int best = 0;
+      for (int r = 1; r < nranks; ++r)
+        if (l[r] < l[best]) best = r;
+      owner[i] = best;
+      l[best] += cost[i];
+    }
+    if (load)
+      for (int r = 0; r < nranks; ++r) load[r] = l[r];
+  });
+}
+
+int tdvp_heff_apply_owned(tdvp_ctx* ctx, int bond, const int* group_owner, int rank, const double* psi_in,
+                          double* psi_out, int on_device) {
+  if (!ctx || !group_owner || !psi_in || !psi_out) return fail(TDVP_EINVAL, "NULL argument");
+  if (bond != 0) return fail(TDVP_EINVAL, "bond must be 0");
+  if (!on_device) return fail(TDVP_EINVAL, "tdvp_heff_apply_owned takes device pointers");
+  return guarded(ctx, [&] {
+    tdvp::Engine* e = ctx->eng;
+    tdvp::HeffPlan& H = e->bond_only() ? e->heff_plan_bond() : e->chain_heff0();
+    std::vector<char> owned(H.g3.tasks.size());
+    for (size_t g = 0; g < owned.size(); ++g) owned[g] = group_owner[g] == rank;
+    H.apply_owned(reinterpret_cast<const tdvp::cplx*>(psi_in), reinterpret_cast<tdvp::cplx*>(psi_out), owned,
+                  e->stream());
+    e->check_status();
     TDVP_CUDA(cudaGetLastError());
   });
 }

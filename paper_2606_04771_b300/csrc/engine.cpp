@@ -370,9 +370,11 @@ unsigned GemmPlan::begin_split(cudaStream_t s, const Bases4& B) const {
   return ++epoch;
 }
 
-void GemmPlan::launch(cudaStream_t s, const Bases4& B, unsigned ep) const {
+void GemmPlan::launch(cudaStream_t s, const Bases4& B, unsigned ep, const int3* tsub, int nsub) const {
+  const int3* tl = tsub ? tsub : dti.as<int3>();
+  const int nt = tsub ? nsub : (int)tiles.size();
   if (kind < 0)
-    launch_gemm_fp64(dt.as<GemmTask>(), ds.as<GemmSeg>(), dti.as<int3>(), (int)tiles.size(), B, s);
+    launch_gemm_fp64(dt.as<GemmTask>(), ds.as<GemmSeg>(), tl, nt, B, s);
   else {
     if (kind == 1) {
       const unsigned e = ep ? ep : begin_split(s, B);
@@ -380,8 +382,11 @@ void GemmPlan::launch(cudaStream_t s, const Bases4& B, unsigned ep) const {
       launch_digits(ddops_d.as<DigitOp>(), (int)dops_d.size(), djb_d.as<int2>(), (int)djobs_d.size(),
                     dtag.as<unsigned>(), dexp.as<int>(), e, B, s, mode);
     }
-    launch_gemm_split(kind, dt.as<GemmTask>(), ds.as<GemmSeg>(), dti.as<int3>(), (int)tiles.size(), dexp.as<int>(),
-                      B, status, s);
+    if (kind == 1)
+      launch_exact_merged_or_alone(ExactSlice{dt.as<GemmTask>(), ds.as<GemmSeg>(), tl, dexp.as<int>(), status, B}, nt,
+                                   s);
+    else
+      launch_gemm_split(kind, dt.as<GemmTask>(), ds.as<GemmSeg>(), tl, nt, dexp.as<int>(), B, status, s);
   }
 }
 
@@ -411,6 +416,22 @@ void CopyPlan::finalize(cudaStream_t s) {
 }
 
 void CopyPlan::launch(cudaStream_t s) const { launch_copy(dt.as<CopyTask>(), dc.as<int2>(), (int)chunks.size(), s); }
+
+void HeffPlan::apply_owned(const cplx* in, cplx* out, const std::vector<char>& owned, cudaStream_t s) const {
+  if (owned.size() != g3.tasks.size()) throw Error(-1, "one ownership flag per output group");
+  std::vector<int3> sub;
+  for (const int3& t : g3.tiles)
+    if (owned[t.x]) sub.push_back(t);
+  DevBuf dsub(std::max<size_t>(sub.size(), 1) * sizeof(int3), s);
+  if (!sub.empty())
+    TDVP_CUDA(cudaMemcpyAsync(dsub.p, sub.data(), sub.size() * sizeof(int3), cudaMemcpyHostToDevice, s));
+  Bases4 B{{0, reinterpret_cast<uintptr_t>(in), reinterpret_cast<uintptr_t>(out), 0}};
+  g1.launch(s, B);
+  const unsigned e = g3.dyn_mode == 1 ? g3.begin_split(s, B) : 0u;
+  lc.launch(s, e);
+  g3.launch(s, B, e, dsub.as<int3>(), (int)sub.size());
+  TDVP_CUDA(cudaStreamSynchronize(s));  // the tile subset's buffer is freed on return
+}
 
 void HeffPlan::apply(const cplx* in, cplx* out, cudaStream_t s) const {
   Bases4 B{{0, reinterpret_cast<uintptr_t>(in), reinterpret_cast<uintptr_t>(out), 0}};
@@ -1348,6 +1369,8 @@ void Engine::plan_heff2_packed(HeffPlan& p, const BTensor& Lenv, const BTensor& 
     }
     p.g3.packed.push_back(std::move(pk));
     p.g3.tasks.push_back(t);
+    p.g3.out_blocks.push_back(oby[bp]);
+    p.g3.task_flops.push_back(0);
   }
   {
     std::map<int, int> task_of;  // output column sector -> stage-3 task
@@ -1362,6 +1385,7 @@ void Engine::plan_heff2_packed(HeffPlan& p, const BTensor& Lenv, const BTensor& 
       p.g3.packed[task_of.at(bp)].a.push_back(
           {t2ptr[id], 0, rows, cols, gk[bp], OP_N, 1.0, (int)orow[ob], segcol[bp].at({k[5], k[6]})});
       p.g3.flops += 8LL * rows * cols * br.s[bp].d;
+      p.g3.task_flops[task_of.at(bp)] += 8LL * rows * cols * br.s[bp].d;
     }
   }
   p.g1.finalize(stream_, gemm_kind_, dstatus_ + 1);
@@ -1495,6 +1519,7 @@ void Engine::plan_heff2(HeffPlan& p, const BTensor& Lenv, const BTensor& Renv, c
     t.seg_begin = (int)p.g3.segs.size();
     auto it = outsegs.find(std::make_tuple(o.key[0], o.key[1], o.key[2], o.key[3], o.key[4]));
     int cnt = 0;
+    long long tf = 0;
     if (it != outsegs.end()) {
       for (int id : it->second) {
         auto& k = t2keys[id];
@@ -1514,11 +1539,14 @@ void Engine::plan_heff2(HeffPlan& p, const BTensor& Lenv, const BTensor& Renv, c
         sg.alpha = 1.0;
         p.g3.segs.push_back(sg);
         p.g3.flops += 8LL * o.rows * rk.rows * rk.cols;
+        tf += 8LL * o.rows * rk.rows * rk.cols;
         ++cnt;
       }
     }
     t.seg_count = cnt;
     p.g3.tasks.push_back(t);
+    p.g3.out_blocks.push_back({ob});
+    p.g3.task_flops.push_back(tf);
   }
   p.g1.finalize(stream_, gemm_kind_, dstatus_ + 1);
   p.lc.finalize(stream_);

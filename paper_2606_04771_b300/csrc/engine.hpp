@@ -130,6 +130,10 @@ struct GemmPlan {
   std::vector<PackedTask> packed;
   std::vector<long long> rowoffs, row_start;
   DevBuf drow;
+  // output blocks (indices into the output tensor's block list) that each task
+  // writes, and its algorithmic flops: the units a multi-GPU matvec distributes
+  std::vector<std::vector<int>> out_blocks;
+  std::vector<long long> task_flops;
   // BF16x4: distinct operands (static: split at the first launch; dynamic: every
   // launch), their split jobs, digit records, group maxima and exponents
   std::vector<DigitOp> dops_s, dops_d;
@@ -153,8 +157,10 @@ struct GemmPlan {
   // BF16x4: split the static operands if not done yet and return the epoch of the
   // next dynamic split (clearing the tags when the counter would wrap)
   unsigned begin_split(cudaStream_t s, const Bases4& B) const;
-  // epoch: 0, or the value begin_split returned (dynamic tags raised by the producer)
-  void launch(cudaStream_t s, const Bases4& B, unsigned epoch = 0) const;
+  // epoch: 0, or the value begin_split returned (dynamic tags raised by the producer);
+  // tiles: a subset of the tile list (device array of n_tiles entries) or nullptr
+  void launch(cudaStream_t s, const Bases4& B, unsigned epoch = 0, const int3* tiles_subset = nullptr,
+              int n_subset = 0) const;
   unsigned* tags() const { return dtag.as<unsigned>(); }
 };
 
@@ -183,6 +189,9 @@ struct HeffPlan {
   LincombPlan lc;
   long long n = 0;  // vector length (complex); input is base 1, output base 2
   void apply(const cplx* in, cplx* out, cudaStream_t s) const;
+  // the whole product except the last stage's tasks outside `owned` (task mask over
+  // g3.tasks): the output blocks of those tasks are not written
+  void apply_owned(const cplx* in, cplx* out, const std::vector<char>& owned, cudaStream_t s) const;
   long long flops() const { return g1.flops + g3.flops; }
 };
 
@@ -194,6 +203,7 @@ struct Opts {
   cudaStream_t stream = nullptr;
   int device = -1;
   double trunc_degen = 1e-8;  // degenerate multiplets are cut together (relative, per-state weight)
+  bool merge = false;         // BF16x4 GEMMs may merge with other contexts' launches
 };
 
 struct StepStats {
@@ -247,6 +257,7 @@ class Engine {
   const Model& model() const { return model_; }
   void check_status();  // throws if a kernel reported non-convergence or a wait timeout
   cudaStream_t stream() const { return stream_; }
+  const Opts& opts() const { return opt_; }
 
   // synthetic single-bond problem (environments and theta given by the caller)
   // synthetic right-canonical random state of L sites with bond dimension about chi_target

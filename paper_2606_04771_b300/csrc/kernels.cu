@@ -1438,7 +1438,8 @@ void launch_jacobi_svd(const SvdTask* tasks, int ntasks, int max_q, int max_swee
 // K7: truncation selection over all sectors of a bond (one CTA)
 // ---------------------------------------------------------------------------
 
-// One CTA of TRUNC_THREADS threads.  Flat entry e of sector s is e = offs[s] + i.
+// Three launches (staging and ranking spread over CTAs, the rules in one CTA of
+// TRUNC_THREADS threads).  Flat entry e of sector s is e = offs[s] + i.
 // A sector's values r are reduced singular values normalised so that r^2 is the
 // weight of the whole multiplet, (2S+1) s^2 with s the singular value of each of its
 // 2S+1 states (Sec. S2.1, S2.4); mult = 2S+1 (1 without SU(2)).
@@ -1456,7 +1457,6 @@ void launch_jacobi_svd(const SvdTask* tasks, int ntasks, int max_q, int max_swee
 //    kept[s] = number of the first K sorted entries that belong to sector s.
 constexpr int TRUNC_THREADS = 1024;
 constexpr int TRUNC_TILE = 2048;
-constexpr int TRUNC_PER = 8;  // entries ranked per thread per pass
 
 template <class T>
 __device__ T block_exclusive_scan(T v, T* sh, T& total) {
@@ -1485,15 +1485,20 @@ __device__ T block_exclusive_scan(T v, T* sh, T& total) {
   return before;
 }
 
-__global__ void __launch_bounds__(TRUNC_THREADS) truncate_kernel(const TruncSector* __restrict__ secs, int nsec,
-                                                                 const int* __restrict__ offs, int n, double eps,
-                                                                 long long chi_max, double degen,
-                                                                 int* __restrict__ owner,
-                                                                 int* __restrict__ order, int* __restrict__ kept,
-                                                                 double* __restrict__ stats,
-                                                                 double* __restrict__ vals) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int sct = warp; sct < nsec; sct += TRUNC_THREADS / 32) {
+// ranking on integer keys: for non-negative doubles the IEEE bit pattern is monotone,
+// the NaN sentinel -1 maps to 0 (the FP64 unit is far too slow on this part for n^2
+// floating-point compares)
+__device__ __forceinline__ unsigned long long trunc_key(double v) {
+  return v >= 0.0 ? (unsigned long long)__double_as_longlong(v) + 1ull : 0ull;
+}
+
+// 1. staging: one warp per sector writes the values, per-state weights and owners
+__global__ void __launch_bounds__(256) truncate_stage_kernel(const TruncSector* __restrict__ secs, int nsec,
+                                                             const int* __restrict__ offs, int n,
+                                                             int* __restrict__ owner, int* __restrict__ kept,
+                                                             double* __restrict__ vals) {
+  const int lane = threadIdx.x & 31;
+  for (int sct = (blockIdx.x * 256 + threadIdx.x) >> 5; sct < nsec; sct += (gridDim.x * 256) >> 5) {
     const TruncSector t = secs[sct];
     for (int i = lane; i < t.r; i += 32) {
       double v = t.sv[i];
@@ -1504,45 +1509,58 @@ __global__ void __launch_bounds__(TRUNC_THREADS) truncate_kernel(const TruncSect
     }
     if (lane == 0) kept[sct] = 0;
   }
-  __syncthreads();
-  // ranking on integer keys: for non-negative doubles the IEEE bit pattern is
-  // monotone, the NaN sentinel -1 maps to 0 (the FP64 unit is far too slow on this
-  // part for n^2 floating-point compares)
-  auto key = [](double v) -> unsigned long long {
-    return v >= 0.0 ? (unsigned long long)__double_as_longlong(v) + 1ull : 0ull;
-  };
+}
+
+// 2. ranking: each CTA ranks TRUNC_RANK_PER_CTA entries (descending key, ties by flat
+// index) against every key, streamed through shared-memory tiles; order[rank] = e
+constexpr int TRUNC_RANK_THREADS = 256;
+constexpr int TRUNC_RANK_PER = 4;
+constexpr int TRUNC_RANK_PER_CTA = TRUNC_RANK_THREADS * TRUNC_RANK_PER;
+__global__ void __launch_bounds__(TRUNC_RANK_THREADS) truncate_rank_kernel(int n, const double* __restrict__ vals,
+                                                                           int* __restrict__ order) {
   __shared__ unsigned long long tile[TRUNC_TILE];
-  for (int e0 = 0; e0 < n; e0 += TRUNC_THREADS * TRUNC_PER) {
-    unsigned long long mine[TRUNC_PER];
-    int rank[TRUNC_PER];
+  const int tid = threadIdx.x, e0 = blockIdx.x * TRUNC_RANK_PER_CTA;
+  unsigned long long mine[TRUNC_RANK_PER];
+  int rank[TRUNC_RANK_PER];
 #pragma unroll
-    for (int j = 0; j < TRUNC_PER; ++j) {
-      int e = e0 + j * TRUNC_THREADS + tid;
-      mine[j] = e < n ? key(vals[n + e]) : 0ull;
-      rank[j] = 0;
-    }
-    for (int f0 = 0; f0 < n; f0 += TRUNC_TILE) {
-      const int m = min(TRUNC_TILE, n - f0);
-      __syncthreads();
-      for (int f = tid; f < m; f += TRUNC_THREADS) tile[f] = key(vals[n + f0 + f]);
-      __syncthreads();
-      for (int f = 0; f < m; ++f) {
-        const unsigned long long vf = tile[f];
-        const int gf = f0 + f;
+  for (int j = 0; j < TRUNC_RANK_PER; ++j) {
+    const int e = e0 + j * TRUNC_RANK_THREADS + tid;
+    mine[j] = e < n ? trunc_key(vals[n + e]) : 0ull;
+    rank[j] = 0;
+  }
+  for (int f0 = 0; f0 < n; f0 += TRUNC_TILE) {
+    const int m = min(TRUNC_TILE, n - f0);
+    __syncthreads();
+    for (int f = tid; f < m; f += TRUNC_RANK_THREADS) tile[f] = trunc_key(vals[n + f0 + f]);
+    __syncthreads();
+    for (int f = 0; f < m; ++f) {
+      const unsigned long long vf = tile[f];
+      const int gf = f0 + f;
 #pragma unroll
-        for (int j = 0; j < TRUNC_PER; ++j) {
-          const int e = e0 + j * TRUNC_THREADS + tid;
-          rank[j] += (vf > mine[j]) || (vf == mine[j] && gf < e);
-        }
+      for (int j = 0; j < TRUNC_RANK_PER; ++j) {
+        const int e = e0 + j * TRUNC_RANK_THREADS + tid;
+        rank[j] += (vf > mine[j]) || (vf == mine[j] && gf < e);
       }
     }
-#pragma unroll
-    for (int j = 0; j < TRUNC_PER; ++j) {
-      int e = e0 + j * TRUNC_THREADS + tid;
-      if (e < n) order[rank[j]] = e;
-    }
   }
-  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < TRUNC_RANK_PER; ++j) {
+    const int e = e0 + j * TRUNC_RANK_THREADS + tid;
+    if (e < n) order[rank[j]] = e;
+  }
+}
+
+// 3. the rules over the ranked list (one CTA)
+__global__ void __launch_bounds__(TRUNC_THREADS) truncate_kernel(const TruncSector* __restrict__ secs, int nsec,
+                                                                 const int* __restrict__ offs, int n, double eps,
+                                                                 long long chi_max, double degen,
+                                                                 int* __restrict__ owner,
+                                                                 int* __restrict__ order, int* __restrict__ kept,
+                                                                 double* __restrict__ stats,
+                                                                 double* __restrict__ vals) {
+  const int tid = threadIdx.x;
+  (void)nsec;
+  (void)offs;
   // sorted entries in contiguous runs per thread: r in [r0, r1)
   const int per = (n + TRUNC_THREADS - 1) / TRUNC_THREADS;
   const int r0 = min(n, tid * per), r1 = min(n, r0 + per);
@@ -1646,7 +1664,11 @@ __global__ void __launch_bounds__(TRUNC_THREADS) truncate_kernel(const TruncSect
 
 void launch_truncate(const TruncSector* secs, int nsec, const int* offs, int n, double eps, long long chi_max,
                      double degen, int* owner, int* order, int* kept, double* stats, double* vals, cudaStream_t s) {
-  note_launch();
+  note_launch(3);
+  truncate_stage_kernel<<<std::max(1, std::min(148, (nsec + 7) / 8)), 256, 0, s>>>(secs, nsec, offs, n, owner, kept,
+                                                                                vals);
+  truncate_rank_kernel<<<std::max(1, (n + TRUNC_RANK_PER_CTA - 1) / TRUNC_RANK_PER_CTA), TRUNC_RANK_THREADS, 0, s>>>(
+      n, vals, order);
   truncate_kernel<<<1, TRUNC_THREADS, 0, s>>>(secs, nsec, offs, n, eps, chi_max, degen, owner, order, kept, stats,
                                               vals);
 }

@@ -49,6 +49,28 @@ int split_tile_m();
 int split_tile_n(int kind);
 void launch_gemm_split(int kind, const GemmTask* tasks, const GemmSeg* segs, const int3* tiles, int ntiles,
                        const int* exps, const Bases4& B, int* status, cudaStream_t s);
+// One BF16x4 launch over the tile lists of several plans (slices): tile ti of the
+// concatenated list is tile ti - start[s] of slice s, start[s] <= ti < start[s + 1].
+constexpr int EXACT_MAX_SLICES = 8;
+struct ExactSlice {
+  const GemmTask* tasks;
+  const GemmSeg* segs;
+  const int3* tiles;
+  const int* exps;
+  int* status;
+  Bases4 B;
+};
+struct ExactLaunch {
+  int nslices;
+  int start[EXACT_MAX_SLICES + 1];
+  ExactSlice sl[EXACT_MAX_SLICES];
+};
+void launch_gemm_exact_merged(const ExactLaunch& L, cudaStream_t s);
+// merge.cpp: the BF16x4 GEMM of one plan, merged with the plans of other contexts
+// that launch at the same moment when merging is on for the calling thread
+void launch_exact_merged_or_alone(const ExactSlice& slice, int ntiles, cudaStream_t s);
+bool& merge_launches_here();  // thread-local switch, set for the duration of a context's call
+void merge_counts(long long* launches, long long* slices);
 // BF16x4 operand splitting (once per launch): group exponent tags of this epoch, then
 // digit records and exponents.  jobs = (operand, first element) in steps of
 // digit_job_size() elements.  tags start at zero; epoch runs 1 .. 2^20 - 1.

@@ -113,10 +113,6 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 __device__ __forceinline__ uint32_t sw_off4(int row, int kk) {
   return row * 128 + ((((kk >> 2) ^ (row & 7)) & 7) << 4) + ((kk & 3) << 2);
 }
-// same for 2-byte elements (64 per row)
-__device__ __forceinline__ uint32_t sw_off2(int row, int kk) {
-  return row * 128 + ((((kk >> 3) ^ (row & 7)) & 7) << 4) + ((kk & 7) << 1);
-}
 
 __device__ __forceinline__ float tf32_round(float x) {
   uint32_t r;
@@ -416,10 +412,6 @@ __device__ __forceinline__ void digits4(int X, float* d) {
   d[3] = (float)d3;
 }
 
-__device__ __forceinline__ void st_bf2(uint8_t* plane, int row, int kk, float v0, float v1) {
-  *reinterpret_cast<__nv_bfloat162*>(plane + sw_off2(row, kk)) = __floats2bfloat162_rn(v0, v1);
-}
-
 // K-major tiles with 64-byte rows (32 bf16) in the 64-byte swizzle: the 16-byte chunk
 // index of a row is XORed with (row / 2) mod 4 (the address bits 7-8 folded onto bits
 // 4-5); 8-row groups are 512 bytes apart
@@ -635,10 +627,18 @@ __device__ __forceinline__ int task_chunks(const GemmTask& t, const GemmSeg* __r
 // planes of a two-stage ring, warp 8 issues the MMAs into one of two TMEM
 // accumulator sets, warps 9-16 drain the other set (exact combination, scaling,
 // FP64 stores) while the next tile accumulates.
-__global__ void __launch_bounds__(XTHREADS, 1)
-    gemm_exact_kernel(const GemmTask* __restrict__ tasks, const GemmSeg* __restrict__ segs,
-                      const int3* __restrict__ tiles, int ntiles, const Bases4 B, const int* __restrict__ exps,
-                      int* __restrict__ status) {
+// The tiles of up to EXACT_MAX_SLICES task lists (one GEMM plan each, with its own
+// bases, exponents and status word) run in one launch: tile ti of the concatenated
+// list belongs to slice s with L.start[s] <= ti < L.start[s + 1].  Every tile is
+// computed the same way whichever launch and CTA take it.
+__device__ __forceinline__ int slice_of(const ExactLaunch& L, int ti) {
+  int s = L.nslices - 1;
+  while (s > 0 && ti < L.start[s]) --s;
+  return s;
+}
+
+__global__ void __launch_bounds__(XTHREADS, 1) gemm_exact_kernel(const __grid_constant__ ExactLaunch L) {
+  const int ntiles = L.start[L.nslices];
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* stage_base =
       reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -681,9 +681,11 @@ __global__ void __launch_bounds__(XTHREADS, 1)
     auto advance = [&](int& ti, int& sgi, int& k0) -> bool {
       k0 += XKC;
       while (ti < ntiles) {
-        const GemmTask& t = tasks[tiles[ti].x];
+        const int sl = slice_of(L, ti);
+        const ExactSlice& S = L.sl[sl];
+        const GemmTask& t = S.tasks[S.tiles[ti - L.start[sl]].x];
         while (sgi < t.seg_count) {
-          if (k0 < segs[t.seg_begin + sgi].k) return true;
+          if (k0 < S.segs[t.seg_begin + sgi].k) return true;
           ++sgi;
           k0 = 0;
         }
@@ -694,9 +696,11 @@ __global__ void __launch_bounds__(XTHREADS, 1)
       return false;
     };
     auto fetch = [&](int ti, int sgi, int k0, unsigned long long* wa, unsigned long long* wb) {
-      const int3 tr = tiles[ti];
-      const GemmTask& t = tasks[tr.x];
-      const GemmSeg& sg = segs[t.seg_begin + sgi];
+      const int sl = slice_of(L, ti);
+      const ExactSlice& S = L.sl[sl];
+      const int3 tr = S.tiles[ti - L.start[sl]];
+      const GemmTask& t = S.tasks[tr.x];
+      const GemmSeg& sg = S.segs[t.seg_begin + sgi];
       const int tn = t.tn > 0 ? t.tn : XN;
       const int m0 = tr.y * TM, n0 = tr.z * tn, kk = sg.k, rows = t.rows, cols = t.cols;
       const unsigned long long* ad = sg.a_dig;
@@ -722,7 +726,8 @@ __global__ void __launch_bounds__(XTHREADS, 1)
     unsigned long long wa[NA], wb[NB], na_[NA], nb_[NB];
     if (have) fetch(ti, sgi, k0, wa, wb);
     for (int it = 0; have && !*verr; ++it) {
-      const int bkm = tasks[tiles[ti].x].b_kmajor;
+      const int bsl = slice_of(L, ti);
+      const int bkm = L.sl[bsl].tasks[L.sl[bsl].tiles[ti - L.start[bsl]].x].b_kmajor;
       int ti2 = ti, sgi2 = sgi, k02 = k0;
       const bool have2 = advance(ti2, sgi2, k02);
       if (have2) fetch(ti2, sgi2, k02, na_, nb_);
@@ -774,7 +779,9 @@ __global__ void __launch_bounds__(XTHREADS, 1)
       int it = 0, j = 0;
       bool ok = true;
       for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
-        const GemmTask t = tasks[tiles[ti].x];
+        const int sl = slice_of(L, ti);
+        const GemmSeg* segs = L.sl[sl].segs;
+        const GemmTask t = L.sl[sl].tasks[L.sl[sl].tiles[ti - L.start[sl]].x];
         if (task_chunks(t, segs) == 0) continue;
         const uint32_t idesc = make_idesc(1u, 128, (uint32_t)(t.tn > 0 ? t.tn : XN));
         const int buf = j & 1;
@@ -829,9 +836,13 @@ __global__ void __launch_bounds__(XTHREADS, 1)
     const int etid = tid - (XPROD + 32);  // 0..255
     int j = 0;
     for (int ti = blockIdx.x; ti < ntiles && !*verr; ti += gridDim.x) {
-      const int3 tr = tiles[ti];
-      const GemmTask t = tasks[tr.x];
-      cplx* const cptr = rebase(B, t.c_base, t.c);
+      const int sl = slice_of(L, ti);
+      const ExactSlice& S = L.sl[sl];
+      const GemmSeg* segs = S.segs;
+      const int* exps = S.exps;
+      const int3 tr = S.tiles[ti - L.start[sl]];
+      const GemmTask t = S.tasks[tr.x];
+      cplx* const cptr = rebase(S.B, t.c_base, t.c);
       const int tn = t.tn > 0 ? t.tn : XN;
       const int m0 = tr.y * TM, n0 = tr.z * tn;
       if (task_chunks(t, segs) == 0) {  // no contribution: the output tile is zero
@@ -886,7 +897,8 @@ __global__ void __launch_bounds__(XTHREADS, 1)
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * XACC) : "memory");
   }
-  if (tid == 0 && err) atomicAdd(status, 1);
+  if (tid == 0 && err)
+    for (int q = 0; q < L.nslices; ++q) atomicAdd(L.sl[q].status, 1);
 }
 
 template <int KIND>
@@ -929,17 +941,28 @@ void launch_gemm_split(int kind, const GemmTask* tasks, const GemmSeg* segs, con
     note_launch();
     gemm_split_kernel<0><<<ntiles, NTHREADS, sm, s>>>(tasks, segs, tiles, B, status);
   } else {
-    const size_t sm = (size_t)XSTAGES * XSTAGE + 1024;
-    static const int nsm = [sm] {  // once per process, thread-safe (function-local static)
-      cudaFuncSetAttribute(gemm_exact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      int dev = 0, n = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-      return n < 1 ? 1 : n;
-    }();
-    note_launch();
-    gemm_exact_kernel<<<ntiles < nsm ? ntiles : nsm, XTHREADS, sm, s>>>(tasks, segs, tiles, ntiles, B, exps, status);
+    ExactLaunch L{};
+    L.nslices = 1;
+    L.start[0] = 0;
+    L.start[1] = ntiles;
+    L.sl[0] = {tasks, segs, tiles, exps, status, B};
+    launch_gemm_exact_merged(L, s);
   }
+}
+
+void launch_gemm_exact_merged(const ExactLaunch& L, cudaStream_t s) {
+  const int ntiles = L.start[L.nslices];
+  if (ntiles <= 0) return;
+  const size_t sm = (size_t)XSTAGES * XSTAGE + 1024;
+  static const int nsm = [sm] {  // once per process, thread-safe (function-local static)
+    cudaFuncSetAttribute(gemm_exact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n < 1 ? 1 : n;
+  }();
+  note_launch();
+  gemm_exact_kernel<<<ntiles < nsm ? ntiles : nsm, XTHREADS, sm, s>>>(L);
 }
 
 int digit_job_size() { return DIGIT_JOB; }

@@ -62,8 +62,11 @@ def footprint_bytes(req: Request, krylov_max=20) -> float:
 class QuenchServer:
     """A running server (its worker threads start at construction)."""
 
-    def __init__(self, hbm_budget_gb=200.0, max_active=8, krylov_max=20, krylov_tol=1e-12, device=-1):
-        o = make_opts(krylov_max=krylov_max, krylov_tol=krylov_tol, device=device)
+    def __init__(self, hbm_budget_gb=200.0, max_active=8, krylov_max=20, krylov_tol=1e-12, device=-1,
+                 merge_launches=False):
+        """merge_launches: the running requests' BF16x4 block GEMMs go out in shared
+        grouped launches (tdvp_opts.merge_launches) instead of one launch per request."""
+        o = make_opts(krylov_max=krylov_max, krylov_tol=krylov_tol, device=device, merge_launches=merge_launches)
         self.h = C.c_void_p()
         check(lib().tdvp_server_create(hbm_budget_gb * 1e9, int(max_active), C.byref(o), C.byref(self.h)))
         self.requests = {}
@@ -194,10 +197,19 @@ def main(argv=None):
     ap.add_argument("--hbm-gb", type=float, default=200.0)
     ap.add_argument("--precision", default="bf16x4", choices=sorted(PREC))
     ap.add_argument("--mode", default="adaptive", choices=sorted(MODE))
+    ap.add_argument("--eps", type=float, default=None, help="truncation threshold (default: the Request default)")
+    ap.add_argument("--merge", action="store_true",
+                    help="shared grouped launches of the running requests' BF16x4 block GEMMs")
     a = ap.parse_args(argv)
     reqs = synthetic_requests(a.requests, a.rate, a.seed, Ls=tuple(a.L), Us=tuple(a.U), ts=tuple(a.t),
                               chis=tuple(a.chi), precision=a.precision, mode=a.mode)
-    with QuenchServer(hbm_budget_gb=a.hbm_gb, max_active=a.max_active) as srv:
+    if a.eps is not None:
+        for r in reqs:
+            r.eps = a.eps
+    from ._lib import merge_count
+
+    m0 = merge_count()
+    with QuenchServer(hbm_budget_gb=a.hbm_gb, max_active=a.max_active, merge_launches=a.merge) as srv:
         try:
             replay(srv, reqs, log=sys.stdout)
         except TdvpError as e:
@@ -207,8 +219,11 @@ def main(argv=None):
     st["requests_per_s"] = st["done"] / st["wall_s"]
     st["steps_per_s"] = st["steps"] / st["wall_s"]
     st["heff_tflops"] = st["heff_flops"] / st["wall_s"] / 1e12
+    m1 = merge_count()
+    st["merged_launches"] = m1[0] - m0[0]
+    st["merged_task_lists"] = m1[1] - m0[1]
     print(json.dumps({"summary": st, "max_active": a.max_active, "rate_per_s": a.rate, "seed": a.seed,
-                      "precision": a.precision, "mode": a.mode}), flush=True)
+                      "precision": a.precision, "mode": a.mode, "merge": a.merge}), flush=True)
 
 
 if __name__ == "__main__":

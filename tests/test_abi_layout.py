@@ -15,7 +15,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 FIELDS = {
     "tdvp_opts": (Opts, ["precision", "krylov_max", "krylov_tol", "timeout_ms", "cuda_stream", "device",
-                         "trunc_degeneracy"]),
+                         "trunc_degeneracy", "merge_launches"]),
     "tdvp_request": (RequestC, ["L", "J", "U", "symmetry", "precision", "mode", "dt", "t_final", "chi_max", "eps",
                                 "occupations"]),
 }

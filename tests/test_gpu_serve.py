@@ -29,12 +29,18 @@ def _alone(r):
         return s.result(i)
 
 
-def test_each_result_is_the_same_alone_and_in_the_mix():
+@pytest.mark.parametrize("merge", [False, True])
+def test_each_result_is_the_same_alone_and_in_the_mix(merge):
+    """merge=True: the requests' BF16x4 block GEMMs go out in shared grouped launches
+    (several requests' tile lists in one persistent launch); every tile is computed the
+    same way in any launch, so the results equal the lone runs."""
+    from paper_2606_04771_b300._lib import merge_count
     from paper_2606_04771_b300.serve import QuenchServer
 
     reqs = _reqs()
     alone = [_alone(r) for r in reqs]
-    with QuenchServer(max_active=len(reqs)) as s:
+    m0 = merge_count()
+    with QuenchServer(max_active=len(reqs), merge_launches=merge) as s:
         ids = [s.submit(r) for r in reqs]
         for i in ids:
             assert s.wait(i, timeout=600) == "done"
@@ -49,6 +55,30 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
     assert st["done"] == len(reqs) and st["failed"] == 0
     assert st["peak_active"] >= 2  # the requests did run side by side
     assert st["latency_p99_s"] >= st["latency_p50_s"] > 0
+    if not merge:
+        assert merge_count() == m0
+
+
+def test_merged_launches_carry_several_requests_and_change_nothing():
+    """Three BF16x4 requests served side by side with merged launches: some launches
+    carry more than one request's tile list, and every result equals the lone run bit
+    for bit."""
+    from paper_2606_04771_b300._lib import merge_count
+    from paper_2606_04771_b300.serve import QuenchServer, Request
+
+    reqs = [Request(L=L, U=4.0, t_final=0.3, chi=128, precision="bf16x4", mode="two") for L in (16, 18, 20)]
+    alone = [_alone(r) for r in reqs]
+    m0 = merge_count()
+    with QuenchServer(max_active=3, merge_launches=True) as s:
+        ids = [s.submit(r) for r in reqs]
+        for i in ids:
+            assert s.wait(i, timeout=600) == "done"
+        mix = [s.result(i) for i in ids]
+    m1 = merge_count()
+    assert m1[0] > m0[0] and m1[1] - m0[1] >= 2 * (m1[0] - m0[0])  # launches that carried >= 2 lists
+    for a, m in zip(alone, mix):
+        for k in KEYS:
+            assert np.array_equal(m[k], a[k]), k
 
 
 def test_served_request_equals_a_chain():
