@@ -440,7 +440,7 @@ def run_engine(args):
         "config": {"workload": "mid-chain two-site TDVP bond updates (L->R + R->L at bond 29) of L=60, "
                                "U(1)xSU(2), chi=4096 (U(1)-equivalent), dt=0.05, eps=1e-9",
                    "chi": int(chis[mid + 1]), "chi_su2": int(red[mid + 1]), "chi_after": int(chis_after[mid + 1]),
-                   "precision": args.precision, "flops_per_step": flops_step,
+                   "precision": args.precision, "flops_per_step": flops_step, "bond_entropy": ents[1],
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": f"replicas x{ws} (independent states, no collective)"},
         "gpu_launches": int(launches),
