@@ -383,8 +383,9 @@ def run_engine(args):
     # H_eff GEMMs of the step are its matvecs x the GEMM time of one matvec
     d = {k: (st1[k] - st0[k]) / args.steps for k in ("jacobi32_ms", "jacobi32_flops", "jacobi64_ms", "jacobi64_flops",
                                                        "matvecs", "env_ms", "env_bytes", "sweeps32", "sweeps64",
-                                                       "splits")}
-    shares = {"jacobi_fp32": d["jacobi32_ms"], "jacobi_fp64": d["jacobi64_ms"],
+                                                       "splits", "gram_ms", "gram_flops", "gram_steps",
+                                                       "gram_fallbacks", "jacobi_ring_calls")}
+    shares = {"jacobi_fp32": d["jacobi32_ms"], "jacobi_fp64": d["jacobi64_ms"], "gram_finish": d["gram_ms"],
               "heff_gemm": d["matvecs"] * heff["gemm_ms"], "env_update": d["env_ms"]}
     top = max(shares, key=shares.get)
     if top == "jacobi_fp32":
@@ -392,7 +393,9 @@ def run_engine(args):
         p32 = alu["fp32_tflops_sustained"]
         roofline = {"bound": "alu", "achieved": a, "peak": p32, "unit": "TFLOP/s", "frac": a / p32,
                     "traffic": JACOBI_TRAFFIC.get("fp32"),
-                    "kernel": "jacobi_coop_kernel<Svd32Task> (FP32 preconditioner of the split)",
+                    "kernel": ("jacobi_ring_kernel (FP32 preconditioner of the split: rings of warps in "
+                               "thread-block clusters)" if d["jacobi_ring_calls"] > 0 else
+                               "jacobi_coop_kernel<Svd32Task> (FP32 preconditioner of the split)"),
                     "peak_source": "measured FP32 SGEMM sustained (torch.matmul 8192^3, TF32 off), of measured",
                     "alg_flops_per_step": d["jacobi32_flops"], "ms_per_step": d["jacobi32_ms"]}
     elif top == "jacobi_fp64":
@@ -402,6 +405,15 @@ def run_engine(args):
                     "traffic": JACOBI_TRAFFIC.get("fp64"), "kernel": "jacobi_coop_kernel<SvdTask> (FP64 Jacobi)",
                     "peak_source": "measured FP64 DGEMM sustained (torch.matmul 4096^3), of measured",
                     "alg_flops_per_step": d["jacobi64_flops"], "ms_per_step": d["jacobi64_ms"]}
+    elif top == "gram_finish":
+        # two of its three steps run on the tensor cores (BF16x4), the third forms the
+        # Gram matrix in FP64: the FP64 GEMM rate bounds it from below
+        a = d["gram_flops"] / (d["gram_ms"] * 1e-3) / 1e12
+        p64 = alu["fp64_tflops_sustained"]
+        roofline = {"bound": "alu", "achieved": a, "peak": p64, "unit": "TFLOP/s", "frac": a / p64,
+                    "traffic": None, "kernel": "Gram finish of the split (BF16x4 and FP64 GEMMs, gram_rot_kernel)",
+                    "peak_source": "measured FP64 DGEMM sustained (torch.matmul 4096^3), of measured",
+                    "alg_flops_per_step": d["gram_flops"], "ms_per_step": d["gram_ms"]}
     elif top == "env_update":
         a = d["env_bytes"] / (d["env_ms"] * 1e-3) / 1e9
         roofline = {"bound": "hbm", "achieved": a, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -417,6 +429,14 @@ def run_engine(args):
         jac[tag] = {"ms_per_step": ms_, "alg_gflop_per_step": fl_ / 1e9, "achieved_tflops": a_,
                     "frac_of_measured": a_ / alu[peak_k] if a_ else None,
                     "sweeps_per_split": d[f"sweeps{tag[2:]}"] / d["splits"] if d["splits"] else None}
+    a_ = d["gram_flops"] / (d["gram_ms"] * 1e-3) / 1e12 if d["gram_ms"] > 0 else None
+    jac["gram_finish"] = {"ms_per_step": d["gram_ms"], "alg_gflop_per_step": d["gram_flops"] / 1e9,
+                          "achieved_tflops": a_,
+                          "steps_per_split": d["gram_steps"] / d["splits"] if d["splits"] else None,
+                          "fallbacks_per_step": d["gram_fallbacks"],
+                          "note": "per split: two BF16x4 steps and one FP64 step (12 p q^2 flops per sector "
+                                  "and step); no single peak applies"}
+    jac["fp32"]["form"] = "ring (clusters)" if d["jacobi_ring_calls"] > 0 else "cooperative grid"
     env = {"ms_per_step": d["env_ms"], "alg_bytes_per_step": d["env_bytes"],
            "gbs": d["env_bytes"] / (d["env_ms"] * 1e-3) / 1e9 if d["env_ms"] > 0 else None}
     env["frac_hbm"] = env["gbs"] / peaks["hbm_gbs"] if env["gbs"] else None
@@ -582,6 +602,25 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def split_updates(args):
+    """Three bond updates at the middle bond of the bench state: each has one split
+    (FP32 ring Jacobi, Gram finish, truncation), so a profiler skipping two launches of a
+    split kernel captures the third update's."""
+    import torch
+
+    from paper_2606_04771_b300 import Chain
+
+    torch.cuda.set_device(0)
+    ch = Chain(60, 1.0, 4.0, symmetry="su2", random_chi=args.chi, seed=synth.SEED_BOND, center=29,
+               precision=args.precision, krylov_max=args.krylov)
+    ents = [ch.bond_update(29, d, 0.05, args.chi, 1e-9) for d in (0, 1, 0)]
+    st = ch.stats()
+    keys = ("splits", "sweeps32", "jacobi32_ms", "jacobi_ring_calls", "gram_ms", "gram_steps", "gram_fallbacks",
+            "split_pmax", "split_qmax")
+    print(json.dumps({"entropies": ents, **{k: st[k] for k in keys}}), flush=True)
+    ch.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -597,11 +636,16 @@ def main():
     ap.add_argument("--no-fp64-check", action="store_true", help="skip the FP64 sweep used for the comparison")
     ap.add_argument("--heff-only", action="store_true",
                     help="only the H_eff.psi profile on the chi=4096 bond (for profiler captures); prints its dict")
+    ap.add_argument("--split-only", action="store_true",
+                    help="only three bond updates (L->R, R->L, L->R) at the middle bond of the chi=4096 state, "
+                         "untimed (for profiler captures of the split's kernels); prints the split statistics")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.split_only:
+        split_updates(args)
     elif args.heff_only:
         import torch
 

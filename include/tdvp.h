@@ -214,8 +214,11 @@ int tdvp_bond_dims(tdvp_ctx* ctx, long long* chi, long long* chi_red);
  * clusters.  out[31] milliseconds of the environment updates of the two-site
  * bond updates (CUDA events around each update) and out[32] their algorithmic
  * bytes (every operand block read once and every result block written once, over
- * the block-GEMM and MPO linear-combination stages).  n = length of out (at most
- * 33). */
+ * the block-GEMM and MPO linear-combination stages).  out[33] milliseconds and
+ * out[34] algorithmic flops (16 p q^2 per sector and step) of the Gram finish of the
+ * split-precision splits, out[35] its steps and out[36] the splits it handed to the
+ * FP64 Jacobi.  out[37] Jacobi calls of the splits that ran as rings of warps in
+ * thread-block clusters.  n = length of out (at most 38). */
 int tdvp_stats(tdvp_ctx* ctx, double* out, int n);
 
 /* ---- single-bond problems (the effective-Hamiltonian benchmark) ------------

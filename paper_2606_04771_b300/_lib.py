@@ -361,13 +361,14 @@ class Chain(_Ctx):
         return chi, red
 
     def stats(self):
-        v = np.zeros(33)
-        check(lib().tdvp_stats(self.h, v.ctypes.data, 33))
+        v = np.zeros(38)
+        check(lib().tdvp_stats(self.h, v.ctypes.data, 38))
         keys = ["seconds", "heff_flops", "env_flops", "matvecs", "max_krylov", "max_discarded", "chi_max_seen",
                 "t_theta", "t_plan", "t_krylov2", "t_split", "t_env", "t_krylov1", "steps", "splits", "sweeps64",
                 "sweeps32", "one_site_steps", "device_bytes", "device_bytes_peak", "jacobi32_ms", "jacobi32_flops",
                 "jacobi64_ms", "jacobi64_flops", "split_pmax", "split_qmax", "split_work", "split_work_small",
-                "jacobi_calls", "jacobi_resident_calls", "jacobi_cluster_calls", "env_ms", "env_bytes"]
+                "jacobi_calls", "jacobi_resident_calls", "jacobi_cluster_calls", "env_ms", "env_bytes", "gram_ms",
+                "gram_flops", "gram_steps", "gram_fallbacks", "jacobi_ring_calls"]
         return dict(zip(keys, v.tolist()))
 
 

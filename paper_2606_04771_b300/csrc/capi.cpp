@@ -269,7 +269,7 @@ int tdvp_stats(tdvp_ctx* ctx, double* out, int n) {
   if (!ctx || !out) return fail(TDVP_EINVAL, "NULL argument");
   return guarded(ctx, [&] {
     const tdvp::StepStats& s = ctx->eng->stats();
-    double v[33] = {s.seconds, (double)s.heff_flops, (double)s.env_flops, (double)s.matvecs, (double)s.max_krylov,
+    double v[38] = {s.seconds, (double)s.heff_flops, (double)s.env_flops, (double)s.matvecs, (double)s.max_krylov,
                     s.max_discarded, (double)s.chi_max_seen, s.phase[0], s.phase[1], s.phase[2], s.phase[3],
                     s.phase[4], s.phase[5], (double)s.steps, (double)s.splits, (double)s.sweeps64,
                     (double)s.sweeps32, (double)s.one_site_steps, (double)ctx->acct.live.load(),
@@ -277,8 +277,10 @@ int tdvp_stats(tdvp_ctx* ctx, double* out, int n) {
                     (double)s.split_pmax, (double)s.split_qmax, s.split_work, s.split_work_small,
                     (double)(s.jacobi32.launches + s.jacobi64.launches),
                     (double)(s.jacobi32.resident + s.jacobi64.resident),
-                    (double)(s.jacobi32.cluster + s.jacobi64.cluster), s.env_ms, s.env_bytes};
-    for (int i = 0; i < n && i < 33; ++i) out[i] = v[i];
+                    (double)(s.jacobi32.cluster + s.jacobi64.cluster), s.env_ms, s.env_bytes,
+                    s.gram.ms, s.gram.flops, (double)s.gram_steps, (double)s.gram_fallbacks,
+                    (double)(s.jacobi32.ring + s.jacobi64.ring)};
+    for (int i = 0; i < n && i < 38; ++i) out[i] = v[i];
   });
 }
 

@@ -142,6 +142,15 @@ struct Svd32Task {
   int p, q;
 };
 
+// One column set of the mixed split's Gram finish: c is the q x q row-major matrix
+// C[a][b] = sum_r G_ra conj(G_rb) (the conjugate of G^H G), zt receives Z^T (row-major
+// q x q, zt[i][k] = Z[k][i]) of the simultaneous rotation G <- G Z.
+struct GramTask {
+  const cplx* c;
+  cplx* zt;
+  int q;
+};
+
 struct BasisTask {  // x[i][kk] = g[i, perm[kk]] / sv[kk] (or / sv[kk]^2); g column-major, rows x .
   const cplx* g;
   const int* perm;

@@ -2220,6 +2220,161 @@ double Engine::split(BTensor& theta, const BondSpace& bl, const BondSpace& br, l
 // caller runs the FP64 split otherwise).
 // ---------------------------------------------------------------------------
 
+// Whether the mixed split finishes with the Gram iteration (default) or with the
+// FP64 Jacobi (TDVP_SPLIT_FINISH=jacobi; read at every split).
+static bool gram_enabled() {
+  const char* e = std::getenv("TDVP_SPLIT_FINISH");
+  return !(e && std::strcmp(e, "jacobi") == 0);
+}
+
+// Largest |tan| of a rotation the Gram step applies simultaneously: 0.1, or
+// TDVP_GRAM_TMAX (read at every split; 0 declines every pair of weight, which hands
+// the split to the Jacobi with G unchanged).
+static double gram_tmax() {
+  const char* e = std::getenv("TDVP_GRAM_TMAX");
+  if (!e || !*e) return 0.1;
+  const double v = std::atof(e);
+  return v < 0 ? 0.0 : (v > 1.0 ? 1.0 : v);
+}
+
+// FP64 finish of the mixed split by Gram iteration.  G (ng column-major sets of p x q,
+// at toff) has nearly orthogonal columns after the FP32 preconditioner.  A step forms
+// C = conj(G^H G) (its tiles on and above the diagonal), turns it into the
+// simultaneous rotation Z = I + X (gram_rot_kernel) and adds G X to G in FP64.  The
+// first two steps form C and G X on the tensor cores (BF16x4 split products: C to
+// ~1e-9 of |g_a||g_b|, since each operand row and column carries its own scale, and
+// the update to ~1e-9 of the update), which takes the FP32-level off-diagonals to
+// the BF16x4 level; the third step forms C with the FP64 GEMM, so its couplings are
+// exact to the FP64 level and its update leaves them at about their square.  The
+// stopping rule is the FP64 Jacobi's: the split is finished after an FP64 step whose
+// couplings were all below 1e-6 relative or 1e-10 absolute (theta has unit norm);
+// otherwise two more steps (BF16x4, FP64) run.  Returns true with the result in G, or
+// false (G still a valid start, rotated by near-orthogonal steps) when near-degenerate
+// columns carry weight or the steps do not settle; the caller then runs the
+// sequential Jacobi.  galt receives G X.
+bool Engine::gram_finish(cplx* G, cplx* galt, const std::vector<int>& P, const std::vector<int>& Q,
+                         const std::vector<long long>& toff) {
+  const int ng = (int)P.size();
+  std::vector<long long> koff(ng);
+  long long kt = 0, ntot = 0;
+  int qmax = 0;
+  double flops = 0;
+  for (int g = 0; g < ng; ++g) {
+    koff[g] = kt;
+    kt += (long long)Q[g] * Q[g];
+    qmax = std::max(qmax, Q[g]);
+    ntot = std::max(ntot, toff[g] + (long long)P[g] * Q[g]);
+    flops += 12.0 * P[g] * (double)Q[g] * Q[g];  // upper half of C (4 p q^2) and G X (8 p q^2)
+  }
+  if (qmax < 2) return false;
+  DevBuf dK(kt * sizeof(cplx), stream_), dZ(kt * sizeof(cplx), stream_), dfl(8 * sizeof(int), stream_);
+  cplx *Kb = dK.as<cplx>(), *Zb = dZ.as<cplx>();
+  int* fl = dfl.as<int>();
+  // pointers relative to launch bases: 1 = G, 2 = galt
+  GemmPlan pk_tc, pk64, pu;
+  std::vector<GramTask> gt;
+  for (int g = 0; g < ng; ++g) {
+    if (Q[g] < 1) continue;
+    GemmTask t{};
+    GemmSeg sg{};
+    sg.alpha = 1.0;
+    t.c = Kb + koff[g];
+    t.rows = Q[g];
+    t.cols = Q[g];
+    t.ldc = Q[g];
+    sg.a = as_off(toff[g]);
+    sg.a_base = 1;
+    sg.lda = P[g];
+    sg.b = as_off(toff[g]);
+    sg.b_base = 1;
+    sg.ldb = P[g];
+    sg.op_b = OP_C;
+    sg.k = P[g];
+    for (GemmPlan* pl : {&pk_tc, &pk64}) {
+      t.seg_begin = (int)pl->segs.size();
+      t.seg_count = 1;
+      pl->segs.push_back(sg);
+      pl->tasks.push_back(t);
+    }
+    GemmTask u{};
+    GemmSeg sh{};
+    sh.alpha = 1.0;
+    u.c = as_off(toff[g]);
+    u.c_base = 2;
+    u.rows = Q[g];
+    u.cols = P[g];
+    u.ldc = P[g];
+    sh.a = Zb + koff[g];
+    sh.lda = Q[g];
+    sh.b = as_off(toff[g]);
+    sh.b_base = 1;
+    sh.ldb = P[g];
+    sh.k = Q[g];
+    u.seg_begin = (int)pu.segs.size();
+    u.seg_count = 1;
+    pu.segs.push_back(sh);
+    pu.tasks.push_back(u);
+    gt.push_back({Kb + koff[g], Zb + koff[g], Q[g]});
+  }
+  pk_tc.finalize(stream_, 1, dstatus_);
+  pk64.finalize(stream_);
+  pu.finalize(stream_, 1, dstatus_);
+  // the Gram matrices are Hermitian: only tiles on and above the diagonal
+  for (GemmPlan* pl : {&pk_tc, &pk64}) {
+    std::vector<int3> up;
+    for (const int3& t : pl->tiles)
+      if (t.y <= t.z) up.push_back(t);
+    pl->tiles.swap(up);
+    pl->dti = upload(pl->tiles, stream_);
+  }
+  DevBuf dgt = upload(gt, stream_);
+  const double tmax = gram_tmax();
+  const Bases4 B{{0, reinterpret_cast<uintptr_t>(G), reinterpret_cast<uintptr_t>(galt), 0}};
+  cudaEvent_t ev[2];
+  TDVP_CUDA(cudaEventCreate(&ev[0]));
+  TDVP_CUDA(cudaEventCreate(&ev[1]));
+  TDVP_CUDA(cudaEventRecord(ev[0], stream_));
+  auto step = [&](bool fp64, int* f) {
+    (fp64 ? pk64 : pk_tc).launch(stream_, B);
+    launch_gram_rot(dgt.as<GramTask>(), (int)gt.size(), qmax, 1e-13, 1e-6, 1e-10, tmax, f, stream_);
+    pu.launch(stream_, B);
+    launch_add_inplace(G, galt, ntot, stream_);
+  };
+  bool ok = false;
+  int steps = 0;
+  float worst = 0.0f;
+  for (int round = 0; round < 2 && !ok; ++round) {
+    TDVP_CUDA(cudaMemsetAsync(fl, 0, 8 * sizeof(int), stream_));
+    if (round == 0) {
+      step(false, fl);
+      steps += 1;
+    }
+    step(false, fl);
+    step(true, fl + 4);
+    steps += 2;
+    int h[8];
+    TDVP_CUDA(cudaMemcpyAsync(h, fl, sizeof(h), cudaMemcpyDeviceToHost, stream_));
+    TDVP_CUDA(cudaStreamSynchronize(stream_));
+    worst = std::max(worst, *reinterpret_cast<float*>(&h[6]));
+    if (h[1] || h[5]) break;  // near-degenerate columns of weight: the Jacobi finishes
+    ok = h[4] == 0;           // the FP64 step saw no coupling above the stopping rule
+  }
+  TDVP_CUDA(cudaEventRecord(ev[1], stream_));
+  TDVP_CUDA(cudaEventSynchronize(ev[1]));
+  float ms = 0;
+  if (cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess) stats_.gram.ms += ms;
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  stats_.gram.flops += steps * flops;
+  stats_.gram.launches += 1;
+  stats_.gram_steps += steps;
+  if (!ok) stats_.gram_fallbacks += 1;
+  if (std::getenv("TDVP_GRAM_DEBUG"))
+    std::fprintf(stderr, "gram: %d steps, ok=%d, last FP64 step's largest relative coupling %.3g\n", steps, (int)ok,
+                 (double)worst);
+  return ok;
+}
+
 double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace& br, long long chi_max, double eps,
                            bool absorb_right, BondSpace& bm, BTensor& X, BTensor& Y, double* s_ent, bool& ok) {
   NvtxRange nvtx_range("split");
@@ -2374,9 +2529,22 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
   // absolute terms (theta has unit norm, so that is a weight a decade below the
   // smallest truncation threshold in use; on the L=60 quench the observables do not
   // move against tighter settings while the stage needs fewer sweeps)
-  stats_.sweeps64 += jacobi(
-      run_jacobi_rounds(dst.as<SvdTask>(), st, 30, 1e-13, dstatus_, stream_, 1e-6, 1e-10, &stats_.jacobi64,
-                        jscratch()));
+  // The Gram finish (gram_finish) reaches the same stopping point with GEMMs; the
+  // Jacobi runs when it declines (near-degenerate columns of weight) or when
+  // TDVP_SPLIT_FINISH=jacobi.
+  std::vector<int> gp(ng), gq(ng);
+  for (int g = 0; g < ng; ++g) {
+    gp[g] = bigP(groups[g]);
+    gq[g] = smallQ(groups[g]);
+  }
+  if (gram_enabled() && gram_finish(G64, W64, gp, gq, toff)) {
+    int qm = 1;
+    for (int g = 0; g < ng; ++g) qm = std::max(qm, gq[g]);
+    launch_svd_finish(dst.as<SvdTask>(), ng, qm, stream_);
+  } else {
+    stats_.sweeps64 += jacobi(run_jacobi_rounds(dst.as<SvdTask>(), st, 30, 1e-13, dstatus_, stream_, 1e-6, 1e-10,
+                                                &stats_.jacobi64, jscratch()));
+  }
   DevBuf dts = upload(ts, stream_), doffs = upload(soff, stream_);
   DevBuf downer(std::max(stot, 1) * sizeof(int), stream_), dorder(std::max(stot, 1) * sizeof(int), stream_);
   DevBuf dkept(std::max(ng, 1) * sizeof(int), stream_), dstats(8 * sizeof(double), stream_);

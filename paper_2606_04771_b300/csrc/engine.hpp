@@ -222,6 +222,11 @@ struct StepStats {
   // the cooperative Jacobi launches of the splits (CUDA-event time and algorithmic
   // flops, as JacobiProfile): FP32 preconditioner and FP64 stage
   JacobiProfile jacobi32, jacobi64;
+  // the Gram finish of the mixed split: device time and algorithmic flops (16 p q^2
+  // per set and step: the Gram matrix and the rotation), steps, and the splits it
+  // handed to the FP64 Jacobi
+  JacobiProfile gram;
+  long long gram_steps = 0, gram_fallbacks = 0;
   // sector shapes of the splits: largest P = max(p, q) and Q = min(p, q) seen, and the
   // one-sided Jacobi work sum P Q^2 over all sectors and over those whose complex64
   // copy (P Q x 8 bytes) fits in 192 KiB of shared memory
@@ -316,6 +321,8 @@ class Engine {
   // split theta at bond (i,i+1); absorb_right: S goes to Y (left-to-right sweep)
   double split(BTensor& theta, const BondSpace& bl, const BondSpace& br, long long chi_max, double eps,
                bool absorb_right, BondSpace& bm, BTensor& X, BTensor& Y, double* s_ent = nullptr);
+  bool gram_finish(cplx* G, cplx* galt, const std::vector<int>& P, const std::vector<int>& Q,
+                   const std::vector<long long>& toff);
   double split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace& br, long long chi_max, double eps,
                      bool absorb_right, BondSpace& bm, BTensor& X, BTensor& Y, double* s_ent, bool& ok);
   void bond_update(int i, bool left_to_right, double tau, long long chi_max, double eps, bool backward,

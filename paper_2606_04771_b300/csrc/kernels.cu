@@ -924,6 +924,279 @@ __global__ void __launch_bounds__(CJT) jacobi_cluster_kernel(const Task* __restr
   }
 }
 
+// ---------------------------------------------------------------------------
+// The FP32 preconditioner as rings of warps inside thread-block clusters.  A
+// sector of n columns (n = q rounded up to even) is served by h = n/2 consecutive
+// warps of one cluster, warp k holding the two columns of round-robin pair k (the
+// pair tourney(r, k, n) gives) in registers: G rows lane + 32 j and the same rows of
+// V.  From one round to the next the circle method moves every column except column
+// 0 by one position, so warp k's first column goes to warp k-1 (warp 1's to warp 0's
+// second slot) and its second column to warp k+1 (warp 0's to warp 1's second slot,
+// the last warp's to its own first slot).  A round is therefore: the pair's
+// reduction and rotation in registers, the outgoing columns written into the
+// receivers' inboxes (shared memory of the receiving CTA, written through
+// distributed shared memory), a cluster barrier, the incoming columns read back.
+// The barrier that protects an inbox from being overwritten before its owner has read
+// it is split: its arrive follows the reads, its wait precedes the next writes, so
+// its latency overlaps the rotation.  Every pair, its order within a sweep and its
+// arithmetic (the expressions of warp_pair_cols) are those of the cooperative
+// kernel, so the results agree bit for bit; but no grid-wide barrier runs, a round
+// costs shared-memory traffic instead of an L2 round trip, and each sector stops after
+// its own first sweep without flags (its flags live in shared memory of the CTA that
+// holds its warp 0, in three slots used in turn so that a slot is cleared a sweep
+// before it is reused).  A per-CTA count of the cluster's unfinished sectors, read
+// after a barrier, ends the loop uniformly over the cluster.
+// ---------------------------------------------------------------------------
+constexpr int RING_NW = 16;    // warps per CTA
+constexpr int RING_CMAX = 16;  // CTAs per cluster: 8, or 16 (non-portable) for sectors of more than 256 columns
+constexpr int RING_RMAX = 10;  // rows per lane at most (p <= 320)
+
+__device__ __forceinline__ unsigned ring_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned ring_cluster_size() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned ring_cluster_id() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned ring_mapa(const void* p, unsigned rank) {
+  unsigned a = (unsigned)__cvta_generic_to_shared(p), r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void ring_st(unsigned addr, float2 v) {
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ void ring_st_s32(unsigned addr, int v) {
+  asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ring_ld_s32(unsigned addr) {
+  int v;
+  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+  return v;
+}
+__device__ __forceinline__ void ring_or(unsigned addr, int v) {
+  asm volatile("red.shared::cluster.or.b32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void ring_add(unsigned addr, int v) {
+  asm volatile("red.shared::cluster.add.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+// the cluster barrier in two halves (every thread of the cluster takes part in each;
+// .aligned: the warp is converged first)
+__device__ __forceinline__ void ring_arrive() {
+  __syncwarp();
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void ring_wait() {
+  __syncwarp();
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// the pair (x = the lower-indexed column) in registers: warp_pair_cols' expressions
+template <int R>
+__device__ __forceinline__ void ring_pair(float2 (&x)[R], float2 (&y)[R], float2 (&vx)[R], float2 (&vy)[R], float tol,
+                                          float tol_flag, float abs_flag, unsigned flag_addr) {
+  float sa = 0, sb = 0, cx = 0, cy = 0;
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    sa = fmaf(x[k].x, x[k].x, fmaf(x[k].y, x[k].y, sa));
+    sb = fmaf(y[k].x, y[k].x, fmaf(y[k].y, y[k].y, sb));
+    cx = fmaf(x[k].x, y[k].x, fmaf(x[k].y, y[k].y, cx));
+    cy = fmaf(x[k].x, y[k].y, fmaf(-x[k].y, y[k].x, cy));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sa += __shfl_xor_sync(0xffffffffu, sa, o);
+    sb += __shfl_xor_sync(0xffffffffu, sb, o);
+    cx += __shfl_xor_sync(0xffffffffu, cx, o);
+    cy += __shfl_xor_sync(0xffffffffu, cy, o);
+  }
+  const float ac = sqrt(fmaf(cx, cx, cy * cy));
+  if (ac == 0.0f || ac <= tol * sqrt(sa * sb)) return;  // warp-uniform
+  const float zeta = (sb - sa) / (2.0f * ac);
+  const float tt = (zeta >= 0 ? 1.0f : -1.0f) / (fabs(zeta) + sqrt(fmaf(zeta, zeta, 1.0f)));
+  const float cs = 1.0f / sqrt(fmaf(tt, tt, 1.0f)), sn = cs * tt;
+  const float ex = cx / ac, ey = cy / ac;
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    rot2<float, float2>(x[k], y[k], cs, sn, ex, ey);
+    rot2<float, float2>(vx[k], vy[k], cs, sn, ex, ey);
+  }
+  if ((threadIdx.x & 31) == 0 && ac > tol_flag * sqrt(sa * sb) && ac > abs_flag) ring_or(flag_addr, 1);
+}
+
+template <int R>
+__device__ __forceinline__ void ring_send(unsigned addr, const float2 (&g)[R], const float2 (&v)[R]) {
+  const unsigned lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    ring_st(addr + (lane + 32 * k) * 8u, g[k]);
+    ring_st(addr + (32 * R + lane + 32 * k) * 8u, v[k]);
+  }
+}
+template <int R>
+__device__ __forceinline__ void ring_recv(const float2* slot, float2 (&g)[R], float2 (&v)[R]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    g[k] = slot[lane + 32 * k];
+    v[k] = slot[32 * R + lane + 32 * k];
+  }
+}
+template <int R>
+__device__ __forceinline__ void ring_load(const Svd32Task& t, int c, float2 (&g)[R], float2 (&v)[R]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    const int r = lane + 32 * k;
+    g[k] = make_float2(0.0f, 0.0f);
+    v[k] = make_float2(0.0f, 0.0f);
+    if (c < t.q) {
+      if (r < t.p) g[k] = t.g[(long long)c * t.p + r];
+      if (r < t.q) v[k] = t.v[(long long)c * t.q + r];
+    }
+  }
+}
+template <int R>
+__device__ __forceinline__ void ring_store(const Svd32Task& t, int c, const float2 (&g)[R], const float2 (&v)[R]) {
+  if (c >= t.q) return;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    const int r = lane + 32 * k;
+    if (r < t.p) t.g[(long long)c * t.p + r] = g[k];
+    if (r < t.q) t.v[(long long)c * t.q + r] = v[k];
+  }
+}
+
+// round-robin players of warp k at round r of a sweep (m = n - 1 rounds)
+__device__ __forceinline__ void ring_players(int k, int r, int m, int& a, int& b) {
+  if (k == 0) {
+    a = 0;
+    b = 1 + r % m;
+  } else {
+    a = 1 + (k + r) % m;
+    b = 1 + (m - k + r) % m;
+  }
+}
+
+// host-built placement: one entry per warp slot of a cluster (C x RING_NW per
+// cluster, in cluster rank order); task < 0 marks an idle slot.  w0 is the slot of
+// the sector's warp 0 within its cluster.
+struct RingWarp {
+  int task, k, w0, h;
+};
+
+template <int R>
+__global__ void __launch_bounds__(RING_NW * 32, 1)
+    jacobi_ring_kernel(const Svd32Task* __restrict__ tasks, const RingWarp* __restrict__ slots,
+                       const int* __restrict__ cl_nsec, int max_sweeps, float tol, float tol_flag, float abs_flag,
+                       int* __restrict__ task_sweeps) {
+  extern __shared__ __align__(16) float2 ring_inbox[];  // [RING_NW][2][64 R]
+  __shared__ int flags_s[RING_NW][3];
+  __shared__ int live_s;
+  const unsigned rank = ring_rank(), csize = ring_cluster_size();
+  const int cl = (int)ring_cluster_id();
+  const int lw = threadIdx.x >> 5;
+  if (threadIdx.x < RING_NW * 3) (&flags_s[0][0])[threadIdx.x] = 0;
+  if (threadIdx.x == 0) live_s = cl_nsec[cl];
+  ring_arrive();
+  ring_wait();  // every CTA's flags and count are set before any remote access
+  const RingWarp wd = slots[((long long)cl * csize + rank) * RING_NW + lw];
+  bool active = wd.task >= 0;
+  Svd32Task t{};
+  int q = 0, m = 1, K = 0;
+  const int k = wd.k;
+  if (active) {
+    t = tasks[wd.task];
+    q = t.q;
+    m = q + (q & 1) - 1;
+    K = wd.h - 1;
+  }
+  constexpr int SLOT = 64 * R;  // float2 per inbox slot: G rows, then V rows
+  const float2* my_a = ring_inbox + (long long)(lw * 2) * SLOT;
+  const float2* my_b = my_a + SLOT;
+  // inbox slot s of the warp at cluster slot w (distributed shared memory address)
+  auto inbox = [&](int w, int s) { return ring_mapa(ring_inbox + (long long)((w % RING_NW) * 2 + s) * SLOT, w / RING_NW); };
+  const unsigned flag_base = active ? ring_mapa(&flags_s[wd.w0 % RING_NW][0], wd.w0 / RING_NW) : 0u;
+  unsigned dst_a = 0, dst_b = 0;  // where this warp's first and second columns go
+  if (active && K >= 1) {
+    const int w = wd.w0 + k;
+    if (k >= 2) dst_a = inbox(w - 1, 0);
+    else if (k == 1) dst_a = inbox(wd.w0, 1);
+    if (k == 0) dst_b = inbox(w + 1, 1);
+    else if (k < K) dst_b = inbox(w + 1, 1);
+  }
+  float2 ga[R], gb[R], va[R], vb[R];
+  int pa = 0, pb = 0, lr = 0, sweep = 0;
+  // a bound on the rounds (every sector ends within max_sweeps sweeps of at most
+  // 2 RING_CMAX RING_NW - 1 rounds): the loop ends even if the count were wrong
+  const long long round_cap = (long long)(max_sweeps > 0 ? max_sweeps : 1) * 2 * RING_CMAX * RING_NW + 8;
+  long long rounds = 0;
+  if (active) {
+    ring_players(k, 0, m, pa, pb);
+    ring_load<R>(t, pa, ga, va);
+    ring_load<R>(t, pb, gb, vb);
+  }
+  ring_arrive();
+  for (;;) {
+    if (active) {
+      if (lr == 0 && k == 0 && (threadIdx.x & 31) == 0) ring_st_s32(flag_base + 4u * ((sweep + 1) % 3), 0);
+      if (pa < q && pb < q) {
+        const unsigned fa = flag_base + 4u * (sweep % 3);
+        if (pa < pb) ring_pair<R>(ga, gb, va, vb, tol, tol_flag, abs_flag, fa);
+        else ring_pair<R>(gb, ga, vb, va, tol, tol_flag, abs_flag, fa);
+      }
+    }
+    ring_wait();
+    if (live_s == 0 || ++rounds > round_cap) break;  // uniform over the cluster (read after the barrier)
+    if (active && K >= 1) {
+      if (k >= 1) ring_send<R>(dst_a, ga, va);
+      if (k < K) ring_send<R>(dst_b, gb, vb);
+    }
+    ring_arrive();
+    ring_wait();
+    if (active) {
+      if (K >= 1) {
+        if (k == K) {
+#pragma unroll
+          for (int j = 0; j < R; ++j) {
+            ga[j] = gb[j];
+            va[j] = vb[j];
+          }
+        } else if (k >= 1) {
+          ring_recv<R>(my_a, ga, va);
+        }
+        ring_recv<R>(my_b, gb, vb);
+      }
+      lr = lr + 1 == m ? 0 : lr + 1;
+      ring_players(k, lr, m, pa, pb);
+      if (lr == 0) {  // a sweep ended: its flags are final (set before this round's barriers)
+        int f = 0;
+        if ((threadIdx.x & 31) == 0) f = ring_ld_s32(flag_base + 4u * (sweep % 3));
+        f = __shfl_sync(0xffffffffu, f, 0);
+        ++sweep;
+        if (f == 0 || sweep >= max_sweeps) {
+          ring_store<R>(t, pa, ga, va);
+          ring_store<R>(t, pb, gb, vb);
+          if (k == 0 && (threadIdx.x & 31) == 0) {
+            task_sweeps[wd.task] = sweep;
+            for (unsigned c = 0; c < csize; ++c) ring_add(ring_mapa(&live_s, c), -1);
+          }
+          active = false;
+        }
+      }
+    }
+    ring_arrive();
+  }
+}
+
 // V = identity for every problem
 __global__ void svd_init_v_kernel(const SvdTask* __restrict__ tasks) {
   const SvdTask t = tasks[blockIdx.x];
@@ -1121,6 +1394,120 @@ static int cluster_size_for(const std::vector<Task>& h_tasks, size_t* smem) {
   return 0;
 }
 
+// Whether the ring form may run the FP32 preconditioner: yes unless
+// TDVP_JACOBI_RING=0 (read at every call).
+static bool ring_enabled() {
+  const char* e = std::getenv("TDVP_JACOBI_RING");
+  return !(e && e[0] == '0');
+}
+
+// Placement of the ring form: sectors (q >= 2) by size, largest first, each on the
+// first cluster with room for its h = ceil(q/2) warps (first fit), at consecutive
+// warp slots; clusters of 8 CTAs, or of 16 when a sector needs more than 8 x RING_NW
+// warps.  Returns the rows per lane R (p <= 32 R) and sets *csize, or returns 0 when
+// some sector does not fit (more than RING_RMAX rows per lane, or more warps than a
+// cluster of 16 holds).
+static int ring_plan(const std::vector<Svd32Task>& h, std::vector<RingWarp>& slots, std::vector<int>& nsec,
+                     int* csize) {
+  std::vector<std::pair<int, int>> order;  // (h, task)
+  int pmax = 0, hmax = 0;
+  for (int e = 0; e < (int)h.size(); ++e) {
+    if (h[e].q < 2) continue;
+    const int hh = (h[e].q + (h[e].q & 1)) / 2;
+    if (h[e].p > 32 * RING_RMAX || hh > RING_CMAX * RING_NW) return 0;
+    order.push_back({hh, e});
+    pmax = std::max(pmax, h[e].p);
+    hmax = std::max(hmax, hh);
+  }
+  if (order.empty()) return 0;
+  const int C = hmax <= 8 * RING_NW ? 8 : RING_CMAX;
+  const int cap = C * RING_NW;
+  std::stable_sort(order.begin(), order.end(), [](const std::pair<int, int>& a, const std::pair<int, int>& b) {
+    return a.first > b.first;
+  });
+  std::vector<int> used;
+  slots.clear();
+  nsec.clear();
+  for (auto& o : order) {
+    int c = 0;
+    while (c < (int)used.size() && used[c] + o.first > cap) ++c;
+    if (c == (int)used.size()) {
+      used.push_back(0);
+      nsec.push_back(0);
+      slots.resize(used.size() * (size_t)cap, RingWarp{-1, 0, 0, 0});
+    }
+    const int w0 = used[c];
+    for (int k = 0; k < o.first; ++k) slots[(size_t)c * cap + w0 + k] = RingWarp{o.second, k, w0, o.first};
+    used[c] += o.first;
+    nsec[c] += 1;
+  }
+  *csize = C;
+  return std::max(2, (pmax + 31) / 32);
+}
+
+// check_only: 0 when one cluster of this shape fits on the device, else 1; otherwise
+// launch (0 on success, -1 on a launch error)
+template <int R>
+static int ring_launch_r(bool check_only, int C, const Svd32Task* d_tasks, const RingWarp* d_slots,
+                         const int* d_nsec, int ncl, int max_sweeps, float tol, float tol_flag, float abs_flag,
+                         int* task_sweeps, cudaStream_t s) {
+  auto kern = jacobi_ring_kernel<R>;
+  const size_t smem = (size_t)RING_NW * 2 * 64 * R * sizeof(float2);
+  static const bool attr = [smem] {  // once per instantiation, thread-safe (function-local static)
+    cudaFuncSetAttribute(jacobi_ring_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(jacobi_ring_kernel<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return true;
+  }();
+  (void)attr;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  cfg.gridDim = dim3((unsigned)(std::max(ncl, 1) * C));
+  cfg.blockDim = dim3(RING_NW * 32);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (check_only) {
+    int active = 0;
+    if (cudaOccupancyMaxActiveClusters(&active, (void*)kern, &cfg) != cudaSuccess || active < 1) {
+      cudaGetLastError();
+      return 1;
+    }
+    return 0;
+  }
+  note_launch();
+  return cudaLaunchKernelEx(&cfg, kern, d_tasks, d_slots, d_nsec, max_sweeps, tol, tol_flag, abs_flag,
+                            task_sweeps) == cudaSuccess
+             ? 0
+             : -1;
+}
+
+static int ring_launch(int R, bool check_only, int C, const Svd32Task* d_tasks, const RingWarp* d_slots,
+                       const int* d_nsec, int ncl, int max_sweeps, float tol, float tol_flag, float abs_flag,
+                       int* task_sweeps, cudaStream_t s) {
+#define TDVP_RING_CASE(RR)                                                                                     \
+  case RR:                                                                                                     \
+    return ring_launch_r<RR>(check_only, C, d_tasks, d_slots, d_nsec, ncl, max_sweeps, tol, tol_flag, abs_flag, \
+                             task_sweeps, s);
+  switch (R) {
+    TDVP_RING_CASE(2)
+    TDVP_RING_CASE(3)
+    TDVP_RING_CASE(4)
+    TDVP_RING_CASE(5)
+    TDVP_RING_CASE(6)
+    TDVP_RING_CASE(7)
+    TDVP_RING_CASE(8)
+    TDVP_RING_CASE(9)
+    TDVP_RING_CASE(10)
+    default: return 1;
+  }
+#undef TDVP_RING_CASE
+}
+
 template <class Task, class S, class C2>
 static int coop_run(const Task* d_tasks, const std::vector<Task>& h_tasks, int max_sweeps, S tol, S tol_flag,
                     S abs_flag, int* nonconv, bool with_v, JacobiProfile* prof, cudaStream_t s,
@@ -1171,7 +1558,20 @@ static int coop_run(const Task* d_tasks, const std::vector<Task>& h_tasks, int m
       }
     }
   }
-  const bool own_launch = all_fit || cl_size > 0;  // resident or cluster form
+  // the ring form (FP32 preconditioner): when enabled and every sector fits a ring
+  int ring_r = 0, ring_c = 0;
+  std::vector<RingWarp> ring_slots;
+  std::vector<int> ring_nsec;
+  if constexpr (std::is_same<Task, Svd32Task>::value) {
+    if (!all_fit && cl_size == 0 && ring_enabled()) ring_r = ring_plan(h_tasks, ring_slots, ring_nsec, &ring_c);
+    if (ring_r > 0 && ring_launch(ring_r, true, ring_c, nullptr, nullptr, nullptr, (int)ring_nsec.size(), 0, 0.f,
+                                  0.f, 0.f, nullptr, s) != 0) {
+      ring_r = 0;
+      ring_slots.clear();
+      ring_nsec.clear();
+    }
+  }
+  const bool own_launch = all_fit || cl_size > 0 || ring_r > 0;  // resident, cluster or ring form
   std::vector<char> resident(nt, 0);
   std::vector<int> rid;
   for (int e = 0; e < nt; ++e) {
@@ -1200,7 +1600,8 @@ static int coop_run(const Task* d_tasks, const std::vector<Task>& h_tasks, int m
   auto up16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
   const size_t b_work = up16(work.size() * sizeof(int2)), b_act = up16(active.size() * sizeof(int)),
                b_rid = up16(rid.size() * sizeof(int)), b_flags = up16((4 * (size_t)nt + 3) * sizeof(int));
-  const size_t b_lists = b_work + b_act + b_rid;
+  const size_t b_rslots = up16(ring_slots.size() * sizeof(RingWarp)), b_rnsec = up16(ring_nsec.size() * sizeof(int));
+  const size_t b_lists = b_work + b_act + b_rid + b_rslots + b_rnsec;
   char* region = nullptr;
   bool owned = false;
   if (scratch) {
@@ -1220,6 +1621,11 @@ static int coop_run(const Task* d_tasks, const std::vector<Task>& h_tasks, int m
     std::memcpy(host.data() + b_work, active.data(), active.size() * sizeof(int));
   }
   if (!rid.empty()) std::memcpy(host.data() + b_work + b_act, rid.data(), rid.size() * sizeof(int));
+  const size_t o_rslots = b_work + b_act + b_rid, o_rnsec = o_rslots + b_rslots;
+  if (!ring_slots.empty()) {
+    std::memcpy(host.data() + o_rslots, ring_slots.data(), ring_slots.size() * sizeof(RingWarp));
+    std::memcpy(host.data() + o_rnsec, ring_nsec.data(), ring_nsec.size() * sizeof(int));
+  }
   if (b_lists) cudaMemcpyAsync(region, host.data(), b_lists, cudaMemcpyHostToDevice, s);
   int2* d_work = work.empty() ? nullptr : reinterpret_cast<int2*>(region);
   int* d_active = work.empty() ? nullptr : reinterpret_cast<int*>(region + b_work);
@@ -1237,7 +1643,15 @@ static int coop_run(const Task* d_tasks, const std::vector<Task>& h_tasks, int m
     cudaEventRecord(ev[0], s);
   }
   int rc = 0;
-  if (!rid.empty() && cl_size > 0) {
+  if (!rid.empty() && ring_r > 0) {
+    if constexpr (std::is_same<Task, Svd32Task>::value) {
+      rc = ring_launch(ring_r, false, ring_c, d_tasks, reinterpret_cast<const RingWarp*>(region + o_rslots),
+                       reinterpret_cast<const int*>(region + o_rnsec), (int)ring_nsec.size(), max_sweeps, tol,
+                       tol_flag, abs_flag, rsw, s) == 0
+               ? 0
+               : -1;
+    }
+  } else if (!rid.empty() && cl_size > 0) {
     note_launch();
     if (cudaLaunchKernelEx(&cfg, cl_kern, (const Task*)d_tasks, (const int*)d_rid, max_sweeps, tol, tol_flag, abs_flag,
                            rsw, rnc) != cudaSuccess)
@@ -1289,8 +1703,9 @@ static int coop_run(const Task* d_tasks, const std::vector<Task>& h_tasks, int m
         prof->flops += (double)task_sweeps(e) * 0.5 * q * (q - 1) * (48.0 * p + (with_v ? 32.0 * q : 0.0));
       }
       prof->launches += 1;
-      if (!rid.empty() && cl_size == 0) prof->resident += 1;
+      if (!rid.empty() && cl_size == 0 && ring_r == 0) prof->resident += 1;
       if (!rid.empty() && cl_size > 0) prof->cluster += 1;
+      if (!rid.empty() && ring_r > 0) prof->ring += 1;
     }
   }
   if (prof) {
@@ -1423,6 +1838,113 @@ void launch_ns_coeff(const NsTask* tasks, int n, cudaStream_t s) {
     note_launch();
     ns_coeff_kernel<<<dim3(8, n), 256, 0, s>>>(tasks);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Gram finish of the mixed split: one simultaneous-rotation step on a column set G
+// whose Gram matrix K = G^H G is nearly diagonal (relative off-diagonals delta of
+// the FP32 level after the FP32 Jacobi).  Every pair (a < b) gets the complex Jacobi
+// rotation of warp_pair_cols computed from K_aa, K_bb and K_ab, and all of them act at
+// once: G <- G Z with Z_ab = sn e, Z_ba = -sn conj(e) (e = K_ab / |K_ab|) and
+// Z_ii = sqrt(1 - sum_k |Z_ki|^2).  To first order in delta this zeroes every K_ab
+// (the rotation angle tends to K_ab / (K_bb - K_aa)), so one step takes delta to
+// O(delta^2), the quadratic convergence of Jacobi methods, as two GEMMs instead of a
+// sweep of dependent rounds.  Simultaneous rotations interfere when an angle is large
+// (near-degenerate columns): pairs with |tan| > tmax are not rotated, and when such a
+// pair carries weight (|K_ab| > abs_flag) flags[1] is set so that the caller finishes
+// with the sequential Jacobi instead; a column whose rotations sum to more than a
+// quarter of its norm does the same.  flags[0] is set when some pair is above
+// tol_flag |g_a||g_b| and abs_flag (the stopping rule of the FP64 Jacobi stage);
+// flags[2] receives the largest such relative coupling (float bits, atomicMax).
+// Only the upper triangle of C is read (K_ab = conj(C[a][b]) for a < b), so the
+// Gram GEMM computes only the tiles on and above the diagonal.  The kernel writes
+// X^T = Z^T - I (row-major, xt[i][k] = Z[k][i] - [i == k]); the caller forms
+// G + G X.  One warp per row i of X^T (the coefficients of new column i).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) gram_rot_kernel(const GramTask* __restrict__ tasks, double tol, double tol_flag,
+                                                       double abs_flag, double tmax, int* __restrict__ flags) {
+  const GramTask t = tasks[blockIdx.y];
+  const int q = t.q;
+  const int lane = threadIdx.x & 31;
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  bool conv = false, big = false;
+  float worst = 0.0f;
+  for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < q; i += nw) {
+    const double si = t.c[(long long)i * q + i].x;
+    double sum = 0.0;
+    for (int k = lane; k < q; k += 32) {
+      if (k == i) continue;
+      const int a = k < i ? k : i, b = k < i ? i : k;
+      const double sa = a == i ? si : t.c[(long long)a * q + a].x;
+      const double sb = b == i ? si : t.c[(long long)b * q + b].x;
+      const cplx cab = t.c[(long long)a * q + b];  // K_ab = conj(C[a][b])
+      const double cx = cab.x, cy = -cab.y;
+      const double ac = sqrt(fma(cx, cx, cy * cy));
+      const double nrm = sqrt(sa * sb);
+      cplx z = {0.0, 0.0};
+      if (ac != 0.0 && ac > tol * nrm) {
+        const bool sig = ac > abs_flag;
+        if (sig && ac > tol_flag * nrm) {
+          conv = true;
+          worst = fmaxf(worst, (float)(ac / nrm));
+        }
+        const double zeta = (sb - sa) / (2.0 * ac);
+        const double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+        if (fabs(tt) <= tmax) {
+          const double cs = 1.0 / sqrt(fma(tt, tt, 1.0)), sn = cs * tt;
+          const double ex = cx / ac, ey = cy / ac;
+          if (k < i) z = {sn * ex, sn * ey};  // Z[a][b] with a = k, b = i
+          else z = {-sn * ex, sn * ey};       // Z[b][a] with a = i, b = k
+          sum = fma(z.x, z.x, fma(z.y, z.y, sum));
+        } else if (sig) {
+          big = true;
+        }
+      }
+      t.zt[(long long)i * q + k] = z;
+    }
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) {
+      if (sum > 0.25 && si > abs_flag) big = true;
+      const double d = sum < 1.0 ? sum : 1.0;
+      t.zt[(long long)i * q + i] = {-d / (1.0 + sqrt(1.0 - d)), 0.0};  // sqrt(1 - d) - 1 without cancellation
+    }
+  }
+  if (__any_sync(0xffffffffu, conv) && lane == 0) atomicOr(&flags[0], 1);
+  if (__any_sync(0xffffffffu, big) && lane == 0) atomicOr(&flags[1], 1);
+  for (int o = 16; o > 0; o >>= 1) worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+  if (lane == 0 && worst > 0.0f) atomicMax(reinterpret_cast<unsigned*>(&flags[2]), __float_as_uint(worst));
+}
+
+void launch_gram_rot(const GramTask* tasks, int n, int qmax, double tol, double tol_flag, double abs_flag,
+                     double tmax, int* flags, cudaStream_t s) {
+  if (n <= 0 || qmax <= 0) return;
+  const int bx = std::min(32, (qmax + 7) / 8);
+  note_launch();
+  gram_rot_kernel<<<dim3(bx, n), 256, 0, s>>>(tasks, tol, tol_flag, abs_flag, tmax, flags);
+}
+
+// g[e] += d[e] for e < n (the Gram step's G <- G + G X, in FP64)
+__global__ void add_inplace_kernel(cplx* __restrict__ g, const cplx* __restrict__ d, long long n) {
+  for (long long e = blockIdx.x * 256LL + threadIdx.x; e < n; e += (long long)gridDim.x * 256) {
+    const cplx a = g[e], b = d[e];
+    g[e] = {a.x + b.x, a.y + b.y};
+  }
+}
+
+void launch_add_inplace(cplx* g, const cplx* d, long long n, cudaStream_t s) {
+  if (n <= 0) return;
+  note_launch();
+  add_inplace_kernel<<<conv_grid(n), 256, 0, s>>>(g, d, n);
+}
+
+// singular values (column norms) and their descending order, as at the end of
+// run_jacobi_rounds, for column sets orthogonalised by another route
+void launch_svd_finish(const SvdTask* tasks, int n, int qmax, cudaStream_t s) {
+  if (n <= 0) return;
+  size_t fs = (size_t)std::max(qmax, 1) * sizeof(double);
+  if (fs > 48 * 1024) cudaFuncSetAttribute(svd_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fs);
+  note_launch();
+  svd_finish_kernel<<<n, 256, fs, s>>>(tasks);
 }
 
 void launch_jacobi_svd(const SvdTask* tasks, int ntasks, int max_q, int max_sweeps, double tol, int* status,

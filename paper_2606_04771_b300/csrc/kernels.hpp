@@ -107,7 +107,8 @@ void launch_jacobi_svd(const SvdTask* tasks, int ntasks, int max_q, int max_swee
 // is accumulated).  Every visited pair is counted as rotated.
 struct JacobiProfile {
   double ms = 0, flops = 0;
-  long long launches = 0, resident = 0, cluster = 0;  // calls; calls that ran CTA-resident, in clusters
+  // calls; calls that ran CTA-resident, in clusters, as rings of warps in clusters
+  long long launches = 0, resident = 0, cluster = 0, ring = 0;
 };
 // Device scratch for the small per-call work lists and flags of the Jacobi drivers:
 // returns at least `bytes` bytes of device memory, usable in stream order on the
@@ -140,6 +141,16 @@ int run_jacobi_rounds(const SvdTask* d_tasks, const std::vector<SvdTask>& h_task
 // caller.
 void launch_truncate(const TruncSector* secs, int nsec, const int* offs, int n, double eps, long long chi_max,
                      double degen, int* owner, int* order, int* kept, double* stats, double* vals, cudaStream_t s);
+// one simultaneous-rotation step of the mixed split's Gram finish over n column sets
+// (GramTask; reads the upper triangle of C, writes X^T = Z^T - I; flags: [0] not
+// converged, [1] fall back to the sequential Jacobi, [2] largest relative coupling
+// above tol_flag as float bits)
+void launch_gram_rot(const GramTask* tasks, int n, int qmax, double tol, double tol_flag, double abs_flag,
+                     double tmax, int* flags, cudaStream_t s);
+// g += d elementwise over n complex values
+void launch_add_inplace(cplx* g, const cplx* d, long long n, cudaStream_t s);
+// column norms of G as singular values, sorted descending with perm (SvdTask layout)
+void launch_svd_finish(const SvdTask* tasks, int n, int qmax, cudaStream_t s);
 void launch_wdot(const DotTask* tasks, int ntasks, double* partial, double* out, int nslots, cudaStream_t s);
 void launch_entropy(const TruncSector* secs, int nsec, double* out, cudaStream_t s);
 void launch_entropy_sv(const TruncSector* secs, int nsec, const double* g, double* out, cudaStream_t s);
