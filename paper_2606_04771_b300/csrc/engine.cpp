@@ -449,6 +449,7 @@ void HeffPlan::apply(const cplx* in, cplx* out, cudaStream_t s) const {
 // a Jacobi driver's sweep count, or the CUDA error of a failed cooperative launch
 static int jacobi(int sweeps) {
   if (sweeps == JACOBI_ENOMEM) throw Error(-3, "Jacobi work lists: device allocation failed");
+  if (sweeps == JACOBI_ETIMEOUT) throw Error(-7, "Jacobi ring: a neighbour exchange timed out");
   if (sweeps < 0) {
     cudaError_t e = cudaGetLastError();
     throw Error(-6, std::string("cooperative Jacobi launch failed: ") + cudaGetErrorString(e));
@@ -2220,6 +2221,17 @@ double Engine::split(BTensor& theta, const BondSpace& bl, const BondSpace& br, l
 // caller runs the FP64 split otherwise).
 // ---------------------------------------------------------------------------
 
+// Which of the mixed split's own products run as BF16x4 digit products on the tensor
+// cores instead of the FP64 pipe: a bit mask from TDVP_SPLIT_GEMM_TC (read at every
+// split; default 0, all FP64): 1 G = W V, 2 the kept basis W^H Z, 4 the Newton-Schulz
+// products, 8 the projection of theta onto the kept basis.  BF16x4 rounds to 2^-30 of
+// each operand row's and column's scale, which for the small singular values of a
+// graded spectrum is a large relative error.
+static int split_tc_mask() {
+  const char* e = std::getenv("TDVP_SPLIT_GEMM_TC");
+  return e && *e ? std::atoi(e) : 0;
+}
+
 // Whether the mixed split finishes with the Gram iteration (default) or with the
 // FP64 Jacobi (TDVP_SPLIT_FINISH=jacobi; read at every split).
 static bool gram_enabled() {
@@ -2266,7 +2278,7 @@ bool Engine::gram_finish(cplx* G, cplx* galt, const std::vector<int>& P, const s
     ntot = std::max(ntot, toff[g] + (long long)P[g] * Q[g]);
     flops += 12.0 * P[g] * (double)Q[g] * Q[g];  // upper half of C (4 p q^2) and G X (8 p q^2)
   }
-  if (qmax < 2) return false;
+  if (qmax < 2 || qmax > gram_qmax()) return false;
   DevBuf dK(kt * sizeof(cplx), stream_), dZ(kt * sizeof(cplx), stream_), dfl(8 * sizeof(int), stream_);
   cplx *Kb = dK.as<cplx>(), *Zb = dZ.as<cplx>();
   int* fl = dfl.as<int>();
@@ -2472,6 +2484,8 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
   }
   gather.finalize(stream_);
   gather.launch(stream_);
+  const int tcm = split_tc_mask();
+  auto kind_of = [&](int bit) { return (tcm & bit) ? 1 : -1; };
   // FP32 preconditioner
   launch_narrow(W64, W32, ttot, stream_);
   std::vector<Svd32Task> st32(ng);
@@ -2514,7 +2528,7 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
       gp.segs.push_back(sg);
       gp.tasks.push_back(t);
     }
-    gp.finalize(stream_);
+    gp.finalize(stream_, kind_of(1), dstatus_);
     gp.launch(stream_, Bases4{{0, 0, 0, 0}});
   }
   std::vector<SvdTask> st(ng);
@@ -2630,7 +2644,7 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
       xp.tasks.push_back(t);
       nt.push_back({Kb + koff[g], k});
     }
-    xp.finalize(stream_);
+    xp.finalize(stream_, kind_of(2), dstatus_);
     xp.launch(stream_, Bases4{{0, 0, 0, 0}});
     // Newton-Schulz in FP64: K = X^H X, F = 1.5 I - 0.5 K, X <- X F (Z reused as scratch)
     DevBuf dnt = upload(nt, stream_);
@@ -2675,10 +2689,10 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
         g2.segs.push_back(sh);
         g2.tasks.push_back(u);
       }
-      g1.finalize(stream_);
+      g1.finalize(stream_, kind_of(4), dstatus_);
       g1.launch(stream_, Bases4{{0, 0, 0, 0}});
       launch_ns_coeff(dnt.as<NsTask>(), (int)nt.size(), stream_);
-      g2.finalize(stream_);
+      g2.finalize(stream_, kind_of(4), dstatus_);
       g2.launch(stream_, Bases4{{0, 0, 0, 0}});
       CopyPlan back;  // X <- X F (Z holds X F; Z rows >= X rows, packed at the same pitch k)
       for (int g = 0; g < ng; ++g) {
@@ -2736,7 +2750,7 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
     pg.segs.push_back(sg);
     pg.tasks.push_back(t);
   }
-  pg.finalize(stream_);
+  pg.finalize(stream_, kind_of(8), dstatus_);
   pg.launch(stream_, Bases4{{0, 0, 0, 0}});
   // renormalise the kept state to unit norm
   DevBuf part((size_t)296 * sizeof(cplx), stream_), nrm(sizeof(cplx), stream_), dgs(sizeof(double), stream_);

@@ -948,7 +948,7 @@ __global__ void __launch_bounds__(CJT) jacobi_cluster_kernel(const Task* __restr
 // after a barrier, ends the loop uniformly over the cluster.
 // ---------------------------------------------------------------------------
 constexpr int RING_NW = 16;    // warps per CTA
-constexpr int RING_CMAX = 16;  // CTAs per cluster: 8, or 16 (non-portable) for sectors of more than 256 columns
+constexpr int RING_CMAX = 16;  // CTAs per cluster at most (more than 8 is a non-portable size)
 constexpr int RING_RMAX = 10;  // rows per lane at most (p <= 320)
 
 __device__ __forceinline__ unsigned ring_rank() {
@@ -1093,108 +1093,192 @@ struct RingWarp {
   int task, k, w0, h;
 };
 
+// mbarriers of the ring (local: shared::cta addresses; remote: shared::cluster addresses)
+constexpr int RING_WAIT_MAX = 1 << 22;  // polls of a ring wait before it reports a timeout
+__device__ __forceinline__ void ring_mb_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void ring_mb_arrive_remote(unsigned addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+// bounded wait for the completion of the phase with this parity; false on timeout
+__device__ __forceinline__ bool ring_mb_wait(unsigned long long* bar, unsigned parity) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+  for (int it = 0; it < RING_WAIT_MAX; ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void ring_red_add_release(unsigned addr, int v) {
+  asm volatile("red.release.cluster.shared::cluster.add.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ring_ld_acquire(unsigned addr) {
+  int v;
+  asm volatile("ld.acquire.cluster.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+  return v;
+}
+
 template <int R>
 __global__ void __launch_bounds__(RING_NW * 32, 1)
-    jacobi_ring_kernel(const Svd32Task* __restrict__ tasks, const RingWarp* __restrict__ slots,
-                       const int* __restrict__ cl_nsec, int max_sweeps, float tol, float tol_flag, float abs_flag,
-                       int* __restrict__ task_sweeps) {
+    jacobi_ring_kernel(const Svd32Task* __restrict__ tasks, const RingWarp* __restrict__ slots, int max_sweeps,
+                       float tol, float tol_flag, float abs_flag, int* __restrict__ task_sweeps,
+                       int* __restrict__ err) {
   extern __shared__ __align__(16) float2 ring_inbox[];  // [RING_NW][2][64 R]
-  __shared__ int flags_s[RING_NW][3];
-  __shared__ int live_s;
+  __shared__ __align__(8) unsigned long long full_bar[RING_NW], free_bar[RING_NW];
+  // per sector whose warp 0 sits at this local warp: rotation flags and sweep-end
+  // arrival counts, three slots each, used in turn
+  __shared__ int sect_s[RING_NW][6];
   const unsigned rank = ring_rank(), csize = ring_cluster_size();
   const int cl = (int)ring_cluster_id();
-  const int lw = threadIdx.x >> 5;
-  if (threadIdx.x < RING_NW * 3) (&flags_s[0][0])[threadIdx.x] = 0;
-  if (threadIdx.x == 0) live_s = cl_nsec[cl];
-  ring_arrive();
-  ring_wait();  // every CTA's flags and count are set before any remote access
+  const int lw = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const RingWarp wd = slots[((long long)cl * csize + rank) * RING_NW + lw];
-  bool active = wd.task >= 0;
+  const bool member = wd.task >= 0;
   Svd32Task t{};
   int q = 0, m = 1, K = 0;
-  const int k = wd.k;
-  if (active) {
+  const int k = wd.k, w = wd.w0 + wd.k;
+  if (member) {
     t = tasks[wd.task];
     q = t.q;
     m = q + (q & 1) - 1;
     K = wd.h - 1;
   }
+  // columns received (full_bar arrivals) and sent (free_bar arrivals) per round: one for
+  // the first and the last warp of a ring, two in between
+  const int n_io = (member && K >= 1) ? ((k == 0 || k == K) ? 1 : 2) : 1;
+  if (threadIdx.x < RING_NW * 6) (&sect_s[0][0])[threadIdx.x] = 0;
+  if (lane == 0) {
+    ring_mb_init(&full_bar[lw], (unsigned)n_io);
+    ring_mb_init(&free_bar[lw], (unsigned)n_io);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  ring_arrive();
+  ring_wait();  // every CTA's barriers and counters are set before any remote access
   constexpr int SLOT = 64 * R;  // float2 per inbox slot: G rows, then V rows
   const float2* my_a = ring_inbox + (long long)(lw * 2) * SLOT;
   const float2* my_b = my_a + SLOT;
-  // inbox slot s of the warp at cluster slot w (distributed shared memory address)
-  auto inbox = [&](int w, int s) { return ring_mapa(ring_inbox + (long long)((w % RING_NW) * 2 + s) * SLOT, w / RING_NW); };
-  const unsigned flag_base = active ? ring_mapa(&flags_s[wd.w0 % RING_NW][0], wd.w0 / RING_NW) : 0u;
-  unsigned dst_a = 0, dst_b = 0;  // where this warp's first and second columns go
-  if (active && K >= 1) {
-    const int w = wd.w0 + k;
-    if (k >= 2) dst_a = inbox(w - 1, 0);
-    else if (k == 1) dst_a = inbox(wd.w0, 1);
-    if (k == 0) dst_b = inbox(w + 1, 1);
-    else if (k < K) dst_b = inbox(w + 1, 1);
+  auto inbox = [&](int x, int s) {
+    return ring_mapa(ring_inbox + (long long)((x % RING_NW) * 2 + s) * SLOT, x / RING_NW);
+  };
+  auto full_of = [&](int x) { return ring_mapa(&full_bar[x % RING_NW], x / RING_NW); };
+  auto free_of = [&](int x) { return ring_mapa(&free_bar[x % RING_NW], x / RING_NW); };
+  unsigned sect = 0, dst_a = 0, dst_b = 0, full_a = 0, full_b = 0, free_a = 0, free_b = 0;
+  if (member) {
+    sect = ring_mapa(&sect_s[wd.w0 % RING_NW][0], wd.w0 / RING_NW);
+    if (K >= 1) {
+      // sends: first column to warp k-1 (warp 1's to warp 0's second slot), second to warp k+1
+      if (k >= 2) {
+        dst_a = inbox(w - 1, 0);
+        full_a = full_of(w - 1);
+      } else if (k == 1) {
+        dst_a = inbox(wd.w0, 1);
+        full_a = full_of(wd.w0);
+      }
+      if (k < K) {
+        dst_b = inbox(w + 1, 1);
+        full_b = full_of(w + 1);
+      }
+      // receives: second column from warp k-1 (warp 0's from warp 1), first from warp k+1
+      free_b = free_of(k == 0 ? w + 1 : w - 1);
+      if (k >= 1 && k < K) free_a = free_of(w + 1);
+    }
   }
   float2 ga[R], gb[R], va[R], vb[R];
   int pa = 0, pb = 0, lr = 0, sweep = 0;
-  // a bound on the rounds (every sector ends within max_sweeps sweeps of at most
-  // 2 RING_CMAX RING_NW - 1 rounds): the loop ends even if the count were wrong
-  const long long round_cap = (long long)(max_sweeps > 0 ? max_sweeps : 1) * 2 * RING_CMAX * RING_NW + 8;
-  long long rounds = 0;
-  if (active) {
+  unsigned full_par = 0, free_par = 0;
+  long long gr = 0;
+  bool failed = false;
+  if (member) {
     ring_players(k, 0, m, pa, pb);
     ring_load<R>(t, pa, ga, va);
     ring_load<R>(t, pb, gb, vb);
   }
-  ring_arrive();
-  for (;;) {
-    if (active) {
-      if (lr == 0 && k == 0 && (threadIdx.x & 31) == 0) ring_st_s32(flag_base + 4u * ((sweep + 1) % 3), 0);
-      if (pa < q && pb < q) {
-        const unsigned fa = flag_base + 4u * (sweep % 3);
-        if (pa < pb) ring_pair<R>(ga, gb, va, vb, tol, tol_flag, abs_flag, fa);
-        else ring_pair<R>(gb, ga, vb, va, tol, tol_flag, abs_flag, fa);
+  while (member) {
+    if (lr == 0 && k == 0 && lane == 0) {  // clear the next sweep's slots (their last readers are done)
+      ring_st_s32(sect + 4u * ((sweep + 1) % 3), 0);
+      ring_st_s32(sect + 4u * (3 + (sweep + 1) % 3), 0);
+    }
+    if (pa < q && pb < q) {
+      const unsigned fa = sect + 4u * (sweep % 3);
+      if (pa < pb) ring_pair<R>(ga, gb, va, vb, tol, tol_flag, abs_flag, fa);
+      else ring_pair<R>(gb, ga, vb, va, tol, tol_flag, abs_flag, fa);
+    }
+    if (lr == m - 1) {  // the sweep's last round: wait until every warp of the ring has rotated
+      __syncwarp();
+      int f = 0, ok = 1;
+      if (lane == 0) {
+        const unsigned cnt = sect + 4u * (3 + sweep % 3);
+        ring_red_add_release(cnt, 1);
+        int it = 0;
+        while (ring_ld_acquire(cnt) < wd.h && ++it < RING_WAIT_MAX) {
+        }
+        ok = it < RING_WAIT_MAX;
+        f = ring_ld_acquire(sect + 4u * (sweep % 3));
+      }
+      f = __shfl_sync(0xffffffffu, f, 0);
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      ++sweep;
+      if (!ok) {
+        failed = true;
+        break;
+      }
+      if (f == 0 || sweep >= max_sweeps) {  // converged: this warp holds the pair it just rotated
+        ring_store<R>(t, pa, ga, va);
+        ring_store<R>(t, pb, gb, vb);
+        if (k == 0 && lane == 0) task_sweeps[wd.task] = sweep;
+        break;
       }
     }
-    ring_wait();
-    if (live_s == 0 || ++rounds > round_cap) break;  // uniform over the cluster (read after the barrier)
-    if (active && K >= 1) {
+    if (K >= 1) {
+      if (gr >= 1) {  // the receivers have read what this warp sent in the previous round
+        if (!ring_mb_wait(&free_bar[lw], free_par)) {
+          failed = true;
+          break;
+        }
+        free_par ^= 1u;
+      }
       if (k >= 1) ring_send<R>(dst_a, ga, va);
       if (k < K) ring_send<R>(dst_b, gb, vb);
-    }
-    ring_arrive();
-    ring_wait();
-    if (active) {
-      if (K >= 1) {
-        if (k == K) {
+      __syncwarp();  // every lane's stores precede lane 0's release
+      if (lane == 0) {
+        if (k >= 1) ring_mb_arrive_remote(full_a);
+        if (k < K) ring_mb_arrive_remote(full_b);
+      }
+      if (k == K) {
 #pragma unroll
-          for (int j = 0; j < R; ++j) {
-            ga[j] = gb[j];
-            va[j] = vb[j];
-          }
-        } else if (k >= 1) {
-          ring_recv<R>(my_a, ga, va);
+        for (int j = 0; j < R; ++j) {
+          ga[j] = gb[j];
+          va[j] = vb[j];
         }
-        ring_recv<R>(my_b, gb, vb);
       }
-      lr = lr + 1 == m ? 0 : lr + 1;
-      ring_players(k, lr, m, pa, pb);
-      if (lr == 0) {  // a sweep ended: its flags are final (set before this round's barriers)
-        int f = 0;
-        if ((threadIdx.x & 31) == 0) f = ring_ld_s32(flag_base + 4u * (sweep % 3));
-        f = __shfl_sync(0xffffffffu, f, 0);
-        ++sweep;
-        if (f == 0 || sweep >= max_sweeps) {
-          ring_store<R>(t, pa, ga, va);
-          ring_store<R>(t, pb, gb, vb);
-          if (k == 0 && (threadIdx.x & 31) == 0) {
-            task_sweeps[wd.task] = sweep;
-            for (unsigned c = 0; c < csize; ++c) ring_add(ring_mapa(&live_s, c), -1);
-          }
-          active = false;
-        }
+      if (!ring_mb_wait(&full_bar[lw], full_par)) {
+        failed = true;
+        break;
+      }
+      full_par ^= 1u;
+      if (k >= 1 && k < K) ring_recv<R>(my_a, ga, va);
+      ring_recv<R>(my_b, gb, vb);
+      __syncwarp();  // every lane's inbox reads precede the credits
+      if (lane == 0) {
+        ring_mb_arrive_remote(free_b);
+        if (k >= 1 && k < K) ring_mb_arrive_remote(free_a);
       }
     }
-    ring_arrive();
+    ++gr;
+    lr = lr + 1 == m ? 0 : lr + 1;
+    ring_players(k, lr, m, pa, pb);
   }
+  if (failed && lane == 0) atomicOr(err, 1);
+  // no CTA leaves while another may still write to its shared memory
+  ring_arrive();
+  ring_wait();
 }
 
 // V = identity for every problem
@@ -1403,14 +1487,16 @@ static bool ring_enabled() {
 
 // Placement of the ring form: sectors (q >= 2) by size, largest first, each on the
 // first cluster with room for its h = ceil(q/2) warps (first fit), at consecutive
-// warp slots; clusters of 8 CTAs, or of 16 when a sector needs more than 8 x RING_NW
-// warps.  Returns the rows per lane R (p <= 32 R) and sets *csize, or returns 0 when
-// some sector does not fit (more than RING_RMAX rows per lane, or more warps than a
-// cluster of 16 holds).
+// warp slots.  Clusters have the fewest CTAs that hold the largest sector (at least
+// 2, at most 16; above 8 the size is non-portable): small clusters keep the barrier
+// cheap and let more clusters be resident at once.  Returns the rows per lane R
+// (p <= 32 R) and sets *csize, or returns 0 when some sector does not fit (more than
+// RING_RMAX rows per lane, or more warps than a cluster of 16 holds).
 static int ring_plan(const std::vector<Svd32Task>& h, std::vector<RingWarp>& slots, std::vector<int>& nsec,
                      int* csize) {
   std::vector<std::pair<int, int>> order;  // (h, task)
   int pmax = 0, hmax = 0;
+  long long hsum = 0;
   for (int e = 0; e < (int)h.size(); ++e) {
     if (h[e].q < 2) continue;
     const int hh = (h[e].q + (h[e].q & 1)) / 2;
@@ -1418,9 +1504,10 @@ static int ring_plan(const std::vector<Svd32Task>& h, std::vector<RingWarp>& slo
     order.push_back({hh, e});
     pmax = std::max(pmax, h[e].p);
     hmax = std::max(hmax, hh);
+    hsum += hh;
   }
   if (order.empty()) return 0;
-  const int C = hmax <= 8 * RING_NW ? 8 : RING_CMAX;
+  const int C = std::max(2, (hmax + RING_NW - 1) / RING_NW);
   const int cap = C * RING_NW;
   std::stable_sort(order.begin(), order.end(), [](const std::pair<int, int>& a, const std::pair<int, int>& b) {
     return a.first > b.first;
@@ -1442,15 +1529,20 @@ static int ring_plan(const std::vector<Svd32Task>& h, std::vector<RingWarp>& slo
     nsec[c] += 1;
   }
   *csize = C;
+  if (std::getenv("TDVP_RING_DEBUG")) {
+    std::fprintf(stderr, "ring: %zu sectors, sum h %lld, h max %d, p max %d, clusters %zu of %d CTAs\n",
+                 order.size(), hsum, hmax, pmax, used.size(), C);
+    for (auto& o : order) std::fprintf(stderr, "  sector p %d q %d\n", h[o.second].p, h[o.second].q);
+  }
   return std::max(2, (pmax + 31) / 32);
 }
 
 // check_only: 0 when one cluster of this shape fits on the device, else 1; otherwise
 // launch (0 on success, -1 on a launch error)
 template <int R>
-static int ring_launch_r(bool check_only, int C, const Svd32Task* d_tasks, const RingWarp* d_slots,
-                         const int* d_nsec, int ncl, int max_sweeps, float tol, float tol_flag, float abs_flag,
-                         int* task_sweeps, cudaStream_t s) {
+static int ring_launch_r(bool check_only, int C, const Svd32Task* d_tasks, const RingWarp* d_slots, int ncl,
+                         int max_sweeps, float tol, float tol_flag, float abs_flag, int* task_sweeps, int* err,
+                         cudaStream_t s) {
   auto kern = jacobi_ring_kernel<R>;
   const size_t smem = (size_t)RING_NW * 2 * 64 * R * sizeof(float2);
   static const bool attr = [smem] {  // once per instantiation, thread-safe (function-local static)
@@ -1477,22 +1569,23 @@ static int ring_launch_r(bool check_only, int C, const Svd32Task* d_tasks, const
       cudaGetLastError();
       return 1;
     }
+    if (std::getenv("TDVP_RING_DEBUG")) std::fprintf(stderr, "ring: %d clusters of %d CTAs resident at once\n", active, C);
     return 0;
   }
   note_launch();
-  return cudaLaunchKernelEx(&cfg, kern, d_tasks, d_slots, d_nsec, max_sweeps, tol, tol_flag, abs_flag,
-                            task_sweeps) == cudaSuccess
+  return cudaLaunchKernelEx(&cfg, kern, d_tasks, d_slots, max_sweeps, tol, tol_flag, abs_flag, task_sweeps,
+                            err) == cudaSuccess
              ? 0
              : -1;
 }
 
-static int ring_launch(int R, bool check_only, int C, const Svd32Task* d_tasks, const RingWarp* d_slots,
-                       const int* d_nsec, int ncl, int max_sweeps, float tol, float tol_flag, float abs_flag,
-                       int* task_sweeps, cudaStream_t s) {
+static int ring_launch(int R, bool check_only, int C, const Svd32Task* d_tasks, const RingWarp* d_slots, int ncl,
+                       int max_sweeps, float tol, float tol_flag, float abs_flag, int* task_sweeps, int* err,
+                       cudaStream_t s) {
 #define TDVP_RING_CASE(RR)                                                                                     \
   case RR:                                                                                                     \
-    return ring_launch_r<RR>(check_only, C, d_tasks, d_slots, d_nsec, ncl, max_sweeps, tol, tol_flag, abs_flag, \
-                             task_sweeps, s);
+    return ring_launch_r<RR>(check_only, C, d_tasks, d_slots, ncl, max_sweeps, tol, tol_flag, abs_flag, \
+                             task_sweeps, err, s);
   switch (R) {
     TDVP_RING_CASE(2)
     TDVP_RING_CASE(3)
@@ -1564,8 +1657,8 @@ static int coop_run(const Task* d_tasks, const std::vector<Task>& h_tasks, int m
   std::vector<int> ring_nsec;
   if constexpr (std::is_same<Task, Svd32Task>::value) {
     if (!all_fit && cl_size == 0 && ring_enabled()) ring_r = ring_plan(h_tasks, ring_slots, ring_nsec, &ring_c);
-    if (ring_r > 0 && ring_launch(ring_r, true, ring_c, nullptr, nullptr, nullptr, (int)ring_nsec.size(), 0, 0.f,
-                                  0.f, 0.f, nullptr, s) != 0) {
+    if (ring_r > 0 && ring_launch(ring_r, true, ring_c, nullptr, nullptr, (int)ring_nsec.size(), 0, 0.f, 0.f, 0.f,
+                                  nullptr, nullptr, s) != 0) {
       ring_r = 0;
       ring_slots.clear();
       ring_nsec.clear();
@@ -1599,7 +1692,7 @@ static int coop_run(const Task* d_tasks, const std::vector<Task>& h_tasks, int m
   // non-convergence of the resident sectors [1], sweeps of the resident sectors [nt]
   auto up16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
   const size_t b_work = up16(work.size() * sizeof(int2)), b_act = up16(active.size() * sizeof(int)),
-               b_rid = up16(rid.size() * sizeof(int)), b_flags = up16((4 * (size_t)nt + 3) * sizeof(int));
+               b_rid = up16(rid.size() * sizeof(int)), b_flags = up16((4 * (size_t)nt + 4) * sizeof(int));
   const size_t b_rslots = up16(ring_slots.size() * sizeof(RingWarp)), b_rnsec = up16(ring_nsec.size() * sizeof(int));
   const size_t b_lists = b_work + b_act + b_rid + b_rslots + b_rnsec;
   char* region = nullptr;
@@ -1635,7 +1728,8 @@ static int coop_run(const Task* d_tasks, const std::vector<Task>& h_tasks, int m
   int* tsw = out + 2;
   int* rnc = tsw + nt;
   int* rsw = rnc + 1;
-  cudaMemsetAsync(out, 0, (2 * nt + 3) * sizeof(int), s);
+  int* ring_err = rsw + nt;
+  cudaMemsetAsync(out, 0, (2 * nt + 4) * sizeof(int), s);
   cudaEvent_t ev[2] = {nullptr, nullptr};
   if (prof) {
     cudaEventCreate(&ev[0]);
@@ -1646,8 +1740,7 @@ static int coop_run(const Task* d_tasks, const std::vector<Task>& h_tasks, int m
   if (!rid.empty() && ring_r > 0) {
     if constexpr (std::is_same<Task, Svd32Task>::value) {
       rc = ring_launch(ring_r, false, ring_c, d_tasks, reinterpret_cast<const RingWarp*>(region + o_rslots),
-                       reinterpret_cast<const int*>(region + o_rnsec), (int)ring_nsec.size(), max_sweeps, tol,
-                       tol_flag, abs_flag, rsw, s) == 0
+                       (int)ring_nsec.size(), max_sweeps, tol, tol_flag, abs_flag, rsw, ring_err, s) == 0
                ? 0
                : -1;
     }
@@ -1686,11 +1779,13 @@ static int coop_run(const Task* d_tasks, const std::vector<Task>& h_tasks, int m
     }
   }
   if (prof) cudaEventRecord(ev[1], s);
-  std::vector<int> h(3 + 2 * nt, 0);
+  std::vector<int> h(4 + 2 * nt, 0);
   int sweeps = -1, nc = 1;
+  bool timed_out = false;
   if (rc == 0) {
-    cudaMemcpyAsync(h.data(), out, (3 + 2 * nt) * sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(h.data(), out, (4 + 2 * nt) * sizeof(int), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
+    timed_out = h[3 + 2 * nt] != 0;  // a ring's neighbour exchange gave up waiting
     auto task_sweeps = [&](int e) { return resident[e] ? h[3 + nt + e] : h[2 + e]; };
     sweeps = h[0];  // the cooperative launch's sweeps (0 when it did not run)
     for (int e : rid) sweeps = max(sweeps, task_sweeps(e));
@@ -1714,6 +1809,7 @@ static int coop_run(const Task* d_tasks, const std::vector<Task>& h_tasks, int m
   }
   if (owned) cudaFreeAsync(region, s);
   if (nonconv) *nonconv = nc;
+  if (timed_out) return JACOBI_ETIMEOUT;
   return rc == 0 ? sweeps : -1;
 }
 
@@ -1865,19 +1961,32 @@ __global__ void __launch_bounds__(256) gram_rot_kernel(const GramTask* __restric
                                                        double abs_flag, double tmax, int* __restrict__ flags) {
   const GramTask t = tasks[blockIdx.y];
   const int q = t.q;
-  const int lane = threadIdx.x & 31;
-  const int nw = gridDim.x * (blockDim.x >> 5);
+  const int i0 = blockIdx.x * 8;  // this CTA's eight rows of X^T (new columns i0 .. i0 + 7)
+  if (i0 >= q) return;            // uniform over the CTA
+  // staged in shared memory: the diagonal of C, and its columns i0 .. i0 + 7 (row k,
+  // column i0 + j at colblk[k * 9 + j]; 9: fewer bank conflicts), which hold K_ki = C[k][i]
+  // for k < i; the rest of a row comes from C's row i, read contiguously
+  extern __shared__ double gram_smem[];
+  double* diag = gram_smem;
+  cplx* colblk = reinterpret_cast<cplx*>(gram_smem + ((q + 1) & ~1));
+  for (int e = threadIdx.x; e < q; e += blockDim.x) diag[e] = t.c[(long long)e * q + e].x;
+  for (int e = threadIdx.x; e < q * 8; e += blockDim.x) {
+    const int k = e >> 3, j = e & 7;
+    colblk[k * 9 + j] = i0 + j < q ? t.c[(long long)k * q + i0 + j] : cplx{0.0, 0.0};
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int i = i0 + w;
   bool conv = false, big = false;
   float worst = 0.0f;
-  for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < q; i += nw) {
-    const double si = t.c[(long long)i * q + i].x;
+  if (i < q) {
+    const double si = diag[i];
     double sum = 0.0;
     for (int k = lane; k < q; k += 32) {
       if (k == i) continue;
-      const int a = k < i ? k : i, b = k < i ? i : k;
-      const double sa = a == i ? si : t.c[(long long)a * q + a].x;
-      const double sb = b == i ? si : t.c[(long long)b * q + b].x;
-      const cplx cab = t.c[(long long)a * q + b];  // K_ab = conj(C[a][b])
+      const bool lower = k < i;  // pair (a, b) = (k, i), else (i, k)
+      const double sa = lower ? diag[k] : si, sb = lower ? si : diag[k];
+      const cplx cab = lower ? colblk[k * 9 + w] : t.c[(long long)i * q + k];  // C[a][b]; K_ab = conj(C[a][b])
       const double cx = cab.x, cy = -cab.y;
       const double ac = sqrt(fma(cx, cx, cy * cy));
       const double nrm = sqrt(sa * sb);
@@ -1893,7 +2002,7 @@ __global__ void __launch_bounds__(256) gram_rot_kernel(const GramTask* __restric
         if (fabs(tt) <= tmax) {
           const double cs = 1.0 / sqrt(fma(tt, tt, 1.0)), sn = cs * tt;
           const double ex = cx / ac, ey = cy / ac;
-          if (k < i) z = {sn * ex, sn * ey};  // Z[a][b] with a = k, b = i
+          if (lower) z = {sn * ex, sn * ey};  // Z[a][b] with a = k, b = i
           else z = {-sn * ex, sn * ey};       // Z[b][a] with a = i, b = k
           sum = fma(z.x, z.x, fma(z.y, z.y, sum));
         } else if (sig) {
@@ -1915,12 +2024,25 @@ __global__ void __launch_bounds__(256) gram_rot_kernel(const GramTask* __restric
   if (lane == 0 && worst > 0.0f) atomicMax(reinterpret_cast<unsigned*>(&flags[2]), __float_as_uint(worst));
 }
 
+// shared memory of gram_rot_kernel for column sets of at most qmax columns
+static size_t gram_smem_bytes(int qmax) {
+  return (size_t)((qmax + 1) & ~1) * sizeof(double) + (size_t)qmax * 9 * sizeof(cplx);
+}
+
+int gram_qmax() { return 1400; }  // 1400 columns: 208 KB of staging
+
 void launch_gram_rot(const GramTask* tasks, int n, int qmax, double tol, double tol_flag, double abs_flag,
                      double tmax, int* flags, cudaStream_t s) {
   if (n <= 0 || qmax <= 0) return;
-  const int bx = std::min(32, (qmax + 7) / 8);
+  static const bool attr = [] {  // once per process, thread-safe (function-local static)
+    cudaFuncSetAttribute(gram_rot_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)gram_smem_bytes(gram_qmax()));
+    return true;
+  }();
+  (void)attr;
   note_launch();
-  gram_rot_kernel<<<dim3(bx, n), 256, 0, s>>>(tasks, tol, tol_flag, abs_flag, tmax, flags);
+  gram_rot_kernel<<<dim3((qmax + 7) / 8, n), 256, gram_smem_bytes(qmax), s>>>(tasks, tol, tol_flag, abs_flag, tmax,
+                                                                              flags);
 }
 
 // g[e] += d[e] for e < n (the Gram step's G <- G + G X, in FP64)

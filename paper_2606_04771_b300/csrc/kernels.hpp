@@ -117,6 +117,8 @@ struct JacobiProfile {
 // region can be had the drivers launch nothing and return JACOBI_ENOMEM.
 using ScratchFn = std::function<void*(size_t)>;
 constexpr int JACOBI_ENOMEM = -3;
+// a bounded wait of the ring form gave up (the kernel stopped; the result is invalid)
+constexpr int JACOBI_ETIMEOUT = -4;
 // FP32 round-robin Jacobi on complex64 working copies (p >= q), accumulating V
 // (from the identity); returns the sweeps run
 int run_jacobi_rounds32(const Svd32Task* d_tasks, const std::vector<Svd32Task>& h_tasks, int max_sweeps, float tol,
@@ -147,6 +149,8 @@ void launch_truncate(const TruncSector* secs, int nsec, const int* offs, int n, 
 // above tol_flag as float bits)
 void launch_gram_rot(const GramTask* tasks, int n, int qmax, double tol, double tol_flag, double abs_flag,
                      double tmax, int* flags, cudaStream_t s);
+// the most columns a column set of the Gram finish may have (its staging in shared memory)
+int gram_qmax();
 // g += d elementwise over n complex values
 void launch_add_inplace(cplx* g, const cplx* d, long long n, cudaStream_t s);
 // column norms of G as singular values, sorted descending with perm (SvdTask layout)
