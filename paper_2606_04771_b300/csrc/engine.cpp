@@ -116,6 +116,20 @@ void GemmPlan::finalize(cudaStream_t s, int kind_, int* status_) {
     for (int a = 0; a < t.tiles_m; ++a)
       for (int b = 0; b < t.tiles_n; ++b) tiles.push_back(make_int3(i, a, b));
   }
+  if (kind < 0) {
+    // FP64 kernel: one CTA per tile, scheduled in list order; the most expensive tiles
+    // first (longest-processing-time order) keep the last wave short.  Each tile is
+    // computed the same way in any order.
+    std::vector<long long> ksum(tasks.size(), 0);
+    for (int i = 0; i < (int)tasks.size(); ++i)
+      for (int k = 0; k < tasks[i].seg_count; ++k) ksum[i] += segs[tasks[i].seg_begin + k].k;
+    auto cost = [&](const int3& t) {
+      const GemmTask& g = tasks[t.x];
+      const long long r = std::min(tm, g.rows - t.y * tm), c = std::min(tm, g.cols - t.z * tm);
+      return ksum[t.x] * r * c;
+    };
+    std::stable_sort(tiles.begin(), tiles.end(), [&](const int3& a, const int3& b) { return cost(a) > cost(b); });
+  }
   if (!rowoffs.empty()) {
     drow = upload(rowoffs, s);
     for (int i = 0; i < (int)tasks.size(); ++i)
@@ -2232,6 +2246,12 @@ static int split_tc_mask() {
   return e && *e ? std::atoi(e) : 0;
 }
 
+// a float from the environment (read at every call), or the default
+static float env_float(const char* name, float dflt) {
+  const char* e = std::getenv(name);
+  return e && *e ? (float)std::atof(e) : dflt;
+}
+
 // Whether the mixed split finishes with the Gram iteration (default) or with the
 // FP64 Jacobi (TDVP_SPLIT_FINISH=jacobi; read at every split).
 static bool gram_enabled() {
@@ -2499,9 +2519,15 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
   }
   DevBuf dst32 = upload(st32, stream_);
   // FP32 stage: rotate while |g_i^H g_j| > 2e-5 |g_i||g_j|, at most 24 sweeps (it
-  // need not converge: the FP64 stage finishes whatever is left)
+  // need not converge: the FP64 stage finishes whatever is left).  A sweep ends the
+  // stage when its rotations were all below that or below min(1e-10, eps / 10) in
+  // absolute terms (theta has unit norm): couplings between columns of negligible
+  // weight, which FP32 cannot resolve anyway, do not keep it going (the FP64 finish
+  // uses the same kind of absolute floor).  TDVP_FP32_TOL / TDVP_FP32_ABS override.
+  const float abs32 = (float)std::min(1e-10, 0.1 * eps);
   const int sw32 =
-      jacobi(run_jacobi_rounds32(dst32.as<Svd32Task>(), st32, 24, 2e-5f, 0.0f, stream_, &stats_.jacobi32, jscratch()));
+      jacobi(run_jacobi_rounds32(dst32.as<Svd32Task>(), st32, 24, env_float("TDVP_FP32_TOL", 2e-5f),
+                                 env_float("TDVP_FP32_ABS", abs32), stream_, &stats_.jacobi32, jscratch()));
   ok = true;
   stats_.sweeps32 += sw32;
   stats_.splits += 1;

@@ -1987,23 +1987,27 @@ __global__ void __launch_bounds__(256) gram_rot_kernel(const GramTask* __restric
       const bool lower = k < i;  // pair (a, b) = (k, i), else (i, k)
       const double sa = lower ? diag[k] : si, sb = lower ? si : diag[k];
       const cplx cab = lower ? colblk[k * 9 + w] : t.c[(long long)i * q + k];  // C[a][b]; K_ab = conj(C[a][b])
-      const double cx = cab.x, cy = -cab.y;
-      const double ac = sqrt(fma(cx, cx, cy * cy));
-      const double nrm = sqrt(sa * sb);
+      // The rotation is computed in FP32 from FP64 inputs (the difference sb - sa is
+      // taken in FP64): a relative error of 1e-7 in the angle leaves a coupling of 1e-7
+      // of the one it removes, far below what the next step sees.  This part's FP64
+      // divisions and square roots would cost ten times more.
+      const float cx = (float)cab.x, cy = (float)-cab.y;
+      const float ac = sqrtf(fmaf(cx, cx, cy * cy));
+      const float nrm = sqrtf((float)sa) * sqrtf((float)sb);
       cplx z = {0.0, 0.0};
-      if (ac != 0.0 && ac > tol * nrm) {
-        const bool sig = ac > abs_flag;
-        if (sig && ac > tol_flag * nrm) {
+      if (ac != 0.0f && nrm > 0.0f && (double)ac > tol * (double)nrm) {  // (weights below FP32's range: not rotated)
+        const bool sig = (double)ac > abs_flag;
+        if (sig && (double)ac > tol_flag * (double)nrm) {
           conv = true;
-          worst = fmaxf(worst, (float)(ac / nrm));
+          worst = fmaxf(worst, ac / nrm);
         }
-        const double zeta = (sb - sa) / (2.0 * ac);
-        const double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
-        if (fabs(tt) <= tmax) {
-          const double cs = 1.0 / sqrt(fma(tt, tt, 1.0)), sn = cs * tt;
-          const double ex = cx / ac, ey = cy / ac;
-          if (lower) z = {sn * ex, sn * ey};  // Z[a][b] with a = k, b = i
-          else z = {-sn * ex, sn * ey};       // Z[b][a] with a = i, b = k
+        const float zeta = (float)(sb - sa) / (2.0f * ac);
+        const float tt = (zeta >= 0 ? 1.0f : -1.0f) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.0f)));
+        if (fabsf(tt) <= (float)tmax) {
+          const float cs = 1.0f / sqrtf(fmaf(tt, tt, 1.0f)), sn = cs * tt;
+          const float ex = cx / ac, ey = cy / ac;
+          if (lower) z = {(double)(sn * ex), (double)(sn * ey)};  // Z[a][b] with a = k, b = i
+          else z = {(double)(-sn * ex), (double)(sn * ey)};       // Z[b][a] with a = i, b = k
           sum = fma(z.x, z.x, fma(z.y, z.y, sum));
         } else if (sig) {
           big = true;
