@@ -76,6 +76,20 @@ void DevBuf::reset() {
   acct = nullptr;
 }
 
+// Host time of a planning section, printed to stderr when TDVP_PLAN_DEBUG is set
+// (read once per process).
+struct PlanClock {
+  const char* name;
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  explicit PlanClock(const char* n) : name(n) {}
+  ~PlanClock() {
+    static const bool on = std::getenv("TDVP_PLAN_DEBUG") != nullptr;
+    if (on)
+      std::fprintf(stderr, "plan %s %.3f ms\n", name,
+                   std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
+  }
+};
+
 template <class T>
 static DevBuf upload(const std::vector<T>& v, cudaStream_t s) {
   DevBuf b(std::max<size_t>(v.size(), 1) * sizeof(T), s);
@@ -84,6 +98,7 @@ static DevBuf upload(const std::vector<T>& v, cudaStream_t s) {
 }
 
 void GemmPlan::finalize(cudaStream_t s, int kind_, int* status_) {
+  PlanClock clk(kind_ == 1 ? (packed.empty() ? "finalize bf16x4" : "finalize bf16x4 packed") : "finalize other");
   kind = kind_;
   status = status_;
   if (!packed.empty() && kind != 1) throw Error(-5, "packed GEMM plans need the BF16x4 kernel");
@@ -114,21 +129,66 @@ void GemmPlan::finalize(cudaStream_t s, int kind_, int* status_) {
     t.tiles_n = (t.cols + tn - 1) / tn;
     t.roff = t.coff = 0;
     for (int a = 0; a < t.tiles_m; ++a)
-      for (int b = 0; b < t.tiles_n; ++b) tiles.push_back(make_int3(i, a, b));
+      for (int b = 0; b < t.tiles_n; ++b)
+        if (!upper_only || a * tm <= b * tn + tn - 1) tiles.push_back(make_int3(i, a, b));
   }
+  kext.clear();
+  fix.clear();
   if (kind < 0) {
-    // FP64 kernel: one CTA per tile, scheduled in list order; the most expensive tiles
-    // first (longest-processing-time order) keep the last wave short.  Each tile is
-    // computed the same way in any order.
+    // FP64 kernel: one CTA per tile item, scheduled in list order.  This part's FP64
+    // pipe is slow enough that a single 64 x 64 tile with K ~ 300 runs for over a
+    // millisecond, so a few large tiles would leave most SMs idle: tiles of a
+    // single-segment task whose cost exceeds an even share of the work (1/4 of the
+    // average over 2 x 148 CTAs) are split along K into chunks written to partial slots
+    // and summed afterwards in a fixed order (results do not depend on scheduling).
+    // Items go in longest-processing-time order.
     std::vector<long long> ksum(tasks.size(), 0);
     for (int i = 0; i < (int)tasks.size(); ++i)
       for (int k = 0; k < tasks[i].seg_count; ++k) ksum[i] += segs[tasks[i].seg_begin + k].k;
-    auto cost = [&](const int3& t) {
+    auto area = [&](const int3& t) {
       const GemmTask& g = tasks[t.x];
-      const long long r = std::min(tm, g.rows - t.y * tm), c = std::min(tm, g.cols - t.z * tm);
-      return ksum[t.x] * r * c;
+      return (long long)std::min(tm, g.rows - t.y * tm) * std::min(tm, g.cols - t.z * tm);
     };
-    std::stable_sort(tiles.begin(), tiles.end(), [&](const int3& a, const int3& b) { return cost(a) > cost(b); });
+    long long total = 0;
+    for (const int3& t : tiles) total += ksum[t.x] * area(t);
+    const long long share = std::max<long long>(total / (4 * 2 * 148), 64LL * 64 * 64);
+    struct Item {
+      int3 t;
+      int4 k;
+      long long cost;
+    };
+    std::vector<Item> items;
+    int slots = 0;
+    for (const int3& t : tiles) {
+      const long long c = ksum[t.x] * area(t);
+      const int K = (int)ksum[t.x];
+      int nch = ksplit && tasks[t.x].seg_count == 1 ? (int)std::min<long long>((c + share - 1) / share, K / 32) : 1;
+      if (nch <= 1) {
+        items.push_back({t, make_int4(0, K, -1, 0), c});
+        continue;
+      }
+      const int step = ((K + nch - 1) / nch + 7) / 8 * 8;  // multiples of the kernel's k step
+      nch = (K + step - 1) / step;
+      fix.push_back(make_int4(t.x, t.y, t.z, slots | (nch << 20)));
+      for (int q = 0; q < nch; ++q) {
+        const int kb = q * step, ke = std::min(K, kb + step);
+        items.push_back({t, make_int4(kb, ke, slots + q, 0), (long long)(ke - kb) * area(t)});
+      }
+      slots += nch;
+    }
+    std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) { return a.cost > b.cost; });
+    tiles.clear();
+    if (!fix.empty()) {
+      for (const Item& it : items) {
+        tiles.push_back(it.t);
+        kext.push_back(it.k);
+      }
+      dkx = upload(kext, s);
+      dfix = upload(fix, s);
+      dws = DevBuf((size_t)slots * 64 * 64 * sizeof(cplx), s);
+    } else {
+      for (const Item& it : items) tiles.push_back(it.t);
+    }
   }
   if (!rowoffs.empty()) {
     drow = upload(rowoffs, s);
@@ -387,9 +447,12 @@ unsigned GemmPlan::begin_split(cudaStream_t s, const Bases4& B) const {
 void GemmPlan::launch(cudaStream_t s, const Bases4& B, unsigned ep, const int3* tsub, int nsub) const {
   const int3* tl = tsub ? tsub : dti.as<int3>();
   const int nt = tsub ? nsub : (int)tiles.size();
-  if (kind < 0)
-    launch_gemm_fp64(dt.as<GemmTask>(), ds.as<GemmSeg>(), tl, nt, B, s);
-  else {
+  if (kind < 0) {
+    const bool split = !tsub && !kext.empty();
+    launch_gemm_fp64(dt.as<GemmTask>(), ds.as<GemmSeg>(), tl, nt, B, s, split ? dkx.as<int4>() : nullptr,
+                     dws.as<cplx>());
+    if (split) launch_gemm_fp64_fix(dt.as<GemmTask>(), dfix.as<int4>(), (int)fix.size(), dws.as<cplx>(), B, s);
+  } else {
     if (kind == 1) {
       const unsigned e = ep ? ep : begin_split(s, B);
       const int mode = dyn_mode == 1 && !ep ? 0 : dyn_mode;  // no producer raised the tags: both passes
@@ -1200,6 +1263,7 @@ static int packed_tile_n(int n) { return n >= 64 ? 64 : std::max(16, (n + 15) / 
 //     output rows go back to their blocks through a row-offset table.
 void Engine::plan_heff2_packed(HeffPlan& p, const BTensor& Lenv, const BTensor& Renv, const BTensor& theta,
                                const BondSpace& bl, const BondSpace& br) {
+  PlanClock clk("heff2 packed total");
   p = HeffPlan();
   p.n = theta.size;
   const Model& M = model_;
@@ -1658,6 +1722,7 @@ static void plan_l_w(Engine* eng, const Model& M, Recoupler& rec, HeffPlan& p, c
 
 void Engine::plan_heff1(HeffPlan& p, const BTensor& Lenv, const BTensor& Renv, const BTensor& Mt, const BondSpace& bl,
                         const BondSpace& br) {
+  PlanClock clk("heff1 total");
   p = HeffPlan();
   p.n = Mt.size;
   std::vector<std::array<int, 5>> t2keys;
@@ -2237,13 +2302,17 @@ double Engine::split(BTensor& theta, const BondSpace& bl, const BondSpace& br, l
 
 // Which of the mixed split's own products run as BF16x4 digit products on the tensor
 // cores instead of the FP64 pipe: a bit mask from TDVP_SPLIT_GEMM_TC (read at every
-// split; default 0, all FP64): 1 G = W V, 2 the kept basis W^H Z, 4 the Newton-Schulz
-// products, 8 the projection of theta onto the kept basis.  BF16x4 rounds to 2^-30 of
-// each operand row's and column's scale, which for the small singular values of a
-// graded spectrum is a large relative error.
+// split; default 10): 1 G = W V, 2 the kept basis W^H Z, 4 the Newton-Schulz products,
+// 8 the projection of theta onto the kept basis.  BF16x4 rounds to 2^-30 of each
+// operand row's and column's scale (plus ~K 2^-32 for the dropped digit orders).  For
+// the kept basis that is a direction error of the smallest kept vectors, which moves
+// the truncated state by (a discarded value) x (that error), and for the projection an
+// absolute error of ~1e-9 of the state, both below the BF16x4 matvec's own.  G = W V
+// and Newton-Schulz stay FP64: G's small columns would carry errors relative to the
+// largest, and Newton-Schulz's product sets the orthonormality of the kept basis.
 static int split_tc_mask() {
   const char* e = std::getenv("TDVP_SPLIT_GEMM_TC");
-  return e && *e ? std::atoi(e) : 0;
+  return e && *e ? std::atoi(e) : 10;
 }
 
 // a float from the environment (read at every call), or the default
@@ -2348,17 +2417,12 @@ bool Engine::gram_finish(cplx* G, cplx* galt, const std::vector<int>& P, const s
     pu.tasks.push_back(u);
     gt.push_back({Kb + koff[g], Zb + koff[g], Q[g]});
   }
+  // the Gram matrices are Hermitian: only tiles on and above the diagonal
+  pk_tc.upper_only = pk64.upper_only = true;
+  pk64.ksplit = true;
   pk_tc.finalize(stream_, 1, dstatus_);
   pk64.finalize(stream_);
   pu.finalize(stream_, 1, dstatus_);
-  // the Gram matrices are Hermitian: only tiles on and above the diagonal
-  for (GemmPlan* pl : {&pk_tc, &pk64}) {
-    std::vector<int3> up;
-    for (const int3& t : pl->tiles)
-      if (t.y <= t.z) up.push_back(t);
-    pl->tiles.swap(up);
-    pl->dti = upload(pl->tiles, stream_);
-  }
   DevBuf dgt = upload(gt, stream_);
   const double tmax = gram_tmax();
   const Bases4 B{{0, reinterpret_cast<uintptr_t>(G), reinterpret_cast<uintptr_t>(galt), 0}};
@@ -2409,6 +2473,16 @@ bool Engine::gram_finish(cplx* G, cplx* galt, const std::vector<int>& P, const s
 
 double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace& br, long long chi_max, double eps,
                            bool absorb_right, BondSpace& bm, BTensor& X, BTensor& Y, double* s_ent, bool& ok) {
+  // TDVP_SPLIT_DEBUG: wall time of each section (synchronising after each one)
+  static const bool sdbg = std::getenv("TDVP_SPLIT_DEBUG") != nullptr;
+  auto st0 = std::chrono::steady_clock::now();
+  auto smark = [&](const char* what) {
+    if (!sdbg) return;
+    cudaStreamSynchronize(stream_);
+    const auto now = std::chrono::steady_clock::now();
+    std::fprintf(stderr, "split %s %.3f ms\n", what, std::chrono::duration<double, std::milli>(now - st0).count());
+    st0 = now;
+  };
   NvtxRange nvtx_range("split");
   const Model& M = model_;
   ok = false;
@@ -2504,6 +2578,7 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
   }
   gather.finalize(stream_);
   gather.launch(stream_);
+  smark("setup+gather");
   const int tcm = split_tc_mask();
   auto kind_of = [&](int bit) { return (tcm & bit) ? 1 : -1; };
   // FP32 preconditioner
@@ -2530,6 +2605,7 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
                                  env_float("TDVP_FP32_ABS", abs32), stream_, &stats_.jacobi32, jscratch()));
   ok = true;
   stats_.sweeps32 += sw32;
+  smark("fp32 jacobi");
   stats_.splits += 1;
   launch_widen(V32, V64, vtot, stream_);
   // G = W V in FP64: row-major G^T (Q x P) = V^T (Q x Q) W^T (Q x P)
@@ -2554,9 +2630,11 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
       gp.segs.push_back(sg);
       gp.tasks.push_back(t);
     }
+    gp.ksplit = true;
     gp.finalize(stream_, kind_of(1), dstatus_);
     gp.launch(stream_, Bases4{{0, 0, 0, 0}});
   }
+  smark("G = W V");
   std::vector<SvdTask> st(ng);
   std::vector<TruncSector> ts(ng);
   for (int g = 0; g < ng; ++g) {
@@ -2585,6 +2663,7 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
     stats_.sweeps64 += jacobi(run_jacobi_rounds(dst.as<SvdTask>(), st, 30, 1e-13, dstatus_, stream_, 1e-6, 1e-10,
                                                 &stats_.jacobi64, jscratch()));
   }
+  smark("fp64 finish");
   DevBuf dts = upload(ts, stream_), doffs = upload(soff, stream_);
   DevBuf downer(std::max(stot, 1) * sizeof(int), stream_), dorder(std::max(stot, 1) * sizeof(int), stream_);
   DevBuf dkept(std::max(ng, 1) * sizeof(int), stream_), dstats(8 * sizeof(double), stream_);
@@ -2597,6 +2676,7 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
   TDVP_CUDA(cudaMemcpyAsync(hstats, dstats.p, 6 * sizeof(double), cudaMemcpyDeviceToHost, stream_));
   TDVP_CUDA(cudaStreamSynchronize(stream_));
   if (hstats[5] != 0.0) cap_hit_ = true;
+  smark("truncation (sync)");
   std::vector<std::pair<std::pair<int, int>, int>> ns;
   for (int g = 0; g < ng; ++g)
     if (kept[g] > 0) ns.push_back({{groups[g].n, groups[g].t}, g});
@@ -2670,9 +2750,13 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
       xp.tasks.push_back(t);
       nt.push_back({Kb + koff[g], k});
     }
+    xp.ksplit = true;
     xp.finalize(stream_, kind_of(2), dstatus_);
     xp.launch(stream_, Bases4{{0, 0, 0, 0}});
-    // Newton-Schulz in FP64: K = X^H X, F = 1.5 I - 0.5 K, X <- X F (Z reused as scratch)
+    // Newton-Schulz in FP64: K = X^H X, F = 1.5 I - 0.5 K, X <- X F (Z reused as scratch).
+    // Two steps: with one, the entropies of a chi = 4096 sweep moved by 2.6e-7 against
+    // 2.7e-8.  Both products stay on the FP64 pipe: BF16x4 products leave ~1e-8 of each
+    // row's scale, which the observables then see (1.7e-7 in n_i over one sweep).
     DevBuf dnt = upload(nt, stream_);
     for (int it = 0; it < 2; ++it) {
       GemmPlan g1, g2;
@@ -2715,9 +2799,11 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
         g2.segs.push_back(sh);
         g2.tasks.push_back(u);
       }
+      g1.ksplit = true;
       g1.finalize(stream_, kind_of(4), dstatus_);
       g1.launch(stream_, Bases4{{0, 0, 0, 0}});
       launch_ns_coeff(dnt.as<NsTask>(), (int)nt.size(), stream_);
+      g2.ksplit = true;
       g2.finalize(stream_, kind_of(4), dstatus_);
       g2.launch(stream_, Bases4{{0, 0, 0, 0}});
       CopyPlan back;  // X <- X F (Z holds X F; Z rows >= X rows, packed at the same pitch k)
@@ -2740,6 +2826,7 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
       back.launch(stream_);
     }
   }
+  smark("kept basis + Newton-Schulz");
   // exact projection for the other factor: C = X^H T (left to right) or M = T X (right to left)
   GemmPlan pg;
   for (int g = 0; g < ng; ++g) {
@@ -2776,8 +2863,10 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
     pg.segs.push_back(sg);
     pg.tasks.push_back(t);
   }
+  pg.ksplit = true;
   pg.finalize(stream_, kind_of(8), dstatus_);
   pg.launch(stream_, Bases4{{0, 0, 0, 0}});
+  smark("projection");
   // renormalise the kept state to unit norm
   DevBuf part((size_t)296 * sizeof(cplx), stream_), nrm(sizeof(cplx), stream_), dgs(sizeof(double), stream_);
   launch_dots(Pr, 0, 1, Pr, pt, part.as<cplx>(), dots_grid(pt), nrm.as<cplx>(), nullptr, stream_);
@@ -2787,6 +2876,7 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
   double gsc = hn.x > 0 ? 1.0 / std::sqrt(hn.x) : 1.0;
   TDVP_CUDA(cudaMemcpyAsync(dgs.p, &gsc, sizeof(double), cudaMemcpyHostToDevice, stream_));
   build_site_layout(X, bl, bm);
+  smark("norm (sync)");
   build_site_layout(Y, bm, br);
   alloc(X, false);
   alloc(Y, false);
@@ -2850,6 +2940,7 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
     launch_entropy_sv(dks.as<TruncSector>(), (int)ks.size(), dstats.as<double>() + 2, dE.as<double>(), stream_);
     TDVP_CUDA(cudaMemcpyAsync(s_ent, dE.p, sizeof(double), cudaMemcpyDeviceToHost, stream_));
   }
+  smark("scatter + entropy");
   TDVP_CUDA(cudaStreamSynchronize(stream_));
   long long chi = 0;
   for (auto& x : bm.s) chi += (long long)x.d * M.mult_dim(x.t);

@@ -124,6 +124,16 @@ struct GemmPlan {
   std::vector<GemmSeg> segs;
   std::vector<int3> tiles;
   DevBuf dt, ds, dti;
+  // only the tiles on and above the diagonal (Hermitian products such as Gram matrices)
+  bool upper_only = false;
+  // FP64 plans may split large single-segment tiles along K (see finalize)
+  bool ksplit = false;
+  // FP64 plans: the K range of each tile (kbeg, kend, partial slot or -1, 0) when some
+  // single-segment tiles are split along K to balance the SMs; the partial tiles
+  // (64 x 64 each in dws) of a split output tile are summed in a fixed order by the
+  // combine step (fix: task, tile row, tile column, first slot | chunk count << 20)
+  std::vector<int4> kext, fix;
+  DevBuf dkx, dfix, dws;
   // packed BF16x4 plans (one segment per task, operands assembled from blocks):
   // packed[i] describes task i; rowoffs holds the stacked-output row offsets that a
   // task with row_start[i] >= 0 reads from index row_start[i] on

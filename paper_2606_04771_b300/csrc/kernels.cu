@@ -48,11 +48,14 @@ constexpr int GK = 8;    // k step
 
 __global__ void __launch_bounds__(256) gemm_fp64_kernel(const GemmTask* __restrict__ tasks,
                                                         const GemmSeg* __restrict__ segs,
-                                                        const int3* __restrict__ tiles, const Bases4 B) {
+                                                        const int3* __restrict__ tiles, const Bases4 B,
+                                                        const int4* __restrict__ kx, cplx* __restrict__ ws) {
   __shared__ cplx As[GK][GT + 1];
   __shared__ cplx Bs[GK][GT + 1];
   const int3 tr = tiles[blockIdx.x];
   const GemmTask t = tasks[tr.x];
+  // the item's K range (a single-segment task split along K) and where it goes
+  const int4 ke = kx ? kx[blockIdx.x] : make_int4(0, 0x7fffffff, -1, 0);
   cplx* const cptr = rebase(B, t.c_base, t.c);
   const int m0 = tr.y * GT, n0 = tr.z * GT;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -66,13 +69,14 @@ __global__ void __launch_bounds__(256) gemm_fp64_kernel(const GemmTask* __restri
     const GemmSeg sg = segs[t.seg_begin + sgi];
     const cplx* const ap = rebase(B, sg.a_base, sg.a);
     const cplx* const bp = rebase(B, sg.b_base, sg.b);
-    for (int k0 = 0; k0 < sg.k; k0 += GK) {
+    const int kend = min(sg.k, ke.y);
+    for (int k0 = ke.x; k0 < kend; k0 += GK) {
       // load A tile: GT rows x GK k
       for (int e = threadIdx.x; e < GT * GK; e += 256) {
         int r = e / GK, kk = e % GK;
         int gr = m0 + r, gk = k0 + kk;
         cplx v = {0.0, 0.0};
-        if (gr < t.rows && gk < sg.k) {
+        if (gr < t.rows && gk < kend) {
           if (sg.op_a == OP_N) v = ap[(long long)gr * sg.lda + gk];
           else v = cconj(ap[(long long)gk * sg.lda + gr]);
         }
@@ -82,7 +86,7 @@ __global__ void __launch_bounds__(256) gemm_fp64_kernel(const GemmTask* __restri
         int kk = e / GT, c = e % GT;
         int gc = n0 + c, gk = k0 + kk;
         cplx v = {0.0, 0.0};
-        if (gc < t.cols && gk < sg.k) {
+        if (gc < t.cols && gk < kend) {
           if (sg.op_b == OP_N) v = bp[(long long)gk * sg.ldb + gc];
           else v = cconj(bp[(long long)gc * sg.ldb + gk]);
         }
@@ -109,6 +113,14 @@ __global__ void __launch_bounds__(256) gemm_fp64_kernel(const GemmTask* __restri
       __syncthreads();
     }
   }
+  if (ke.z >= 0) {  // a K chunk: the whole 64 x 64 partial tile to its slot (zeros outside C)
+    cplx* const part = ws + (long long)ke.z * (GT * GT);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) part[(ty + 16 * i) * GT + tx + 16 * j] = acc[i][j];
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     int r = m0 + ty + 16 * i;
@@ -121,11 +133,40 @@ __global__ void __launch_bounds__(256) gemm_fp64_kernel(const GemmTask* __restri
   }
 }
 
+// C tile = the sum of its K-chunk partials, in chunk order
+__global__ void __launch_bounds__(256) gemm_fp64_fix_kernel(const GemmTask* __restrict__ tasks,
+                                                            const int4* __restrict__ fix,
+                                                            const cplx* __restrict__ ws, const Bases4 B) {
+  const int4 f = fix[blockIdx.x];
+  const GemmTask t = tasks[f.x];
+  cplx* const cptr = rebase(B, t.c_base, t.c);
+  const int slot0 = f.w & 0xFFFFF, nch = f.w >> 20;
+  const int m0 = f.y * GT, n0 = f.z * GT;
+  for (int e = threadIdx.x; e < GT * GT; e += 256) {
+    const int r = m0 + e / GT, c = n0 + e % GT;
+    if (r >= t.rows || c >= t.cols) continue;
+    cplx v = ws[(long long)slot0 * (GT * GT) + e];
+    for (int q = 1; q < nch; ++q) {
+      const cplx w = ws[(long long)(slot0 + q) * (GT * GT) + e];
+      v.x += w.x;
+      v.y += w.y;
+    }
+    cptr[(long long)r * t.ldc + c] = v;
+  }
+}
+
 void launch_gemm_fp64(const GemmTask* tasks, const GemmSeg* segs, const int3* tiles, int ntiles, const Bases4& B,
-                      cudaStream_t s) {
+                      cudaStream_t s, const int4* kx, cplx* ws) {
   if (ntiles <= 0) return;
   note_launch();
-  gemm_fp64_kernel<<<ntiles, 256, 0, s>>>(tasks, segs, tiles, B);
+  gemm_fp64_kernel<<<ntiles, 256, 0, s>>>(tasks, segs, tiles, B, kx, ws);
+}
+
+void launch_gemm_fp64_fix(const GemmTask* tasks, const int4* fix, int nfix, const cplx* ws, const Bases4& B,
+                          cudaStream_t s) {
+  if (nfix <= 0) return;
+  note_launch();
+  gemm_fp64_fix_kernel<<<nfix, 256, 0, s>>>(tasks, fix, ws, B);
 }
 
 // ---------------------------------------------------------------------------

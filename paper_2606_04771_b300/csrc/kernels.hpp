@@ -35,8 +35,14 @@ struct KrylovState {
   int bad;  // set when a non-finite value appeared
 };
 
+// kx (or nullptr): per tile item its K range and partial slot (-1: write C directly;
+// else the 64 x 64 partial goes to ws + slot 4096, single-segment tasks only)
 void launch_gemm_fp64(const GemmTask* tasks, const GemmSeg* segs, const int3* tiles, int ntiles, const Bases4& B,
-                      cudaStream_t s);
+                      cudaStream_t s, const int4* kx = nullptr, cplx* ws = nullptr);
+// sums the partial tiles of each split output tile (fix: task, tile row, tile column,
+// first slot | count << 20) in slot order and writes C
+void launch_gemm_fp64_fix(const GemmTask* tasks, const int4* fix, int nfix, const cplx* ws, const Bases4& B,
+                          cudaStream_t s);
 // epoch: the BF16x4 split epoch the output row tags are raised to (tasks with tags)
 void launch_lincomb(const LincombTask* tasks, const LincombTerm* terms, const int2* chunks, int nchunks,
                     cudaStream_t s, unsigned epoch = 0);
