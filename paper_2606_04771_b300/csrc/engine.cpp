@@ -210,7 +210,27 @@ void GemmPlan::finalize(cudaStream_t s, int kind_, int* status_) {
 void GemmPlan::plan_digits(cudaStream_t s) {
   // side, base, ptr, rows, cols, ld, op, alpha, static
   typedef std::tuple<int, int, uintptr_t, int, int, int, int, double, int> Key;
-  std::map<Key, int> idx;
+  struct KeyHash {
+    size_t operator()(const Key& k) const {
+      uint64_t h = 1469598103934665603ull;
+      auto mix = [&](uint64_t v) { h = (h ^ v) * 1099511628211ull; };
+      mix((uint64_t)std::get<0>(k));
+      mix((uint64_t)std::get<1>(k));
+      mix((uint64_t)std::get<2>(k));
+      mix((uint64_t)std::get<3>(k));
+      mix((uint64_t)std::get<4>(k));
+      mix((uint64_t)std::get<5>(k));
+      mix((uint64_t)std::get<6>(k));
+      double a = std::get<7>(k);
+      uint64_t ab;
+      std::memcpy(&ab, &a, sizeof(ab));
+      mix(ab);
+      mix((uint64_t)std::get<8>(k));
+      return (size_t)h;
+    }
+  };
+  std::unordered_map<Key, int, KeyHash> idx;
+  idx.reserve(4 * segs.size() + 16);
   std::vector<Key> keys;
   std::vector<int> parent;
   auto get = [&](const Key& k) {
@@ -247,21 +267,20 @@ void GemmPlan::plan_digits(cudaStream_t s) {
   }
   // a group is static only if every operand in it is; static groups take the first
   // offsets so that the per-launch maxima reset covers the dynamic range only
-  std::map<int, int> gstat;
+  // per union-find root (an operand index): static (1) unless one member is dynamic
+  std::vector<int> gstat(keys.size(), -1);
   for (int i = 0; i < (int)keys.size(); ++i) {
     const int r = find(i);
-    auto it = gstat.find(r);
     const int st = std::get<8>(keys[i]);
-    if (it == gstat.end()) gstat[r] = st;
-    else it->second &= st;
+    gstat[r] = gstat[r] < 0 ? st : (gstat[r] & st);
   }
-  std::map<int, int> goff;
+  std::vector<int> goff(keys.size(), -1);
   long long ng = 0;
   for (int pass = 1; pass >= 0; --pass) {
     if (pass == 0) ngrp_static = (int)ng;
     for (int i = 0; i < (int)keys.size(); ++i) {
       const int r = find(i);
-      if (goff.count(r) || gstat[r] != pass) continue;
+      if (goff[r] >= 0 || gstat[r] != pass) continue;
       goff[r] = (int)ng;
       ng += std::get<0>(keys[r]) == 0 ? std::get<3>(keys[r]) : std::get<4>(keys[r]);
     }
@@ -532,6 +551,18 @@ static int jacobi(int sweeps) {
     throw Error(-6, std::string("cooperative Jacobi launch failed: ") + cudaGetErrorString(e));
   }
   return sweeps;
+}
+
+// 64-bit key of a recoupled block (a', s1', c', s2', b', w2, b): bond sector indices
+// below 4096, the middle label tc' (2S or 2S^z, possibly negative) within +-2047, site
+// and channel indices below 8
+static inline uint64_t t2key(int ap, int s1p, int tcp, int s2p, int bp, int w2, int b) {
+  const int tco = tcp + 2048;
+  if ((unsigned)ap >= 4096u || (unsigned)tco >= 4096u || (unsigned)bp >= 4096u || (unsigned)b >= 4096u ||
+      (unsigned)s1p >= 8u || (unsigned)s2p >= 8u || (unsigned)w2 >= 8u)
+    throw Error(-5, "recoupled block key out of range");
+  return ((uint64_t)ap << 45) | ((uint64_t)s1p << 42) | ((uint64_t)tco << 30) | ((uint64_t)s2p << 27) |
+         ((uint64_t)bp << 15) | ((uint64_t)w2 << 12) | (uint64_t)b;
 }
 
 static inline cplx* as_off(long long off) { return reinterpret_cast<cplx*>(static_cast<uintptr_t>(off) * sizeof(cplx)); }
@@ -1264,6 +1295,14 @@ static int packed_tile_n(int n) { return n >= 64 ? 64 : std::max(16, (n + 15) / 
 void Engine::plan_heff2_packed(HeffPlan& p, const BTensor& Lenv, const BTensor& Renv, const BTensor& theta,
                                const BondSpace& bl, const BondSpace& br) {
   PlanClock clk("heff2 packed total");
+  static const bool pdbg = std::getenv("TDVP_PLAN_DEBUG") != nullptr;
+  auto pt0 = std::chrono::steady_clock::now();
+  auto pmark = [&](const char* what) {
+    if (!pdbg) return;
+    const auto now = std::chrono::steady_clock::now();
+    std::fprintf(stderr, "plan heff2 %s %.3f ms\n", what, std::chrono::duration<double, std::milli>(now - pt0).count());
+    pt0 = now;
+  };
   p = HeffPlan();
   p.n = theta.size;
   const Model& M = model_;
@@ -1335,8 +1374,9 @@ void Engine::plan_heff2_packed(HeffPlan& p, const BTensor& Lenv, const BTensor& 
     p.g1.packed.push_back(std::move(pk));
     p.g1.tasks.push_back(t);
   }
+  pmark("stage 1");
   // stage 2: recoupling terms (as plan_heff2)
-  std::map<std::tuple<int, int, int, int, int, int, int>, int> t2idx;
+  std::unordered_map<uint64_t, int> t2idx;
   std::vector<std::vector<std::pair<int, double>>> t2terms;
   std::vector<std::array<int, 7>> t2keys;
   for (int i = 0; i < (int)t1v.size(); ++i) {
@@ -1350,7 +1390,7 @@ void Engine::plan_heff2_packed(HeffPlan& p, const BTensor& Lenv, const BTensor& 
       if (bp < 0) continue;
       if (Renv.find(bkey(b, e.w2, bp)) < 0) continue;
       if (bl.s[ap].n + M.site[e.s1p].n + M.site[e.s2p].n != nbp) throw Error(-5, "charge mismatch in recoupling");
-      auto key = std::make_tuple(ap, e.s1p, e.tcp, e.s2p, bp, e.w2, b);
+      const uint64_t key = t2key(ap, e.s1p, e.tcp, e.s2p, bp, e.w2, b);
       auto it = t2idx.find(key);
       int id;
       if (it == t2idx.end()) {
@@ -1364,6 +1404,7 @@ void Engine::plan_heff2_packed(HeffPlan& p, const BTensor& Lenv, const BTensor& 
       t2terms[id].push_back({i, e.f});
     }
   }
+  pmark("stage 2");
   // stage 3 grouping by output column sector b'
   const int nsr = (int)br.s.size();
   std::vector<std::vector<int>> oby(nsr);  // output (theta) blocks by right sector
@@ -1467,6 +1508,7 @@ void Engine::plan_heff2_packed(HeffPlan& p, const BTensor& Lenv, const BTensor& 
       p.g3.task_flops[task_of.at(bp)] += 8LL * rows * cols * br.s[bp].d;
     }
   }
+  pmark("stage 3");
   p.g1.finalize(stream_, gemm_kind_, dstatus_ + 1);
   p.g3.dyn_tags_external = true;
   p.g3.finalize(stream_, gemm_kind_, dstatus_ + 1);
@@ -1538,7 +1580,7 @@ void Engine::plan_heff2(HeffPlan& p, const BTensor& Lenv, const BTensor& Renv, c
     p.g1.flops += 8LL * lk.rows * lk.cols * th.cols;
   }
   // step 2: recoupling into T2(a',s1',c',s2',b',w2,b)
-  std::map<std::tuple<int, int, int, int, int, int, int>, int> t2idx;
+  std::unordered_map<uint64_t, int> t2idx;
   std::vector<std::vector<std::pair<int, double>>> t2terms;
   std::vector<std::array<int, 7>> t2keys;
   for (int i = 0; i < (int)t1info.size(); ++i) {
@@ -1552,7 +1594,7 @@ void Engine::plan_heff2(HeffPlan& p, const BTensor& Lenv, const BTensor& Renv, c
       if (bp < 0) continue;
       if (Renv.find(bkey(b, e.w2, bp)) < 0) continue;
       if (bl.s[ap].n + M.site[e.s1p].n + M.site[e.s2p].n != nbp) throw Error(-5, "charge mismatch in recoupling");
-      auto key = std::make_tuple(ap, e.s1p, e.tcp, e.s2p, bp, e.w2, b);
+      const uint64_t key = t2key(ap, e.s1p, e.tcp, e.s2p, bp, e.w2, b);
       auto it = t2idx.find(key);
       int id;
       if (it == t2idx.end()) {
