@@ -14,11 +14,12 @@ namespace tdvp {
 
 void BondSpace::build_index() {
   idx.clear();
-  for (int k = 0; k < (int)s.size(); ++k) idx[{s[k].n, s[k].t}] = k;
+  idx.reserve(2 * s.size() + 1);
+  for (int k = 0; k < (int)s.size(); ++k) idx[key(s[k].n, s[k].t)] = k;
 }
 
 int BondSpace::find(int n, int t) const {
-  auto it = idx.find({n, t});
+  auto it = idx.find(key(n, t));
   return it == idx.end() ? -1 : it->second;
 }
 

@@ -35,7 +35,8 @@ struct Sector {
 
 struct BondSpace {
   std::vector<Sector> s;
-  std::map<std::pair<int, int>, int> idx;
+  std::unordered_map<uint64_t, int> idx;  // (n, t) packed as key(n, t) -> sector index
+  static uint64_t key(int n, int t) { return ((uint64_t)(uint32_t)n << 32) | (uint32_t)t; }
   void build_index();
   int find(int n, int t) const;
   long long chi_red() const;   // sum d
