@@ -1835,6 +1835,10 @@ static int coop_run(const Task* d_tasks, const std::vector<Task>& h_tasks, int m
     auto task_sweeps = [&](int e) { return resident[e] ? h[3 + nt + e] : h[2 + e]; };
     sweeps = h[0];  // the cooperative launch's sweeps (0 when it did not run)
     for (int e : rid) sweeps = max(sweeps, task_sweeps(e));
+    if (ring_r > 0 && std::getenv("TDVP_RING_DEBUG")) {
+      for (int e : rid)
+        std::fprintf(stderr, "ring sweeps: p %d q %d sweeps %d\n", h_tasks[e].p, h_tasks[e].q, task_sweeps(e));
+    }
     nc = (h[1] | h[2 + nt]) ? 1 : 0;
     if (prof) {
       float ms = 0;

@@ -458,9 +458,13 @@ __device__ __forceinline__ unsigned biased_exp(double x) {
   return (unsigned)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FF);
 }
 
-__global__ void __launch_bounds__(256) digit_max_kernel(const DigitOp* __restrict__ ops, const Bases4 B,
-                                                        unsigned* __restrict__ tags, unsigned epoch) {
-  const DigitOp o = ops[blockIdx.x];
+__global__ void __launch_bounds__(256) digit_max_kernel(const DigitOp* __restrict__ ops,
+                                                        const int2* __restrict__ jobs, const Bases4 B,
+                                                        unsigned* __restrict__ tags, unsigned epoch, int job) {
+  // one CTA per job: elements [e0, e0 + job) of one operand (the jobs of
+  // digit_convert_kernel), so a large operand is reduced by many CTAs at once
+  const int2 jb = jobs[blockIdx.x];
+  const DigitOp o = ops[jb.x];
   const cplx* src = rebase(B, o.base, o.src);
   extern __shared__ unsigned slot[];
   const int nslot = o.side == 0 ? o.rows : o.cols;
@@ -470,11 +474,11 @@ __global__ void __launch_bounds__(256) digit_max_kernel(const DigitOp* __restric
   if (local)
     for (int i = threadIdx.x; i < nslot; i += 256) slot[i] = 0u;
   __syncthreads();
-  const long long n = (long long)o.rows * o.cols;
+  const long long n = min((long long)o.rows * o.cols, (long long)jb.y + job);
   // storage order: OP_N stores rows of length cols, OP_C stores columns of length rows
   const int inner = o.op == OP_N ? o.cols : o.rows;
 #pragma unroll 4
-  for (long long e = threadIdx.x; e < n; e += 256) {
+  for (long long e = jb.y + threadIdx.x; e < n; e += 256) {
     const int outer = (int)(e / inner), in = (int)(e - (long long)outer * inner);
     const cplx v = src[(long long)outer * o.ld + in];
     const int r = o.op == OP_N ? outer : in, c = o.op == OP_N ? in : outer;
@@ -984,7 +988,7 @@ void launch_digits(const DigitOp* ops, int nops, const int2* jobs, int njobs, un
   }
   if (mode == 0) {
     note_launch();
-    digit_max_kernel<<<nops, 256, sm, s>>>(ops, B, tags, epoch);
+    digit_max_kernel<<<njobs, 256, sm, s>>>(ops, jobs, B, tags, epoch, digit_job_size());
   }
   note_launch();
   digit_convert_kernel<<<njobs, 256, 0, s>>>(ops, jobs, B, tags, epoch, exps);
