@@ -39,6 +39,7 @@ struct GemmTask {
   const long long* rowoff;
   int tn;
   int b_kmajor;  // BF16x4: the B records are stored column by column (K contiguous)
+  int img;       // BF16x4 packed task: a_dig / b_dig hold tile images (DigitOp::img_nkc)
 };
 
 // op flags
@@ -77,6 +78,12 @@ struct DigitOp {
   // group row grp + row0 + r (A) or column grp + col0 + c (B); an operand of its own
   // has row0 = col0 = 0, dig_ld = cols and kmajor = 0
   int dig_ld, row0, col0, kmajor;
+  // tile images (packed plans): img_nkc > 0 writes the digits straight into the BF16
+  // planes of the GEMM's shared-memory tiles, tile after tile, at dig (A: 64 complex
+  // rows x 16 complex k per 32 KB tile, embedded as [[re, -im], [im, re]]; B: img_tn
+  // complex columns x 16 complex k per 16 KB tile), so that the GEMM fetches each
+  // stage with bulk copies instead of unpacking records
+  int img_nkc, img_tn;
 };
 
 template <class T>

@@ -375,14 +375,22 @@ void GemmPlan::plan_packed(cudaStream_t s) {
   }
   if (ng > INT32_MAX) throw Error(-5, "GEMM plan too large for 32-bit scale offsets");
   ngrp = (int)ng;
+  // Operands as tile images (the BF16 planes of the GEMM's shared-memory stages, tile
+  // after tile, fetched by bulk copies) unless TDVP_HEFF_IMAGES=0, which keeps 8-byte
+  // digit records unpacked by the producer warps.  Offsets in 8-byte units.
+  const char* ie = std::getenv("TDVP_HEFF_IMAGES");
+  const bool images = !(ie && ie[0] == '0');
   std::vector<long long> aoff(nt), boff(nt);
+  std::vector<int> nkc(nt), tnw(nt);
   long long nrec = 0;
   for (int i = 0; i < nt; ++i) {
     const long long K = segs[tasks[i].seg_begin].k;
+    nkc[i] = (int)((K + 15) / 16);
+    tnw[i] = tasks[i].tn > 0 ? tasks[i].tn : split_tile_n(1);
     aoff[i] = nrec;
-    nrec += (long long)tasks[i].rows * K;
+    nrec += images ? (long long)tasks[i].tiles_m * nkc[i] * (32768 / 8) : (long long)tasks[i].rows * K;
     boff[i] = nrec;
-    nrec += K * tasks[i].cols;
+    nrec += images ? (long long)tasks[i].tiles_n * nkc[i] * (16384 / 8) : K * tasks[i].cols;
   }
   ddig = DevBuf(std::max<long long>(nrec, 1) * sizeof(unsigned long long), s);
   TDVP_CUDA(cudaMemsetAsync(ddig.p, 0, std::max<long long>(nrec, 1) * sizeof(unsigned long long), s));
@@ -396,7 +404,8 @@ void GemmPlan::plan_packed(cudaStream_t s) {
   dops_d.clear();
   djobs_s.clear();
   djobs_d.clear();
-  auto add = [&](const PackedSrc& q, int side, bool st, long long grp, unsigned long long* base, int ld) {
+  auto add = [&](const PackedSrc& q, int side, bool st, long long grp, unsigned long long* base, int ld, int kc,
+                 int tn) {
     std::vector<DigitOp>& ops = st ? dops_s : dops_d;
     std::vector<int2>& jobs = st ? djobs_s : djobs_d;
     DigitOp o{};
@@ -414,6 +423,8 @@ void GemmPlan::plan_packed(cudaStream_t s) {
     o.row0 = q.row0;
     o.col0 = q.col0;
     o.kmajor = side == 1;  // B records column by column (K contiguous)
+    o.img_nkc = images ? kc : 0;
+    o.img_tn = tn;
     const long long n = (long long)o.rows * o.cols;
     for (long long e = 0; e < n; e += job) jobs.push_back(make_int2((int)ops.size(), (int)e));
     ops.push_back(o);
@@ -422,9 +433,10 @@ void GemmPlan::plan_packed(cudaStream_t s) {
     GemmTask& t = tasks[i];
     GemmSeg& g = segs[t.seg_begin];
     const int K = g.k;
-    for (const PackedSrc& q : packed[i].a) add(q, 0, packed[i].a_static, ga[i], dig + aoff[i], K);
-    for (const PackedSrc& q : packed[i].b) add(q, 1, packed[i].b_static, gb[i], dig + boff[i], K);
+    for (const PackedSrc& q : packed[i].a) add(q, 0, packed[i].a_static, ga[i], dig + aoff[i], K, nkc[i], tnw[i]);
+    for (const PackedSrc& q : packed[i].b) add(q, 1, packed[i].b_static, gb[i], dig + boff[i], K, nkc[i], tnw[i]);
     t.b_kmajor = 1;
+    t.img = images ? 1 : 0;
     t.roff = (int)ga[i];
     t.coff = (int)gb[i];
     g.a_dig = dig + aoff[i];
@@ -442,6 +454,13 @@ void GemmPlan::plan_packed(cudaStream_t s) {
     const int K = o.dig_ld;  // row-major A and K-major B records: lines of length K
     const bool whole = o.side == 0 ? (o.col0 == 0 && o.cols == K) : (o.row0 == 0 && o.rows == K);
     if (!whole || (o.side == 0 ? o.rows : o.cols) > digit_slots()) own = false;
+  }
+  {
+    // the fused kernel gives each operand one CTA; the two passes spread every operand
+    // over the conversion's jobs and measure slightly faster on the chi = 4096 bond
+    // (0.305 against 0.314 ms per matvec): TDVP_DIGIT_FUSED=1 selects the fused kernel
+    const char* e = std::getenv("TDVP_DIGIT_FUSED");
+    if (!(e && e[0] == '1')) own = false;
   }
   dyn_mode = dyn_tags_external ? 1 : (own ? 2 : 0);
   std::vector<int> cost(nt, 0);

@@ -68,6 +68,19 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile
 }
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// arrive on a stage's full barrier announcing the bytes its bulk copies will bring
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
+               : "memory");
+}
+// global -> shared bulk copy (16-byte aligned, size a multiple of 16) completing on b
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(b))
+               : "memory");
+}
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -515,6 +528,36 @@ __device__ __forceinline__ unsigned long long pack_digits(double re, double im, 
   return w;
 }
 
+// one element's digits into the operand's records, or into its tile image (the
+// planes of the GEMM stage it will be copied to, in the stage's swizzled layout)
+__device__ __forceinline__ void store_digits(const DigitOp& o, int r, int c, double re, double im, int e) {
+  if (o.img_nkc <= 0) {
+    const long long at = o.kmajor ? (long long)(o.col0 + c) * o.dig_ld + o.row0 + r
+                                  : (long long)(o.row0 + r) * o.dig_ld + o.col0 + c;
+    o.dig[at] = pack_digits(re, im, e);
+    return;
+  }
+  float dr[4], di[4];
+  digits4(fixed30(re, e), dr);
+  digits4(fixed30(im, e), di);
+  uint8_t* base = reinterpret_cast<uint8_t*>(o.dig);
+  if (o.side == 0) {  // A: row R, k; embedded rows 2m (re, -im) and 2m + 1 (im, re)
+    const int R = o.row0 + r, k = o.col0 + c, m = R & 63, kk = k & 15;
+    uint8_t* t = base + ((long long)(R >> 6) * o.img_nkc + (k >> 4)) * (4 * XA_PLANE);
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      st_bf2_64(t + p * XA_PLANE, 2 * m, 2 * kk, dr[p], -di[p]);
+      st_bf2_64(t + p * XA_PLANE, 2 * m + 1, 2 * kk, di[p], dr[p]);
+    }
+  } else {  // B: k, column n; row n of the tile holds (re, im)
+    const int k = o.row0 + r, n = o.col0 + c, kk = k & 15;
+    uint8_t* t = base + ((long long)(n / o.img_tn) * o.img_nkc + (k >> 4)) * (4 * XB_PLANE);
+#pragma unroll
+    for (int p = 0; p < 4; ++p) st_bf2_64(t + p * XB_PLANE, n % o.img_tn, 2 * kk, dr[p], di[p]);
+  }
+}
+
+
 // pass 2: every element of every operand as one 8-byte record (Re digits 0-3, Im
 // digits 0-3, signed bytes) at its place in the digit records (row-major, or column-
 // major for a K-major B operand); jobs = (operand, first element).  The thread of
@@ -550,9 +593,7 @@ __global__ void __launch_bounds__(256) digit_convert_kernel(const DigitOp* __res
     const int gi = o.grp + (o.side == 0 ? o.row0 + r : o.col0 + c);
     const int ex = tag_exp(tags[gi], epoch);
     if (o.side == 0 ? c == 0 : r == 0) exps[gi] = ex;
-    const long long at = o.kmajor ? (long long)(o.col0 + c) * o.dig_ld + o.row0 + r
-                                  : (long long)(o.row0 + r) * o.dig_ld + o.col0 + c;
-    o.dig[at] = pack_digits(v.x, v.y, ex);
+    store_digits(o, r, c, v.x, v.y, ex);
   }
 }
 
@@ -597,9 +638,7 @@ __global__ void __launch_bounds__(256) digit_split_own_kernel(const DigitOp* __r
       v.y *= o.alpha;
     }
     const unsigned ex = slot[o.side == 0 ? r : c];
-    const long long at = o.kmajor ? (long long)(o.col0 + c) * o.dig_ld + o.row0 + r
-                                  : (long long)(o.row0 + r) * o.dig_ld + o.col0 + c;
-    o.dig[at] = pack_digits(v.x, v.y, ex ? (int)ex - 1022 : -2000);
+    store_digits(o, r, c, v.x, v.y, ex ? (int)ex - 1022 : -2000);
   }
 }
 
@@ -725,19 +764,53 @@ __global__ void __launch_bounds__(XTHREADS, 1) gemm_exact_kernel(const __grid_co
                     : 0ull;
       }
     };
+    auto is_img = [&](int tix) {
+      const int sl = slice_of(L, tix);
+      return L.sl[sl].tasks[L.sl[sl].tiles[tix - L.start[sl]].x].img != 0;
+    };
     int ti = blockIdx.x, sgi = 0, k0 = -XKC;
     bool have = advance(ti, sgi, k0);
     unsigned long long wa[NA], wb[NB], na_[NA], nb_[NB];
-    if (have) fetch(ti, sgi, k0, wa, wb);
+    if (have && !is_img(ti)) fetch(ti, sgi, k0, wa, wb);
     for (int it = 0; have && !*verr; ++it) {
       const int bsl = slice_of(L, ti);
       const int bkm = L.sl[bsl].tasks[L.sl[bsl].tiles[ti - L.start[bsl]].x].b_kmajor;
       int ti2 = ti, sgi2 = sgi, k02 = k0;
       const bool have2 = advance(ti2, sgi2, k02);
-      if (have2) fetch(ti2, sgi2, k02, na_, nb_);
+      if (have2 && !is_img(ti2)) fetch(ti2, sgi2, k02, na_, nb_);
       const int s = it % XSTAGES;
       if (!mbar_wait(&empty_bar[s], ((it / XSTAGES) & 1) ^ 1, verr)) break;
       uint8_t* st = stage_base + (size_t)s * XSTAGE;
+      if (is_img(ti)) {
+        // tile images: one thread fetches the stage's A and B planes with two bulk
+        // copies; the other producer warps only arrive, as the barrier counts eight
+        if (warp == 0 && lane == 0) {
+          const ExactSlice& S = L.sl[bsl];
+          const int3 tr = S.tiles[ti - L.start[bsl]];
+          const GemmTask& t = S.tasks[tr.x];
+          const GemmSeg& sg = S.segs[t.seg_begin + sgi];
+          const int nkc = (sg.k + XKC - 1) / XKC, kc = k0 / XKC;
+          const uint8_t* ga = reinterpret_cast<const uint8_t*>(sg.a_dig) +
+                              ((long long)tr.y * nkc + kc) * (long long)(4 * XA_PLANE);
+          const uint8_t* gb = reinterpret_cast<const uint8_t*>(sg.b_dig) +
+                              ((long long)tr.z * nkc + kc) * (long long)(4 * XB_PLANE);
+          mbar_arrive_expect(&full_bar[s], 4 * XA_PLANE + 4 * XB_PLANE);
+          bulk_g2s(st, ga, 4 * XA_PLANE, &full_bar[s]);
+          bulk_g2s(st + 4 * XA_PLANE, gb, 4 * XB_PLANE, &full_bar[s]);
+        } else if (lane == 0) {
+          mbar_arrive(&full_bar[s]);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < NA; ++j) wa[j] = na_[j];
+#pragma unroll
+        for (int j = 0; j < NB; ++j) wb[j] = nb_[j];
+        ti = ti2;
+        sgi = sgi2;
+        k0 = k02;
+        have = have2;
+        continue;
+      }
       // A: 64 complex rows x 16 complex k -> 4 digit planes of 128 rows x 32 bf16,
       // B: 16 complex k x 64 complex n -> 4 digit planes of 64 rows x 32 bf16.  A half
       // warp fills one 64-byte row; the upper half warp writes its two embedded rows in
