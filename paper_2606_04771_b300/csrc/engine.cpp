@@ -380,6 +380,7 @@ void GemmPlan::plan_packed(cudaStream_t s) {
   // digit records unpacked by the producer warps.  Offsets in 8-byte units.
   const char* ie = std::getenv("TDVP_HEFF_IMAGES");
   const bool images = !(ie && ie[0] == '0');
+  images_ = images;
   std::vector<long long> aoff(nt), boff(nt);
   std::vector<int> nkc(nt), tnw(nt);
   long long nrec = 0;
@@ -498,7 +499,9 @@ void GemmPlan::launch(cudaStream_t s, const Bases4& B, unsigned ep, const int3* 
                     dtag.as<unsigned>(), dexp.as<int>(), e, B, s, mode);
     }
     if (kind == 1)
-      launch_exact_merged_or_alone(ExactSlice{dt.as<GemmTask>(), ds.as<GemmSeg>(), tl, dexp.as<int>(), status, B}, nt,
+      launch_exact_merged_or_alone(ExactSlice{dt.as<GemmTask>(), ds.as<GemmSeg>(), tl, dexp.as<int>(), status, B,
+                                              images_ ? 1 : 0},
+                                   nt,
                                    s);
     else
       launch_gemm_split(kind, dt.as<GemmTask>(), ds.as<GemmSeg>(), tl, nt, dexp.as<int>(), B, status, s);

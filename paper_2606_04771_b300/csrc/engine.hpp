@@ -128,6 +128,8 @@ struct GemmPlan {
   bool upper_only = false;
   // FP64 plans may split large single-segment tiles along K (see finalize)
   bool ksplit = false;
+  // BF16x4 packed plans: the operands are tile images (plan_packed)
+  bool images_ = false;
   // FP64 plans: the K range of each tile (kbeg, kend, partial slot or -1, 0) when some
   // single-segment tiles are split along K to balance the SMs; the partial tiles
   // (64 x 64 each in dws) of a split output tile are summed in a fixed order by the

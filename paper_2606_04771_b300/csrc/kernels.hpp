@@ -65,6 +65,7 @@ struct ExactSlice {
   const int* exps;
   int* status;
   Bases4 B;
+  int img;  // every task holds tile images (GemmTask::img)
 };
 struct ExactLaunch {
   int nslices;

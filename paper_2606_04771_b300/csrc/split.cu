@@ -680,6 +680,10 @@ __device__ __forceinline__ int slice_of(const ExactLaunch& L, int ti) {
   return s;
 }
 
+// IMG: every task of the launch holds tile images; one producer thread then walks its
+// tiles with their descriptors loaded once per tile and fetches every stage by bulk
+// copies (the full barriers count that one arrival), and warps 1-7 have no work.
+template <bool IMG>
 __global__ void __launch_bounds__(XTHREADS, 1) gemm_exact_kernel(const __grid_constant__ ExactLaunch L) {
   const int ntiles = L.start[L.nslices];
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -691,7 +695,7 @@ __global__ void __launch_bounds__(XTHREADS, 1) gemm_exact_kernel(const __grid_co
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
     for (int s = 0; s < XSTAGES; ++s) {
-      mbar_init(&full_bar[s], XPROD / 32);
+      mbar_init(&full_bar[s], IMG ? 1 : XPROD / 32);
       mbar_init(&empty_bar[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -713,7 +717,38 @@ __global__ void __launch_bounds__(XTHREADS, 1) gemm_exact_kernel(const __grid_co
   const uint32_t tmem = tmem_slot;
   volatile int* verr = &err;
 
-  if (warp < XPROD / 32) {
+  if (IMG && warp < XPROD / 32) {
+    // ---------------- producer: bulk copies of tile images ----------------
+    if (warp == 0 && lane == 0) {
+      int it = 0;
+      for (int ti = blockIdx.x; ti < ntiles && !*verr; ti += gridDim.x) {
+        const int sl = slice_of(L, ti);
+        const ExactSlice& S = L.sl[sl];
+        const int3 tr = S.tiles[ti - L.start[sl]];
+        const GemmTask t = S.tasks[tr.x];
+        if (task_chunks(t, S.segs) == 0) continue;  // the MMA issuer skips it too
+        const GemmSeg sg = S.segs[t.seg_begin];     // packed tasks: one segment
+        const int nkc = (sg.k + XKC - 1) / XKC;
+        const uint8_t* ga =
+            reinterpret_cast<const uint8_t*>(sg.a_dig) + (long long)tr.y * nkc * (long long)(4 * XA_PLANE);
+        const uint8_t* gb =
+            reinterpret_cast<const uint8_t*>(sg.b_dig) + (long long)tr.z * nkc * (long long)(4 * XB_PLANE);
+        bool ok = true;
+        for (int kc = 0; kc < nkc; ++kc, ++it) {
+          const int s = it % XSTAGES;
+          if (!mbar_wait(&empty_bar[s], ((it / XSTAGES) & 1) ^ 1, verr)) {
+            ok = false;
+            break;
+          }
+          uint8_t* st = stage_base + (size_t)s * XSTAGE;
+          mbar_arrive_expect(&full_bar[s], 4 * XA_PLANE + 4 * XB_PLANE);
+          bulk_g2s(st, ga + (long long)kc * (4 * XA_PLANE), 4 * XA_PLANE, &full_bar[s]);
+          bulk_g2s(st + 4 * XA_PLANE, gb + (long long)kc * (4 * XB_PLANE), 4 * XB_PLANE, &full_bar[s]);
+        }
+        if (!ok) break;
+      }
+    }
+  } else if (warp < XPROD / 32) {
     // ---------------- producers ----------------
     // The CTA's chunks (tile, segment, k0) in order; the records of the next chunk are
     // loaded into registers before the current chunk is unpacked, so the loads of one
@@ -1032,14 +1067,18 @@ void launch_gemm_exact_merged(const ExactLaunch& L, cudaStream_t s) {
   if (ntiles <= 0) return;
   const size_t sm = (size_t)XSTAGES * XSTAGE + 1024;
   static const int nsm = [sm] {  // once per process, thread-safe (function-local static)
-    cudaFuncSetAttribute(gemm_exact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(gemm_exact_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(gemm_exact_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     int dev = 0, n = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
     return n < 1 ? 1 : n;
   }();
+  bool img = true;
+  for (int i = 0; i < L.nslices; ++i) img = img && L.sl[i].img != 0;
   note_launch();
-  gemm_exact_kernel<<<ntiles < nsm ? ntiles : nsm, XTHREADS, sm, s>>>(L);
+  if (img) gemm_exact_kernel<true><<<ntiles < nsm ? ntiles : nsm, XTHREADS, sm, s>>>(L);
+  else gemm_exact_kernel<false><<<ntiles < nsm ? ntiles : nsm, XTHREADS, sm, s>>>(L);
 }
 
 int digit_job_size() { return DIGIT_JOB; }
