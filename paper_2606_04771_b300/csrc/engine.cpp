@@ -2817,13 +2817,28 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
     xp.ksplit = true;
     xp.finalize(stream_, kind_of(2), dstatus_);
     xp.launch(stream_, Bases4{{0, 0, 0, 0}});
-    // Newton-Schulz in FP64: K = X^H X, F = 1.5 I - 0.5 K, X <- X F (Z reused as scratch).
-    // Two steps: with one, the entropies of a chi = 4096 sweep moved by 2.6e-7 against
-    // 2.7e-8.  Both products stay on the FP64 pipe: BF16x4 products leave ~1e-8 of each
-    // row's scale, which the observables then see (1.7e-7 in n_i over one sweep).
-    DevBuf dnt = upload(nt, stream_);
+    // Newton-Schulz, X <- X (3 I - X^H X) / 2 = X + X E with E = (I - X^H X) / 2, two
+    // steps (with one, the entropies of a chi = 4096 sweep moved by 2.6e-7 against 2.7e-8).
+    // K = X^H X is formed on the FP64 pipe (its tiles on and above the diagonal): it
+    // sets the orthonormality the step reaches.  E is of the size of X's departure from
+    // orthonormality (~1e-7), so the correction X E runs as BF16x4 digit products (their
+    // 2^-30 relative error is ~1e-16 of X) and is added to X in FP64.
+    std::vector<const cplx*> eptr;
+    long long et = 0;
+    for (const NsTask& x : nt) et += (long long)x.k * x.k;
+    DevBuf dE(std::max<long long>(et, 1) * sizeof(cplx), stream_);
+    {
+      long long o = 0;
+      for (const NsTask& x : nt) {
+        eptr.push_back(dE.as<cplx>() + o);
+        o += (long long)x.k * x.k;
+      }
+    }
+    DevBuf dnt = upload(nt, stream_), dep = upload(eptr, stream_);
     for (int it = 0; it < 2; ++it) {
       GemmPlan g1, g2;
+      LincombPlan add;
+      int ti = 0;
       for (int g = 0; g < ng; ++g) {
         const Grp& G = groups[g];
         const int k = kept[g];
@@ -2855,39 +2870,35 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
         u.ldc = k;
         sh.a = Xb + xoff[g];
         sh.lda = k;
-        sh.b = Kb + koff[g];
+        sh.b = eptr[ti];
         sh.ldb = k;
         sh.k = k;
         u.seg_begin = (int)g2.segs.size();
         u.seg_count = 1;
         g2.segs.push_back(sh);
         g2.tasks.push_back(u);
+        // X += Z (Z rows >= X rows, packed at the same pitch k)
+        LincombTask lt{};
+        lt.out = Xb + xoff[g];
+        lt.rows = dim;
+        lt.cols = k;
+        lt.ld_out = k;
+        lt.term_begin = (int)add.terms.size();
+        lt.term_count = 2;
+        add.terms.push_back({Xb + xoff[g], k, 1.0});
+        add.terms.push_back({Zb + zoff[g], k, 1.0});
+        add.tasks.push_back(lt);
+        ++ti;
       }
+      g1.upper_only = true;
       g1.ksplit = true;
-      g1.finalize(stream_, kind_of(4), dstatus_);
+      g1.finalize(stream_, (tcm & 4) ? 1 : -1, dstatus_);
       g1.launch(stream_, Bases4{{0, 0, 0, 0}});
-      launch_ns_coeff(dnt.as<NsTask>(), (int)nt.size(), stream_);
-      g2.ksplit = true;
-      g2.finalize(stream_, kind_of(4), dstatus_);
+      launch_ns_corr(dnt.as<NsTask>(), dep.as<const cplx*>(), (int)nt.size(), stream_);
+      g2.finalize(stream_, 1, dstatus_);
       g2.launch(stream_, Bases4{{0, 0, 0, 0}});
-      CopyPlan back;  // X <- X F (Z holds X F; Z rows >= X rows, packed at the same pitch k)
-      for (int g = 0; g < ng; ++g) {
-        const Grp& G = groups[g];
-        const int k = kept[g];
-        if (!k || from_g(G)) continue;
-        CopyTask c{};
-        c.src = Zb + zoff[g];
-        c.dst = Xb + xoff[g];
-        c.rows = xrows(G);
-        c.cols = k;
-        c.src_rs = k;
-        c.src_cs = 1;
-        c.dst_rs = k;
-        c.dst_cs = 1;
-        back.tasks.push_back(c);
-      }
-      back.finalize(stream_);
-      back.launch(stream_);
+      add.finalize(stream_);
+      add.launch(stream_);
     }
   }
   smark("kept basis + Newton-Schulz");

@@ -1957,6 +1957,20 @@ __global__ void ns_coeff_kernel(const NsTask* __restrict__ tasks) {
   }
 }
 
+// E = (I - K) / 2 for the Newton-Schulz correction X <- X + X E (k x k, row-major),
+// from K's upper triangle only (K Hermitian: K[i][j] = conj(K[j][i]) below it), into e
+__global__ void ns_corr_kernel(const NsTask* __restrict__ tasks, const cplx* const* __restrict__ outs) {
+  const NsTask t = tasks[blockIdx.y];
+  cplx* const e = const_cast<cplx*>(outs[blockIdx.y]);
+  const int n = t.k * t.k;
+  for (int x = blockIdx.x * 256 + threadIdx.x; x < n; x += gridDim.x * 256) {
+    const int i = x / t.k, j = x - i * t.k;
+    cplx g = i <= j ? t.g[x] : t.g[(long long)j * t.k + i];
+    if (i > j) g.y = -g.y;
+    e[x] = {(i == j ? 0.5 : 0.0) - 0.5 * g.x, -0.5 * g.y};
+  }
+}
+
 static int conv_grid(long long n) {
   long long b = (n + 255) / 256;
   return (int)(b < 1184 ? (b < 1 ? 1 : b) : 1184);
@@ -1977,6 +1991,12 @@ void launch_basis64(const BasisTask* tasks, int n, cudaStream_t s) {
   if (n > 0) {
     note_launch();
     basis64_kernel<<<dim3(32, n), 256, 0, s>>>(tasks);
+  }
+}
+void launch_ns_corr(const NsTask* tasks, const cplx* const* outs, int n, cudaStream_t s) {
+  if (n > 0) {
+    note_launch();
+    ns_corr_kernel<<<dim3(8, n), 256, 0, s>>>(tasks, outs);
   }
 }
 void launch_ns_coeff(const NsTask* tasks, int n, cudaStream_t s) {

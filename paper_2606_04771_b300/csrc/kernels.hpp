@@ -135,6 +135,9 @@ void launch_narrow(const cplx* src, float2* dst, long long n, cudaStream_t s);
 void launch_widen(const float2* src, cplx* dst, long long n, cudaStream_t s);
 void launch_basis64(const BasisTask* tasks, int n, cudaStream_t s);
 void launch_ns_coeff(const NsTask* tasks, int n, cudaStream_t s);
+// E = (I - K) / 2 into outs[i] from the upper triangle of task i's K (Newton-Schulz
+// correction form X <- X + X E)
+void launch_ns_corr(const NsTask* tasks, const cplx* const* outs, int n, cudaStream_t s);
 // in-place Cholesky K = R^H R (upper R) and R^-1 for each task; a non-positive pivot
 // adds 1 to *status
 void launch_chol_inv(const CholTask* tasks, int n, double shift_rel, int* status, cudaStream_t s);
