@@ -2359,21 +2359,23 @@ double Engine::split(BTensor& theta, const BondSpace& bl, const BondSpace& br, l
 // cold start needs (both measured on the chi = 4096 chain).  The basis the sweep keeps (left for left to right, right for right
 // to left) is G/S when it is W's column space, otherwise W^H G / S^2
 // re-orthonormalised by two Newton-Schulz steps X <- X (3 I - X^H X) / 2 (the
-// overlaps it starts from are O(1e-7)); the other factor is the exact FP64
+// overlaps it starts from reach ~1e-3 for the vectors of the smallest kept values,
+// whose division by S^2 amplifies the O(1e-7) errors of G); the other factor is the exact FP64
 // projection of theta onto that basis.  ok is set when the split was done here (the
 // caller runs the FP64 split otherwise).
 // ---------------------------------------------------------------------------
 
 // Which of the mixed split's own products run as BF16x4 digit products on the tensor
 // cores instead of the FP64 pipe: a bit mask from TDVP_SPLIT_GEMM_TC (read at every
-// split; default 10): 1 G = W V, 2 the kept basis W^H Z, 4 the Newton-Schulz products,
-// 8 the projection of theta onto the kept basis.  BF16x4 rounds to 2^-30 of each
+// split; default 10): 1 G = W V, 2 the kept basis W^H Z, 4 the Gram matrix of the
+// second Newton-Schulz step (the first step's always runs as BF16x4), 8 the projection of theta onto the kept basis.  BF16x4 rounds to 2^-30 of each
 // operand row's and column's scale (plus ~K 2^-32 for the dropped digit orders).  For
 // the kept basis that is a direction error of the smallest kept vectors, which moves
 // the truncated state by (a discarded value) x (that error), and for the projection an
 // absolute error of ~1e-9 of the state, both below the BF16x4 matvec's own.  G = W V
-// and Newton-Schulz stay FP64: G's small columns would carry errors relative to the
-// largest, and Newton-Schulz's product sets the orthonormality of the kept basis.
+// and the last Newton-Schulz Gram matrix stay FP64: G's small columns would carry
+// errors relative to the largest, and that Gram matrix sets the orthonormality of the
+// kept basis.
 static int split_tc_mask() {
   const char* e = std::getenv("TDVP_SPLIT_GEMM_TC");
   return e && *e ? std::atoi(e) : 10;
@@ -2819,10 +2821,13 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
     xp.launch(stream_, Bases4{{0, 0, 0, 0}});
     // Newton-Schulz, X <- X (3 I - X^H X) / 2 = X + X E with E = (I - X^H X) / 2, two
     // steps (with one, the entropies of a chi = 4096 sweep moved by 2.6e-7 against 2.7e-8).
-    // K = X^H X is formed on the FP64 pipe (its tiles on and above the diagonal): it
-    // sets the orthonormality the step reaches.  E is of the size of X's departure from
-    // orthonormality (~1e-7), so the correction X E runs as BF16x4 digit products (their
-    // 2^-30 relative error is ~1e-16 of X) and is added to X in FP64.
+    // Only its tiles on and above the diagonal of K = X^H X are formed.  X's columns of
+    // small singular values start about u32 sigma_max / sigma (up to ~1e-3) away from
+    // orthonormal, and the first step brings that to its square: its K may carry the
+    // 2^-30 relative error of BF16x4 digit products.  The second step's K, which sets the
+    // orthonormality reached, is formed on the FP64 pipe.  E is of the size of X's
+    // departure from orthonormality, so the correction X E runs as BF16x4 digit products
+    // (error ~2^-30 |E| of X) and is added to X in FP64.
     std::vector<const cplx*> eptr;
     long long et = 0;
     for (const NsTask& x : nt) et += (long long)x.k * x.k;
@@ -2892,7 +2897,7 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
       }
       g1.upper_only = true;
       g1.ksplit = true;
-      g1.finalize(stream_, (tcm & 4) ? 1 : -1, dstatus_);
+      g1.finalize(stream_, (tcm & 4) || it == 0 ? 1 : -1, dstatus_);
       g1.launch(stream_, Bases4{{0, 0, 0, 0}});
       launch_ns_corr(dnt.as<NsTask>(), dep.as<const cplx*>(), (int)nt.size(), stream_);
       g2.finalize(stream_, 1, dstatus_);
