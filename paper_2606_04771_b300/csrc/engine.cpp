@@ -15,6 +15,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
+#include <mutex>
 #include <chrono>
 #include <cmath>
 #include <cstdint>
@@ -90,6 +91,18 @@ struct PlanClock {
   }
 };
 
+// hash of a small array of ints (FNV-1a over the values), for the planners' maps
+struct IntArrayHash {
+  template <size_t N>
+  size_t operator()(const std::array<int, N>& a) const {
+    uint64_t h = 1469598103934665603ull;
+    for (int v : a) h = (h ^ (uint64_t)(uint32_t)v) * 1099511628211ull;
+    return (size_t)h;
+  }
+};
+template <size_t N, class V>
+using IntArrayMap = std::unordered_map<std::array<int, N>, V, IntArrayHash>;
+
 template <class T>
 static DevBuf upload(const std::vector<T>& v, cudaStream_t s) {
   DevBuf b(std::max<size_t>(v.size(), 1) * sizeof(T), s);
@@ -102,24 +115,47 @@ void GemmPlan::finalize(cudaStream_t s, int kind_, int* status_) {
   kind = kind_;
   status = status_;
   if (!packed.empty() && kind != 1) throw Error(-5, "packed GEMM plans need the BF16x4 kernel");
-  // algorithmic bytes: each distinct operand block read once, each output written once
-  std::map<std::pair<int, uintptr_t>, long long> seen;
+  static const bool fdbg = std::getenv("TDVP_PLAN_DEBUG") != nullptr;
+  auto ft0 = std::chrono::steady_clock::now();
+  auto fmark = [&](const char* what) {
+    if (!fdbg) return;
+    const auto now = std::chrono::steady_clock::now();
+    std::fprintf(stderr, "plan   finalize %s %.3f ms (%zu tasks, %zu segs)\n", what,
+                 std::chrono::duration<double, std::milli>(now - ft0).count(), tasks.size(), segs.size());
+    ft0 = now;
+  };
+  // algorithmic bytes: each distinct operand block (base, address) read once, with the
+  // size of its last use, and each output written once
+  struct Use {
+    int base;
+    uintptr_t ptr;
+    long long n;
+  };
+  std::vector<Use> seen;
   bytes = 0;
   for (int i = 0; i < (int)tasks.size(); ++i) {
     const GemmTask& t = tasks[i];
     bytes += (long long)t.rows * t.cols * (long long)sizeof(cplx);
     if (!packed.empty()) {
-      for (const PackedSrc& q : packed[i].a) seen[{q.base, reinterpret_cast<uintptr_t>(q.src)}] = (long long)q.rows * q.cols;
-      for (const PackedSrc& q : packed[i].b) seen[{q.base, reinterpret_cast<uintptr_t>(q.src)}] = (long long)q.rows * q.cols;
+      for (const PackedSrc& q : packed[i].a)
+        seen.push_back({q.base, reinterpret_cast<uintptr_t>(q.src), (long long)q.rows * q.cols});
+      for (const PackedSrc& q : packed[i].b)
+        seen.push_back({q.base, reinterpret_cast<uintptr_t>(q.src), (long long)q.rows * q.cols});
       continue;
     }
     for (int k = 0; k < t.seg_count; ++k) {
       const GemmSeg& g = segs[t.seg_begin + k];
-      seen[{g.a_base, reinterpret_cast<uintptr_t>(g.a)}] = (long long)t.rows * g.k;
-      seen[{g.b_base, reinterpret_cast<uintptr_t>(g.b)}] = (long long)g.k * t.cols;
+      seen.push_back({g.a_base, reinterpret_cast<uintptr_t>(g.a), (long long)t.rows * g.k});
+      seen.push_back({g.b_base, reinterpret_cast<uintptr_t>(g.b), (long long)g.k * t.cols});
     }
   }
-  for (auto& e : seen) bytes += e.second * (long long)sizeof(cplx);
+  std::stable_sort(seen.begin(), seen.end(), [](const Use& x, const Use& y) {
+    return x.base != y.base ? x.base < y.base : x.ptr < y.ptr;
+  });
+  for (size_t i = 0; i < seen.size(); ++i)
+    if (i + 1 == seen.size() || seen[i + 1].base != seen[i].base || seen[i + 1].ptr != seen[i].ptr)
+      bytes += seen[i].n * (long long)sizeof(cplx);
+  fmark("bytes");
   tiles.clear();
   const int tm = kind < 0 ? 64 : split_tile_m(), tn0 = kind < 0 ? 64 : split_tile_n(kind);
   for (int i = 0; i < (int)tasks.size(); ++i) {
@@ -195,11 +231,14 @@ void GemmPlan::finalize(cudaStream_t s, int kind_, int* status_) {
     for (int i = 0; i < (int)tasks.size(); ++i)
       tasks[i].rowoff = (i < (int)row_start.size() && row_start[i] >= 0) ? drow.as<long long>() + row_start[i] : nullptr;
   }
+  fmark("tiles");
   if (kind == 1 && !packed.empty()) plan_packed(s);
   else if (kind == 1) plan_digits(s);
+  fmark("digits");
   dt = upload(tasks, s);
   ds = upload(segs, s);
   dti = upload(tiles, s);
+  fmark("upload");
 }
 
 // BF16x4: every distinct operand block (same storage, shape, op and alpha) is split
@@ -593,6 +632,34 @@ static inline cplx* as_off(long long off) { return reinterpret_cast<cplx*>(stati
 // construction
 // ---------------------------------------------------------------------------
 
+// The engine's device buffers come from the current device's default memory pool
+// (cudaMallocAsync).  With the pool's default release threshold of zero, every stream
+// synchronisation hands the unused memory back and the next allocations map it again;
+// a bond update allocates and frees its work buffers many times between syncs.  The
+// pool is therefore allowed to keep up to TDVP_POOL_KEEP_MB megabytes (default 4096)
+// of freed memory, once per device and process; a larger threshold already set is
+// left as it is.
+static void keep_pool_memory() {
+  static std::mutex m;
+  static std::vector<int> done;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  std::lock_guard<std::mutex> g(m);
+  if (std::find(done.begin(), done.end(), dev) != done.end()) return;
+  done.push_back(dev);
+  const char* e = std::getenv("TDVP_POOL_KEEP_MB");
+  const unsigned long long want = (unsigned long long)(e && *e ? std::atoll(e) : 4096) << 20;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  unsigned long long cur = 0;
+  if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &cur) == cudaSuccess && cur < want)
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, (void*)&want);
+  cudaGetLastError();
+}
+
 void Engine::init_common(bool su2, double J, double U, const Opts& o) {
   opt_ = o;
   if (o.krylov_max < 1 || o.krylov_max > KRYLOV_MAX) throw Error(-1, "krylov_max must be in [1, 32]");
@@ -608,6 +675,7 @@ void Engine::init_common(bool su2, double J, double U, const Opts& o) {
     TDVP_CUDA(cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking));
     own_stream_ = true;
   }
+  keep_pool_memory();
   const char* pe = std::getenv("TDVP_PROFILE_PHASES");
   profile_ = pe && pe[0] == '1';
   TDVP_CUDA(cudaMallocHost(&pinned_, 4096));
@@ -1397,20 +1465,42 @@ void Engine::plan_heff2_packed(HeffPlan& p, const BTensor& Lenv, const BTensor& 
     p.g1.tasks.push_back(t);
   }
   pmark("stage 1");
-  // stage 2: recoupling terms (as plan_heff2)
+  // stage 2: recoupling terms (as plan_heff2).  The output sector b' of a term and the
+  // existence of R(b, w2, b') depend on (b, w2, 2S_b') alone: a table filled on first use.
+  int tmin = 0, tmax = -1;
+  for (int k = 0; k < (int)br.s.size(); ++k) {
+    tmin = k ? std::min(tmin, br.s[k].t) : br.s[k].t;
+    tmax = k ? std::max(tmax, br.s[k].t) : br.s[k].t;
+  }
+  const int nch = (int)M.chan.size(), tl = tmax - tmin + 1;
+  const bool tabled = tl > 0 && (long long)br.s.size() * nch * tl <= (1LL << 24);
+  std::vector<int> bpc(tabled ? (size_t)br.s.size() * nch * tl : 0, -2);
+  auto target = [&](int b, int w2, int tbp) {
+    int* c = nullptr;
+    if (tabled) {
+      if (tbp < tmin || tbp > tmax) return -1;  // no sector of br has that spin
+      c = &bpc[((size_t)b * nch + w2) * tl + (tbp - tmin)];
+      if (*c != -2) return *c;
+    }
+    int bp = br.find(br.s[b].n + M.chan[w2].n, tbp);
+    if (bp >= 0 && Renv.find(bkey(b, w2, bp)) < 0) bp = -1;
+    if (c) *c = bp;
+    return bp;
+  };
   std::unordered_map<uint64_t, int> t2idx;
   std::vector<std::vector<std::pair<int, double>>> t2terms;
   std::vector<std::array<int, 7>> t2keys;
+  long long nterm = 0;
   for (int i = 0; i < (int)t1v.size(); ++i) {
     const Block& lk = Lenv.blocks[t1v[i].lb];
     const Block& th = theta.blocks[t1v[i].tb];
     int ap = lk.key[0], w = lk.key[1], a = th.key[0], s1 = th.key[1], tc = th.key[2], s2 = th.key[3], b = th.key[4];
     const auto& rc = rec_->two_site(bl.s[ap].t, w, bl.s[a].t, s1, tc, s2, br.s[b].t);
+    nterm += (long long)rc.size();
     for (const auto& e : rc) {
-      int nbp = br.s[b].n + M.chan[e.w2].n;
-      int bp = br.find(nbp, e.tbp);
+      const int bp = target(b, e.w2, e.tbp);
       if (bp < 0) continue;
-      if (Renv.find(bkey(b, e.w2, bp)) < 0) continue;
+      const int nbp = br.s[bp].n;
       if (bl.s[ap].n + M.site[e.s1p].n + M.site[e.s2p].n != nbp) throw Error(-5, "charge mismatch in recoupling");
       const uint64_t key = t2key(ap, e.s1p, e.tcp, e.s2p, bp, e.w2, b);
       auto it = t2idx.find(key);
@@ -1426,14 +1516,20 @@ void Engine::plan_heff2_packed(HeffPlan& p, const BTensor& Lenv, const BTensor& 
       t2terms[id].push_back({i, e.f});
     }
   }
+  if (pdbg)
+    std::fprintf(stderr, "plan heff2 %zu T1 views, %lld recoupling terms, %zu T2 blocks\n", t1v.size(), nterm,
+                 t2keys.size());
   pmark("stage 2");
   // stage 3 grouping by output column sector b'
   const int nsr = (int)br.s.size();
   std::vector<std::vector<int>> oby(nsr);  // output (theta) blocks by right sector
   for (int ob = 0; ob < (int)theta.blocks.size(); ++ob) oby[theta.blocks[ob].key[4]].push_back(ob);
   std::vector<long long> orow(theta.blocks.size(), 0);
-  std::vector<std::map<std::pair<int, int>, int>> segcol(nsr);  // (w2, b) -> column offset
-  std::vector<int> gk(nsr, 0), gm(nsr, 0), t2g(nsr, -1);
+  // the (w2, b) channels of each output column sector, in increasing (w2, b) order, at
+  // column offsets segoff[bp][j]; colof[id] is the column offset of T2 block id
+  std::vector<std::vector<std::pair<int, int>>> segcol(nsr);
+  std::vector<std::vector<int>> segoff(nsr);
+  std::vector<int> gk(nsr, 0), gm(nsr, 0), t2g(nsr, -1), colof(t2keys.size(), 0), obof(t2keys.size(), -1);
   for (int bp = 0; bp < nsr; ++bp) {
     int m = 0;
     for (int ob : oby[bp]) {
@@ -1442,14 +1538,28 @@ void Engine::plan_heff2_packed(HeffPlan& p, const BTensor& Lenv, const BTensor& 
     }
     gm[bp] = m;
   }
-  for (const auto& k : t2keys) segcol[k[4]][{k[5], k[6]}] = 0;
-  for (int bp = 0; bp < nsr; ++bp) {
-    int kk = 0;
-    for (auto& e : segcol[bp]) {
-      e.second = kk;
-      kk += br.s[e.first.second].d;
+  if (nch >= (1 << 8) || nsr >= (1 << 24)) throw Error(-5, "too many sectors or channels for the stage-3 layout");
+  auto chkey = [](int bp, int w2, int b) { return ((uint64_t)bp << 32) | ((uint64_t)w2 << 24) | (uint64_t)b; };
+  {
+    std::unordered_map<uint64_t, int> seen;
+    seen.reserve(2 * t2keys.size() + 16);
+    for (const auto& k : t2keys)
+      if (seen.emplace(chkey(k[4], k[5], k[6]), 0).second) segcol[k[4]].push_back({k[5], k[6]});
+    for (int bp = 0; bp < nsr; ++bp) {
+      std::sort(segcol[bp].begin(), segcol[bp].end());
+      int kk = 0;
+      for (const auto& e : segcol[bp]) {
+        segoff[bp].push_back(kk);
+        seen[chkey(bp, e.first, e.second)] = kk;
+        kk += br.s[e.second].d;
+      }
+      gk[bp] = kk;
     }
-    gk[bp] = kk;
+    for (int id = 0; id < (int)t2keys.size(); ++id) {
+      const auto& k = t2keys[id];
+      colof[id] = seen.at(chkey(k[4], k[5], k[6]));
+      obof[id] = theta.find(bkey(k[0], k[1], k[2], k[3], k[4]));
+    }
   }
   p.t2.kind = THETA;
   for (int bp = 0; bp < nsr; ++bp)
@@ -1462,9 +1572,9 @@ void Engine::plan_heff2_packed(HeffPlan& p, const BTensor& Lenv, const BTensor& 
   for (int id = 0; id < (int)t2keys.size(); ++id) {
     const auto& k = t2keys[id];
     const int bp = k[4];
-    const int ob = theta.find(bkey(k[0], k[1], k[2], k[3], k[4]));
+    const int ob = obof[id];
     if (ob < 0) throw Error(-5, "recoupled block outside the two-site layout");
-    t2ptr[id] = p.t2.ptr(t2g[bp]) + orow[ob] * gk[bp] + segcol[bp].at({k[5], k[6]});
+    t2ptr[id] = p.t2.ptr(t2g[bp]) + orow[ob] * gk[bp] + colof[id];
     LincombTask t{};
     t.out = t2ptr[id];
     t.rows = bl.s[k[0]].d;
@@ -1502,11 +1612,11 @@ void Engine::plan_heff2_packed(HeffPlan& p, const BTensor& Lenv, const BTensor& 
     pk.a_static = false;
     pk.b_static = true;
     if (t2g[bp] >= 0) {
-      for (auto& e : segcol[bp]) {
-        const int w2 = e.first.first, b = e.first.second;
+      for (size_t j = 0; j < segcol[bp].size(); ++j) {
+        const int w2 = segcol[bp][j].first, b = segcol[bp][j].second;
         const int rb = Renv.find(bkey(b, w2, bp));
         const Block& rk = Renv.blocks[rb];
-        pk.b.push_back({Renv.ptr(rb), 0, rk.rows, rk.cols, rk.cols, OP_N, 1.0, e.second, 0});
+        pk.b.push_back({Renv.ptr(rb), 0, rk.rows, rk.cols, rk.cols, OP_N, 1.0, segoff[bp][j], 0});
       }
     }
     p.g3.packed.push_back(std::move(pk));
@@ -1514,37 +1624,28 @@ void Engine::plan_heff2_packed(HeffPlan& p, const BTensor& Lenv, const BTensor& 
     p.g3.out_blocks.push_back(oby[bp]);
     p.g3.task_flops.push_back(0);
   }
+  std::vector<int> task_of(nsr, -1);  // output column sector -> stage-3 task
   {
-    std::map<int, int> task_of;  // output column sector -> stage-3 task
     int ti = 0;
     for (int bp = 0; bp < nsr; ++bp)
       if (!oby[bp].empty()) task_of[bp] = ti++;
     for (int id = 0; id < (int)t2keys.size(); ++id) {
       const auto& k = t2keys[id];
       const int bp = k[4];
-      const int ob = theta.find(bkey(k[0], k[1], k[2], k[3], k[4]));
+      const int ob = obof[id];
       const int rows = bl.s[k[0]].d, cols = br.s[k[6]].d;
-      p.g3.packed[task_of.at(bp)].a.push_back(
-          {t2ptr[id], 0, rows, cols, gk[bp], OP_N, 1.0, (int)orow[ob], segcol[bp].at({k[5], k[6]})});
+      p.g3.packed[task_of[bp]].a.push_back({t2ptr[id], 0, rows, cols, gk[bp], OP_N, 1.0, (int)orow[ob], colof[id]});
       p.g3.flops += 8LL * rows * cols * br.s[bp].d;
-      p.g3.task_flops[task_of.at(bp)] += 8LL * rows * cols * br.s[bp].d;
+      p.g3.task_flops[task_of[bp]] += 8LL * rows * cols * br.s[bp].d;
     }
   }
   pmark("stage 3");
   p.g1.finalize(stream_, gemm_kind_, dstatus_ + 1);
   p.g3.dyn_tags_external = true;
   p.g3.finalize(stream_, gemm_kind_, dstatus_ + 1);
-  {  // the linear combination raises the exponent tags of the stage-3 operand's rows
-    std::map<int, int> task_of;
-    int ti = 0;
-    for (int bp = 0; bp < nsr; ++bp)
-      if (!oby[bp].empty()) task_of[bp] = ti++;
-    for (int id = 0; id < (int)t2keys.size(); ++id) {
-      const auto& k = t2keys[id];
-      const int ob = theta.find(bkey(k[0], k[1], k[2], k[3], k[4]));
-      p.lc.tasks[id].tags = p.g3.tags() + p.g3.tasks[task_of.at(k[4])].roff + orow[ob];
-    }
-  }
+  // the linear combination raises the exponent tags of the stage-3 operand's rows
+  for (int id = 0; id < (int)t2keys.size(); ++id)
+    p.lc.tasks[id].tags = p.g3.tags() + p.g3.tasks[task_of[t2keys[id][4]]].roff + orow[obof[id]];
   p.lc.finalize(stream_);
 }
 
@@ -1646,10 +1747,10 @@ void Engine::plan_heff2(HeffPlan& p, const BTensor& Lenv, const BTensor& Renv, c
     p.lc.bytes += (long long)sizeof(cplx) * bk.rows * bk.cols * (1 + t.term_count);
   }
   // step 3: theta'(a',s1',c',s2',b') = sum_{w2,b} T2 R(b,w2,b')
-  std::map<std::tuple<int, int, int, int, int>, std::vector<int>> outsegs;
+  IntArrayMap<5, std::vector<int>> outsegs;
   for (int id = 0; id < (int)t2keys.size(); ++id) {
     auto& k = t2keys[id];
-    outsegs[std::make_tuple(k[0], k[1], k[2], k[3], k[4])].push_back(id);
+    outsegs[{k[0], k[1], k[2], k[3], k[4]}].push_back(id);
   }
   for (int ob = 0; ob < (int)theta.blocks.size(); ++ob) {
     const Block& o = theta.blocks[ob];
@@ -1660,7 +1761,7 @@ void Engine::plan_heff2(HeffPlan& p, const BTensor& Lenv, const BTensor& Renv, c
     t.cols = o.cols;
     t.ldc = o.cols;
     t.seg_begin = (int)p.g3.segs.size();
-    auto it = outsegs.find(std::make_tuple(o.key[0], o.key[1], o.key[2], o.key[3], o.key[4]));
+    auto it = outsegs.find({o.key[0], o.key[1], o.key[2], o.key[3], o.key[4]});
     int cnt = 0;
     long long tf = 0;
     if (it != outsegs.end()) {
@@ -1739,7 +1840,8 @@ static void plan_l_w(Engine* eng, const Model& M, Recoupler& rec, HeffPlan& p, c
     p.g1.tasks.push_back(t);
     p.g1.flops += 8LL * lk.rows * lk.cols * x.cols;
   }
-  std::map<std::array<int, 5>, int> idx;
+  IntArrayMap<5, int> idx;
+  idx.reserve(4 * info.size() + 16);
   std::vector<std::vector<std::pair<int, double>>> terms;
   for (int i = 0; i < (int)info.size(); ++i) {
     const Block& lk = Lenv.blocks[info[i].first];
@@ -1794,7 +1896,7 @@ void Engine::plan_heff1(HeffPlan& p, const BTensor& Lenv, const BTensor& Renv, c
     return Renv.find(bkey(k[4], k[3], k[2])) >= 0 && Mt.find(bkey(k[0], k[1], k[2])) >= 0;
   };
   plan_l_w(this, model_, *rec_, p, Lenv, Mt, bl, br, keep, t2keys, stream_, &Engine::alloc);
-  std::map<std::array<int, 3>, std::vector<int>> outsegs;
+  IntArrayMap<3, std::vector<int>> outsegs;
   for (int id = 0; id < (int)t2keys.size(); ++id) outsegs[{t2keys[id][0], t2keys[id][1], t2keys[id][2]}].push_back(id);
   for (int ob = 0; ob < (int)Mt.blocks.size(); ++ob) {
     const Block& o = Mt.blocks[ob];
@@ -1844,7 +1946,7 @@ void Engine::update_left_env(const BTensor& Lin, const BTensor& A, BTensor& Lout
     return Lout.find(bkey(k[2], k[3], k[4])) >= 0 && A.find(bkey(k[0], k[1], k[2])) >= 0;
   };
   plan_l_w(this, model_, *rec_, p, Lin, A, bl, br, keep, t2keys, stream_, &Engine::alloc);
-  std::map<std::array<int, 3>, std::vector<int>> outsegs;  // (b'', w', b)
+  IntArrayMap<3, std::vector<int>> outsegs;  // (b'', w', b)
   for (int id = 0; id < (int)t2keys.size(); ++id) outsegs[{t2keys[id][2], t2keys[id][3], t2keys[id][4]}].push_back(id);
   for (int ob = 0; ob < (int)Lout.blocks.size(); ++ob) {
     const Block& o = Lout.blocks[ob];
@@ -1929,7 +2031,8 @@ void Engine::update_right_env(const BTensor& Rin, const BTensor& Bt, BTensor& Ro
     p.g1.flops += 8LL * x.rows * x.cols * rk.cols;
   }
   // step 2: F2(a,w,a'',s',b')
-  std::map<std::array<int, 5>, int> idx;
+  IntArrayMap<5, int> idx;
+  idx.reserve(4 * info.size() + 16);
   std::vector<std::array<int, 5>> keys;
   std::vector<std::vector<std::pair<int, double>>> terms;
   for (int i = 0; i < (int)info.size(); ++i) {
@@ -1972,7 +2075,7 @@ void Engine::update_right_env(const BTensor& Rin, const BTensor& Bt, BTensor& Ro
     p.lc.tasks.push_back(t);
   }
   // step 3: R'(a,w,a'') = sum_{s',b'} F2(a,w,a'',s',b') B(a'',s',b')^H
-  std::map<std::array<int, 3>, std::vector<int>> outsegs;
+  IntArrayMap<3, std::vector<int>> outsegs;
   for (int id = 0; id < (int)keys.size(); ++id) outsegs[{keys[id][0], keys[id][1], keys[id][2]}].push_back(id);
   for (int ob = 0; ob < (int)Rout.blocks.size(); ++ob) {
     const Block& o = Rout.blocks[ob];
