@@ -1491,11 +1491,28 @@ void Engine::plan_heff2_packed(HeffPlan& p, const BTensor& Lenv, const BTensor& 
   std::vector<std::vector<std::pair<int, double>>> t2terms;
   std::vector<std::array<int, 7>> t2keys;
   long long nterm = 0;
+  // the views of one theta block come together, and their terms depend on (2S_a', w) alone
+  int memo_tb = -1;
+  std::vector<std::tuple<int, int, const std::vector<Recouple2>*>> memo;
   for (int i = 0; i < (int)t1v.size(); ++i) {
     const Block& lk = Lenv.blocks[t1v[i].lb];
     const Block& th = theta.blocks[t1v[i].tb];
     int ap = lk.key[0], w = lk.key[1], a = th.key[0], s1 = th.key[1], tc = th.key[2], s2 = th.key[3], b = th.key[4];
-    const auto& rc = rec_->two_site(bl.s[ap].t, w, bl.s[a].t, s1, tc, s2, br.s[b].t);
+    if (t1v[i].tb != memo_tb) {
+      memo.clear();
+      memo_tb = t1v[i].tb;
+    }
+    const std::vector<Recouple2>* rcp = nullptr;
+    for (const auto& m : memo)
+      if (std::get<0>(m) == bl.s[ap].t && std::get<1>(m) == w) {
+        rcp = std::get<2>(m);
+        break;
+      }
+    if (!rcp) {
+      rcp = &rec_->two_site(bl.s[ap].t, w, bl.s[a].t, s1, tc, s2, br.s[b].t);
+      memo.emplace_back(bl.s[ap].t, w, rcp);
+    }
+    const auto& rc = *rcp;
     nterm += (long long)rc.size();
     for (const auto& e : rc) {
       const int bp = target(b, e.w2, e.tbp);
