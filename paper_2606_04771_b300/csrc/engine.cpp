@@ -2487,18 +2487,23 @@ double Engine::split(BTensor& theta, const BondSpace& bl, const BondSpace& br, l
 
 // Which of the mixed split's own products run as BF16x4 digit products on the tensor
 // cores instead of the FP64 pipe: a bit mask from TDVP_SPLIT_GEMM_TC (read at every
-// split; default 10): 1 G = W V, 2 the kept basis W^H Z, 4 the Gram matrix of the
-// second Newton-Schulz step (the first step's always runs as BF16x4), 8 the projection of theta onto the kept basis.  BF16x4 rounds to 2^-30 of each
+// split; default 26): 1 G = W V, 2 the kept basis W^H Z, 4 the Gram matrix of the
+// second Newton-Schulz step (the first step's always runs as BF16x4), 8 the projection,
+// 16 G = W V of the sectors whose kept basis is G's own column side (G / S). of theta onto the kept basis.  BF16x4 rounds to 2^-30 of each
 // operand row's and column's scale (plus ~K 2^-32 for the dropped digit orders).  For
 // the kept basis that is a direction error of the smallest kept vectors, which moves
 // the truncated state by (a discarded value) x (that error), and for the projection an
 // absolute error of ~1e-9 of the state, both below the BF16x4 matvec's own.  G = W V
-// and the last Newton-Schulz Gram matrix stay FP64: G's small columns would carry
-// errors relative to the largest, and that Gram matrix sets the orthonormality of the
-// kept basis.
+// and the last Newton-Schulz Gram matrix stay FP64 where the kept basis is W^H G / S^2:
+// that product divides G's errors (2^-32 of the largest column) by S^2, and that Gram
+// matrix sets the orthonormality of the kept basis.  Where the basis is G / S itself, a
+// BF16x4 G is the exact G of W + dW with |dW| ~ 2^-32 |W| (each operand row and column
+// keeps its own scale), and the Gram finish, the truncation and the projection then act
+// on that matrix: the split is the exact truncated split of a matrix within the BF16x4
+// matvec's own error of theta.
 static int split_tc_mask() {
   const char* e = std::getenv("TDVP_SPLIT_GEMM_TC");
-  return e && *e ? std::atoi(e) : 10;
+  return e && *e ? std::atoi(e) : 26;
 }
 
 // a float from the environment (read at every call), or the default
@@ -2796,9 +2801,11 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
   launch_widen(V32, V64, vtot, stream_);
   // G = W V in FP64: row-major G^T (Q x P) = V^T (Q x Q) W^T (Q x P)
   {
-    GemmPlan gp;
+    // gp[1]: the groups whose kept basis is G's own column side, gp[0]: the others
+    GemmPlan gp[2];
     for (int g = 0; g < ng; ++g) {
       const int P = bigP(groups[g]), Q = smallQ(groups[g]);
+      GemmPlan& pl = gp[from_g(groups[g]) ? 1 : 0];
       GemmTask t{};
       GemmSeg sg{};
       sg.alpha = 1.0;
@@ -2811,14 +2818,17 @@ double Engine::split_mixed(BTensor& theta, const BondSpace& bl, const BondSpace&
       sg.b = W64 + toff[g];
       sg.ldb = P;
       sg.k = Q;
-      t.seg_begin = (int)gp.segs.size();
+      t.seg_begin = (int)pl.segs.size();
       t.seg_count = 1;
-      gp.segs.push_back(sg);
-      gp.tasks.push_back(t);
+      pl.segs.push_back(sg);
+      pl.tasks.push_back(t);
     }
-    gp.ksplit = true;
-    gp.finalize(stream_, kind_of(1), dstatus_);
-    gp.launch(stream_, Bases4{{0, 0, 0, 0}});
+    for (int k = 0; k < 2; ++k) {
+      if (gp[k].tasks.empty()) continue;
+      gp[k].ksplit = true;
+      gp[k].finalize(stream_, (tcm & 1) || (k == 1 && (tcm & 16)) ? 1 : -1, dstatus_);
+      gp[k].launch(stream_, Bases4{{0, 0, 0, 0}});
+    }
   }
   smark("G = W V");
   std::vector<SvdTask> st(ng);
