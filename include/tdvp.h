@@ -81,16 +81,24 @@ typedef struct {
 
 /* Environment: when every sector of a split has at most 32 columns and a working
  * copy within TDVP_JACOBI_RESIDENT_BYTES (read at every split; default and maximum
- * 196608 bytes), each sector's Jacobi runs inside one CTA's shared memory;
- * otherwise all sectors share the cooperative grid-wide kernel
- * (TDVP_JACOBI_RESIDENT_BYTES=0 skips the first form).  With
- * TDVP_JACOBI_CLUSTER=1, splits whose sectors each fit in the shared memory of a
- * cluster of at most 8 CTAs run one thread-block cluster per sector instead of
- * the cooperative kernel (off by default: slower on the measured workloads).
- * All forms give the same result, bit for bit.
+ * 196608 bytes), each sector's Jacobi runs inside one CTA's shared memory.
+ * Otherwise each sector with at most 320 rows runs on a ring of warps in one
+ * thread-block cluster (TDVP_JACOBI_RING=0 turns this form off), and the rest share
+ * the cooperative grid-wide kernel (TDVP_JACOBI_RESIDENT_BYTES=0 skips the first
+ * form).  With TDVP_JACOBI_CLUSTER=1, splits whose sectors each fit in the shared
+ * memory of a cluster of at most 8 CTAs run one cluster per sector with the columns
+ * stationary in distributed shared memory (off by default: slower on the measured
+ * workloads).  All forms give the same result, bit for bit.
  * TDVP_JACOBI_CTAS_PER_SM (1..8, default 4, read at every launch) sets the CTAs
  * per SM of the cooperative Jacobi grid (bounded by its occupancy); results do
- * not depend on it. */
+ * not depend on it.
+ *
+ * Device memory: contexts allocate from the current device's default memory pool
+ * (cudaMallocAsync on their stream).  The first context created on a device in a
+ * process raises that pool's release threshold to TDVP_POOL_KEEP_MB megabytes
+ * (default 4096; a higher threshold already set is kept), so that memory freed
+ * between two synchronisations is reused instead of being returned and mapped
+ * again.  That much freed memory may stay reserved by the process. */
 
 /* Fill *o with the defaults listed above. */
 void tdvp_opts_default(tdvp_opts* o);
