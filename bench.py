@@ -52,8 +52,12 @@ SU2_MATVEC_FLOPS = 3.063e9
 # DRAM bytes per launch of the timed kernels from ncu captures of their current
 # versions (dram__bytes_read.sum + dram__bytes_write.sum); absent = not captured since
 # the kernel last changed.
-HEFF_TRAFFIC = {}
-JACOBI_TRAFFIC = {}
+# BF16x4 H_eff: gemm_exact_kernel<1> (tile images), stage 1 41.8 MB + stage 3 158.5 MB
+# per matvec (`--heff-only`, ncu -k regex:gemm_exact -s 2 -c 2; the per-launch digit
+# splits not included).  FP32 Jacobi: jacobi_ring_kernel<9>, 12.6 MB read, 0 written, on
+# one chi = 4096 split of the bench bond (`--split-only`, ncu -k regex:jacobi_ring).
+HEFF_TRAFFIC = {"bf16x4": 200.3e6}
+JACOBI_TRAFFIC = {"fp32": 12.6e6}
 
 
 def config2_tables():
@@ -373,7 +377,9 @@ def run_engine(args):
         pnote = f"{peak_kind} bf16 burst (BF16X4 issues 10 digit products per complex-embedded MAC)"
     achieved = heff["tflops"]
     roofline_heff = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": HEFF_TRAFFIC.get(args.precision), "traffic_unit": "DRAM bytes per matvec (ncu)",
+                     "traffic": (HEFF_TRAFFIC.get(args.precision)
+                                 if os.environ.get("TDVP_HEFF_IMAGES", "1") != "0" else None),
+                     "traffic_unit": "DRAM bytes per matvec (ncu)",
                      "alg_bytes_per_matvec": heff["stage_alg_bytes"][0] + heff["stage_alg_bytes"][2],
                      "kernel": "grouped block GEMM of H_eff.psi (stages 1+3), chi=4096 bond",
                      "peak_source": pnote, "tensor_pipe_frac_upper": achieved * issued / peak,
@@ -392,7 +398,7 @@ def run_engine(args):
         a = d["jacobi32_flops"] / (d["jacobi32_ms"] * 1e-3) / 1e12
         p32 = alu["fp32_tflops_sustained"]
         roofline = {"bound": "alu", "achieved": a, "peak": p32, "unit": "TFLOP/s", "frac": a / p32,
-                    "traffic": JACOBI_TRAFFIC.get("fp32"),
+                    "traffic": JACOBI_TRAFFIC.get("fp32") if d["jacobi_ring_calls"] > 0 else None,
                     "kernel": ("jacobi_ring_kernel (FP32 preconditioner of the split: rings of warps in "
                                "thread-block clusters)" if d["jacobi_ring_calls"] > 0 else
                                "jacobi_coop_kernel<Svd32Task> (FP32 preconditioner of the split)"),
