@@ -381,8 +381,9 @@ int tdvp_truncate(int nsec, const int* r, const int* mult, const double* sv, dou
  * which every GPU that loads the library holds until the process exits.
  *   - max(p, q) must be <= TDVP_SVD_NOALLOC_MAX, otherwise TDVP_EINVAL.
  *   - The first call on a device (with that device current) performs a one-time
- *     set-up (it looks up the workspace's device address); make that first
- *     call before any stream capture.
+ *     set-up (it looks up the workspace's device address).
+ *   - No call may be made while a stream is capturing: every call copies its
+ *     work lists from host memory and synchronises its stream before returning.
  *   - Every call uses the same workspace, which keeps the last call's contents
  *     (each call rewrites what it reads and clears its convergence flag).  Calls
  *     that overlap on the GPU race on the workspace: serialise them.

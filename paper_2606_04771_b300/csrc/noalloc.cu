@@ -15,8 +15,9 @@
 //   - max(p, q) <= TDVP_SVD_NOALLOC_MAX (512); larger sizes are rejected with
 //     TDVP_EINVAL and a message.
 //   - The first call on a device (with that device current) looks up the
-//     array's device address with cudaGetSymbolAddress and caches it; make that
-//     first call before any stream capture.
+//     array's device address with cudaGetSymbolAddress and caches it.
+//   - No call may be made while a stream is capturing: every call copies its work
+//     lists from host memory and synchronises its stream before returning.
 //   - All calls share the one array and it keeps the last call's contents; every
 //     region is rewritten before it is read and the convergence flag is cleared
 //     at the start of each call.  Calls whose work overlaps on the GPU (for
